@@ -1,0 +1,493 @@
+"""Pins of the FP64 oracle to facts outside itself: hand-computed values, the
+paper's invariant (Suppl. A), its three equivalent forms of the entropy
+gradient (Suppl. B, Sec. 4.4, Algorithm 1), closed forms, library routines
+(scipy rotations, Gauss-Legendre quadrature), brute force, and central finite
+differences.  CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_09277_gb300 import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# Entropy on the weights (Sec. 4.3) and its gradient (Sec. 4.4, Suppl. B)
+# --------------------------------------------------------------------------
+
+def test_golden_two_half():
+    rows = np.loadtxt(os.path.join(GOLDEN, "entropy_two_half.txt"))
+    a = rows[:2]
+    H, d1, d2 = rows[2], rows[3], rows[4]
+    assert oracle.entropy(a) == pytest.approx(H, abs=1e-15)
+    for fn in (oracle.dH_dalpha_direct, oracle.dH_dalpha_closed, oracle.dH_dalpha_alg1):
+        g = fn(a)
+        assert g[0] == pytest.approx(d1, abs=1e-15)
+        assert g[1] == pytest.approx(d2, abs=1e-15)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 30, 120])
+def test_entropy_grad_three_ways_and_fd(n):
+    rng = np.random.default_rng(n)
+    a = rng.uniform(1.0 / 255, 0.99, n)
+    # keep T above t_min like the renderer does
+    a = np.minimum(a, 0.5) if n > 10 else a
+    d = oracle.dH_dalpha_direct(a)
+    c = oracle.dH_dalpha_closed(a)
+    g = oracle.dH_dalpha_alg1(a)
+    scale = np.abs(d).max()
+    assert np.abs(d - c).max() <= 1e-12 * scale
+    assert np.abs(d - g).max() <= 1e-12 * scale
+    for i in range(n):
+        h = 1e-6
+        ap, am = a.copy(), a.copy()
+        ap[i] += h
+        am[i] -= h
+        fd = (oracle.entropy(ap) - oracle.entropy(am)) / (2 * h)
+        assert fd == pytest.approx(d[i], rel=1e-6, abs=1e-8)
+
+
+def test_entropy_uniform_maximum():
+    # weights all equal to 1/(n+1): alpha_i = 1/(n+2-i) gives w_i = 1/(n+1)
+    n = 9
+    a = np.array([1.0 / (n + 1 - i) for i in range(n)])
+    assert oracle.entropy(a) == pytest.approx(math.log(n + 1), rel=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Compositing invariants on a full config-1 view
+# --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def cfg1():
+    scene, cams, targets, prm = scenes.config1()
+    proj = oracle.preprocess(scene, cams[0], prm)
+    lists = oracle.build_lists(proj, cams[0])
+    fwd = oracle.render_fwd(proj, lists, cams[0], prm)
+    return scene, cams, targets, prm, proj, lists, fwd
+
+
+def test_weights_sum_to_unity(cfg1):
+    """Suppl. A: sum_{i<=N} w_i + T_{N+1} = 1 at every pixel.  With every
+    colour set to 1 the composite equals sum w."""
+    scene, cams, targets, prm, proj, lists, fwd = cfg1
+    p1 = dict(proj)
+    p1["P9"] = proj["P9"].copy()
+    p1["P9"][:, 6:9] = 1.0
+    f1 = oracle.render_fwd(p1, lists, cams[0], prm)
+    s = f1["image"][..., 0] + f1["final_T"]
+    assert np.abs(s - 1.0).max() < 1e-12
+    assert (f1["final_T"] >= np.float32(prm["t_min"])).all()
+
+
+def test_entropy_bounds(cfg1):
+    *_, fwd = cfg1
+    H, nb = fwd["entropy"], fwd["nblend"]
+    assert (H >= -1e-15).all()
+    assert (H <= np.log(nb + 1.0) + 1e-12).all()
+    assert (H[nb == 0] == pytest.approx(0.0, abs=1e-15))
+
+
+def test_list_lengths_match_tiles_touched(cfg1):
+    scene, cams, targets, prm, proj, lists, fwd = cfg1
+    ts, ids = lists
+    assert ts[-1] == proj["tiles"].sum()
+    # every Gaussian appears in exactly tiles_touched lists
+    counts = np.bincount(ids, minlength=proj["tiles"].size)
+    assert (counts == proj["tiles"]).all()
+    # each list is sorted by (depth bits, id)
+    dk = proj["depth"].view(np.uint32)
+    for t in range(len(ts) - 1):
+        seg = ids[ts[t]:ts[t + 1]]
+        key = dk[seg].astype(np.uint64) * (1 << 32) + seg.astype(np.uint64)
+        assert (np.diff(key.astype(np.float64)) > 0).all() or len(seg) < 2
+
+
+# --------------------------------------------------------------------------
+# Projection (Sec. 3): closed forms and library routines
+# --------------------------------------------------------------------------
+
+def _one(mu, ls, q, op, sh0=(0.0, 0.0, 0.0)):
+    sh = np.zeros((1, 16, 3), np.float32)
+    sh[0, 0] = sh0
+    return {"means": np.array([mu], np.float32), "log_scales": np.array([ls], np.float32),
+            "quats": np.array([q], np.float32), "opacity_logits": np.array([op], np.float32),
+            "sh": sh, "sh_degree": 0}
+
+
+def test_isotropic_on_axis_closed_form():
+    """A single isotropic Gaussian (scale s0, identity rotation) on the optical
+    axis at depth z, dilation 0: Sigma' = (f s0 / z)^2 I, conic = (z/(f s0))^2 I,
+    r = ceil(3 f s0 / z); C(p) = c min(0.99, sigma exp(-|p - mu'|^2 z^2 / (2 f^2 s0^2)))
+    where that is >= 1/255 inside the rect, H = -w log w - (1 - w) log(1 - w)."""
+    W = H = 64
+    f, z, s0 = 64.0, 3.0, 0.09375  # f s0 / z = 2 px exactly
+    op = 1.5
+    prm = scenes.params(dilation=0.0)
+    cam = scenes.camera(W, H, f)
+    scene = _one((0.0, 0.0, z), [math.log(s0)] * 3, (1.0, 0.0, 0.0, 0.0), op,
+                 sh0=(0.5 * 2 * math.sqrt(math.pi),) * 3)
+    proj = oracle.preprocess(scene, cam, prm)
+    s0 = math.exp(float(scene["log_scales"][0, 0]))  # the stored FP32 log-scale
+    sig_px = f * s0 / z
+    P9 = proj["P9"][0]
+    assert P9[0] == pytest.approx(W / 2, abs=1e-12) and P9[1] == pytest.approx(H / 2, abs=1e-12)
+    assert P9[2] == pytest.approx(1 / sig_px ** 2, rel=1e-12)
+    assert P9[3] == pytest.approx(0.0, abs=1e-14)
+    assert P9[4] == pytest.approx(1 / sig_px ** 2, rel=1e-12)
+    sigma = 1 / (1 + math.exp(-float(np.float32(op))))
+    assert P9[5] == pytest.approx(sigma, rel=1e-14)
+    col = float(scene["sh"][0, 0, 0]) / (2 * math.sqrt(math.pi)) + 0.5  # Y00 sh0 + 0.5 ~ 1
+    assert P9[6:9] == pytest.approx([col] * 3, rel=1e-14)
+    r = math.ceil(3 * sig_px)
+    assert proj["radius"][0] == r
+    lists = oracle.build_lists(proj, cam)
+    fwd = oracle.render_fwd(proj, lists, cam, prm)
+    TX = W // 16
+    x0, y0, x1, y1 = proj["rect"][0]
+    amin, amax = float(np.float32(1 / 255)), float(np.float32(0.99))
+    for v in range(H):
+        for u in range(W):
+            tx, ty = u // 16, v // 16
+            inside = x0 <= tx < x1 and y0 <= ty < y1
+            d2 = (u + 0.5 - W / 2) ** 2 + (v + 0.5 - H / 2) ** 2
+            a = min(amax, sigma * math.exp(-d2 / (2 * sig_px ** 2)))
+            w = a if (inside and a >= amin) else 0.0
+            assert fwd["image"][v, u, 0] == pytest.approx(w * col, abs=1e-14)
+            Hc = 0.0 if w == 0.0 else -w * math.log(w) - (1 - w) * math.log(1 - w)
+            assert fwd["entropy"][v, u] == pytest.approx(Hc, abs=1e-14)
+    assert TX == 4
+
+
+def _rot_scipy(q_wxyz):
+    from scipy.spatial.transform import Rotation
+    w, x, y, z = q_wxyz
+    return Rotation.from_quat([x, y, z, w]).as_matrix()  # scalar-last in scipy
+
+
+def _pinhole(cam, X):
+    wtc = cam["world_to_cam"].astype(np.float64)
+    t = wtc[:, :3] @ X + wtc[:, 3]
+    return np.array([cam["fx"] * t[0] / t[2] + cam["cx"], cam["fy"] * t[1] / t[2] + cam["cy"]])
+
+
+def test_projection_matches_library_linearisation():
+    """EWA (Sec. 3): Sigma' = J Sigma J^T + dilation I, with J the Jacobian of
+    the pinhole map at the mean (here by central differences of the pinhole
+    map itself) and Sigma = R S S^T R^T with R from scipy's quaternion
+    rotation; conic = Sigma'^-1; opacity = scipy.special.expit(logit)."""
+    from scipy.special import expit
+    rng = np.random.default_rng(5)
+    pos = np.array([0.7, -0.4, -1.0])
+    cam = scenes.camera(200, 150, 180.0, scenes.look_at(pos, (0.1, 0.2, 3.0)), pos)
+    prm = scenes.params()
+    for _ in range(20):
+        mu = np.array([rng.uniform(-0.5, 0.7), rng.uniform(-0.3, 0.6), rng.uniform(2.5, 4.0)])
+        ls = rng.normal(-3.0, 0.5, 3)
+        q = rng.standard_normal(4)
+        op = rng.normal()
+        sc = _one(mu, ls, q, op)
+        proj = oracle.preprocess(sc, cam, prm)
+        X = sc["means"][0].astype(np.float64)
+        Jn = np.zeros((2, 3))
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = 1e-6
+            Jn[:, k] = (_pinhole(cam, X + e) - _pinhole(cam, X - e)) / 2e-6
+        qq = sc["quats"][0].astype(np.float64)
+        R = _rot_scipy(qq / np.linalg.norm(qq))
+        S = np.diag(np.exp(sc["log_scales"][0].astype(np.float64)))
+        Sig = R @ S @ S.T @ R.T
+        S2 = Jn @ Sig @ Jn.T + float(np.float32(0.3)) * np.eye(2)
+        K = np.linalg.inv(S2)
+        P9 = proj["P9"][0]
+        assert P9[0:2] == pytest.approx(_pinhole(cam, X), rel=1e-12)
+        assert P9[2] == pytest.approx(K[0, 0], rel=1e-7)
+        assert P9[3] == pytest.approx(K[0, 1], rel=1e-6, abs=1e-9)
+        assert P9[4] == pytest.approx(K[1, 1], rel=1e-7)
+        assert P9[5] == pytest.approx(expit(float(sc["opacity_logits"][0])), rel=1e-14)
+        # radius: 3 sqrt of the larger eigenvalue, rounded up
+        lam = np.linalg.eigvalsh(S2).max()
+        assert proj["radius"][0] == math.ceil(3 * math.sqrt(lam))
+
+
+def test_near_plane_culls():
+    cam = scenes.camera(64, 64, 64.0)
+    prm = scenes.params()
+    sc = _one((0.0, 0.0, 0.1999), [-3.0] * 3, (1, 0, 0, 0), 0.0)
+    assert oracle.preprocess(sc, cam, prm)["tiles"][0] == 0
+    sc = _one((0.0, 0.0, 0.25), [-3.0] * 3, (1, 0, 0, 0), 0.0)
+    assert oracle.preprocess(sc, cam, prm)["tiles"][0] > 0
+
+
+def test_depth_key_is_fp32_of_fp64_depth():
+    pos = np.array([0.3, -0.2, -0.5])
+    cam = scenes.camera(64, 64, 64.0, scenes.look_at(pos, (0.0, 0.1, 3.0)), pos)
+    sc, _, _, prm = scenes.tiny_scene(8, seed=3, width=64, height=64)
+    proj = oracle.preprocess(sc, cam, prm)
+    R = cam["world_to_cam"].astype(np.float64)
+    m = sc["means"].astype(np.float64)
+    tz = ((R[2, 0] * m[:, 0] + R[2, 1] * m[:, 1]) + R[2, 2] * m[:, 2]) + R[2, 3]
+    assert (proj["depth"] == tz.astype(np.float32)).all()
+
+
+# --------------------------------------------------------------------------
+# Spherical harmonics (Sec. 3: colour in SH up to degree 3)
+# --------------------------------------------------------------------------
+
+def test_sh_orthonormal_by_quadrature():
+    """int_S2 Y_i Y_j = delta_ij: Gauss-Legendre in cos(theta) (exact for
+    polynomials up to degree 2n-1) times a uniform grid in phi (exact for
+    trigonometric polynomials below the grid size)."""
+    zs, wz = np.polynomial.legendre.leggauss(12)
+    nphi = 16
+    phis = 2 * np.pi * np.arange(nphi) / nphi
+    dirs, wts = [], []
+    for z, w in zip(zs, wz):
+        r = math.sqrt(1 - z * z)
+        for ph in phis:
+            dirs.append((r * math.cos(ph), r * math.sin(ph), z))
+            wts.append(w * 2 * np.pi / nphi)
+    Y = oracle.sh_basis(3, np.array(dirs))
+    G = (Y * np.array(wts)[:, None]).T @ Y
+    assert np.abs(G - np.eye(16)).max() < 1e-12
+
+
+def test_sh_harmonic_and_homogeneous():
+    """Each basis function is a homogeneous harmonic polynomial of its degree:
+    Y(2x) = 2^l Y(x) and its Laplacian (second central differences, exact for
+    cubics up to rounding) vanishes."""
+    rng = np.random.default_rng(0)
+    degs = [0] + [1] * 3 + [2] * 5 + [3] * 7
+    for _ in range(10):
+        x = rng.standard_normal(3)
+        Y1 = oracle.sh_basis(3, x)[0]
+        Y2 = oracle.sh_basis(3, 2 * x)[0]
+        assert Y2 == pytest.approx(Y1 * 2.0 ** np.array(degs), rel=1e-12, abs=1e-14)
+        h = 1e-2
+        lap = -6 * Y1
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = h
+            lap = lap + oracle.sh_basis(3, x + e)[0] + oracle.sh_basis(3, x - e)[0]
+        assert np.abs(lap / h ** 2).max() < 1e-8
+    assert oracle.sh_basis(0, np.array([0.0, 0.0, 1.0]))[0, 0] == pytest.approx(
+        1 / (2 * math.sqrt(math.pi)), rel=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Tile lists and compositing against a per-pixel brute force
+# --------------------------------------------------------------------------
+
+def _brute_force(proj, cam, prm):
+    """Per pixel: every Gaussian whose rect covers the pixel's tile, sorted by
+    (depth, id), composited front to back (Sec. 3)."""
+    W, H = cam["width"], cam["height"]
+    amax, amin, tmin = (float(np.float32(prm[k])) for k in ("alpha_max", "alpha_min", "t_min"))
+    P9, rect, tiles, depth = proj["P9"], proj["rect"], proj["tiles"], proj["depth"]
+    img = np.zeros((H, W, 3))
+    Tf = np.ones((H, W))
+    Hm = np.zeros((H, W))
+    last = np.zeros((H, W), np.int32)
+    for v in range(H):
+        for u in range(W):
+            tx, ty = u // 16, v // 16
+            cand = [i for i in range(len(tiles)) if tiles[i] > 0 and rect[i, 0] <= tx < rect[i, 2]
+                    and rect[i, 1] <= ty < rect[i, 3]]
+            cand.sort(key=lambda i: (depth[i], i))
+            T, swl = 1.0, 0.0
+            for pos, i in enumerate(cand):
+                g = P9[i]
+                dx, dy = u + 0.5 - g[0], v + 0.5 - g[1]
+                a = min(amax, g[5] * math.exp(-0.5 * (g[2] * dx * dx + 2 * g[3] * dx * dy
+                                                        + g[4] * dy * dy)))
+                if a < amin:
+                    continue
+                if T * (1 - a) < tmin:
+                    break
+                w = a * T
+                img[v, u] += w * g[6:9]
+                swl += w * math.log(w)
+                T *= 1 - a
+                last[v, u] = pos + 1
+            Tf[v, u] = T
+            Hm[v, u] = -(swl + T * math.log(T))
+    return img, Tf, Hm, last
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tiled_equals_brute_force(seed):
+    scene, cams, _, prm = scenes.tiny_scene(8, seed=seed, width=48, height=40)
+    scene["opacity_logits"][:] = 3.0  # long enough to reach the T stop
+    cam = cams[0]
+    proj = oracle.preprocess(scene, cam, prm)
+    lists = oracle.build_lists(proj, cam)
+    fwd = oracle.render_fwd(proj, lists, cam, prm)
+    img, Tf, Hm, last = _brute_force(proj, cam, prm)
+    assert np.abs(fwd["image"] - img).max() < 1e-13
+    assert np.abs(fwd["final_T"] - Tf).max() < 1e-13
+    assert np.abs(fwd["entropy"] - Hm).max() < 1e-13
+    assert (fwd["last"] == last).all()
+
+
+# --------------------------------------------------------------------------
+# Gradients: central finite differences of the whole FP64 loss
+# --------------------------------------------------------------------------
+
+def _loss_and_state(scene, cams, targets, prm):
+    L, views, _, _ = oracle.step(scene, cams, targets, prm, scenes.GAMMA, with_grad=False)
+    ints = [np.concatenate([v["proj"]["rect"].ravel(), v["fwd"]["last"].ravel(),
+                            v["fwd"]["nblend"].ravel(), v["fwd"]["neval"].ravel(),
+                            v["proj"]["clamped"].ravel()]) for v in views]
+    return L, ints
+
+
+def _fd_check(scene, cams, targets, prm, rel_tol=2e-6):
+    L0, grads, _ = None, None, None
+    L0, views, grads, _ = oracle.step(scene, cams, targets, prm, scenes.GAMMA)
+    margins = min(v["fwd"]["margin"].min() for v in views)
+    assert margins > 1e-4, "scene too close to a threshold for finite differences"
+    checked = skipped = 0
+    worst = 0.0
+    for key in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        arr = scene[key]
+        K = (scene["sh_degree"] + 1) ** 2
+        idxs = list(np.ndindex(arr.shape))
+        if key == "sh":
+            idxs = [ix for ix in idxs if ix[1] < K]
+        for ix in idxs:
+            x0 = float(arr[ix])
+            h = 1e-6 * max(1.0, abs(x0))
+            vals = []
+            ints = []
+            for s in (+1, -1):
+                sc = {k: (np.array(v, np.float64) if isinstance(v, np.ndarray) else v)
+                      for k, v in scene.items()}
+                sc[key][ix] = x0 + s * h
+                Ls, ii = _loss_and_state(sc, cams, targets, prm)
+                vals.append(Ls)
+                ints.append(ii)
+            if any((a != b).any() for a, b in zip(ints[0], ints[1])):
+                skipped += 1
+                continue
+            fd = (vals[0] - vals[1]) / (2 * h)
+            an = grads[key][ix]
+            err = abs(fd - an)
+            tol = rel_tol * max(abs(fd), abs(an)) + 1e-9
+            worst = max(worst, err / (abs(fd) + 1e-12))
+            assert err <= tol, (key, ix, fd, an)
+            checked += 1
+    assert skipped <= 0.05 * (checked + skipped)
+    return checked
+
+
+@pytest.mark.parametrize("seed,deg", [(0, 0), (1, 3), (2, 3)])
+def test_full_gradient_matches_finite_differences(seed, deg):
+    scene, cams, targets, prm = scenes.tiny_scene(6, seed=seed, width=32, height=32,
+                                                  sh_degree=deg)
+    assert _fd_check(scene, cams, targets, prm) > 50
+
+
+def test_gradient_fd_rotated_camera_and_fov_clamp():
+    """A rotated camera, and one wide Gaussian whose mean lies outside the
+    clamped field of view (x/z clamp active) but whose footprint still
+    reaches the image."""
+    scene, _, _, prm = scenes.tiny_scene(5, seed=4, width=32, height=32, sh_degree=1)
+    pos = np.array([0.2, -0.1, -0.3])
+    cam = scenes.camera(32, 32, 32.0, scenes.look_at(pos, (0.0, 0.0, 3.0)), pos)
+    # Gaussian 0: far to the side, large: x/z = 0.9 > 1.3 * 16/32
+    wtc = cam["world_to_cam"].astype(np.float64)
+    Rw = wtc[:, :3]
+    p_cam = np.array([2.7, 0.0, 3.0])
+    scene["means"][0] = (Rw.T @ (p_cam - wtc[:, 3])).astype(np.float32)
+    scene["log_scales"][0] = [-0.5, -0.7, -0.6]
+    targets = scenes.noise_targets([cam], 9)
+    proj = oracle.preprocess(scene, cam, prm)
+    assert proj["tiles"][0] > 0
+    assert _fd_check(scene, [cam], targets, prm) > 40
+
+
+def test_render_bwd_against_fd_of_2d_attributes(cfg1):
+    """The compositing gradient alone (Sec. 4.4 closed forms + Suppl. C chain)
+    against central differences in the 2D attributes of a small view."""
+    scene, cams, targets, prm = scenes.tiny_scene(7, seed=11, width=32, height=32)
+    cam = cams[0]
+    proj = oracle.preprocess(scene, cam, prm)
+    lists = oracle.build_lists(proj, cam)
+    fwd = oracle.render_fwd(proj, lists, cam, prm)
+    L, dC, dH = oracle.loss(fwd["image"], fwd["entropy"], targets[0], scenes.GAMMA)
+    g9 = oracle.render_bwd(proj, lists, cam, prm, dC, dH)
+    for i in range(7):
+        if proj["tiles"][i] == 0:
+            continue
+        for k in range(9):
+            h = 1e-6 * max(1.0, abs(proj["P9"][i, k]))
+            Ls = []
+            for s in (1, -1):
+                p2 = dict(proj)
+                p2["P9"] = proj["P9"].copy()
+                p2["P9"][i, k] += s * h
+                f2 = oracle.render_fwd(p2, lists, cam, prm)
+                # the L1 sign pattern and decisions must not move
+                assert (f2["last"] == fwd["last"]).all()
+                Ls.append(oracle.loss(f2["image"], f2["entropy"], targets[0], scenes.GAMMA)[0])
+            fd = (Ls[0] - Ls[1]) / (2 * h)
+            assert fd == pytest.approx(g9[i, k], rel=1e-5, abs=1e-9), (i, k)
+
+
+# --------------------------------------------------------------------------
+# Scale reset (Sec. 4.2) and loss (Sec. 3, Sec. 4.3)
+# --------------------------------------------------------------------------
+
+def test_scale_reset_multiplies_scales():
+    rng = np.random.default_rng(0)
+    ls = rng.normal(-4, 1, 300).astype(np.float32)
+    for zeta in (0.2, 0.5, 0.9):
+        out = oracle.scale_reset(ls, zeta)
+        ref = zeta * np.exp(ls.astype(np.float64))
+        assert np.abs(np.exp(out) / ref - 1).max() < 4 * np.finfo(np.float64).eps
+
+
+def test_loss_definition():
+    rng = np.random.default_rng(0)
+    img = rng.random((5, 7, 3))
+    ent = rng.random((5, 7))
+    tgt = rng.random((5, 7, 3)).astype(np.float32)
+    L, dC, dH = oracle.loss(img, ent, tgt, 0.015, 0.5)
+    M = 35
+    ref = 0.5 * (np.abs(img - tgt).sum() / (3 * M) + 0.015 * ent.sum() / M)
+    assert L == pytest.approx(ref, rel=1e-14)
+    assert dC == pytest.approx(0.5 * np.sign(img - tgt) / (3 * M), rel=1e-15)
+    assert dH == pytest.approx(np.full((5, 7), 0.5 * 0.015 / M), rel=1e-15)
+
+
+def test_fov_clamp_linearises_at_the_clamped_direction():
+    """Outside the clamped field of view the EWA Jacobian is the pinhole
+    Jacobian at the camera-space point whose x/z (y/z) is clamped to
+    fov_clamp * (W/2)/fx ((H/2)/fy); the 2D mean itself is not clamped."""
+    cam = scenes.camera(64, 48, 64.0)
+    prm = scenes.params()
+    lim_x = float(np.float32(1.3)) * 32 / 64.0
+    for mu in ([2.4, 0.3, 3.0], [-2.7, -0.2, 3.5]):
+        sc = _one(mu, [-0.3, -0.9, -0.6], (0.9, 0.2, -0.3, 0.1), 0.0)
+        proj = oracle.preprocess(sc, cam, prm)
+        X = sc["means"][0].astype(np.float64)
+        Xc = X.copy()
+        Xc[0] = np.sign(X[0]) * lim_x * X[2]
+        Jn = np.zeros((2, 3))
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = 1e-6
+            Jn[:, k] = (_pinhole(cam, Xc + e) - _pinhole(cam, Xc - e)) / 2e-6
+        qq = sc["quats"][0].astype(np.float64)
+        R = _rot_scipy(qq / np.linalg.norm(qq))
+        S = np.diag(np.exp(sc["log_scales"][0].astype(np.float64)))
+        S2 = Jn @ R @ S @ S @ R.T @ Jn.T + float(np.float32(0.3)) * np.eye(2)
+        K = np.linalg.inv(S2)
+        P9 = proj["P9"][0]
+        assert P9[0:2] == pytest.approx(_pinhole(cam, X), rel=1e-12)
+        assert P9[[2, 3, 4]] == pytest.approx([K[0, 0], K[0, 1], K[1, 1]], rel=1e-6)
