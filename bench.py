@@ -1,0 +1,432 @@
+#!/usr/bin/env python
+"""Benchmark of the differentiable tile rasterizer with the entropy term:
+one step = projection, per-tile list construction (key duplication and radix
+sort), front-to-back blending with the weight entropy, the L1 + entropy loss,
+the reverse-order adjoint back to every Gaussian parameter, and the scale
+reset, over one batch of synthetic inputs resident in HBM.
+
+Default workload (N=1): 1,000,000 Gaussians from 64 anisotropic clusters,
+SH degree 3, one 1237x822 view (the scene-scale configuration).
+Metric: blended Gaussian-pixels per second over the whole forward + backward
+step (higher is better); ms per step is reported alongside.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs an independent replica on its own seeded
+scene (the path shards by view/scene and needs no data exchange); the
+barrier and the max-over-ranks time are timing plumbing only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import signal
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd ms/iter and blended Gaussian-pixels/s, batched+mixed vs plain at stated err"
+UNIT = "blended Gaussian-pixels/s"
+L2_BYTES = 129 * 1024 * 1024
+
+# Algorithmic FP32 operation counts per pair (add/mul/min/transcendental = 1,
+# fused multiply-add = 2), from the per-pair formulas of the blending and its
+# adjoint:
+#   forward:  10 per evaluated pair (pixel offset 2, base-2 exponent 8)
+#             +14 per blended pair (exp, clamp, 1-alpha, T(1-alpha), w,
+#                 colour 3 FMA, log, entropy FMA)
+#   backward: 10 per evaluated pair, +72 per blended pair (transmittance
+#             recovery 8, colour part of dL/dalpha 14, entropy part 7, colour
+#             gradient 3, S and R updates 9, alpha->sigma,d 2, conic 12,
+#             mean 8, per-pixel summation of the 9 gradients 9)
+FWD_EVAL, FWD_BLEND = 10, 14
+BWD_EVAL, BWD_BLEND = 10, 72
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5"])
+    ap.add_argument("--attr", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--persistent", type=int, default=0,
+                    help="CTAs of the persistent list-length-ordered launch (0 = one CTA per tile)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-band-rows", type=int, default=2,
+                    help="tile rows of the view the CPU oracle sample renders")
+    return ap.parse_args()
+
+
+def workload(name, seed):
+    from paper_2603_09277_gb300 import scenes
+    if name == "cfg1":
+        return scenes.config1(seed=seed), "cfg1: 10k Gaussians, 256x256, SH0, fwd+bwd L1+entropy"
+    if name == "cfg2":
+        return scenes.config2(seed=seed), ("cfg2: 1M Gaussians (64 clusters, r=10), SH3, "
+                                           "one 1237x822 view, fwd+bwd L1+entropy")
+    if name == "cfg3":
+        return scenes.config3(seed=seed), ("cfg3: 3M Gaussians, 8 views {3x309x205, 3x618x411, "
+                                           "2x1237x822}, fwd+bwd L1+entropy")
+    if name == "cfg4":
+        return scenes.config4(seed=seed), "cfg4: 10k Gaussians, 256x256, k=0"
+    return scenes.config5(seed=seed), "cfg5: 3M Gaussians, 1920x1080, SH0, fwd+bwd L1+entropy"
+
+
+# ---------------------------------------------------------------------------
+# Clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i] == "Active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])),
+                "sm_max_mhz": float(max(r[1] for r in rows)), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def oracle_sample(scene, cams, targets, prm, gamma, band_rows):
+    """Runs the FP64 oracle's whole pipeline on a band of `band_rows` tile
+    rows through the middle of view 0: projection of every Gaussian, the tile
+    lists, forward and backward on the band's pixels, and the projection
+    adjoint of every Gaussian that received a gradient.  Returns
+    (blended pairs, seconds, description)."""
+    import oracle
+    cam = cams[0]
+    W, H = cam["width"], cam["height"]
+    TY = (H + 15) // 16
+    t_start = max(0, TY // 2 - band_rows // 2)
+    rows = np.arange(H) // 16
+    band = (rows >= t_start) & (rows < t_start + band_rows)
+    mask = np.repeat(band[:, None], W, axis=1)
+    t0 = time.perf_counter()
+    proj = oracle.preprocess(scene, cam, prm)
+    lists = oracle.build_lists(proj, cam)
+    fwd = oracle.render_fwd(proj, lists, cam, prm, mask=mask)
+    M = W * H
+    dC = np.where(fwd["image"] - targets[0] > 0, 1.0, -1.0) / (3 * M)
+    dC[~mask] = 0
+    dH = np.where(mask, gamma / M, 0.0)
+    g9 = oracle.render_bwd(proj, lists, cam, prm, dC, dH, mask=mask)
+    touched = (np.abs(g9).sum(1) > 0).astype(np.uint8)
+    oracle.preprocess_bwd(scene, cam, prm, g9, gmask=touched)
+    dt = time.perf_counter() - t0
+    nb = int(fwd["nblend"][mask].sum())
+    desc = ("FP64 oracle, %d tile rows (%d of %d pixels) of view 0: projection of all %d "
+            "Gaussians, lists, fwd+bwd on the band, projection adjoint of the %d Gaussians "
+            "with a gradient" % (band_rows, int(mask.sum()), M, scene["means"].shape[0],
+                                 int(touched.sum())))
+    return nb, dt, desc
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    (scene, cams, targets, prm), wl = workload(args.config, 0)
+    from paper_2603_09277_gb300 import scenes
+    for _ in range(args.warmup):
+        oracle_sample(scene, cams, targets, prm, scenes.GAMMA, 1)
+    nbs, dts = [], []
+    desc = ""
+    for _ in range(args.steps):
+        nb, dt, desc = oracle_sample(scene, cams, targets, prm, scenes.GAMMA, 1)
+        nbs.append(nb)
+        dts.append(dt)
+    value = sum(nbs) / sum(dts)
+    cores = oracle.num_threads()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * np.mean(dts),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl, "sample": "1 tile row band per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def traffic_from_profiles(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was captured from the current render source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        data = json.load(open(path))
+    except ValueError:
+        return None
+    src = os.path.join(ROOT, "paper_2603_09277_gb300", "csrc", "render.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    ent = data.get(kernel)
+    if not ent or ent.get("render_cu_sha256_16") != h:
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2603_09277_gb300 import gs, scenes
+    from paper_2603_09277_gb300.rasterize import Rasterizer, scene_to_device, targets_to_device
+
+    (scene, cams, targets, prm), wl = workload(args.config, rank)
+    N = scene["means"].shape[0]
+    r = Rasterizer(cams, prm, N, attr_dtype=args.attr, device=dev, persistent=args.persistent)
+    p = scene_to_device(scene, dev)
+    tgt = targets_to_device(targets, dev)
+    ls_work = p["log_scales"].clone()  # the scale reset writes a working copy
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    gamma = scenes.GAMMA
+
+    def step(sync, ev=None):
+        e = ev if ev is not None else [None] * 8
+        if e[0] is not None:
+            e[0].record()
+        r.preprocess(p)
+        if e[1] is not None:
+            e[1].record()
+        r.bin_sort(sync=sync)
+        if e[2] is not None:
+            e[2].record()
+        r.render_fwd(stats=True, events=(e[5], e[6]) if e[5] is not None else None)
+        r.loss(tgt, gamma)
+        if e[3] is not None:
+            e[3].record()
+        r.render_bwd(p, events=(e[7], e[4]) if e[7] is not None else None)
+        gs.gs_scale_reset(ls_work, 0.2)
+        if e[4] is not None:
+            pass
+
+    # warm-up with host-synchronised pair counting (sizes the pair buffers)
+    for _ in range(max(args.warmup, 3)):
+        step(True)
+    torch.cuda.synchronize()
+    # workload statistics (outside the timed region)
+    P = r.num_pairs
+    nb_step = int(r.stats[0].item())
+    ne_step = int(r.stats[1].item())
+    bwd_eval = int(r.last_idx.sum().item())
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(K)]
+    for e in evs:  # materialise the event handles
+        for x in e:
+            x.record()
+    torch.cuda.synchronize()
+    launches0 = gs.gs_kernel_launches()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.fill_(float(k))  # L2 flush between timed steps (outside the step events)
+        e = evs[k]
+        e[0].record()
+        r.preprocess(p)
+        e[1].record()
+        r.bin_sort(sync=False)
+        e[2].record()
+        r.render_fwd(stats=False, events=(e[5], e[6]))
+        r.loss(tgt, gamma)
+        e[3].record()
+        r.render_bwd(p, events=(e[7], e[8]))
+        gs.gs_scale_reset(ls_work, 0.2)
+        e[4].record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = gs.gs_kernel_launches() - launches0
+    status = int(r.status_dev.item())
+    if status != 0:
+        raise RuntimeError("pair capacity overflow in the timed region (status %d)" % status)
+    step_ms = [e[0].elapsed_time(e[4]) for e in evs]
+    phase = {
+        "preprocess": float(np.mean([e[0].elapsed_time(e[1]) for e in evs])),
+        "bin_sort": float(np.mean([e[1].elapsed_time(e[2]) for e in evs])),
+        "render_fwd_kernel": float(np.mean([e[5].elapsed_time(e[6]) for e in evs])),
+        "render_fwd+loss": float(np.mean([e[2].elapsed_time(e[3]) for e in evs])),
+        "render_bwd_kernel": float(np.mean([e[7].elapsed_time(e[8]) for e in evs])),
+        "render_bwd+preprocess_bwd+reset": float(np.mean([e[3].elapsed_time(e[4]) for e in evs])),
+    }
+    t_total = sum(step_ms) / 1000.0
+    if world > 1:
+        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+        nbt = torch.tensor([nb_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(nbt)
+        nb_all = float(nbt.item())
+    else:
+        nb_all = float(nb_step)
+    value = nb_all * K / t_total
+    ms = 1000.0 * t_total / K
+
+    # roofline of the dominant kernel (blending forward or backward)
+    fwd_ms, bwd_ms = phase["render_fwd_kernel"], phase["render_bwd_kernel"]
+    peak = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 TFLOP/s at the maximum SM clock
+    if bwd_ms >= fwd_ms:
+        kname, kms = "render_bwd_kernel", bwd_ms
+        flops = BWD_EVAL * bwd_eval + BWD_BLEND * nb_step
+    else:
+        kname, kms = "render_fwd_kernel", fwd_ms
+        flops = FWD_EVAL * ne_step + FWD_BLEND * nb_step
+    achieved = flops / (kms / 1000.0) / 1e12
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic_from_profiles(kname),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "flops_per_launch": flops}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.as_tensor(scene[k], dtype=torch.float32).contiguous().pin_memory()
+                for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+        host_tgt = torch.cat([torch.as_tensor(t).reshape(-1, 3) for t in targets]).pin_memory()
+        out_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+        out_g = {k: torch.empty_like(v).pin_memory() for k, v in host.items()}
+        h2d = sum(v.numel() * 4 for v in host.values()) + host_tgt.numel() * 4
+        d2h = 8 + sum(v.numel() * 4 for v in out_g.values())
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_ms = []
+        for k in range(K + 1):
+            flush.fill_(float(k))
+            a.record()
+            for kk, v in host.items():
+                p[kk].copy_(v, non_blocking=True)
+            tgt.copy_(host_tgt, non_blocking=True)
+            r.preprocess(p)
+            r.bin_sort(sync=False)
+            r.render_fwd()
+            r.loss(tgt, gamma)
+            r.render_bwd(p)
+            gs.gs_scale_reset(ls_work, 0.2)
+            out_loss.copy_(r.loss_dev, non_blocking=True)
+            for kk in out_g:
+                out_g[kk].copy_(r.grads[kk][:out_g[kk].shape[0]], non_blocking=True)
+            b.record()
+            b.synchronize()
+            if k > 0:
+                e2e_ms.append(a.elapsed_time(b))
+        t_e2e = sum(e2e_ms) / 1000.0
+        if world > 1:
+            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": nb_all * K / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000.0 * t_e2e / K}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        nb_c, dt_c, desc = oracle_sample(scene, cams, targets, prm, gamma, args.cpu_band_rows)
+        cpu = {"value": nb_c / dt_c, "unit": UNIT, "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": desc, "seconds": dt_c}
+
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.attr, "data": "synthetic",
+            "config": {"workload": wl, "N": N, "views": len(cams), "pairs": P,
+                       "blended_pairs": nb_step, "evaluated_pairs": ne_step,
+                       "bwd_evaluated_pairs": bwd_eval, "attr_dtype": args.attr,
+                       "launch": ("persistent %d CTAs, list-length queue" % args.persistent
+                                  if args.persistent else "one CTA per 16x16 tile"),
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "phases_ms": phase,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,250 @@
+/*
+ * gs.h -- C ABI of libgs: the differentiable 16x16-tile Gaussian rasterizer
+ * with the entropy term on blending weights and the periodic scale reset of
+ * "Speeding Up the Learning of 3D Gaussians with Much Shorter Gaussian Lists"
+ * (arXiv 2603.09277), built for NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named in a struct or argument as "device" are CUDA device
+ *    memory owned by the caller (the library never frees them).  "host"
+ *    pointers are ordinary host memory read during the call.
+ *  - Every call enqueues work on `stream` (a cudaStream_t; NULL is the legacy
+ *    default stream) and returns without synchronising, except gs_bin_sort
+ *    when `num_pairs_host` is non-NULL (it then waits for the pair count).
+ *  - Return value: GS_OK (0) or a negative GS_ERR_* code.  Argument errors are
+ *    detected on the host before anything is enqueued.  GS_ERR_CUDA keeps the
+ *    cudaError_t text for gs_last_error_string().
+ *  - Outputs are fully overwritten, gradients included (the calls zero them).
+ *  - Views: V cameras of possibly different sizes.  Per-(view, Gaussian)
+ *    arrays have V*N rows, row v*N + g.  Per-pixel arrays hold the views back
+ *    to back, view v starting at pixel offset sum_{u<v} W_u H_u, row-major
+ *    within a view.  Tiles are numbered globally: view v's tile (tx, ty) is
+ *    tile_offset_v + ty * TX_v + tx with TX_v = ceil(W_v / 16),
+ *    TY_v = ceil(H_v / 16), tile_offset_v = sum_{u<v} TX_u TY_u.
+ *  - Pixel (x, y) is sampled at (x + 0.5, y + 0.5); the background is black.
+ *
+ * Error behaviour on the device: no kernel traps or asserts.  Capacity
+ * overflow of the pair buffers is reported through a device status word
+ * (GS_ERR_CAPACITY) together with the required pair count.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* gs_stream; /* cudaStream_t */
+
+enum gs_status {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = -1,
+    GS_ERR_CUDA = -2,
+    GS_ERR_CAPACITY = -3,
+    GS_ERR_TIMEOUT = -4,
+    GS_ERR_UNSUPPORTED = -5
+};
+
+/* Staging precision of the per-Gaussian render records (Gaussian attributes
+ * only; exponent, transmittance and every accumulation stay FP32). */
+enum gs_attr_dtype { GS_ATTR_F32 = 0, GS_ATTR_F16 = 1, GS_ATTR_BF16 = 2 };
+
+#define GS_TILE 16
+#define GS_MAX_VIEWS 64
+#define GS_SH_COEFFS_MAX 16
+
+/* Pinhole camera (Sec. 3: "for rendering from a given camera viewpoint").
+ * world_to_cam: row-major 3x4 [R | t], camera x right, y down, z forward.
+ * cam_pos: camera centre in world space (used for the SH view direction). */
+typedef struct {
+    int width, height;
+    float fx, fy, cx, cy;
+    float world_to_cam[12];
+    float cam_pos[3];
+} gs_camera;
+
+/* Thresholds and projection constants.  The paper states none of them; the
+ * defaults follow the 3DGS family it builds on:
+ *   alpha_max 0.99 (alpha clamp), alpha_min 1/255 (entries below are
+ *   skipped), t_min 1e-4 (the walk stops before blending an entry that would
+ *   leave T < t_min), dilation 0.3 (added to the 2D covariance diagonal),
+ *   near_z 0.2, fov_clamp 1.3 (x/z and y/z clamp of the EWA Jacobian in
+ *   units of the half field of view). */
+typedef struct {
+    float alpha_max, alpha_min, t_min, dilation, near_z, fov_clamp;
+    int sh_degree;  /* degree in use, 0..3 */
+    int sh_stride;  /* SH coefficients stored per Gaussian, >= (sh_degree+1)^2, <= 16 */
+    int attr_dtype; /* enum gs_attr_dtype */
+} gs_params;
+
+/* Projected per-(view, Gaussian) attributes, V*N rows, device memory. */
+typedef struct {
+    void* records;           /* required: gs_record_bytes(attr_dtype) per row, 16-B aligned */
+    float* depth;            /* required [V*N]: FP32 camera-space depth (0 when culled) */
+    int* rect;               /* required [V*N][4]: tile rect x0, y0, x1, y1 (half-open) */
+    unsigned* tiles_touched; /* required [V*N]: (x1-x0)(y1-y0), 0 when culled */
+    int* radius;             /* optional [V*N]: ceil(3 sqrt(lambda_max)) px */
+    float* mean2d;           /* optional [V*N][2] */
+    float* conic_opacity;    /* optional [V*N][4]: a, b, c, sigma; d = -1/2(a dx^2 + 2b dx dy + c dy^2) */
+    float* rgb;              /* optional [V*N][3]: clamped SH colour */
+} gs_proj;
+
+/* Optional launch controls of the render calls (NULL = defaults). */
+typedef struct {
+    const unsigned* tile_order;    /* device [total_tiles]: tile processing order, e.g. from
+                                      gs_tile_queue (longest list first); NULL = natural order */
+    unsigned* work_counter;        /* device [1]: work-claim counter for a persistent launch,
+                                      reset by the call on the stream; required if ctas > 0 */
+    int ctas;                      /* 0: one CTA per tile; > 0: persistent grid of that many
+                                      CTAs claiming tiles from tile_order through work_counter */
+    unsigned long long* stats;     /* device [2] (optional): += blended pairs, += evaluated pairs
+                                      (forward only) */
+    void* ev_begin;                /* optional cudaEvent_t recorded on the stream right before the
+                                      blending kernel (for live per-kernel timing) */
+    void* ev_end;                  /* optional cudaEvent_t recorded right after it */
+} gs_launch;
+
+/* ---------------------------------------------------------------------- */
+/* Sizes and helpers                                                       */
+/* ---------------------------------------------------------------------- */
+
+/* Bytes of one render record for the given staging dtype (48 for F32, 32 for
+ * F16/BF16); -1 for an unknown dtype. */
+int gs_record_bytes(int attr_dtype);
+
+/* Total number of 16x16 tiles over the V views (host cams), or -1. */
+long long gs_total_tiles(const gs_camera* cams_host, int V);
+
+/* Total pixels over the V views, or -1. */
+long long gs_total_pixels(const gs_camera* cams_host, int V);
+
+/* Workspace bytes that gs_bin_sort needs for n_rows = V*N projected rows, a
+ * pair capacity and a tile count. */
+size_t gs_bin_sort_workspace_size(long long n_rows, long long pair_capacity, long long total_tiles);
+
+/* Workspace bytes that gs_loss_l1_entropy needs for `total_pixels` pixels. */
+size_t gs_loss_workspace_size(long long total_pixels);
+
+/* Workspace bytes that gs_tile_queue needs. */
+size_t gs_tile_queue_workspace_size(long long total_tiles);
+
+const char* gs_status_string(int status);
+/* Text of the last CUDA error seen by this thread's calls ("" if none). */
+const char* gs_last_error_string(void);
+/* Library build string (architecture and version). */
+const char* gs_version(void);
+/* Number of kernels this process has launched through libgs so far (all
+ * threads, all devices); for launch accounting. */
+unsigned long long gs_kernel_launches(void);
+
+/* ---------------------------------------------------------------------- */
+/* Hot path                                                                */
+/* ---------------------------------------------------------------------- */
+
+/* Projection of every Gaussian into every view (Sec. 3, Background: the
+ * 3D covariance Sigma = R S S^T R^T from the quaternion (w, x, y, z) and
+ * s = exp(log_scale), EWA splatting to a 2D mean and covariance, the
+ * inverse covariance, opacity sigmoid(logit), SH colour up to degree 3 plus
+ * 0.5 clamped at 0), the 3-sigma radius and the tile rect.
+ *   means [N][3], log_scales [N][3], quats [N][4] (need not be unit length),
+ *   opacity_logits [N], sh [N][prm->sh_stride][3]: device, FP32.
+ *   cams_host [V], prm host.  out: device buffers with V*N rows.
+ * A Gaussian is culled (tiles_touched 0) when its FP32 depth (the FP32
+ * rounding of the FP64 camera-space z) is <= near_z, its 2D covariance is
+ * singular, a projected value is not finite, or its rect is empty. */
+int gs_preprocess(const float* means, const float* log_scales, const float* quats,
+                  const float* opacity_logits, const float* sh, int N,
+                  const gs_camera* cams_host, int V, const gs_params* prm, const gs_proj* out,
+                  gs_stream stream);
+
+/* Per-tile Gaussian lists (Sec. 3: "the splatting process produces a
+ * Gaussian list at each pixel"; sorted by depth for the blending of Sec. 3).
+ * Result: sorted_vals[0..P) holds row indices v*N + g ordered by
+ * (global tile, FP32 depth bits, g), i.e. the order of the 64-bit key
+ * (tile << 32) | depth_bits with ties by Gaussian id; tile_ranges[2t],
+ * tile_ranges[2t+1] = [start, end) of tile t in sorted_vals (0, 0 if empty).
+ *   proj: output of gs_preprocess (depth, rect, tiles_touched are read).
+ *   workspace: device, >= gs_bin_sort_workspace_size(V*N, pair_capacity,
+ *   total_tiles) bytes, 256-B aligned.
+ *   sorted_vals [pair_capacity], tile_ranges [2*total_tiles], num_pairs_dev [1],
+ *   status_dev [1]: device outputs.  sorted_keys [pair_capacity] (optional):
+ *   the 64-bit keys in sorted order.
+ *   num_pairs_host (optional): if non-NULL the call synchronises `stream`,
+ *   writes P there and returns GS_ERR_CAPACITY when P > pair_capacity
+ *   (nothing beyond the count is then written).  If NULL (the form for CUDA
+ *   graph capture) nothing is synchronised; on overflow the device writes
+ *   *status_dev = GS_ERR_CAPACITY, keeps P in *num_pairs_dev, empties every
+ *   range, and the caller regrows and reruns. */
+int gs_bin_sort(const gs_proj* proj, int N, const gs_camera* cams_host, int V,
+                void* workspace, size_t workspace_bytes, long long pair_capacity,
+                unsigned* sorted_vals, unsigned long long* sorted_keys, unsigned* tile_ranges,
+                long long* num_pairs_dev, long long* num_pairs_host, int* status_dev,
+                gs_stream stream);
+
+/* Front-to-back alpha blending per 16x16 tile (Sec. 3) with the entropy of
+ * the blending weights (Sec. 4.3).  Per pixel, over its tile's list:
+ *   alpha = min(alpha_max, sigma exp(d)); entries with alpha < alpha_min are
+ *   skipped; the walk stops before blending an entry with
+ *   T (1 - alpha) < t_min; w = alpha T; C += w c; T *= 1 - alpha.
+ *   H = -sum w ln w - T ln T over the blended entries and the background.
+ * Outputs (device, per pixel): image [P][3], final_T [P], last_idx [P]
+ * (1-based list position of the last blended entry, 0 if none), entropy [P]
+ * (may be NULL).  opt: see gs_launch (NULL = one CTA per tile). */
+int gs_render_fwd(const gs_proj* proj, int N, const gs_camera* cams_host, int V,
+                  const gs_params* prm, const unsigned* sorted_vals, const unsigned* tile_ranges,
+                  float* image, float* final_T, unsigned* last_idx, float* entropy,
+                  const gs_launch* opt, gs_stream stream);
+
+/* Loss of Sec. 3 (L_base with lambda = 0, i.e. the L1 term) plus the
+ * entropy term of Sec. 4.3, per view averaged over its M_v pixels, then
+ * averaged over the V views:
+ *   L = (1/V) sum_v [ (1/(3 M_v)) sum |C - C*| + gamma (1/M_v) sum_j H_j ].
+ * Writes loss_dev [1] (double, device), dL_dimage [P][3] = sign(C - C*) /
+ * (3 M_v V) with sign(0) = 0, and dL_dentropy [P] = gamma / (M_v V) (may be
+ * NULL).  entropy may be NULL when gamma == 0.  workspace: device,
+ * gs_loss_workspace_size(P) bytes. */
+int gs_loss_l1_entropy(const float* image, const float* target, const float* entropy,
+                       const gs_camera* cams_host, int V, float gamma, double* loss_dev,
+                       float* dL_dimage, float* dL_dentropy, void* workspace,
+                       size_t workspace_bytes, gs_stream stream);
+
+/* Reverse-order adjoint of gs_render_fwd and gs_preprocess (Sec. 4.4 and
+ * Suppl. B-C).  Per pixel, from its last blended entry back to the first:
+ * T_i = T_{i+1} / (1 - alpha_i), the colour part of dL/dalpha_i, and the
+ * entropy part (-ln w_i - 1) T_i + R_{i+1} / (1 - alpha_i) carried by
+ * Algorithm 1's running R; then alpha -> sigma, exponent -> conic, 2D mean
+ * (Suppl. C), colour; then through the projection to the parameters.
+ *   dL_dimage [P][3], dL_dentropy [P] (may be NULL: no entropy term),
+ *   final_T, last_idx: from gs_render_fwd.  Parameters as in gs_preprocess.
+ *   grad2d [V*N][12] device scratch/output (zeroed by the call): per row
+ *   dL/d(mean2d x, y, conic a, b, c, sigma, r, g, b) and 3 pad floats.
+ *   g_* : device, shapes of the parameters, overwritten. */
+int gs_render_bwd(const gs_proj* proj, int N, const gs_camera* cams_host, int V,
+                  const gs_params* prm, const unsigned* sorted_vals, const unsigned* tile_ranges,
+                  const float* final_T, const unsigned* last_idx, const float* dL_dimage,
+                  const float* dL_dentropy, const float* means, const float* log_scales,
+                  const float* quats, const float* opacity_logits, const float* sh,
+                  float* grad2d, float* g_means, float* g_log_scales, float* g_quats,
+                  float* g_opacity_logits, float* g_sh, const gs_launch* opt, gs_stream stream);
+
+/* Scale reset (Sec. 4.2): s <- zeta s for every Gaussian, i.e.
+ * log_scales[i] += ln(zeta) in place, n = 3N floats.  0 < zeta < 1, else
+ * GS_ERR_INVALID_ARG.  Optimiser state is not touched. */
+int gs_scale_reset(float* log_scales, long long n, float zeta, gs_stream stream);
+
+/* Tile work queue for the batched launch: the global tile ids ordered by
+ * list length (end - start), longest first, ties by tile id.
+ *   tile_ranges [2*total_tiles] device in; tile_order [total_tiles] device out;
+ *   workspace: gs_tile_queue_workspace_size(total_tiles) bytes. */
+int gs_tile_queue(const unsigned* tile_ranges, long long total_tiles, unsigned* tile_order,
+                  void* workspace, size_t workspace_bytes, gs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H */

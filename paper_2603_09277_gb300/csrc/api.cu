@@ -1,0 +1,376 @@
+// api.cu -- the extern "C" entry points of include/gs.h: argument checks,
+// per-call camera tables, and the small kernels that do not belong to a
+// larger stage (loss, scale reset).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+// Stage launchers defined in the other translation units.
+int launch_preprocess(const float* means, const float* log_scales, const float* quats,
+                      const float* opacity_logits, const float* sh, int N, const CamTable& ct,
+                      const gs_params* prm, const gs_proj* out, cudaStream_t st);
+int launch_preprocess_bwd(const float* means, const float* log_scales, const float* quats,
+                          const float* opacity_logits, const float* sh, int N, const CamTable& ct,
+                          const gs_params* prm, const unsigned* tiles_touched, const float* grad2d,
+                          float* g_means, float* g_ls, float* g_quats, float* g_opac, float* g_sh,
+                          cudaStream_t st);
+size_t bin_sort_workspace_size(long long n_rows, long long cap, long long total_tiles);
+int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* workspace,
+                    size_t ws_bytes, long long cap, unsigned* sorted_vals,
+                    unsigned long long* sorted_keys, unsigned* ranges, long long* num_pairs_dev,
+                    long long* num_pairs_host, int* status_dev, cudaStream_t st);
+size_t tile_queue_workspace_size(long long T);
+int launch_tile_queue(const unsigned* ranges, long long T, unsigned* order, void* ws,
+                      size_t ws_bytes, cudaStream_t st);
+int launch_render_fwd(const gs_proj* proj, const CamTable& ct, const gs_params* prm,
+                      const unsigned* vals, const unsigned* ranges, float* image, float* final_T,
+                      unsigned* last_idx, float* entropy, const gs_launch* opt, cudaStream_t st);
+int launch_render_bwd(const gs_proj* proj, const CamTable& ct, const gs_params* prm,
+                      const unsigned* vals, const unsigned* ranges, const float* final_T,
+                      const unsigned* last_idx, const float* dL_dimage, const float* dL_dentropy,
+                      float* grad2d, const gs_launch* opt, cudaStream_t st);
+
+namespace {
+thread_local char g_err[512] = "";
+unsigned long long g_launches = 0;
+
+void set_error_text(const char* msg) {
+  strncpy(g_err, msg, sizeof(g_err) - 1);
+  g_err[sizeof(g_err) - 1] = 0;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int invalid(const char* what) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "invalid argument: %s", what);
+  set_error_text(buf);
+  return GS_ERR_INVALID_ARG;
+}
+}  // namespace
+
+int set_cuda_error(cudaError_t e) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "CUDA error %d: %s", (int)e, cudaGetErrorString(e));
+  set_error_text(buf);
+  return GS_ERR_CUDA;
+}
+
+void count_launches(int n) { __atomic_fetch_add(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+
+int check_launch() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GS_OK : set_cuda_error(e);
+}
+
+bool build_cam_table(const gs_camera* cams, int V, const gs_params* prm, CamTable* ct) {
+  if (!cams || V < 1 || V > GS_MAX_VIEWS) return false;
+  memset(ct, 0, sizeof(*ct));
+  ct->V = V;
+  long long tiles = 0, pix = 0;
+  const float fovc = prm ? prm->fov_clamp : 1.3f;
+  for (int v = 0; v < V; ++v) {
+    const gs_camera& c = cams[v];
+    if (c.width <= 0 || c.height <= 0 || !(c.fx > 0.f) || !(c.fy > 0.f)) return false;
+    CamInfo& d = ct->c[v];
+    for (int r = 0; r < 3; ++r) {
+      for (int j = 0; j < 3; ++j) d.R[r * 3 + j] = c.world_to_cam[r * 4 + j];
+      d.t[r] = c.world_to_cam[r * 4 + 3];
+      d.cp[r] = c.cam_pos[r];
+    }
+    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+    d.limx = fovc * (0.5f * (float)c.width / c.fx);
+    d.limy = fovc * (0.5f * (float)c.height / c.fy);
+    d.W = c.width; d.H = c.height;
+    d.TX = (c.width + kTile - 1) / kTile;
+    d.TY = (c.height + kTile - 1) / kTile;
+    d.tile_off = (int)tiles;
+    d.pix_off = pix;
+    tiles += (long long)d.TX * d.TY;
+    pix += (long long)c.width * c.height;
+    if (tiles >= (1ll << 31)) return false;
+  }
+  ct->total_tiles = (int)tiles;
+  return true;
+}
+
+RenderConsts render_consts(const gs_params* prm) {
+  RenderConsts rc;
+  rc.alpha_max = prm->alpha_max;
+  rc.alpha_min = prm->alpha_min;
+  rc.log2_alpha_min = log2f(prm->alpha_min);
+  rc.t_min = prm->t_min;
+  return rc;
+}
+
+namespace {
+
+bool params_ok(const gs_params* p) {
+  if (!p) return false;
+  if (p->sh_degree < 0 || p->sh_degree > 3) return false;
+  int K = (p->sh_degree + 1) * (p->sh_degree + 1);
+  if (p->sh_stride < K || p->sh_stride > GS_SH_COEFFS_MAX) return false;
+  if (p->attr_dtype < GS_ATTR_F32 || p->attr_dtype > GS_ATTR_BF16) return false;
+  if (!(p->alpha_max > 0.f && p->alpha_max < 1.f)) return false;
+  if (!(p->alpha_min > 0.f && p->alpha_min < p->alpha_max)) return false;
+  if (!(p->t_min > 0.f && p->t_min < 1.f)) return false;
+  if (!(p->dilation >= 0.f) || !(p->near_z > 0.f) || !(p->fov_clamp > 0.f)) return false;
+  return true;
+}
+
+bool proj_ok(const gs_proj* p, bool need_records) {
+  if (!p || !p->depth || !p->rect || !p->tiles_touched) return false;
+  if (need_records && (!p->records || !aligned(p->records, 16))) return false;
+  if (!aligned(p->rect, 16)) return false;
+  if (p->mean2d && !aligned(p->mean2d, 8)) return false;
+  if (p->conic_opacity && !aligned(p->conic_opacity, 16)) return false;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Loss kernels: per-pixel L1 + gamma H contributions with their gradients,
+// block partial sums in double, then one block sums the partials in a fixed
+// order (deterministic).
+// ---------------------------------------------------------------------------
+constexpr int kLossThreads = 256;
+constexpr int kLossMaxBlocks = 1024;
+
+__global__ void __launch_bounds__(kLossThreads) loss_kernel(
+    const float* __restrict__ image, const float* __restrict__ target,
+    const float* __restrict__ entropy, const CamTable ct, long long P, float gamma,
+    float* __restrict__ dimg, float* __restrict__ dent, double* __restrict__ partials) {
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
+       i += (long long)gridDim.x * blockDim.x) {
+    int v = find_view_of_pixel(ct, i);
+    const double M = (double)ct.c[v].W * ct.c[v].H;
+    const double wv = 1.0 / (M * ct.V);
+    double l1 = 0.0;
+    for (int ch = 0; ch < 3; ++ch) {
+      float r = image[3 * i + ch] - target[3 * i + ch];
+      l1 += fabs((double)r);
+      float sg = r > 0.f ? 1.f : (r < 0.f ? -1.f : 0.f);
+      dimg[3 * i + ch] = (float)(sg * wv / 3.0);
+    }
+    double h = entropy ? (double)entropy[i] : 0.0;
+    if (dent) dent[i] = (float)(gamma * wv);
+    acc += wv * (l1 / 3.0 + (double)gamma * h);
+  }
+  __shared__ double s[kLossThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kLossThreads / 32; ++k) t += s[k];
+    partials[blockIdx.x] = t;
+  }
+}
+
+__global__ void loss_finalize_kernel(const double* __restrict__ partials, int n,
+                                     double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) t += partials[i];
+    *out = t;
+  }
+}
+
+__global__ void scale_reset_kernel(float* __restrict__ ls, long long n, float delta) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    ls[i] += delta;
+}
+
+int loss_blocks(long long P) {
+  return (int)std::max<long long>(1, std::min<long long>(kLossMaxBlocks, (P + kLossThreads - 1) / kLossThreads));
+}
+
+}  // namespace
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+int gs_record_bytes(int attr_dtype) {
+  switch (attr_dtype) {
+    case GS_ATTR_F32: return (int)sizeof(RecF32);
+    case GS_ATTR_F16:
+    case GS_ATTR_BF16: return (int)sizeof(RecH16);
+  }
+  return -1;
+}
+
+long long gs_total_tiles(const gs_camera* cams, int V) {
+  CamTable ct;
+  if (!build_cam_table(cams, V, nullptr, &ct)) return -1;
+  return ct.total_tiles;
+}
+
+long long gs_total_pixels(const gs_camera* cams, int V) {
+  CamTable ct;
+  if (!build_cam_table(cams, V, nullptr, &ct)) return -1;
+  return ct.c[V - 1].pix_off + (long long)ct.c[V - 1].W * ct.c[V - 1].H;
+}
+
+size_t gs_bin_sort_workspace_size(long long n_rows, long long cap, long long total_tiles) {
+  if (n_rows < 0 || cap < 0 || total_tiles < 0) return 0;
+  return bin_sort_workspace_size(n_rows, cap, total_tiles);
+}
+
+size_t gs_loss_workspace_size(long long total_pixels) {
+  return sizeof(double) * (size_t)loss_blocks(total_pixels);
+}
+
+size_t gs_tile_queue_workspace_size(long long total_tiles) {
+  return tile_queue_workspace_size(total_tiles);
+}
+
+const char* gs_status_string(int s) {
+  switch (s) {
+    case GS_OK: return "ok";
+    case GS_ERR_INVALID_ARG: return "invalid argument";
+    case GS_ERR_CUDA: return "CUDA error";
+    case GS_ERR_CAPACITY: return "pair capacity exceeded";
+    case GS_ERR_TIMEOUT: return "timeout";
+    case GS_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* gs_last_error_string(void) { return g_err; }
+
+const char* gs_version(void) { return "libgs 0.1 sm_103a tile16"; }
+
+unsigned long long gs_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+int gs_preprocess(const float* means, const float* log_scales, const float* quats,
+                  const float* opacity_logits, const float* sh, int N, const gs_camera* cams,
+                  int V, const gs_params* prm, const gs_proj* out, gs_stream stream) {
+  if (N < 0) return invalid("N < 0");
+  if (!params_ok(prm)) return invalid("params");
+  CamTable ct;
+  if (!build_cam_table(cams, V, prm, &ct)) return invalid("cameras");
+  if ((long long)N * V >= (1ll << 32)) return invalid("V*N must be < 2^32");
+  if (!proj_ok(out, true)) return invalid("projection buffers (NULL or misaligned)");
+  if (N > 0 && (!means || !log_scales || !quats || !opacity_logits || !sh))
+    return invalid("parameter pointers");
+  if (N > 0 && !aligned(quats, 16)) return invalid("quats must be 16-byte aligned");
+  return launch_preprocess(means, log_scales, quats, opacity_logits, sh, N, ct, prm, out,
+                           (cudaStream_t)stream);
+}
+
+int gs_bin_sort(const gs_proj* proj, int N, const gs_camera* cams, int V, void* workspace,
+                size_t workspace_bytes, long long pair_capacity, unsigned* sorted_vals,
+                unsigned long long* sorted_keys, unsigned* tile_ranges, long long* num_pairs_dev,
+                long long* num_pairs_host, int* status_dev, gs_stream stream) {
+  if (N < 0) return invalid("N < 0");
+  CamTable ct;
+  if (!build_cam_table(cams, V, nullptr, &ct)) return invalid("cameras");
+  if (!proj_ok(proj, false)) return invalid("projection buffers");
+  if (pair_capacity < 0 || pair_capacity >= (1ll << 32)) return invalid("pair_capacity");
+  if (!tile_ranges || !num_pairs_dev || !status_dev) return invalid("output pointers");
+  if (pair_capacity > 0 && !sorted_vals) return invalid("sorted_vals");
+  if (!workspace || !aligned(workspace, 256)) return invalid("workspace (NULL or not 256-B aligned)");
+  if (workspace_bytes < bin_sort_workspace_size((long long)N * V, pair_capacity, ct.total_tiles))
+    return invalid("workspace too small");
+  return launch_bin_sort(proj, N, ct, workspace, workspace_bytes, pair_capacity, sorted_vals,
+                         sorted_keys, tile_ranges, num_pairs_dev, num_pairs_host, status_dev,
+                         (cudaStream_t)stream);
+}
+
+int gs_render_fwd(const gs_proj* proj, int N, const gs_camera* cams, int V, const gs_params* prm,
+                  const unsigned* sorted_vals, const unsigned* tile_ranges, float* image,
+                  float* final_T, unsigned* last_idx, float* entropy, const gs_launch* opt,
+                  gs_stream stream) {
+  if (N < 0) return invalid("N < 0");
+  if (!params_ok(prm)) return invalid("params");
+  CamTable ct;
+  if (!build_cam_table(cams, V, prm, &ct)) return invalid("cameras");
+  if (!proj_ok(proj, true)) return invalid("projection buffers");
+  if (!tile_ranges || !image || !final_T || !last_idx) return invalid("output pointers");
+  if (!aligned(tile_ranges, 8)) return invalid("tile_ranges must be 8-byte aligned");
+  if (opt && opt->ctas > 0 && !opt->work_counter) return invalid("persistent launch needs work_counter");
+  return launch_render_fwd(proj, ct, prm, sorted_vals, tile_ranges, image, final_T, last_idx,
+                           entropy, opt, (cudaStream_t)stream);
+}
+
+int gs_loss_l1_entropy(const float* image, const float* target, const float* entropy,
+                       const gs_camera* cams, int V, float gamma, double* loss_dev,
+                       float* dL_dimage, float* dL_dentropy, void* workspace,
+                       size_t workspace_bytes, gs_stream stream) {
+  CamTable ct;
+  if (!build_cam_table(cams, V, nullptr, &ct)) return invalid("cameras");
+  long long P = ct.c[V - 1].pix_off + (long long)ct.c[V - 1].W * ct.c[V - 1].H;
+  if (!image || !target || !loss_dev || !dL_dimage) return invalid("pointers");
+  if (gamma != 0.f && !entropy) return invalid("entropy is required when gamma != 0");
+  if (!(gamma >= 0.f)) return invalid("gamma");
+  int nb = loss_blocks(P);
+  if (!workspace || workspace_bytes < sizeof(double) * (size_t)nb) return invalid("workspace");
+  cudaStream_t st = (cudaStream_t)stream;
+  double* partials = reinterpret_cast<double*>(workspace);
+  loss_kernel<<<nb, kLossThreads, 0, st>>>(image, target, gamma != 0.f ? entropy : nullptr, ct, P,
+                                           gamma, dL_dimage, dL_dentropy, partials);
+  loss_finalize_kernel<<<1, 32, 0, st>>>(partials, nb, loss_dev);
+  count_launches(2);
+  return check_launch();
+}
+
+int gs_render_bwd(const gs_proj* proj, int N, const gs_camera* cams, int V, const gs_params* prm,
+                  const unsigned* sorted_vals, const unsigned* tile_ranges, const float* final_T,
+                  const unsigned* last_idx, const float* dL_dimage, const float* dL_dentropy,
+                  const float* means, const float* log_scales, const float* quats,
+                  const float* opacity_logits, const float* sh, float* grad2d, float* g_means,
+                  float* g_log_scales, float* g_quats, float* g_opacity_logits, float* g_sh,
+                  const gs_launch* opt, gs_stream stream) {
+  if (N < 0) return invalid("N < 0");
+  if (!params_ok(prm)) return invalid("params");
+  CamTable ct;
+  if (!build_cam_table(cams, V, prm, &ct)) return invalid("cameras");
+  if (!proj_ok(proj, true)) return invalid("projection buffers");
+  if (!tile_ranges || !final_T || !last_idx || !dL_dimage) return invalid("forward outputs");
+  if (!grad2d || !aligned(grad2d, 16)) return invalid("grad2d (NULL or not 16-B aligned)");
+  if (N > 0 && (!means || !log_scales || !quats || !opacity_logits || !sh)) return invalid("params");
+  if (N > 0 && (!g_means || !g_log_scales || !g_quats || !g_opacity_logits || !g_sh))
+    return invalid("gradient outputs");
+  if (N > 0 && (!aligned(quats, 16) || !aligned(g_quats, 16))) return invalid("quat alignment");
+  if (opt && opt->ctas > 0 && !opt->work_counter) return invalid("persistent launch needs work_counter");
+  cudaStream_t st = (cudaStream_t)stream;
+  GS_TRY_CUDA(cudaMemsetAsync(grad2d, 0, sizeof(float) * 12 * (size_t)N * V, st));
+  int rc = launch_render_bwd(proj, ct, prm, sorted_vals, tile_ranges, final_T, last_idx,
+                             dL_dimage, dL_dentropy, grad2d, opt, st);
+  if (rc != GS_OK) return rc;
+  return launch_preprocess_bwd(means, log_scales, quats, opacity_logits, sh, N, ct, prm,
+                               proj->tiles_touched, grad2d, g_means, g_log_scales, g_quats,
+                               g_opacity_logits, g_sh, st);
+}
+
+int gs_scale_reset(float* log_scales, long long n, float zeta, gs_stream stream) {
+  if (!(zeta > 0.f && zeta < 1.f)) return invalid("zeta must be in (0, 1)");
+  if (n < 0 || (n > 0 && !log_scales)) return invalid("log_scales");
+  if (n == 0) return GS_OK;
+  const float delta = (float)log((double)zeta);
+  unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, 152ll * 8);
+  scale_reset_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(log_scales, n, delta);
+  count_launches(1);
+  return check_launch();
+}
+
+int gs_tile_queue(const unsigned* tile_ranges, long long total_tiles, unsigned* tile_order,
+                  void* workspace, size_t workspace_bytes, gs_stream stream) {
+  if (total_tiles < 0 || total_tiles >= (1ll << 31)) return invalid("total_tiles");
+  if (total_tiles > 0 && (!tile_ranges || !tile_order)) return invalid("pointers");
+  if (!workspace || !aligned(workspace, 256)) return invalid("workspace");
+  return launch_tile_queue(tile_ranges, total_tiles, tile_order, workspace, workspace_bytes,
+                           (cudaStream_t)stream);
+}
+
+}  // extern "C"

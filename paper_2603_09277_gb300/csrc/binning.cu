@@ -1,0 +1,561 @@
+// binning.cu -- per-tile Gaussian lists (Sec. 3: each pixel's list of the
+// Gaussians that cover it, sorted by depth).
+//
+// The lists are the (tile, depth, id)-ordered pairs of every visible
+// (view, Gaussian) row with every tile of its rect.  Instead of one sort
+// of 64-bit (tile << 32 | depth) keys over all P pairs, the work is split
+// so that the P-sized sort only carries the tile bits:
+//   1. compact the visible rows (scan of a visibility flag);
+//   2. stable LSD radix sort of the visible rows by FP32 depth bits
+//      (N-sized: 4 passes of 8 bits over 8-byte items);
+//   3. exclusive scan of tiles_touched in depth order -> pair offsets, P;
+//   4. duplicate: each row writes (global tile, row) for its rect, in depth
+//      order (so equal tiles appear in (depth, id) order);
+//   5. stable LSD radix sort of the pairs by tile id, ceil(log2 tiles) bits;
+//   6. per-tile [start, end) ranges from the sorted tile ids.
+// The stable tile sort of depth-ordered pairs yields exactly the order of
+// the 64-bit key sort with ties by Gaussian id.
+//
+// All kernels read their element counts from device memory and use grids
+// sized from host-known upper bounds, so the whole sequence can be captured
+// in a CUDA graph (no host synchronisation needed).  None of them waits on
+// another block.
+#include <algorithm>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;                       // per thread
+constexpr int kScanTile = kScanThreads * kScanItems; // 4096 items per block
+
+// ----------------------------------------------------------------------------
+// Block-wide exclusive scan helpers (256 threads).
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Returns the exclusive prefix of x over the block; *total receives the block
+// total in every thread.
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long x,
+                                                              unsigned long long* total) {
+  __shared__ unsigned long long s_w[kScanThreads / 32 + 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long inc = warp_incl_scan(x);
+  if (lane == 31) s_w[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long t = lane < kScanThreads / 32 ? s_w[lane] : 0ull;
+    unsigned long long ti = warp_incl_scan(t);
+    if (lane < kScanThreads / 32) s_w[lane] = ti - t;
+    if (lane == 31) s_w[kScanThreads / 32] = ti;
+  }
+  __syncthreads();
+  unsigned long long r = s_w[w] + inc - x;
+  *total = s_w[kScanThreads / 32];
+  __syncthreads();
+  return r;
+}
+
+// Value source for the scans: either tiles_touched[i] (or its gather through
+// an index array) or a visibility flag.
+struct ScanSrc {
+  const unsigned* vals;   // values
+  const unsigned* index;  // optional gather index (vals[index[i]])
+  int flag;               // 1: use (value > 0) instead of the value
+  __device__ __forceinline__ unsigned get(long long i) const {
+    unsigned v = index ? vals[index[i]] : vals[i];
+    return flag ? (v > 0u ? 1u : 0u) : v;
+  }
+};
+
+// Phase 1: per-block sums.
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(ScanSrc src, const long long* n_dev,
+                                                                   long long n_host,
+                                                                   unsigned long long* block_sums) {
+  long long n = n_dev ? *n_dev : n_host;
+  long long base = (long long)blockIdx.x * kScanTile;
+  unsigned long long s = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    long long i = base + (long long)k * kScanThreads + threadIdx.x;
+    if (i < n) s += src.get(i);
+  }
+  unsigned long long tot;
+  block_excl_scan(s, &tot);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+// Phase 2: exclusive scan of the block sums in one block; writes the grand
+// total to *total.
+__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(unsigned long long* block_sums,
+                                                                   int nblocks,
+                                                                   long long* total) {
+  __shared__ unsigned long long s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nblocks; base += kScanThreads) {
+    int i = base + threadIdx.x;
+    unsigned long long x = i < nblocks ? block_sums[i] : 0ull;
+    unsigned long long tot;
+    unsigned long long ex = block_excl_scan(x, &tot);
+    if (i < nblocks) block_sums[i] = s_carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = (long long)s_carry;
+}
+
+// Phase 3 (compaction form): rows with tiles_touched > 0 are written, in
+// order, as (depth bits, row) to keys/vals.
+__global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
+    const unsigned* __restrict__ tiles_touched, const float* __restrict__ depth, long long n,
+    const unsigned long long* __restrict__ block_offsets, unsigned* __restrict__ keys,
+    unsigned* __restrict__ vals) {
+  long long base = (long long)blockIdx.x * kScanTile;
+  // each thread owns kScanItems consecutive items for an ordered compaction
+  long long first = base + (long long)threadIdx.x * kScanItems;
+  unsigned cnt = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    long long i = first + k;
+    if (i < n && tiles_touched[i] > 0u) ++cnt;
+  }
+  unsigned long long tot;
+  unsigned long long off = block_excl_scan(cnt, &tot) + block_offsets[blockIdx.x];
+  for (int k = 0; k < kScanItems; ++k) {
+    long long i = first + k;
+    if (i < n && tiles_touched[i] > 0u) {
+      keys[off] = __float_as_uint(depth[i]);
+      vals[off] = (unsigned)i;
+      ++off;
+    }
+  }
+}
+
+// Phase 3 (offsets form): out[i] = exclusive prefix of tiles_touched in
+// depth order (rows given by `rows`), for i < n_dev.
+__global__ void __launch_bounds__(kScanThreads) scan_offsets_kernel(
+    const unsigned* __restrict__ tiles_touched, const unsigned* __restrict__ rows,
+    const long long* __restrict__ n_dev, const unsigned long long* __restrict__ block_offsets,
+    unsigned long long* __restrict__ out) {
+  long long n = *n_dev;
+  long long base = (long long)blockIdx.x * kScanTile;
+  long long first = base + (long long)threadIdx.x * kScanItems;
+  if (base >= n) return;
+  unsigned long long s = 0;
+  unsigned loc[kScanItems];
+  for (int k = 0; k < kScanItems; ++k) {
+    long long i = first + k;
+    loc[k] = i < n ? tiles_touched[rows[i]] : 0u;
+    s += loc[k];
+  }
+  unsigned long long tot;
+  unsigned long long off = block_excl_scan(s, &tot) + block_offsets[blockIdx.x];
+  for (int k = 0; k < kScanItems; ++k) {
+    long long i = first + k;
+    if (i < n) out[i] = off;
+    off += loc[k];
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Stable LSD radix sort of (u32 key, u32 value) pairs, 8-bit digits,
+// reduce-then-scan with a fixed grid.  Each block owns a contiguous chunk of
+// whole 2048-item tiles; n is read from device memory.
+// ----------------------------------------------------------------------------
+constexpr int kRadixThreads = 256;
+constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr int kRadixIpt = 8;                                // items per thread per tile
+constexpr int kRadixTile = kRadixThreads * kRadixIpt;       // 2048
+constexpr int kRadixBins = 256;
+
+__device__ __forceinline__ long long radix_chunk(long long n, int nblocks) {
+  long long per = (n + nblocks - 1) / nblocks;
+  return (per + kRadixTile - 1) / kRadixTile * kRadixTile;
+}
+
+__global__ void __launch_bounds__(kRadixThreads) radix_upsweep_kernel(
+    const unsigned* __restrict__ keys, const long long* __restrict__ n_dev, int shift,
+    unsigned* __restrict__ hist /* [256][nblocks] */) {
+  __shared__ unsigned s_h[kRadixWarps][kRadixBins];
+  const int w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kRadixWarps * kRadixBins; i += kRadixThreads)
+    (&s_h[0][0])[i] = 0u;
+  __syncthreads();
+  long long n = *n_dev;
+  long long chunk = radix_chunk(n, gridDim.x);
+  long long b0 = (long long)blockIdx.x * chunk;
+  long long b1 = min(n, b0 + chunk);
+  for (long long i = b0 + threadIdx.x; i < b1; i += kRadixThreads) {
+    unsigned d = (keys[i] >> shift) & 0xffu;
+    atomicAdd(&s_h[w][d], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRadixBins; d += kRadixThreads) {
+    unsigned s = 0;
+    for (int k = 0; k < kRadixWarps; ++k) s += s_h[k][d];
+    hist[(long long)d * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// Exclusive scan of hist[256 * nblocks] (digit-major) in one block.
+__global__ void __launch_bounds__(kScanThreads) radix_scan_kernel(unsigned* __restrict__ hist,
+                                                                  int count) {
+  __shared__ unsigned long long s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  // each thread takes a contiguous run per round for better locality
+  constexpr int kRun = 8;
+  for (int base = 0; base < count; base += kScanThreads * kRun) {
+    int first = base + threadIdx.x * kRun;
+    unsigned loc[kRun];
+    unsigned long long s = 0;
+    for (int k = 0; k < kRun; ++k) {
+      loc[k] = first + k < count ? hist[first + k] : 0u;
+      s += loc[k];
+    }
+    unsigned long long tot;
+    unsigned long long off = block_excl_scan(s, &tot) + s_carry;
+    for (int k = 0; k < kRun; ++k) {
+      if (first + k < count) hist[first + k] = (unsigned)off;
+      off += loc[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
+    const unsigned* __restrict__ keys_in, const unsigned* __restrict__ vals_in,
+    unsigned* __restrict__ keys_out, unsigned* __restrict__ vals_out,
+    const long long* __restrict__ n_dev, int shift, const unsigned* __restrict__ offsets) {
+  __shared__ unsigned s_wc[kRadixWarps][kRadixBins + 1];  // per-warp digit counters (+ dummy)
+  __shared__ unsigned s_base[kRadixBins];                 // running global offset per digit
+  __shared__ unsigned s_tot[kRadixBins];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  long long n = *n_dev;
+  long long chunk = radix_chunk(n, gridDim.x);
+  long long b0 = (long long)blockIdx.x * chunk;
+  long long b1 = min(n, b0 + chunk);
+  for (int d = threadIdx.x; d < kRadixBins; d += kRadixThreads)
+    s_base[d] = offsets[(long long)d * gridDim.x + blockIdx.x];
+  for (int i = threadIdx.x; i < kRadixWarps * (kRadixBins + 1); i += kRadixThreads)
+    (&s_wc[0][0])[i] = 0u;
+  __syncthreads();
+  for (long long t0 = b0; t0 < b1; t0 += kRadixTile) {
+    unsigned k[kRadixIpt], v[kRadixIpt], dg[kRadixIpt], loc[kRadixIpt];
+#pragma unroll
+    for (int i = 0; i < kRadixIpt; ++i) {
+      long long idx = t0 + (long long)w * (32 * kRadixIpt) + i * 32 + lane;
+      bool ok = idx < b1;
+      k[i] = ok ? keys_in[idx] : 0u;
+      v[i] = ok ? vals_in[idx] : 0u;
+      dg[i] = ok ? ((k[i] >> shift) & 0xffu) : (unsigned)kRadixBins;
+    }
+#pragma unroll
+    for (int i = 0; i < kRadixIpt; ++i) {
+      unsigned peers = __match_any_sync(0xffffffffu, dg[i]);
+      unsigned rank = __popc(peers & lt_mask);
+      unsigned base = s_wc[w][dg[i]];
+      __syncwarp();
+      if (rank == 0) s_wc[w][dg[i]] = base + __popc(peers);
+      __syncwarp();
+      loc[i] = base + rank;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadixBins; d += kRadixThreads) {
+      unsigned run = 0;
+      for (int ww = 0; ww < kRadixWarps; ++ww) {
+        unsigned c = s_wc[ww][d];
+        s_wc[ww][d] = run;
+        run += c;
+      }
+      s_tot[d] = run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kRadixIpt; ++i) {
+      if (dg[i] < (unsigned)kRadixBins) {
+        unsigned pos = s_base[dg[i]] + s_wc[w][dg[i]] + loc[i];
+        keys_out[pos] = k[i];
+        vals_out[pos] = v[i];
+      }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadixBins; d += kRadixThreads) {
+      s_base[d] += s_tot[d];
+      for (int ww = 0; ww < kRadixWarps; ++ww) s_wc[ww][d] = 0u;
+    }
+    if (threadIdx.x < kRadixWarps) s_wc[threadIdx.x][kRadixBins] = 0u;
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Pair generation, ranges, capacity check.
+// ----------------------------------------------------------------------------
+__global__ void capacity_check_kernel(const long long* __restrict__ P, long long capacity,
+                                      int* __restrict__ status, long long* __restrict__ p_eff) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    bool over = *P > capacity;
+    *status = over ? GS_ERR_CAPACITY : GS_OK;
+    *p_eff = over ? 0 : *P;  // on overflow every later stage sees zero pairs
+  }
+}
+
+__global__ void __launch_bounds__(256) duplicate_kernel(
+    const unsigned* __restrict__ rows, const long long* __restrict__ n_vis,
+    const unsigned long long* __restrict__ offsets, const int* __restrict__ rect, int N,
+    const CamTable ct, const long long* __restrict__ p_eff, unsigned* __restrict__ tkeys,
+    unsigned* __restrict__ tvals) {
+  long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= *n_vis || *p_eff == 0) return;
+  unsigned row = rows[j];
+  int v = (int)(row / (unsigned)N);
+  const CamInfo& c = ct.c[v];
+  int4 r = reinterpret_cast<const int4*>(rect)[row];
+  unsigned long long off = offsets[j];
+  for (int ty = r.y; ty < r.w; ++ty) {
+    unsigned tb = (unsigned)(c.tile_off + ty * c.TX);
+    for (int tx = r.x; tx < r.z; ++tx) {
+      tkeys[off] = tb + (unsigned)tx;
+      tvals[off] = row;
+      ++off;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) ranges_kernel(const unsigned* __restrict__ tkeys,
+                                                     const long long* __restrict__ p_eff,
+                                                     unsigned* __restrict__ ranges) {
+  long long P = *p_eff;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned t = tkeys[i];
+    if (i == 0 || tkeys[i - 1] != t) ranges[2ll * t] = (unsigned)i;
+    if (i == P - 1 || tkeys[i + 1] != t) ranges[2ll * t + 1] = (unsigned)(i + 1);
+  }
+}
+
+__global__ void __launch_bounds__(256) keys64_kernel(const unsigned* __restrict__ tkeys,
+                                                     const unsigned* __restrict__ tvals,
+                                                     const float* __restrict__ depth,
+                                                     const long long* __restrict__ p_eff,
+                                                     unsigned long long* __restrict__ out) {
+  long long P = *p_eff;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = ((unsigned long long)tkeys[i] << 32) | __float_as_uint(depth[tvals[i]]);
+}
+
+__global__ void set_count_kernel(long long* __restrict__ dst, const long long* __restrict__ src) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *dst = *src;
+}
+
+// ----------------------------------------------------------------------------
+// Workspace layout.
+// ----------------------------------------------------------------------------
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Workspace {
+  unsigned long long* block_sums;  // scan block sums
+  long long* counters;             // [0] n_vis, [1] P, [2] P effective
+  unsigned* rk[2];                 // row keys (depth bits), double buffer
+  unsigned* rv[2];                 // row values, double buffer
+  unsigned long long* offsets;     // pair offsets per visible row
+  unsigned* pk[2];                 // pair keys (tile), double buffer; pk[1] may alias output
+  unsigned* pv;                    // pair values scratch
+  unsigned* hist;                  // radix histograms
+  size_t bytes;
+};
+
+constexpr int kRadixGrid = 2 * 152;  // fixed radix grid (2 CTAs per SM)
+
+inline long long scan_blocks(long long n) { return (n + kScanTile - 1) / kScanTile; }
+
+Workspace carve(void* base, long long n_rows, long long cap) {
+  Workspace w;
+  char* p = reinterpret_cast<char*>(base);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* r = p ? p + off : nullptr;
+    off += align256(bytes);
+    return r;
+  };
+  long long nb = scan_blocks(n_rows > cap ? n_rows : cap) + 1;
+  w.block_sums = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * nb));
+  w.counters = reinterpret_cast<long long*>(take(sizeof(long long) * 4));
+  for (int i = 0; i < 2; ++i) w.rk[i] = reinterpret_cast<unsigned*>(take(4 * (n_rows + 1)));
+  for (int i = 0; i < 2; ++i) w.rv[i] = reinterpret_cast<unsigned*>(take(4 * (n_rows + 1)));
+  w.offsets = reinterpret_cast<unsigned long long*>(take(8 * (n_rows + 1)));
+  for (int i = 0; i < 2; ++i) w.pk[i] = reinterpret_cast<unsigned*>(take(4 * (cap + 1)));
+  w.pv = reinterpret_cast<unsigned*>(take(4 * (cap + 1)));
+  w.hist = reinterpret_cast<unsigned*>(take(4ull * kRadixBins * kRadixGrid));
+  w.bytes = off;
+  return w;
+}
+
+// Runs the radix passes over bits [0, bits) of keys; data starts in
+// (k[0], v[0]) and ends in (k[res], v[res]); returns res.
+int radix_sort(unsigned* k[2], unsigned* v[2], const long long* n_dev, long long n_bound, int bits,
+               unsigned* hist, cudaStream_t st) {
+  int cur = 0;
+  if (n_bound == 0) return cur;
+  int grid = (int)std::min<long long>(kRadixGrid, (n_bound + kRadixTile - 1) / kRadixTile);
+  if (grid < 1) grid = 1;
+  for (int shift = 0; shift < bits; shift += 8) {
+    radix_upsweep_kernel<<<grid, kRadixThreads, 0, st>>>(k[cur], n_dev, shift, hist);
+    radix_scan_kernel<<<1, kScanThreads, 0, st>>>(hist, kRadixBins * grid);
+    radix_downsweep_kernel<<<grid, kRadixThreads, 0, st>>>(k[cur], v[cur], k[1 - cur], v[1 - cur],
+                                                           n_dev, shift, hist);
+    count_launches(3);
+    cur = 1 - cur;
+  }
+  return cur;
+}
+
+int bits_for(long long count) {
+  int b = 0;
+  while (b < 32 && (1ll << b) < count) ++b;
+  return b;
+}
+
+}  // namespace
+
+size_t bin_sort_workspace_size(long long n_rows, long long cap, long long total_tiles) {
+  (void)total_tiles;
+  return carve(nullptr, n_rows, cap).bytes;
+}
+
+int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* workspace,
+                    size_t ws_bytes, long long cap, unsigned* sorted_vals,
+                    unsigned long long* sorted_keys, unsigned* ranges, long long* num_pairs_dev,
+                    long long* num_pairs_host, int* status_dev, cudaStream_t st) {
+  const long long n_rows = (long long)N * ct.V;
+  Workspace w = carve(workspace, n_rows, cap);
+  if (ws_bytes < w.bytes) return GS_ERR_INVALID_ARG;
+  long long* n_vis = w.counters;
+  long long* P = w.counters + 1;
+  long long* p_eff = w.counters + 2;
+  GS_TRY_CUDA(cudaMemsetAsync(w.counters, 0, 4 * sizeof(long long), st));
+  GS_TRY_CUDA(cudaMemsetAsync(ranges, 0, 2 * sizeof(unsigned) * (size_t)ct.total_tiles, st));
+  unsigned* rows_sorted = w.rv[0];
+  const long long nb = scan_blocks(n_rows);
+  if (n_rows > 0) {
+    // 1. compaction of the visible rows, keyed by FP32 depth bits
+    ScanSrc vis{proj->tiles_touched, nullptr, 1};
+    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(vis, nullptr, n_rows, w.block_sums);
+    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(w.block_sums, (int)nb, n_vis);
+    compact_visible_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(
+        proj->tiles_touched, proj->depth, n_rows, w.block_sums, w.rk[0], w.rv[0]);
+    // 2. stable depth sort of the visible rows (ties keep row order = id order)
+    int res = radix_sort(w.rk, w.rv, n_vis, n_rows, 32, w.hist, st);
+    rows_sorted = w.rv[res];
+    // 3. pair offsets in depth order and the pair count P
+    ScanSrc tt{proj->tiles_touched, rows_sorted, 0};
+    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(tt, n_vis, 0, w.block_sums);
+    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(w.block_sums, (int)nb, P);
+    scan_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(proj->tiles_touched, rows_sorted,
+                                                               n_vis, w.block_sums, w.offsets);
+    count_launches(6);
+  }
+  capacity_check_kernel<<<1, 32, 0, st>>>(P, cap, status_dev, p_eff);
+  set_count_kernel<<<1, 32, 0, st>>>(num_pairs_dev, P);
+  count_launches(2);
+  GS_TRY_CUDA(cudaGetLastError());
+  long long p_bound = cap;
+  if (num_pairs_host) {
+    long long p_host = 0;
+    GS_TRY_CUDA(cudaMemcpyAsync(&p_host, P, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    GS_TRY_CUDA(cudaStreamSynchronize(st));
+    *num_pairs_host = p_host;
+    if (p_host > cap) return GS_ERR_CAPACITY;
+    p_bound = p_host;
+  }
+  if (n_rows == 0 || p_bound == 0) return check_launch();
+  // 4. duplicate in depth order, into the buffer pair the last tile pass
+  //    reads from so that the sorted values end in sorted_vals
+  const int tbits = bits_for(ct.total_tiles);
+  const int passes = (tbits + 7) / 8;
+  unsigned* pk[2] = {w.pk[0], w.pk[1]};
+  unsigned* pv[2];
+  if (passes % 2 == 0) {
+    pv[0] = sorted_vals;
+    pv[1] = w.pv;
+  } else {
+    pv[0] = w.pv;
+    pv[1] = sorted_vals;
+  }
+  duplicate_kernel<<<(unsigned)((n_rows + 255) / 256), 256, 0, st>>>(
+      rows_sorted, n_vis, w.offsets, proj->rect, N, ct, p_eff, pk[0], pv[0]);
+  count_launches(1);
+  // 5. stable sort of the pairs by global tile id
+  int res2 = radix_sort(pk, pv, p_eff, p_bound, tbits, w.hist, st);
+  // 6. per-tile ranges (and the optional 64-bit keys)
+  unsigned grid = (unsigned)std::min<long long>((p_bound + 255) / 256, 152ll * 16);
+  ranges_kernel<<<grid, 256, 0, st>>>(pk[res2], p_eff, ranges);
+  count_launches(1);
+  if (sorted_keys) {
+    keys64_kernel<<<grid, 256, 0, st>>>(pk[res2], pv[res2], proj->depth, p_eff, sorted_keys);
+    count_launches(1);
+  }
+  return check_launch();
+}
+
+// ----------------------------------------------------------------------------
+// Tile queue: global tile ids ordered by list length, longest first.
+// ----------------------------------------------------------------------------
+namespace {
+__global__ void queue_keys_kernel(const unsigned* __restrict__ ranges, long long T,
+                                  unsigned* __restrict__ keys, unsigned* __restrict__ vals) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+       t += (long long)gridDim.x * blockDim.x) {
+    unsigned len = ranges[2 * t + 1] - ranges[2 * t];
+    keys[t] = 0xffffffffu - len;
+    vals[t] = (unsigned)t;
+  }
+}
+}  // namespace
+
+size_t tile_queue_workspace_size(long long T) {
+  return align256(4 * (T + 1)) * 3 + align256(sizeof(long long) * 2) +
+         align256(4ull * kRadixBins * kRadixGrid);
+}
+
+int launch_tile_queue(const unsigned* ranges, long long T, unsigned* order, void* ws,
+                      size_t ws_bytes, cudaStream_t st) {
+  if (ws_bytes < tile_queue_workspace_size(T)) return GS_ERR_INVALID_ARG;
+  if (T == 0) return GS_OK;
+  char* p = reinterpret_cast<char*>(ws);
+  unsigned* k0 = reinterpret_cast<unsigned*>(p);
+  p += align256(4 * (T + 1));
+  unsigned* k1 = reinterpret_cast<unsigned*>(p);
+  p += align256(4 * (T + 1));
+  unsigned* v1 = reinterpret_cast<unsigned*>(p);
+  p += align256(4 * (T + 1));
+  long long* n_dev = reinterpret_cast<long long*>(p);
+  p += align256(sizeof(long long) * 2);
+  unsigned* hist = reinterpret_cast<unsigned*>(p);
+  GS_TRY_CUDA(cudaMemcpyAsync(n_dev, &T, sizeof(long long), cudaMemcpyHostToDevice, st));
+  unsigned grid = (unsigned)std::min<long long>((T + 255) / 256, 1024);
+  // 4 passes (even): the result ends in the first buffer, i.e. `order`
+  queue_keys_kernel<<<grid, 256, 0, st>>>(ranges, T, k0, order);
+  count_launches(1);
+  unsigned* k[2] = {k0, k1};
+  unsigned* v[2] = {order, v1};
+  radix_sort(k, v, n_dev, T, 32, hist, st);
+  return check_launch();
+}
+
+}  // namespace gs

@@ -1,0 +1,510 @@
+// preprocess.cu -- per-Gaussian projection (forward) and its adjoint.
+//
+// Forward (Sec. 3, Background): Sigma = R S S^T R^T from the normalised
+// quaternion and s = exp(log_scale); EWA splatting Sigma' = J W Sigma W^T J^T
+// + dilation I with the perspective Jacobian J at the camera-space mean; the
+// conic Sigma'^-1; opacity sigmoid(logit); real SH colour up to degree 3,
+// + 0.5, clamped at 0; the 3-sigma radius and the 16x16 tile rect.
+//
+// One thread per Gaussian loops over the views, so the view-independent
+// part (activations, Sigma) is computed once.  Parameter loads are
+// coalesced across the warp; quaternions and SH rows use 16-byte loads.
+//
+// Backward: hand-derived adjoint of the same steps, one thread per
+// Gaussian, summing over views; Sigma's gradient is accumulated over views
+// and pushed to scale and rotation once.
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+// Real SH basis up to degree 3 (orthonormal, Condon-Shortley phase), order
+// (l, m), m = -l..l, at a unit direction.
+constexpr float kY0 = 0.28209479177387814f;   // sqrt(1/(4 pi))
+constexpr float kY1 = 0.48860251190291992f;   // sqrt(3/(4 pi))
+constexpr float kY2a = 1.0925484305920792f;   // sqrt(15/pi)/2
+constexpr float kY2b = 0.31539156525252005f;  // sqrt(5/pi)/4
+constexpr float kY2c = 0.54627421529603959f;  // sqrt(15/pi)/4
+constexpr float kY3a = 0.59004358992664352f;  // sqrt(35/(2 pi))/4
+constexpr float kY3b = 2.8906114426405538f;   // sqrt(105/pi)/2
+constexpr float kY3c = 0.45704579946446572f;  // sqrt(21/(2 pi))/4
+constexpr float kY3d = 0.3731763325901154f;   // sqrt(7/pi)/4
+constexpr float kY3e = 1.4453057213202769f;   // sqrt(105/pi)/4
+
+__device__ __forceinline__ int sh_count(int deg) { return (deg + 1) * (deg + 1); }
+
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float* Y) {
+  Y[0] = kY0;
+  if (deg < 1) return;
+  Y[1] = -kY1 * y;
+  Y[2] = kY1 * z;
+  Y[3] = -kY1 * x;
+  if (deg < 2) return;
+  float xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = kY2a * x * y;
+  Y[5] = -kY2a * y * z;
+  Y[6] = kY2b * (2.f * zz - xx - yy);
+  Y[7] = -kY2a * x * z;
+  Y[8] = kY2c * (xx - yy);
+  if (deg < 3) return;
+  Y[9] = -kY3a * y * (3.f * xx - yy);
+  Y[10] = kY3b * x * y * z;
+  Y[11] = -kY3c * y * (4.f * zz - xx - yy);
+  Y[12] = kY3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+  Y[13] = -kY3c * x * (4.f * zz - xx - yy);
+  Y[14] = kY3e * z * (xx - yy);
+  Y[15] = -kY3a * x * (xx - 3.f * yy);
+}
+
+// Gradient of each basis polynomial with respect to (x, y, z), contracted
+// with coefficients c[k]: returns sum_k c[k] grad Y_k.
+__device__ __forceinline__ float3 sh_basis_grad_dot(int deg, float x, float y, float z,
+                                                    const float* c) {
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+  if (deg < 1) return make_float3(0.f, 0.f, 0.f);
+  gy += -kY1 * c[1];
+  gz += kY1 * c[2];
+  gx += -kY1 * c[3];
+  if (deg >= 2) {
+    gx += kY2a * y * c[4];
+    gy += kY2a * x * c[4];
+    gy += -kY2a * z * c[5];
+    gz += -kY2a * y * c[5];
+    gx += -2.f * kY2b * x * c[6];
+    gy += -2.f * kY2b * y * c[6];
+    gz += 4.f * kY2b * z * c[6];
+    gx += -kY2a * z * c[7];
+    gz += -kY2a * x * c[7];
+    gx += 2.f * kY2c * x * c[8];
+    gy += -2.f * kY2c * y * c[8];
+  }
+  if (deg >= 3) {
+    float xx = x * x, yy = y * y, zz = z * z;
+    gx += -6.f * kY3a * x * y * c[9];
+    gy += -kY3a * (3.f * xx - 3.f * yy) * c[9];
+    gx += kY3b * y * z * c[10];
+    gy += kY3b * x * z * c[10];
+    gz += kY3b * x * y * c[10];
+    gx += 2.f * kY3c * x * y * c[11];
+    gy += -kY3c * (4.f * zz - xx - 3.f * yy) * c[11];
+    gz += -8.f * kY3c * y * z * c[11];
+    gx += -6.f * kY3d * x * z * c[12];
+    gy += -6.f * kY3d * y * z * c[12];
+    gz += kY3d * (6.f * zz - 3.f * xx - 3.f * yy) * c[12];
+    gx += -kY3c * (4.f * zz - 3.f * xx - yy) * c[13];
+    gy += 2.f * kY3c * x * y * c[13];
+    gz += -8.f * kY3c * x * z * c[13];
+    gx += 2.f * kY3e * x * z * c[14];
+    gy += -2.f * kY3e * y * z * c[14];
+    gz += kY3e * (xx - yy) * c[14];
+    gx += -kY3a * (3.f * xx - 3.f * yy) * c[15];
+    gy += 6.f * kY3a * x * y * c[15];
+  }
+  return make_float3(gx, gy, gz);
+}
+
+// Loads SH coefficient k (3 channels) of Gaussian g.
+__device__ __forceinline__ float3 load_sh(const float* sh, long long g, int stride, int k) {
+  const float* p = sh + (g * stride + k) * 3;
+  return make_float3(__ldg(p), __ldg(p + 1), __ldg(p + 2));
+}
+
+// Rotation matrix of a unit quaternion (w, x, y, z), row-major.
+__device__ __forceinline__ void quat_to_rot(float w, float x, float y, float z, float* R) {
+  R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+struct Activated {
+  float mean[3];
+  float s[3];      // scales
+  float q[4];      // unit quaternion
+  float qnorm;     // |q| before normalisation
+  float Rq[9];
+  float Sig[6];    // Sigma: xx, xy, xz, yy, yz, zz
+  float sigma;     // opacity
+};
+
+__device__ __forceinline__ Activated activate(const float* means, const float* log_scales,
+                                              const float* quats, const float* opacity_logits,
+                                              int g) {
+  Activated a;
+  a.mean[0] = __ldg(means + 3ll * g);
+  a.mean[1] = __ldg(means + 3ll * g + 1);
+  a.mean[2] = __ldg(means + 3ll * g + 2);
+  for (int k = 0; k < 3; ++k) a.s[k] = expf(__ldg(log_scales + 3ll * g + k));
+  float4 q = __ldg(reinterpret_cast<const float4*>(quats) + g);
+  float n2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+  a.qnorm = sqrtf(n2);
+  float inv = rsqrtf(n2);
+  a.q[0] = q.x * inv; a.q[1] = q.y * inv; a.q[2] = q.z * inv; a.q[3] = q.w * inv;
+  quat_to_rot(a.q[0], a.q[1], a.q[2], a.q[3], a.Rq);
+  float M[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) M[i * 3 + j] = a.Rq[i * 3 + j] * a.s[j];
+  a.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+  a.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+  a.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+  a.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+  a.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+  a.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+  float o = __ldg(opacity_logits + g);
+  a.sigma = 1.f / (1.f + expf(-o));
+  return a;
+}
+
+// Camera-space mean.  The depth is the FP32 rounding of the FP64 value
+// ((R20 mx + R21 my) + R22 mz) + t2 (products of FP32 values are exact in
+// FP64, so the result does not depend on FMA contraction).
+__device__ __forceinline__ float depth_of(const CamInfo& c, const float* m) {
+  double z = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)c.R[6], (double)m[0]),
+                                           __dmul_rn((double)c.R[7], (double)m[1])),
+                                 __dmul_rn((double)c.R[8], (double)m[2])),
+                       (double)c.t[2]);
+  return __double2float_rn(z);
+}
+
+struct Projected {
+  bool ok;
+  float tx, ty, tz, ux, uy;
+  bool clx, cly;       // Jacobian clamp active in x / y
+  float J00, J02, J11, J12;
+  float T[6];          // J W (2x3)
+  float A, B, C;       // Sigma' + dilation I
+  float det;
+  float ca, cb, cc;    // conic
+  float mx, my;        // 2D mean
+};
+
+__device__ __forceinline__ Projected project(const CamInfo& c, const Activated& a, float depth,
+                                             float dilation) {
+  Projected p;
+  const float* m = a.mean;
+  p.tx = c.R[0] * m[0] + c.R[1] * m[1] + c.R[2] * m[2] + c.t[0];
+  p.ty = c.R[3] * m[0] + c.R[4] * m[1] + c.R[5] * m[2] + c.t[1];
+  p.tz = depth;
+  float itz = 1.f / p.tz;
+  p.ux = p.tx * itz;
+  p.uy = p.ty * itz;
+  p.clx = p.ux < -c.limx || p.ux > c.limx;
+  p.cly = p.uy < -c.limy || p.uy > c.limy;
+  float uxc = fminf(fmaxf(p.ux, -c.limx), c.limx);
+  float uyc = fminf(fmaxf(p.uy, -c.limy), c.limy);
+  p.J00 = c.fx * itz;
+  p.J02 = -c.fx * uxc * itz;
+  p.J11 = c.fy * itz;
+  p.J12 = -c.fy * uyc * itz;
+  for (int j = 0; j < 3; ++j) {
+    p.T[j] = p.J00 * c.R[j] + p.J02 * c.R[6 + j];
+    p.T[3 + j] = p.J11 * c.R[3 + j] + p.J12 * c.R[6 + j];
+  }
+  const float* S = a.Sig;  // xx xy xz yy yz zz
+  float TS[6];
+  for (int i = 0; i < 2; ++i) {
+    const float* t = p.T + 3 * i;
+    TS[3 * i + 0] = t[0] * S[0] + t[1] * S[1] + t[2] * S[2];
+    TS[3 * i + 1] = t[0] * S[1] + t[1] * S[3] + t[2] * S[4];
+    TS[3 * i + 2] = t[0] * S[2] + t[1] * S[4] + t[2] * S[5];
+  }
+  p.A = TS[0] * p.T[0] + TS[1] * p.T[1] + TS[2] * p.T[2] + dilation;
+  p.B = TS[0] * p.T[3] + TS[1] * p.T[4] + TS[2] * p.T[5];
+  p.C = TS[3] * p.T[3] + TS[4] * p.T[4] + TS[5] * p.T[5] + dilation;
+  p.det = p.A * p.C - p.B * p.B;
+  p.ok = p.det > 0.f;
+  float idet = 1.f / p.det;
+  p.ca = p.C * idet;
+  p.cb = -p.B * idet;
+  p.cc = p.A * idet;
+  p.mx = c.fx * p.ux + c.cx;
+  p.my = c.fy * p.uy + c.cy;
+  return p;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) preprocess_kernel(
+    const float* __restrict__ means, const float* __restrict__ log_scales,
+    const float* __restrict__ quats, const float* __restrict__ opacity_logits,
+    const float* __restrict__ sh, int N, const CamTable ct, float dilation, float near_z,
+    int sh_deg, int sh_stride, gs_proj out) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= N) return;
+  Activated a = activate(means, log_scales, quats, opacity_logits, g);
+  const int K = sh_count(sh_deg);
+  for (int v = 0; v < ct.V; ++v) {
+    const CamInfo& c = ct.c[v];
+    long long row = (long long)v * N + g;
+    float depth = depth_of(c, a.mean);
+    out.depth[row] = depth;
+    bool vis = depth > near_z;
+    Projected p;
+    int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+    float r = 0.f;
+    if (vis) {
+      p = project(c, a, depth, dilation);
+      vis = p.ok && isfinite(p.mx) && isfinite(p.my) && isfinite(p.ca) && isfinite(p.cb) &&
+            isfinite(p.cc);
+    }
+    if (vis) {
+      // larger eigenvalue of [[A, B], [B, C]] in the cancellation-free form
+      float hd = 0.5f * (p.A - p.C);
+      float lam = 0.5f * (p.A + p.C) + sqrtf(hd * hd + p.B * p.B);
+      r = ceilf(3.f * sqrtf(lam));
+      const float inv16 = 1.f / kTile;
+      float fx0 = floorf((p.mx - r) * inv16), fx1 = floorf((p.mx + r) * inv16) + 1.f;
+      float fy0 = floorf((p.my - r) * inv16), fy1 = floorf((p.my + r) * inv16) + 1.f;
+      x0 = (int)fminf(fmaxf(fx0, 0.f), (float)c.TX);
+      x1 = (int)fminf(fmaxf(fx1, 0.f), (float)c.TX);
+      y0 = (int)fminf(fmaxf(fy0, 0.f), (float)c.TY);
+      y1 = (int)fminf(fmaxf(fy1, 0.f), (float)c.TY);
+      vis = (x1 > x0) && (y1 > y0) && isfinite(r);
+    }
+    if (!vis) {
+      reinterpret_cast<int4*>(out.rect)[row] = make_int4(0, 0, 0, 0);
+      out.tiles_touched[row] = 0u;
+      if (out.radius) out.radius[row] = 0;
+      continue;
+    }
+    // SH colour at the direction from the camera centre to the mean
+    float vx = a.mean[0] - c.cp[0], vy = a.mean[1] - c.cp[1], vz = a.mean[2] - c.cp[2];
+    float il = rsqrtf(vx * vx + vy * vy + vz * vz);
+    float Y[16];
+    sh_basis(sh_deg, vx * il, vy * il, vz * il, Y);
+    float cr = 0.5f, cg = 0.5f, cbl = 0.5f;
+    for (int k = 0; k < K; ++k) {
+      float3 s = load_sh(sh, g, sh_stride, k);
+      cr += Y[k] * s.x;
+      cg += Y[k] * s.y;
+      cbl += Y[k] * s.z;
+    }
+    cr = fmaxf(cr, 0.f);
+    cg = fmaxf(cg, 0.f);
+    cbl = fmaxf(cbl, 0.f);
+
+    Splat s;
+    s.mx = p.mx;
+    s.my = p.my;
+    s.A2 = -0.5f * kLog2e * p.ca;
+    s.B2 = -kLog2e * p.cb;
+    s.C2 = -0.5f * kLog2e * p.cc;
+    s.L2S = log2f(a.sigma);
+    s.R = cr;
+    s.G = cg;
+    s.B = cbl;
+    s.sigma = a.sigma;
+    store_record<DT>(out.records, row, s);
+    reinterpret_cast<int4*>(out.rect)[row] = make_int4(x0, y0, x1, y1);
+    out.tiles_touched[row] = (unsigned)((x1 - x0) * (y1 - y0));
+    if (out.radius) out.radius[row] = (int)r;
+    if (out.mean2d) reinterpret_cast<float2*>(out.mean2d)[row] = make_float2(p.mx, p.my);
+    if (out.conic_opacity)
+      reinterpret_cast<float4*>(out.conic_opacity)[row] = make_float4(p.ca, p.cb, p.cc, a.sigma);
+    if (out.rgb) {
+      out.rgb[3 * row] = cr;
+      out.rgb[3 * row + 1] = cg;
+      out.rgb[3 * row + 2] = cbl;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the projection.  grad2d rows: dL/d(mx, my, a, b, c, sigma, r, g, b).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) preprocess_bwd_kernel(
+    const float* __restrict__ means, const float* __restrict__ log_scales,
+    const float* __restrict__ quats, const float* __restrict__ opacity_logits,
+    const float* __restrict__ sh, int N, const CamTable ct, float dilation, float near_z,
+    int sh_deg, int sh_stride, const unsigned* __restrict__ tiles_touched,
+    const float* __restrict__ grad2d, float* __restrict__ g_means, float* __restrict__ g_ls,
+    float* __restrict__ g_quats, float* __restrict__ g_opac, float* __restrict__ g_sh) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= N) return;
+  const int K = sh_count(sh_deg);
+  for (int k = 0; k < sh_stride * 3; ++k) g_sh[(long long)g * sh_stride * 3 + k] = 0.f;
+
+  Activated a = activate(means, log_scales, quats, opacity_logits, g);
+  float gm[3] = {0.f, 0.f, 0.f};
+  float gSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma, symmetric (xx xy xz yy yz zz),
+                                                   // off-diagonals hold the (i,j) entry
+  float gsig = 0.f;
+  for (int v = 0; v < ct.V; ++v) {
+    long long row = (long long)v * N + g;
+    if (tiles_touched[row] == 0u) continue;
+    const float4* G4 = reinterpret_cast<const float4*>(grad2d + row * 12);
+    float4 G0 = G4[0], G1 = G4[1], G2 = G4[2];
+    // G0 = (mx, my, a, b), G1 = (c, sigma, r, g), G2 = (b, pad, pad, pad)
+    const CamInfo& c = ct.c[v];
+    float depth = depth_of(c, a.mean);
+    Projected p = project(c, a, depth, dilation);
+
+    gsig += G1.y;
+
+    // --- colour -> SH coefficients and view direction
+    float vx = a.mean[0] - c.cp[0], vy = a.mean[1] - c.cp[1], vz = a.mean[2] - c.cp[2];
+    float il = rsqrtf(vx * vx + vy * vy + vz * vz);
+    float dx = vx * il, dy = vy * il, dz = vz * il;
+    float Y[16];
+    sh_basis(sh_deg, dx, dy, dz, Y);
+    float raw[3] = {0.5f, 0.5f, 0.5f};
+    for (int k = 0; k < K; ++k) {
+      float3 s = load_sh(sh, g, sh_stride, k);
+      raw[0] += Y[k] * s.x;
+      raw[1] += Y[k] * s.y;
+      raw[2] += Y[k] * s.z;
+    }
+    float grgb[3] = {raw[0] < 0.f ? 0.f : G1.z, raw[1] < 0.f ? 0.f : G1.w,
+                     raw[2] < 0.f ? 0.f : G2.x};
+    float cdot[16];
+    for (int k = 0; k < K; ++k) {
+      float3 s = load_sh(sh, g, sh_stride, k);
+      float* gs = g_sh + ((long long)g * sh_stride + k) * 3;
+      gs[0] += Y[k] * grgb[0];
+      gs[1] += Y[k] * grgb[1];
+      gs[2] += Y[k] * grgb[2];
+      cdot[k] = s.x * grgb[0] + s.y * grgb[1] + s.z * grgb[2];
+    }
+    if (sh_deg > 0) {
+      float3 gd = sh_basis_grad_dot(sh_deg, dx, dy, dz, cdot);
+      float dd = gd.x * dx + gd.y * dy + gd.z * dz;
+      gm[0] += (gd.x - dx * dd) * il;
+      gm[1] += (gd.y - dy * dd) * il;
+      gm[2] += (gd.z - dz * dd) * il;
+    }
+
+    // --- conic -> Sigma' (with dilation):  dL/dSigma' = -K Gk K
+    float ka = p.ca, kb = p.cb, kc = p.cc;
+    float ga = G0.z, gb = G0.w, gc = G1.x;
+    float M00 = ka * ka * ga + ka * kb * gb + kb * kb * gc;
+    float M01 = ka * kb * ga + 0.5f * (kb * kb + ka * kc) * gb + kb * kc * gc;
+    float M11 = kb * kb * ga + kb * kc * gb + kc * kc * gc;
+    float GS00 = -M00, GS01 = -M01, GS11 = -M11;  // symmetric dL/dSigma' (full matrix entries)
+
+    // --- Sigma' = T Sigma T^T: dL/dSigma += T^T GS T ; dL/dT = 2 GS T Sigma
+    const float* T = p.T;
+    float GT_[6];  // GS T (2x3)
+    for (int j = 0; j < 3; ++j) {
+      GT_[j] = GS00 * T[j] + GS01 * T[3 + j];
+      GT_[3 + j] = GS01 * T[j] + GS11 * T[3 + j];
+    }
+    // T^T (GS T): 3x3 symmetric
+    gSig[0] += T[0] * GT_[0] + T[3] * GT_[3];
+    gSig[1] += T[0] * GT_[1] + T[3] * GT_[4];
+    gSig[2] += T[0] * GT_[2] + T[3] * GT_[5];
+    gSig[3] += T[1] * GT_[1] + T[4] * GT_[4];
+    gSig[4] += T[1] * GT_[2] + T[4] * GT_[5];
+    gSig[5] += T[2] * GT_[2] + T[5] * GT_[5];
+    const float* S = a.Sig;
+    float gT[6];
+    for (int i = 0; i < 2; ++i) {
+      const float* gt = GT_ + 3 * i;
+      gT[3 * i + 0] = 2.f * (gt[0] * S[0] + gt[1] * S[1] + gt[2] * S[2]);
+      gT[3 * i + 1] = 2.f * (gt[0] * S[1] + gt[1] * S[3] + gt[2] * S[4]);
+      gT[3 * i + 2] = 2.f * (gt[0] * S[2] + gt[1] * S[4] + gt[2] * S[5]);
+    }
+    // --- T = J W
+    float gJ00 = gT[0] * c.R[0] + gT[1] * c.R[1] + gT[2] * c.R[2];
+    float gJ02 = gT[0] * c.R[6] + gT[1] * c.R[7] + gT[2] * c.R[8];
+    float gJ11 = gT[3] * c.R[3] + gT[4] * c.R[4] + gT[5] * c.R[5];
+    float gJ12 = gT[3] * c.R[6] + gT[4] * c.R[7] + gT[5] * c.R[8];
+    // --- J(t) and the 2D mean(t)
+    float itz = 1.f / p.tz;
+    float gtx = 0.f, gty = 0.f, gtz = 0.f;
+    gtz += -gJ00 * c.fx * itz * itz - gJ11 * c.fy * itz * itz;
+    if (p.clx) {
+      gtz += -gJ02 * p.J02 * itz;
+    } else {
+      gtx += -gJ02 * c.fx * itz * itz;
+      gtz += -2.f * gJ02 * p.J02 * itz;
+    }
+    if (p.cly) {
+      gtz += -gJ12 * p.J12 * itz;
+    } else {
+      gty += -gJ12 * c.fy * itz * itz;
+      gtz += -2.f * gJ12 * p.J12 * itz;
+    }
+    gtx += G0.x * c.fx * itz;
+    gty += G0.y * c.fy * itz;
+    gtz += -(G0.x * c.fx * p.ux + G0.y * c.fy * p.uy) * itz;
+    // --- t = W mean + t_w
+    gm[0] += c.R[0] * gtx + c.R[3] * gty + c.R[6] * gtz;
+    gm[1] += c.R[1] * gtx + c.R[4] * gty + c.R[7] * gtz;
+    gm[2] += c.R[2] * gtx + c.R[5] * gty + c.R[8] * gtz;
+  }
+  g_means[3ll * g] = gm[0];
+  g_means[3ll * g + 1] = gm[1];
+  g_means[3ll * g + 2] = gm[2];
+  g_opac[g] = gsig * a.sigma * (1.f - a.sigma);
+
+  // --- Sigma = M M^T with M = Rq diag(s):  dL/dM = 2 GSig M
+  float Gf[9] = {gSig[0], gSig[1], gSig[2], gSig[1], gSig[3], gSig[4], gSig[2], gSig[4], gSig[5]};
+  float M[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) M[i * 3 + j] = a.Rq[i * 3 + j] * a.s[j];
+  float GM[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      GM[i * 3 + j] = 2.f * (Gf[i * 3] * M[j] + Gf[i * 3 + 1] * M[3 + j] + Gf[i * 3 + 2] * M[6 + j]);
+  float GR[9];
+  for (int j = 0; j < 3; ++j) {
+    float gs_ = GM[j] * a.Rq[j] + GM[3 + j] * a.Rq[3 + j] + GM[6 + j] * a.Rq[6 + j];
+    g_ls[3ll * g + j] = gs_ * a.s[j];
+    for (int i = 0; i < 3; ++i) GR[i * 3 + j] = GM[i * 3 + j] * a.s[j];
+  }
+  // --- rotation matrix of the unit quaternion
+  float w = a.q[0], x = a.q[1], y = a.q[2], z = a.q[3];
+  float gw = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
+  float gx = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + z * GR[6] +
+                    w * GR[7] - 2.f * x * GR[8]);
+  float gy = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + z * GR[5] - w * GR[6] +
+                    z * GR[7] - 2.f * y * GR[8]);
+  float gz = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4] +
+                    y * GR[5] + x * GR[6] + y * GR[7]);
+  // --- normalisation q / |q|
+  float dotq = w * gw + x * gx + y * gy + z * gz;
+  float iq = 1.f / a.qnorm;
+  float4 gq = make_float4((gw - w * dotq) * iq, (gx - x * dotq) * iq, (gy - y * dotq) * iq,
+                          (gz - z * dotq) * iq);
+  reinterpret_cast<float4*>(g_quats)[g] = gq;
+}
+
+}  // namespace
+
+int launch_preprocess(const float* means, const float* log_scales, const float* quats,
+                      const float* opacity_logits, const float* sh, int N, const CamTable& ct,
+                      const gs_params* prm, const gs_proj* out, cudaStream_t st) {
+  if (N == 0) return GS_OK;
+  dim3 block(256), grid((N + 255) / 256);
+  switch (prm->attr_dtype) {
+    case GS_ATTR_F32:
+      preprocess_kernel<GS_ATTR_F32><<<grid, block, 0, st>>>(means, log_scales, quats, opacity_logits,
+          sh, N, ct, prm->dilation, prm->near_z, prm->sh_degree, prm->sh_stride, *out);
+      break;
+    case GS_ATTR_F16:
+      preprocess_kernel<GS_ATTR_F16><<<grid, block, 0, st>>>(means, log_scales, quats, opacity_logits,
+          sh, N, ct, prm->dilation, prm->near_z, prm->sh_degree, prm->sh_stride, *out);
+      break;
+    case GS_ATTR_BF16:
+      preprocess_kernel<GS_ATTR_BF16><<<grid, block, 0, st>>>(means, log_scales, quats, opacity_logits,
+          sh, N, ct, prm->dilation, prm->near_z, prm->sh_degree, prm->sh_stride, *out);
+      break;
+    default:
+      return GS_ERR_INVALID_ARG;
+  }
+  count_launches(1);
+  return check_launch();
+}
+
+int launch_preprocess_bwd(const float* means, const float* log_scales, const float* quats,
+                          const float* opacity_logits, const float* sh, int N, const CamTable& ct,
+                          const gs_params* prm, const unsigned* tiles_touched, const float* grad2d,
+                          float* g_means, float* g_ls, float* g_quats, float* g_opac, float* g_sh,
+                          cudaStream_t st) {
+  if (N == 0) return GS_OK;
+  preprocess_bwd_kernel<<<(N + 255) / 256, 256, 0, st>>>(
+      means, log_scales, quats, opacity_logits, sh, N, ct, prm->dilation, prm->near_z,
+      prm->sh_degree, prm->sh_stride, tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh);
+  count_launches(1);
+  return check_launch();
+}
+
+}  // namespace gs

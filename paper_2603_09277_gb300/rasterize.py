@@ -1,0 +1,244 @@
+"""Device-memory owner and autograd wrappers over the libgs C ABI.
+
+``Rasterizer`` allocates every buffer the hot path needs (torch tensors used
+as device memory) and calls the C entry points in order; each step of the
+computation runs in libgs kernels.  ``rasterize`` / ``l1_entropy_loss`` are
+torch.autograd.Function wrappers for training loops.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import gs
+
+PARAM_KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+def scene_to_device(scene, device="cuda", requires_grad=False):
+    """numpy scene dict -> dict of contiguous float32 CUDA tensors."""
+    out = {}
+    for k in PARAM_KEYS:
+        t = torch.as_tensor(scene[k], dtype=torch.float32).contiguous().to(device)
+        out[k] = t.requires_grad_(requires_grad) if requires_grad else t
+    out["sh_degree"] = int(scene["sh_degree"])
+    return out
+
+
+def targets_to_device(targets, device="cuda"):
+    """List of [H,W,3] arrays -> one flat [sum HW, 3] float32 tensor."""
+    return torch.cat([torch.as_tensor(t, dtype=torch.float32).reshape(-1, 3) for t in targets]).to(
+        device).contiguous()
+
+
+class Rasterizer:
+    """Buffers and calls for one fixed set of views and Gaussian count.
+
+    cams: list of camera dicts; prm: threshold dict (see scenes.params);
+    N: Gaussian count; attr_dtype: "f32" | "f16" | "bf16" record staging;
+    persistent: 0 (one CTA per tile) or the CTA count of a persistent launch
+    claiming tiles from a list-length-ordered queue (the batched form).
+    """
+
+    def __init__(self, cams, prm, N, sh_stride=16, attr_dtype="f32", device="cuda",
+                 pair_capacity=None, persistent=0, keep_debug=False):
+        self.device = torch.device(device)
+        self.cams = cams
+        self.cams_c = gs.make_cameras(cams)
+        self.prm = dict(prm)
+        self.prm_c = gs.make_params(prm, sh_stride, attr_dtype)
+        self.N = int(N)
+        self.V = len(cams)
+        self.sh_stride = sh_stride
+        self.rows = self.N * self.V
+        self.total_tiles = gs.gs_total_tiles(self.cams_c)
+        self.total_pixels = gs.gs_total_pixels(self.cams_c)
+        if self.total_tiles < 0:
+            raise ValueError("invalid cameras")
+        dev = self.device
+        i32 = dict(dtype=torch.int32, device=dev)
+        f32 = dict(dtype=torch.float32, device=dev)
+        rb = gs.gs_record_bytes(self.prm_c.attr_dtype)
+        R = max(self.rows, 1)
+        self.records = torch.empty(R * rb, dtype=torch.uint8, device=dev)
+        self.depth = torch.empty(R, **f32)
+        self.rect = torch.empty(R, 4, **i32)
+        self.tiles_touched = torch.empty(R, **i32)
+        self.keep_debug = keep_debug
+        if keep_debug:
+            self.radius = torch.empty(R, **i32)
+            self.mean2d = torch.empty(R, 2, **f32)
+            self.conic_opacity = torch.empty(R, 4, **f32)
+            self.rgb = torch.empty(R, 3, **f32)
+            self.proj_c = gs.make_proj(self.records, self.depth, self.rect, self.tiles_touched,
+                                       self.radius, self.mean2d, self.conic_opacity, self.rgb)
+        else:
+            self.proj_c = gs.make_proj(self.records, self.depth, self.rect, self.tiles_touched)
+        self.tile_ranges = torch.zeros(max(self.total_tiles, 1), 2, **i32)
+        self.num_pairs_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.status_dev = torch.zeros(1, **i32)
+        self.capacity = 0
+        self._alloc_pairs(pair_capacity if pair_capacity is not None else max(1 << 20, 8 * self.rows))
+        P = max(self.total_pixels, 1)
+        self.image = torch.empty(P, 3, **f32)
+        self.final_T = torch.empty(P, **f32)
+        self.last_idx = torch.empty(P, **i32)
+        self.entropy = torch.empty(P, **f32)
+        self.loss_dev = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.dL_dimage = torch.empty(P, 3, **f32)
+        self.dL_dentropy = torch.empty(P, **f32)
+        self.loss_ws = torch.empty(gs.gs_loss_workspace_size(P), dtype=torch.uint8, device=dev)
+        self.grad2d = torch.empty(R, 12, **f32)
+        self.grads = {
+            "means": torch.empty(max(self.N, 1), 3, **f32),
+            "log_scales": torch.empty(max(self.N, 1), 3, **f32),
+            "quats": torch.empty(max(self.N, 1), 4, **f32),
+            "opacity_logits": torch.empty(max(self.N, 1), **f32),
+            "sh": torch.empty(max(self.N, 1), sh_stride, 3, **f32),
+        }
+        self.stats = torch.zeros(2, dtype=torch.int64, device=dev)
+        self.persistent = int(persistent)
+        self.tile_order = None
+        if self.persistent:
+            self.tile_order = torch.empty(max(self.total_tiles, 1), **i32)
+            self.work_counter = torch.zeros(1, **i32)
+            self.queue_ws = torch.empty(gs.gs_tile_queue_workspace_size(self.total_tiles),
+                                        dtype=torch.uint8, device=dev)
+        self.num_pairs = None
+
+    def _launch(self, stats=False, events=None):
+        ev = events if events is not None else (None, None)
+        if self.persistent:
+            return gs.make_launch(self.tile_order, self.work_counter, self.persistent,
+                                  self.stats if stats else None, ev[0], ev[1])
+        return gs.make_launch(None, None, 0, self.stats if stats else None, ev[0], ev[1])
+
+    def _alloc_pairs(self, cap):
+        cap = int(min(max(cap, 1), (1 << 32) - 1))
+        self.capacity = cap
+        dev = self.device
+        self.sorted_vals = torch.empty(cap, dtype=torch.int32, device=dev)
+        ws = gs.gs_bin_sort_workspace_size(self.rows, cap, self.total_tiles)
+        self.bin_ws = torch.empty(ws, dtype=torch.uint8, device=dev)
+        self.sorted_keys = None
+
+    # -- steps -------------------------------------------------------------
+    def preprocess(self, p, stream=None):
+        gs.gs_preprocess(p["means"], p["log_scales"], p["quats"], p["opacity_logits"], p["sh"],
+                         self.N, self.cams_c, self.prm_c, self.proj_c, stream)
+
+    def bin_sort(self, sync=True, keys=False, stream=None):
+        """Builds the per-tile lists.  With sync, regrows the pair buffers on
+        overflow and returns the pair count; without, returns None (graph form)."""
+        if keys and (self.sorted_keys is None or self.sorted_keys.numel() < self.capacity):
+            self.sorted_keys = torch.empty(self.capacity, dtype=torch.int64, device=self.device)
+        while True:
+            st, P = gs.gs_bin_sort(self.proj_c, self.N, self.cams_c, self.bin_ws, self.capacity,
+                                   self.sorted_vals, self.sorted_keys if keys else None,
+                                   self.tile_ranges, self.num_pairs_dev, self.status_dev,
+                                   sync_count=sync, stream=stream)
+            if st == gs.GS_OK:
+                break
+            self._alloc_pairs(int(P * 1.25) + 1024)
+            if keys:
+                self.sorted_keys = torch.empty(self.capacity, dtype=torch.int64, device=self.device)
+        self.num_pairs = P
+        if self.persistent:
+            gs.gs_tile_queue(self.tile_ranges, self.total_tiles, self.tile_order, self.queue_ws,
+                             stream)
+        return P
+
+    def render_fwd(self, stats=False, stream=None, events=None):
+        """events: optional (begin, end) recorded torch.cuda.Events placed
+        around the blending kernel."""
+        if stats:
+            self.stats.zero_()
+        gs.gs_render_fwd(self.proj_c, self.N, self.cams_c, self.prm_c, self.sorted_vals,
+                         self.tile_ranges, self.image, self.final_T, self.last_idx, self.entropy,
+                         self._launch(stats, events), stream)
+
+    def loss(self, target, gamma, stream=None):
+        gs.gs_loss_l1_entropy(self.image, target, self.entropy, self.cams_c, gamma, self.loss_dev,
+                              self.dL_dimage, self.dL_dentropy, self.loss_ws, stream)
+        return self.loss_dev
+
+    def render_bwd(self, p, dL_dimage=None, dL_dentropy="auto", stream=None, events=None):
+        dimg = self.dL_dimage if dL_dimage is None else dL_dimage
+        dent = self.dL_dentropy if isinstance(dL_dentropy, str) else dL_dentropy
+        g = self.grads
+        gs.gs_render_bwd(self.proj_c, self.N, self.cams_c, self.prm_c, self.sorted_vals,
+                         self.tile_ranges, self.final_T, self.last_idx, dimg, dent, p["means"],
+                         p["log_scales"], p["quats"], p["opacity_logits"], p["sh"], self.grad2d,
+                         g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"],
+                         self._launch(False, events), stream)
+        return g
+
+    def step(self, p, target, gamma, sync=True, stream=None):
+        """One forward + backward of L1 + gamma * entropy; returns the device loss."""
+        self.preprocess(p, stream)
+        self.bin_sort(sync=sync, stream=stream)
+        self.render_fwd(stream=stream)
+        self.loss(target, gamma, stream)
+        self.render_bwd(p, stream=stream)
+        return self.loss_dev
+
+    # -- views of per-pixel outputs ------------------------------------------
+    def view_slices(self):
+        out, off = [], 0
+        for c in self.cams:
+            n = c["width"] * c["height"]
+            out.append((off, off + n, c["height"], c["width"]))
+            off += n
+        return out
+
+    def image_of(self, v):
+        a, b, H, W = self.view_slices()[v]
+        return self.image[a:b].reshape(H, W, 3)
+
+
+class _Rasterize(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, rast):
+        p = {"means": means.contiguous(), "log_scales": log_scales.contiguous(),
+             "quats": quats.contiguous(), "opacity_logits": opacity_logits.contiguous(),
+             "sh": sh.contiguous()}
+        rast.preprocess(p)
+        rast.bin_sort()
+        rast.render_fwd()
+        ctx.rast = rast
+        ctx.save_for_backward(*[p[k] for k in PARAM_KEYS])
+        return rast.image.clone(), rast.entropy.clone()
+
+    @staticmethod
+    def backward(ctx, g_image, g_entropy):
+        rast = ctx.rast
+        p = dict(zip(PARAM_KEYS, ctx.saved_tensors))
+        g_image = g_image.contiguous() if g_image is not None else torch.zeros_like(rast.image)
+        g_entropy = g_entropy.contiguous() if g_entropy is not None else None
+        g = rast.render_bwd(p, g_image, g_entropy)
+        return (g["means"].clone(), g["log_scales"].clone(), g["quats"].clone(),
+                g["opacity_logits"].clone(), g["sh"].clone(), None)
+
+
+def rasterize(params, rast):
+    """Differentiable render: returns (image [sum HW, 3], entropy [sum HW])."""
+    return _Rasterize.apply(params["means"], params["log_scales"], params["quats"],
+                            params["opacity_logits"], params["sh"], rast)
+
+
+class _L1Entropy(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, image, entropy, target, rast, gamma):
+        gs.gs_loss_l1_entropy(image.contiguous(), target, entropy.contiguous(), rast.cams_c, gamma,
+                              rast.loss_dev, rast.dL_dimage, rast.dL_dentropy, rast.loss_ws)
+        ctx.save_for_backward(rast.dL_dimage.clone(), rast.dL_dentropy.clone())
+        return rast.loss_dev.clone().to(torch.float32).reshape(())
+
+    @staticmethod
+    def backward(ctx, g):
+        di, de = ctx.saved_tensors
+        return di * g, de * g, None, None, None
+
+
+def l1_entropy_loss(image, entropy, target, rast, gamma):
+    """L = (1/V) sum_v [mean L1_v + gamma mean H_v], computed by libgs."""
+    return _L1Entropy.apply(image, entropy, target, rast, gamma)

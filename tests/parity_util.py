@@ -1,0 +1,120 @@
+"""Shared helpers of the GPU parity tests: run the libgs path through the
+C ABI, run the oracle, and derive the threshold-boundary exclusions.
+
+Exclusion rules (from the oracle only, never from the GPU results):
+- a Gaussian whose rect could round differently in FP32 (oracle boundary
+  flag) is left out of the bit-exact rect/list checks, and every tile within
+  one tile of its rect is left out of the pixel checks (its list may hold
+  one entry more or less);
+- a pixel whose smallest relative distance of any threshold test
+  (alpha_min, alpha_max, t_min) is below MARGIN may take the other branch in
+  FP32 and is left out of the pixel checks;
+- gradients are compared per tensor on the relative norm, and element-wise
+  on the Gaussians that no excluded pixel evaluates.
+"""
+import numpy as np
+import torch
+
+import oracle
+from paper_2603_09277_gb300.rasterize import Rasterizer, scene_to_device, targets_to_device
+
+MARGIN = 1e-4       # relative threshold margin below which a pixel is excluded
+IMG_TOL = 1e-5      # absolute, images / T / entropy (FP32 vs FP64)
+GRAD_TOL = 1e-4     # relative, gradient tensors (norm), FP32 vs FP64
+
+
+def run_gpu(scene, cams, prm, target=None, gamma=0.015, attr="f32", persistent=0,
+            dL_dimage=None, dL_dentropy=None, keys=True):
+    """Runs preprocess, bin_sort, render_fwd, loss (if target) and
+    render_bwd through the C ABI.  dL_dimage / dL_dentropy (numpy, per
+    pixel) override the loss gradients.  Returns numpy arrays."""
+    N = scene["means"].shape[0]
+    rast = Rasterizer(cams, prm, N, attr_dtype=attr, keep_debug=True, persistent=persistent)
+    p = scene_to_device(scene)
+    rast.preprocess(p)
+    P = rast.bin_sort(keys=keys)
+    rast.render_fwd(stats=True)
+    out = {"P": P}
+    if target is not None:
+        tgt = targets_to_device(target)
+        rast.loss(tgt, gamma)
+        out["loss"] = float(rast.loss_dev.item())
+    if dL_dimage is not None:
+        dimg = torch.as_tensor(np.ascontiguousarray(dL_dimage, np.float32).reshape(-1, 3)).cuda()
+        dent = (None if dL_dentropy is None else
+                torch.as_tensor(np.ascontiguousarray(dL_dentropy, np.float32).reshape(-1)).cuda())
+        rast.render_bwd(p, dimg, dent)
+    elif target is not None:
+        rast.render_bwd(p)
+    torch.cuda.synchronize()
+    n = lambda t: t.detach().cpu().numpy()
+    out.update({
+        "rast": rast,
+        "depth": n(rast.depth), "rect": n(rast.rect), "tiles": n(rast.tiles_touched),
+        "radius": n(rast.radius), "mean2d": n(rast.mean2d), "conic_opacity": n(rast.conic_opacity),
+        "rgb": n(rast.rgb), "ranges": n(rast.tile_ranges).astype(np.int64),
+        "vals": n(rast.sorted_vals)[:P].astype(np.int64) if P else np.zeros(0, np.int64),
+        "keys": (n(rast.sorted_keys)[:P].view(np.uint64) if (keys and P) else None),
+        "image": n(rast.image), "final_T": n(rast.final_T),
+        "last": n(rast.last_idx).astype(np.int64), "entropy": n(rast.entropy),
+        "stats": n(rast.stats),
+        "grad2d": n(rast.grad2d),
+        "grads": {k: n(v) for k, v in rast.grads.items()},
+    })
+    return out
+
+
+def view_pixels(cams):
+    out, off = [], 0
+    for c in cams:
+        n = c["width"] * c["height"]
+        out.append((off, off + n))
+        off += n
+    return out
+
+
+def view_tiles(cams):
+    out, off = [], 0
+    for c in cams:
+        tx, ty = oracle.tile_grid(c)
+        out.append((off, off + tx * ty))
+        off += tx * ty
+    return out
+
+
+def pixel_exclusion(ora_view, cam, margin=MARGIN):
+    """Boolean [H,W]: pixels left out of the pixel checks of one view."""
+    proj, fwd = ora_view["proj"], ora_view["fwd"]
+    W, H = cam["width"], cam["height"]
+    TX, TY = oracle.tile_grid(cam)
+    bad_tiles = np.zeros((TY, TX), bool)
+    for i in np.nonzero(proj["boundary"])[0]:
+        x0, y0, x1, y1 = proj["rect"][i]
+        if proj["tiles"][i] == 0:
+            # a culled-by-rect Gaussian may appear with a one-tile rect in FP32
+            x0 = y0 = 0
+            x1, y1 = TX, TY
+        bad_tiles[max(0, y0 - 1):min(TY, y1 + 1), max(0, x0 - 1):min(TX, x1 + 1)] = True
+    px_tiles = bad_tiles[np.arange(H)[:, None] // 16, np.arange(W)[None, :] // 16]
+    return px_tiles | (fwd["margin"] < margin)
+
+
+def gaussian_exclusion(ora_view, cam, bad_pixels):
+    """Boolean [N]: Gaussians in any list of a tile holding an excluded pixel,
+    or with the boundary flag."""
+    proj = ora_view["proj"]
+    ts, ids = ora_view["lists"]
+    TX, TY = oracle.tile_grid(cam)
+    N = proj["tiles"].size
+    bad = proj["boundary"].astype(bool).copy()
+    H, W = bad_pixels.shape
+    tiles_bad = np.zeros(TX * TY, bool)
+    ys, xs = np.nonzero(bad_pixels)
+    tiles_bad[(ys // 16) * TX + xs // 16] = True
+    for t in np.nonzero(tiles_bad)[0]:
+        bad[ids[ts[t]:ts[t + 1]]] = True
+    return bad
+
+
+def rel_norm_err(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))

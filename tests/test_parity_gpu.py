@@ -1,0 +1,419 @@
+"""GPU path (libgs through its C ABI) against the FP64 oracle on the same
+seeded inputs.  Integer outputs bit-exact, images within 1e-5 absolute,
+gradients within 1e-4 relative (tensor norm), with the threshold-boundary
+exclusions derived from the oracle (parity_util)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2603_09277_gb300 import scenes
+
+from parity_util import (GRAD_TOL, IMG_TOL, gaussian_exclusion, pixel_exclusion, rel_norm_err,
+                         run_gpu, view_pixels, view_tiles)
+
+pytestmark = pytest.mark.gpu
+
+GAMMA = scenes.GAMMA
+
+
+def _oracle_full(scene, cams, targets, prm, gamma=GAMMA):
+    L, views, grads, g9 = oracle.step(scene, cams, targets, prm, gamma)
+    return L, views, grads, g9
+
+
+def _stack_pixels(views, key, cams):
+    return np.concatenate([v["fwd"][key].reshape(c["width"] * c["height"], -1).squeeze(-1)
+                           if v["fwd"][key].ndim == 2 else
+                           v["fwd"][key].reshape(c["width"] * c["height"], -1)
+                           for v, c in zip(views, cams)])
+
+
+def check_projection(g, views, cams, N):
+    for v, cam in enumerate(cams):
+        pr = views[v]["proj"]
+        rows = slice(v * N, (v + 1) * N)
+        # depth key: FP32 of FP64 depth, bit-exact for every Gaussian in front of the camera
+        front = pr["depth"] > np.float32(0.2)
+        assert (g["depth"][rows][front].view(np.uint32) == pr["depth"][front].view(np.uint32)).all()
+        ok = ~pr["boundary"].astype(bool)
+        assert (g["tiles"][rows][ok] == pr["tiles"][ok]).all()
+        vis = ok & (pr["tiles"] > 0)
+        assert (g["rect"][rows][vis] == pr["rect"][vis]).all()
+        assert (g["radius"][rows][vis] == pr["radius"][vis]).all()
+        P9 = pr["P9"][vis]
+        assert np.abs(g["mean2d"][rows][vis] - P9[:, 0:2]).max() < 2e-3
+        conic = g["conic_opacity"][rows][vis][:, :3]
+        scale = np.abs(P9[:, 2:5]).max(1, keepdims=True)
+        assert (np.abs(conic - P9[:, 2:5]) / scale).max() < 1e-4
+        assert np.abs(g["conic_opacity"][rows][vis][:, 3] - P9[:, 5]).max() < 1e-6
+        assert np.abs(g["rgb"][rows][vis] - P9[:, 6:9]).max() < 1e-5
+
+
+def check_lists(g, views, cams, N):
+    vt = view_tiles(cams)
+    for v, cam in enumerate(cams):
+        ts, ids = views[v]["lists"]
+        flagged = views[v]["proj"]["boundary"].astype(bool)
+        t0, t1 = vt[v]
+        mism = 0
+        for t in range(t1 - t0):
+            a, b = g["ranges"][t0 + t]
+            glist = g["vals"][a:b] - v * N
+            olist = ids[ts[t]:ts[t + 1]]
+            if flagged.any():
+                glist = glist[~flagged[glist]]
+                olist = olist[~flagged[olist]]
+            if len(glist) != len(olist) or (glist != olist).any():
+                mism += 1
+        assert mism == 0
+    if g["keys"] is not None and len(g["vals"]):
+        tiles = (g["keys"] >> np.uint64(32)).astype(np.int64)
+        dbits = (g["keys"] & np.uint64(0xffffffff)).astype(np.uint32)
+        assert (np.diff(tiles) >= 0).all()
+        assert (dbits == g["depth"][g["vals"]].view(np.uint32)).all()
+
+
+def check_pixels(g, views, cams):
+    vp = view_pixels(cams)
+    worst = {}
+    for v, cam in enumerate(cams):
+        a, b = vp[v]
+        f = views[v]["fwd"]
+        bad = pixel_exclusion(views[v], cam).reshape(-1)
+        ok = ~bad
+        assert ok.mean() > 0.97, "too many excluded pixels"
+        img_err = np.abs(g["image"][a:b] - f["image"].reshape(-1, 3))[ok].max()
+        t_err = np.abs(g["final_T"][a:b] - f["final_T"].reshape(-1))[ok].max()
+        h_err = np.abs(g["entropy"][a:b] - f["entropy"].reshape(-1))[ok].max()
+        assert (g["last"][a:b][ok] == f["last"].reshape(-1)[ok]).all()
+        worst[v] = (img_err, t_err, h_err, int(bad.sum()))
+        assert img_err <= IMG_TOL, worst
+        assert t_err <= IMG_TOL, worst
+        assert h_err <= IMG_TOL, worst
+    return worst
+
+
+def check_grads(g, ora_grads, views, cams, N, K):
+    bad = np.zeros(N, bool)
+    for v, cam in enumerate(cams):
+        bp = pixel_exclusion(views[v], cam)
+        bad |= gaussian_exclusion(views[v], cam, bp)
+    res = {}
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        gg, oo = g["grads"][k], ora_grads[k]
+        if k == "sh":
+            gg, oo = gg[:, :K], oo[:, :K]
+        e = rel_norm_err(gg, oo)
+        res[k] = e
+        assert e <= GRAD_TOL, (k, e)
+        ok = ~bad
+        scale = np.abs(oo[ok]).max()
+        d = np.abs(gg[ok] - oo[ok])
+        # element-wise: 1e-4 relative with an absolute floor of 1e-4 of the
+        # tensor's largest entry (atomic summation order in FP32)
+        assert (d <= GRAD_TOL * np.abs(oo[ok]) + GRAD_TOL * scale).all(), k
+    return res
+
+
+@pytest.fixture(scope="module")
+def cfg1_case():
+    scene, cams, targets, prm = scenes.config1()
+    L, views, grads, g9 = _oracle_full(scene, cams, targets, prm)
+    # the GPU backward takes the oracle's loss gradients (no GPU value feeds the oracle)
+    g = run_gpu(scene, cams, prm, target=targets, dL_dimage=views[0]["dL_dC"],
+                dL_dentropy=views[0]["dL_dH"])
+    return scene, cams, targets, prm, L, views, grads, g
+
+
+def test_cfg1_projection(cfg1_case):
+    scene, cams, targets, prm, L, views, grads, g = cfg1_case
+    check_projection(g, views, cams, scene["means"].shape[0])
+
+
+def test_cfg1_lists(cfg1_case):
+    scene, cams, targets, prm, L, views, grads, g = cfg1_case
+    assert g["P"] == views[0]["lists"][0][-1] or views[0]["proj"]["boundary"].any()
+    check_lists(g, views, cams, scene["means"].shape[0])
+
+
+def test_cfg1_pixels(cfg1_case):
+    scene, cams, targets, prm, L, views, grads, g = cfg1_case
+    check_pixels(g, views, cams)
+    # blended-pair statistic equals the oracle's count on the same pixels
+    nb = views[0]["fwd"]["nblend"].sum()
+    assert abs(int(g["stats"][0]) - int(nb)) <= 0.001 * nb
+
+
+def test_cfg1_loss_value(cfg1_case):
+    scene, cams, targets, prm, L, views, grads, g = cfg1_case
+    assert g["loss"] == pytest.approx(L, rel=1e-5)
+
+
+def test_cfg1_gradients(cfg1_case):
+    scene, cams, targets, prm, L, views, grads, g = cfg1_case
+    check_grads(g, grads, views, cams, scene["means"].shape[0], 1)
+
+
+def test_loss_kernel_parity():
+    """gs_loss_l1_entropy against the oracle loss on a seeded random image."""
+    from paper_2603_09277_gb300.rasterize import Rasterizer, targets_to_device
+    cams = [scenes.camera(37, 23, 37.0), scenes.camera(64, 48, 64.0)]
+    rng = np.random.default_rng(3)
+    imgs = [rng.random((c["height"], c["width"], 3)).astype(np.float32) for c in cams]
+    ents = [rng.random((c["height"], c["width"])).astype(np.float32) for c in cams]
+    tg = scenes.noise_targets(cams, 4)
+    rast = Rasterizer(cams, scenes.params(), 1)
+    rast.image.copy_(targets_to_device(imgs))
+    rast.entropy.copy_(torch.cat([torch.as_tensor(e.reshape(-1)) for e in ents]).cuda())
+    rast.loss(targets_to_device(tg), 0.015)
+    torch.cuda.synchronize()
+    L = 0.0
+    dCs, dHs = [], []
+    for v in range(2):
+        Lv, dC, dH = oracle.loss(imgs[v], ents[v], tg[v], 0.015, 0.5)
+        L += Lv
+        dCs.append(dC.reshape(-1, 3))
+        dHs.append(dH.reshape(-1))
+    assert rast.loss_dev.item() == pytest.approx(L, rel=1e-6)
+    assert np.abs(rast.dL_dimage.cpu().numpy() - np.concatenate(dCs)).max() < 1e-12 + 1e-6 * np.abs(
+        np.concatenate(dCs)).max()
+    assert np.allclose(rast.dL_dentropy.cpu().numpy(), np.concatenate(dHs), rtol=1e-6)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_sh3_small_scene(seed):
+    """SH degree 3, rotated orbit camera, ragged image size, 20k Gaussians."""
+    scene = scenes.cluster_scene(20_000, seed=seed, radius=3.0)
+    pos = np.array([2.5, 0.4, -2.0])
+    cams = [scenes.camera(200, 137, 170.0, scenes.look_at(pos, (0.0, 0.0, 0.0)), pos)]
+    prm = scenes.params(sh_degree=3)
+    targets = scenes.noise_targets(cams, seed + 7)
+    L, views, grads, g9 = _oracle_full(scene, cams, targets, prm)
+    g = run_gpu(scene, cams, prm, target=targets, dL_dimage=views[0]["dL_dC"],
+                dL_dentropy=views[0]["dL_dH"])
+    N = scene["means"].shape[0]
+    check_projection(g, views, cams, N)
+    check_lists(g, views, cams, N)
+    check_pixels(g, views, cams)
+    check_grads(g, grads, views, cams, N, 16)
+
+
+def test_multiview_uneven_sizes():
+    """Three views of uneven size in one launch: every per-view output equals
+    the oracle's; gradients sum over views."""
+    scene = scenes.box_scene(6000, seed=2)
+    cams = scenes.yaw_cameras([(77, 51), (154, 102), (160, 96)], [0.0, 6.0, -9.0])
+    prm = scenes.params()
+    targets = scenes.noise_targets(cams, 3)
+    L, views, grads, g9 = _oracle_full(scene, cams, targets, prm)
+    dC = np.concatenate([v["dL_dC"].reshape(-1, 3) for v in views])
+    dH = np.concatenate([v["dL_dH"].reshape(-1) for v in views])
+    g = run_gpu(scene, cams, prm, target=targets, dL_dimage=dC, dL_dentropy=dH)
+    N = scene["means"].shape[0]
+    check_projection(g, views, cams, N)
+    check_lists(g, views, cams, N)
+    check_pixels(g, views, cams)
+    assert g["loss"] == pytest.approx(L, rel=1e-5)
+    check_grads(g, grads, views, cams, N, 1)
+
+
+def test_persistent_queue_matches_one_cta_per_tile():
+    """The persistent, list-length-ordered launch gives bit-identical forward
+    outputs and gradients equal up to FP32 atomic order."""
+    scene = scenes.box_scene(8000, seed=5)
+    cams = scenes.yaw_cameras([(100, 70), (200, 140), (64, 64)], [0.0, 4.0, -3.0])
+    prm = scenes.params()
+    targets = scenes.noise_targets(cams, 6)
+    a = run_gpu(scene, cams, prm, target=targets)
+    b = run_gpu(scene, cams, prm, target=targets, persistent=2 * 152)
+    for k in ("image", "final_T", "last", "entropy"):
+        assert (a[k] == b[k]).all(), k
+    for k in a["grads"]:
+        assert rel_norm_err(b["grads"][k], a["grads"][k]) < 1e-5, k
+    # the queue is ordered by list length, longest first
+    order = b["rast"].tile_order.cpu().numpy()
+    ln = (b["ranges"][:, 1] - b["ranges"][:, 0])[order]
+    assert (np.diff(ln) <= 0).all()
+    assert sorted(order.tolist()) == list(range(len(order)))
+
+
+@pytest.mark.parametrize("attr", ["f16", "bf16"])
+def test_mixed_precision_error_is_reported(attr):
+    """Attributes staged in 16 bits, FP32 exponent/transmittance/accumulation:
+    the error against the FP64 oracle is measured per output (no parity bar),
+    and must stay far below the signal."""
+    scene, cams, targets, prm = scenes.config1()
+    L, views, grads, g9 = _oracle_full(scene, cams, targets, prm)
+    g = run_gpu(scene, cams, prm, target=targets, attr=attr, dL_dimage=views[0]["dL_dC"],
+                dL_dentropy=views[0]["dL_dH"])
+    f = views[0]["fwd"]
+    err_img = np.abs(g["image"] - f["image"].reshape(-1, 3)).mean()
+    err_h = np.abs(g["entropy"] - f["entropy"].reshape(-1)).mean()
+    assert err_img < 2e-2 and err_h < 5e-2
+    e = rel_norm_err(g["grads"]["means"], grads["means"])
+    assert e < 0.5
+
+
+def test_scale_reset_parity():
+    from paper_2603_09277_gb300 import gs
+    rng = np.random.default_rng(0)
+    ls = rng.normal(-4, 1, (1000, 3)).astype(np.float32)
+    t = torch.as_tensor(ls).cuda()
+    gs.gs_scale_reset(t, 0.2)
+    torch.cuda.synchronize()
+    ref = oracle.scale_reset(ls, 0.2)
+    got = t.cpu().numpy().astype(np.float64)
+    ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    assert (np.abs(got - ref) <= 1.0 * ulp).all()
+    with pytest.raises(Exception):
+        gs.gs_scale_reset(t, 1.5)
+
+
+# ---------------------------------------------------------------------------
+# Edge cases
+# ---------------------------------------------------------------------------
+
+def test_empty_scene_and_all_culled():
+    cams = [scenes.camera(40, 30, 40.0)]
+    prm = scenes.params()
+    scene = scenes.box_scene(5, seed=0, box=((-1, 1), (-1, 1), (-3, -2)))  # behind the camera
+    g = run_gpu(scene, cams, prm, target=scenes.noise_targets(cams, 1))
+    assert g["P"] == 0
+    assert (g["image"] == 0).all() and (g["final_T"] == 1).all() and (g["last"] == 0).all()
+    assert np.abs(g["entropy"]).max() == 0
+    for k, v in g["grads"].items():
+        assert (v == 0).all(), k
+
+
+def test_nan_parameters_are_culled():
+    cams = [scenes.camera(48, 48, 48.0)]
+    prm = scenes.params()
+    scene = scenes.box_scene(50, seed=1)
+    scene["means"][3] = np.nan
+    scene["log_scales"][7] = np.inf
+    g = run_gpu(scene, cams, prm, target=scenes.noise_targets(cams, 1))
+    assert g["tiles"][3] == 0 and g["tiles"][7] == 0
+    assert np.isfinite(g["image"]).all()
+
+
+def test_capacity_overflow_regrows():
+    scene, cams, targets, prm = scenes.config1(n=2000)
+    from paper_2603_09277_gb300.rasterize import Rasterizer, scene_to_device
+    r = Rasterizer(cams, prm, 2000, pair_capacity=16)
+    p = scene_to_device(scene)
+    r.preprocess(p)
+    P = r.bin_sort()
+    assert r.capacity >= P > 16
+    # graph form: no host sync; overflow is reported on the device and ranges are empty
+    r2 = Rasterizer(cams, prm, 2000, pair_capacity=16)
+    r2.preprocess(p)
+    r2.bin_sort(sync=False)
+    torch.cuda.synchronize()
+    assert int(r2.status_dev.item()) == -3
+    assert int(r2.num_pairs_dev.item()) == P
+    assert (r2.tile_ranges == 0).all()
+
+
+def test_single_gaussian_closed_form():
+    """One isotropic Gaussian on the optical axis, dilation 0: the GPU image
+    equals c min(0.99, sigma exp(-r^2/(2 s^2))) inside the rect."""
+    W = H = 64
+    cam = scenes.camera(W, H, 64.0)
+    prm = scenes.params(dilation=0.0)
+    sc = {"means": np.array([[0, 0, 3.0]], np.float32),
+          "log_scales": np.full((1, 3), math.log(0.09375), np.float32),
+          "quats": np.array([[1, 0, 0, 0]], np.float32),
+          "opacity_logits": np.array([1.5], np.float32),
+          "sh": np.zeros((1, 16, 3), np.float32), "sh_degree": 0}
+    sc["sh"][0, 0] = 0.5 * 2 * math.sqrt(math.pi)
+    g = run_gpu(sc, [cam], prm)
+    s0 = math.exp(float(sc["log_scales"][0, 0]))
+    sp = 64.0 * s0 / 3.0
+    sig = 1 / (1 + math.exp(-1.5))
+    col = float(sc["sh"][0, 0, 0]) / (2 * math.sqrt(math.pi)) + 0.5
+    img = g["image"].reshape(H, W, 3)[..., 0]
+    x0, y0, x1, y1 = g["rect"][0]
+    for v in range(H):
+        for u in range(W):
+            inside = x0 <= u // 16 < x1 and y0 <= v // 16 < y1
+            d2 = (u + 0.5 - 32) ** 2 + (v + 0.5 - 32) ** 2
+            a = min(np.float32(0.99), sig * math.exp(-d2 / (2 * sp * sp)))
+            w = a if (inside and a >= np.float32(1 / 255)) else 0.0
+            assert img[v, u] == pytest.approx(w * col, abs=2e-6)
+
+
+# ---------------------------------------------------------------------------
+# Full-size configuration (1M Gaussians, 1237x822, SH degree 3) on samples
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def cfg2_case():
+    scene, cams, targets, prm = scenes.config2()
+    cam = cams[0]
+    proj = oracle.preprocess(scene, cam, prm)
+    lists = oracle.build_lists(proj, cam)
+    return scene, cams, targets, prm, proj, lists
+
+
+def test_cfg2_projection_and_lists(cfg2_case):
+    scene, cams, targets, prm, proj, lists = cfg2_case
+    g = run_gpu(scene, cams, prm, keys=False)
+    views = [{"proj": proj, "lists": lists}]
+    N = scene["means"].shape[0]
+    check_projection(g, views, cams, N)
+    g["keys"] = None
+    check_lists(g, views, cams, N)
+
+
+def test_cfg2_sampled_pixels_and_gradients(cfg2_case):
+    scene, cams, targets, prm, proj, lists = cfg2_case
+    cam = cams[0]
+    W, H = cam["width"], cam["height"]
+    N = scene["means"].shape[0]
+    rng = np.random.default_rng(0)
+    # Gaussians to check: visible, not flagged, small rect
+    cand = np.nonzero((proj["tiles"] > 0) & (proj["tiles"] <= 4) & (proj["boundary"] == 0))[0]
+    pick = rng.choice(cand, 24, replace=False)
+    TX, TY = oracle.tile_grid(cam)
+    tmask = np.zeros((TY, TX), bool)
+    for i in pick:
+        x0, y0, x1, y1 = proj["rect"][i]
+        tmask[y0:y1, x0:x1] = True
+    pmask = tmask[np.arange(H)[:, None] // 16, np.arange(W)[None, :] // 16]
+    # plus random pixels for the forward check
+    extra = np.zeros(H * W, bool)
+    extra[rng.choice(H * W, 3000, replace=False)] = True
+    fmask = pmask | extra.reshape(H, W)
+    fwd = oracle.render_fwd(proj, lists, cam, prm, mask=fmask)
+    # oracle loss gradient on the masked pixels (fixed per-pixel weights of the full view)
+    M = W * H
+    dC = np.where(fwd["image"] - targets[0] > 0, 1.0, -1.0) / (3 * M)
+    dC[~fmask] = 0.0
+    dH = np.where(fmask, GAMMA / M, 0.0)
+    g9 = oracle.render_bwd(proj, lists, cam, prm, dC, dH, mask=pmask)
+    gm = np.zeros(N, np.uint8)
+    gm[pick] = 1
+    og = oracle.preprocess_bwd(scene, cam, prm, g9, gmask=gm)
+    g = run_gpu(scene, cams, prm, dL_dimage=dC.astype(np.float32), dL_dentropy=dH.astype(np.float32),
+                keys=False)
+    view = {"proj": proj, "lists": lists, "fwd": fwd}
+    bad = pixel_exclusion(view, cam) | ~fmask
+    ok = ~bad.reshape(-1)
+    assert ok.sum() > 2000
+    assert np.abs(g["image"][ok] - fwd["image"].reshape(-1, 3)[ok]).max() <= IMG_TOL
+    assert np.abs(g["final_T"][ok] - fwd["final_T"].reshape(-1)[ok]).max() <= IMG_TOL
+    assert np.abs(g["entropy"][ok] - fwd["entropy"].reshape(-1)[ok]).max() <= IMG_TOL
+    assert (g["last"][ok] == fwd["last"].reshape(-1)[ok]).all()
+    # gradients of the picked Gaussians: their whole footprint is inside pmask
+    badg = gaussian_exclusion(view, cam, pixel_exclusion(view, cam) & pmask)
+    use = pick[~badg[pick]]
+    assert len(use) >= 12
+    for k in ("means", "log_scales", "quats", "opacity_logits"):
+        e = rel_norm_err(g["grads"][k][use], og[k][use])
+        assert e <= GRAD_TOL, (k, e)
+    e = rel_norm_err(g["grads"]["sh"][use], og["sh"][use])
+    assert e <= GRAD_TOL
