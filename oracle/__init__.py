@@ -113,7 +113,9 @@ def tile_grid(cam):
 def preprocess(scene, cam, prm):
     """Per-Gaussian projection of one view.  Returns dict with P9 [N,9]
     (mean2d x,y; conic a,b,c; opacity; rgb), depth [N] f32, radius, rect
-    [N,4], tiles [N], clamped [N,3], boundary [N] (rect may differ in FP32)."""
+    [N,4], tiles [N], clamped [N,3], boundary [N] (rect may differ in FP32),
+    rect_lo / rect_hi [N,4] (intersection / union of the rects reachable
+    under the FP32 rounding bands; set for flagged Gaussians)."""
     lib = _load()
     means, ls, q, op, sh = (_f64(scene["means"]), _f64(scene["log_scales"]),
                             _f64(scene["quats"]), _f64(scene["opacity_logits"]),
@@ -129,12 +131,14 @@ def preprocess(scene, cam, prm):
         "tiles": np.zeros(N, np.int32),
         "clamped": np.zeros((N, 3), np.int32),
         "boundary": np.zeros(N, np.int32),
+        "rect_lo": np.zeros((N, 4), np.int32),
+        "rect_hi": np.zeros((N, 4), np.int32),
     }
     lib.ora_preprocess(ctypes.c_int(N), _p(means), _p(ls), _p(q), _p(op), _p(sh),
                        ctypes.c_int(Kst), ctypes.c_int(deg), _p(cam_vector(cam)),
                        _p(prm_vector(prm)), _p(out["P9"]), _p(out["depth"]), _p(out["radius"]),
                        _p(out["rect"]), _p(out["tiles"]), _p(out["clamped"]),
-                       _p(out["boundary"]))
+                       _p(out["boundary"]), _p(out["rect_lo"]), _p(out["rect_hi"]))
     return out
 
 

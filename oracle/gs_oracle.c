@@ -139,6 +139,8 @@ typedef struct {
     int tiles;       /* (x1-x0)*(y1-y0)                                        */
     int clamped[3];  /* SH colour channel clamped at 0                         */
     int boundary;    /* 1: the rect could differ under FP32 rounding           */
+    int rect_lo[4];  /* tiles in the rect under every admissible rounding      */
+    int rect_hi[4];  /* tiles in the rect under some admissible rounding       */
 } proj_int;
 
 /* Tile rect from the four pixel-space edges mx - r, mx + r, my - r, my + r:
@@ -248,19 +250,28 @@ static void project_one(const cx mu[3], const cx ls[3], const cx q[4], cx o,
     rect_of_edges(mxr - r, mxr + r, myr - r, myr + r, TX, TY, pi->rect);
     pi->radius = (int)r;
     pi->tiles = (pi->rect[2] - pi->rect[0]) * (pi->rect[3] - pi->rect[1]);
-    /* Boundary flag: does a rounding of the radius within EPS_R, or of any one
-     * edge within EPS_PX, change the rect? */
+    /* Boundary flag: does a rounding of the radius within EPS_R, or of the
+     * edges within EPS_PX, change the rect?  rect_lo / rect_hi bound every
+     * rect reachable that way (intersection / union). */
     {
         double rs[3] = {r, ceil(rf * (1.0 - EPS_R)), ceil(rf * (1.0 + EPS_R))};
-        for (int a = 0; a < 3 && !pi->boundary; ++a) {
+        memcpy(pi->rect_lo, pi->rect, sizeof pi->rect);
+        memcpy(pi->rect_hi, pi->rect, sizeof pi->rect);
+        for (int a = 0; a < 3; ++a) {
             double e[4] = {mxr - rs[a], mxr + rs[a], myr - rs[a], myr + rs[a]};
-            for (int k = 0; k < 4 && !pi->boundary; ++k)
-                for (int sg = -1; sg <= 1 && !pi->boundary; ++sg) {
+            for (int k = 0; k < 4; ++k)
+                for (int sg = -1; sg <= 1; ++sg) {
                     double f[4] = {e[0], e[1], e[2], e[3]};
                     f[k] += sg * EPS_PX;
                     int r1[4];
                     rect_of_edges(f[0], f[1], f[2], f[3], TX, TY, r1);
                     if (memcmp(r1, pi->rect, sizeof r1)) pi->boundary = 1;
+                    for (int c = 0; c < 2; ++c) {
+                        if (r1[c] > pi->rect_lo[c]) pi->rect_lo[c] = r1[c];
+                        if (r1[c] < pi->rect_hi[c]) pi->rect_hi[c] = r1[c];
+                        if (r1[c + 2] < pi->rect_lo[c + 2]) pi->rect_lo[c + 2] = r1[c + 2];
+                        if (r1[c + 2] > pi->rect_hi[c + 2]) pi->rect_hi[c + 2] = r1[c + 2];
+                    }
                 }
         }
     }
@@ -312,7 +323,7 @@ void ora_preprocess(int N, const double* means, const double* ls, const double* 
                     const double* opac, const double* sh, int Kst, int deg,
                     const double* camv, const double* prmv,
                     double* out9, float* depth, int* radius, int* rect, int* tiles,
-                    int* clamped, int* boundary) {
+                    int* clamped, int* boundary, int* rect_lo, int* rect_hi) {
     cam_t c = load_cam(camv);
     prm_t p = load_prm(prmv);
 #pragma omp parallel for schedule(static)
@@ -328,6 +339,12 @@ void ora_preprocess(int N, const double* means, const double* ls, const double* 
         tiles[i] = pi.culled ? 0 : pi.tiles;
         for (int k = 0; k < 3; ++k) clamped[3 * (size_t)i + k] = pi.clamped[k];
         boundary[i] = pi.boundary;
+        for (int k = 0; k < 4; ++k) {
+            /* a Gaussian culled for another reason never has a rect */
+            int keep = pi.boundary || !pi.culled;
+            rect_lo[4 * (size_t)i + k] = keep ? pi.rect_lo[k] : 0;
+            rect_hi[4 * (size_t)i + k] = keep ? pi.rect_hi[k] : 0;
+        }
     }
 }
 

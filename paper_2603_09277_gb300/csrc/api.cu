@@ -174,12 +174,21 @@ __global__ void __launch_bounds__(kLossThreads) loss_kernel(
   }
 }
 
-__global__ void loss_finalize_kernel(const double* __restrict__ partials, int n,
-                                     double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < n; ++i) t += partials[i];
-    *out = t;
+// Sums the block partials in a fixed order: thread t adds partials t, t+256,
+// ..., then a fixed shuffle tree and a fixed sum over the 8 warps.
+__global__ void __launch_bounds__(kLossThreads) loss_finalize_kernel(
+    const double* __restrict__ partials, int n, double* __restrict__ out) {
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += kLossThreads) t += partials[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  __shared__ double s[kLossThreads / 32];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int k = 0; k < kLossThreads / 32; ++k) r += s[k];
+    *out = r;
   }
 }
 
@@ -319,7 +328,7 @@ int gs_loss_l1_entropy(const float* image, const float* target, const float* ent
   double* partials = reinterpret_cast<double*>(workspace);
   loss_kernel<<<nb, kLossThreads, 0, st>>>(image, target, gamma != 0.f ? entropy : nullptr, ct, P,
                                            gamma, dL_dimage, dL_dentropy, partials);
-  loss_finalize_kernel<<<1, 32, 0, st>>>(partials, nb, loss_dev);
+  loss_finalize_kernel<<<1, kLossThreads, 0, st>>>(partials, nb, loss_dev);
   count_launches(2);
   return check_launch();
 }
@@ -348,6 +357,7 @@ int gs_render_bwd(const gs_proj* proj, int N, const gs_camera* cams, int V, cons
   int rc = launch_render_bwd(proj, ct, prm, sorted_vals, tile_ranges, final_T, last_idx,
                              dL_dimage, dL_dentropy, grad2d, opt, st);
   if (rc != GS_OK) return rc;
+  GS_TRY_CUDA(cudaMemsetAsync(g_sh, 0, sizeof(float) * 3 * (size_t)prm->sh_stride * N, st));
   return launch_preprocess_bwd(means, log_scales, quats, opacity_logits, sh, N, ct, prm,
                                proj->tiles_touched, grad2d, g_means, g_log_scales, g_quats,
                                g_opacity_logits, g_sh, st);

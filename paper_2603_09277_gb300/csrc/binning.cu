@@ -363,6 +363,10 @@ __global__ void set_count_kernel(long long* __restrict__ dst, const long long* _
   if (threadIdx.x == 0 && blockIdx.x == 0) *dst = *src;
 }
 
+__global__ void set_value_kernel(long long* __restrict__ dst, long long v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
+}
+
 // ----------------------------------------------------------------------------
 // Workspace layout.
 // ----------------------------------------------------------------------------
@@ -547,7 +551,8 @@ int launch_tile_queue(const unsigned* ranges, long long T, unsigned* order, void
   long long* n_dev = reinterpret_cast<long long*>(p);
   p += align256(sizeof(long long) * 2);
   unsigned* hist = reinterpret_cast<unsigned*>(p);
-  GS_TRY_CUDA(cudaMemcpyAsync(n_dev, &T, sizeof(long long), cudaMemcpyHostToDevice, st));
+  set_value_kernel<<<1, 32, 0, st>>>(n_dev, T);
+  count_launches(1);
   unsigned grid = (unsigned)std::min<long long>((T + 255) / 256, 1024);
   // 4 passes (even): the result ends in the first buffer, i.e. `order`
   queue_keys_kernel<<<grid, 256, 0, st>>>(ranges, T, k0, order);

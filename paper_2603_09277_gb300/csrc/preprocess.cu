@@ -319,8 +319,7 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(
     float* __restrict__ g_quats, float* __restrict__ g_opac, float* __restrict__ g_sh) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
-  const int K = sh_count(sh_deg);
-  for (int k = 0; k < sh_stride * 3; ++k) g_sh[(long long)g * sh_stride * 3 + k] = 0.f;
+  const int K = sh_count(sh_deg);  // g_sh arrives zeroed (memset by the caller)
 
   Activated a = activate(means, log_scales, quats, opacity_logits, g);
   float gm[3] = {0.f, 0.f, 0.f};

@@ -3,9 +3,9 @@ C ABI, run the oracle, and derive the threshold-boundary exclusions.
 
 Exclusion rules (from the oracle only, never from the GPU results):
 - a Gaussian whose rect could round differently in FP32 (oracle boundary
-  flag) is left out of the bit-exact rect/list checks, and every tile within
-  one tile of its rect is left out of the pixel checks (its list may hold
-  one entry more or less);
+  flag) is left out of the bit-exact rect/list checks, and the tiles that
+  lie in some but not every rect reachable under the rounding bands are
+  left out of the pixel checks (their lists may hold one entry more or less);
 - a pixel whose smallest relative distance of any threshold test
   (alpha_min, alpha_max, t_min) is below MARGIN may take the other branch in
   FP32 and is left out of the pixel checks;
@@ -88,15 +88,58 @@ def pixel_exclusion(ora_view, cam, margin=MARGIN):
     W, H = cam["width"], cam["height"]
     TX, TY = oracle.tile_grid(cam)
     bad_tiles = np.zeros((TY, TX), bool)
+    amin = float(np.float32(1.0 / 255))
     for i in np.nonzero(proj["boundary"])[0]:
-        x0, y0, x1, y1 = proj["rect"][i]
-        if proj["tiles"][i] == 0:
-            # a culled-by-rect Gaussian may appear with a one-tile rect in FP32
-            x0 = y0 = 0
-            x1, y1 = TX, TY
-        bad_tiles[max(0, y0 - 1):min(TY, y1 + 1), max(0, x0 - 1):min(TX, x1 + 1)] = True
+        # tiles that are in some reachable rect but not in every one ...
+        hx0, hy0, hx1, hy1 = proj["rect_hi"][i]
+        lx0, ly0, lx1, ly1 = proj["rect_lo"][i]
+        m = np.zeros((TY, TX), bool)
+        m[hy0:hy1, hx0:hx1] = True
+        if lx1 > lx0 and ly1 > ly0:
+            m[ly0:ly1, lx0:lx1] = False
+        # ... and where the Gaussian's alpha reaches alpha_min at some pixel
+        # (elsewhere it is skipped whether or not it is listed)
+        g = proj["P9"][i]
+        for ty, tx in zip(*np.nonzero(m)):
+            u = np.arange(tx * 16, min(W, tx * 16 + 16)) + 0.5 - g[0]
+            v = np.arange(ty * 16, min(H, ty * 16 + 16)) + 0.5 - g[1]
+            du, dv = np.meshgrid(u, v)
+            a = g[5] * np.exp(-0.5 * (g[2] * du * du + 2 * g[3] * du * dv + g[4] * dv * dv))
+            if a.max() >= amin * (1 - margin):
+                bad_tiles[ty, tx] = True
     px_tiles = bad_tiles[np.arange(H)[:, None] // 16, np.arange(W)[None, :] // 16]
     return px_tiles | (fwd["margin"] < margin)
+
+
+def last_ids_gpu(g, cams, v, N):
+    """Row id of each pixel's last blended entry (-1 if none), GPU side."""
+    a, b = view_pixels(cams)[v]
+    t0 = view_tiles(cams)[v][0]
+    cam = cams[v]
+    W, H = cam["width"], cam["height"]
+    TX = (W + 15) // 16
+    yy, xx = np.divmod(np.arange(W * H), W)
+    tile = t0 + (yy // 16) * TX + xx // 16
+    last = g["last"][a:b]
+    start = g["ranges"][tile, 0]
+    out = np.full(W * H, -1, np.int64)
+    has = last > 0
+    out[has] = g["vals"][start[has] + last[has] - 1] - v * N
+    return out
+
+
+def last_ids_oracle(view, cam):
+    """Gaussian id of each pixel's last blended entry (-1 if none), oracle side."""
+    ts, ids = view["lists"]
+    W, H = cam["width"], cam["height"]
+    TX = (W + 15) // 16
+    yy, xx = np.divmod(np.arange(W * H), W)
+    tile = (yy // 16) * TX + xx // 16
+    last = view["fwd"]["last"].reshape(-1)
+    out = np.full(W * H, -1, np.int64)
+    has = last > 0
+    out[has] = ids[ts[tile[has]] + last[has] - 1]
+    return out
 
 
 def gaussian_exclusion(ora_view, cam, bad_pixels):
