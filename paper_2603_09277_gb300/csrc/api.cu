@@ -141,26 +141,34 @@ bool proj_ok(const gs_proj* p, bool need_records) {
 constexpr int kLossThreads = 256;
 constexpr int kLossMaxBlocks = 1024;
 
+struct LossViews {
+  int V;
+  long long pix_off[GS_MAX_VIEWS];
+  float g_img[GS_MAX_VIEWS];  // 1 / (3 M_v V): |dL/dC| per channel
+  float g_ent[GS_MAX_VIEWS];  // gamma / (M_v V)
+  double w[GS_MAX_VIEWS];     // 1 / (M_v V)
+};
+
 __global__ void __launch_bounds__(kLossThreads) loss_kernel(
     const float* __restrict__ image, const float* __restrict__ target,
-    const float* __restrict__ entropy, const CamTable ct, long long P, float gamma,
+    const float* __restrict__ entropy, const LossViews lv, long long P, float gamma,
     float* __restrict__ dimg, float* __restrict__ dent, double* __restrict__ partials) {
   double acc = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
        i += (long long)gridDim.x * blockDim.x) {
-    int v = find_view_of_pixel(ct, i);
-    const double M = (double)ct.c[v].W * ct.c[v].H;
-    const double wv = 1.0 / (M * ct.V);
-    double l1 = 0.0;
+    int v = 0;
+    while (v + 1 < lv.V && i >= lv.pix_off[v + 1]) ++v;
+    float l1 = 0.f;
+#pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
-      float r = image[3 * i + ch] - target[3 * i + ch];
-      l1 += fabs((double)r);
-      float sg = r > 0.f ? 1.f : (r < 0.f ? -1.f : 0.f);
-      dimg[3 * i + ch] = (float)(sg * wv / 3.0);
+      const float r = image[3 * i + ch] - target[3 * i + ch];
+      l1 += fabsf(r);
+      dimg[3 * i + ch] = r > 0.f ? lv.g_img[v] : (r < 0.f ? -lv.g_img[v] : 0.f);
     }
-    double h = entropy ? (double)entropy[i] : 0.0;
-    if (dent) dent[i] = (float)(gamma * wv);
-    acc += wv * (l1 / 3.0 + (double)gamma * h);
+    const float h = entropy ? entropy[i] : 0.f;
+    if (dent) dent[i] = lv.g_ent[v];
+    // per pixel: (1/(M_v V)) (|r|_1 / 3 + gamma H), summed in double
+    acc += lv.w[v] * ((double)l1 * (1.0 / 3.0) + (double)gamma * (double)h);
   }
   __shared__ double s[kLossThreads / 32];
 #pragma unroll
@@ -326,7 +334,16 @@ int gs_loss_l1_entropy(const float* image, const float* target, const float* ent
   if (!workspace || workspace_bytes < sizeof(double) * (size_t)nb) return invalid("workspace");
   cudaStream_t st = (cudaStream_t)stream;
   double* partials = reinterpret_cast<double*>(workspace);
-  loss_kernel<<<nb, kLossThreads, 0, st>>>(image, target, gamma != 0.f ? entropy : nullptr, ct, P,
+  LossViews lv;
+  lv.V = V;
+  for (int v = 0; v < V; ++v) {
+    const double M = (double)ct.c[v].W * ct.c[v].H;
+    lv.pix_off[v] = ct.c[v].pix_off;
+    lv.w[v] = 1.0 / (M * V);
+    lv.g_img[v] = (float)(1.0 / (3.0 * M * V));
+    lv.g_ent[v] = (float)((double)gamma / (M * V));
+  }
+  loss_kernel<<<nb, kLossThreads, 0, st>>>(image, target, gamma != 0.f ? entropy : nullptr, lv, P,
                                            gamma, dL_dimage, dL_dentropy, partials);
   loss_finalize_kernel<<<1, kLossThreads, 0, st>>>(partials, nb, loss_dev);
   count_launches(2);

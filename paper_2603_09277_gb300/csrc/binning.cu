@@ -207,38 +207,36 @@ __global__ void __launch_bounds__(kRadixThreads) radix_upsweep_kernel(
   }
 }
 
-// Exclusive scan of hist[256 * nblocks] (digit-major) in one block.
+// Per-digit exclusive scan over the blocks: block d scans hist[d][0..G) in
+// place and writes the digit total to totals[d].  G <= 1024.
 __global__ void __launch_bounds__(kScanThreads) radix_scan_kernel(unsigned* __restrict__ hist,
-                                                                  int count) {
-  __shared__ unsigned long long s_carry;
-  if (threadIdx.x == 0) s_carry = 0;
-  __syncthreads();
-  // each thread takes a contiguous run per round for better locality
-  constexpr int kRun = 8;
-  for (int base = 0; base < count; base += kScanThreads * kRun) {
-    int first = base + threadIdx.x * kRun;
-    unsigned loc[kRun];
-    unsigned long long s = 0;
-    for (int k = 0; k < kRun; ++k) {
-      loc[k] = first + k < count ? hist[first + k] : 0u;
-      s += loc[k];
-    }
-    unsigned long long tot;
-    unsigned long long off = block_excl_scan(s, &tot) + s_carry;
-    for (int k = 0; k < kRun; ++k) {
-      if (first + k < count) hist[first + k] = (unsigned)off;
-      off += loc[k];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) s_carry += tot;
-    __syncthreads();
+                                                                  int G,
+                                                                  unsigned* __restrict__ totals) {
+  unsigned* h = hist + (long long)blockIdx.x * G;
+  constexpr int kPer = 4;  // 256 threads x 4 >= 1024 blocks
+  unsigned loc[kPer];
+  unsigned long long s = 0;
+  const int first = threadIdx.x * kPer;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    loc[k] = first + k < G ? h[first + k] : 0u;
+    s += loc[k];
   }
+  unsigned long long tot;
+  unsigned long long off = block_excl_scan(s, &tot);
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    if (first + k < G) h[first + k] = (unsigned)off;
+    off += loc[k];
+  }
+  if (threadIdx.x == 0) totals[blockIdx.x] = (unsigned)tot;
 }
 
 __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
     const unsigned* __restrict__ keys_in, const unsigned* __restrict__ vals_in,
     unsigned* __restrict__ keys_out, unsigned* __restrict__ vals_out,
-    const long long* __restrict__ n_dev, int shift, const unsigned* __restrict__ offsets) {
+    const long long* __restrict__ n_dev, int shift, const unsigned* __restrict__ offsets,
+    const unsigned* __restrict__ totals) {
   __shared__ unsigned s_wc[kRadixWarps][kRadixBins + 1];  // per-warp digit counters (+ dummy)
   __shared__ unsigned s_base[kRadixBins];                 // running global offset per digit
   __shared__ unsigned s_tot[kRadixBins];
@@ -248,8 +246,12 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
   long long chunk = radix_chunk(n, gridDim.x);
   long long b0 = (long long)blockIdx.x * chunk;
   long long b1 = min(n, b0 + chunk);
-  for (int d = threadIdx.x; d < kRadixBins; d += kRadixThreads)
-    s_base[d] = offsets[(long long)d * gridDim.x + blockIdx.x];
+  {
+    // digit base = exclusive scan of the digit totals (256 threads, one digit each)
+    unsigned long long tot;
+    unsigned long long db = block_excl_scan(totals[threadIdx.x], &tot);
+    s_base[threadIdx.x] = (unsigned)db + offsets[(long long)threadIdx.x * gridDim.x + blockIdx.x];
+  }
   for (int i = threadIdx.x; i < kRadixWarps * (kRadixBins + 1); i += kRadixThreads)
     (&s_wc[0][0])[i] = 0u;
   __syncthreads();
@@ -314,24 +316,42 @@ __global__ void capacity_check_kernel(const long long* __restrict__ P, long long
   }
 }
 
+// One warp per 32 consecutive depth-sorted rows; for each row in turn the 32
+// lanes write its tiles (row-major over the rect), so long rects do not
+// serialise one thread and the writes of a row are coalesced.
 __global__ void __launch_bounds__(256) duplicate_kernel(
     const unsigned* __restrict__ rows, const long long* __restrict__ n_vis,
     const unsigned long long* __restrict__ offsets, const int* __restrict__ rect, int N,
     const CamTable ct, const long long* __restrict__ p_eff, unsigned* __restrict__ tkeys,
     unsigned* __restrict__ tvals) {
-  long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= *n_vis || *p_eff == 0) return;
-  unsigned row = rows[j];
-  int v = (int)(row / (unsigned)N);
-  const CamInfo& c = ct.c[v];
-  int4 r = reinterpret_cast<const int4*>(rect)[row];
-  unsigned long long off = offsets[j];
-  for (int ty = r.y; ty < r.w; ++ty) {
-    unsigned tb = (unsigned)(c.tile_off + ty * c.TX);
-    for (int tx = r.x; tx < r.z; ++tx) {
-      tkeys[off] = tb + (unsigned)tx;
-      tvals[off] = row;
-      ++off;
+  const long long n = *n_vis;
+  if (*p_eff == 0) return;
+  const int lane = threadIdx.x & 31;
+  const long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll;
+  if (base >= n) return;
+  // each lane fetches one row's descriptor, then the warp walks them in order
+  const long long j = base + lane;
+  unsigned row = 0;
+  int4 r = make_int4(0, 0, 0, 0);
+  unsigned long long off = 0;
+  if (j < n) {
+    row = rows[j];
+    r = reinterpret_cast<const int4*>(rect)[row];
+    off = offsets[j];
+  }
+  const int cnt = (int)min(32ll, n - base);
+  for (int k = 0; k < cnt; ++k) {
+    const unsigned rw = __shfl_sync(0xffffffffu, row, k);
+    const int x0 = __shfl_sync(0xffffffffu, r.x, k), y0 = __shfl_sync(0xffffffffu, r.y, k);
+    const int x1 = __shfl_sync(0xffffffffu, r.z, k), y1 = __shfl_sync(0xffffffffu, r.w, k);
+    const unsigned long long o = __shfl_sync(0xffffffffu, off, k);
+    const int w = x1 - x0;
+    const int total = w * (y1 - y0);
+    const CamInfo& c = ct.c[(int)(rw / (unsigned)N)];
+    for (int t = lane; t < total; t += 32) {
+      const int ty = y0 + t / w, tx = x0 + t % w;
+      tkeys[o + t] = (unsigned)(c.tile_off + ty * c.TX + tx);
+      tvals[o + t] = rw;
     }
   }
 }
@@ -405,7 +425,7 @@ Workspace carve(void* base, long long n_rows, long long cap) {
   w.offsets = reinterpret_cast<unsigned long long*>(take(8 * (n_rows + 1)));
   for (int i = 0; i < 2; ++i) w.pk[i] = reinterpret_cast<unsigned*>(take(4 * (cap + 1)));
   w.pv = reinterpret_cast<unsigned*>(take(4 * (cap + 1)));
-  w.hist = reinterpret_cast<unsigned*>(take(4ull * kRadixBins * kRadixGrid));
+  w.hist = reinterpret_cast<unsigned*>(take(4ull * kRadixBins * (kRadixGrid + 1)));
   w.bytes = off;
   return w;
 }
@@ -420,9 +440,10 @@ int radix_sort(unsigned* k[2], unsigned* v[2], const long long* n_dev, long long
   if (grid < 1) grid = 1;
   for (int shift = 0; shift < bits; shift += 8) {
     radix_upsweep_kernel<<<grid, kRadixThreads, 0, st>>>(k[cur], n_dev, shift, hist);
-    radix_scan_kernel<<<1, kScanThreads, 0, st>>>(hist, kRadixBins * grid);
+    radix_scan_kernel<<<kRadixBins, kScanThreads, 0, st>>>(hist, grid, hist + kRadixBins * grid);
     radix_downsweep_kernel<<<grid, kRadixThreads, 0, st>>>(k[cur], v[cur], k[1 - cur], v[1 - cur],
-                                                           n_dev, shift, hist);
+                                                           n_dev, shift, hist,
+                                                           hist + kRadixBins * grid);
     count_launches(3);
     cur = 1 - cur;
   }
@@ -534,7 +555,7 @@ __global__ void queue_keys_kernel(const unsigned* __restrict__ ranges, long long
 
 size_t tile_queue_workspace_size(long long T) {
   return align256(4 * (T + 1)) * 3 + align256(sizeof(long long) * 2) +
-         align256(4ull * kRadixBins * kRadixGrid);
+         align256(4ull * kRadixBins * (kRadixGrid + 1));
 }
 
 int launch_tile_queue(const unsigned* ranges, long long T, unsigned* order, void* ws,

@@ -320,6 +320,19 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
   const int K = sh_count(sh_deg);  // g_sh arrives zeroed (memset by the caller)
+  bool any = false;
+  for (int v = 0; v < ct.V; ++v) any |= tiles_touched[(long long)v * N + g] != 0u;
+  if (!any) {
+    g_means[3ll * g] = 0.f;
+    g_means[3ll * g + 1] = 0.f;
+    g_means[3ll * g + 2] = 0.f;
+    g_ls[3ll * g] = 0.f;
+    g_ls[3ll * g + 1] = 0.f;
+    g_ls[3ll * g + 2] = 0.f;
+    reinterpret_cast<float4*>(g_quats)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    g_opac[g] = 0.f;
+    return;
+  }
 
   Activated a = activate(means, log_scales, quats, opacity_logits, g);
   float gm[3] = {0.f, 0.f, 0.f};
