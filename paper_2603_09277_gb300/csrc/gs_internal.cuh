@@ -45,30 +45,32 @@ struct RenderConsts {
 
 // ---------------------------------------------------------------------------
 // Render record: what the blending loop needs of one (view, Gaussian) row.
-// The exponent is kept in base 2 with the opacity folded in:
-//   e = A2 dx^2 + B2 dx dy + C2 dy^2 + L2S,   alpha = 2^e,
-//   A2 = -a/2 log2(e), B2 = -b log2(e), C2 = -c/2 log2(e), L2S = log2(sigma),
-// where (a, b, c) is the conic and dx, dy = pixel - mean2d.
+// The exponent is kept in base 2 with the opacity folded in and the inverse
+// covariance in square-root form:
+//   p = f11 dx,  q = f21 dx + f22 dy,   e = L2S - p^2 - q^2,   alpha = 2^e,
+// with F = [[f11, 0], [f21, f22]] = sqrt(log2(e)/2) L^-1, L the Cholesky
+// factor of the 2D covariance (so F^T F = log2(e)/2 conic), L2S = log2(sigma)
+// and (dx, dy) = pixel - mean2d.  The 2D mean is stored as an integer part
+// (hx, hy) and a fraction (lx, ly); blending kernels rebase it on the tile.
 // ---------------------------------------------------------------------------
 struct __align__(16) RecF32 {  // 48 bytes
-  float4 r0;  // mx, my, A2, B2
-  float4 r1;  // C2, L2S, R, G
-  float4 r2;  // B, sigma, 0, 0
+  float4 r0;  // hx, hy, lx, ly
+  float4 r1;  // f11, f21, f22, L2S
+  float4 r2;  // R, G, B, sigma
 };
 struct __align__(16) RecH16 {  // 32 bytes: mean in FP32, the rest in 16-bit
-  float2 m;           // mx, my
-  uint32_t ab;        // A2, B2
-  uint32_t cl;        // C2, L2S
+  float4 m;           // hx, hy, lx, ly
+  uint32_t f1;        // f11, f21
+  uint32_t f2;        // f22, L2S
   uint32_t rg;        // R, G
   uint32_t bs;        // B, sigma
-  uint32_t pad0, pad1;
 };
 
-// The unpacked record staged in shared memory (FP32 in every variant).
+// The unpacked record.
 struct Splat {
-  float mx, my, A2, B2;
-  float C2, L2S, R, G;
-  float B, sigma;
+  float hx, hy, lx, ly;
+  float f11, f21, f22, L2S;
+  float R, G, B, sigma;
 };
 
 template <int DT>
@@ -100,21 +102,18 @@ template <int DT>
 __device__ __forceinline__ void store_record(void* recs, long long row, const Splat& s) {
   if constexpr (DT == GS_ATTR_F32) {
     RecF32* r = reinterpret_cast<RecF32*>(recs) + row;
-    r->r0 = make_float4(s.mx, s.my, s.A2, s.B2);
-    r->r1 = make_float4(s.C2, s.L2S, s.R, s.G);
-    r->r2 = make_float4(s.B, s.sigma, 0.f, 0.f);
+    r->r0 = make_float4(s.hx, s.hy, s.lx, s.ly);
+    r->r1 = make_float4(s.f11, s.f21, s.f22, s.L2S);
+    r->r2 = make_float4(s.R, s.G, s.B, s.sigma);
   } else {
-    RecH16 h;
-    h.m = make_float2(s.mx, s.my);
-    h.ab = Half2Of<DT>::pack(s.A2, s.B2);
-    h.cl = Half2Of<DT>::pack(s.C2, s.L2S);
-    h.rg = Half2Of<DT>::pack(s.R, s.G);
-    h.bs = Half2Of<DT>::pack(s.B, s.sigma);
-    h.pad0 = h.pad1 = 0u;
-    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<RecH16*>(recs) + row);
-    const uint4* src = reinterpret_cast<const uint4*>(&h);
-    dst[0] = src[0];
-    dst[1] = src[1];
+    RecH16* r = reinterpret_cast<RecH16*>(recs) + row;
+    r->m = make_float4(s.hx, s.hy, s.lx, s.ly);
+    uint4 q;
+    q.x = Half2Of<DT>::pack(s.f11, s.f21);
+    q.y = Half2Of<DT>::pack(s.f22, s.L2S);
+    q.z = Half2Of<DT>::pack(s.R, s.G);
+    q.w = Half2Of<DT>::pack(s.B, s.sigma);
+    *reinterpret_cast<uint4*>(&r->f1) = q;
   }
 }
 
@@ -124,29 +123,37 @@ __device__ __forceinline__ Splat load_record(const void* recs, unsigned row) {
   if constexpr (DT == GS_ATTR_F32) {
     const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const RecF32*>(recs) + row);
     float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
-    s.mx = a.x; s.my = a.y; s.A2 = a.z; s.B2 = a.w;
-    s.C2 = b.x; s.L2S = b.y; s.R = b.z; s.G = b.w;
-    s.B = c.x; s.sigma = c.y;
+    s.hx = a.x; s.hy = a.y; s.lx = a.z; s.ly = a.w;
+    s.f11 = b.x; s.f21 = b.y; s.f22 = b.z; s.L2S = b.w;
+    s.R = c.x; s.G = c.y; s.B = c.z; s.sigma = c.w;
   } else {
     const uint4* p = reinterpret_cast<const uint4*>(reinterpret_cast<const RecH16*>(recs) + row);
     uint4 a = __ldg(p), b = __ldg(p + 1);
-    s.mx = __uint_as_float(a.x); s.my = __uint_as_float(a.y);
-    float2 ab = Half2Of<DT>::unpack(a.z), cl = Half2Of<DT>::unpack(a.w);
-    float2 rg = Half2Of<DT>::unpack(b.x), bs = Half2Of<DT>::unpack(b.y);
-    s.A2 = ab.x; s.B2 = ab.y; s.C2 = cl.x; s.L2S = cl.y;
+    s.hx = __uint_as_float(a.x); s.hy = __uint_as_float(a.y);
+    s.lx = __uint_as_float(a.z); s.ly = __uint_as_float(a.w);
+    float2 f1 = Half2Of<DT>::unpack(b.x), f2 = Half2Of<DT>::unpack(b.y);
+    float2 rg = Half2Of<DT>::unpack(b.z), bs = Half2Of<DT>::unpack(b.w);
+    s.f11 = f1.x; s.f21 = f1.y; s.f22 = f2.x; s.L2S = f2.y;
     s.R = rg.x; s.G = rg.y; s.B = bs.x; s.sigma = bs.y;
   }
   return s;
 }
 
-// Base-2 exponent of alpha at pixel offset (dx, dy).  The forward and the
-// backward kernels both call this, with explicit roundings, so that they take
-// identical skip/stop decisions.
-__device__ __forceinline__ float splat_exponent(float A2, float B2, float C2, float L2S, float dx,
-                                                float dy) {
-  float t = __fmaf_rn(B2, dy, __fmul_rn(A2, dx));   // A2 dx + B2 dy
-  float e = __fmaf_rn(__fmul_rn(C2, dy), dy, L2S);   // C2 dy^2 + L2S
-  return __fmaf_rn(dx, t, e);
+// Mean relative to a tile origin (ox, oy): the integer parts subtract
+// exactly, so the result is accurate to the rounding of a small number.
+__device__ __forceinline__ float2 tile_relative_mean(const Splat& s, float ox, float oy) {
+  return make_float2(__fadd_rn(__fsub_rn(s.hx, ox), s.lx), __fadd_rn(__fsub_rn(s.hy, oy), s.ly));
+}
+
+// Base-2 exponent of alpha at the tile-relative pixel offset (dx, dy), and
+// the factor components p, q.  The forward and the backward kernels both call
+// this, with explicit roundings, so that they take identical skip/stop
+// decisions.
+__device__ __forceinline__ float splat_exponent(float f11, float f21, float f22, float L2S,
+                                                float dx, float dy, float& p, float& q) {
+  p = __fmul_rn(f11, dx);
+  q = __fmaf_rn(f21, dx, __fmul_rn(f22, dy));
+  return __fmaf_rn(-q, q, __fmaf_rn(-p, p, L2S));
 }
 
 __device__ __forceinline__ float fast_exp2(float x) {

@@ -165,6 +165,68 @@ __device__ __forceinline__ float depth_of(const CamInfo& c, const float* m) {
   return __double2float_rn(z);
 }
 
+// ---------------------------------------------------------------------------
+// Error-free FP32 transformations (FP32x2 "double-float" arithmetic): the
+// camera-space mean and the 2D mean are carried as unevaluated sums hi + lo,
+// so that cancellation in R mean + t (scene coordinates far larger than the
+// camera-space offset) does not cost pixel-level precision.
+// ---------------------------------------------------------------------------
+struct F2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ F2 two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// r0 m0 + r1 m1 + r2 m2 + t, accurate to about FP32 epsilon squared.
+__device__ __forceinline__ F2 dot3_plus(float r0, float r1, float r2, const float* m, float t) {
+  F2 p0 = two_prod(r0, m[0]), p1 = two_prod(r1, m[1]), p2 = two_prod(r2, m[2]);
+  F2 s1 = two_sum(p0.hi, p1.hi);
+  F2 s2 = two_sum(s1.hi, p2.hi);
+  F2 s3 = two_sum(s2.hi, t);
+  float err = __fadd_rn(__fadd_rn(__fadd_rn(p0.lo, p1.lo), __fadd_rn(p2.lo, s1.lo)),
+                        __fadd_rn(s2.lo, s3.lo));
+  return fast_two_sum(s3.hi, err);
+}
+
+// (x.hi + x.lo) / (y.hi + y.lo) as a double-float.
+__device__ __forceinline__ F2 div2(F2 x, F2 y) {
+  float q = __fdiv_rn(x.hi, y.hi);
+  // x - q y, exactly for the hi parts
+  float r = __fmaf_rn(-q, y.hi, x.hi);
+  r = __fadd_rn(r, __fsub_rn(x.lo, __fmul_rn(q, y.lo)));
+  return fast_two_sum(q, __fdiv_rn(r, y.hi));
+}
+
+// f (u.hi + u.lo) + c as a double-float.
+__device__ __forceinline__ F2 affine2(float f, F2 u, float c) {
+  F2 p = two_prod(f, u.hi);
+  F2 s = two_sum(p.hi, c);
+  return fast_two_sum(s.hi, __fadd_rn(__fadd_rn(p.lo, __fmul_rn(f, u.lo)), s.lo));
+}
+
+// a d - b c with one rounding (Kahan's FMA form).
+__device__ __forceinline__ float det2(float a, float b, float c, float d) {
+  float w = __fmul_rn(b, c);
+  float e = __fmaf_rn(-b, c, w);
+  float f = __fmaf_rn(a, d, -w);
+  return __fadd_rn(f, e);
+}
+
 struct Projected {
   bool ok;
   float tx, ty, tz, ux, uy;
@@ -172,21 +234,30 @@ struct Projected {
   float J00, J02, J11, J12;
   float T[6];          // J W (2x3)
   float A, B, C;       // Sigma' + dilation I
-  float det;
+  float det;           // det(Sigma' + dilation I)
   float ca, cb, cc;    // conic
-  float mx, my;        // 2D mean
+  float f11, f21, f22; // sqrt(log2(e)/2) L^-1 with L L^T = Sigma' + dilation I
+  F2 mx, my;           // 2D mean (double-float)
 };
 
+// EWA projection (Sec. 3).  Sigma' = N N^T with N = J W M (M = R S): the
+// Cholesky factor of Sigma' + dilation I and its determinant are formed from
+// N directly (rows n0, n1): det = |n0 x n1|^2 + d (|n0|^2 + |n1|^2) + d^2,
+// which avoids squaring the condition number of Sigma'.
 __device__ __forceinline__ Projected project(const CamInfo& c, const Activated& a, float depth,
                                              float dilation) {
   Projected p;
   const float* m = a.mean;
-  p.tx = c.R[0] * m[0] + c.R[1] * m[1] + c.R[2] * m[2] + c.t[0];
-  p.ty = c.R[3] * m[0] + c.R[4] * m[1] + c.R[5] * m[2] + c.t[1];
+  F2 tx = dot3_plus(c.R[0], c.R[1], c.R[2], m, c.t[0]);
+  F2 ty = dot3_plus(c.R[3], c.R[4], c.R[5], m, c.t[1]);
+  F2 tz = {depth, 0.f};
+  p.tx = tx.hi;
+  p.ty = ty.hi;
   p.tz = depth;
+  F2 ux = div2(tx, tz), uy = div2(ty, tz);
+  p.ux = ux.hi;
+  p.uy = uy.hi;
   float itz = 1.f / p.tz;
-  p.ux = p.tx * itz;
-  p.uy = p.ty * itz;
   p.clx = p.ux < -c.limx || p.ux > c.limx;
   p.cly = p.uy < -c.limy || p.uy > c.limy;
   float uxc = fminf(fmaxf(p.ux, -c.limx), c.limx);
@@ -199,25 +270,39 @@ __device__ __forceinline__ Projected project(const CamInfo& c, const Activated& 
     p.T[j] = p.J00 * c.R[j] + p.J02 * c.R[6 + j];
     p.T[3 + j] = p.J11 * c.R[3 + j] + p.J12 * c.R[6 + j];
   }
-  const float* S = a.Sig;  // xx xy xz yy yz zz
-  float TS[6];
-  for (int i = 0; i < 2; ++i) {
-    const float* t = p.T + 3 * i;
-    TS[3 * i + 0] = t[0] * S[0] + t[1] * S[1] + t[2] * S[2];
-    TS[3 * i + 1] = t[0] * S[1] + t[1] * S[3] + t[2] * S[4];
-    TS[3 * i + 2] = t[0] * S[2] + t[1] * S[4] + t[2] * S[5];
+  // N = T M, M = Rq diag(s)
+  float n0[3], n1[3];
+  for (int j = 0; j < 3; ++j) {
+    float mj0 = a.Rq[j] * a.s[j], mj1 = a.Rq[3 + j] * a.s[j], mj2 = a.Rq[6 + j] * a.s[j];
+    n0[j] = p.T[0] * mj0 + p.T[1] * mj1 + p.T[2] * mj2;
+    n1[j] = p.T[3] * mj0 + p.T[4] * mj1 + p.T[5] * mj2;
   }
-  p.A = TS[0] * p.T[0] + TS[1] * p.T[1] + TS[2] * p.T[2] + dilation;
-  p.B = TS[0] * p.T[3] + TS[1] * p.T[4] + TS[2] * p.T[5];
-  p.C = TS[3] * p.T[3] + TS[4] * p.T[4] + TS[5] * p.T[5] + dilation;
-  p.det = p.A * p.C - p.B * p.B;
-  p.ok = p.det > 0.f;
-  float idet = 1.f / p.det;
-  p.ca = p.C * idet;
-  p.cb = -p.B * idet;
-  p.cc = p.A * idet;
-  p.mx = c.fx * p.ux + c.cx;
-  p.my = c.fy * p.uy + c.cy;
+  float s00 = n0[0] * n0[0] + n0[1] * n0[1] + n0[2] * n0[2];
+  float s11 = n1[0] * n1[0] + n1[1] * n1[1] + n1[2] * n1[2];
+  float s01 = n0[0] * n1[0] + n0[1] * n1[1] + n0[2] * n1[2];
+  float cx0 = det2(n0[1], n0[2], n1[1], n1[2]);
+  float cx1 = det2(n0[2], n0[0], n1[2], n1[0]);
+  float cx2 = det2(n0[0], n0[1], n1[0], n1[1]);
+  p.A = s00 + dilation;
+  p.B = s01;
+  p.C = s11 + dilation;
+  p.det = (cx0 * cx0 + cx1 * cx1 + cx2 * cx2) + dilation * (s00 + s11) + dilation * dilation;
+  p.ok = p.det > 0.f && p.A > 0.f;
+  // L = [[l11, 0], [l21, l22]], L L^T = [[A, B], [B, C]]
+  const float l11 = sqrtf(p.A);
+  const float l21 = p.B / l11;
+  const float l22 = sqrtf(p.det) / l11;
+  const float kc = 0.8493218002880191f;  // sqrt(log2(e) / 2)
+  p.f11 = kc / l11;
+  p.f22 = kc / l22;
+  p.f21 = -kc * l21 / (l11 * l22);
+  // conic = L^-T L^-1
+  const float i11 = 1.f / l11, i22 = 1.f / l22, i21 = -l21 / (l11 * l22);
+  p.ca = i11 * i11 + i21 * i21;
+  p.cb = i21 * i22;
+  p.cc = i22 * i22;
+  p.mx = affine2(c.fx, ux, c.cx);
+  p.my = affine2(c.fy, uy, c.cy);
   return p;
 }
 
@@ -242,8 +327,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(
     float r = 0.f;
     if (vis) {
       p = project(c, a, depth, dilation);
-      vis = p.ok && isfinite(p.mx) && isfinite(p.my) && isfinite(p.ca) && isfinite(p.cb) &&
-            isfinite(p.cc);
+      vis = p.ok && isfinite(p.mx.hi) && isfinite(p.my.hi) && isfinite(p.f11) &&
+            isfinite(p.f21) && isfinite(p.f22) && isfinite(p.ca) && isfinite(p.cc);
     }
     if (vis) {
       // larger eigenvalue of [[A, B], [B, C]] in the cancellation-free form
@@ -251,8 +336,9 @@ __global__ void __launch_bounds__(256) preprocess_kernel(
       float lam = 0.5f * (p.A + p.C) + sqrtf(hd * hd + p.B * p.B);
       r = ceilf(3.f * sqrtf(lam));
       const float inv16 = 1.f / kTile;
-      float fx0 = floorf((p.mx - r) * inv16), fx1 = floorf((p.mx + r) * inv16) + 1.f;
-      float fy0 = floorf((p.my - r) * inv16), fy1 = floorf((p.my + r) * inv16) + 1.f;
+      const float mx = p.mx.hi, my = p.my.hi;
+      float fx0 = floorf((mx - r) * inv16), fx1 = floorf((mx + r) * inv16) + 1.f;
+      float fy0 = floorf((my - r) * inv16), fy1 = floorf((my + r) * inv16) + 1.f;
       x0 = (int)fminf(fmaxf(fx0, 0.f), (float)c.TX);
       x1 = (int)fminf(fmaxf(fx1, 0.f), (float)c.TX);
       y0 = (int)fminf(fmaxf(fy0, 0.f), (float)c.TY);
@@ -282,11 +368,14 @@ __global__ void __launch_bounds__(256) preprocess_kernel(
     cbl = fmaxf(cbl, 0.f);
 
     Splat s;
-    s.mx = p.mx;
-    s.my = p.my;
-    s.A2 = -0.5f * kLog2e * p.ca;
-    s.B2 = -kLog2e * p.cb;
-    s.C2 = -0.5f * kLog2e * p.cc;
+    // 2D mean as integer + fraction (the fraction carries the low part)
+    s.hx = rintf(p.mx.hi);
+    s.hy = rintf(p.my.hi);
+    s.lx = __fadd_rn(__fsub_rn(p.mx.hi, s.hx), p.mx.lo);
+    s.ly = __fadd_rn(__fsub_rn(p.my.hi, s.hy), p.my.lo);
+    s.f11 = p.f11;
+    s.f21 = p.f21;
+    s.f22 = p.f22;
     s.L2S = log2f(a.sigma);
     s.R = cr;
     s.G = cg;
@@ -296,7 +385,9 @@ __global__ void __launch_bounds__(256) preprocess_kernel(
     reinterpret_cast<int4*>(out.rect)[row] = make_int4(x0, y0, x1, y1);
     out.tiles_touched[row] = (unsigned)((x1 - x0) * (y1 - y0));
     if (out.radius) out.radius[row] = (int)r;
-    if (out.mean2d) reinterpret_cast<float2*>(out.mean2d)[row] = make_float2(p.mx, p.my);
+    if (out.mean2d)
+      reinterpret_cast<float2*>(out.mean2d)[row] =
+          make_float2(__fadd_rn(p.mx.hi, p.mx.lo), __fadd_rn(p.my.hi, p.my.lo));
     if (out.conic_opacity)
       reinterpret_cast<float4*>(out.conic_opacity)[row] = make_float4(p.ca, p.cb, p.cc, a.sigma);
     if (out.rgb) {

@@ -8,7 +8,8 @@
 // as soon as every pixel is done (__syncthreads_count over the batch).
 //
 // Forward, per pixel (Sec. 3 and Sec. 4.3):
-//   e = log2(sigma g) (base-2 exponent with the opacity folded in)
+//   e = log2(sigma g) = L2S - |F (x - mean)|^2 (base 2, opacity folded in,
+//   F the square-root factor of the conic; the mean is rebased on the tile)
 //   skip if e < log2(alpha_min); alpha = min(alpha_max, 2^e)
 //   stop before blending if T (1 - alpha) < t_min
 //   w = alpha T; C += w c; sum_wl += w log2 w; T *= 1 - alpha
@@ -37,7 +38,9 @@ constexpr int kBatch = kThreads;
 struct TileCoord {
   int view, px, py;
   bool inside;
-  long long pix;  // global pixel index (valid when inside)
+  long long pix;   // global pixel index (valid when inside)
+  float ox, oy;    // tile origin in pixels
+  float rx, ry;    // pixel centre relative to the tile origin
 };
 
 __device__ __forceinline__ TileCoord tile_coord(const CamTable& ct, int tile) {
@@ -50,6 +53,10 @@ __device__ __forceinline__ TileCoord tile_coord(const CamTable& ct, int tile) {
   t.py = ty * kTile + (threadIdx.x >> 4);
   t.inside = t.px < c.W && t.py < c.H;
   t.pix = c.pix_off + (long long)t.py * c.W + t.px;
+  t.ox = (float)(tx * kTile);
+  t.oy = (float)(ty * kTile);
+  t.rx = (float)(threadIdx.x & (kTile - 1)) + 0.5f;
+  t.ry = (float)(threadIdx.x >> 4) + 0.5f;
   return t;
 }
 
@@ -75,7 +82,7 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
   __shared__ float s2[kBatch];
   const int tid = threadIdx.x;
   TileCoord tc = tile_coord(ct, tile);
-  const float pxf = (float)tc.px + 0.5f, pyf = (float)tc.py + 0.5f;
+  const float pxf = tc.rx, pyf = tc.ry;
   const uint2 r = a.ranges[tile];
   float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, swl = 0.f;
   unsigned last = 0;
@@ -86,8 +93,9 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
     unsigned idx = base + tid;
     if (idx < r.y) {
       Splat s = load_record<DT>(a.recs, a.vals[idx]);
-      s0[tid] = make_float4(s.mx, s.my, s.A2, s.B2);
-      s1[tid] = make_float4(s.C2, s.L2S, s.R, s.G);
+      const float2 m = tile_relative_mean(s, tc.ox, tc.oy);
+      s0[tid] = make_float4(m.x, m.y, s.f11, s.f21);
+      s1[tid] = make_float4(s.f22, s.L2S, s.R, s.G);
       s2[tid] = s.B;
     }
     __syncthreads();
@@ -97,7 +105,8 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
         const float4 g0 = s0[k];
         const float4 g1 = s1[k];
         const float dx = pxf - g0.x, dy = pyf - g0.y;
-        const float e = splat_exponent(g0.z, g0.w, g1.x, g1.y, dx, dy);
+        float pp, qq;
+        const float e = splat_exponent(g0.z, g0.w, g1.x, g1.y, dx, dy, pp, qq);
         ++ne;
         if (e < rc.log2_alpha_min) continue;
         const float alpha = fminf(rc.alpha_max, fast_exp2(e));
@@ -200,7 +209,7 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   TileCoord tc = tile_coord(ct, tile);
-  const float pxf = (float)tc.px + 0.5f, pyf = (float)tc.py + 0.5f;
+  const float pxf = tc.rx, pyf = tc.ry;
   const uint2 r = a.ranges[tile];
   float T = 1.f, gr = 0.f, gg = 0.f, gb = 0.f, gH = 0.f;
   unsigned last = 0;
@@ -228,8 +237,9 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
     if (tid < cnt) {
       const unsigned row = a.vals[r.x + start + tid];
       Splat s = load_record<DT>(a.recs, row);
-      s0[tid] = make_float4(s.mx, s.my, s.A2, s.B2);
-      s1[tid] = make_float4(s.C2, s.L2S, s.R, s.G);
+      const float2 m = tile_relative_mean(s, tc.ox, tc.oy);
+      s0[tid] = make_float4(m.x, m.y, s.f11, s.f21);
+      s1[tid] = make_float4(s.f22, s.L2S, s.R, s.G);
       s2[tid] = make_float2(s.B, s.sigma);
       s_row[tid] = row;
     }
@@ -243,7 +253,8 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
       const float4 g1 = s1[k];
       if (pos < last) {
         const float dx = pxf - g0.x, dy = pyf - g0.y;
-        const float e = splat_exponent(g0.z, g0.w, g1.x, g1.y, dx, dy);
+        float pp, qq;
+        const float e = splat_exponent(g0.z, g0.w, g1.x, g1.y, dx, dy, pp, qq);
         if (e >= rc.log2_alpha_min) {
           contrib = true;
           const float2 g2 = s2[k];
@@ -268,12 +279,13 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
           if (araw <= rc.alpha_max) {
             const float dd = dA * araw;
             d_s = dd / g2.y;  // dA * g with g = araw / sigma
-            const float ca = -2.f * kLn2 * g0.z, cbc = -kLn2 * g0.w, cc = -2.f * kLn2 * g1.x;
             d_a = -0.5f * dd * dx * dx;
             d_b = -dd * dx * dy;
             d_c = -0.5f * dd * dy * dy;
-            d_mx = dd * (ca * dx + cbc * dy);
-            d_my = dd * (cbc * dx + cc * dy);
+            // d d / d mean = conic (dx, dy) = F^T (p, q) / (log2(e) / 2)
+            const float k2 = 2.f * kLn2 * dd;
+            d_mx = k2 * (g0.z * pp + g0.w * qq);
+            d_my = k2 * (g1.x * qq);
           }
         }
       }
