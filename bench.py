@@ -59,7 +59,7 @@ def log(*a):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5"])
@@ -68,8 +68,10 @@ def parse():
                     help="CTAs of the persistent list-length-ordered launch (0 = one CTA per tile)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-band-rows", type=int, default=2,
-                    help="tile rows of the view the CPU oracle sample renders")
+    ap.add_argument("--cpu-band-rows", type=int, default=0,
+                    help="tile rows of view 0 the CPU oracle sample renders (0 = the whole view)")
+    ap.add_argument("--ref-band-rows", type=int, default=8,
+                    help="tile rows per step of the reference (oracle) arm")
     return ap.parse_args()
 
 
@@ -153,6 +155,8 @@ def oracle_sample(scene, cams, targets, prm, gamma, band_rows):
     cam = cams[0]
     W, H = cam["width"], cam["height"]
     TY = (H + 15) // 16
+    if band_rows <= 0 or band_rows > TY:
+        band_rows = TY
     t_start = max(0, TY // 2 - band_rows // 2)
     rows = np.arange(H) // 16
     band = (rows >= t_start) & (rows < t_start + band_rows)
@@ -187,11 +191,11 @@ def run_reference(args):
     (scene, cams, targets, prm), wl = workload(args.config, 0)
     from paper_2603_09277_gb300 import scenes
     for _ in range(args.warmup):
-        oracle_sample(scene, cams, targets, prm, scenes.GAMMA, 1)
+        oracle_sample(scene, cams, targets, prm, scenes.GAMMA, args.ref_band_rows)
     nbs, dts = [], []
     desc = ""
     for _ in range(args.steps):
-        nb, dt, desc = oracle_sample(scene, cams, targets, prm, scenes.GAMMA, 1)
+        nb, dt, desc = oracle_sample(scene, cams, targets, prm, scenes.GAMMA, args.ref_band_rows)
         nbs.append(nb)
         dts.append(dt)
     value = sum(nbs) / sum(dts)
@@ -200,7 +204,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * np.mean(dts),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": wl, "sample": "1 tile row band per step"},
+            "config": {"workload": wl,
+                       "sample": "%d tile rows of view 0 per step" % args.ref_band_rows},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -272,8 +277,6 @@ def main():
             e[3].record()
         r.render_bwd(p, events=(e[7], e[4]) if e[7] is not None else None)
         gs.gs_scale_reset(ls_work, 0.2)
-        if e[4] is not None:
-            pass
 
     # warm-up with host-synchronised pair counting (sizes the pair buffers)
     for _ in range(max(args.warmup, 3)):

@@ -161,7 +161,9 @@ def build_lists(proj, cam):
 def render_fwd(proj, lists, cam, prm, mask=None):
     """Compositing of one view.  Returns image [H,W,3], final_T, last (1-based
     list position of the last blended entry, 0 if none), entropy, nblend,
-    neval and margin (smallest relative distance of any threshold test)."""
+    neval, margin (smallest relative distance of any threshold test) and
+    first_near (first list position whose test is within 1e-3 of a
+    threshold, -1 if none)."""
     lib = _load()
     W, H = cam["width"], cam["height"]
     ts, ids = lists
@@ -174,12 +176,13 @@ def render_fwd(proj, lists, cam, prm, mask=None):
         "nblend": np.zeros((H, W), np.int32),
         "neval": np.zeros((H, W), np.int32),
         "margin": np.full((H, W), np.inf, np.float64),
+        "first_near": np.full((H, W), -1, np.int32),
     }
     m = None if mask is None else np.ascontiguousarray(mask, np.uint8)
     lib.ora_render_fwd(ctypes.c_int(W), ctypes.c_int(H), _p(ts), _p(ids), _p(proj["P9"]),
                        _p(prm_vector(prm)), _p(m), _p(o["image"]), _p(o["final_T"]),
                        _p(o["last"]), _p(o["entropy"]), _p(o["nblend"]), _p(o["neval"]),
-                       _p(o["margin"]))
+                       _p(o["margin"]), _p(o["first_near"]))
     return o
 
 

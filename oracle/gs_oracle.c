@@ -413,15 +413,21 @@ typedef struct {
 static double rel(double a, double b) { return fabs(a - b) / fabs(b); }
 
 /* Walks one pixel; fills bl (if not NULL) with the blended entries. */
+/* Threshold band of the first_near output: list positions from the first
+ * entry whose threshold test lies within this relative distance may be
+ * decided differently by an FP32 implementation. */
+#define NEAR_BAND 1e-3
+
 static int walk_pixel(double px, double py, const int* ids, long long s, long long e,
                       const double* P9, const prm_t* p, blend_t* bl,
                       double C[3], double* Tout, double* Hout, int* last, int* neval,
-                      double* margin) {
+                      double* margin, int* first_near) {
     double T = 1.0, swl = 0.0;
     int nb = 0;
     C[0] = C[1] = C[2] = 0.0;
     *last = 0;
     *neval = 0;
+    *first_near = -1;
     double mg = INFINITY;
     for (long long j = s; j < e; ++j) {
         const double* g = P9 + 9 * (size_t)ids[j];
@@ -430,11 +436,14 @@ static int walk_pixel(double px, double py, const int* ids, long long s, long lo
         double gd = exp(d);
         double araw = g[5] * gd;
         ++*neval;
-        mg = fmin(mg, fmin(rel(araw, p->amin), rel(araw, p->amax)));
+        double me = fmin(rel(araw, p->amin), rel(araw, p->amax));
+        mg = fmin(mg, me);
+        if (me < NEAR_BAND && *first_near < 0) *first_near = (int)(j - s);
         double ah = fmin(p->amax, araw);
         if (ah < p->amin) continue;
         double testT = T * (1.0 - ah);
         mg = fmin(mg, rel(testT, p->tmin));
+        if (rel(testT, p->tmin) < NEAR_BAND && *first_near < 0) *first_near = (int)(j - s);
         if (testT < p->tmin) break;
         double w = ah * T;
         for (int ch = 0; ch < 3; ++ch) C[ch] += w * g[6 + ch];
@@ -459,7 +468,7 @@ static int walk_pixel(double px, double py, const int* ids, long long s, long lo
 void ora_render_fwd(int W, int H, const long long* tile_start, const int* ids,
                     const double* P9, const double* prmv, const unsigned char* mask,
                     double* image, double* finalT, int* last, double* entropy,
-                    int* nblend, int* neval, double* margin) {
+                    int* nblend, int* neval, double* margin, int* first_near) {
     prm_t p = load_prm(prmv);
     int TX = (W + TILE - 1) / TILE;
 #pragma omp parallel for schedule(dynamic, 64)
@@ -468,9 +477,9 @@ void ora_render_fwd(int W, int H, const long long* tile_start, const int* ids,
         int u = pix % W, v = pix / W;
         int tile = (v / TILE) * TX + (u / TILE);
         double C[3], T, Hv, mg;
-        int lst, ne;
+        int lst, ne, fn;
         int nb = walk_pixel(u + 0.5, v + 0.5, ids, tile_start[tile], tile_start[tile + 1], P9, &p,
-                            NULL, C, &T, &Hv, &lst, &ne, &mg);
+                            NULL, C, &T, &Hv, &lst, &ne, &mg, &fn);
         for (int ch = 0; ch < 3; ++ch) image[3 * (size_t)pix + ch] = C[ch];
         finalT[pix] = T;
         last[pix] = lst;
@@ -478,6 +487,7 @@ void ora_render_fwd(int W, int H, const long long* tile_start, const int* ids,
         nblend[pix] = nb;
         neval[pix] = ne;
         margin[pix] = mg;
+        first_near[pix] = fn;
     }
 }
 
@@ -578,9 +588,9 @@ void ora_render_bwd(int W, int H, const long long* tile_start, const int* ids,
             int u = pix % W, v = pix / W;
             int tile = (v / TILE) * TX + (u / TILE);
             double C[3], Tf, Hv, mg;
-            int lst, ne;
+            int lst, ne, fn;
             int n = walk_pixel(u + 0.5, v + 0.5, ids, tile_start[tile], tile_start[tile + 1], P9,
-                               &p, bl, C, &Tf, &Hv, &lst, &ne, &mg);
+                               &p, bl, C, &Tf, &Hv, &lst, &ne, &mg, &fn);
             const double* gC = dL_dC + 3 * (size_t)pix;
             double gH = dL_dH ? dL_dH[pix] : 0.0;
             for (int b = 0; b < n; ++b) w[b] = bl[b].ah * bl[b].T;

@@ -143,19 +143,27 @@ def last_ids_oracle(view, cam):
 
 
 def gaussian_exclusion(ora_view, cam, bad_pixels):
-    """Boolean [N]: Gaussians in any list of a tile holding an excluded pixel,
-    or with the boundary flag."""
-    proj = ora_view["proj"]
+    """Boolean [N]: Gaussians whose gradient an FP32 threshold decision may
+    change by more than the tolerance: the boundary-flagged ones; at a pixel
+    with a near-threshold test, the entry at the first near-threshold list
+    position and the next two (a flipped skip or clamp changes that entry's
+    own contribution entirely; later entries only through T, by a factor
+    within alpha_min of 1, and a flipped stop adds entries of weight below
+    t_min); at a pixel of a tile whose list may gain or lose a flagged
+    Gaussian of visible alpha, the whole list."""
+    proj, fwd = ora_view["proj"], ora_view["fwd"]
     ts, ids = ora_view["lists"]
     TX, TY = oracle.tile_grid(cam)
-    N = proj["tiles"].size
     bad = proj["boundary"].astype(bool).copy()
-    H, W = bad_pixels.shape
-    tiles_bad = np.zeros(TX * TY, bool)
+    margin_bad = fwd["margin"] < MARGIN
     ys, xs = np.nonzero(bad_pixels)
-    tiles_bad[(ys // 16) * TX + xs // 16] = True
-    for t in np.nonzero(tiles_bad)[0]:
-        bad[ids[ts[t]:ts[t + 1]]] = True
+    for y, x in zip(ys, xs):
+        t = (y // 16) * TX + x // 16
+        fn = int(fwd["first_near"][y, x])
+        if margin_bad[y, x] and fn >= 0:
+            bad[ids[ts[t] + fn:min(ts[t + 1], ts[t] + fn + 3)]] = True
+        else:
+            bad[ids[ts[t]:ts[t + 1]]] = True
     return bad
 
 
