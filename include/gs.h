@@ -106,6 +106,7 @@ typedef struct {
     void* ev_begin;                /* optional cudaEvent_t recorded on the stream right before the
                                       blending kernel (for live per-kernel timing) */
     void* ev_end;                  /* optional cudaEvent_t recorded right after it */
+    int pixels_per_thread;         /* 1, 2 or 4 pixels of a column per thread (0 = 2) */
 } gs_launch;
 
 /* ---------------------------------------------------------------------- */

@@ -145,15 +145,26 @@ __device__ __forceinline__ float2 tile_relative_mean(const Splat& s, float ox, f
   return make_float2(__fadd_rn(__fsub_rn(s.hx, ox), s.lx), __fadd_rn(__fsub_rn(s.hy, oy), s.ly));
 }
 
-// Base-2 exponent of alpha at the tile-relative pixel offset (dx, dy), and
-// the factor components p, q.  The forward and the backward kernels both call
-// this, with explicit roundings, so that they take identical skip/stop
-// decisions.
-__device__ __forceinline__ float splat_exponent(float f11, float f21, float f22, float L2S,
-                                                float dx, float dy, float& p, float& q) {
-  p = __fmul_rn(f11, dx);
-  q = __fmaf_rn(f21, dx, __fmul_rn(f22, dy));
-  return __fmaf_rn(-q, q, __fmaf_rn(-p, p, L2S));
+// Base-2 exponent of alpha at the tile-relative pixel offset (dx, dy):
+//   p = f11 dx, q = f22 dy + f21 dx, e = (L2S - p^2) - q^2.
+// The column part (p, f21 dx, L2S - p^2) is shared by the pixels of one
+// column.  The forward and the backward kernels both evaluate it with these
+// explicit roundings, so that they take identical skip/stop decisions.
+struct SplatColumn {
+  float p, qx, base;
+};
+
+__device__ __forceinline__ SplatColumn splat_column(float f11, float f21, float L2S, float dx) {
+  SplatColumn c;
+  c.p = __fmul_rn(f11, dx);
+  c.qx = __fmul_rn(f21, dx);
+  c.base = __fmaf_rn(-c.p, c.p, L2S);
+  return c;
+}
+
+__device__ __forceinline__ float splat_row(const SplatColumn& c, float f22, float dy, float& q) {
+  q = __fmaf_rn(f22, dy, c.qx);
+  return __fmaf_rn(-q, q, c.base);
 }
 
 __device__ __forceinline__ float fast_exp2(float x) {

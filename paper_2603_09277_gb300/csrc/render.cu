@@ -1,11 +1,13 @@
 // render.cu -- per-tile front-to-back blending with the weight entropy
 // (forward) and its reverse-order adjoint with Algorithm 1 fused in.
 //
-// One CTA of 256 threads owns one 16x16 tile, one thread per pixel.  The
-// tile's list is streamed through shared memory in batches of 256 records
-// (one gathered 16-byte-vector record per thread), and every thread walks the
+// One CTA owns one 16x16 tile.  A thread owns PPT (1, 2 or 4) vertically
+// adjacent pixels of one column, so a warp covers a 16 x (2 PPT) block and the
+// column-dependent part of every exponent is shared by the thread's pixels.
+// The tile's list is streamed through shared memory in batches of 256
+// records (gathered with 16-byte vector loads) and every thread walks the
 // batch from shared memory (warp-broadcast reads).  The forward stops a CTA
-// as soon as every pixel is done (__syncthreads_count over the batch).
+// as soon as every pixel is done (__syncthreads_count per batch).
 //
 // Forward, per pixel (Sec. 3 and Sec. 4.3):
 //   e = log2(sigma g) = L2S - |F (x - mean)|^2 (base 2, opacity folded in,
@@ -21,8 +23,10 @@
 //   S += w_i c_i; R += (ln w_i + 1) w_i    (R starts at (ln T_N+1 + 1) T_N+1)
 //   then dsigma = dalpha g, dd = dalpha alpha (unless clamped),
 //   dconic = dd (-dx^2/2, -dx dy, -dy^2/2), dmean = dd conic (dx, dy).
-// The 9 per-Gaussian values are summed over the warp with shuffles and added
-// to grad2d with vector atomics by one lane.
+// The thread sums the 9 per-Gaussian values over its pixels, the warp sums
+// them with a split-transpose shuffle reduction (12 shuffles leave one of
+// the 9 totals in each of 9 lane pairs) and 9 lanes add them to grad2d with
+// one atomic instruction.
 //
 // Launch forms: one CTA per tile (optionally in a given tile order), or a
 // persistent grid whose CTAs claim tiles from a queue with one atomicAdd per
@@ -32,32 +36,42 @@
 namespace gs {
 namespace {
 
-constexpr int kThreads = kTilePix;  // 256
-constexpr int kBatch = kThreads;
+constexpr int kBatch = kTilePix;  // 256 records per staging batch
+constexpr unsigned kFull = 0xffffffffu;
 
-struct TileCoord {
-  int view, px, py;
-  bool inside;
-  long long pix;   // global pixel index (valid when inside)
-  float ox, oy;    // tile origin in pixels
-  float rx, ry;    // pixel centre relative to the tile origin
+template <int PPT>
+struct TileGeom {
+  static constexpr int kThreads = kTilePix / PPT;
+  int view;
+  long long pix0;   // global index of the thread's first pixel
+  int W;            // view width (pixel stride of a row)
+  float ox, oy;     // tile origin
+  float rx;         // pixel-centre x relative to the tile origin
+  float ry0;        // first pixel-centre y relative to the tile origin
+  unsigned inside;  // bit k: pixel k lies in the image
 };
 
-__device__ __forceinline__ TileCoord tile_coord(const CamTable& ct, int tile) {
-  TileCoord t;
-  t.view = find_view_of_tile(ct, tile);
-  const CamInfo& c = ct.c[t.view];
-  int local = tile - c.tile_off;
-  int tx = local % c.TX, ty = local / c.TX;
-  t.px = tx * kTile + (threadIdx.x & (kTile - 1));
-  t.py = ty * kTile + (threadIdx.x >> 4);
-  t.inside = t.px < c.W && t.py < c.H;
-  t.pix = c.pix_off + (long long)t.py * c.W + t.px;
-  t.ox = (float)(tx * kTile);
-  t.oy = (float)(ty * kTile);
-  t.rx = (float)(threadIdx.x & (kTile - 1)) + 0.5f;
-  t.ry = (float)(threadIdx.x >> 4) + 0.5f;
-  return t;
+template <int PPT>
+__device__ __forceinline__ TileGeom<PPT> tile_geom(const CamTable& ct, int tile) {
+  TileGeom<PPT> g;
+  g.view = find_view_of_tile(ct, tile);
+  const CamInfo& c = ct.c[g.view];
+  const int local = tile - c.tile_off;
+  const int tx = local % c.TX, ty = local / c.TX;
+  const int lx = threadIdx.x & (kTile - 1);
+  const int ly0 = (threadIdx.x >> 4) * PPT;
+  const int px = tx * kTile + lx, py0 = ty * kTile + ly0;
+  g.W = c.W;
+  g.pix0 = c.pix_off + (long long)py0 * c.W + px;
+  g.ox = (float)(tx * kTile);
+  g.oy = (float)(ty * kTile);
+  g.rx = (float)lx + 0.5f;
+  g.ry0 = (float)ly0 + 0.5f;
+  g.inside = 0u;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k)
+    if (px < c.W && py0 + k < c.H) g.inside |= 1u << k;
+  return g;
 }
 
 struct FwdArgs {
@@ -73,80 +87,93 @@ struct FwdArgs {
   unsigned long long* stats;
 };
 
-template <int DT>
+template <int DT, int PPT, bool STATS>
 __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts& rc,
                                          const FwdArgs& a, int tile, unsigned long long& n_bl,
                                          unsigned long long& n_ev) {
+  constexpr int NT = TileGeom<PPT>::kThreads;
   __shared__ float4 s0[kBatch];
   __shared__ float4 s1[kBatch];
   __shared__ float s2[kBatch];
   const int tid = threadIdx.x;
-  TileCoord tc = tile_coord(ct, tile);
-  const float pxf = tc.rx, pyf = tc.ry;
+  const TileGeom<PPT> tg = tile_geom<PPT>(ct, tile);
   const uint2 r = a.ranges[tile];
-  float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, swl = 0.f;
-  unsigned last = 0;
-  bool done = !tc.inside;
+  float T[PPT], cr[PPT], cg[PPT], cb[PPT], swl[PPT];
+  unsigned last[PPT];
+  unsigned live = tg.inside;  // bit k: pixel k still walking
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    T[k] = 1.f;
+    cr[k] = cg[k] = cb[k] = swl[k] = 0.f;
+    last[k] = 0u;
+  }
   unsigned nb = 0, ne = 0;
   for (unsigned base = r.x; base < r.y; base += kBatch) {
-    if (__syncthreads_count(done) == kThreads) break;
-    unsigned idx = base + tid;
-    if (idx < r.y) {
-      Splat s = load_record<DT>(a.recs, a.vals[idx]);
-      const float2 m = tile_relative_mean(s, tc.ox, tc.oy);
-      s0[tid] = make_float4(m.x, m.y, s.f11, s.f21);
-      s1[tid] = make_float4(s.f22, s.L2S, s.R, s.G);
-      s2[tid] = s.B;
+    if (__syncthreads_count(live == 0u) == NT) break;
+    for (int j = tid; j < kBatch; j += NT) {
+      const unsigned idx = base + j;
+      if (idx < r.y) {
+        const Splat s = load_record<DT>(a.recs, a.vals[idx]);
+        const float2 m = tile_relative_mean(s, tg.ox, tg.oy);
+        s0[j] = make_float4(m.x, m.y, s.f11, s.f21);
+        s1[j] = make_float4(s.f22, s.L2S, s.R, s.G);
+        s2[j] = s.B;
+      }
     }
     __syncthreads();
-    const int cnt = min((unsigned)kBatch, r.y - base);
-    if (!done) {
-      for (int k = 0; k < cnt; ++k) {
-        const float4 g0 = s0[k];
-        const float4 g1 = s1[k];
-        const float dx = pxf - g0.x, dy = pyf - g0.y;
-        float pp, qq;
-        const float e = splat_exponent(g0.z, g0.w, g1.x, g1.y, dx, dy, pp, qq);
-        ++ne;
+    const int cnt = (int)min((unsigned)kBatch, r.y - base);
+    for (int k = 0; k < cnt && live; ++k) {
+      const float4 g0 = s0[k];
+      const float4 g1 = s1[k];
+      const SplatColumn col = splat_column(g0.z, g0.w, g1.y, tg.rx - g0.x);
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) {
+        if (!(live & (1u << q))) continue;
+        float qq;
+        const float e = splat_row(col, g1.x, tg.ry0 + (float)q - g0.y, qq);
+        if (STATS) ++ne;
         if (e < rc.log2_alpha_min) continue;
         const float alpha = fminf(rc.alpha_max, fast_exp2(e));
-        const float test_T = T * (1.f - alpha);
+        const float test_T = T[q] * (1.f - alpha);
         if (test_T < rc.t_min) {
-          done = true;
-          break;
+          live &= ~(1u << q);
+          continue;
         }
-        const float w = alpha * T;
-        cr = __fmaf_rn(w, g1.z, cr);
-        cg = __fmaf_rn(w, g1.w, cg);
-        cb = __fmaf_rn(w, s2[k], cb);
-        swl = __fmaf_rn(w, fast_log2(w), swl);
-        T = test_T;
-        last = base - r.x + k + 1;
-        ++nb;
+        const float w = alpha * T[q];
+        cr[q] = __fmaf_rn(w, g1.z, cr[q]);
+        cg[q] = __fmaf_rn(w, g1.w, cg[q]);
+        cb[q] = __fmaf_rn(w, s2[k], cb[q]);
+        swl[q] = __fmaf_rn(w, fast_log2(w), swl[q]);
+        T[q] = test_T;
+        last[q] = base - r.x + k + 1;
+        if (STATS) ++nb;
       }
     }
   }
-  if (tc.inside) {
-    const long long p = tc.pix;
-    a.image[3 * p] = cr;
-    a.image[3 * p + 1] = cg;
-    a.image[3 * p + 2] = cb;
-    a.final_T[p] = T;
-    a.last_idx[p] = last;
-    if (a.entropy) a.entropy[p] = -kLn2 * (swl + T * fast_log2(T));
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    if (!(tg.inside & (1u << q))) continue;
+    const long long p = tg.pix0 + (long long)q * tg.W;
+    a.image[3 * p] = cr[q];
+    a.image[3 * p + 1] = cg[q];
+    a.image[3 * p + 2] = cb[q];
+    a.final_T[p] = T[q];
+    a.last_idx[p] = last[q];
+    if (a.entropy) a.entropy[p] = -kLn2 * (swl[q] + T[q] * fast_log2(T[q]));
   }
-  n_bl += nb;
-  n_ev += ne;
+  if (STATS) {
+    n_bl += nb;
+    n_ev += ne;
+  }
   __syncthreads();  // shared staging is reused by the next tile
 }
 
 __device__ __forceinline__ void flush_stats(unsigned long long* stats, unsigned long long nb,
                                             unsigned long long ne) {
-  if (!stats) return;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    nb += __shfl_xor_sync(0xffffffffu, nb, o);
-    ne += __shfl_xor_sync(0xffffffffu, ne, o);
+    nb += __shfl_xor_sync(kFull, nb, o);
+    ne += __shfl_xor_sync(kFull, ne, o);
   }
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(stats, nb);
@@ -154,10 +181,11 @@ __device__ __forceinline__ void flush_stats(unsigned long long* stats, unsigned 
   }
 }
 
-template <int DT>
-__global__ void __launch_bounds__(kThreads) render_fwd_kernel(const CamTable ct,
-                                                              const RenderConsts rc,
-                                                              const FwdArgs a, int persistent) {
+template <int DT, int PPT, bool STATS>
+__global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(const CamTable ct,
+                                                                    const RenderConsts rc,
+                                                                    const FwdArgs a,
+                                                                    int persistent) {
   unsigned long long nb = 0, ne = 0;
   if (persistent) {
     __shared__ unsigned s_t;
@@ -167,13 +195,13 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const CamTable ct,
       const unsigned t = s_t;
       __syncthreads();
       if (t >= (unsigned)ct.total_tiles) break;
-      fwd_tile<DT>(ct, rc, a, a.order ? (int)a.order[t] : (int)t, nb, ne);
+      fwd_tile<DT, PPT, STATS>(ct, rc, a, a.order ? (int)a.order[t] : (int)t, nb, ne);
     }
   } else {
     const int t = blockIdx.x;
-    fwd_tile<DT>(ct, rc, a, a.order ? (int)a.order[t] : t, nb, ne);
+    fwd_tile<DT, PPT, STATS>(ct, rc, a, a.order ? (int)a.order[t] : t, nb, ne);
   }
-  flush_stats(a.stats, nb, ne);
+  if (STATS) flush_stats(a.stats, nb, ne);
 }
 
 // ---------------------------------------------------------------------------
@@ -192,13 +220,48 @@ struct BwdArgs {
   unsigned* counter;
 };
 
-__device__ __forceinline__ float warp_sum(float x) {
+// Split-transpose warp sum of v[0..8]: at each butterfly level a lane keeps
+// one part of its values and sends the other, so 5 + 3 + 2 + 1 + 1 shuffles
+// leave the warp total of value slot(lane) in the lane; returns the slot
+// (0..8) or -1 for lanes left without a distinct total.  Lane pairs (l, l^1)
+// hold the same total.
+__device__ __forceinline__ float warp_sum9(const float v[9], int lane, int& slot) {
+  const bool b = lane & 16, c = lane & 8, d = lane & 4, e = lane & 2;
+  float u[5];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
+  for (int i = 0; i < 5; ++i) {
+    const float hi = i < 4 ? v[5 + i] : 0.f;
+    const float keep = b ? hi : v[i];
+    const float send = b ? v[i] : hi;
+    u[i] = keep + __shfl_xor_sync(kFull, send, 16);
+  }
+  float w[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float hi = i < 2 ? u[3 + i] : 0.f;
+    const float keep = c ? hi : u[i];
+    const float send = c ? u[i] : hi;
+    w[i] = keep + __shfl_xor_sync(kFull, send, 8);
+  }
+  float x[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float hi = i < 1 ? w[2] : 0.f;
+    const float keep = d ? hi : w[i];
+    const float send = d ? w[i] : hi;
+    x[i] = keep + __shfl_xor_sync(kFull, send, 4);
+  }
+  float y = (e ? x[1] : x[0]) + __shfl_xor_sync(kFull, e ? x[0] : x[1], 2);
+  y += __shfl_xor_sync(kFull, y, 1);
+  // slot held by the lane group (b, c, d, e) = index 8b + 4c + 2d + e, as
+  // 4-bit fields (0xF: no distinct total)
+  constexpr unsigned long long kSlots = 0xFFF8F765FF43F210ull;
+  const unsigned sel = (unsigned)((kSlots >> (4 * ((lane >> 1) & 15))) & 0xF);
+  slot = (sel == 0xF || (lane & 1)) ? -1 : (int)sel;
+  return y;
 }
 
-template <int DT>
+template <int DT, int PPT>
 __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts& rc,
                                          const BwdArgs& a, int tile) {
   __shared__ float4 s0[kBatch];
@@ -206,105 +269,107 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
   __shared__ float2 s2[kBatch];
   __shared__ unsigned s_row[kBatch];
   __shared__ unsigned s_max;
+  constexpr int NT = TileGeom<PPT>::kThreads;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  TileCoord tc = tile_coord(ct, tile);
-  const float pxf = tc.rx, pyf = tc.ry;
+  const TileGeom<PPT> tg = tile_geom<PPT>(ct, tile);
   const uint2 r = a.ranges[tile];
-  float T = 1.f, gr = 0.f, gg = 0.f, gb = 0.f, gH = 0.f;
-  unsigned last = 0;
-  if (tc.inside) {
-    const long long p = tc.pix;
-    T = a.final_T[p];
-    last = a.last_idx[p];
-    gr = a.dL_dimage[3 * p];
-    gg = a.dL_dimage[3 * p + 1];
-    gb = a.dL_dimage[3 * p + 2];
-    if (a.dL_dentropy) gH = a.dL_dentropy[p];
+  float T[PPT], gr[PPT], gg[PPT], gb[PPT], gH[PPT], Sr[PPT], Sg[PPT], Sb[PPT], Rent[PPT];
+  unsigned last[PPT];
+  unsigned mylast = 0;
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    T[q] = 1.f;
+    gr[q] = gg[q] = gb[q] = gH[q] = 0.f;
+    last[q] = 0u;
+    if (tg.inside & (1u << q)) {
+      const long long p = tg.pix0 + (long long)q * tg.W;
+      T[q] = a.final_T[p];
+      last[q] = a.last_idx[p];
+      gr[q] = a.dL_dimage[3 * p];
+      gg[q] = a.dL_dimage[3 * p + 1];
+      gb[q] = a.dL_dimage[3 * p + 2];
+      if (a.dL_dentropy) gH[q] = a.dL_dentropy[p];
+    }
+    Sr[q] = Sg[q] = Sb[q] = 0.f;
+    Rent[q] = (fast_log2(T[q]) * kLn2 + 1.f) * T[q];
+    mylast = max(mylast, last[q]);
   }
   if (tid == 0) s_max = 0u;
   __syncthreads();
-  if (last) atomicMax(&s_max, last);
+  if (mylast) atomicMax(&s_max, mylast);
   __syncthreads();
   const unsigned maxlast = s_max;
-  // colour accumulator S = sum_{k > i} w_k c_k and entropy accumulator R
-  float Sr = 0.f, Sg = 0.f, Sb = 0.f;
-  float Rent = (fast_log2(T) * kLn2 + 1.f) * T;
   for (unsigned end = maxlast; end > 0;) {
     const unsigned start = end > (unsigned)kBatch ? end - kBatch : 0u;
     const int cnt = (int)(end - start);
     __syncthreads();
-    if (tid < cnt) {
-      const unsigned row = a.vals[r.x + start + tid];
-      Splat s = load_record<DT>(a.recs, row);
-      const float2 m = tile_relative_mean(s, tc.ox, tc.oy);
-      s0[tid] = make_float4(m.x, m.y, s.f11, s.f21);
-      s1[tid] = make_float4(s.f22, s.L2S, s.R, s.G);
-      s2[tid] = make_float2(s.B, s.sigma);
-      s_row[tid] = row;
+    for (int j = tid; j < cnt; j += NT) {
+      const unsigned row = a.vals[r.x + start + j];
+      const Splat s = load_record<DT>(a.recs, row);
+      const float2 m = tile_relative_mean(s, tg.ox, tg.oy);
+      s0[j] = make_float4(m.x, m.y, s.f11, s.f21);
+      s1[j] = make_float4(s.f22, s.L2S, s.R, s.G);
+      s2[j] = make_float2(s.B, s.sigma);
+      s_row[j] = row;
     }
     __syncthreads();
     for (int k = cnt - 1; k >= 0; --k) {
       const unsigned pos = start + (unsigned)k;  // 0-based list position
-      float d_mx = 0.f, d_my = 0.f, d_a = 0.f, d_b = 0.f, d_c = 0.f, d_s = 0.f;
-      float d_r = 0.f, d_g = 0.f, d_bl = 0.f;
+      const bool any_here = pos < mylast;
+      if (!__any_sync(kFull, any_here)) continue;
+      float gsum[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) gsum[i] = 0.f;
       bool contrib = false;
-      const float4 g0 = s0[k];
-      const float4 g1 = s1[k];
-      if (pos < last) {
-        const float dx = pxf - g0.x, dy = pyf - g0.y;
-        float pp, qq;
-        const float e = splat_exponent(g0.z, g0.w, g1.x, g1.y, dx, dy, pp, qq);
-        if (e >= rc.log2_alpha_min) {
+      if (any_here) {
+        const float4 g0 = s0[k];
+        const float4 g1 = s1[k];
+        const float2 g2 = s2[k];
+        const float dx = tg.rx - g0.x;
+        const SplatColumn col = splat_column(g0.z, g0.w, g1.y, dx);
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+          if (pos >= last[q]) continue;
+          const float dy = tg.ry0 + (float)q - g0.y;
+          float qq;
+          const float e = splat_row(col, g1.x, dy, qq);
+          if (e < rc.log2_alpha_min) continue;
           contrib = true;
-          const float2 g2 = s2[k];
           const float araw = fast_exp2(e);
           const float alpha = fminf(rc.alpha_max, araw);
-          const float om = 1.f - alpha;
-          const float iom = 1.f / om;
-          const float Ti = T * iom;
+          const float iom = 1.f / (1.f - alpha);
+          const float Ti = T[q] * iom;
           const float w = alpha * Ti;
           const float lnw = fast_log2(w) * kLn2;
-          float dA = gr * (Ti * g1.z - Sr * iom) + gg * (Ti * g1.w - Sg * iom) +
-                     gb * (Ti * g2.x - Sb * iom);
-          dA += gH * ((-lnw - 1.f) * Ti + Rent * iom);
-          d_r = w * gr;
-          d_g = w * gg;
-          d_bl = w * gb;
-          Sr = __fmaf_rn(w, g1.z, Sr);
-          Sg = __fmaf_rn(w, g1.w, Sg);
-          Sb = __fmaf_rn(w, g2.x, Sb);
-          Rent = __fmaf_rn(lnw + 1.f, w, Rent);
-          T = Ti;
+          float dA = gr[q] * (Ti * g1.z - Sr[q] * iom) + gg[q] * (Ti * g1.w - Sg[q] * iom) +
+                     gb[q] * (Ti * g2.x - Sb[q] * iom);
+          dA += gH[q] * ((-lnw - 1.f) * Ti + Rent[q] * iom);
+          gsum[6] += w * gr[q];
+          gsum[7] += w * gg[q];
+          gsum[8] += w * gb[q];
+          Sr[q] = __fmaf_rn(w, g1.z, Sr[q]);
+          Sg[q] = __fmaf_rn(w, g1.w, Sg[q]);
+          Sb[q] = __fmaf_rn(w, g2.x, Sb[q]);
+          Rent[q] = __fmaf_rn(lnw + 1.f, w, Rent[q]);
+          T[q] = Ti;
           if (araw <= rc.alpha_max) {
             const float dd = dA * araw;
-            d_s = dd / g2.y;  // dA * g with g = araw / sigma
-            d_a = -0.5f * dd * dx * dx;
-            d_b = -dd * dx * dy;
-            d_c = -0.5f * dd * dy * dy;
+            gsum[5] += dd / g2.y;  // dA * g with g = araw / sigma
+            gsum[2] += -0.5f * dd * dx * dx;
+            gsum[3] += -dd * dx * dy;
+            gsum[4] += -0.5f * dd * dy * dy;
             // d d / d mean = conic (dx, dy) = F^T (p, q) / (log2(e) / 2)
             const float k2 = 2.f * kLn2 * dd;
-            d_mx = k2 * (g0.z * pp + g0.w * qq);
-            d_my = k2 * (g1.x * qq);
+            gsum[0] += k2 * (g0.z * col.p + g0.w * qq);
+            gsum[1] += k2 * (g1.x * qq);
           }
         }
       }
-      if (__any_sync(0xffffffffu, contrib)) {
-        d_mx = warp_sum(d_mx);
-        d_my = warp_sum(d_my);
-        d_a = warp_sum(d_a);
-        d_b = warp_sum(d_b);
-        d_c = warp_sum(d_c);
-        d_s = warp_sum(d_s);
-        d_r = warp_sum(d_r);
-        d_g = warp_sum(d_g);
-        d_bl = warp_sum(d_bl);
-        if (lane == 0) {
-          float4* G = reinterpret_cast<float4*>(a.grad2d + 12ll * s_row[k]);
-          atomicAdd(G, make_float4(d_mx, d_my, d_a, d_b));
-          atomicAdd(G + 1, make_float4(d_c, d_s, d_r, d_g));
-          atomicAdd(reinterpret_cast<float*>(G + 2), d_bl);
-        }
+      if (__any_sync(kFull, contrib)) {
+        int slot;
+        const float tot = warp_sum9(gsum, lane, slot);
+        if (slot >= 0) atomicAdd(a.grad2d + 12ll * s_row[k] + slot, tot);
       }
     }
     end = start;
@@ -312,10 +377,11 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
   __syncthreads();
 }
 
-template <int DT>
-__global__ void __launch_bounds__(kThreads) render_bwd_kernel(const CamTable ct,
-                                                              const RenderConsts rc,
-                                                              const BwdArgs a, int persistent) {
+template <int DT, int PPT>
+__global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(const CamTable ct,
+                                                                    const RenderConsts rc,
+                                                                    const BwdArgs a,
+                                                                    int persistent) {
   if (persistent) {
     __shared__ unsigned s_t;
     for (;;) {
@@ -324,11 +390,11 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const CamTable ct,
       const unsigned t = s_t;
       __syncthreads();
       if (t >= (unsigned)ct.total_tiles) break;
-      bwd_tile<DT>(ct, rc, a, a.order ? (int)a.order[t] : (int)t);
+      bwd_tile<DT, PPT>(ct, rc, a, a.order ? (int)a.order[t] : (int)t);
     }
   } else {
     const int t = blockIdx.x;
-    bwd_tile<DT>(ct, rc, a, a.order ? (int)a.order[t] : t);
+    bwd_tile<DT, PPT>(ct, rc, a, a.order ? (int)a.order[t] : t);
   }
 }
 
@@ -338,17 +404,34 @@ int record_event(void* ev, cudaStream_t st) {
   return GS_OK;
 }
 
+template <int DT, int PPT>
+void launch_fwd_ppt(const CamTable& ct, const RenderConsts& rc, const FwdArgs& a, int ctas,
+                    cudaStream_t st) {
+  const int grid = ctas > 0 ? ctas : ct.total_tiles;
+  const int pers = ctas > 0 ? 1 : 0;
+  if (a.stats)
+    render_fwd_kernel<DT, PPT, true><<<grid, kTilePix / PPT, 0, st>>>(ct, rc, a, pers);
+  else
+    render_fwd_kernel<DT, PPT, false><<<grid, kTilePix / PPT, 0, st>>>(ct, rc, a, pers);
+}
+
+template <int DT, int PPT>
+void launch_bwd_ppt(const CamTable& ct, const RenderConsts& rc, const BwdArgs& a, int ctas,
+                    cudaStream_t st) {
+  const int grid = ctas > 0 ? ctas : ct.total_tiles;
+  render_bwd_kernel<DT, PPT><<<grid, kTilePix / PPT, 0, st>>>(ct, rc, a, ctas > 0 ? 1 : 0);
+}
+
 template <int DT>
 int launch_fwd_t(const CamTable& ct, const RenderConsts& rc, const FwdArgs& a, int ctas,
                  const gs_launch* opt, cudaStream_t st) {
   int e = record_event(opt ? opt->ev_begin : nullptr, st);
   if (e != GS_OK) return e;
+  const int ppt = (opt && opt->pixels_per_thread) ? opt->pixels_per_thread : 2;
   if (ct.total_tiles > 0) {
-    if (ctas > 0) {
-      render_fwd_kernel<DT><<<ctas, kThreads, 0, st>>>(ct, rc, a, 1);
-    } else {
-      render_fwd_kernel<DT><<<ct.total_tiles, kThreads, 0, st>>>(ct, rc, a, 0);
-    }
+    if (ppt == 1) launch_fwd_ppt<DT, 1>(ct, rc, a, ctas, st);
+    else if (ppt == 4) launch_fwd_ppt<DT, 4>(ct, rc, a, ctas, st);
+    else launch_fwd_ppt<DT, 2>(ct, rc, a, ctas, st);
     count_launches(1);
   }
   e = record_event(opt ? opt->ev_end : nullptr, st);
@@ -361,12 +444,11 @@ int launch_bwd_t(const CamTable& ct, const RenderConsts& rc, const BwdArgs& a, i
                  const gs_launch* opt, cudaStream_t st) {
   int e = record_event(opt ? opt->ev_begin : nullptr, st);
   if (e != GS_OK) return e;
+  const int ppt = (opt && opt->pixels_per_thread) ? opt->pixels_per_thread : 2;
   if (ct.total_tiles > 0) {
-    if (ctas > 0) {
-      render_bwd_kernel<DT><<<ctas, kThreads, 0, st>>>(ct, rc, a, 1);
-    } else {
-      render_bwd_kernel<DT><<<ct.total_tiles, kThreads, 0, st>>>(ct, rc, a, 0);
-    }
+    if (ppt == 1) launch_bwd_ppt<DT, 1>(ct, rc, a, ctas, st);
+    else if (ppt == 4) launch_bwd_ppt<DT, 4>(ct, rc, a, ctas, st);
+    else launch_bwd_ppt<DT, 2>(ct, rc, a, ctas, st);
     count_launches(1);
   }
   e = record_event(opt ? opt->ev_end : nullptr, st);
