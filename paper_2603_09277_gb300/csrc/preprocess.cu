@@ -11,8 +11,10 @@
 // coalesced across the warp; quaternions and SH rows use 16-byte loads.
 //
 // Backward: hand-derived adjoint of the same steps, one thread per
-// Gaussian, summing over views; Sigma's gradient is accumulated over views
-// and pushed to scale and rotation once.
+// Gaussian, summing over views; the covariance part runs through the
+// Cholesky factor of the 2D covariance (whitened form) and accumulates the
+// log-scale and rotation-matrix gradients over views, pushed to the
+// quaternion once.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -427,8 +429,9 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(
 
   Activated a = activate(means, log_scales, quats, opacity_logits, g);
   float gm[3] = {0.f, 0.f, 0.f};
-  float gSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma, symmetric (xx xy xz yy yz zz),
-                                                   // off-diagonals hold the (i,j) entry
+  float gls[3] = {0.f, 0.f, 0.f};  // dL/d log-scale, summed over views
+  float gRq[9];                    // dL/d(rotation matrix entries), summed over views
+  for (int k = 0; k < 9; ++k) gRq[k] = 0.f;
   float gsig = 0.f;
   for (int v = 0; v < ct.V; ++v) {
     long long row = (long long)v * N + g;
@@ -474,36 +477,56 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(
       gm[2] += (gd.z - dz * dd) * il;
     }
 
-    // --- conic -> Sigma' (with dilation):  dL/dSigma' = -K Gk K
-    float ka = p.ca, kb = p.cb, kc = p.cc;
-    float ga = G0.z, gb = G0.w, gc = G1.x;
-    float M00 = ka * ka * ga + ka * kb * gb + kb * kb * gc;
-    float M01 = ka * kb * ga + 0.5f * (kb * kb + ka * kc) * gb + kb * kc * gc;
-    float M11 = kb * kb * ga + kb * kc * gb + kc * kc * gc;
-    float GS00 = -M00, GS01 = -M01, GS11 = -M11;  // symmetric dL/dSigma' (full matrix entries)
-
-    // --- Sigma' = T Sigma T^T: dL/dSigma += T^T GS T ; dL/dT = 2 GS T Sigma
+    // --- conic -> (N, T), in whitened form.  With Sigma' + dilation I =
+    // N N^T + d I = L L^T (L from the forward), Gk the gradient of the conic
+    // as a symmetric matrix and G^ = L^-1 Gk L^-T, Z = L^-1 N, T^ = L^-1 T:
+    //   dL/dN = -2 L^-T G^ Z,   dL/dM = -2 T^T G^ Z,
+    //   dL/d log s_j = -2 Z_j^T G^ Z_j (Z_j = column j of Z).
+    // Every factor is scaled by L^-1, so the condition number of Sigma' is
+    // not squared as it would be through dL/dSigma' = -K Gk K.
     const float* T = p.T;
-    float GT_[6];  // GS T (2x3)
+    const float l11 = sqrtf(p.A);
+    const float l21 = p.B / l11;
+    const float l22 = sqrtf(p.det) / l11;
+    const float i11 = 1.f / l11, i22 = 1.f / l22;
+    const float i21 = -l21 * i11 * i22;
+    float Th[6];
     for (int j = 0; j < 3; ++j) {
-      GT_[j] = GS00 * T[j] + GS01 * T[3 + j];
-      GT_[3 + j] = GS01 * T[j] + GS11 * T[3 + j];
+      Th[j] = T[j] * i11;
+      Th[3 + j] = (T[3 + j] - l21 * Th[j]) * i22;
     }
-    // T^T (GS T): 3x3 symmetric
-    gSig[0] += T[0] * GT_[0] + T[3] * GT_[3];
-    gSig[1] += T[0] * GT_[1] + T[3] * GT_[4];
-    gSig[2] += T[0] * GT_[2] + T[3] * GT_[5];
-    gSig[3] += T[1] * GT_[1] + T[4] * GT_[4];
-    gSig[4] += T[1] * GT_[2] + T[4] * GT_[5];
-    gSig[5] += T[2] * GT_[2] + T[5] * GT_[5];
-    const float* S = a.Sig;
+    float Z[6];
+    for (int j = 0; j < 3; ++j) {
+      Z[j] = a.s[j] * (Th[0] * a.Rq[j] + Th[1] * a.Rq[3 + j] + Th[2] * a.Rq[6 + j]);
+      Z[3 + j] = a.s[j] * (Th[3] * a.Rq[j] + Th[4] * a.Rq[3 + j] + Th[5] * a.Rq[6 + j]);
+    }
+    const float ga = G0.z, gbh = 0.5f * G0.w, gc = G1.x;
+    const float G00 = i11 * i11 * ga;
+    const float G01 = i11 * (i21 * ga + i22 * gbh);
+    const float G11 = i21 * i21 * ga + 2.f * i21 * i22 * gbh + i22 * i22 * gc;
+    float GZ[6];
+    for (int j = 0; j < 3; ++j) {
+      GZ[j] = G00 * Z[j] + G01 * Z[3 + j];
+      GZ[3 + j] = G01 * Z[j] + G11 * Z[3 + j];
+    }
+    for (int j = 0; j < 3; ++j) {
+      gls[j] += -2.f * (Z[j] * GZ[j] + Z[3 + j] * GZ[3 + j]);
+      for (int i = 0; i < 3; ++i)
+        gRq[i * 3 + j] += -2.f * a.s[j] * (Th[i] * GZ[j] + Th[3 + i] * GZ[3 + j]);
+    }
+    // dL/dT = dL/dN M^T with dL/dN = -2 L^-T G^ Z
+    float gN[6];
+    for (int j = 0; j < 3; ++j) {
+      gN[j] = -2.f * (i11 * GZ[j] + i21 * GZ[3 + j]);
+      gN[3 + j] = -2.f * i22 * GZ[3 + j];
+    }
     float gT[6];
-    for (int i = 0; i < 2; ++i) {
-      const float* gt = GT_ + 3 * i;
-      gT[3 * i + 0] = 2.f * (gt[0] * S[0] + gt[1] * S[1] + gt[2] * S[2]);
-      gT[3 * i + 1] = 2.f * (gt[0] * S[1] + gt[1] * S[3] + gt[2] * S[4]);
-      gT[3 * i + 2] = 2.f * (gt[0] * S[2] + gt[1] * S[4] + gt[2] * S[5]);
-    }
+    for (int r = 0; r < 2; ++r)
+      for (int i = 0; i < 3; ++i) {
+        float acc = 0.f;
+        for (int j = 0; j < 3; ++j) acc += gN[3 * r + j] * a.Rq[i * 3 + j] * a.s[j];
+        gT[3 * r + i] = acc;
+      }
     // --- T = J W
     float gJ00 = gT[0] * c.R[0] + gT[1] * c.R[1] + gT[2] * c.R[2];
     float gJ02 = gT[0] * c.R[6] + gT[1] * c.R[7] + gT[2] * c.R[8];
@@ -538,21 +561,8 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(
   g_means[3ll * g + 2] = gm[2];
   g_opac[g] = gsig * a.sigma * (1.f - a.sigma);
 
-  // --- Sigma = M M^T with M = Rq diag(s):  dL/dM = 2 GSig M
-  float Gf[9] = {gSig[0], gSig[1], gSig[2], gSig[1], gSig[3], gSig[4], gSig[2], gSig[4], gSig[5]};
-  float M[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) M[i * 3 + j] = a.Rq[i * 3 + j] * a.s[j];
-  float GM[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j)
-      GM[i * 3 + j] = 2.f * (Gf[i * 3] * M[j] + Gf[i * 3 + 1] * M[3 + j] + Gf[i * 3 + 2] * M[6 + j]);
-  float GR[9];
-  for (int j = 0; j < 3; ++j) {
-    float gs_ = GM[j] * a.Rq[j] + GM[3 + j] * a.Rq[3 + j] + GM[6 + j] * a.Rq[6 + j];
-    g_ls[3ll * g + j] = gs_ * a.s[j];
-    for (int i = 0; i < 3; ++i) GR[i * 3 + j] = GM[i * 3 + j] * a.s[j];
-  }
+  for (int j = 0; j < 3; ++j) g_ls[3ll * g + j] = gls[j];
+  const float* GR = gRq;
   // --- rotation matrix of the unit quaternion
   float w = a.q[0], x = a.q[1], y = a.q[2], z = a.q[3];
   float gw = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
