@@ -244,6 +244,40 @@ int gs_scale_reset(float* log_scales, long long n, float zeta, gs_stream stream)
 int gs_tile_queue(const unsigned* tile_ranges, long long total_tiles, unsigned* tile_order,
                   void* workspace, size_t workspace_bytes, gs_stream stream);
 
+/* ---------------------------------------------------------------------- */
+/* Tile queue without allocation                                           */
+/* ---------------------------------------------------------------------- */
+
+/* Largest tile count gs_tile_queue_static accepts. */
+#define GS_TILE_QUEUE_STATIC_MAX_TILES 65536
+
+/* Same result as gs_tile_queue (tile ids ordered by list length, longest
+ * first, ties by tile id), for callers that cannot allocate device memory:
+ * code whose device memory comes from a fixed pool or arena owned by a host
+ * application, code on a latency-critical thread where cudaMalloc /
+ * cudaFree would synchronise the device, and code paths that must not
+ * allocate at all.  The paper has no counterpart; this is a library
+ * convenience.
+ *
+ * Instead of a caller-provided workspace it uses a scratch array in device
+ * global memory that the library declares at file scope (about 1.05 MB,
+ * enough for GS_TILE_QUEUE_STATIC_MAX_TILES tiles); every GPU that loads
+ * the library holds that memory until the process exits.  The call itself
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *   tile_ranges [2*total_tiles] device in; tile_order [total_tiles] device out.
+ *   total_tiles > GS_TILE_QUEUE_STATIC_MAX_TILES: GS_ERR_INVALID_ARG, with the
+ *   limit in gs_last_error_string(), before anything is enqueued.
+ * The first call on a device looks up the scratch array's device address on
+ * the current device (cudaGetSymbolAddress) and caches it; make that first
+ * call before any stream capture on that device.
+ * All calls share the one array and it keeps the last call's contents (no
+ * part needs to start at zero: a call writes every word before reading it).
+ * Calls whose work overlaps on the GPU (different streams without ordering,
+ * or different host threads) race on the array: order them on one stream or
+ * with events. */
+int gs_tile_queue_static(const unsigned* tile_ranges, long long total_tiles, unsigned* tile_order,
+                         gs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,11 @@ int invalid(const char* what) {
 }
 }  // namespace
 
+int set_error_text_and_status(const char* msg, int status) {
+  set_error_text(msg);
+  return status;
+}
+
 int set_cuda_error(cudaError_t e) {
   char buf[512];
   snprintf(buf, sizeof buf, "CUDA error %d: %s", (int)e, cudaGetErrorString(e));

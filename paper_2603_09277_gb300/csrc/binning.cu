@@ -21,6 +21,7 @@
 // in a CUDA graph (no host synchronisation needed).  None of them waits on
 // another block.
 #include <algorithm>
+#include <mutex>
 
 #include "gs_internal.cuh"
 
@@ -585,3 +586,65 @@ int launch_tile_queue(const unsigned* ranges, long long T, unsigned* order, void
 }
 
 }  // namespace gs
+
+// ----------------------------------------------------------------------------
+// Tile queue without allocation: the same sort, run in a fixed scratch array
+// in device global memory that the library owns (see gs_tile_queue_static in
+// include/gs.h).
+// ----------------------------------------------------------------------------
+
+// Scratch of the no-allocation tile queue, sized for
+// GS_TILE_QUEUE_STATIC_MAX_TILES tiles with the layout of launch_tile_queue:
+// three key/value arrays, the count, and the radix histograms.  Every GPU that
+// loads the library holds these bytes until the process exits.
+static __device__ __align__(256) unsigned char g_queue_scratch[
+    ((4ull * (GS_TILE_QUEUE_STATIC_MAX_TILES + 1) + 255) / 256 * 256) * 3 + 256 +
+    (4ull * 256 * (2 * 152 + 1) + 255) / 256 * 256];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_queue_scratch_mutex;
+void* g_queue_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_queue_scratch on the current device, looked up once per
+// device (in host code the array's name is only a stand-in, not a device
+// address).
+int queue_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return gs::set_cuda_error(e);
+  if (dev < 0 || dev >= kMaxDevices)
+    return gs::set_error_text_and_status("unsupported device index", GS_ERR_UNSUPPORTED);
+  std::lock_guard<std::mutex> lock(g_queue_scratch_mutex);
+  if (!g_queue_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_queue_scratch);
+    if (e != cudaSuccess) return gs::set_cuda_error(e);
+    g_queue_scratch_ptr[dev] = p;
+  }
+  *out = g_queue_scratch_ptr[dev];
+  return GS_OK;
+}
+
+}  // namespace
+
+extern "C" int gs_tile_queue_static(const unsigned* tile_ranges, long long total_tiles,
+                                    unsigned* tile_order, gs_stream stream) {
+  if (total_tiles < 0 || total_tiles > GS_TILE_QUEUE_STATIC_MAX_TILES) {
+    char buf[160];
+    snprintf(buf, sizeof buf,
+             "invalid argument: gs_tile_queue_static supports at most %d tiles (got %lld)",
+             GS_TILE_QUEUE_STATIC_MAX_TILES, total_tiles);
+    return gs::set_error_text_and_status(buf, GS_ERR_INVALID_ARG);
+  }
+  if (total_tiles > 0 && (!tile_ranges || !tile_order))
+    return gs::set_error_text_and_status("invalid argument: pointers", GS_ERR_INVALID_ARG);
+  void* scratch = nullptr;
+  const int rc = queue_scratch_address(&scratch);
+  if (rc != GS_OK) return rc;
+  // Nothing in the scratch needs to start at zero: each call writes every word
+  // it reads (keys, values, histograms, the count) before reading it.
+  return gs::launch_tile_queue(tile_ranges, total_tiles, tile_order, scratch,
+                               sizeof(g_queue_scratch), (cudaStream_t)stream);
+}

@@ -7,6 +7,7 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <stdio.h>
 
 #include "gs.h"
 
@@ -198,6 +199,7 @@ __device__ __forceinline__ int find_view_of_pixel(const CamTable& ct, long long 
 // ---------------------------------------------------------------------------
 namespace gs {
 int set_cuda_error(cudaError_t e);
+int set_error_text_and_status(const char* msg, int status);
 void count_launches(int n);
 int check_launch();
 bool build_cam_table(const gs_camera* cams, int V, const gs_params* prm, CamTable* ct);

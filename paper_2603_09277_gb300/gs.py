@@ -93,6 +93,7 @@ def _load():
                               vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, P(GsLaunch), vp]),
         "gs_scale_reset": (i, [vp, ll, f, vp]),
         "gs_tile_queue": (i, [vp, ll, vp, vp, sz, vp]),
+        "gs_tile_queue_static": (i, [vp, ll, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -105,7 +106,8 @@ _lib = _load()
 EXPORTED = ["gs_record_bytes", "gs_total_tiles", "gs_total_pixels", "gs_bin_sort_workspace_size",
             "gs_loss_workspace_size", "gs_tile_queue_workspace_size", "gs_status_string",
             "gs_last_error_string", "gs_version", "gs_kernel_launches", "gs_preprocess", "gs_bin_sort", "gs_render_fwd",
-            "gs_loss_l1_entropy", "gs_render_bwd", "gs_scale_reset", "gs_tile_queue"]
+            "gs_loss_l1_entropy", "gs_render_bwd", "gs_scale_reset", "gs_tile_queue",
+            "gs_tile_queue_static"]
 
 
 def library_path() -> str:
@@ -278,3 +280,14 @@ def gs_tile_queue(tile_ranges, total_tiles, tile_order, workspace, stream=None):
     return _check("gs_tile_queue", _lib.gs_tile_queue(
         _ptr(tile_ranges), total_tiles, _ptr(tile_order), _ptr(workspace),
         workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def gs_tile_queue_static(tile_ranges, total_tiles, tile_order, stream=None):
+    """Tile queue in the library's fixed scratch array (no allocation);
+    returns the status instead of raising on GS_ERR_INVALID_ARG."""
+    st = _lib.gs_tile_queue_static(_ptr(tile_ranges), total_tiles, _ptr(tile_order),
+                                   _stream(stream))
+    if st not in (GS_OK, GS_ERR_INVALID_ARG):
+        raise GsError("gs_tile_queue_static", st)
+    return st
+
