@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--persistent", type=int, default=0,
                     help="CTAs of the persistent list-length-ordered launch (0 = one CTA per tile)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the comparison of launch forms and staging precisions")
+    ap.add_argument("--ppt", type=int, default=0, help="pixels per thread of the blending kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-band-rows", type=int, default=0,
                     help="tile rows of view 0 the CPU oracle sample renders (0 = the whole view)")
@@ -234,6 +237,41 @@ def traffic_from_profiles(kernel):
     return ent.get("bytes_per_launch")
 
 
+def time_variant(make, p, tgt, gamma, flush, steps, warmup=2):
+    """Mean ms per fwd+bwd step (projection .. adjoint) of the rasterizers
+    `make()` returns (run back to back: one per view for the per-view form)."""
+    import torch
+    rs = make()
+    for _ in range(warmup):
+        for r in rs:
+            r.preprocess(p)
+            r.bin_sort(sync=True)
+            r.render_fwd()
+            r.loss(tgt[r], gamma) if isinstance(tgt, dict) else r.loss(tgt, gamma)
+            r.render_bwd(p)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        a.record()
+        for r in rs:
+            r.preprocess(p)
+            r.bin_sort(sync=False)
+            r.render_fwd()
+            r.loss(tgt[r], gamma) if isinstance(tgt, dict) else r.loss(tgt, gamma)
+            r.render_bwd(p)
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    if any(int(r.status_dev.item()) != 0 for r in rs):
+        raise RuntimeError("pair capacity overflow in a variant")
+    out = float(np.mean(ms))
+    del rs
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -254,7 +292,8 @@ def main():
 
     (scene, cams, targets, prm), wl = workload(args.config, rank)
     N = scene["means"].shape[0]
-    r = Rasterizer(cams, prm, N, attr_dtype=args.attr, device=dev, persistent=args.persistent)
+    r = Rasterizer(cams, prm, N, attr_dtype=args.attr, device=dev, persistent=args.persistent,
+                   pixels_per_thread=args.ppt)
     p = scene_to_device(scene, dev)
     tgt = targets_to_device(targets, dev)
     ls_work = p["log_scales"].clone()  # the scale reset writes a working copy
@@ -397,6 +436,35 @@ def main():
         e2e = {"value": nb_all * K / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000.0 * t_e2e / K}
 
+    # launch forms and staging precisions on the same workload ("batched +
+    # mixed vs plain"): fwd+bwd ms per step, no scale reset, L2 flushed
+    variants = None
+    if world == 1 and not args.no_variants:
+        KV = max(5, min(20, K))
+        variants = {}
+        V = len(cams)
+        forms = [("plain_f32", dict()), ("persistent_f32", dict(persistent=152 * 8)),
+                 ("plain_f16", dict(attr_dtype="f16")), ("plain_bf16", dict(attr_dtype="bf16")),
+                 ("persistent_bf16", dict(persistent=152 * 8, attr_dtype="bf16")),
+                 ("plain_f32_1px", dict(pixels_per_thread=1)),
+                 ("plain_f32_4px", dict(pixels_per_thread=4))]
+        for name, kw in forms:
+            variants[name] = time_variant(
+                lambda kw=kw: [Rasterizer(cams, prm, N, device=dev, pair_capacity=r.capacity,
+                                          **kw)], p, tgt, gamma, flush, KV)
+        if V > 1:
+            # the unbatched form: one single-view pipeline per view, back to back
+            offs = np.cumsum([0] + [c["width"] * c["height"] for c in cams])
+
+            def per_view():
+                rs = [Rasterizer([c], prm, N, device=dev) for c in cams]
+                return rs
+            rs_probe = per_view()
+            tg = {rr: tgt[offs[v]:offs[v + 1]] for v, rr in enumerate(rs_probe)}
+            variants["per_view_f32"] = time_variant(lambda: rs_probe, p, tg, gamma, flush, KV)
+        variants = {k: {"ms_per_step": v, "value": nb_all / (v / 1000.0)}
+                    for k, v in variants.items()}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -420,6 +488,7 @@ def main():
                        "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "phases_ms": phase,
+            "variants": variants,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

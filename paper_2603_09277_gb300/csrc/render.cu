@@ -38,6 +38,9 @@ namespace {
 
 constexpr int kBatch = kTilePix;  // 256 records per staging batch
 constexpr unsigned kFull = 0xffffffffu;
+// A row coordinate this far from every mean makes the exponent -inf (f22 > 0),
+// so a finished or outside pixel never passes the alpha_min test again.
+constexpr float kFar = 1e30f;
 
 template <int PPT>
 struct TileGeom {
@@ -101,11 +104,13 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
   float T[PPT], cr[PPT], cg[PPT], cb[PPT], swl[PPT];
   unsigned last[PPT];
   unsigned live = tg.inside;  // bit k: pixel k still walking
+  float ry[PPT];              // pixel-centre y relative to the tile; kFar once finished
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     T[k] = 1.f;
     cr[k] = cg[k] = cb[k] = swl[k] = 0.f;
     last[k] = 0u;
+    ry[k] = (live & (1u << k)) ? tg.ry0 + (float)k : kFar;
   }
   unsigned nb = 0, ne = 0;
   for (unsigned base = r.x; base < r.y; base += kBatch) {
@@ -126,17 +131,24 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
       const float4 g0 = s0[k];
       const float4 g1 = s1[k];
       const SplatColumn col = splat_column(g0.z, g0.w, g1.y, tg.rx - g0.x);
+      float e[PPT];
+      float emax = -INFINITY;
 #pragma unroll
       for (int q = 0; q < PPT; ++q) {
-        if (!(live & (1u << q))) continue;
         float qq;
-        const float e = splat_row(col, g1.x, tg.ry0 + (float)q - g0.y, qq);
-        if (STATS) ++ne;
-        if (e < rc.log2_alpha_min) continue;
-        const float alpha = fminf(rc.alpha_max, fast_exp2(e));
+        e[q] = splat_row(col, g1.x, ry[q] - g0.y, qq);
+        emax = fmaxf(emax, e[q]);
+      }
+      if (STATS) ne += __popc(live);
+      if (emax < rc.log2_alpha_min) continue;  // no pixel of this thread is reached
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) {
+        if (e[q] < rc.log2_alpha_min) continue;
+        const float alpha = fminf(rc.alpha_max, fast_exp2(e[q]));
         const float test_T = T[q] * (1.f - alpha);
         if (test_T < rc.t_min) {
           live &= ~(1u << q);
+          ry[q] = kFar;  // finished pixels evaluate to e = -inf from here on
           continue;
         }
         const float w = alpha * T[q];
@@ -266,7 +278,7 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
                                          const BwdArgs& a, int tile) {
   __shared__ float4 s0[kBatch];
   __shared__ float4 s1[kBatch];
-  __shared__ float2 s2[kBatch];
+  __shared__ float2 s2[kBatch];  // (B, 1 / sigma)
   __shared__ unsigned s_row[kBatch];
   __shared__ unsigned s_max;
   constexpr int NT = TileGeom<PPT>::kThreads;
@@ -310,7 +322,7 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
       const float2 m = tile_relative_mean(s, tg.ox, tg.oy);
       s0[j] = make_float4(m.x, m.y, s.f11, s.f21);
       s1[j] = make_float4(s.f22, s.L2S, s.R, s.G);
-      s2[j] = make_float2(s.B, s.sigma);
+      s2[j] = make_float2(s.B, 1.f / s.sigma);
       s_row[j] = row;
     }
     __syncthreads();
@@ -338,7 +350,7 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
           contrib = true;
           const float araw = fast_exp2(e);
           const float alpha = fminf(rc.alpha_max, araw);
-          const float iom = 1.f / (1.f - alpha);
+          const float iom = fast_rcp(1.f - alpha);
           const float Ti = T[q] * iom;
           const float w = alpha * Ti;
           const float lnw = fast_log2(w) * kLn2;
@@ -355,7 +367,7 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
           T[q] = Ti;
           if (araw <= rc.alpha_max) {
             const float dd = dA * araw;
-            gsum[5] += dd / g2.y;  // dA * g with g = araw / sigma
+            gsum[5] += dd * g2.y;  // dA * g with g = araw / sigma
             gsum[2] += -0.5f * dd * dx * dx;
             gsum[3] += -dd * dx * dy;
             gsum[4] += -0.5f * dd * dy * dy;
@@ -366,10 +378,22 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
           }
         }
       }
-      if (__any_sync(kFull, contrib)) {
-        int slot;
-        const float tot = warp_sum9(gsum, lane, slot);
-        if (slot >= 0) atomicAdd(a.grad2d + 12ll * s_row[k] + slot, tot);
+      const unsigned who = __ballot_sync(kFull, contrib);
+      if (who) {
+        float* G = a.grad2d + 12ll * s_row[k];
+        if (__popc(who) == 1) {
+          // one contributing lane: its values are the warp totals
+          if (contrib) {
+            atomicAdd(reinterpret_cast<float4*>(G), make_float4(gsum[0], gsum[1], gsum[2], gsum[3]));
+            atomicAdd(reinterpret_cast<float4*>(G) + 1,
+                      make_float4(gsum[4], gsum[5], gsum[6], gsum[7]));
+            atomicAdd(G + 8, gsum[8]);
+          }
+        } else {
+          int slot;
+          const float tot = warp_sum9(gsum, lane, slot);
+          if (slot >= 0) atomicAdd(G + slot, tot);
+        }
       }
     }
     end = start;
