@@ -260,7 +260,7 @@ int gs_tile_queue(const unsigned* tile_ranges, long long total_tiles, unsigned* 
  * convenience.
  *
  * Instead of a caller-provided workspace it uses a scratch array in device
- * global memory that the library declares at file scope (about 1.05 MB,
+ * global memory that the library declares at file scope (about 1.35 MB,
  * enough for GS_TILE_QUEUE_STATIC_MAX_TILES tiles); every GPU that loads
  * the library holds that memory until the process exits.  The call itself
  * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).

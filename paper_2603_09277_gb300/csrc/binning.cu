@@ -233,6 +233,11 @@ __global__ void __launch_bounds__(kScanThreads) radix_scan_kernel(unsigned* __re
   if (threadIdx.x == 0) totals[blockIdx.x] = (unsigned)tot;
 }
 
+// Scatter of one radix pass.  Per 2048-item tile: digits ranked with warp
+// match_any (stable within the tile), the tile is reordered by digit in shared
+// memory, then written out so that consecutive threads store consecutive
+// addresses of one digit's run (coalesced), and each digit's running global
+// offset advances by the tile's count.
 __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
     const unsigned* __restrict__ keys_in, const unsigned* __restrict__ vals_in,
     unsigned* __restrict__ keys_out, unsigned* __restrict__ vals_out,
@@ -240,7 +245,10 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
     const unsigned* __restrict__ totals) {
   __shared__ unsigned s_wc[kRadixWarps][kRadixBins + 1];  // per-warp digit counters (+ dummy)
   __shared__ unsigned s_base[kRadixBins];                 // running global offset per digit
-  __shared__ unsigned s_tot[kRadixBins];
+  __shared__ unsigned s_tot[kRadixBins];                  // tile count per digit
+  __shared__ unsigned s_off[kRadixBins];                  // tile-local start per digit
+  __shared__ unsigned s_key[kRadixTile];
+  __shared__ unsigned s_val[kRadixTile];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   long long n = *n_dev;
@@ -257,13 +265,14 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
     (&s_wc[0][0])[i] = 0u;
   __syncthreads();
   for (long long t0 = b0; t0 < b1; t0 += kRadixTile) {
+    const int cnt = (int)min((long long)kRadixTile, b1 - t0);
     unsigned k[kRadixIpt], v[kRadixIpt], dg[kRadixIpt], loc[kRadixIpt];
 #pragma unroll
     for (int i = 0; i < kRadixIpt; ++i) {
-      long long idx = t0 + (long long)w * (32 * kRadixIpt) + i * 32 + lane;
-      bool ok = idx < b1;
-      k[i] = ok ? keys_in[idx] : 0u;
-      v[i] = ok ? vals_in[idx] : 0u;
+      const int li = w * (32 * kRadixIpt) + i * 32 + lane;
+      const bool ok = li < cnt;
+      k[i] = ok ? keys_in[t0 + li] : 0u;
+      v[i] = ok ? vals_in[t0 + li] : 0u;
       dg[i] = ok ? ((k[i] >> shift) & 0xffu) : (unsigned)kRadixBins;
     }
 #pragma unroll
@@ -277,7 +286,9 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
       loc[i] = base + rank;
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadixBins; d += kRadixThreads) {
+    {
+      // per digit (one per thread): prefix over warps, tile count, tile-local start
+      const int d = threadIdx.x;
       unsigned run = 0;
       for (int ww = 0; ww < kRadixWarps; ++ww) {
         unsigned c = s_wc[ww][d];
@@ -285,22 +296,33 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
         run += c;
       }
       s_tot[d] = run;
+      unsigned long long tt;
+      s_off[d] = (unsigned)block_excl_scan(run, &tt);
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kRadixIpt; ++i) {
       if (dg[i] < (unsigned)kRadixBins) {
-        unsigned pos = s_base[dg[i]] + s_wc[w][dg[i]] + loc[i];
-        keys_out[pos] = k[i];
-        vals_out[pos] = v[i];
+        const unsigned lp = s_off[dg[i]] + s_wc[w][dg[i]] + loc[i];
+        s_key[lp] = k[i];
+        s_val[lp] = v[i];
       }
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadixBins; d += kRadixThreads) {
+    for (int i = threadIdx.x; i < cnt; i += kRadixThreads) {
+      const unsigned kk = s_key[i];
+      const unsigned d = (kk >> shift) & 0xffu;
+      const unsigned pos = s_base[d] + (unsigned)i - s_off[d];
+      keys_out[pos] = kk;
+      vals_out[pos] = s_val[i];
+    }
+    __syncthreads();
+    {
+      const int d = threadIdx.x;
       s_base[d] += s_tot[d];
       for (int ww = 0; ww < kRadixWarps; ++ww) s_wc[ww][d] = 0u;
+      if (d < kRadixWarps) s_wc[d][kRadixBins] = 0u;
     }
-    if (threadIdx.x < kRadixWarps) s_wc[threadIdx.x][kRadixBins] = 0u;
     __syncthreads();
   }
 }
@@ -405,7 +427,7 @@ struct Workspace {
   size_t bytes;
 };
 
-constexpr int kRadixGrid = 2 * 152;  // fixed radix grid (2 CTAs per SM)
+constexpr int kRadixGrid = 4 * 152;  // fixed radix grid (4 CTAs per SM)
 
 inline long long scan_blocks(long long n) { return (n + kScanTile - 1) / kScanTile; }
 
@@ -599,7 +621,7 @@ int launch_tile_queue(const unsigned* ranges, long long T, unsigned* order, void
 // loads the library holds these bytes until the process exits.
 static __device__ __align__(256) unsigned char g_queue_scratch[
     ((4ull * (GS_TILE_QUEUE_STATIC_MAX_TILES + 1) + 255) / 256 * 256) * 3 + 256 +
-    (4ull * 256 * (2 * 152 + 1) + 255) / 256 * 256];
+    (4ull * gs::kRadixBins * (gs::kRadixGrid + 1) + 255) / 256 * 256];
 
 namespace {
 
