@@ -233,8 +233,8 @@ __global__ void __launch_bounds__(kScanThreads) radix_scan_kernel(unsigned* __re
   if (threadIdx.x == 0) totals[blockIdx.x] = (unsigned)tot;
 }
 
-// Scatter of one radix pass.  Per 2048-item tile: digits ranked with warp
-// match_any (stable within the tile), the tile is reordered by digit in shared
+// Scatter of one radix pass.  Per 2048-item tile: digits ranked within each
+// warp from bit ballots (stable within the tile), the tile is reordered by digit in shared
 // memory, then written out so that consecutive threads store consecutive
 // addresses of one digit's run (coalesced), and each digit's running global
 // offset advances by the tile's count.
@@ -277,7 +277,16 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
     }
 #pragma unroll
     for (int i = 0; i < kRadixIpt; ++i) {
-      unsigned peers = __match_any_sync(0xffffffffu, dg[i]);
+      // lanes holding the same digit: one ballot per digit bit plus validity
+      const bool valid = dg[i] < (unsigned)kRadixBins;
+      const unsigned vm = __ballot_sync(0xffffffffu, valid);
+      unsigned peers = valid ? vm : ~vm;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const bool bit = (dg[i] >> b) & 1u;
+        const unsigned m = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? m : ~m;
+      }
       unsigned rank = __popc(peers & lt_mask);
       unsigned base = s_wc[w][dg[i]];
       __syncwarp();
@@ -339,9 +348,10 @@ __global__ void capacity_check_kernel(const long long* __restrict__ P, long long
   }
 }
 
-// One warp per 32 consecutive depth-sorted rows; for each row in turn the 32
-// lanes write its tiles (row-major over the rect), so long rects do not
-// serialise one thread and the writes of a row are coalesced.
+// One warp per 32 consecutive depth-sorted rows.  Their pairs are contiguous
+// in the output, so the warp spreads all of them over its lanes: lane t of a
+// round writes pair t, whose row is found by a binary search over the rows'
+// exclusive tile counts (held one per lane), and the stores are coalesced.
 __global__ void __launch_bounds__(256) duplicate_kernel(
     const unsigned* __restrict__ rows, const long long* __restrict__ n_vis,
     const unsigned long long* __restrict__ offsets, const int* __restrict__ rect, int N,
@@ -352,42 +362,82 @@ __global__ void __launch_bounds__(256) duplicate_kernel(
   const int lane = threadIdx.x & 31;
   const long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll;
   if (base >= n) return;
-  // each lane fetches one row's descriptor, then the warp walks them in order
   const long long j = base + lane;
-  unsigned row = 0;
-  int4 r = make_int4(0, 0, 0, 0);
-  unsigned long long off = 0;
+  unsigned row = 0, cnt = 0;
+  int x0 = 0, y0 = 0, w = 1, tb = 0, TX = 1;
   if (j < n) {
     row = rows[j];
-    r = reinterpret_cast<const int4*>(rect)[row];
-    off = offsets[j];
+    const int4 r = reinterpret_cast<const int4*>(rect)[row];
+    const CamInfo& c = ct.c[(int)(row / (unsigned)N)];
+    x0 = r.x;
+    y0 = r.y;
+    w = r.z - r.x;
+    cnt = (unsigned)(w * (r.w - r.y));
+    tb = c.tile_off;
+    TX = c.TX;
   }
-  const int cnt = (int)min(32ll, n - base);
-  for (int k = 0; k < cnt; ++k) {
-    const unsigned rw = __shfl_sync(0xffffffffu, row, k);
-    const int x0 = __shfl_sync(0xffffffffu, r.x, k), y0 = __shfl_sync(0xffffffffu, r.y, k);
-    const int x1 = __shfl_sync(0xffffffffu, r.z, k), y1 = __shfl_sync(0xffffffffu, r.w, k);
-    const unsigned long long o = __shfl_sync(0xffffffffu, off, k);
-    const int w = x1 - x0;
-    const int total = w * (y1 - y0);
-    const CamInfo& c = ct.c[(int)(rw / (unsigned)N)];
-    for (int t = lane; t < total; t += 32) {
-      const int ty = y0 + t / w, tx = x0 + t % w;
-      tkeys[o + t] = (unsigned)(c.tile_off + ty * c.TX + tx);
-      tvals[o + t] = rw;
+  // exclusive prefix of the tile counts over the warp's rows
+  unsigned incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const unsigned excl = incl - cnt;
+  const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+  const unsigned long long o0 = __shfl_sync(0xffffffffu, offsets[base], 0);
+  for (unsigned t0 = 0; t0 < total; t0 += 32) {
+    const unsigned t = t0 + lane;
+    // largest lane r with excl_r <= t (that row has t - excl_r < cnt_r)
+    int r = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const unsigned e = __shfl_sync(0xffffffffu, excl, r + step);
+      if (e <= t) r += step;
+    }
+    const unsigned er = __shfl_sync(0xffffffffu, excl, r);
+    const unsigned rw = __shfl_sync(0xffffffffu, row, r);
+    const int rx0 = __shfl_sync(0xffffffffu, x0, r), ry0 = __shfl_sync(0xffffffffu, y0, r);
+    const int rwid = __shfl_sync(0xffffffffu, w, r);
+    const int rtb = __shfl_sync(0xffffffffu, tb, r), rTX = __shfl_sync(0xffffffffu, TX, r);
+    if (t < total) {
+      const int k = (int)(t - er);
+      const int ty = ry0 + k / rwid, tx = rx0 + k % rwid;
+      tkeys[o0 + t] = (unsigned)(rtb + ty * rTX + tx);
+      tvals[o0 + t] = rw;
     }
   }
 }
 
+// Per-tile [start, end) from the sorted tile ids: each thread reads 4
+// consecutive ids with one 16-byte load (the array is 256-byte aligned) plus
+// its neighbours, and marks where the id changes.
 __global__ void __launch_bounds__(256) ranges_kernel(const unsigned* __restrict__ tkeys,
                                                      const long long* __restrict__ p_eff,
                                                      unsigned* __restrict__ ranges) {
-  long long P = *p_eff;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
-       i += (long long)gridDim.x * blockDim.x) {
-    unsigned t = tkeys[i];
-    if (i == 0 || tkeys[i - 1] != t) ranges[2ll * t] = (unsigned)i;
-    if (i == P - 1 || tkeys[i + 1] != t) ranges[2ll * t + 1] = (unsigned)(i + 1);
+  const long long P = *p_eff;
+  const long long groups = (P + 3) / 4;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < groups;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long i0 = 4 * g;
+    unsigned k[6];
+    if (i0 + 3 < P) {
+      const uint4 v = reinterpret_cast<const uint4*>(tkeys)[g];
+      k[1] = v.x; k[2] = v.y; k[3] = v.z; k[4] = v.w;
+    } else {
+      for (int q = 0; q < 4; ++q) k[1 + q] = i0 + q < P ? tkeys[i0 + q] : 0u;
+    }
+    k[0] = i0 > 0 ? tkeys[i0 - 1] : 0xffffffffu;
+    k[5] = i0 + 4 < P ? tkeys[i0 + 4] : 0xffffffffu;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long long i = i0 + q;
+      if (i >= P) break;
+      const unsigned t = k[1 + q];
+      if (i == 0 || k[q] != t) ranges[2ll * t] = (unsigned)i;
+      const unsigned nxt = (i == P - 1) ? 0xffffffffu : (q < 3 ? k[2 + q] : k[5]);
+      if (i == P - 1 || nxt != t) ranges[2ll * t + 1] = (unsigned)(i + 1);
+    }
   }
 }
 
