@@ -348,64 +348,80 @@ __global__ void capacity_check_kernel(const long long* __restrict__ P, long long
   }
 }
 
-// One warp per 32 consecutive depth-sorted rows.  Their pairs are contiguous
-// in the output, so the warp spreads all of them over its lanes: lane t of a
-// round writes pair t, whose row is found by a binary search over the rows'
-// exclusive tile counts (held one per lane), and the stores are coalesced.
-__global__ void __launch_bounds__(256) duplicate_kernel(
+// Pair duplication, load-balanced over pairs.  The depth-sorted visible rows
+// own contiguous pair ranges [offset_j, offset_j + tiles_j).  Pairs are cut
+// into blocks of kDupPairs; mark_block_starts records, for every block, the row
+// that owns its first pair (each block boundary lies in exactly one row), and
+// duplicate_kernel then has each CTA load the descriptors of the rows that
+// overlap its pairs into shared memory and find the row of each of its pairs
+// by binary search there.  Every CTA writes kDupPairs consecutive pairs with
+// coalesced stores, however the tile counts are distributed over the rows.
+constexpr int kDupThreads = 256;
+constexpr int kDupPairs = 1024;
+
+__global__ void __launch_bounds__(256) mark_block_starts_kernel(
     const unsigned* __restrict__ rows, const long long* __restrict__ n_vis,
-    const unsigned long long* __restrict__ offsets, const int* __restrict__ rect, int N,
-    const CamTable ct, const long long* __restrict__ p_eff, unsigned* __restrict__ tkeys,
-    unsigned* __restrict__ tvals) {
+    const unsigned long long* __restrict__ offsets, const unsigned* __restrict__ tiles_touched,
+    const long long* __restrict__ p_eff, unsigned* __restrict__ block_row) {
   const long long n = *n_vis;
   if (*p_eff == 0) return;
-  const int lane = threadIdx.x & 31;
-  const long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll;
-  if (base >= n) return;
-  const long long j = base + lane;
-  unsigned row = 0, cnt = 0;
-  int x0 = 0, y0 = 0, w = 1, tb = 0, TX = 1;
-  if (j < n) {
-    row = rows[j];
-    const int4 r = reinterpret_cast<const int4*>(rect)[row];
-    const CamInfo& c = ct.c[(int)(row / (unsigned)N)];
-    x0 = r.x;
-    y0 = r.y;
-    w = r.z - r.x;
-    cnt = (unsigned)(w * (r.w - r.y));
-    tb = c.tile_off;
-    TX = c.TX;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long o = offsets[j];
+    const unsigned long long c = tiles_touched[rows[j]];
+    for (unsigned long long b = (o + kDupPairs - 1) / kDupPairs; b * kDupPairs < o + c; ++b)
+      block_row[b] = (unsigned)j;
   }
-  // exclusive prefix of the tile counts over the warp's rows
-  unsigned incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
+}
+
+__global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
+    const unsigned* __restrict__ rows, const long long* __restrict__ n_vis,
+    const unsigned long long* __restrict__ offsets, const int* __restrict__ rect, int N,
+    const CamTable ct, const long long* __restrict__ p_eff,
+    const unsigned* __restrict__ block_row, unsigned* __restrict__ tkeys,
+    unsigned* __restrict__ tvals) {
+  __shared__ long long s_off[kDupPairs];  // row pair offset relative to the block start
+  __shared__ int4 s_rect[kDupPairs];
+  __shared__ unsigned s_row[kDupPairs];
+  __shared__ int s_nrows;
+  const long long P = *p_eff;
+  const long long start = (long long)blockIdx.x * kDupPairs;
+  if (start >= P) return;
+  const long long end = min(P, start + kDupPairs);
+  const long long n = *n_vis;
+  const long long j0 = block_row[blockIdx.x];
+  if (threadIdx.x == 0) s_nrows = 0;
+  __syncthreads();
+  // rows j0 .. j0 + nrows - 1 overlap [start, end); at most kDupPairs of them
+  for (int i = threadIdx.x; i < kDupPairs; i += kDupThreads) {
+    const long long j = j0 + i;
+    if (j < n) {
+      const unsigned long long o = offsets[j];
+      if ((long long)o < end) {
+        const unsigned row = rows[j];
+        s_off[i] = (long long)o - start;  // negative for a row that began before the block
+        s_rect[i] = reinterpret_cast<const int4*>(rect)[row];
+        s_row[i] = row;
+        atomicMax(&s_nrows, i + 1);
+      }
+    }
   }
-  const unsigned excl = incl - cnt;
-  const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
-  const unsigned long long o0 = __shfl_sync(0xffffffffu, offsets[base], 0);
-  for (unsigned t0 = 0; t0 < total; t0 += 32) {
-    const unsigned t = t0 + lane;
-    // largest lane r with excl_r <= t (that row has t - excl_r < cnt_r)
-    int r = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const unsigned e = __shfl_sync(0xffffffffu, excl, r + step);
-      if (e <= t) r += step;
+  __syncthreads();
+  const int nr = s_nrows;
+  for (int t = threadIdx.x; t < (int)(end - start); t += kDupThreads) {
+    int lo = 0, hi = nr - 1;  // last row with s_off <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_off[mid] <= (long long)t) lo = mid; else hi = mid - 1;
     }
-    const unsigned er = __shfl_sync(0xffffffffu, excl, r);
-    const unsigned rw = __shfl_sync(0xffffffffu, row, r);
-    const int rx0 = __shfl_sync(0xffffffffu, x0, r), ry0 = __shfl_sync(0xffffffffu, y0, r);
-    const int rwid = __shfl_sync(0xffffffffu, w, r);
-    const int rtb = __shfl_sync(0xffffffffu, tb, r), rTX = __shfl_sync(0xffffffffu, TX, r);
-    if (t < total) {
-      const int k = (int)(t - er);
-      const int ty = ry0 + k / rwid, tx = rx0 + k % rwid;
-      tkeys[o0 + t] = (unsigned)(rtb + ty * rTX + tx);
-      tvals[o0 + t] = rw;
-    }
+    const int4 r = s_rect[lo];
+    const unsigned rw = s_row[lo];
+    const int k = (int)((long long)t - s_off[lo]);
+    const int w = r.z - r.x;
+    const CamInfo& c = ct.c[(int)(rw / (unsigned)N)];
+    const int ty = r.y + k / w, tx = r.x + k % w;
+    tkeys[start + t] = (unsigned)(c.tile_off + ty * c.TX + tx);
+    tvals[start + t] = rw;
   }
 }
 
@@ -474,6 +490,7 @@ struct Workspace {
   unsigned* pk[2];                 // pair keys (tile), double buffer; pk[1] may alias output
   unsigned* pv;                    // pair values scratch
   unsigned* hist;                  // radix histograms
+  unsigned* block_row;             // first row of every duplication block
   size_t bytes;
 };
 
@@ -499,6 +516,7 @@ Workspace carve(void* base, long long n_rows, long long cap) {
   for (int i = 0; i < 2; ++i) w.pk[i] = reinterpret_cast<unsigned*>(take(4 * (cap + 1)));
   w.pv = reinterpret_cast<unsigned*>(take(4 * (cap + 1)));
   w.hist = reinterpret_cast<unsigned*>(take(4ull * kRadixBins * (kRadixGrid + 1)));
+  w.block_row = reinterpret_cast<unsigned*>(take(4ull * ((cap + kDupPairs - 1) / kDupPairs + 1)));
   w.bytes = off;
   return w;
 }
@@ -595,9 +613,15 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
     pv[0] = w.pv;
     pv[1] = sorted_vals;
   }
-  duplicate_kernel<<<(unsigned)((n_rows + 255) / 256), 256, 0, st>>>(
-      rows_sorted, n_vis, w.offsets, proj->rect, N, ct, p_eff, pk[0], pv[0]);
-  count_launches(1);
+  {
+    const unsigned g1 = (unsigned)std::min<long long>((n_rows + 255) / 256, 152ll * 32);
+    mark_block_starts_kernel<<<g1, 256, 0, st>>>(rows_sorted, n_vis, w.offsets,
+                                                proj->tiles_touched, p_eff, w.block_row);
+    const unsigned g2 = (unsigned)((p_bound + kDupPairs - 1) / kDupPairs);
+    duplicate_kernel<<<g2, kDupThreads, 0, st>>>(rows_sorted, n_vis, w.offsets, proj->rect, N, ct,
+                                                p_eff, w.block_row, pk[0], pv[0]);
+    count_launches(2);
+  }
   // 5. stable sort of the pairs by global tile id
   int res2 = radix_sort(pk, pv, p_eff, p_bound, tbits, w.hist, st);
   // 6. per-tile ranges (and the optional 64-bit keys)
