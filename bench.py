@@ -328,18 +328,15 @@ def main():
     bwd_eval = int(r.last_idx.sum().item())
 
     K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(K)]
+    # (1) eager steps with CUDA events between the phases: the per-phase
+    # breakdown and the live per-kernel durations of the blending kernels
+    KE = min(K, 20)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(KE)]
     for e in evs:  # materialise the event handles
         for x in e:
             x.record()
     torch.cuda.synchronize()
-    launches0 = gs.gs_kernel_launches()
-    sampler = ClockSampler(local)
-    sampler.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    for k in range(K):
+    for k in range(KE):
         flush.fill_(float(k))  # L2 flush between timed steps (outside the step events)
         e = evs[k]
         e[0].record()
@@ -354,12 +351,7 @@ def main():
         gs.gs_scale_reset(ls_work, 0.2)
         e[4].record()
     torch.cuda.synchronize()
-    clocks = sampler.stop()
-    launches = gs.gs_kernel_launches() - launches0
-    status = int(r.status_dev.item())
-    if status != 0:
-        raise RuntimeError("pair capacity overflow in the timed region (status %d)" % status)
-    step_ms = [e[0].elapsed_time(e[4]) for e in evs]
+    eager_ms = float(np.mean([e[0].elapsed_time(e[4]) for e in evs]))
     phase = {
         "preprocess": float(np.mean([e[0].elapsed_time(e[1]) for e in evs])),
         "bin_sort": float(np.mean([e[1].elapsed_time(e[2]) for e in evs])),
@@ -368,6 +360,45 @@ def main():
         "render_bwd_kernel": float(np.mean([e[7].elapsed_time(e[8]) for e in evs])),
         "render_bwd+preprocess_bwd+reset": float(np.mean([e[3].elapsed_time(e[4]) for e in evs])),
     }
+
+    # (2) the timed region: the whole step captured once in a CUDA graph (no
+    # host synchronisation inside a step: the pair count stays on the device
+    # and overflow is checked after the run) and replayed K times
+    graph = torch.cuda.CUDAGraph()
+    cap_stream = torch.cuda.Stream()
+    cap_stream.wait_stream(torch.cuda.current_stream())
+    launches_c0 = gs.gs_kernel_launches()
+    with torch.cuda.stream(cap_stream):
+        with torch.cuda.graph(graph, stream=cap_stream):
+            r.preprocess(p)
+            r.bin_sort(sync=False)
+            r.render_fwd()
+            r.loss(tgt, gamma)
+            r.render_bwd(p)
+            gs.gs_scale_reset(ls_work, 0.2)
+    torch.cuda.current_stream().wait_stream(cap_stream)
+    kernels_per_step = gs.gs_kernel_launches() - launches_c0
+    graph.replay()
+    torch.cuda.synchronize()
+    gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.fill_(float(k))  # L2 flush between timed steps (outside the step events)
+        gev[k][0].record()
+        graph.replay()
+        gev[k][1].record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = kernels_per_step * K
+    status = int(r.status_dev.item())
+    if status != 0:
+        raise RuntimeError("pair capacity overflow in the timed region (status %d)" % status)
+    step_ms = [a.elapsed_time(b) for a, b in gev]
     t_total = sum(step_ms) / 1000.0
     if world > 1:
         t = torch.tensor([t_total], device=dev, dtype=torch.float64)
@@ -486,6 +517,9 @@ def main():
                        "launch": ("persistent %d CTAs, list-length queue" % args.persistent
                                   if args.persistent else "one CTA per 16x16 tile"),
                        "l2": "flushed (256 MB write) before every timed step",
+                       "timed_form": "whole step captured in one CUDA graph, replayed",
+                       "eager_ms_per_step": eager_ms,
+                       "kernels_per_step": kernels_per_step,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "phases_ms": phase,
             "variants": variants,
