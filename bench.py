@@ -70,6 +70,14 @@ def parse():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the comparison of launch forms and staging precisions")
     ap.add_argument("--ppt", type=int, default=0, help="pixels per thread of the blending kernels")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use --ppt/--persistent as given instead of the autotuned launch form")
+    ap.add_argument("--sweep", action="store_true",
+                    help="list-length sweep (cfg4): one JSON line per scale/opacity point")
+    ap.add_argument("--train", type=int, default=0,
+                    help="run the synthetic training loop (cfg5 form) for this many iterations")
+    ap.add_argument("--train-size", default="960x540", help="training view size WxH")
+    ap.add_argument("--train-n", type=int, default=3_000_000, help="Gaussians in the training scene")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-band-rows", type=int, default=0,
                     help="tile rows of view 0 the CPU oracle sample renders (0 = the whole view)")
@@ -237,6 +245,121 @@ def traffic_from_profiles(kernel):
     return ent.get("bytes_per_launch")
 
 
+def run_sweep(args, dev):
+    """cfg4: the 10k-Gaussian 256x256 scene with scales x 0.5^k and the
+    opacity-logit mean varied; per point the pair count, the mean list
+    length per tile, evaluated and blended entries per pixel, and the fwd+bwd
+    time and throughput (CUDA graph replay, L2 flushed)."""
+    import torch
+    from paper_2603_09277_gb300 import scenes
+    from paper_2603_09277_gb300.rasterize import Rasterizer, scene_to_device, targets_to_device
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    for k in range(-2, 5):
+        for om in (-2.0, 0.0, 2.0, 4.0):
+            scene, cams, targets, prm = scenes.config4(k=k, opacity_mean=om)
+            N = scene["means"].shape[0]
+            p = scene_to_device(scene, dev)
+            tgt = targets_to_device(targets, dev)
+            r = Rasterizer(cams, prm, N, device=dev)
+            for _ in range(2):
+                r.step(p, tgt, scenes.GAMMA, sync=True)
+                r.render_fwd(stats=True)
+            torch.cuda.synchronize()
+            nb, ne = int(r.stats[0].item()), int(r.stats[1].item())
+            g = torch.cuda.CUDAGraph()
+            cs = torch.cuda.Stream()
+            cs.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(cs):
+                with torch.cuda.graph(g, stream=cs):
+                    r.step(p, tgt, scenes.GAMMA, sync=False)
+            torch.cuda.current_stream().wait_stream(cs)
+            g.replay()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ms = []
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                a.record()
+                g.replay()
+                b.record()
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            pix = cams[0]["width"] * cams[0]["height"]
+            m = float(np.mean(ms))
+            print(json.dumps({"sweep": "cfg4", "scale_exp_k": k, "opacity_logit_mean": om,
+                              "pairs": r.num_pairs, "mean_list_per_tile": r.num_pairs / r.total_tiles,
+                              "evaluated_per_pixel": ne / pix, "blended_per_pixel": nb / pix,
+                              "ms_per_step": m, "blended_per_s": nb / (m / 1000.0)}), flush=True)
+            del r, g
+            torch.cuda.empty_cache()
+
+
+def run_train(args, dev):
+    """cfg5 training form: a seeded ground-truth Gaussian set renders targets
+    over 32 orbit views; a perturbed copy is fitted with torch Adam through the
+    rasterizer's autograd functions (L1 + gamma entropy, gamma = 0.015), with
+    the scale reset (zeta = 0.2) every 500 iterations.  Logs loss, PSNR and the
+    mean per-tile list length."""
+    import torch
+    from paper_2603_09277_gb300 import gs, scenes
+    from paper_2603_09277_gb300.rasterize import (Rasterizer, l1_entropy_loss, rasterize,
+                                                  scene_to_device)
+    W, H = (int(x) for x in args.train_size.split("x"))
+    n = args.train_n
+    gt_scene, _, _, prm = scenes.config5(seed=2, n=n, width=W, height=H)
+    cams = scenes.orbit_cameras(32, W, H, seed=3)
+    gt = scene_to_device(gt_scene, dev)
+    # targets rendered from the ground-truth set
+    targets = []
+    for c in cams:
+        rr = Rasterizer([c], prm, n, device=dev)
+        rr.preprocess(gt)
+        rr.bin_sort()
+        rr.render_fwd()
+        targets.append(rr.image.clone())
+        del rr
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(4)
+    init = {k: np.array(v, copy=True) if isinstance(v, np.ndarray) else v for k, v in gt_scene.items()}
+    init["means"] = (init["means"] + rng.normal(0, 0.01, init["means"].shape)).astype(np.float32)
+    init["log_scales"] = (init["log_scales"] + rng.normal(0, 0.1, init["log_scales"].shape)).astype(np.float32)
+    init["opacity_logits"] = (init["opacity_logits"] + rng.normal(0, 0.5, n)).astype(np.float32)
+    init["sh"][:, 0] = (init["sh"][:, 0] + rng.normal(0, 0.05, (n, 3))).astype(np.float32)
+    p = scene_to_device(init, dev, requires_grad=True)
+    params = [p[k] for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+    opt = torch.optim.Adam([
+        {"params": [p["means"]], "lr": 1.6e-4},
+        {"params": [p["log_scales"]], "lr": 5e-3},
+        {"params": [p["quats"]], "lr": 1e-3},
+        {"params": [p["opacity_logits"]], "lr": 5e-2},
+        {"params": [p["sh"]], "lr": 2.5e-3},
+    ], eps=1e-15)
+    rasts = [Rasterizer([c], prm, n, device=dev) for c in cams[:1]]
+    r = rasts[0]
+    t0 = time.perf_counter()
+    order = np.random.default_rng(5).integers(0, len(cams), args.train)
+    for it in range(1, args.train + 1):
+        v = int(order[it - 1])
+        r.cams = [cams[v]]
+        r.cams_c = gs.make_cameras([cams[v]])
+        img, ent = rasterize(p, r)
+        loss = l1_entropy_loss(img, ent, targets[v], r, scenes.GAMMA)
+        opt.zero_grad(set_to_none=True)
+        loss.backward()
+        opt.step()
+        with torch.no_grad():
+            p["quats"].div_(p["quats"].norm(dim=1, keepdim=True).clamp_min(1e-8))
+        if it % 500 == 0:
+            gs.gs_scale_reset(p["log_scales"].data, 0.2)
+        if it % 100 == 0 or it == 1:
+            with torch.no_grad():
+                mse = float(((img - targets[v]) ** 2).mean().item())
+            print(json.dumps({"train_iter": it, "loss": float(loss.item()),
+                              "psnr": -10.0 * math.log10(max(mse, 1e-12)),
+                              "pairs": r.num_pairs, "mean_list_per_tile": r.num_pairs / r.total_tiles,
+                              "seconds": time.perf_counter() - t0}), flush=True)
+
+
 def time_variant(make, p, tgt, gamma, flush, steps, warmup=2):
     """Mean ms per fwd+bwd step (projection .. adjoint) of the rasterizers
     `make()` returns (run back to back: one per view for the per-view form)."""
@@ -290,12 +413,23 @@ def main():
     from paper_2603_09277_gb300 import gs, scenes
     from paper_2603_09277_gb300.rasterize import Rasterizer, scene_to_device, targets_to_device
 
+    if args.sweep:
+        run_sweep(args, dev)
+        return
+    if args.train:
+        run_train(args, dev)
+        return
+
     (scene, cams, targets, prm), wl = workload(args.config, rank)
     N = scene["means"].shape[0]
-    r = Rasterizer(cams, prm, N, attr_dtype=args.attr, device=dev, persistent=args.persistent,
-                   pixels_per_thread=args.ppt)
     p = scene_to_device(scene, dev)
     tgt = targets_to_device(targets, dev)
+    form = {"pixels_per_thread": args.ppt, "persistent": args.persistent}
+    tuned = None
+    if not args.no_autotune:
+        from paper_2603_09277_gb300 import autotune
+        form, tuned = autotune.tune(cams, prm, p, tgt, scenes.GAMMA, attr_dtype=args.attr)
+    r = Rasterizer(cams, prm, N, attr_dtype=args.attr, device=dev, **form)
     ls_work = p["log_scales"].clone()  # the scale reset writes a working copy
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     gamma = scenes.GAMMA
@@ -514,8 +648,11 @@ def main():
             "config": {"workload": wl, "N": N, "views": len(cams), "pairs": P,
                        "blended_pairs": nb_step, "evaluated_pairs": ne_step,
                        "bwd_evaluated_pairs": bwd_eval, "attr_dtype": args.attr,
-                       "launch": ("persistent %d CTAs, list-length queue" % args.persistent
-                                  if args.persistent else "one CTA per 16x16 tile"),
+                       "launch": ("persistent %d CTAs over the list-length queue"
+                                  % form["persistent"] if form["persistent"]
+                                  else "one CTA per 16x16 tile")
+                       + ", %d px/thread" % (form["pixels_per_thread"] or 2),
+                       "autotune_ms": tuned,
                        "l2": "flushed (256 MB write) before every timed step",
                        "timed_form": "whole step captured in one CUDA graph, replayed",
                        "eager_ms_per_step": eager_ms,

@@ -142,19 +142,21 @@ def preprocess(scene, cam, prm):
     return out
 
 
-def build_lists(proj, cam):
+def build_lists(proj, cam, tile_mask=None):
     """Per-tile lists: tile_start [TX*TY+1] int64 and ids [P] int32, each
-    tile's ids sorted by (FP32 depth bits, Gaussian id)."""
+    tile's ids sorted by (FP32 depth bits, Gaussian id).  tile_mask
+    (optional bool [TX*TY]) keeps only the marked tiles' lists."""
     lib = _load()
     TX, TY = tile_grid(cam)
     rect, tiles, depth = proj["rect"], proj["tiles"], proj["depth"]
     N = rect.shape[0]
     ts = np.zeros(TX * TY + 1, np.int64)
+    m = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8).reshape(-1)
     P = lib.ora_build_lists(ctypes.c_int(N), _p(rect), _p(tiles), _p(depth), ctypes.c_int(TX),
-                            ctypes.c_int(TY), _p(ts), ctypes.c_void_p(0))
+                            ctypes.c_int(TY), _p(ts), ctypes.c_void_p(0), _p(m))
     ids = np.zeros(max(P, 1), np.int32)
     lib.ora_build_lists(ctypes.c_int(N), _p(rect), _p(tiles), _p(depth), ctypes.c_int(TX),
-                        ctypes.c_int(TY), _p(ts), _p(ids))
+                        ctypes.c_int(TY), _p(ts), _p(ids), _p(m))
     return ts, ids[:P]
 
 

@@ -371,11 +371,20 @@ static uint32_t float_bits(float f) {
 }
 
 /* Returns the number of (tile, Gaussian) pairs.  With ids != NULL fills
- * tile_start[0..TX*TY] and ids[0..P) (the concatenated per-tile lists). */
+ * tile_start[0..TX*TY] and ids[0..P) (the concatenated per-tile lists).
+ * tile_mask (nullable, TX*TY bytes) keeps only the lists of the marked tiles
+ * (the others are left empty); the returned count is then of kept pairs. */
 long long ora_build_lists(int N, const int* rect, const int* tiles, const float* depth,
-                          int TX, int TY, long long* tile_start, int* ids) {
+                          int TX, int TY, long long* tile_start, int* ids,
+                          const unsigned char* tile_mask) {
     long long P = 0;
-    for (int i = 0; i < N; ++i) P += tiles[i];
+    for (int i = 0; i < N; ++i) {
+        if (tiles[i] <= 0) continue;
+        if (!tile_mask) { P += tiles[i]; continue; }
+        for (int ty = rect[4 * i + 1]; ty < rect[4 * i + 3]; ++ty)
+            for (int tx = rect[4 * i + 0]; tx < rect[4 * i + 2]; ++tx)
+                P += tile_mask[ty * TX + tx] ? 1 : 0;
+    }
     if (!ids) return P;
     pair_t* pr = (pair_t*)malloc(sizeof(pair_t) * (size_t)(P > 0 ? P : 1));
     long long k = 0;
@@ -383,6 +392,7 @@ long long ora_build_lists(int N, const int* rect, const int* tiles, const float*
         if (tiles[i] <= 0) continue;
         for (int ty = rect[4 * i + 1]; ty < rect[4 * i + 3]; ++ty)
             for (int tx = rect[4 * i + 0]; tx < rect[4 * i + 2]; ++tx) {
+                if (tile_mask && !tile_mask[ty * TX + tx]) continue;
                 pr[k].tile = ty * TX + tx;
                 pr[k].dkey = float_bits(depth[i]);
                 pr[k].id = i;

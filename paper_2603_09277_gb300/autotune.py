@@ -1,0 +1,91 @@
+"""Launch-form autotuner for the blending kernels.
+
+Times the candidate launch forms (pixels per thread 1/2/4, one CTA per tile
+or a persistent grid over the list-length-ordered tile queue) on the caller's
+actual workload (a few whole fwd+bwd steps each, L2 flushed between steps),
+and caches the fastest form per workload signature (views and their sizes,
+Gaussian count, staging dtype, device name) in a JSON file under
+paper_2603_09277_gb300/_build/.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import torch
+
+from .rasterize import Rasterizer
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+CANDIDATES = [
+    {"pixels_per_thread": 1, "persistent": 0},
+    {"pixels_per_thread": 2, "persistent": 0},
+    {"pixels_per_thread": 4, "persistent": 0},
+    {"pixels_per_thread": 2, "persistent": 152 * 8},
+    {"pixels_per_thread": 4, "persistent": 152 * 8},
+]
+
+
+def signature(cams, N, attr_dtype):
+    views = ",".join("%dx%d" % (c["width"], c["height"]) for c in cams)
+    return "%s|N=%d|%s|%s" % (views, N, attr_dtype, torch.cuda.get_device_name())
+
+
+def _load():
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(db):
+    os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+    tmp = CACHE + ".%d.tmp" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(db, f, indent=1)
+    os.replace(tmp, CACHE)
+
+
+def time_form(cams, prm, params, target, gamma, form, attr_dtype="f32", steps=5, warmup=2):
+    """Mean ms of a whole eager fwd+bwd step with the given launch form."""
+    N = params["means"].shape[0]
+    r = Rasterizer(cams, prm, N, attr_dtype=attr_dtype, **form)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=r.device)
+    for _ in range(warmup):
+        r.step(params, target, gamma, sync=True)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        a.record()
+        r.step(params, target, gamma, sync=False)
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    if int(r.status_dev.item()) != 0:
+        raise RuntimeError("pair capacity overflow while tuning")
+    return sum(ms) / len(ms)
+
+
+def tune(cams, prm, params, target, gamma, attr_dtype="f32", force=False, steps=5):
+    """Returns (best form dict, {form: ms}) and caches the choice."""
+    key = signature(cams, params["means"].shape[0], attr_dtype)
+    db = _load()
+    if not force and key in db:
+        return db[key]["best"], db[key]["ms"]
+    times = {}
+    for form in CANDIDATES:
+        name = "ppt%d_%s" % (form["pixels_per_thread"],
+                             "persistent" if form["persistent"] else "per_tile")
+        times[name] = time_form(cams, prm, params, target, gamma, form, attr_dtype, steps)
+        torch.cuda.empty_cache()
+    best_name = min(times, key=times.get)
+    best = CANDIDATES[[("ppt%d_%s" % (f["pixels_per_thread"],
+                                       "persistent" if f["persistent"] else "per_tile"))
+                       for f in CANDIDATES].index(best_name)]
+    db[key] = {"best": best, "ms": times, "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
+    _store(db)
+    return best, times

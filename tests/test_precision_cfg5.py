@@ -1,0 +1,91 @@
+"""Mixed-precision staging at full size (3,000,000 Gaussians, one 1920x1080
+view): render records in FP32, FP16 and BF16 (the 2D mean always FP32;
+exponent, transmittance and accumulation FP32), each against the FP64
+oracle on sampled pixels and sampled Gaussians.  FP32 must meet the parity
+bar; the 16-bit forms have no bar (their error per output is the measured
+quantity) and only sanity bounds.  With GS_REPORT_DIR set the table is
+written there as precision_cfg5.json."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2603_09277_gb300 import scenes
+
+from parity_util import (GRAD_TOL, IMG_TOL, gaussian_exclusion, last_ids_gpu, last_ids_oracle,
+                         pixel_exclusion, rel_norm_err, run_gpu)
+
+pytestmark = pytest.mark.gpu
+
+
+def test_cfg5_staging_precision_error_per_output():
+    scene, cams, targets, prm = scenes.config5()
+    cam = cams[0]
+    W, H = cam["width"], cam["height"]
+    N = scene["means"].shape[0]
+    TX, TY = oracle.tile_grid(cam)
+    proj = oracle.preprocess(scene, cam, prm)
+    rng = np.random.default_rng(0)
+    # sampled Gaussians (visible, not flagged, small rect) and random tiles
+    cand = np.nonzero((proj["tiles"] > 0) & (proj["tiles"] <= 4) & (proj["boundary"] == 0))[0]
+    pick = rng.choice(cand, 16, replace=False)
+    tmask = np.zeros((TY, TX), bool)
+    for i in pick:
+        x0, y0, x1, y1 = proj["rect"][i]
+        tmask[y0:y1, x0:x1] = True
+    gmask_tiles = tmask.copy()
+    tmask.reshape(-1)[rng.choice(TX * TY, 48, replace=False)] = True
+    lists = oracle.build_lists(proj, cam, tile_mask=tmask)
+    pmask = tmask[np.arange(H)[:, None] // 16, np.arange(W)[None, :] // 16]
+    gpix = gmask_tiles[np.arange(H)[:, None] // 16, np.arange(W)[None, :] // 16]
+    fwd = oracle.render_fwd(proj, lists, cam, prm, mask=pmask)
+    M = W * H
+    dC = np.where(fwd["image"] - targets[0] > 0, 1.0, -1.0) / (3 * M)
+    dC[~pmask] = 0.0
+    dH = np.where(pmask, scenes.GAMMA / M, 0.0)
+    g9 = oracle.render_bwd(proj, lists, cam, prm, dC, dH, mask=gpix)
+    gm = np.zeros(N, np.uint8)
+    gm[pick] = 1
+    og = oracle.preprocess_bwd(scene, cam, prm, g9, gmask=gm)
+    view = {"proj": proj, "lists": lists, "fwd": fwd}
+    bad = pixel_exclusion(view, cam) | ~pmask
+    ok = ~bad.reshape(-1)
+    badg = gaussian_exclusion(view, cam, pixel_exclusion(view, cam) & gpix)
+    use = pick[~badg[pick]]
+    report = {"workload": "cfg5: 3M Gaussians, 1920x1080, SH0", "pixels_checked": int(ok.sum()),
+              "gaussians_checked": int(len(use))}
+    for attr in ("f32", "f16", "bf16"):
+        g = run_gpu(scene, cams, prm, attr=attr, dL_dimage=dC.astype(np.float32),
+                    dL_dentropy=dH.astype(np.float32), keys=False)
+        row = {}
+        for k, o in (("image", fwd["image"].reshape(-1, 3)), ("final_T", fwd["final_T"].reshape(-1)),
+                     ("entropy", fwd["entropy"].reshape(-1))):
+            d = np.abs(g[k] - o).reshape(M, -1).max(1)[ok]
+            row[k] = {"max_abs": float(d.max()), "mean_abs": float(d.mean())}
+        row["last_entry_match"] = float(
+            (last_ids_gpu(g, cams, 0, N)[ok] == last_ids_oracle(view, cam)[ok]).mean())
+        for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+            gg, oo = g["grads"][k][use], og[k][use]
+            if k == "sh":
+                gg, oo = gg[:, :1], oo[:, :1]
+            row["grad_" + k] = rel_norm_err(gg, oo)
+        report[attr] = row
+    out = os.environ.get("GS_REPORT_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, "precision_cfg5.json"), "w") as f:
+            json.dump(report, f, indent=1)
+    print(json.dumps(report))
+    f32 = report["f32"]
+    assert report["pixels_checked"] > 10000 and report["gaussians_checked"] >= 8
+    assert f32["image"]["max_abs"] <= IMG_TOL and f32["final_T"]["max_abs"] <= IMG_TOL
+    assert f32["entropy"]["max_abs"] <= IMG_TOL and f32["last_entry_match"] == 1.0
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        assert f32["grad_" + k] <= GRAD_TOL, k
+    for attr in ("f16", "bf16"):
+        assert report[attr]["image"]["mean_abs"] < 2e-2
+        assert report[attr]["grad_means"] < 0.5
