@@ -144,7 +144,8 @@ class Rasterizer:
             self._alloc_pairs(int(P * 1.25) + 1024)
             if keys:
                 self.sorted_keys = torch.empty(self.capacity, dtype=torch.int64, device=self.device)
-        self.num_pairs = P
+        if P is not None:
+            self.num_pairs = P
         if self.persistent:
             gs.gs_tile_queue(self.tile_ranges, self.total_tiles, self.tile_order, self.queue_ws,
                              stream)

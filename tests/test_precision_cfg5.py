@@ -30,19 +30,26 @@ def test_cfg5_staging_precision_error_per_output():
     TX, TY = oracle.tile_grid(cam)
     proj = oracle.preprocess(scene, cam, prm)
     rng = np.random.default_rng(0)
-    # sampled Gaussians (visible, not flagged, small rect) and random tiles
+    # candidate Gaussians (visible, not flagged, small rect) and random tiles;
+    # the checked Gaussians are the candidates no threshold flip can change
     cand = np.nonzero((proj["tiles"] > 0) & (proj["tiles"] <= 4) & (proj["boundary"] == 0))[0]
-    pick = rng.choice(cand, 16, replace=False)
+    cand = rng.choice(cand, 200, replace=False)
     tmask = np.zeros((TY, TX), bool)
-    for i in pick:
+    for i in cand:
         x0, y0, x1, y1 = proj["rect"][i]
         tmask[y0:y1, x0:x1] = True
-    gmask_tiles = tmask.copy()
     tmask.reshape(-1)[rng.choice(TX * TY, 48, replace=False)] = True
     lists = oracle.build_lists(proj, cam, tile_mask=tmask)
     pmask = tmask[np.arange(H)[:, None] // 16, np.arange(W)[None, :] // 16]
-    gpix = gmask_tiles[np.arange(H)[:, None] // 16, np.arange(W)[None, :] // 16]
     fwd = oracle.render_fwd(proj, lists, cam, prm, mask=pmask)
+    view0 = {"proj": proj, "lists": lists, "fwd": fwd}
+    excl = gaussian_exclusion(view0, cam, pixel_exclusion(view0, cam) & pmask)
+    pick = cand[~excl[cand]][:16]
+    gmask_tiles = np.zeros((TY, TX), bool)
+    for i in pick:
+        x0, y0, x1, y1 = proj["rect"][i]
+        gmask_tiles[y0:y1, x0:x1] = True
+    gpix = gmask_tiles[np.arange(H)[:, None] // 16, np.arange(W)[None, :] // 16]
     M = W * H
     dC = np.where(fwd["image"] - targets[0] > 0, 1.0, -1.0) / (3 * M)
     dC[~pmask] = 0.0
