@@ -34,10 +34,11 @@ def test_cfg5_staging_precision_error_per_output():
     TX, TY = oracle.tile_grid(cam)
     proj = oracle.preprocess(scene, cam, prm)
     rng = np.random.default_rng(0)
-    # candidates: the front-most small, unflagged Gaussians (deeper ones are
-    # rarely reached before T < t_min); sampled tiles: their rects plus 48 random
-    cand = np.nonzero((proj["tiles"] > 0) & (proj["tiles"] <= 9) & (proj["boundary"] == 0))[0]
-    cand = cand[np.argsort(proj["depth"][cand], kind="stable")[:200]]
+    # candidates: the 48 front-most unflagged Gaussians with rects of at most
+    # 6x6 tiles (deeper ones are rarely reached before T < t_min in this dense
+    # scene); sampled tiles: their rects plus 48 random tiles
+    cand = np.nonzero((proj["tiles"] > 0) & (proj["tiles"] <= 36) & (proj["boundary"] == 0))[0]
+    cand = cand[np.argsort(proj["depth"][cand], kind="stable")[:48]]
     tmask = np.zeros((TY, TX), bool)
     for i in cand:
         x0, y0, x1, y1 = proj["rect"][i]
