@@ -21,6 +21,7 @@
 //   dL/dalpha_i = sum_ch g_ch (T_i c_i - S / (1 - alpha_i))
 //               + gH ((-ln w_i - 1) T_i + R / (1 - alpha_i))
 //   S += w_i c_i; R += (ln w_i + 1) w_i    (R starts at (ln T_N+1 + 1) T_N+1)
+//   (only g . S is needed, so it is carried instead of S: g . S += w_i g . c_i)
 //   then dsigma = dalpha g, dd = dalpha alpha (unless clamped),
 //   dconic = dd (-dx^2/2, -dx dy, -dy^2/2), dmean = dd conic (dx, dy).
 // The thread sums the 9 per-Gaussian values over its pixels, the warp sums
@@ -286,7 +287,8 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
   const int lane = tid & 31;
   const TileGeom<PPT> tg = tile_geom<PPT>(ct, tile);
   const uint2 r = a.ranges[tile];
-  float T[PPT], gr[PPT], gg[PPT], gb[PPT], gH[PPT], Sr[PPT], Sg[PPT], Sb[PPT], Rent[PPT];
+  // per pixel: T, dL/dC, dL/dH, gS = dL/dC . S (S = sum_{k>i} w_k c_k) and R
+  float T[PPT], gr[PPT], gg[PPT], gb[PPT], gH[PPT], gS[PPT], Rent[PPT];
   unsigned last[PPT];
   unsigned mylast = 0;
 #pragma unroll
@@ -303,7 +305,7 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
       gb[q] = a.dL_dimage[3 * p + 2];
       if (a.dL_dentropy) gH[q] = a.dL_dentropy[p];
     }
-    Sr[q] = Sg[q] = Sb[q] = 0.f;
+    gS[q] = 0.f;
     Rent[q] = (fast_log2(T[q]) * kLn2 + 1.f) * T[q];
     mylast = max(mylast, last[q]);
   }
@@ -354,15 +356,14 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
           const float Ti = T[q] * iom;
           const float w = alpha * Ti;
           const float lnw = fast_log2(w) * kLn2;
-          float dA = gr[q] * (Ti * g1.z - Sr[q] * iom) + gg[q] * (Ti * g1.w - Sg[q] * iom) +
-                     gb[q] * (Ti * g2.x - Sb[q] * iom);
+          // colour part: dL/dC . (T_i c_i - S / (1 - alpha_i)) = T_i gc - gS / (1 - alpha_i)
+          const float gc = __fmaf_rn(gb[q], g2.x, __fmaf_rn(gg[q], g1.w, gr[q] * g1.z));
+          float dA = __fmaf_rn(Ti, gc, -gS[q] * iom);
           dA += gH[q] * ((-lnw - 1.f) * Ti + Rent[q] * iom);
           gsum[6] += w * gr[q];
           gsum[7] += w * gg[q];
           gsum[8] += w * gb[q];
-          Sr[q] = __fmaf_rn(w, g1.z, Sr[q]);
-          Sg[q] = __fmaf_rn(w, g1.w, Sg[q]);
-          Sb[q] = __fmaf_rn(w, g2.x, Sb[q]);
+          gS[q] = __fmaf_rn(w, gc, gS[q]);  // S += w c  =>  dL/dC . S += w gc
           Rent[q] = __fmaf_rn(lnw + 1.f, w, Rent[q]);
           T[q] = Ti;
           if (araw <= rc.alpha_max) {
