@@ -403,7 +403,7 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
 }
 
 template <int DT, int PPT>
-__global__ void __launch_bounds__(kTilePix / PPT, 4 * PPT) render_bwd_kernel(const CamTable ct,
+__global__ void __launch_bounds__(kTilePix / PPT, PPT == 4 ? 1 : 4 * PPT) render_bwd_kernel(const CamTable ct,
                                                                     const RenderConsts rc,
                                                                     const BwdArgs a,
                                                                     int persistent) {
