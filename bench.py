@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5"])
     ap.add_argument("--attr", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--n", type=int, default=0,
+                    help="override the configuration's Gaussian count (smaller cases for profiling)")
     ap.add_argument("--persistent", type=int, default=0,
                     help="CTAs of the persistent list-length-ordered launch (0 = one CTA per tile)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -86,19 +88,22 @@ def parse():
     return ap.parse_args()
 
 
-def workload(name, seed):
+def workload(name, seed, n=0):
     from paper_2603_09277_gb300 import scenes
+    kw = {"n": n} if n else {}
+    tag = " (N overridden: %d)" % n if n else ""
     if name == "cfg1":
-        return scenes.config1(seed=seed), "cfg1: 10k Gaussians, 256x256, SH0, fwd+bwd L1+entropy"
+        return scenes.config1(seed=seed, **kw), "cfg1: 10k Gaussians, 256x256, SH0, fwd+bwd L1+entropy" + tag
     if name == "cfg2":
-        return scenes.config2(seed=seed), ("cfg2: 1M Gaussians (64 clusters, r=10), SH3, "
-                                           "one 1237x822 view, fwd+bwd L1+entropy")
+        return scenes.config2(seed=seed, **kw), ("cfg2: 1M Gaussians (64 clusters, r=10), SH3, "
+                                                 "one 1237x822 view, fwd+bwd L1+entropy" + tag)
     if name == "cfg3":
-        return scenes.config3(seed=seed), ("cfg3: 3M Gaussians, 8 views {3x309x205, 3x618x411, "
-                                           "2x1237x822}, fwd+bwd L1+entropy")
+        return scenes.config3(seed=seed, **kw), ("cfg3: 3M Gaussians, 8 views {3x309x205, "
+                                                 "3x618x411, 2x1237x822}, fwd+bwd L1+entropy" + tag)
     if name == "cfg4":
-        return scenes.config4(seed=seed), "cfg4: 10k Gaussians, 256x256, k=0"
-    return scenes.config5(seed=seed), "cfg5: 3M Gaussians, 1920x1080, SH0, fwd+bwd L1+entropy"
+        return scenes.config4(seed=seed, **kw), "cfg4: 10k Gaussians, 256x256, k=0" + tag
+    return scenes.config5(seed=seed, **kw), ("cfg5: 3M Gaussians, 1920x1080, SH0, fwd+bwd "
+                                             "L1+entropy" + tag)
 
 
 # ---------------------------------------------------------------------------
@@ -199,7 +204,7 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    (scene, cams, targets, prm), wl = workload(args.config, 0)
+    (scene, cams, targets, prm), wl = workload(args.config, 0, args.n)
     from paper_2603_09277_gb300 import scenes
     for _ in range(args.warmup):
         oracle_sample(scene, cams, targets, prm, scenes.GAMMA, args.ref_band_rows)
@@ -420,7 +425,7 @@ def main():
         run_train(args, dev)
         return
 
-    (scene, cams, targets, prm), wl = workload(args.config, rank)
+    (scene, cams, targets, prm), wl = workload(args.config, rank, args.n)
     N = scene["means"].shape[0]
     p = scene_to_device(scene, dev)
     tgt = targets_to_device(targets, dev)
