@@ -390,22 +390,23 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
   const long long end = min(P, start + kDupPairs);
   const long long n = *n_vis;
   const long long j0 = block_row[blockIdx.x];
-  if (threadIdx.x == 0) s_nrows = 0;
-  __syncthreads();
-  // rows j0 .. j0 + nrows - 1 overlap [start, end); at most kDupPairs of them
-  for (int i = threadIdx.x; i < kDupPairs; i += kDupThreads) {
+  // rows j0 .. j1 overlap [start, end): j1 is the row holding the next block's
+  // first pair (it belongs here only if it starts before `end`), or the last row
+  const long long j1 = (end < P) ? (long long)block_row[blockIdx.x + 1] : n - 1;
+  const int cand = (int)min((long long)kDupPairs, j1 - j0 + 1);
+  for (int i = threadIdx.x; i < cand; i += kDupThreads) {
     const long long j = j0 + i;
-    if (j < n) {
-      const unsigned long long o = offsets[j];
-      if ((long long)o < end) {
-        const unsigned row = rows[j];
-        s_off[i] = (long long)o - start;  // negative for a row that began before the block
-        s_rect[i] = reinterpret_cast<const int4*>(rect)[row];
-        s_row[i] = row;
-        atomicMax(&s_nrows, i + 1);
-      }
+    const unsigned long long o = offsets[j];
+    if ((long long)o < end) {
+      const unsigned row = rows[j];
+      s_off[i] = (long long)o - start;  // negative for a row that began before the block
+      s_rect[i] = reinterpret_cast<const int4*>(rect)[row];
+      s_row[i] = row;
     }
   }
+  if (threadIdx.x == 0)
+    s_nrows = (j1 - j0 + 1 <= kDupPairs && (long long)offsets[j1] < end) ? (int)(j1 - j0 + 1)
+                                                                         : (int)(j1 - j0);
   __syncthreads();
   const int nr = s_nrows;
   for (int t = threadIdx.x; t < (int)(end - start); t += kDupThreads) {
