@@ -403,30 +403,16 @@ __global__ void __launch_bounds__(256) preprocess_kernel(
 // ---------------------------------------------------------------------------
 // Adjoint of the projection.  grad2d rows: dL/d(mx, my, a, b, c, sigma, r, g, b).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) preprocess_bwd_kernel(
-    const float* __restrict__ means, const float* __restrict__ log_scales,
+// Adjoint of one Gaussian (visible in at least one view); the outputs arrive
+// zeroed.
+__device__ __forceinline__ void adjoint_one(
+    int g, const float* __restrict__ means, const float* __restrict__ log_scales,
     const float* __restrict__ quats, const float* __restrict__ opacity_logits,
-    const float* __restrict__ sh, int N, const CamTable ct, float dilation, float near_z,
-    int sh_deg, int sh_stride, const unsigned* __restrict__ tiles_touched,
-    const float* __restrict__ grad2d, float* __restrict__ g_means, float* __restrict__ g_ls,
-    float* __restrict__ g_quats, float* __restrict__ g_opac, float* __restrict__ g_sh) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= N) return;
-  const int K = sh_count(sh_deg);  // g_sh arrives zeroed (memset by the caller)
-  bool any = false;
-  for (int v = 0; v < ct.V; ++v) any |= tiles_touched[(long long)v * N + g] != 0u;
-  if (!any) {
-    g_means[3ll * g] = 0.f;
-    g_means[3ll * g + 1] = 0.f;
-    g_means[3ll * g + 2] = 0.f;
-    g_ls[3ll * g] = 0.f;
-    g_ls[3ll * g + 1] = 0.f;
-    g_ls[3ll * g + 2] = 0.f;
-    reinterpret_cast<float4*>(g_quats)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-    g_opac[g] = 0.f;
-    return;
-  }
-
+    const float* __restrict__ sh, int N, const CamTable& ct, float dilation, int sh_deg,
+    int sh_stride, const unsigned* __restrict__ tiles_touched, const float* __restrict__ grad2d,
+    float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
+    float* __restrict__ g_opac, float* __restrict__ g_sh) {
+  const int K = sh_count(sh_deg);
   Activated a = activate(means, log_scales, quats, opacity_logits, g);
   float gm[3] = {0.f, 0.f, 0.f};
   float gls[3] = {0.f, 0.f, 0.f};  // dL/d log-scale, summed over views
@@ -580,6 +566,73 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(
   reinterpret_cast<float4*>(g_quats)[g] = gq;
 }
 
+// The adjoint over Gaussians, compacted per block: each CTA owns 2048
+// consecutive Gaussians, zeroes the gradients of those no view sees, lists
+// the others in shared memory (ascending), then its threads take the listed
+// Gaussians densely, so a scene where most Gaussians are culled does not run
+// the long adjoint on warps with one or two live lanes.
+constexpr int kAdjThreads = 256;
+constexpr int kAdjPer = 8;
+constexpr int kAdjSpan = kAdjThreads * kAdjPer;
+constexpr int kAdjWarps = kAdjThreads / 32;
+
+__global__ void __launch_bounds__(kAdjThreads) preprocess_bwd_kernel(
+    const float* __restrict__ means, const float* __restrict__ log_scales,
+    const float* __restrict__ quats, const float* __restrict__ opacity_logits,
+    const float* __restrict__ sh, int N, const CamTable ct, float dilation, int sh_deg,
+    int sh_stride, const unsigned* __restrict__ tiles_touched, const float* __restrict__ grad2d,
+    float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
+    float* __restrict__ g_opac, float* __restrict__ g_sh) {
+  __shared__ int s_list[kAdjSpan];
+  __shared__ int s_off[kAdjPer * kAdjWarps + 1];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int base = blockIdx.x * kAdjSpan;
+  unsigned ball[kAdjPer];
+  // pass k covers Gaussians base + k*256 + tid: the (k, warp, lane) order is
+  // ascending in g
+#pragma unroll
+  for (int k = 0; k < kAdjPer; ++k) {
+    const int g = base + k * kAdjThreads + tid;
+    bool any = false;
+    if (g < N) {
+      for (int v = 0; v < ct.V; ++v) any |= tiles_touched[(long long)v * N + g] != 0u;
+      if (!any) {  // g_sh arrives zeroed (memset by the caller)
+        g_means[3ll * g] = 0.f;
+        g_means[3ll * g + 1] = 0.f;
+        g_means[3ll * g + 2] = 0.f;
+        g_ls[3ll * g] = 0.f;
+        g_ls[3ll * g + 1] = 0.f;
+        g_ls[3ll * g + 2] = 0.f;
+        reinterpret_cast<float4*>(g_quats)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        g_opac[g] = 0.f;
+      }
+    }
+    ball[k] = __ballot_sync(0xffffffffu, any);
+    if (lane == 0) s_off[k * kAdjWarps + w] = __popc(ball[k]);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int i = 0; i < kAdjPer * kAdjWarps; ++i) {
+      const int c = s_off[i];
+      s_off[i] = run;
+      run += c;
+    }
+    s_off[kAdjPer * kAdjWarps] = run;
+  }
+  __syncthreads();
+  const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+  for (int k = 0; k < kAdjPer; ++k)
+    if (ball[k] & (1u << lane))
+      s_list[s_off[k * kAdjWarps + w] + __popc(ball[k] & below)] = base + k * kAdjThreads + tid;
+  __syncthreads();
+  const int total = s_off[kAdjPer * kAdjWarps];
+  for (int i = tid; i < total; i += kAdjThreads)
+    adjoint_one(s_list[i], means, log_scales, quats, opacity_logits, sh, N, ct, dilation, sh_deg,
+                sh_stride, tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh);
+}
+
 }  // namespace
 
 int launch_preprocess(const float* means, const float* log_scales, const float* quats,
@@ -613,9 +666,9 @@ int launch_preprocess_bwd(const float* means, const float* log_scales, const flo
                           float* g_means, float* g_ls, float* g_quats, float* g_opac, float* g_sh,
                           cudaStream_t st) {
   if (N == 0) return GS_OK;
-  preprocess_bwd_kernel<<<(N + 255) / 256, 256, 0, st>>>(
-      means, log_scales, quats, opacity_logits, sh, N, ct, prm->dilation, prm->near_z,
-      prm->sh_degree, prm->sh_stride, tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh);
+  preprocess_bwd_kernel<<<(N + kAdjSpan - 1) / kAdjSpan, kAdjThreads, 0, st>>>(
+      means, log_scales, quats, opacity_logits, sh, N, ct, prm->dilation, prm->sh_degree,
+      prm->sh_stride, tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh);
   count_launches(1);
   return check_launch();
 }
