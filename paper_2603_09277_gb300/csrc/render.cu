@@ -53,6 +53,8 @@ struct TileGeom {
   float rx;         // pixel-centre x relative to the tile origin
   float ry0;        // first pixel-centre y relative to the tile origin
   unsigned inside;  // bit k: pixel k lies in the image
+  float xmax;       // largest pixel-centre x of the tile inside the image (relative)
+  unsigned rows;    // bit r: tile row r lies in the image
 };
 
 template <int PPT>
@@ -75,7 +77,63 @@ __device__ __forceinline__ TileGeom<PPT> tile_geom(const CamTable& ct, int tile)
 #pragma unroll
   for (int k = 0; k < PPT; ++k)
     if (px < c.W && py0 + k < c.H) g.inside |= 1u << k;
+  g.xmax = (float)(min(kTile, c.W - tx * kTile) - 1) + 0.5f;
+  const int nrow = min(kTile, c.H - ty * kTile);
+  g.rows = (1u << nrow) - 1u;
   return g;
+}
+
+// Rows of the tile (bit r: pixel centres at tile-relative y = r + 0.5) in
+// which some pixel centre with x in [0.5, xmax] may pass the alpha_min test.
+// A pixel passes when e = L2S - p^2 - q^2 >= log2(alpha_min), that is when
+// p^2 + q^2 <= rho2 = L2S - log2(alpha_min).  Along one row p^2 + q^2 is a
+// convex quadratic in x; its least value over the segment is taken at the
+// stationary point clamped to the segment.  The limit is widened by a bound
+// on the FP32 rounding of this test and of the per-pixel exponent (32 times
+// the first-order estimate), so a row left out holds no pixel the per-pixel
+// test would blend, and skipping it leaves every output unchanged.
+__device__ __forceinline__ unsigned splat_rows(float mx, float my, float f11, float f21, float f22,
+                                               float L2S, float log2_amin, float xmax,
+                                               unsigned rows) {
+  const float rho2 = L2S - log2_amin;
+  if (!(rho2 >= 0.f)) return 0u;  // e <= L2S < log2(alpha_min) everywhere
+  const float rho = sqrtf(rho2);
+  const float x0 = 0.5f - mx, x1 = xmax - mx;
+  const float X =
+      (fabsf(f11) + fabsf(f21)) * (16.f + fabsf(mx)) + fabsf(f22) * (16.f + fabsf(my)) + rho;
+  const float lim = rho2 + 0x1p-18f * (rho * X + rho2 + 8.f);
+  const float a = __fmaf_rn(f11, f11, f21 * f21);
+  const float k = -f21 * f22 / a;  // stationary x of row dy is k dy
+  unsigned m = 0u;
+#pragma unroll 4
+  for (int r = 0; r < kTile; ++r) {
+    const float dy = ((float)r + 0.5f) - my;
+    const float dx = fminf(fmaxf(k * dy, x0), x1);
+    const float pv = f11 * dx;
+    const float qv = __fmaf_rn(f21, dx, f22 * dy);
+    if (__fmaf_rn(pv, pv, qv * qv) <= lim) m |= 1u << r;
+  }
+  return m & rows;
+}
+
+// Builds the warp's list of staged entries (ascending) whose rows mask meets
+// the warp's rows; returns its length.
+template <int PPT>
+__device__ __forceinline__ int warp_entries(const unsigned short* s_rows, unsigned char* list,
+                                            int cnt, int lane, int warp) {
+  constexpr unsigned kBand = (1u << (2 * PPT)) - 1u;
+  const unsigned band = kBand << (warp * 2 * PPT);
+  const unsigned below = (1u << lane) - 1u;
+  int n = 0;
+  for (int c = 0; c < cnt; c += 32) {
+    const int j = c + lane;
+    const bool hit = j < cnt && (s_rows[j] & band);
+    const unsigned b = __ballot_sync(kFull, hit);
+    if (hit) list[n + __popc(b & below)] = (unsigned char)j;
+    n += __popc(b);
+  }
+  __syncwarp();
+  return n;
 }
 
 struct FwdArgs {
@@ -96,14 +154,18 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
                                          const FwdArgs& a, int tile, unsigned long long& n_bl,
                                          unsigned long long& n_ev) {
   constexpr int NT = TileGeom<PPT>::kThreads;
+  constexpr int NW = NT / 32;
   __shared__ float4 s0[kBatch];
   __shared__ float4 s1[kBatch];
   __shared__ float s2[kBatch];
-  const int tid = threadIdx.x;
+  __shared__ unsigned short s_rows[kBatch];
+  __shared__ unsigned char s_list[NW][kBatch];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const TileGeom<PPT> tg = tile_geom<PPT>(ct, tile);
   const uint2 r = a.ranges[tile];
   float T[PPT], cr[PPT], cg[PPT], cb[PPT], swl[PPT];
   unsigned last[PPT];
+  unsigned stop[PPT];         // entries the definition tests (statistics only)
   unsigned live = tg.inside;  // bit k: pixel k still walking
   float ry[PPT];              // pixel-centre y relative to the tile; kFar once finished
 #pragma unroll
@@ -111,6 +173,7 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
     T[k] = 1.f;
     cr[k] = cg[k] = cb[k] = swl[k] = 0.f;
     last[k] = 0u;
+    stop[k] = r.y - r.x;
     ry[k] = (live & (1u << k)) ? tg.ry0 + (float)k : kFar;
   }
   unsigned nb = 0, ne = 0;
@@ -124,11 +187,18 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
         s0[j] = make_float4(m.x, m.y, s.f11, s.f21);
         s1[j] = make_float4(s.f22, s.L2S, s.R, s.G);
         s2[j] = s.B;
+        s_rows[j] = (unsigned short)splat_rows(m.x, m.y, s.f11, s.f21, s.f22, s.L2S,
+                                               rc.log2_alpha_min, tg.xmax, tg.rows);
       }
     }
     __syncthreads();
     const int cnt = (int)min((unsigned)kBatch, r.y - base);
-    for (int k = 0; k < cnt && live; ++k) {
+    // only the entries that may reach a pixel of this warp's rows
+    const int n = __any_sync(kFull, live != 0u)
+                      ? warp_entries<PPT>(s_rows, s_list[warp], cnt, lane, warp)
+                      : 0;
+    for (int i = 0; i < n && live; ++i) {
+      const int k = s_list[warp][i];
       const float4 g0 = s0[k];
       const float4 g1 = s1[k];
       const SplatColumn col = splat_column(g0.z, g0.w, g1.y, tg.rx - g0.x);
@@ -140,7 +210,6 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
         e[q] = splat_row(col, g1.x, ry[q] - g0.y, qq);
         emax = fmaxf(emax, e[q]);
       }
-      if (STATS) ne += __popc(live);
       if (emax < rc.log2_alpha_min) continue;  // no pixel of this thread is reached
 #pragma unroll
       for (int q = 0; q < PPT; ++q) {
@@ -150,6 +219,7 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
         if (test_T < rc.t_min) {
           live &= ~(1u << q);
           ry[q] = kFar;  // finished pixels evaluate to e = -inf from here on
+          if (STATS) stop[q] = base - r.x + k + 1;
           continue;
         }
         const float w = alpha * T[q];
@@ -173,6 +243,7 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
     a.final_T[p] = T[q];
     a.last_idx[p] = last[q];
     if (a.entropy) a.entropy[p] = -kLn2 * (swl[q] + T[q] * fast_log2(T[q]));
+    if (STATS) ne += stop[q];
   }
   if (STATS) {
     n_bl += nb;
@@ -281,10 +352,13 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
   __shared__ float4 s1[kBatch];
   __shared__ float2 s2[kBatch];  // (B, 1 / sigma)
   __shared__ unsigned s_row[kBatch];
-  __shared__ unsigned s_max;
+  __shared__ unsigned short s_rows[kBatch];
   constexpr int NT = TileGeom<PPT>::kThreads;
+  constexpr int NW = NT / 32;
+  __shared__ unsigned char s_list[NW][kBatch];
+  __shared__ unsigned s_max;
   const int tid = threadIdx.x;
-  const int lane = tid & 31;
+  const int lane = tid & 31, warp = tid >> 5;
   const TileGeom<PPT> tg = tile_geom<PPT>(ct, tile);
   const uint2 r = a.ranges[tile];
   // per pixel: T, dL/dC, dL/dH, gS = dL/dC . S (S = sum_{k>i} w_k c_k) and R
@@ -326,9 +400,16 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
       s1[j] = make_float4(s.f22, s.L2S, s.R, s.G);
       s2[j] = make_float2(s.B, 1.f / s.sigma);
       s_row[j] = row;
+      s_rows[j] = (unsigned short)splat_rows(m.x, m.y, s.f11, s.f21, s.f22, s.L2S,
+                                             rc.log2_alpha_min, tg.xmax, tg.rows);
     }
     __syncthreads();
-    for (int k = cnt - 1; k >= 0; --k) {
+    // only the entries that may reach a pixel of this warp's rows, last first
+    const int n = __any_sync(kFull, mylast > start)
+                      ? warp_entries<PPT>(s_rows, s_list[warp], cnt, lane, warp)
+                      : 0;
+    for (int i = n - 1; i >= 0; --i) {
+      const int k = s_list[warp][i];
       const unsigned pos = start + (unsigned)k;  // 0-based list position
       const bool any_here = pos < mylast;
       if (!__any_sync(kFull, any_here)) continue;
