@@ -78,7 +78,7 @@ bool build_cam_table(const gs_camera* cams, int V, const gs_params* prm, CamTabl
   if (!cams || V < 1 || V > GS_MAX_VIEWS) return false;
   memset(ct, 0, sizeof(*ct));
   ct->V = V;
-  long long tiles = 0, pix = 0;
+  long long tiles = 0, pix = 0, sts = 0;
   const float fovc = prm ? prm->fov_clamp : 1.3f;
   for (int v = 0; v < V; ++v) {
     const gs_camera& c = cams[v];
@@ -95,13 +95,18 @@ bool build_cam_table(const gs_camera* cams, int V, const gs_params* prm, CamTabl
     d.W = c.width; d.H = c.height;
     d.TX = (c.width + kTile - 1) / kTile;
     d.TY = (c.height + kTile - 1) / kTile;
+    d.STX = (d.TX + kSuperTile - 1) / kSuperTile;
+    d.STY = (d.TY + kSuperTile - 1) / kSuperTile;
+    d.st_off = (int)sts;
     d.tile_off = (int)tiles;
     d.pix_off = pix;
+    sts += (long long)d.STX * d.STY;
     tiles += (long long)d.TX * d.TY;
     pix += (long long)c.width * c.height;
     if (tiles >= (1ll << 31)) return false;
   }
   ct->total_tiles = (int)tiles;
+  ct->total_st = (int)sts;
   return true;
 }
 

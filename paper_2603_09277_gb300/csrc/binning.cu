@@ -23,6 +23,8 @@
 #include <algorithm>
 #include <mutex>
 
+#include <atomic>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -142,27 +144,84 @@ __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
   }
 }
 
-// Phase 3 (offsets form): out[i] = exclusive prefix of tiles_touched in
-// depth order (rows given by `rows`), for i < n_dev.
-__global__ void __launch_bounds__(kScanThreads) scan_offsets_kernel(
-    const unsigned* __restrict__ tiles_touched, const unsigned* __restrict__ rows,
-    const long long* __restrict__ n_dev, const unsigned long long* __restrict__ block_offsets,
-    unsigned long long* __restrict__ out) {
-  long long n = *n_dev;
-  long long base = (long long)blockIdx.x * kScanTile;
-  long long first = base + (long long)threadIdx.x * kScanItems;
+// ----------------------------------------------------------------------------
+// Per visible row (depth order): its tile rect clamped to the view, the
+// number of pairs it makes (rect area) and the number of super-tiles its
+// rect meets.  Every later stage derives counts from this same clamped rect,
+// so the pair and super-tile counts agree everywhere.
+// ----------------------------------------------------------------------------
+static_assert(kSuperTile == 8, "super-tile masks hold 8x8 tiles");
+
+__device__ __forceinline__ int4 view_rect(const int* __restrict__ rect, unsigned row, int N,
+                                          const CamTable& ct) {
+  int4 r = reinterpret_cast<const int4*>(rect)[row];
+  const CamInfo& c = ct.c[row / (unsigned)N];
+  r.x = max(r.x, 0);
+  r.y = max(r.y, 0);
+  r.z = min(r.z, c.TX);
+  r.w = min(r.w, c.TY);
+  if (r.z <= r.x || r.w <= r.y) r = make_int4(0, 0, 0, 0);
+  return r;
+}
+
+// Super-tile span [x0, x1) x [y0, y1) of a non-empty tile rect.
+__device__ __forceinline__ int4 st_span(const int4 r) {
+  return make_int4(r.x >> 3, r.y >> 3, ((r.z - 1) >> 3) + 1, ((r.w - 1) >> 3) + 1);
+}
+
+__device__ __forceinline__ unsigned st_count(const int4 r) {
+  if (r.z <= r.x) return 0u;
+  const int4 q = st_span(r);
+  return (unsigned)((q.z - q.x) * (q.w - q.y));
+}
+
+// Gathers the clamped rect of every depth-ordered row (so later stages read
+// them in order) and forms per-block sums of the super-tile counts and of
+// the pair counts.
+__global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
+    const unsigned* __restrict__ rows, const long long* __restrict__ n_dev,
+    const int* __restrict__ rect, int N, const CamTable ct, int4* __restrict__ rect_sorted,
+    unsigned long long* __restrict__ sums_q, unsigned long long* __restrict__ sums_p) {
+  const long long n = *n_dev;
+  const long long base = (long long)blockIdx.x * kScanTile;
+  unsigned long long q = 0, pp = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    const long long i = base + (long long)k * kScanThreads + threadIdx.x;
+    if (i < n) {
+      const int4 r = view_rect(rect, rows[i], N, ct);
+      rect_sorted[i] = r;
+      q += st_count(r);
+      pp += (unsigned long long)((r.z - r.x) * (r.w - r.y));
+    }
+  }
+  unsigned long long tq, tp;
+  block_excl_scan(q, &tq);
+  block_excl_scan(pp, &tp);
+  if (threadIdx.x == 0) {
+    sums_q[blockIdx.x] = tq;
+    sums_p[blockIdx.x] = tp;
+  }
+}
+
+// out[i] = exclusive prefix of the super-tile counts in depth order.
+__global__ void __launch_bounds__(kScanThreads) row_offsets_kernel(
+    const int4* __restrict__ rect_sorted, const long long* __restrict__ n_dev,
+    const unsigned long long* __restrict__ block_offsets, unsigned long long* __restrict__ out) {
+  const long long n = *n_dev;
+  const long long base = (long long)blockIdx.x * kScanTile;
+  const long long first = base + (long long)threadIdx.x * kScanItems;
   if (base >= n) return;
-  unsigned long long s = 0;
+  unsigned long long sum = 0;
   unsigned loc[kScanItems];
   for (int k = 0; k < kScanItems; ++k) {
-    long long i = first + k;
-    loc[k] = i < n ? tiles_touched[rows[i]] : 0u;
-    s += loc[k];
+    const long long i = first + k;
+    loc[k] = i < n ? st_count(rect_sorted[i]) : 0u;
+    sum += loc[k];
   }
   unsigned long long tot;
-  unsigned long long off = block_excl_scan(s, &tot) + block_offsets[blockIdx.x];
+  unsigned long long off = block_excl_scan(sum, &tot) + block_offsets[blockIdx.x];
   for (int k = 0; k < kScanItems; ++k) {
-    long long i = first + k;
+    const long long i = first + k;
     if (i < n) out[i] = off;
     off += loc[k];
   }
@@ -186,7 +245,7 @@ __device__ __forceinline__ long long radix_chunk(long long n, int nblocks) {
 
 __global__ void __launch_bounds__(kRadixThreads) radix_upsweep_kernel(
     const unsigned* __restrict__ keys, const long long* __restrict__ n_dev, int shift,
-    unsigned* __restrict__ hist /* [256][nblocks] */) {
+    unsigned dmask, unsigned* __restrict__ hist /* [256][nblocks] */) {
   __shared__ unsigned s_h[kRadixWarps][kRadixBins];
   const int w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kRadixWarps * kRadixBins; i += kRadixThreads)
@@ -196,9 +255,17 @@ __global__ void __launch_bounds__(kRadixThreads) radix_upsweep_kernel(
   long long chunk = radix_chunk(n, gridDim.x);
   long long b0 = (long long)blockIdx.x * chunk;
   long long b1 = min(n, b0 + chunk);
-  for (long long i = b0 + threadIdx.x; i < b1; i += kRadixThreads) {
-    unsigned d = (keys[i] >> shift) & 0xffu;
-    atomicAdd(&s_h[w][d], 1u);
+  // kRadixIpt loads in flight per thread
+  for (long long t0 = b0; t0 < b1; t0 += kRadixTile) {
+    unsigned kk[kRadixIpt];
+#pragma unroll
+    for (int i = 0; i < kRadixIpt; ++i) {
+      const long long j = t0 + i * kRadixThreads + threadIdx.x;
+      kk[i] = j < b1 ? keys[j] : 0xffffffffu;
+    }
+#pragma unroll
+    for (int i = 0; i < kRadixIpt; ++i)
+      if (t0 + i * kRadixThreads + threadIdx.x < b1) atomicAdd(&s_h[w][(kk[i] >> shift) & dmask], 1u);
   }
   __syncthreads();
   for (int d = threadIdx.x; d < kRadixBins; d += kRadixThreads) {
@@ -233,15 +300,17 @@ __global__ void __launch_bounds__(kScanThreads) radix_scan_kernel(unsigned* __re
   if (threadIdx.x == 0) totals[blockIdx.x] = (unsigned)tot;
 }
 
-// Scatter of one radix pass.  Per 2048-item tile: digits ranked within each
-// warp from bit ballots (stable within the tile), the tile is reordered by digit in shared
+// Scatter of one radix pass (digit = (key >> shift) & dmask, at most 8
+// bits).  Per 2048-item tile: digits ranked within each warp from bit
+// ballots (stable within the tile), the tile is reordered by digit in shared
 // memory, then written out so that consecutive threads store consecutive
 // addresses of one digit's run (coalesced), and each digit's running global
-// offset advances by the tile's count.
-__global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
+// offset advances by the tile's count.  The next tile's keys and values are
+// loaded into registers while the current one is ranked and written.
+__global__ void __launch_bounds__(kRadixThreads, 3) radix_downsweep_kernel(
     const unsigned* __restrict__ keys_in, const unsigned* __restrict__ vals_in,
     unsigned* __restrict__ keys_out, unsigned* __restrict__ vals_out,
-    const long long* __restrict__ n_dev, int shift, const unsigned* __restrict__ offsets,
+    const long long* __restrict__ n_dev, int shift, int dbits, const unsigned* __restrict__ offsets,
     const unsigned* __restrict__ totals) {
   __shared__ unsigned s_wc[kRadixWarps][kRadixBins + 1];  // per-warp digit counters (+ dummy)
   __shared__ unsigned s_base[kRadixBins];                 // running global offset per digit
@@ -251,6 +320,7 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
   __shared__ unsigned s_val[kRadixTile];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
+  const unsigned dmask = (1u << dbits) - 1u;
   long long n = *n_dev;
   long long chunk = radix_chunk(n, gridDim.x);
   long long b0 = (long long)blockIdx.x * chunk;
@@ -264,16 +334,33 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
   for (int i = threadIdx.x; i < kRadixWarps * (kRadixBins + 1); i += kRadixThreads)
     (&s_wc[0][0])[i] = 0u;
   __syncthreads();
+  unsigned nk[kRadixIpt], nv[kRadixIpt];
+  const int lbase = w * (32 * kRadixIpt) + lane;
+  if (b0 < b1) {
+#pragma unroll
+    for (int i = 0; i < kRadixIpt; ++i) {
+      const long long j = b0 + lbase + i * 32;
+      nk[i] = j < b1 ? keys_in[j] : 0u;
+      nv[i] = j < b1 ? vals_in[j] : 0u;
+    }
+  }
   for (long long t0 = b0; t0 < b1; t0 += kRadixTile) {
     const int cnt = (int)min((long long)kRadixTile, b1 - t0);
     unsigned k[kRadixIpt], v[kRadixIpt], dg[kRadixIpt], loc[kRadixIpt];
 #pragma unroll
     for (int i = 0; i < kRadixIpt; ++i) {
-      const int li = w * (32 * kRadixIpt) + i * 32 + lane;
-      const bool ok = li < cnt;
-      k[i] = ok ? keys_in[t0 + li] : 0u;
-      v[i] = ok ? vals_in[t0 + li] : 0u;
-      dg[i] = ok ? ((k[i] >> shift) & 0xffu) : (unsigned)kRadixBins;
+      k[i] = nk[i];
+      v[i] = nv[i];
+      dg[i] = lbase + i * 32 < cnt ? ((k[i] >> shift) & dmask) : (unsigned)kRadixBins;
+    }
+    const long long t1 = t0 + kRadixTile;
+    if (t1 < b1) {
+#pragma unroll
+      for (int i = 0; i < kRadixIpt; ++i) {
+        const long long j = t1 + lbase + i * 32;
+        nk[i] = j < b1 ? keys_in[j] : 0u;
+        nv[i] = j < b1 ? vals_in[j] : 0u;
+      }
     }
 #pragma unroll
     for (int i = 0; i < kRadixIpt; ++i) {
@@ -283,9 +370,11 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
       unsigned peers = valid ? vm : ~vm;
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
-        const bool bit = (dg[i] >> b) & 1u;
-        const unsigned m = __ballot_sync(0xffffffffu, bit);
-        peers &= bit ? m : ~m;
+        if (b < dbits) {
+          const bool bit = (dg[i] >> b) & 1u;
+          const unsigned m = __ballot_sync(0xffffffffu, bit);
+          peers &= bit ? m : ~m;
+        }
       }
       unsigned rank = __popc(peers & lt_mask);
       unsigned base = s_wc[w][dg[i]];
@@ -320,7 +409,7 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
     __syncthreads();
     for (int i = threadIdx.x; i < cnt; i += kRadixThreads) {
       const unsigned kk = s_key[i];
-      const unsigned d = (kk >> shift) & 0xffu;
+      const unsigned d = (kk >> shift) & dmask;
       const unsigned pos = s_base[d] + (unsigned)i - s_off[d];
       keys_out[pos] = kk;
       vals_out[pos] = s_val[i];
@@ -337,98 +426,150 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
 }
 
 // ----------------------------------------------------------------------------
-// Pair generation, ranges, capacity check.
+// Capacity check, super-pair generation, per-tile expansion.
 // ----------------------------------------------------------------------------
-__global__ void capacity_check_kernel(const long long* __restrict__ P, long long capacity,
-                                      int* __restrict__ status, long long* __restrict__ p_eff) {
+__global__ void capacity_check_kernel(const long long* __restrict__ P,
+                                      const long long* __restrict__ Q, long long capacity,
+                                      int* __restrict__ status, long long* __restrict__ p_eff,
+                                      long long* __restrict__ q_eff) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     bool over = *P > capacity;
     *status = over ? GS_ERR_CAPACITY : GS_OK;
     *p_eff = over ? 0 : *P;  // on overflow every later stage sees zero pairs
+    *q_eff = over ? 0 : *Q;  // (Q <= P: a super-pair holds at least one pair)
   }
 }
 
-// Pair duplication, load-balanced over pairs.  The depth-sorted visible rows
-// own contiguous pair ranges [offset_j, offset_j + tiles_j).  Pairs are cut
-// into blocks of kDupPairs; mark_block_starts records, for every block, the row
-// that owns its first pair (each block boundary lies in exactly one row), and
-// duplicate_kernel then has each CTA load the descriptors of the rows that
-// overlap its pairs into shared memory and find the row of each of its pairs
-// by binary search there.  Every CTA writes kDupPairs consecutive pairs with
-// coalesced stores, however the tile counts are distributed over the rows.
+// Super-pair duplication, load-balanced over super-pairs.  The depth-sorted
+// visible rows own contiguous ranges [offset_j, offset_j + count_j) of
+// (super-tile, row) items.  Items are cut into blocks of kDupPairs;
+// mark_block_starts records, for every block, the row that owns its first
+// item, and duplicate_kernel has each CTA load the descriptors of the rows
+// overlapping its items into shared memory, mark where each row starts, and
+// find the owner of every item with a block-wide max-scan of those marks.
+// Each thread then walks 4 consecutive items through the owner's super-tile
+// rect and stores them with one 16-byte store per array.
 constexpr int kDupThreads = 256;
 constexpr int kDupPairs = 1024;
+static_assert(kDupPairs == 4 * kDupThreads, "duplicate_kernel stores 4 items per thread");
 
 __global__ void __launch_bounds__(256) mark_block_starts_kernel(
-    const unsigned* __restrict__ rows, const long long* __restrict__ n_vis,
-    const unsigned long long* __restrict__ offsets, const unsigned* __restrict__ tiles_touched,
-    const long long* __restrict__ p_eff, unsigned* __restrict__ block_row) {
+    const int4* __restrict__ rect_sorted, const long long* __restrict__ n_vis,
+    const unsigned long long* __restrict__ offsets, const long long* __restrict__ q_eff,
+    unsigned* __restrict__ block_row) {
   const long long n = *n_vis;
-  if (*p_eff == 0) return;
+  if (*q_eff == 0) return;
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += (long long)gridDim.x * blockDim.x) {
     const unsigned long long o = offsets[j];
-    const unsigned long long c = tiles_touched[rows[j]];
+    const unsigned long long c = st_count(rect_sorted[j]);
     for (unsigned long long b = (o + kDupPairs - 1) / kDupPairs; b * kDupPairs < o + c; ++b)
       block_row[b] = (unsigned)j;
   }
 }
 
 __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
-    const unsigned* __restrict__ rows, const long long* __restrict__ n_vis,
-    const unsigned long long* __restrict__ offsets, const int* __restrict__ rect, int N,
-    const CamTable ct, const long long* __restrict__ p_eff,
-    const unsigned* __restrict__ block_row, unsigned* __restrict__ tkeys,
-    unsigned* __restrict__ tvals) {
-  __shared__ long long s_off[kDupPairs];  // row pair offset relative to the block start
-  __shared__ int4 s_rect[kDupPairs];
-  __shared__ unsigned s_row[kDupPairs];
-  __shared__ int s_nrows;
-  const long long P = *p_eff;
+    const unsigned* __restrict__ rows, const int4* __restrict__ rect_sorted,
+    const long long* __restrict__ n_vis, const unsigned long long* __restrict__ offsets, int N,
+    const CamTable ct, const long long* __restrict__ q_eff,
+    const unsigned* __restrict__ block_row, unsigned* __restrict__ skeys,
+    unsigned* __restrict__ svals, int vec16) {
+  constexpr int kPer = kDupPairs / kDupThreads;  // 4 consecutive items per thread
+  __shared__ int s_off[kDupPairs];     // row item offset relative to the block start
+  __shared__ int4 s_info[kDupPairs];   // (super-tile id of the span origin, span width, STX, row)
+  __shared__ int s_own[kDupPairs];     // slot of the row starting at item t (max-scanned)
+  __shared__ int s_wmax[kDupThreads / 32];
+  const long long Q = *q_eff;
   const long long start = (long long)blockIdx.x * kDupPairs;
-  if (start >= P) return;
-  const long long end = min(P, start + kDupPairs);
+  if (start >= Q) return;
+  const long long end = min(Q, start + kDupPairs);
   const long long n = *n_vis;
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   const long long j0 = block_row[blockIdx.x];
   // rows j0 .. j1 overlap [start, end): j1 is the row holding the next block's
-  // first pair (it belongs here only if it starts before `end`), or the last row
-  const long long j1 = (end < P) ? (long long)block_row[blockIdx.x + 1] : n - 1;
+  // first item (it belongs here only if it starts before `end`), or the last row
+  const long long j1 = (end < Q) ? (long long)block_row[blockIdx.x + 1] : n - 1;
   const int cand = (int)min((long long)kDupPairs, j1 - j0 + 1);
-  for (int i = threadIdx.x; i < cand; i += kDupThreads) {
+  for (int t = tid; t < kDupPairs; t += kDupThreads) s_own[t] = 0;
+  __syncthreads();
+  for (int i = tid; i < cand; i += kDupThreads) {
     const long long j = j0 + i;
-    const unsigned long long o = offsets[j];
-    if ((long long)o < end) {
+    const long long o = (long long)offsets[j];
+    if (o < end) {
       const unsigned row = rows[j];
-      s_off[i] = (long long)o - start;  // negative for a row that began before the block
-      s_rect[i] = reinterpret_cast<const int4*>(rect)[row];
-      s_row[i] = row;
+      const int4 q = st_span(rect_sorted[j]);
+      const CamInfo& c = ct.c[row / (unsigned)N];
+      s_off[i] = (int)(o - start);  // negative for a row that began before the block
+      s_info[i] = make_int4(c.st_off + q.y * c.STX + q.x, q.z - q.x, c.STX, (int)row);
+      // a row with no items shares its start with the next row: the later wins
+      if (o >= start) atomicMax(&s_own[o - start], i);
     }
   }
-  if (threadIdx.x == 0)
-    s_nrows = (j1 - j0 + 1 <= kDupPairs && (long long)offsets[j1] < end) ? (int)(j1 - j0 + 1)
-                                                                         : (int)(j1 - j0);
   __syncthreads();
-  const int nr = s_nrows;
-  for (int t = threadIdx.x; t < (int)(end - start); t += kDupThreads) {
-    int lo = 0, hi = nr - 1;  // last row with s_off <= t
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_off[mid] <= (long long)t) lo = mid; else hi = mid - 1;
+  // owner of item t = the last row starting at or before t: an inclusive
+  // max-scan of the start marks (slot numbers grow with the offset)
+  int own[kPer];
+  int m = 0;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    m = max(m, s_own[tid * kPer + q]);
+    own[q] = m;
+  }
+  int incl = m;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl = max(incl, y);
+  }
+  if (lane == 31) s_wmax[wp] = incl;
+  int before = __shfl_up_sync(0xffffffffu, incl, 1);
+  if (lane == 0) before = 0;
+  __syncthreads();
+  for (int k = 0; k < wp; ++k) before = max(before, s_wmax[k]);
+  const int np = (int)(end - start);
+  unsigned kk[kPer], vv[kPer];
+  int cur = -1, id = 0, x = 0, wdt = 1, stride = 1;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int t = tid * kPer + q;
+    const int slot = max(before, own[q]);
+    if (slot != cur) {
+      // first item of this row in the thread: position within the span
+      const int4 in = s_info[slot];
+      const int k = t - s_off[slot];
+      wdt = max(in.y, 1);
+      stride = in.z;
+      const int ky = k / wdt;
+      x = k - ky * wdt;
+      id = in.x + ky * stride;
+      vv[q] = (unsigned)in.w;
+      cur = slot;
+    } else {
+      vv[q] = vv[q > 0 ? q - 1 : 0];
+      if (++x == wdt) {  // next span row
+        x = 0;
+        id += stride;
+      }
     }
-    const int4 r = s_rect[lo];
-    const unsigned rw = s_row[lo];
-    const int k = (int)((long long)t - s_off[lo]);
-    const int w = r.z - r.x;
-    const CamInfo& c = ct.c[(int)(rw / (unsigned)N)];
-    const int ty = r.y + k / w, tx = r.x + k % w;
-    tkeys[start + t] = (unsigned)(c.tile_off + ty * c.TX + tx);
-    tvals[start + t] = rw;
+    kk[q] = (unsigned)(id + x);
+  }
+  const int t0 = tid * kPer;
+  if (vec16 && t0 + kPer <= np) {  // skeys and svals 16-byte aligned
+    reinterpret_cast<uint4*>(skeys + start)[tid] = make_uint4(kk[0], kk[1], kk[2], kk[3]);
+    reinterpret_cast<uint4*>(svals + start)[tid] = make_uint4(vv[0], vv[1], vv[2], vv[3]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q)
+      if (t0 + q < np) {
+        skeys[start + t0 + q] = kk[q];
+        svals[start + t0 + q] = vv[q];
+      }
   }
 }
 
-// Per-tile [start, end) from the sorted tile ids: each thread reads 4
-// consecutive ids with one 16-byte load (the array is 256-byte aligned) plus
-// its neighbours, and marks where the id changes.
+// Per-key [start, end) from sorted u32 keys: each thread reads 4
+// consecutive keys with one 16-byte load (the array is 256-byte aligned) plus
+// its neighbours, and marks where the key changes.
 __global__ void __launch_bounds__(256) ranges_kernel(const unsigned* __restrict__ tkeys,
                                                      const long long* __restrict__ p_eff,
                                                      unsigned* __restrict__ ranges) {
@@ -458,15 +599,331 @@ __global__ void __launch_bounds__(256) ranges_kernel(const unsigned* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(256) keys64_kernel(const unsigned* __restrict__ tkeys,
-                                                     const unsigned* __restrict__ tvals,
-                                                     const float* __restrict__ depth,
-                                                     const long long* __restrict__ p_eff,
-                                                     unsigned long long* __restrict__ out) {
-  long long P = *p_eff;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
-       i += (long long)gridDim.x * blockDim.x)
-    out[i] = ((unsigned long long)tkeys[i] << 32) | __float_as_uint(depth[tvals[i]]);
+// ----------------------------------------------------------------------------
+// Expansion of the super-tile-sorted rows into per-tile lists.  A super-tile's
+// rows (depth order) are cut into segments of kSeg; per segment and per tile
+// of the super-tile (64), the count of rows covering the tile; per tile, the
+// exclusive scan of those counts over the super-tile's segments; per tile,
+// the list start (scan over all tiles); then every segment writes each of
+// its rows into the lists of the tiles it covers, ranks from warp ballots,
+// so each list keeps the depth order of the rows.
+// ----------------------------------------------------------------------------
+constexpr int kSeg = 1024;
+
+__device__ __forceinline__ int view_of_st(const CamTable& ct, int s) {
+  int v = 0;
+  while (v + 1 < ct.V && ct.c[v + 1].st_off <= s) ++v;
+  return v;
+}
+
+// Segments of every super-tile: seg_first[s] (exclusive scan of
+// ceil(len_s / kSeg)), seg_first[S] = total, seg_st[g] = super-tile of g.
+// One CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) st_segments_kernel(const uint2* __restrict__ st_ranges,
+                                                           int S, unsigned* __restrict__ seg_first,
+                                                           unsigned* __restrict__ seg_st,
+                                                           long long* __restrict__ n_seg) {
+  __shared__ unsigned s_w[32];
+  __shared__ unsigned s_carry;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) s_carry = 0u;
+  __syncthreads();
+  for (int base = 0; base < S; base += 1024) {
+    const int s = base + tid;
+    unsigned cnt = 0u;
+    if (s < S) {
+      const uint2 r = st_ranges[s];
+      cnt = (r.y - r.x + kSeg - 1) / kSeg;
+    }
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      const unsigned t = s_w[lane];
+      unsigned ti = t;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, ti, o);
+        if (lane >= o) ti += y;
+      }
+      s_w[lane] = ti - t;
+    }
+    __syncthreads();
+    if (s < S) seg_first[s] = s_carry + s_w[w] + incl - cnt;
+    __syncthreads();
+    if (tid == 1023) s_carry += s_w[31] + incl;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    seg_first[S] = s_carry;
+    *n_seg = (long long)s_carry;
+  }
+  __syncthreads();
+  for (int s = tid; s < S; s += 1024)
+    for (unsigned g = seg_first[s]; g < seg_first[s + 1]; ++g) seg_st[g] = (unsigned)s;
+}
+
+// Rows [b, e) of segment g of super-tile s, its view and tile origin.
+struct SegInfo {
+  unsigned b, e;
+  int view, ox, oy;
+};
+
+__device__ __forceinline__ SegInfo seg_info(long long g, const uint2* __restrict__ st_ranges,
+                                            const unsigned* __restrict__ seg_first,
+                                            const unsigned* __restrict__ seg_st,
+                                            const CamTable& ct) {
+  SegInfo si;
+  const int s = (int)seg_st[g];
+  const uint2 rg = st_ranges[s];
+  si.b = rg.x + (unsigned)(g - seg_first[s]) * (unsigned)kSeg;
+  si.e = min(rg.y, si.b + (unsigned)kSeg);
+  si.view = view_of_st(ct, s);
+  const CamInfo& c = ct.c[si.view];
+  const int sl = s - c.st_off;
+  si.ox = (sl % c.STX) * kSuperTile;
+  si.oy = (sl / c.STX) * kSuperTile;
+  return si;
+}
+
+// Per segment: each row's rect within the super-tile as a 16-bit descriptor
+// (x0 | x1 << 4 | y0 << 8 | y1 << 12, tile units in 0..8), stored for the
+// expansion, and the count of rows covering each of the 64 tiles (2D
+// difference counts in shared memory, summed at the end).
+__global__ void __launch_bounds__(256) st_count_kernel(
+    const unsigned* __restrict__ sp_rows, const uint2* __restrict__ st_ranges,
+    const unsigned* __restrict__ seg_first, const unsigned* __restrict__ seg_st,
+    const long long* __restrict__ n_seg, const int* __restrict__ rect, int N, const CamTable ct,
+    unsigned* __restrict__ desc, unsigned* __restrict__ hist) {
+  __shared__ int s_d[9 * 9];
+  const long long G = *n_seg;
+  for (long long g = blockIdx.x; g < G; g += gridDim.x) {
+    for (int i = threadIdx.x; i < 81; i += blockDim.x) s_d[i] = 0;
+    __syncthreads();
+    const SegInfo si = seg_info(g, st_ranges, seg_first, seg_st, ct);
+    for (unsigned i = si.b + threadIdx.x; i < si.e; i += blockDim.x) {
+      const int4 r = view_rect(rect, sp_rows[i], N, ct);
+      const int x0 = max(r.x - si.ox, 0), x1 = min(r.z - si.ox, kSuperTile);
+      const int y0 = max(r.y - si.oy, 0), y1 = min(r.w - si.oy, kSuperTile);
+      if (x1 <= x0 || y1 <= y0) {  // no tile here (not produced by consistent inputs)
+        desc[i] = 0u;
+        continue;
+      }
+      desc[i] = (unsigned)(x0 | (x1 << 4) | (y0 << 8) | (y1 << 12));
+      atomicAdd(&s_d[y0 * 9 + x0], 1);
+      atomicAdd(&s_d[y0 * 9 + x1], -1);
+      atomicAdd(&s_d[y1 * 9 + x0], -1);
+      atomicAdd(&s_d[y1 * 9 + x1], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 64) {
+      const int lx = threadIdx.x & 7, ly = threadIdx.x >> 3;
+      int sum = 0;
+      for (int y = 0; y <= ly; ++y)
+        for (int x = 0; x <= lx; ++x) sum += s_d[y * 9 + x];
+      hist[g * 64 + threadIdx.x] = (unsigned)sum;
+    }
+    __syncthreads();
+  }
+}
+
+// One CTA per super-tile, 16 groups x 64 tiles: exclusive scan of every
+// tile's counts over the super-tile's segments (in place), and the tile's
+// total list length.
+__global__ void __launch_bounds__(1024) st_scan_kernel(const unsigned* __restrict__ seg_first,
+                                                       const CamTable ct,
+                                                       unsigned* __restrict__ hist,
+                                                       unsigned* __restrict__ tile_cnt) {
+  __shared__ unsigned s_part[16][64];
+  const int s = blockIdx.x;
+  const int k = threadIdx.x >> 6, bt = threadIdx.x & 63;
+  const unsigned g0 = seg_first[s], L = seg_first[s + 1] - g0;
+  const unsigned per = (L + 15u) / 16u;
+  const unsigned a = min(L, (unsigned)k * per), e = min(L, a + per);
+  unsigned sum = 0u;
+  for (unsigned g = a; g < e; ++g) sum += hist[(long long)(g0 + g) * 64 + bt];
+  s_part[k][bt] = sum;
+  __syncthreads();
+  if (k == 0) {
+    unsigned run = 0u;
+    for (int kk = 0; kk < 16; ++kk) {
+      const unsigned x = s_part[kk][bt];
+      s_part[kk][bt] = run;
+      run += x;
+    }
+    const CamInfo& c = ct.c[view_of_st(ct, s)];
+    const int sl = s - c.st_off;
+    const int tx = (sl % c.STX) * kSuperTile + (bt & 7);
+    const int ty = (sl / c.STX) * kSuperTile + (bt >> 3);
+    if (tx < c.TX && ty < c.TY) tile_cnt[c.tile_off + ty * c.TX + tx] = run;
+  }
+  __syncthreads();
+  unsigned run = s_part[k][bt];
+  for (unsigned g = a; g < e; ++g) {
+    unsigned* h = hist + (long long)(g0 + g) * 64 + bt;
+    const unsigned x = *h;
+    *h = run;
+    run += x;
+  }
+}
+
+// Exclusive scan of the list lengths over all T tiles (one CTA of 1024
+// threads): list starts, and ranges [start, end) ((0, 0) for an empty list).
+__global__ void __launch_bounds__(1024) tile_scan_kernel(const unsigned* __restrict__ tile_cnt,
+                                                         int T, unsigned* __restrict__ tile_start,
+                                                         unsigned* __restrict__ ranges) {
+  __shared__ unsigned s_w[32];
+  __shared__ unsigned s_carry;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) s_carry = 0u;
+  __syncthreads();
+  for (int base = 0; base < T; base += 1024) {
+    const int t = base + tid;
+    const unsigned cnt = t < T ? tile_cnt[t] : 0u;
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      const unsigned x = s_w[lane];
+      unsigned xi = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, xi, o);
+        if (lane >= o) xi += y;
+      }
+      s_w[lane] = xi - x;
+    }
+    __syncthreads();
+    const unsigned start = s_carry + s_w[w] + incl - cnt;
+    if (t < T) {
+      tile_start[t] = start;
+      ranges[2ll * t] = cnt ? start : 0u;
+      ranges[2ll * t + 1] = cnt ? start + cnt : 0u;
+    }
+    __syncthreads();
+    if (tid == 1023) s_carry = start + cnt;
+    __syncthreads();
+  }
+}
+
+// Expansion: per segment, rows in chunks of 256 (one per thread, 8 warps of
+// 32 consecutive rows).  Each warp counts its rows per tile with a 2D
+// difference grid of its own; a prefix over the warps and the running list
+// positions give every warp its first slot per tile; then, per tile some
+// row of the warp covers, a ballot ranks the covering lanes, so every list
+// receives its rows in the segment's (depth) order with coalesced stores.
+__global__ void __launch_bounds__(256) st_emit_kernel(
+    const unsigned* __restrict__ sp_rows, const unsigned* __restrict__ desc,
+    const uint2* __restrict__ st_ranges, const unsigned* __restrict__ seg_first,
+    const unsigned* __restrict__ seg_st, const long long* __restrict__ n_seg,
+    const unsigned* __restrict__ hist, const unsigned* __restrict__ tile_start, const CamTable ct,
+    const float* __restrict__ depth, unsigned* __restrict__ out_vals,
+    unsigned long long* __restrict__ out_keys) {
+  __shared__ unsigned s_run[64];     // next list slot per tile of the super-tile
+  __shared__ int s_d[8][84];         // per-warp 9x9 difference grid, then counts
+  __shared__ unsigned s_pos[8][64];  // per-warp first slot per tile
+  __shared__ int s_tile[64];         // global tile id (-1 outside the view)
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const long long G = *n_seg;
+  for (long long g = blockIdx.x; g < G; g += gridDim.x) {
+    const SegInfo si = seg_info(g, st_ranges, seg_first, seg_st, ct);
+    __syncthreads();  // the previous segment's readers of s_run / s_tile are done
+    if (tid < 64) {
+      const CamInfo& c = ct.c[si.view];
+      const int tx = si.ox + (tid & 7), ty = si.oy + (tid >> 3);
+      const bool in = tx < c.TX && ty < c.TY;
+      const int t = in ? c.tile_off + ty * c.TX + tx : -1;
+      s_tile[tid] = t;
+      s_run[tid] = in ? tile_start[t] + hist[g * 64 + tid] : 0u;
+    }
+    for (unsigned c0 = si.b; c0 < si.e; c0 += 256) {
+      const unsigned i = c0 + tid;
+      unsigned d = 0u, row = 0u;
+      if (i < si.e) {
+        d = desc[i];
+        row = sp_rows[i];
+      }
+      const int x0 = d & 15u, x1 = (d >> 4) & 15u, y0 = (d >> 8) & 15u, y1 = (d >> 12) & 15u;
+      const bool any = x1 > x0;  // (y1 > y0 too: empty descriptors are 0)
+      unsigned long long mask = 0ull;
+      if (any) {
+        const unsigned long long xb = (unsigned long long)(((1u << x1) - 1u) & ~((1u << x0) - 1u));
+        const unsigned long long ym =
+            (y1 >= 8 ? ~0ull : ((1ull << (8 * y1)) - 1ull)) & ~((1ull << (8 * y0)) - 1ull);
+        mask = (xb * 0x0101010101010101ull) & ym;
+      }
+      // per-warp counts per tile from a 2D difference grid
+      for (int q = lane; q < 81; q += 32) s_d[w][q] = 0;
+      __syncwarp();
+      if (any) {
+        atomicAdd(&s_d[w][y0 * 9 + x0], 1);
+        atomicAdd(&s_d[w][y0 * 9 + x1], -1);
+        atomicAdd(&s_d[w][y1 * 9 + x0], -1);
+        atomicAdd(&s_d[w][y1 * 9 + x1], 1);
+      }
+      __syncwarp();
+      if (lane < 8) {  // prefix along x, row `lane`
+        int run = 0;
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+          run += s_d[w][lane * 9 + x];
+          s_d[w][lane * 9 + x] = run;
+        }
+      }
+      __syncwarp();
+      if (lane < 8) {  // prefix along y, column `lane`
+        int run = 0;
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+          run += s_d[w][y * 9 + lane];
+          s_d[w][y * 9 + lane] = run;
+        }
+      }
+      __syncthreads();
+      if (tid < 64) {
+        unsigned run = s_run[tid];
+        const int cell = (tid >> 3) * 9 + (tid & 7);
+#pragma unroll
+        for (int ww = 0; ww < 8; ++ww) {
+          s_pos[ww][tid] = run;
+          run += (unsigned)s_d[ww][cell];
+        }
+        s_run[tid] = run;
+      }
+      __syncthreads();
+      const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)mask);
+      const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(mask >> 32));
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const unsigned byte = ((r < 4 ? lo : hi) >> (8 * (r & 3))) & 0xffu;
+        if (byte == 0u) continue;  // warp-uniform
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+          const int bt = 8 * r + x;
+          const bool mine = (mask >> bt) & 1ull;
+          const unsigned bal = __ballot_sync(0xffffffffu, mine);
+          if (mine) {
+            const unsigned pos = s_pos[w][bt] + __popc(bal & lt);
+            out_vals[pos] = row;
+            if (out_keys)
+              out_keys[pos] = ((unsigned long long)(unsigned)s_tile[bt] << 32) |
+                              __float_as_uint(depth[row]);
+          }
+        }
+      }
+    }
+  }
 }
 
 __global__ void set_count_kernel(long long* __restrict__ dst, const long long* __restrict__ src) {
@@ -484,14 +941,22 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Workspace {
   unsigned long long* block_sums;  // scan block sums
-  long long* counters;             // [0] n_vis, [1] P, [2] P effective
+  unsigned long long* block_sums2; // second scan's block sums
+  long long* counters;             // [0] n_vis, [1] P, [2] P eff., [3] Q, [4] Q eff., [5] segments
   unsigned* rk[2];                 // row keys (depth bits), double buffer
   unsigned* rv[2];                 // row values, double buffer
-  unsigned long long* offsets;     // pair offsets per visible row
-  unsigned* pk[2];                 // pair keys (tile), double buffer; pk[1] may alias output
-  unsigned* pv;                    // pair values scratch
+  unsigned long long* offsets;     // super-pair offsets per visible row
+  int4* rect_sorted;               // clamped rect per visible row, depth order
+  unsigned* pk[2];                 // super-pair keys (super-tile), double buffer; later descriptors
+  unsigned* pv;                    // super-pair values (rows)
   unsigned* hist;                  // radix histograms
   unsigned* block_row;             // first row of every duplication block
+  unsigned* st_ranges;             // [2 * super-tiles] rows of each super-tile
+  unsigned* seg_first;             // [super-tiles + 1] first segment of each super-tile
+  unsigned* seg_st;                // super-tile of every segment
+  unsigned* seg_hist;              // [segments][64] per-tile counts, then bases
+  unsigned* tile_cnt;              // [tiles] list lengths
+  unsigned* tile_start;            // [tiles] list starts
   size_t bytes;
 };
 
@@ -499,7 +964,11 @@ constexpr int kRadixGrid = 4 * 152;  // fixed radix grid (4 CTAs per SM)
 
 inline long long scan_blocks(long long n) { return (n + kScanTile - 1) / kScanTile; }
 
-Workspace carve(void* base, long long n_rows, long long cap) {
+// Upper bound of the expansion segments: sum over super-tiles of
+// ceil(len / kSeg) <= Q / kSeg + super-tiles, and Q <= P <= cap.
+inline long long max_segments(long long cap, long long tiles) { return cap / kSeg + tiles + 2; }
+
+Workspace carve(void* base, long long n_rows, long long cap, long long tiles) {
   Workspace w;
   char* p = reinterpret_cast<char*>(base);
   size_t off = 0;
@@ -508,33 +977,69 @@ Workspace carve(void* base, long long n_rows, long long cap) {
     off += align256(bytes);
     return r;
   };
-  long long nb = scan_blocks(n_rows > cap ? n_rows : cap) + 1;
+  const long long nb = scan_blocks(n_rows > cap ? n_rows : cap) + 1;
+  const long long ms = max_segments(cap, tiles);
   w.block_sums = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * nb));
-  w.counters = reinterpret_cast<long long*>(take(sizeof(long long) * 4));
+  w.block_sums2 = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * nb));
+  w.counters = reinterpret_cast<long long*>(take(sizeof(long long) * 8));
   for (int i = 0; i < 2; ++i) w.rk[i] = reinterpret_cast<unsigned*>(take(4 * (n_rows + 1)));
   for (int i = 0; i < 2; ++i) w.rv[i] = reinterpret_cast<unsigned*>(take(4 * (n_rows + 1)));
   w.offsets = reinterpret_cast<unsigned long long*>(take(8 * (n_rows + 1)));
+  w.rect_sorted = reinterpret_cast<int4*>(take(16 * (n_rows + 1)));
   for (int i = 0; i < 2; ++i) w.pk[i] = reinterpret_cast<unsigned*>(take(4 * (cap + 1)));
   w.pv = reinterpret_cast<unsigned*>(take(4 * (cap + 1)));
   w.hist = reinterpret_cast<unsigned*>(take(4ull * kRadixBins * (kRadixGrid + 1)));
   w.block_row = reinterpret_cast<unsigned*>(take(4ull * ((cap + kDupPairs - 1) / kDupPairs + 1)));
+  w.st_ranges = reinterpret_cast<unsigned*>(take(8ull * (tiles + 1)));
+  w.seg_first = reinterpret_cast<unsigned*>(take(4ull * (tiles + 2)));
+  w.seg_st = reinterpret_cast<unsigned*>(take(4ull * ms));
+  w.seg_hist = reinterpret_cast<unsigned*>(take(4ull * 64 * ms));
+  w.tile_cnt = reinterpret_cast<unsigned*>(take(4ull * (tiles + 1)));
+  w.tile_start = reinterpret_cast<unsigned*>(take(4ull * (tiles + 1)));
   w.bytes = off;
   return w;
 }
 
 // Runs the radix passes over bits [0, bits) of keys; data starts in
 // (k[0], v[0]) and ends in (k[res], v[res]); returns res.
+// CTAs of radix_downsweep_kernel resident on the current device at once
+// (cached per device).
+int radix_resident_ctas() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return kRadixGrid;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, radix_downsweep_kernel,
+                                                    kRadixThreads, 0) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      per_sm < 1 || sms < 1) {
+    cudaGetLastError();
+    return kRadixGrid;
+  }
+  v = per_sm * sms;
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 int radix_sort(unsigned* k[2], unsigned* v[2], const long long* n_dev, long long n_bound, int bits,
                unsigned* hist, cudaStream_t st) {
   int cur = 0;
   if (n_bound == 0) return cur;
-  int grid = (int)std::min<long long>(kRadixGrid, (n_bound + kRadixTile - 1) / kRadixTile);
+  // one wave: at most the CTAs of the scatter kernel resident on the device
+  int grid = (int)std::min<long long>(std::min(kRadixGrid, radix_resident_ctas()),
+                                      (n_bound + kRadixTile - 1) / kRadixTile);
   if (grid < 1) grid = 1;
-  for (int shift = 0; shift < bits; shift += 8) {
-    radix_upsweep_kernel<<<grid, kRadixThreads, 0, st>>>(k[cur], n_dev, shift, hist);
+  // the fewest 8-bit-or-narrower passes, with equal digit widths
+  const int passes = (bits + 7) / 8;
+  const int dbits = passes ? (bits + passes - 1) / passes : 0;
+  for (int shift = 0; shift < bits; shift += dbits) {
+    radix_upsweep_kernel<<<grid, kRadixThreads, 0, st>>>(k[cur], n_dev, shift,
+                                                         (1u << dbits) - 1u, hist);
     radix_scan_kernel<<<kRadixBins, kScanThreads, 0, st>>>(hist, grid, hist + kRadixBins * grid);
     radix_downsweep_kernel<<<grid, kRadixThreads, 0, st>>>(k[cur], v[cur], k[1 - cur], v[1 - cur],
-                                                           n_dev, shift, hist,
+                                                           n_dev, shift, dbits, hist,
                                                            hist + kRadixBins * grid);
     count_launches(3);
     cur = 1 - cur;
@@ -551,8 +1056,7 @@ int bits_for(long long count) {
 }  // namespace
 
 size_t bin_sort_workspace_size(long long n_rows, long long cap, long long total_tiles) {
-  (void)total_tiles;
-  return carve(nullptr, n_rows, cap).bytes;
+  return carve(nullptr, n_rows, cap, total_tiles).bytes;
 }
 
 int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* workspace,
@@ -560,13 +1064,17 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
                     unsigned long long* sorted_keys, unsigned* ranges, long long* num_pairs_dev,
                     long long* num_pairs_host, int* status_dev, cudaStream_t st) {
   const long long n_rows = (long long)N * ct.V;
-  Workspace w = carve(workspace, n_rows, cap);
+  const long long T = ct.total_tiles;
+  const int S = ct.total_st;
+  Workspace w = carve(workspace, n_rows, cap, T);
   if (ws_bytes < w.bytes) return GS_ERR_INVALID_ARG;
   long long* n_vis = w.counters;
   long long* P = w.counters + 1;
   long long* p_eff = w.counters + 2;
-  GS_TRY_CUDA(cudaMemsetAsync(w.counters, 0, 4 * sizeof(long long), st));
-  GS_TRY_CUDA(cudaMemsetAsync(ranges, 0, 2 * sizeof(unsigned) * (size_t)ct.total_tiles, st));
+  long long* Q = w.counters + 3;
+  long long* q_eff = w.counters + 4;
+  long long* n_seg = w.counters + 5;
+  GS_TRY_CUDA(cudaMemsetAsync(w.counters, 0, 8 * sizeof(long long), st));
   unsigned* rows_sorted = w.rv[0];
   const long long nb = scan_blocks(n_rows);
   if (n_rows > 0) {
@@ -579,15 +1087,17 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
     // 2. stable depth sort of the visible rows (ties keep row order = id order)
     int res = radix_sort(w.rk, w.rv, n_vis, n_rows, 32, w.hist, st);
     rows_sorted = w.rv[res];
-    // 3. pair offsets in depth order and the pair count P
-    ScanSrc tt{proj->tiles_touched, rows_sorted, 0};
-    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(tt, n_vis, 0, w.block_sums);
-    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(w.block_sums, (int)nb, P);
-    scan_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(proj->tiles_touched, rows_sorted,
-                                                               n_vis, w.block_sums, w.offsets);
-    count_launches(6);
+    // 3. per row in depth order: super-tile offsets, the super-pair count Q
+    //    and the pair count P
+    rows_gather_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(
+        rows_sorted, n_vis, proj->rect, N, ct, w.rect_sorted, w.block_sums, w.block_sums2);
+    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(w.block_sums, (int)nb, Q);
+    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(w.block_sums2, (int)nb, P);
+    row_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(w.rect_sorted, n_vis, w.block_sums,
+                                                              w.offsets);
+    count_launches(7);
   }
-  capacity_check_kernel<<<1, 32, 0, st>>>(P, cap, status_dev, p_eff);
+  capacity_check_kernel<<<1, 32, 0, st>>>(P, Q, cap, status_dev, p_eff, q_eff);
   set_count_kernel<<<1, 32, 0, st>>>(num_pairs_dev, P);
   count_launches(2);
   GS_TRY_CUDA(cudaGetLastError());
@@ -597,42 +1107,62 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
     GS_TRY_CUDA(cudaMemcpyAsync(&p_host, P, sizeof(long long), cudaMemcpyDeviceToHost, st));
     GS_TRY_CUDA(cudaStreamSynchronize(st));
     *num_pairs_host = p_host;
-    if (p_host > cap) return GS_ERR_CAPACITY;
+    if (p_host > cap) {
+      GS_TRY_CUDA(cudaMemsetAsync(ranges, 0, 2 * sizeof(unsigned) * (size_t)T, st));
+      return GS_ERR_CAPACITY;
+    }
     p_bound = p_host;
   }
-  if (n_rows == 0 || p_bound == 0) return check_launch();
-  // 4. duplicate in depth order, into the buffer pair the last tile pass
-  //    reads from so that the sorted values end in sorted_vals
-  const int tbits = bits_for(ct.total_tiles);
-  const int passes = (tbits + 7) / 8;
-  unsigned* pk[2] = {w.pk[0], w.pk[1]};
-  unsigned* pv[2];
-  if (passes % 2 == 0) {
-    pv[0] = sorted_vals;
-    pv[1] = w.pv;
-  } else {
-    pv[0] = w.pv;
-    pv[1] = sorted_vals;
+  if (n_rows == 0 || p_bound == 0 || S == 0) {
+    GS_TRY_CUDA(cudaMemsetAsync(ranges, 0, 2 * sizeof(unsigned) * (size_t)T, st));
+    return check_launch();
   }
+  // 4. super-pairs (super-tile, row) in depth order of the rows, into the
+  //    buffers that the super-tile sort leaves in (pk[res], pv)
+  const int sbits = bits_for(S);
+  const int spasses = (sbits + 7) / 8;
+  unsigned* sk[2] = {w.pk[0], w.pk[1]};
+  unsigned* sv[2];
+  if (spasses % 2 == 0) {
+    sv[0] = w.pv;
+    sv[1] = sorted_vals;
+  } else {
+    sv[0] = sorted_vals;
+    sv[1] = w.pv;
+  }
+  const long long q_bound = p_bound;  // Q <= P
   {
     const unsigned g1 = (unsigned)std::min<long long>((n_rows + 255) / 256, 152ll * 32);
-    mark_block_starts_kernel<<<g1, 256, 0, st>>>(rows_sorted, n_vis, w.offsets,
-                                                proj->tiles_touched, p_eff, w.block_row);
-    const unsigned g2 = (unsigned)((p_bound + kDupPairs - 1) / kDupPairs);
-    duplicate_kernel<<<g2, kDupThreads, 0, st>>>(rows_sorted, n_vis, w.offsets, proj->rect, N, ct,
-                                                p_eff, w.block_row, pk[0], pv[0]);
+    mark_block_starts_kernel<<<g1, 256, 0, st>>>(w.rect_sorted, n_vis, w.offsets, q_eff,
+                                                w.block_row);
+    const unsigned g2 = (unsigned)((q_bound + kDupPairs - 1) / kDupPairs);
+    const int vec16 = (reinterpret_cast<uintptr_t>(sv[0]) % 16 == 0) ? 1 : 0;
+    duplicate_kernel<<<g2, kDupThreads, 0, st>>>(rows_sorted, w.rect_sorted, n_vis, w.offsets, N,
+                                                ct, q_eff, w.block_row, sk[0], sv[0], vec16);
     count_launches(2);
   }
-  // 5. stable sort of the pairs by global tile id
-  int res2 = radix_sort(pk, pv, p_eff, p_bound, tbits, w.hist, st);
-  // 6. per-tile ranges (and the optional 64-bit keys)
-  unsigned grid = (unsigned)std::min<long long>((p_bound + 255) / 256, 152ll * 16);
-  ranges_kernel<<<grid, 256, 0, st>>>(pk[res2], p_eff, ranges);
-  count_launches(1);
-  if (sorted_keys) {
-    keys64_kernel<<<grid, 256, 0, st>>>(pk[res2], pv[res2], proj->depth, p_eff, sorted_keys);
-    count_launches(1);
-  }
+  // 5. stable sort of the super-pairs by super-tile id
+  const int sres = radix_sort(sk, sv, q_eff, q_bound, sbits, w.hist, st);
+  const unsigned* sp_keys = sk[sres];
+  const unsigned* sp_rows = sv[sres];  // == w.pv
+  unsigned* desc = sk[1 - sres];
+  // 6. rows of every super-tile, segments, per-tile counts and list starts
+  GS_TRY_CUDA(cudaMemsetAsync(w.st_ranges, 0, 2 * sizeof(unsigned) * (size_t)S, st));
+  const unsigned gq = (unsigned)std::min<long long>((q_bound + 1023) / 1024, 152ll * 16);
+  ranges_kernel<<<gq, 256, 0, st>>>(sp_keys, q_eff, w.st_ranges);
+  st_segments_kernel<<<1, 1024, 0, st>>>(reinterpret_cast<const uint2*>(w.st_ranges), S,
+                                         w.seg_first, w.seg_st, n_seg);
+  const unsigned gs = (unsigned)std::min<long long>(max_segments(q_bound, S), 152ll * 8);
+  st_count_kernel<<<gs, 256, 0, st>>>(sp_rows, reinterpret_cast<const uint2*>(w.st_ranges),
+                                      w.seg_first, w.seg_st, n_seg, proj->rect, N, ct, desc,
+                                      w.seg_hist);
+  st_scan_kernel<<<(unsigned)S, 1024, 0, st>>>(w.seg_first, ct, w.seg_hist, w.tile_cnt);
+  tile_scan_kernel<<<1, 1024, 0, st>>>(w.tile_cnt, (int)T, w.tile_start, ranges);
+  // 7. every row into the lists of the tiles it covers, in depth order
+  st_emit_kernel<<<gs, 256, 0, st>>>(sp_rows, desc, reinterpret_cast<const uint2*>(w.st_ranges),
+                                     w.seg_first, w.seg_st, n_seg, w.seg_hist, w.tile_start, ct,
+                                     proj->depth, sorted_vals, sorted_keys);
+  count_launches(6);
   return check_launch();
 }
 

@@ -15,6 +15,7 @@ namespace gs {
 
 constexpr int kTile = GS_TILE;               // 16x16 pixel tiles
 constexpr int kTilePix = kTile * kTile;      // 256 pixels per tile
+constexpr int kSuperTile = 8;                // binning groups 8x8 tiles into a super-tile
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
@@ -26,6 +27,8 @@ struct CamInfo {
   float cp[3];       // camera centre in world space
   float limx, limy;  // clamp of x/z, y/z in the EWA Jacobian
   int W, H, TX, TY;
+  int STX, STY;      // super-tiles (kSuperTile x kSuperTile tiles) per row / column
+  int st_off;        // first global super-tile id of this view
   int tile_off;      // first global tile id of this view
   long long pix_off; // first pixel of this view in per-pixel arrays
 };
@@ -33,6 +36,7 @@ struct CamInfo {
 struct CamTable {
   int V;
   int total_tiles;
+  int total_st;  // super-tiles over all views
   CamInfo c[GS_MAX_VIEWS];
 };
 
