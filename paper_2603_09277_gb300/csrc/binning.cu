@@ -2,19 +2,26 @@
 // Gaussians that cover it, sorted by depth).
 //
 // The lists are the (tile, depth, id)-ordered pairs of every visible
-// (view, Gaussian) row with every tile of its rect.  Instead of one sort
-// of 64-bit (tile << 32 | depth) keys over all P pairs, the work is split
-// so that the P-sized sort only carries the tile bits:
+// (view, Gaussian) row with every tile of its rect.  Instead of sorting all
+// P pairs, the sort works on rows and on row x super-tile items (a
+// super-tile is 8x8 tiles), and the pairs are only ever written once, into
+// their final slots:
 //   1. compact the visible rows (scan of a visibility flag);
 //   2. stable LSD radix sort of the visible rows by FP32 depth bits
-//      (N-sized: 4 passes of 8 bits over 8-byte items);
-//   3. exclusive scan of tiles_touched in depth order -> pair offsets, P;
-//   4. duplicate: each row writes (global tile, row) for its rect, in depth
-//      order (so equal tiles appear in (depth, id) order);
-//   5. stable LSD radix sort of the pairs by tile id, ceil(log2 tiles) bits;
-//   6. per-tile [start, end) ranges from the sorted tile ids.
-// The stable tile sort of depth-ordered pairs yields exactly the order of
-// the 64-bit key sort with ties by Gaussian id.
+//      (4 passes of 8 bits; ties keep row order = Gaussian id order);
+//   3. gather every row's rect in depth order; scans give the pair count P
+//      and each row's offset among the super-tile items (count Q <= P);
+//   4. duplicate: each row writes (super-tile, row) for the super-tiles its
+//      rect meets, in depth order (load-balanced over items);
+//   5. stable radix sort of the items by super-tile id (one pass for up to
+//      256 super-tiles), so every super-tile holds its rows in depth order;
+//   6. per segment of 1024 rows of a super-tile: each row's rect within the
+//      super-tile and per-tile counts; scans over segments and over all
+//      tiles give every tile's list start (the ranges);
+//   7. expansion: each segment writes its rows into the lists of the tiles
+//      they cover, ranked by warp ballots, which keeps the depth order.
+// The result is exactly the order of a 64-bit (tile << 32 | depth) key sort
+// with ties by Gaussian id.
 //
 // All kernels read their element counts from device memory and use grids
 // sized from host-known upper bounds, so the whole sequence can be captured
