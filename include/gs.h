@@ -84,7 +84,7 @@ typedef struct {
 /* Projected per-(view, Gaussian) attributes, V*N rows, device memory. */
 typedef struct {
     void* records;           /* required: gs_record_bytes(attr_dtype) per row, 16-B aligned */
-    float* depth;            /* required [V*N]: FP32 camera-space depth (0 when culled) */
+    float* depth;            /* required [V*N]: FP32 camera-space depth of every row */
     int* rect;               /* required [V*N][4]: tile rect x0, y0, x1, y1 (half-open) */
     unsigned* tiles_touched; /* required [V*N]: (x1-x0)(y1-y0), 0 when culled */
     int* radius;             /* optional [V*N]: ceil(3 sqrt(lambda_max)) px */

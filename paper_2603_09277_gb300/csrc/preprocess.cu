@@ -419,6 +419,7 @@ __device__ __forceinline__ void adjoint_one(
   float gRq[9];                    // dL/d(rotation matrix entries), summed over views
   for (int k = 0; k < 9; ++k) gRq[k] = 0.f;
   float gsig = 0.f;
+  bool first_view = true;
   for (int v = 0; v < ct.V; ++v) {
     long long row = (long long)v * N + g;
     if (tiles_touched[row] == 0u) continue;
@@ -447,14 +448,25 @@ __device__ __forceinline__ void adjoint_one(
     float grgb[3] = {raw[0] < 0.f ? 0.f : G1.z, raw[1] < 0.f ? 0.f : G1.w,
                      raw[2] < 0.f ? 0.f : G2.x};
     float cdot[16];
+    // the first view that sees the Gaussian stores, later ones accumulate
     for (int k = 0; k < K; ++k) {
-      float3 s = load_sh(sh, g, sh_stride, k);
-      float* gs = g_sh + ((long long)g * sh_stride + k) * 3;
-      gs[0] += Y[k] * grgb[0];
-      gs[1] += Y[k] * grgb[1];
-      gs[2] += Y[k] * grgb[2];
-      cdot[k] = s.x * grgb[0] + s.y * grgb[1] + s.z * grgb[2];
+      {
+        float3 s = load_sh(sh, g, sh_stride, k);
+        float* gs = g_sh + ((long long)g * sh_stride + k) * 3;
+        const float a0 = Y[k] * grgb[0], a1 = Y[k] * grgb[1], a2 = Y[k] * grgb[2];
+        if (first_view) {
+          gs[0] = a0;
+          gs[1] = a1;
+          gs[2] = a2;
+        } else {
+          gs[0] += a0;
+          gs[1] += a1;
+          gs[2] += a2;
+        }
+        cdot[k] = s.x * grgb[0] + s.y * grgb[1] + s.z * grgb[2];
+      }
     }
+    first_view = false;
     if (sh_deg > 0) {
       float3 gd = sh_basis_grad_dot(sh_deg, dx, dy, dz, cdot);
       float dd = gd.x * dx + gd.y * dy + gd.z * dz;
@@ -566,11 +578,25 @@ __device__ __forceinline__ void adjoint_one(
   reinterpret_cast<float4*>(g_quats)[g] = gq;
 }
 
+// Zeroes p[0, n) with the block's threads (16-byte stores where aligned).
+__device__ __forceinline__ void zero_span(float* p, long long n) {
+  if (n <= 0) return;
+  long long head = (long long)((16 - (reinterpret_cast<uintptr_t>(p) & 15)) & 15) / 4;
+  if ((reinterpret_cast<uintptr_t>(p) & 3) != 0) head = n;  // not even 4-byte aligned
+  head = min(head, n);
+  for (long long i = threadIdx.x; i < head; i += blockDim.x) p[i] = 0.f;
+  float4* q = reinterpret_cast<float4*>(p + head);
+  const long long n4 = (n - head) / 4;
+  for (long long i = threadIdx.x; i < n4; i += blockDim.x) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long long i = head + 4 * n4 + threadIdx.x; i < n; i += blockDim.x) p[i] = 0.f;
+}
+
 // The adjoint over Gaussians, compacted per block: each CTA owns 2048
-// consecutive Gaussians, zeroes the gradients of those no view sees, lists
-// the others in shared memory (ascending), then its threads take the listed
+// consecutive Gaussians, zeroes their gradients, lists the ones some view
+// sees in shared memory (ascending), then its threads take the listed
 // Gaussians densely, so a scene where most Gaussians are culled does not run
-// the long adjoint on warps with one or two live lanes.
+// the long adjoint on warps with one or two live lanes.  (The zeroing is
+// ordered before the adjoint's writes by the barriers of the list build.)
 constexpr int kAdjThreads = 256;
 constexpr int kAdjPer = 8;
 constexpr int kAdjSpan = kAdjThreads * kAdjPer;
@@ -587,6 +613,12 @@ __global__ void __launch_bounds__(kAdjThreads) preprocess_bwd_kernel(
   __shared__ int s_off[kAdjPer * kAdjWarps + 1];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int base = blockIdx.x * kAdjSpan;
+  const long long cnt = min((long long)kAdjSpan, (long long)N - base);
+  // every gradient of the CTA's Gaussians starts at zero (contiguous spans)
+  zero_span(g_means + 3ll * base, 3 * cnt);
+  zero_span(g_ls + 3ll * base, 3 * cnt);
+  zero_span(g_quats + 4ll * base, 4 * cnt);
+  zero_span(g_opac + base, cnt);  // (g_sh is zeroed by the caller)
   unsigned ball[kAdjPer];
   // pass k covers Gaussians base + k*256 + tid: the (k, warp, lane) order is
   // ascending in g
@@ -596,16 +628,6 @@ __global__ void __launch_bounds__(kAdjThreads) preprocess_bwd_kernel(
     bool any = false;
     if (g < N) {
       for (int v = 0; v < ct.V; ++v) any |= tiles_touched[(long long)v * N + g] != 0u;
-      if (!any) {  // g_sh arrives zeroed (memset by the caller)
-        g_means[3ll * g] = 0.f;
-        g_means[3ll * g + 1] = 0.f;
-        g_means[3ll * g + 2] = 0.f;
-        g_ls[3ll * g] = 0.f;
-        g_ls[3ll * g + 1] = 0.f;
-        g_ls[3ll * g + 2] = 0.f;
-        reinterpret_cast<float4*>(g_quats)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-        g_opac[g] = 0.f;
-      }
     }
     ball[k] = __ballot_sync(0xffffffffu, any);
     if (lane == 0) s_off[k * kAdjWarps + w] = __popc(ball[k]);

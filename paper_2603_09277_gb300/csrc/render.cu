@@ -21,7 +21,8 @@
 //   dL/dalpha_i = sum_ch g_ch (T_i c_i - S / (1 - alpha_i))
 //               + gH ((-ln w_i - 1) T_i + R / (1 - alpha_i))
 //   S += w_i c_i; R += (ln w_i + 1) w_i    (R starts at (ln T_N+1 + 1) T_N+1)
-//   (only g . S is needed, so it is carried instead of S: g . S += w_i g . c_i)
+//   (only g . S is needed, so it is carried instead of S: g . S += w_i g . c_i;
+//   R and gH are carried in base-2 units, R / ln 2 and gH ln 2)
 //   then dsigma = dalpha g, dd = dalpha alpha (unless clamped),
 //   dconic = dd (-dx^2/2, -dx dy, -dy^2/2), dmean = dd conic (dx, dy).
 // The thread sums the 9 per-Gaussian values over its pixels, the warp sums
@@ -380,7 +381,8 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
       if (a.dL_dentropy) gH[q] = a.dL_dentropy[p];
     }
     gS[q] = 0.f;
-    Rent[q] = (fast_log2(T[q]) * kLn2 + 1.f) * T[q];
+    Rent[q] = (fast_log2(T[q]) + kLog2e) * T[q];
+    gH[q] *= kLn2;
     mylast = max(mylast, last[q]);
   }
   if (tid == 0) s_max = 0u;
@@ -436,16 +438,16 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
           const float iom = fast_rcp(1.f - alpha);
           const float Ti = T[q] * iom;
           const float w = alpha * Ti;
-          const float lnw = fast_log2(w) * kLn2;
+          const float L = fast_log2(w) + kLog2e;
           // colour part: dL/dC . (T_i c_i - S / (1 - alpha_i)) = T_i gc - gS / (1 - alpha_i)
           const float gc = __fmaf_rn(gb[q], g2.x, __fmaf_rn(gg[q], g1.w, gr[q] * g1.z));
           float dA = __fmaf_rn(Ti, gc, -gS[q] * iom);
-          dA += gH[q] * ((-lnw - 1.f) * Ti + Rent[q] * iom);
+          dA = __fmaf_rn(gH[q], __fmaf_rn(-L, Ti, Rent[q] * iom), dA);
           gsum[6] += w * gr[q];
           gsum[7] += w * gg[q];
           gsum[8] += w * gb[q];
           gS[q] = __fmaf_rn(w, gc, gS[q]);  // S += w c  =>  dL/dC . S += w gc
-          Rent[q] = __fmaf_rn(lnw + 1.f, w, Rent[q]);
+          Rent[q] = __fmaf_rn(L, w, Rent[q]);
           T[q] = Ti;
           if (araw <= rc.alpha_max) {
             const float dd = dA * araw;
