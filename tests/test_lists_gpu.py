@@ -1,0 +1,86 @@
+"""Per-tile lists (ranges, list contents and their (depth, id) order) against
+the oracle's plain definition on layouts that exercise the list
+construction's corners: a view with more than 256 super-tiles of 8x8 tiles
+(the super-tile sort then takes two radix passes), views whose tile grids
+end inside a super-tile (1x1, 9x9, 2x19, 63x2 tiles), Gaussians whose rects
+span many super-tiles, and the largest view count (64 views)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2603_09277_gb300 import scenes
+
+from parity_util import run_gpu, view_tiles
+
+pytestmark = pytest.mark.gpu
+
+
+def _compare_lists(scene, cams, prm):
+    N = scene["means"].shape[0]
+    g = run_gpu(scene, cams, prm, keys=True)
+    vt = view_tiles(cams)
+    total = 0
+    for v, cam in enumerate(cams):
+        proj = oracle.preprocess(scene, cam, prm)
+        ts, ids = oracle.build_lists(proj, cam)
+        flagged = proj["boundary"].astype(bool)
+        t0, t1 = vt[v]
+        rng = g["ranges"][t0:t1]
+        lens = rng[:, 1] - rng[:, 0]
+        if not flagged.any():
+            # ranges bit-exact: starts are the running sum of the lengths over
+            # all tiles of all views; empty lists are (0, 0)
+            assert (lens == np.diff(ts)).all()
+        for t in range(t1 - t0):
+            a, b = rng[t]
+            glist = g["vals"][a:b] - v * N
+            olist = ids[ts[t]:ts[t + 1]]
+            if flagged.any():
+                glist = glist[~flagged[glist]]
+                olist = olist[~flagged[olist]]
+            assert len(glist) == len(olist) and (glist == olist).all(), (v, t)
+        total += len(ids)
+    ranges = g["ranges"]
+    nz = ranges[:, 1] > ranges[:, 0]
+    # non-empty lists tile sorted_vals in global tile order without gaps
+    starts, ends = ranges[nz, 0], ranges[nz, 1]
+    assert starts[0] == 0 and (starts[1:] == ends[:-1]).all() and ends[-1] == g["P"]
+    assert (ranges[~nz] == 0).all()
+    # 64-bit keys (tile << 32 | depth bits): the tile of every slot, and
+    # non-decreasing overall (tile first, then depth within a tile)
+    keys = g["keys"].view(np.int64)
+    assert ((keys >> 32) == np.repeat(np.nonzero(nz)[0], ends - starts)).all()
+    assert (np.diff(keys) >= 0).all()
+    assert ((keys & 0xffffffff).astype(np.uint32) == g["depth"][g["vals"]].view(np.uint32)).all()
+    any_flagged = any(oracle.preprocess(scene, c, prm)["boundary"].any() for c in cams)
+    return g["P"], total, any_flagged
+
+
+def test_lists_view_with_two_pass_super_tile_sort():
+    # 2600 x 2100 px: 163 x 132 tiles -> 21 x 17 = 357 super-tiles (9 bits, two passes)
+    scene = scenes.box_scene(20_000, seed=5, ls_mean=-4.0, ls_std=0.8)
+    cams = [scenes.camera(2600, 2100, 2600.0)]
+    P, total, flagged = _compare_lists(scene, cams, scenes.params())
+    assert P > 100_000 and (flagged or P == total)
+
+
+def test_lists_ragged_super_tile_borders_and_wide_rects():
+    # tile grids of 1x1, 9x9, 2x19 and 63x2; large Gaussians whose rects span
+    # several super-tiles
+    sizes = [(16, 16), (129, 135), (20, 300), (1000, 31)]
+    cams = [scenes.camera(w, h, float(w)) for w, h in sizes]
+    scene = scenes.box_scene(3_000, seed=6, ls_mean=-2.0, ls_std=1.0)
+    P, total, flagged = _compare_lists(scene, cams, scenes.params())
+    assert P > 10_000 and (flagged or P == total)
+
+
+def test_lists_sixty_four_views():
+    rng = np.random.default_rng(7)
+    yaws = list(rng.uniform(-20.0, 20.0, 64))
+    sizes = [(int(w), int(h)) for w, h in zip(rng.integers(24, 200, 64), rng.integers(24, 160, 64))]
+    cams = scenes.yaw_cameras(sizes, yaws)
+    scene = scenes.box_scene(2_000, seed=8)
+    P, total, flagged = _compare_lists(scene, cams, scenes.params())
+    assert P > 10_000 and (flagged or P == total)
