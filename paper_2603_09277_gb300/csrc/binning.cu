@@ -480,10 +480,11 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
     const long long* __restrict__ n_vis, const unsigned long long* __restrict__ offsets, int N,
     const CamTable ct, const long long* __restrict__ q_eff,
     const unsigned* __restrict__ block_row, unsigned* __restrict__ skeys,
-    unsigned* __restrict__ svals, int vec16) {
+    unsigned* __restrict__ svals, int vec16, int packed) {
   constexpr int kPer = kDupPairs / kDupThreads;  // 4 consecutive items per thread
   __shared__ int s_off[kDupPairs];     // row item offset relative to the block start
   __shared__ int4 s_info[kDupPairs];   // (super-tile id of the span origin, span width, STX, row)
+  __shared__ unsigned s_rel[kDupPairs];  // rect relative to the span origin (packed)
   __shared__ int s_own[kDupPairs];     // slot of the row starting at item t (max-scanned)
   __shared__ int s_wmax[kDupThreads / 32];
   const long long Q = *q_eff;
@@ -504,10 +505,15 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
     const long long o = (long long)offsets[j];
     if (o < end) {
       const unsigned row = rows[j];
-      const int4 q = st_span(rect_sorted[j]);
+      const int4 r = rect_sorted[j];
+      const int4 q = st_span(r);
       const CamInfo& c = ct.c[row / (unsigned)N];
       s_off[i] = (int)(o - start);  // negative for a row that began before the block
       s_info[i] = make_int4(c.st_off + q.y * c.STX + q.x, q.z - q.x, c.STX, (int)row);
+      // first-column / first-row offsets inside the super-tile and the rect's
+      // end relative to the span origin (tiles; < 8192 when packed)
+      s_rel[i] = (unsigned)(r.x & 7) | ((unsigned)(r.y & 7) << 3) |
+                 ((unsigned)(r.z - 8 * q.x) << 6) | ((unsigned)(r.w - 8 * q.y) << 19);
       // a row with no items shares its start with the next row: the later wins
       if (o >= start) atomicMax(&s_own[o - start], i);
     }
@@ -535,7 +541,8 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
   for (int k = 0; k < wp; ++k) before = max(before, s_wmax[k]);
   const int np = (int)(end - start);
   unsigned kk[kPer], vv[kPer];
-  int cur = -1, id = 0, x = 0, wdt = 1, stride = 1;
+  int cur = -1, id = 0, x = 0, y = 0, wdt = 1, stride = 1;
+  unsigned rel = 0u;
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
     const int t = tid * kPer + q;
@@ -546,19 +553,29 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
       const int k = t - s_off[slot];
       wdt = max(in.y, 1);
       stride = in.z;
-      const int ky = k / wdt;
-      x = k - ky * wdt;
-      id = in.x + ky * stride;
+      y = k / wdt;
+      x = k - y * wdt;
+      id = in.x + y * stride;
       vv[q] = (unsigned)in.w;
+      rel = s_rel[slot];
       cur = slot;
     } else {
       vv[q] = vv[q > 0 ? q - 1 : 0];
       if (++x == wdt) {  // next span row
         x = 0;
+        ++y;
         id += stride;
       }
     }
-    kk[q] = (unsigned)(id + x);
+    unsigned key = (unsigned)(id + x);
+    if (packed) {
+      // the row's rect inside this super-tile: x0 | x1 << 4 | y0 << 8 | y1 << 12
+      const int ex = (int)((rel >> 6) & 8191u), ey = (int)(rel >> 19);
+      const unsigned x0 = x == 0 ? (rel & 7u) : 0u, y0 = y == 0 ? ((rel >> 3) & 7u) : 0u;
+      const unsigned x1 = (unsigned)min(ex - 8 * x, 8), y1 = (unsigned)min(ey - 8 * y, 8);
+      key |= (x0 | (x1 << 4) | (y0 << 8) | (y1 << 12)) << 16;
+    }
+    kk[q] = key;
   }
   const int t0 = tid * kPer;
   if (vec16 && t0 + kPer <= np) {  // skeys and svals 16-byte aligned
@@ -579,6 +596,7 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
 // its neighbours, and marks where the key changes.
 __global__ void __launch_bounds__(256) ranges_kernel(const unsigned* __restrict__ tkeys,
                                                      const long long* __restrict__ p_eff,
+                                                     unsigned kmask,
                                                      unsigned* __restrict__ ranges) {
   const long long P = *p_eff;
   const long long groups = (P + 3) / 4;
@@ -588,12 +606,12 @@ __global__ void __launch_bounds__(256) ranges_kernel(const unsigned* __restrict_
     unsigned k[6];
     if (i0 + 3 < P) {
       const uint4 v = reinterpret_cast<const uint4*>(tkeys)[g];
-      k[1] = v.x; k[2] = v.y; k[3] = v.z; k[4] = v.w;
+      k[1] = v.x & kmask; k[2] = v.y & kmask; k[3] = v.z & kmask; k[4] = v.w & kmask;
     } else {
-      for (int q = 0; q < 4; ++q) k[1 + q] = i0 + q < P ? tkeys[i0 + q] : 0u;
+      for (int q = 0; q < 4; ++q) k[1 + q] = i0 + q < P ? tkeys[i0 + q] & kmask : 0u;
     }
-    k[0] = i0 > 0 ? tkeys[i0 - 1] : 0xffffffffu;
-    k[5] = i0 + 4 < P ? tkeys[i0 + 4] : 0xffffffffu;
+    k[0] = i0 > 0 ? tkeys[i0 - 1] & kmask : 0xffffffffu;
+    k[5] = i0 + 4 < P ? tkeys[i0 + 4] & kmask : 0xffffffffu;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const long long i = i0 + q;
@@ -698,42 +716,88 @@ __device__ __forceinline__ SegInfo seg_info(long long g, const uint2* __restrict
   return si;
 }
 
-// Per segment: each row's rect within the super-tile as a 16-bit descriptor
-// (x0 | x1 << 4 | y0 << 8 | y1 << 12, tile units in 0..8), stored for the
-// expansion, and the count of rows covering each of the 64 tiles (2D
-// difference counts in shared memory, summed at the end).
+// Ballots of a warp's 32 rows (one per lane) over the rows and the columns of
+// an 8x8 super-tile: B[r] = lanes whose rect covers tile row r, X[c] = lanes
+// whose rect covers tile column c; the lanes covering tile (r, c) are
+// B[r] & X[c].  d = x0 | x1 << 4 | y0 << 8 | y1 << 12 (0: no tile).
+__device__ __forceinline__ void rect_ballots(unsigned d, unsigned B[8], unsigned X[8]) {
+  const unsigned x0 = d & 15u, x1 = (d >> 4) & 15u, y0 = (d >> 8) & 15u, y1 = (d >> 12) & 15u;
+#pragma unroll
+  for (unsigned r = 0; r < 8; ++r) {
+    B[r] = __ballot_sync(0xffffffffu, y0 <= r && r < y1);
+    X[r] = __ballot_sync(0xffffffffu, x0 <= r && r < x1);
+  }
+}
+
+// Counts of the warp's rows covering tiles `lane` and `lane + 32` of the
+// super-tile (tile b = 8 row + column).
+__device__ __forceinline__ void lane_tile_counts(const unsigned B[8], const unsigned X[8],
+                                                 int lane, unsigned& c0, unsigned& c1) {
+  const int r = lane >> 3, c = lane & 7;
+  unsigned b0 = B[0], b1 = B[4], x = X[0];
+#pragma unroll
+  for (int k = 1; k < 4; ++k) {
+    b0 = r == k ? B[k] : b0;
+    b1 = r == k ? B[k + 4] : b1;
+  }
+#pragma unroll
+  for (int k = 1; k < 8; ++k) x = c == k ? X[k] : x;
+  c0 = __popc(b0 & x);
+  c1 = __popc(b1 & x);
+}
+
+// Rect of row `row` inside the super-tile with tile origin (ox, oy), as a
+// descriptor (0 when it covers no tile of it).
+__device__ __forceinline__ unsigned st_desc(const int* __restrict__ rect, unsigned row, int N,
+                                            const CamTable& ct, int ox, int oy) {
+  const int4 r = view_rect(rect, row, N, ct);
+  const int x0 = max(r.x - ox, 0), x1 = min(r.z - ox, kSuperTile);
+  const int y0 = max(r.y - oy, 0), y1 = min(r.w - oy, kSuperTile);
+  if (x1 <= x0 || y1 <= y0) return 0u;  // (not produced by consistent inputs)
+  return (unsigned)(x0 | (x1 << 4) | (y0 << 8) | (y1 << 12));
+}
+
+// Per segment: the count of rows covering each of the 64 tiles (warp ballots,
+// summed over the CTA's warps).  The rect descriptors travel in the items'
+// keys (bits 16-31) when `packed`; otherwise they are formed here from the
+// rects and stored in desc for the expansion.
 __global__ void __launch_bounds__(256) st_count_kernel(
-    const unsigned* __restrict__ sp_rows, const uint2* __restrict__ st_ranges,
-    const unsigned* __restrict__ seg_first, const unsigned* __restrict__ seg_st,
-    const long long* __restrict__ n_seg, const int* __restrict__ rect, int N, const CamTable ct,
-    unsigned* __restrict__ desc, unsigned* __restrict__ hist) {
-  __shared__ int s_d[9 * 9];
+    const unsigned* __restrict__ sp_keys, const unsigned* __restrict__ sp_rows,
+    const uint2* __restrict__ st_ranges, const unsigned* __restrict__ seg_first,
+    const unsigned* __restrict__ seg_st, const long long* __restrict__ n_seg, int packed,
+    const int* __restrict__ rect, int N, const CamTable ct, unsigned* __restrict__ desc,
+    unsigned* __restrict__ hist) {
+  __shared__ unsigned s_cnt[8][64];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const long long G = *n_seg;
   for (long long g = blockIdx.x; g < G; g += gridDim.x) {
-    for (int i = threadIdx.x; i < 81; i += blockDim.x) s_d[i] = 0;
-    __syncthreads();
     const SegInfo si = seg_info(g, st_ranges, seg_first, seg_st, ct);
-    for (unsigned i = si.b + threadIdx.x; i < si.e; i += blockDim.x) {
-      const int4 r = view_rect(rect, sp_rows[i], N, ct);
-      const int x0 = max(r.x - si.ox, 0), x1 = min(r.z - si.ox, kSuperTile);
-      const int y0 = max(r.y - si.oy, 0), y1 = min(r.w - si.oy, kSuperTile);
-      if (x1 <= x0 || y1 <= y0) {  // no tile here (not produced by consistent inputs)
-        desc[i] = 0u;
-        continue;
+    unsigned a0 = 0u, a1 = 0u;
+    for (unsigned c0 = si.b + 32u * w; c0 < si.e; c0 += 256u) {  // warp-uniform
+      const unsigned i = c0 + lane;
+      unsigned d = 0u;
+      if (i < si.e) {
+        if (packed) {
+          d = sp_keys[i] >> 16;
+        } else {
+          d = st_desc(rect, sp_rows[i], N, ct, si.ox, si.oy);
+          desc[i] = d;
+        }
       }
-      desc[i] = (unsigned)(x0 | (x1 << 4) | (y0 << 8) | (y1 << 12));
-      atomicAdd(&s_d[y0 * 9 + x0], 1);
-      atomicAdd(&s_d[y0 * 9 + x1], -1);
-      atomicAdd(&s_d[y1 * 9 + x0], -1);
-      atomicAdd(&s_d[y1 * 9 + x1], 1);
+      unsigned B[8], X[8], n0, n1;
+      rect_ballots(d, B, X);
+      lane_tile_counts(B, X, lane, n0, n1);
+      a0 += n0;
+      a1 += n1;
     }
+    s_cnt[w][lane] = a0;
+    s_cnt[w][lane + 32] = a1;
     __syncthreads();
-    if (threadIdx.x < 64) {
-      const int lx = threadIdx.x & 7, ly = threadIdx.x >> 3;
-      int sum = 0;
-      for (int y = 0; y <= ly; ++y)
-        for (int x = 0; x <= lx; ++x) sum += s_d[y * 9 + x];
-      hist[g * 64 + threadIdx.x] = (unsigned)sum;
+    if (tid < 64) {
+      unsigned sum = 0u;
+#pragma unroll
+      for (int ww = 0; ww < 8; ++ww) sum += s_cnt[ww][tid];
+      hist[g * 64 + tid] = sum;
     }
     __syncthreads();
   }
@@ -824,22 +888,23 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const unsigned* __restr
 }
 
 // Expansion: per segment, rows in chunks of 256 (one per thread, 8 warps of
-// 32 consecutive rows).  Each warp counts its rows per tile with a 2D
-// difference grid of its own; a prefix over the warps and the running list
-// positions give every warp its first slot per tile; then, per tile some
-// row of the warp covers, a ballot ranks the covering lanes, so every list
-// receives its rows in the segment's (depth) order with coalesced stores.
+// 32 consecutive rows).  Each warp takes its row and column ballots over the
+// super-tile, counts its rows per tile, a prefix over the warps and the
+// running list positions give every warp its first slot per tile, and the
+// lanes covering tile (r, c) (B[r] & X[c]) write their rows at consecutive
+// slots, so every list receives its rows in the segment's (depth) order with
+// coalesced stores.
 __global__ void __launch_bounds__(256) st_emit_kernel(
-    const unsigned* __restrict__ sp_rows, const unsigned* __restrict__ desc,
-    const uint2* __restrict__ st_ranges, const unsigned* __restrict__ seg_first,
-    const unsigned* __restrict__ seg_st, const long long* __restrict__ n_seg,
-    const unsigned* __restrict__ hist, const unsigned* __restrict__ tile_start, const CamTable ct,
-    const float* __restrict__ depth, unsigned* __restrict__ out_vals,
-    unsigned long long* __restrict__ out_keys) {
-  __shared__ unsigned s_run[64];     // next list slot per tile of the super-tile
-  __shared__ int s_d[8][84];         // per-warp 9x9 difference grid, then counts
-  __shared__ unsigned s_pos[8][64];  // per-warp first slot per tile
-  __shared__ int s_tile[64];         // global tile id (-1 outside the view)
+    const unsigned* __restrict__ sp_keys, const unsigned* __restrict__ sp_rows,
+    const unsigned* __restrict__ desc, int packed, const uint2* __restrict__ st_ranges,
+    const unsigned* __restrict__ seg_first, const unsigned* __restrict__ seg_st,
+    const long long* __restrict__ n_seg, const unsigned* __restrict__ hist,
+    const unsigned* __restrict__ tile_start, const CamTable ct, const float* __restrict__ depth,
+    unsigned* __restrict__ out_vals, unsigned long long* __restrict__ out_keys) {
+  __shared__ unsigned s_run[64];                   // next list slot per tile of the super-tile
+  __shared__ unsigned s_cnt[8][64];                // per-warp counts per tile
+  __shared__ __align__(16) unsigned s_pos[8][64];  // per-warp first slot per tile
+  __shared__ int s_tile[64];                       // global tile id (-1 outside the view)
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const long long G = *n_seg;
@@ -858,73 +923,42 @@ __global__ void __launch_bounds__(256) st_emit_kernel(
       const unsigned i = c0 + tid;
       unsigned d = 0u, row = 0u;
       if (i < si.e) {
-        d = desc[i];
+        d = packed ? (sp_keys[i] >> 16) : desc[i];
         row = sp_rows[i];
       }
-      const int x0 = d & 15u, x1 = (d >> 4) & 15u, y0 = (d >> 8) & 15u, y1 = (d >> 12) & 15u;
-      const bool any = x1 > x0;  // (y1 > y0 too: empty descriptors are 0)
-      unsigned long long mask = 0ull;
-      if (any) {
-        const unsigned long long xb = (unsigned long long)(((1u << x1) - 1u) & ~((1u << x0) - 1u));
-        const unsigned long long ym =
-            (y1 >= 8 ? ~0ull : ((1ull << (8 * y1)) - 1ull)) & ~((1ull << (8 * y0)) - 1ull);
-        mask = (xb * 0x0101010101010101ull) & ym;
-      }
-      // per-warp counts per tile from a 2D difference grid
-      for (int q = lane; q < 81; q += 32) s_d[w][q] = 0;
-      __syncwarp();
-      if (any) {
-        atomicAdd(&s_d[w][y0 * 9 + x0], 1);
-        atomicAdd(&s_d[w][y0 * 9 + x1], -1);
-        atomicAdd(&s_d[w][y1 * 9 + x0], -1);
-        atomicAdd(&s_d[w][y1 * 9 + x1], 1);
-      }
-      __syncwarp();
-      if (lane < 8) {  // prefix along x, row `lane`
-        int run = 0;
-#pragma unroll
-        for (int x = 0; x < 8; ++x) {
-          run += s_d[w][lane * 9 + x];
-          s_d[w][lane * 9 + x] = run;
-        }
-      }
-      __syncwarp();
-      if (lane < 8) {  // prefix along y, column `lane`
-        int run = 0;
-#pragma unroll
-        for (int y = 0; y < 8; ++y) {
-          run += s_d[w][y * 9 + lane];
-          s_d[w][y * 9 + lane] = run;
-        }
-      }
+      unsigned B[8], X[8], n0, n1;
+      rect_ballots(d, B, X);
+      lane_tile_counts(B, X, lane, n0, n1);
+      s_cnt[w][lane] = n0;
+      s_cnt[w][lane + 32] = n1;
       __syncthreads();
       if (tid < 64) {
         unsigned run = s_run[tid];
-        const int cell = (tid >> 3) * 9 + (tid & 7);
 #pragma unroll
         for (int ww = 0; ww < 8; ++ww) {
           s_pos[ww][tid] = run;
-          run += (unsigned)s_d[ww][cell];
+          run += s_cnt[ww][tid];
         }
         s_run[tid] = run;
       }
       __syncthreads();
-      const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)mask);
-      const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(mask >> 32));
+      const unsigned x0 = d & 15u, x1 = (d >> 4) & 15u;
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const unsigned byte = ((r < 4 ? lo : hi) >> (8 * (r & 3))) & 0xffu;
-        if (byte == 0u) continue;  // warp-uniform
+        if (B[r] == 0u) continue;  // warp-uniform
+        const uint4 pa = *reinterpret_cast<const uint4*>(&s_pos[w][8 * r]);
+        const uint4 pb = *reinterpret_cast<const uint4*>(&s_pos[w][8 * r + 4]);
+        const unsigned sp[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+        const bool in_row = (B[r] >> lane) & 1u;
 #pragma unroll
-        for (int x = 0; x < 8; ++x) {
-          const int bt = 8 * r + x;
-          const bool mine = (mask >> bt) & 1ull;
-          const unsigned bal = __ballot_sync(0xffffffffu, mine);
-          if (mine) {
-            const unsigned pos = s_pos[w][bt] + __popc(bal & lt);
+        for (unsigned c = 0; c < 8; ++c) {
+          const unsigned bal = B[r] & X[c];
+          if (bal == 0u) continue;  // warp-uniform
+          if (in_row && x0 <= c && c < x1) {
+            const unsigned pos = sp[c] + __popc(bal & lt);
             out_vals[pos] = row;
             if (out_keys)
-              out_keys[pos] = ((unsigned long long)(unsigned)s_tile[bt] << 32) |
+              out_keys[pos] = ((unsigned long long)(unsigned)s_tile[8 * r + c] << 32) |
                               __float_as_uint(depth[row]);
           }
         }
@@ -1138,6 +1172,11 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
     sv[1] = w.pv;
   }
   const long long q_bound = p_bound;  // Q <= P
+  // the rect descriptors ride in the keys' upper 16 bits when the super-tile
+  // ids fit the lower 16 and every rect end fits the packed field
+  int packed = S <= 65536 ? 1 : 0;
+  for (int v = 0; v < ct.V; ++v)
+    if (ct.c[v].TX > 8000 || ct.c[v].TY > 8000) packed = 0;
   {
     const unsigned g1 = (unsigned)std::min<long long>((n_rows + 255) / 256, 152ll * 32);
     mark_block_starts_kernel<<<g1, 256, 0, st>>>(w.rect_sorted, n_vis, w.offsets, q_eff,
@@ -1145,7 +1184,8 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
     const unsigned g2 = (unsigned)((q_bound + kDupPairs - 1) / kDupPairs);
     const int vec16 = (reinterpret_cast<uintptr_t>(sv[0]) % 16 == 0) ? 1 : 0;
     duplicate_kernel<<<g2, kDupThreads, 0, st>>>(rows_sorted, w.rect_sorted, n_vis, w.offsets, N,
-                                                ct, q_eff, w.block_row, sk[0], sv[0], vec16);
+                                                ct, q_eff, w.block_row, sk[0], sv[0], vec16,
+                                                packed);
     count_launches(2);
   }
   // 5. stable sort of the super-pairs by super-tile id
@@ -1156,19 +1196,21 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
   // 6. rows of every super-tile, segments, per-tile counts and list starts
   GS_TRY_CUDA(cudaMemsetAsync(w.st_ranges, 0, 2 * sizeof(unsigned) * (size_t)S, st));
   const unsigned gq = (unsigned)std::min<long long>((q_bound + 1023) / 1024, 152ll * 16);
-  ranges_kernel<<<gq, 256, 0, st>>>(sp_keys, q_eff, w.st_ranges);
+  ranges_kernel<<<gq, 256, 0, st>>>(sp_keys, q_eff, packed ? 0xffffu : 0xffffffffu, w.st_ranges);
   st_segments_kernel<<<1, 1024, 0, st>>>(reinterpret_cast<const uint2*>(w.st_ranges), S,
                                          w.seg_first, w.seg_st, n_seg);
   const unsigned gs = (unsigned)std::min<long long>(max_segments(q_bound, S), 152ll * 8);
-  st_count_kernel<<<gs, 256, 0, st>>>(sp_rows, reinterpret_cast<const uint2*>(w.st_ranges),
-                                      w.seg_first, w.seg_st, n_seg, proj->rect, N, ct, desc,
+  st_count_kernel<<<gs, 256, 0, st>>>(sp_keys, sp_rows,
+                                      reinterpret_cast<const uint2*>(w.st_ranges), w.seg_first,
+                                      w.seg_st, n_seg, packed, proj->rect, N, ct, desc,
                                       w.seg_hist);
   st_scan_kernel<<<(unsigned)S, 1024, 0, st>>>(w.seg_first, ct, w.seg_hist, w.tile_cnt);
   tile_scan_kernel<<<1, 1024, 0, st>>>(w.tile_cnt, (int)T, w.tile_start, ranges);
   // 7. every row into the lists of the tiles it covers, in depth order
-  st_emit_kernel<<<gs, 256, 0, st>>>(sp_rows, desc, reinterpret_cast<const uint2*>(w.st_ranges),
-                                     w.seg_first, w.seg_st, n_seg, w.seg_hist, w.tile_start, ct,
-                                     proj->depth, sorted_vals, sorted_keys);
+  st_emit_kernel<<<gs, 256, 0, st>>>(sp_keys, sp_rows, desc, packed,
+                                     reinterpret_cast<const uint2*>(w.st_ranges), w.seg_first,
+                                     w.seg_st, n_seg, w.seg_hist, w.tile_start, ct, proj->depth,
+                                     sorted_vals, sorted_keys);
   count_launches(6);
   return check_launch();
 }
