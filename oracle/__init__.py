@@ -14,7 +14,9 @@ marshals numpy arrays through ctypes.
 Functions (all inputs are numpy arrays as produced by ``scenes``):
 
 - ``preprocess``: per-Gaussian projection of one view (Sec. 3).
-- ``build_lists``: per-tile Gaussian lists sorted by (depth key, id).
+- ``build_lists``: per-tile Gaussian lists sorted by (depth key, id), for
+  square tiles of 16 px (3DGS) or 8 px (prm["tile"] = 8: LiteGS and the
+  paper's own runs, Sec. 5 "Effect of tile sizes").
 - ``render_fwd``: compositing, transmittance and per-pixel entropy (Sec. 3,
   Sec. 4.3), with a per-pixel threshold margin.
 - ``render_bwd``: dL/d(2D attributes) from the closed forms (Sec. 4.4,
@@ -101,13 +103,25 @@ def cam_vector(cam) -> np.ndarray:
 
 
 def prm_vector(prm) -> np.ndarray:
-    """Thresholds are FP32 numbers by definition; widen the FP32 values."""
+    """Thresholds are FP32 numbers by definition; widen the FP32 values.
+    The last entry is the tile side in pixels (16 unless prm says 8)."""
     keys = ["alpha_max", "alpha_min", "t_min", "dilation", "near_z", "fov_clamp"]
-    return np.array([np.float32(prm[k]) for k in keys], np.float64)
+    v = [np.float32(prm[k]) for k in keys] + [tile_of(prm)]
+    return np.array(v, np.float64)
 
 
-def tile_grid(cam):
-    return (cam["width"] + TILE - 1) // TILE, (cam["height"] + TILE - 1) // TILE
+def tile_of(prm) -> int:
+    """Tile side in pixels: 16 (3DGS) or 8 (LiteGS and the paper's runs,
+    Sec. 5 "Effect of tile sizes")."""
+    t = int(prm.get("tile", TILE)) if prm is not None else TILE
+    if t not in (8, 16):
+        raise ValueError("tile side must be 8 or 16")
+    return t
+
+
+def tile_grid(cam, prm=None):
+    t = tile_of(prm)
+    return (cam["width"] + t - 1) // t, (cam["height"] + t - 1) // t
 
 
 def preprocess(scene, cam, prm):
@@ -134,6 +148,7 @@ def preprocess(scene, cam, prm):
         "rect_lo": np.zeros((N, 4), np.int32),
         "rect_hi": np.zeros((N, 4), np.int32),
     }
+    out["tile"] = tile_of(prm)
     lib.ora_preprocess(ctypes.c_int(N), _p(means), _p(ls), _p(q), _p(op), _p(sh),
                        ctypes.c_int(Kst), ctypes.c_int(deg), _p(cam_vector(cam)),
                        _p(prm_vector(prm)), _p(out["P9"]), _p(out["depth"]), _p(out["radius"]),
@@ -147,7 +162,7 @@ def build_lists(proj, cam, tile_mask=None):
     tile's ids sorted by (FP32 depth bits, Gaussian id).  tile_mask
     (optional bool [TX*TY]) keeps only the marked tiles' lists."""
     lib = _load()
-    TX, TY = tile_grid(cam)
+    TX, TY = tile_grid(cam, {"tile": proj.get("tile", TILE)})
     rect, tiles, depth = proj["rect"], proj["tiles"], proj["depth"]
     N = rect.shape[0]
     ts = np.zeros(TX * TY + 1, np.int64)

@@ -1,5 +1,5 @@
 /*
- * gs_oracle.c -- plain FP64 CPU oracle for the differentiable 16x16-tile
+ * gs_oracle.c -- plain FP64 CPU oracle for the differentiable square-tile
  * Gaussian rasterizer with the entropy term on blending weights
  * ("Speeding Up the Learning of 3D Gaussians with Much Shorter Gaussian
  * Lists", arXiv 2603.09277).
@@ -38,8 +38,6 @@
 
 typedef double complex cx;
 
-#define TILE 16
-
 /* ------------------------------------------------------------------------ */
 /* Camera and threshold parameters, passed from Python as flat double arrays. */
 /*  cam[0..1]  width, height                                                   */
@@ -48,6 +46,8 @@ typedef double complex cx;
 /*  cam[18..20] camera centre in world space                                   */
 /*  prm[0..5]  alpha_max, alpha_min, t_min, dilation, near_z, fov_clamp        */
 /*             (the FP32 values, widened)                                      */
+/*  prm[6]     tile side in pixels (16 as in 3DGS; 8 as in LiteGS and the      */
+/*             paper's own runs, Sec. 5 "Effect of tile sizes")                */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int W, H;
@@ -57,6 +57,7 @@ typedef struct {
 
 typedef struct {
     double amax, amin, tmin, dil, near_z, fovc;
+    int tile;
 } prm_t;
 
 static cam_t load_cam(const double* c) {
@@ -73,7 +74,7 @@ static cam_t load_cam(const double* c) {
 }
 
 static prm_t load_prm(const double* p) {
-    prm_t q = {p[0], p[1], p[2], p[3], p[4], p[5]};
+    prm_t q = {p[0], p[1], p[2], p[3], p[4], p[5], (int)p[6]};
     return q;
 }
 
@@ -144,11 +145,12 @@ typedef struct {
 } proj_int;
 
 /* Tile rect from the four pixel-space edges mx - r, mx + r, my - r, my + r:
- * the half-open range of 16-pixel tiles whose pixels [16k, 16k + 16) meet
- * [edge0, edge1], clamped to the tile grid. */
-static void rect_of_edges(double l, double r, double t, double b, int TX, int TY, int out[4]) {
-    double x0 = floor(l / TILE), x1 = floor(r / TILE) + 1.0;
-    double y0 = floor(t / TILE), y1 = floor(b / TILE) + 1.0;
+ * the half-open range of tiles (side `tile` px) whose pixels
+ * [tile k, tile k + tile) meet [edge0, edge1], clamped to the tile grid. */
+static void rect_of_edges(double l, double r, double t, double b, int TX, int TY, int tile,
+                          int out[4]) {
+    double x0 = floor(l / tile), x1 = floor(r / tile) + 1.0;
+    double y0 = floor(t / tile), y1 = floor(b / tile) + 1.0;
     x0 = fmin(fmax(x0, 0.0), (double)TX);
     x1 = fmin(fmax(x1, 0.0), (double)TX);
     y0 = fmin(fmax(y0, 0.0), (double)TY);
@@ -245,9 +247,9 @@ static void project_one(const cx mu[3], const cx ls[3], const cx q[4], cx o,
     double lam = mid + sqrt(fmax(mid * mid - detr, 0.0));
     double rf = 3.0 * sqrt(lam);
     double r = ceil(rf);
-    int TX = (c->W + TILE - 1) / TILE, TY = (c->H + TILE - 1) / TILE;
+    int TX = (c->W + p->tile - 1) / p->tile, TY = (c->H + p->tile - 1) / p->tile;
     double mxr = creal(mx), myr = creal(my);
-    rect_of_edges(mxr - r, mxr + r, myr - r, myr + r, TX, TY, pi->rect);
+    rect_of_edges(mxr - r, mxr + r, myr - r, myr + r, TX, TY, p->tile, pi->rect);
     pi->radius = (int)r;
     pi->tiles = (pi->rect[2] - pi->rect[0]) * (pi->rect[3] - pi->rect[1]);
     /* Boundary flag: does a rounding of the radius within EPS_R, or of the
@@ -264,7 +266,7 @@ static void project_one(const cx mu[3], const cx ls[3], const cx q[4], cx o,
                     double f[4] = {e[0], e[1], e[2], e[3]};
                     f[k] += sg * EPS_PX;
                     int r1[4];
-                    rect_of_edges(f[0], f[1], f[2], f[3], TX, TY, r1);
+                    rect_of_edges(f[0], f[1], f[2], f[3], TX, TY, p->tile, r1);
                     if (memcmp(r1, pi->rect, sizeof r1)) pi->boundary = 1;
                     for (int c = 0; c < 2; ++c) {
                         if (r1[c] > pi->rect_lo[c]) pi->rect_lo[c] = r1[c];
@@ -480,12 +482,12 @@ void ora_render_fwd(int W, int H, const long long* tile_start, const int* ids,
                     double* image, double* finalT, int* last, double* entropy,
                     int* nblend, int* neval, double* margin, int* first_near) {
     prm_t p = load_prm(prmv);
-    int TX = (W + TILE - 1) / TILE;
+    int TX = (W + p.tile - 1) / p.tile;
 #pragma omp parallel for schedule(dynamic, 64)
     for (int pix = 0; pix < W * H; ++pix) {
         if (mask && !mask[pix]) continue;
         int u = pix % W, v = pix / W;
-        int tile = (v / TILE) * TX + (u / TILE);
+        int tile = (v / p.tile) * TX + (u / p.tile);
         double C[3], T, Hv, mg;
         int lst, ne, fn;
         int nb = walk_pixel(u + 0.5, v + 0.5, ids, tile_start[tile], tile_start[tile + 1], P9, &p,
@@ -583,9 +585,9 @@ void ora_render_bwd(int W, int H, const long long* tile_start, const int* ids,
                     const double* P9, const double* prmv, const unsigned char* mask,
                     const double* dL_dC, const double* dL_dH, double* grad9) {
     prm_t p = load_prm(prmv);
-    int TX = (W + TILE - 1) / TILE;
+    int TX = (W + p.tile - 1) / p.tile;
     long long maxlen = 0;
-    int TY = (H + TILE - 1) / TILE;
+    int TY = (H + p.tile - 1) / p.tile;
     for (int t = 0; t < TX * TY; ++t)
         if (tile_start[t + 1] - tile_start[t] > maxlen) maxlen = tile_start[t + 1] - tile_start[t];
 #pragma omp parallel
@@ -596,7 +598,7 @@ void ora_render_bwd(int W, int H, const long long* tile_start, const int* ids,
         for (int pix = 0; pix < W * H; ++pix) {
             if (mask && !mask[pix]) continue;
             int u = pix % W, v = pix / W;
-            int tile = (v / TILE) * TX + (u / TILE);
+            int tile = (v / p.tile) * TX + (u / p.tile);
             double C[3], Tf, Hv, mg;
             int lst, ne, fn;
             int n = walk_pixel(u + 0.5, v + 0.5, ids, tile_start[tile], tile_start[tile + 1], P9,

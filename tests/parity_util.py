@@ -73,10 +73,10 @@ def view_pixels(cams):
     return out
 
 
-def view_tiles(cams):
+def view_tiles(cams, tile=16):
     out, off = [], 0
     for c in cams:
-        tx, ty = oracle.tile_grid(c)
+        tx, ty = oracle.tile_grid(c, {"tile": tile})
         out.append((off, off + tx * ty))
         off += tx * ty
     return out
@@ -86,7 +86,8 @@ def pixel_exclusion(ora_view, cam, margin=MARGIN):
     """Boolean [H,W]: pixels left out of the pixel checks of one view."""
     proj, fwd = ora_view["proj"], ora_view["fwd"]
     W, H = cam["width"], cam["height"]
-    TX, TY = oracle.tile_grid(cam)
+    T = proj.get("tile", 16)
+    TX, TY = oracle.tile_grid(cam, {"tile": T})
     bad_tiles = np.zeros((TY, TX), bool)
     amin = float(np.float32(1.0 / 255))
     for i in np.nonzero(proj["boundary"])[0]:
@@ -101,25 +102,26 @@ def pixel_exclusion(ora_view, cam, margin=MARGIN):
         # (elsewhere it is skipped whether or not it is listed)
         g = proj["P9"][i]
         for ty, tx in zip(*np.nonzero(m)):
-            u = np.arange(tx * 16, min(W, tx * 16 + 16)) + 0.5 - g[0]
-            v = np.arange(ty * 16, min(H, ty * 16 + 16)) + 0.5 - g[1]
+            u = np.arange(tx * T, min(W, tx * T + T)) + 0.5 - g[0]
+            v = np.arange(ty * T, min(H, ty * T + T)) + 0.5 - g[1]
             du, dv = np.meshgrid(u, v)
             a = g[5] * np.exp(-0.5 * (g[2] * du * du + 2 * g[3] * du * dv + g[4] * dv * dv))
             if a.max() >= amin * (1 - margin):
                 bad_tiles[ty, tx] = True
-    px_tiles = bad_tiles[np.arange(H)[:, None] // 16, np.arange(W)[None, :] // 16]
+    px_tiles = bad_tiles[np.arange(H)[:, None] // T, np.arange(W)[None, :] // T]
     return px_tiles | (fwd["margin"] < margin)
 
 
-def last_ids_gpu(g, cams, v, N):
+def last_ids_gpu(g, cams, v, N, tile_px=16):
     """Row id of each pixel's last blended entry (-1 if none), GPU side."""
     a, b = view_pixels(cams)[v]
-    t0 = view_tiles(cams)[v][0]
+    t0 = view_tiles(cams, tile_px)[v][0]
     cam = cams[v]
     W, H = cam["width"], cam["height"]
-    TX = (W + 15) // 16
+    T = tile_px
+    TX = (W + T - 1) // T
     yy, xx = np.divmod(np.arange(W * H), W)
-    tile = t0 + (yy // 16) * TX + xx // 16
+    tile = t0 + (yy // T) * TX + xx // T
     last = g["last"][a:b]
     start = g["ranges"][tile, 0]
     out = np.full(W * H, -1, np.int64)
@@ -132,9 +134,10 @@ def last_ids_oracle(view, cam):
     """Gaussian id of each pixel's last blended entry (-1 if none), oracle side."""
     ts, ids = view["lists"]
     W, H = cam["width"], cam["height"]
-    TX = (W + 15) // 16
+    T = view["proj"].get("tile", 16)
+    TX = (W + T - 1) // T
     yy, xx = np.divmod(np.arange(W * H), W)
-    tile = (yy // 16) * TX + xx // 16
+    tile = (yy // T) * TX + xx // T
     last = view["fwd"]["last"].reshape(-1)
     out = np.full(W * H, -1, np.int64)
     has = last > 0
@@ -153,12 +156,13 @@ def gaussian_exclusion(ora_view, cam, bad_pixels):
     Gaussian of visible alpha, the whole list."""
     proj, fwd = ora_view["proj"], ora_view["fwd"]
     ts, ids = ora_view["lists"]
-    TX, TY = oracle.tile_grid(cam)
+    T = proj.get("tile", 16)
+    TX, TY = oracle.tile_grid(cam, {"tile": T})
     bad = proj["boundary"].astype(bool).copy()
     margin_bad = fwd["margin"] < MARGIN
     ys, xs = np.nonzero(bad_pixels)
     for y, x in zip(ys, xs):
-        t = (y // 16) * TX + x // 16
+        t = (y // T) * TX + x // T
         fn = int(fwd["first_near"][y, x])
         if margin_bad[y, x] and fn >= 0:
             bad[ids[ts[t] + fn:min(ts[t + 1], ts[t] + fn + 3)]] = True

@@ -150,9 +150,10 @@ def test_isotropic_on_axis_closed_form():
     TX = W // 16
     x0, y0, x1, y1 = proj["rect"][0]
     amin, amax = float(np.float32(1 / 255)), float(np.float32(0.99))
+    side = oracle.tile_of(prm)
     for v in range(H):
         for u in range(W):
-            tx, ty = u // 16, v // 16
+            tx, ty = u // side, v // side
             inside = x0 <= tx < x1 and y0 <= ty < y1
             d2 = (u + 0.5 - W / 2) ** 2 + (v + 0.5 - H / 2) ** 2
             a = min(amax, sigma * math.exp(-d2 / (2 * sig_px ** 2)))
@@ -293,9 +294,10 @@ def _brute_force(proj, cam, prm):
     Tf = np.ones((H, W))
     Hm = np.zeros((H, W))
     last = np.zeros((H, W), np.int32)
+    side = oracle.tile_of(prm)
     for v in range(H):
         for u in range(W):
-            tx, ty = u // 16, v // 16
+            tx, ty = u // side, v // side
             cand = [i for i in range(len(tiles)) if tiles[i] > 0 and rect[i, 0] <= tx < rect[i, 2]
                     and rect[i, 1] <= ty < rect[i, 3]]
             cand.sort(key=lambda i: (depth[i], i))
@@ -319,9 +321,10 @@ def _brute_force(proj, cam, prm):
     return img, Tf, Hm, last
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
-def test_tiled_equals_brute_force(seed):
+@pytest.mark.parametrize("seed,tile", [(0, 16), (1, 16), (2, 16), (3, 8), (4, 8)])
+def test_tiled_equals_brute_force(seed, tile):
     scene, cams, _, prm = scenes.tiny_scene(8, seed=seed, width=48, height=40)
+    prm["tile"] = tile
     scene["opacity_logits"][:] = 3.0  # long enough to reach the T stop
     cam = cams[0]
     proj = oracle.preprocess(scene, cam, prm)
@@ -390,6 +393,42 @@ def test_full_gradient_matches_finite_differences(seed, deg):
     scene, cams, targets, prm = scenes.tiny_scene(6, seed=seed, width=32, height=32,
                                                   sh_degree=deg)
     assert _fd_check(scene, cams, targets, prm) > 50
+
+
+def test_full_gradient_matches_finite_differences_8px_tiles():
+    scene, cams, targets, prm = scenes.tiny_scene(6, seed=4, width=32, height=32, sh_degree=1)
+    prm["tile"] = 8
+    assert _fd_check(scene, cams, targets, prm) > 50
+
+
+def test_rect_8px_tiles_from_mean_and_radius(cfg1):
+    """With 8-pixel tiles the rect is the range of 8-pixel tiles that the
+    square [mean - r, mean + r] meets, clamped to the grid (the 3-sigma
+    rule of Sec. 3 with the tile side of the paper's runs), and it lies
+    inside the 16-pixel rect at twice the resolution."""
+    scene, cams, targets, prm, proj16, lists, fwd = cfg1
+    cam = cams[0]
+    prm8 = dict(prm, tile=8)
+    proj8 = oracle.preprocess(scene, cam, prm8)
+    TX, TY = oracle.tile_grid(cam, prm8)
+    assert (TX, TY) == ((cam["width"] + 7) // 8, (cam["height"] + 7) // 8)
+    ok = (proj8["tiles"] > 0) & (proj8["boundary"] == 0)
+    mx, my = proj8["P9"][ok, 0], proj8["P9"][ok, 1]
+    r = proj8["radius"][ok].astype(np.float64)
+    exp = np.stack([np.clip(np.floor((mx - r) / 8), 0, TX), np.clip(np.floor((my - r) / 8), 0, TY),
+                    np.clip(np.floor((mx + r) / 8) + 1, 0, TX),
+                    np.clip(np.floor((my + r) / 8) + 1, 0, TY)], 1).astype(np.int64)
+    assert (proj8["rect"][ok] == exp).all()
+    # the radius and the projected attributes do not depend on the tiling
+    assert (proj8["radius"] == proj16["radius"]).all()
+    assert np.array_equal(proj8["P9"], proj16["P9"])
+    both = ok & (proj16["boundary"] == 0) & (proj16["tiles"] > 0)
+    r8, r16 = proj8["rect"][both], proj16["rect"][both]
+    assert (r8[:, :2] >= 2 * r16[:, :2]).all() and (r8[:, 2:] <= 2 * r16[:, 2:]).all()
+    # lists: every Gaussian in exactly tiles_touched 8-pixel lists
+    ts, ids = oracle.build_lists(proj8, cam)
+    assert len(ts) == TX * TY + 1
+    assert (np.bincount(ids, minlength=proj8["tiles"].size) == proj8["tiles"]).all()
 
 
 def test_gradient_fd_rotated_camera_and_fov_clamp():
