@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the comparison of launch forms and staging precisions")
     ap.add_argument("--ppt", type=int, default=0, help="pixels per thread of the blending kernels")
+    ap.add_argument("--tile", type=int, default=16, choices=[16, 8],
+                    help="tile side in pixels (16: 3DGS; 8: LiteGS and the paper's runs)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use --ppt/--persistent as given instead of the autotuned launch form")
     ap.add_argument("--sweep", action="store_true",
@@ -205,6 +207,7 @@ def run_reference(args):
     import oracle
     oracle.build()
     (scene, cams, targets, prm), wl = workload(args.config, 0, args.n)
+    prm["tile"] = args.tile
     from paper_2603_09277_gb300 import scenes
     for _ in range(args.warmup):
         oracle_sample(scene, cams, targets, prm, scenes.GAMMA, args.ref_band_rows)
@@ -426,6 +429,9 @@ def main():
         return
 
     (scene, cams, targets, prm), wl = workload(args.config, rank, args.n)
+    prm["tile"] = args.tile
+    if args.tile != 16:
+        wl += ", %dx%d tiles" % (args.tile, args.tile)
     N = scene["means"].shape[0]
     p = scene_to_device(scene, dev)
     tgt = targets_to_device(targets, dev)
@@ -653,9 +659,10 @@ def main():
             "config": {"workload": wl, "N": N, "views": len(cams), "pairs": P,
                        "blended_pairs": nb_step, "evaluated_pairs": ne_step,
                        "bwd_evaluated_pairs": bwd_eval, "attr_dtype": args.attr,
+                       "tile": args.tile,
                        "launch": ("persistent %d CTAs over the list-length queue"
                                   % form["persistent"] if form["persistent"]
-                                  else "one CTA per 16x16 tile")
+                                  else "one CTA per %dx%d tile" % (args.tile, args.tile))
                        + ", %d px/thread" % (form["pixels_per_thread"] or 2),
                        "autotune_ms": tuned,
                        "l2": "flushed (256 MB write) before every timed step",

@@ -53,7 +53,7 @@ enum gs_status {
  * only; exponent, transmittance and every accumulation stay FP32). */
 enum gs_attr_dtype { GS_ATTR_F32 = 0, GS_ATTR_F16 = 1, GS_ATTR_BF16 = 2 };
 
-#define GS_TILE 16
+#define GS_TILE 16 /* default tile side in pixels; 8 is the other supported side */
 #define GS_MAX_VIEWS 64
 #define GS_SH_COEFFS_MAX 16
 
@@ -79,6 +79,9 @@ typedef struct {
     int sh_degree;  /* degree in use, 0..3 */
     int sh_stride;  /* SH coefficients stored per Gaussian, >= (sh_degree+1)^2, <= 16 */
     int attr_dtype; /* enum gs_attr_dtype */
+    int tile_size;  /* tile side in pixels: 16 (3DGS; 0 also means 16) or 8 (LiteGS and the
+                       paper's own runs, Sec. 5 "Effect of tile sizes"); every call of one
+                       pipeline must use the same side */
 } gs_params;
 
 /* Projected per-(view, Gaussian) attributes, V*N rows, device memory. */
@@ -117,8 +120,9 @@ typedef struct {
  * F16/BF16); -1 for an unknown dtype. */
 int gs_record_bytes(int attr_dtype);
 
-/* Total number of 16x16 tiles over the V views (host cams), or -1. */
-long long gs_total_tiles(const gs_camera* cams_host, int V);
+/* Total number of tiles of side tile_size (16 or 8; 0 means 16) over the V
+ * views (host cams), or -1. */
+long long gs_total_tiles(const gs_camera* cams_host, int V, int tile_size);
 
 /* Total pixels over the V views, or -1. */
 long long gs_total_pixels(const gs_camera* cams_host, int V);
@@ -169,6 +173,7 @@ int gs_preprocess(const float* means, const float* log_scales, const float* quat
  * (tile << 32) | depth_bits with ties by Gaussian id; tile_ranges[2t],
  * tile_ranges[2t+1] = [start, end) of tile t in sorted_vals (0, 0 if empty).
  *   proj: output of gs_preprocess (depth, rect, tiles_touched are read).
+ *   tile_size: the tile side gs_preprocess used (prm->tile_size).
  *   workspace: device, >= gs_bin_sort_workspace_size(V*N, pair_capacity,
  *   total_tiles) bytes, 256-B aligned.
  *   sorted_vals [pair_capacity], tile_ranges [2*total_tiles], num_pairs_dev [1],
@@ -180,13 +185,13 @@ int gs_preprocess(const float* means, const float* log_scales, const float* quat
  *   graph capture) nothing is synchronised; on overflow the device writes
  *   *status_dev = GS_ERR_CAPACITY, keeps P in *num_pairs_dev, empties every
  *   range, and the caller regrows and reruns. */
-int gs_bin_sort(const gs_proj* proj, int N, const gs_camera* cams_host, int V,
+int gs_bin_sort(const gs_proj* proj, int N, const gs_camera* cams_host, int V, int tile_size,
                 void* workspace, size_t workspace_bytes, long long pair_capacity,
                 unsigned* sorted_vals, unsigned long long* sorted_keys, unsigned* tile_ranges,
                 long long* num_pairs_dev, long long* num_pairs_host, int* status_dev,
                 gs_stream stream);
 
-/* Front-to-back alpha blending per 16x16 tile (Sec. 3) with the entropy of
+/* Front-to-back alpha blending per tile (16x16 or 8x8 pixels, Sec. 3) with the entropy of
  * the blending weights (Sec. 4.3).  Per pixel, over its tile's list:
  *   alpha = min(alpha_max, sigma exp(d)); entries with alpha < alpha_min are
  *   skipped; the walk stops before blending an entry with

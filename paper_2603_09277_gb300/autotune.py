@@ -27,9 +27,15 @@ CANDIDATES = [
 ]
 
 
-def signature(cams, N, attr_dtype):
+def signature(cams, N, attr_dtype, tile=16):
     views = ",".join("%dx%d" % (c["width"], c["height"]) for c in cams)
-    return "%s|N=%d|%s|%s" % (views, N, attr_dtype, torch.cuda.get_device_name())
+    return "%s|N=%d|%s|tile=%d|%s" % (views, N, attr_dtype, tile, torch.cuda.get_device_name())
+
+
+def candidates(tile=16):
+    """Launch forms to try; 8-pixel tiles take 1 or 2 pixels per thread (a
+    CTA of one tile must hold at least one full warp)."""
+    return [f for f in CANDIDATES if tile == 16 or f["pixels_per_thread"] <= 2]
 
 
 def _load():
@@ -72,20 +78,22 @@ def time_form(cams, prm, params, target, gamma, form, attr_dtype="f32", steps=5,
 
 def tune(cams, prm, params, target, gamma, attr_dtype="f32", force=False, steps=5):
     """Returns (best form dict, {form: ms}) and caches the choice."""
-    key = signature(cams, params["means"].shape[0], attr_dtype)
+    tile = int(prm.get("tile", 16))
+    key = signature(cams, params["means"].shape[0], attr_dtype, tile)
     db = _load()
     if not force and key in db:
         return db[key]["best"], db[key]["ms"]
     times = {}
-    for form in CANDIDATES:
+    cands = candidates(tile)
+    for form in cands:
         name = "ppt%d_%s" % (form["pixels_per_thread"],
                              "persistent" if form["persistent"] else "per_tile")
         times[name] = time_form(cams, prm, params, target, gamma, form, attr_dtype, steps)
         torch.cuda.empty_cache()
     best_name = min(times, key=times.get)
-    best = CANDIDATES[[("ppt%d_%s" % (f["pixels_per_thread"],
-                                       "persistent" if f["persistent"] else "per_tile"))
-                       for f in CANDIDATES].index(best_name)]
+    best = cands[[("ppt%d_%s" % (f["pixels_per_thread"],
+                                  "persistent" if f["persistent"] else "per_tile"))
+                  for f in cands].index(best_name)]
     db[key] = {"best": best, "ms": times, "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
     _store(db)
     return best, times

@@ -74,10 +74,13 @@ int check_launch() {
   return e == cudaSuccess ? GS_OK : set_cuda_error(e);
 }
 
-bool build_cam_table(const gs_camera* cams, int V, const gs_params* prm, CamTable* ct) {
+bool build_cam_table(const gs_camera* cams, int V, const gs_params* prm, int tile, CamTable* ct) {
   if (!cams || V < 1 || V > GS_MAX_VIEWS) return false;
+  if (tile == 0) tile = kTile;
+  if (tile != 16 && tile != 8) return false;
   memset(ct, 0, sizeof(*ct));
   ct->V = V;
+  ct->tile = tile;
   long long tiles = 0, pix = 0, sts = 0;
   const float fovc = prm ? prm->fov_clamp : 1.3f;
   for (int v = 0; v < V; ++v) {
@@ -93,8 +96,8 @@ bool build_cam_table(const gs_camera* cams, int V, const gs_params* prm, CamTabl
     d.limx = fovc * (0.5f * (float)c.width / c.fx);
     d.limy = fovc * (0.5f * (float)c.height / c.fy);
     d.W = c.width; d.H = c.height;
-    d.TX = (c.width + kTile - 1) / kTile;
-    d.TY = (c.height + kTile - 1) / kTile;
+    d.TX = (c.width + tile - 1) / tile;
+    d.TY = (c.height + tile - 1) / tile;
     d.STX = (d.TX + kSuperTile - 1) / kSuperTile;
     d.STY = (d.TY + kSuperTile - 1) / kSuperTile;
     d.st_off = (int)sts;
@@ -131,6 +134,7 @@ bool params_ok(const gs_params* p) {
   if (!(p->alpha_min > 0.f && p->alpha_min < p->alpha_max)) return false;
   if (!(p->t_min > 0.f && p->t_min < 1.f)) return false;
   if (!(p->dilation >= 0.f) || !(p->near_z > 0.f) || !(p->fov_clamp > 0.f)) return false;
+  if (p->tile_size != 0 && p->tile_size != 8 && p->tile_size != 16) return false;
   return true;
 }
 
@@ -236,15 +240,15 @@ int gs_record_bytes(int attr_dtype) {
   return -1;
 }
 
-long long gs_total_tiles(const gs_camera* cams, int V) {
+long long gs_total_tiles(const gs_camera* cams, int V, int tile_size) {
   CamTable ct;
-  if (!build_cam_table(cams, V, nullptr, &ct)) return -1;
+  if (!build_cam_table(cams, V, nullptr, tile_size, &ct)) return -1;
   return ct.total_tiles;
 }
 
 long long gs_total_pixels(const gs_camera* cams, int V) {
   CamTable ct;
-  if (!build_cam_table(cams, V, nullptr, &ct)) return -1;
+  if (!build_cam_table(cams, V, nullptr, 0, &ct)) return -1;
   return ct.c[V - 1].pix_off + (long long)ct.c[V - 1].W * ct.c[V - 1].H;
 }
 
@@ -285,7 +289,7 @@ int gs_preprocess(const float* means, const float* log_scales, const float* quat
   if (N < 0) return invalid("N < 0");
   if (!params_ok(prm)) return invalid("params");
   CamTable ct;
-  if (!build_cam_table(cams, V, prm, &ct)) return invalid("cameras");
+  if (!build_cam_table(cams, V, prm, prm->tile_size, &ct)) return invalid("cameras");
   if ((long long)N * V >= (1ll << 32)) return invalid("V*N must be < 2^32");
   if (!proj_ok(out, true)) return invalid("projection buffers (NULL or misaligned)");
   if (N > 0 && (!means || !log_scales || !quats || !opacity_logits || !sh))
@@ -295,13 +299,15 @@ int gs_preprocess(const float* means, const float* log_scales, const float* quat
                            (cudaStream_t)stream);
 }
 
-int gs_bin_sort(const gs_proj* proj, int N, const gs_camera* cams, int V, void* workspace,
+int gs_bin_sort(const gs_proj* proj, int N, const gs_camera* cams, int V, int tile_size,
+                void* workspace,
                 size_t workspace_bytes, long long pair_capacity, unsigned* sorted_vals,
                 unsigned long long* sorted_keys, unsigned* tile_ranges, long long* num_pairs_dev,
                 long long* num_pairs_host, int* status_dev, gs_stream stream) {
   if (N < 0) return invalid("N < 0");
   CamTable ct;
-  if (!build_cam_table(cams, V, nullptr, &ct)) return invalid("cameras");
+  if (tile_size != 0 && tile_size != 8 && tile_size != 16) return invalid("tile_size (8 or 16)");
+  if (!build_cam_table(cams, V, nullptr, tile_size, &ct)) return invalid("cameras");
   if (!proj_ok(proj, false)) return invalid("projection buffers");
   if (pair_capacity < 0 || pair_capacity >= (1ll << 32)) return invalid("pair_capacity");
   if (!tile_ranges || !num_pairs_dev || !status_dev) return invalid("output pointers");
@@ -321,7 +327,7 @@ int gs_render_fwd(const gs_proj* proj, int N, const gs_camera* cams, int V, cons
   if (N < 0) return invalid("N < 0");
   if (!params_ok(prm)) return invalid("params");
   CamTable ct;
-  if (!build_cam_table(cams, V, prm, &ct)) return invalid("cameras");
+  if (!build_cam_table(cams, V, prm, prm->tile_size, &ct)) return invalid("cameras");
   if (!proj_ok(proj, true)) return invalid("projection buffers");
   if (!tile_ranges || !image || !final_T || !last_idx) return invalid("output pointers");
   if (!aligned(tile_ranges, 8)) return invalid("tile_ranges must be 8-byte aligned");
@@ -335,7 +341,7 @@ int gs_loss_l1_entropy(const float* image, const float* target, const float* ent
                        float* dL_dimage, float* dL_dentropy, void* workspace,
                        size_t workspace_bytes, gs_stream stream) {
   CamTable ct;
-  if (!build_cam_table(cams, V, nullptr, &ct)) return invalid("cameras");
+  if (!build_cam_table(cams, V, nullptr, 0, &ct)) return invalid("cameras");
   long long P = ct.c[V - 1].pix_off + (long long)ct.c[V - 1].W * ct.c[V - 1].H;
   if (!image || !target || !loss_dev || !dL_dimage) return invalid("pointers");
   if (gamma != 0.f && !entropy) return invalid("entropy is required when gamma != 0");
@@ -370,7 +376,7 @@ int gs_render_bwd(const gs_proj* proj, int N, const gs_camera* cams, int V, cons
   if (N < 0) return invalid("N < 0");
   if (!params_ok(prm)) return invalid("params");
   CamTable ct;
-  if (!build_cam_table(cams, V, prm, &ct)) return invalid("cameras");
+  if (!build_cam_table(cams, V, prm, prm->tile_size, &ct)) return invalid("cameras");
   if (!proj_ok(proj, true)) return invalid("projection buffers");
   if (!tile_ranges || !final_T || !last_idx || !dL_dimage) return invalid("forward outputs");
   if (!grad2d || !aligned(grad2d, 16)) return invalid("grad2d (NULL or not 16-B aligned)");

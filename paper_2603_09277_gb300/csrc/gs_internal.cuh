@@ -13,8 +13,7 @@
 
 namespace gs {
 
-constexpr int kTile = GS_TILE;               // 16x16 pixel tiles
-constexpr int kTilePix = kTile * kTile;      // 256 pixels per tile
+constexpr int kTile = GS_TILE;               // default tile side (16 px; 8 also supported)
 constexpr int kSuperTile = 8;                // binning groups 8x8 tiles into a super-tile
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
@@ -35,6 +34,7 @@ struct CamInfo {
 
 struct CamTable {
   int V;
+  int tile;  // tile side in pixels (16 or 8)
   int total_tiles;
   int total_st;  // super-tiles over all views
   CamInfo c[GS_MAX_VIEWS];
@@ -212,7 +212,8 @@ int set_cuda_error(cudaError_t e);
 int set_error_text_and_status(const char* msg, int status);
 void count_launches(int n);
 int check_launch();
-bool build_cam_table(const gs_camera* cams, int V, const gs_params* prm, CamTable* ct);
+// tile: the tile side (0 means 16); fov_clamp comes from prm (1.3 if NULL).
+bool build_cam_table(const gs_camera* cams, int V, const gs_params* prm, int tile, CamTable* ct);
 RenderConsts render_consts(const gs_params* prm);
 }  // namespace gs
 

@@ -337,10 +337,10 @@ __global__ void __launch_bounds__(256) preprocess_kernel(
       float hd = 0.5f * (p.A - p.C);
       float lam = 0.5f * (p.A + p.C) + sqrtf(hd * hd + p.B * p.B);
       r = ceilf(3.f * sqrtf(lam));
-      const float inv16 = 1.f / kTile;
+      const float inv_tile = 1.f / (float)ct.tile;  // exact: the side is a power of two
       const float mx = p.mx.hi, my = p.my.hi;
-      float fx0 = floorf((mx - r) * inv16), fx1 = floorf((mx + r) * inv16) + 1.f;
-      float fy0 = floorf((my - r) * inv16), fy1 = floorf((my + r) * inv16) + 1.f;
+      float fx0 = floorf((mx - r) * inv_tile), fx1 = floorf((mx + r) * inv_tile) + 1.f;
+      float fy0 = floorf((my - r) * inv_tile), fy1 = floorf((my + r) * inv_tile) + 1.f;
       x0 = (int)fminf(fmaxf(fx0, 0.f), (float)c.TX);
       x1 = (int)fminf(fmaxf(fx1, 0.f), (float)c.TX);
       y0 = (int)fminf(fmaxf(fy0, 0.f), (float)c.TY);

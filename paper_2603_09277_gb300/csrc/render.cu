@@ -1,9 +1,11 @@
 // render.cu -- per-tile front-to-back blending with the weight entropy
 // (forward) and its reverse-order adjoint with Algorithm 1 fused in.
 //
-// One CTA owns one 16x16 tile.  A thread owns PPT (1, 2 or 4) vertically
-// adjacent pixels of one column, so a warp covers a 16 x (2 PPT) block and the
-// column-dependent part of every exponent is shared by the thread's pixels.
+// One CTA owns one tile of TS x TS pixels (TS = 16, or 8 as in the paper's
+// runs).  A thread owns PPT (1, 2 or 4; 1 or 2 for 8x8 tiles) vertically
+// adjacent pixels of one column, so a warp covers a TS x (32 / TS) PPT block
+// and the column-dependent part of every exponent is shared by the thread's
+// pixels.
 // The tile's list is streamed through shared memory in batches of 256
 // records (gathered with 16-byte vector loads) and every thread walks the
 // batch from shared memory (warp-broadcast reads).  The forward stops a CTA
@@ -38,15 +40,15 @@
 namespace gs {
 namespace {
 
-constexpr int kBatch = kTilePix;  // 256 records per staging batch
+constexpr int kBatch = 256;  // records per staging batch
 constexpr unsigned kFull = 0xffffffffu;
 // A row coordinate this far from every mean makes the exponent -inf (f22 > 0),
 // so a finished or outside pixel never passes the alpha_min test again.
 constexpr float kFar = 1e30f;
 
-template <int PPT>
+template <int TS, int PPT>
 struct TileGeom {
-  static constexpr int kThreads = kTilePix / PPT;
+  static constexpr int kThreads = TS * TS / PPT;
   int view;
   long long pix0;   // global index of the thread's first pixel
   int W;            // view width (pixel stride of a row)
@@ -58,28 +60,28 @@ struct TileGeom {
   unsigned rows;    // bit r: tile row r lies in the image
 };
 
-template <int PPT>
-__device__ __forceinline__ TileGeom<PPT> tile_geom(const CamTable& ct, int tile) {
-  TileGeom<PPT> g;
+template <int TS, int PPT>
+__device__ __forceinline__ TileGeom<TS, PPT> tile_geom(const CamTable& ct, int tile) {
+  TileGeom<TS, PPT> g;
   g.view = find_view_of_tile(ct, tile);
   const CamInfo& c = ct.c[g.view];
   const int local = tile - c.tile_off;
   const int tx = local % c.TX, ty = local / c.TX;
-  const int lx = threadIdx.x & (kTile - 1);
-  const int ly0 = (threadIdx.x >> 4) * PPT;
-  const int px = tx * kTile + lx, py0 = ty * kTile + ly0;
+  const int lx = threadIdx.x & (TS - 1);
+  const int ly0 = (threadIdx.x / TS) * PPT;
+  const int px = tx * TS + lx, py0 = ty * TS + ly0;
   g.W = c.W;
   g.pix0 = c.pix_off + (long long)py0 * c.W + px;
-  g.ox = (float)(tx * kTile);
-  g.oy = (float)(ty * kTile);
+  g.ox = (float)(tx * TS);
+  g.oy = (float)(ty * TS);
   g.rx = (float)lx + 0.5f;
   g.ry0 = (float)ly0 + 0.5f;
   g.inside = 0u;
 #pragma unroll
   for (int k = 0; k < PPT; ++k)
     if (px < c.W && py0 + k < c.H) g.inside |= 1u << k;
-  g.xmax = (float)(min(kTile, c.W - tx * kTile) - 1) + 0.5f;
-  const int nrow = min(kTile, c.H - ty * kTile);
+  g.xmax = (float)(min(TS, c.W - tx * TS) - 1) + 0.5f;
+  const int nrow = min(TS, c.H - ty * TS);
   g.rows = (1u << nrow) - 1u;
   return g;
 }
@@ -93,6 +95,7 @@ __device__ __forceinline__ TileGeom<PPT> tile_geom(const CamTable& ct, int tile)
 // on the FP32 rounding of this test and of the per-pixel exponent (32 times
 // the first-order estimate), so a row left out holds no pixel the per-pixel
 // test would blend, and skipping it leaves every output unchanged.
+template <int TS>
 __device__ __forceinline__ unsigned splat_rows(float mx, float my, float f11, float f21, float f22,
                                                float L2S, float log2_amin, float xmax,
                                                unsigned rows) {
@@ -101,13 +104,14 @@ __device__ __forceinline__ unsigned splat_rows(float mx, float my, float f11, fl
   const float rho = sqrtf(rho2);
   const float x0 = 0.5f - mx, x1 = xmax - mx;
   const float X =
-      (fabsf(f11) + fabsf(f21)) * (16.f + fabsf(mx)) + fabsf(f22) * (16.f + fabsf(my)) + rho;
+      (fabsf(f11) + fabsf(f21)) * ((float)TS + fabsf(mx)) + fabsf(f22) * ((float)TS + fabsf(my)) +
+      rho;
   const float lim = rho2 + 0x1p-18f * (rho * X + rho2 + 8.f);
   const float a = __fmaf_rn(f11, f11, f21 * f21);
   const float k = -f21 * f22 / a;  // stationary x of row dy is k dy
   unsigned m = 0u;
 #pragma unroll 4
-  for (int r = 0; r < kTile; ++r) {
+  for (int r = 0; r < TS; ++r) {
     const float dy = ((float)r + 0.5f) - my;
     const float dx = fminf(fmaxf(k * dy, x0), x1);
     const float pv = f11 * dx;
@@ -119,11 +123,12 @@ __device__ __forceinline__ unsigned splat_rows(float mx, float my, float f11, fl
 
 // Builds the warp's list of staged entries (ascending) whose rows mask meets
 // the warp's rows; returns its length.
-template <int PPT>
+template <int TS, int PPT>
 __device__ __forceinline__ int warp_entries(const unsigned short* s_rows, unsigned char* list,
                                             int cnt, int lane, int warp) {
-  constexpr unsigned kBand = (1u << (2 * PPT)) - 1u;
-  const unsigned band = kBand << (warp * 2 * PPT);
+  constexpr int kRows = (32 / TS) * PPT;  // tile rows of one warp
+  constexpr unsigned kBand = (1u << kRows) - 1u;
+  const unsigned band = kBand << (warp * kRows);
   const unsigned below = (1u << lane) - 1u;
   int n = 0;
   for (int c = 0; c < cnt; c += 32) {
@@ -150,19 +155,20 @@ struct FwdArgs {
   unsigned long long* stats;
 };
 
-template <int DT, int PPT, bool STATS>
+template <int DT, int TS, int PPT, bool STATS>
 __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts& rc,
                                          const FwdArgs& a, int tile, unsigned long long& n_bl,
                                          unsigned long long& n_ev) {
-  constexpr int NT = TileGeom<PPT>::kThreads;
+  constexpr int NT = TileGeom<TS, PPT>::kThreads;
   constexpr int NW = NT / 32;
+  static_assert(NW >= 1, "a tile needs at least one full warp");
   __shared__ float4 s0[kBatch];
   __shared__ float4 s1[kBatch];
   __shared__ float s2[kBatch];
   __shared__ unsigned short s_rows[kBatch];
   __shared__ unsigned char s_list[NW][kBatch];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const TileGeom<PPT> tg = tile_geom<PPT>(ct, tile);
+  const TileGeom<TS, PPT> tg = tile_geom<TS, PPT>(ct, tile);
   const uint2 r = a.ranges[tile];
   float T[PPT], cr[PPT], cg[PPT], cb[PPT], swl[PPT];
   unsigned last[PPT];
@@ -188,15 +194,15 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
         s0[j] = make_float4(m.x, m.y, s.f11, s.f21);
         s1[j] = make_float4(s.f22, s.L2S, s.R, s.G);
         s2[j] = s.B;
-        s_rows[j] = (unsigned short)splat_rows(m.x, m.y, s.f11, s.f21, s.f22, s.L2S,
-                                               rc.log2_alpha_min, tg.xmax, tg.rows);
+        s_rows[j] = (unsigned short)splat_rows<TS>(m.x, m.y, s.f11, s.f21, s.f22, s.L2S,
+                                                   rc.log2_alpha_min, tg.xmax, tg.rows);
       }
     }
     __syncthreads();
     const int cnt = (int)min((unsigned)kBatch, r.y - base);
     // only the entries that may reach a pixel of this warp's rows
     const int n = __any_sync(kFull, live != 0u)
-                      ? warp_entries<PPT>(s_rows, s_list[warp], cnt, lane, warp)
+                      ? warp_entries<TS, PPT>(s_rows, s_list[warp], cnt, lane, warp)
                       : 0;
     for (int i = 0; i < n && live; ++i) {
       const int k = s_list[warp][i];
@@ -266,8 +272,8 @@ __device__ __forceinline__ void flush_stats(unsigned long long* stats, unsigned 
   }
 }
 
-template <int DT, int PPT, bool STATS>
-__global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(const CamTable ct,
+template <int DT, int TS, int PPT, bool STATS>
+__global__ void __launch_bounds__(TS * TS / PPT) render_fwd_kernel(const CamTable ct,
                                                                     const RenderConsts rc,
                                                                     const FwdArgs a,
                                                                     int persistent) {
@@ -280,11 +286,11 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(const CamTab
       const unsigned t = s_t;
       __syncthreads();
       if (t >= (unsigned)ct.total_tiles) break;
-      fwd_tile<DT, PPT, STATS>(ct, rc, a, a.order ? (int)a.order[t] : (int)t, nb, ne);
+      fwd_tile<DT, TS, PPT, STATS>(ct, rc, a, a.order ? (int)a.order[t] : (int)t, nb, ne);
     }
   } else {
     const int t = blockIdx.x;
-    fwd_tile<DT, PPT, STATS>(ct, rc, a, a.order ? (int)a.order[t] : t, nb, ne);
+    fwd_tile<DT, TS, PPT, STATS>(ct, rc, a, a.order ? (int)a.order[t] : t, nb, ne);
   }
   if (STATS) flush_stats(a.stats, nb, ne);
 }
@@ -346,7 +352,7 @@ __device__ __forceinline__ float warp_sum9(const float v[9], int lane, int& slot
   return y;
 }
 
-template <int DT, int PPT>
+template <int DT, int TS, int PPT>
 __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts& rc,
                                          const BwdArgs& a, int tile) {
   __shared__ float4 s0[kBatch];
@@ -354,13 +360,14 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
   __shared__ float2 s2[kBatch];  // (B, 1 / sigma)
   __shared__ unsigned s_row[kBatch];
   __shared__ unsigned short s_rows[kBatch];
-  constexpr int NT = TileGeom<PPT>::kThreads;
+  constexpr int NT = TileGeom<TS, PPT>::kThreads;
   constexpr int NW = NT / 32;
+  static_assert(NW >= 1, "a tile needs at least one full warp");
   __shared__ unsigned char s_list[NW][kBatch];
   __shared__ unsigned s_max;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const TileGeom<PPT> tg = tile_geom<PPT>(ct, tile);
+  const TileGeom<TS, PPT> tg = tile_geom<TS, PPT>(ct, tile);
   const uint2 r = a.ranges[tile];
   // per pixel: T, dL/dC, dL/dH, gS = dL/dC . S (S = sum_{k>i} w_k c_k) and R
   float T[PPT], gr[PPT], gg[PPT], gb[PPT], gH[PPT], gS[PPT], Rent[PPT];
@@ -402,13 +409,13 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
       s1[j] = make_float4(s.f22, s.L2S, s.R, s.G);
       s2[j] = make_float2(s.B, 1.f / s.sigma);
       s_row[j] = row;
-      s_rows[j] = (unsigned short)splat_rows(m.x, m.y, s.f11, s.f21, s.f22, s.L2S,
-                                             rc.log2_alpha_min, tg.xmax, tg.rows);
+      s_rows[j] = (unsigned short)splat_rows<TS>(m.x, m.y, s.f11, s.f21, s.f22, s.L2S,
+                                                 rc.log2_alpha_min, tg.xmax, tg.rows);
     }
     __syncthreads();
     // only the entries that may reach a pixel of this warp's rows, last first
     const int n = __any_sync(kFull, mylast > start)
-                      ? warp_entries<PPT>(s_rows, s_list[warp], cnt, lane, warp)
+                      ? warp_entries<TS, PPT>(s_rows, s_list[warp], cnt, lane, warp)
                       : 0;
     for (int i = n - 1; i >= 0; --i) {
       const int k = s_list[warp][i];
@@ -485,8 +492,9 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
   __syncthreads();
 }
 
-template <int DT, int PPT>
-__global__ void __launch_bounds__(kTilePix / PPT, PPT == 4 ? 1 : 4 * PPT) render_bwd_kernel(const CamTable ct,
+template <int DT, int TS, int PPT>
+__global__ void __launch_bounds__(TS * TS / PPT, (TS == 16 && PPT != 4) ? 4 * PPT : 1)
+    render_bwd_kernel(const CamTable ct,
                                                                     const RenderConsts rc,
                                                                     const BwdArgs a,
                                                                     int persistent) {
@@ -498,11 +506,11 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 4 ? 1 : 4 * PPT) render
       const unsigned t = s_t;
       __syncthreads();
       if (t >= (unsigned)ct.total_tiles) break;
-      bwd_tile<DT, PPT>(ct, rc, a, a.order ? (int)a.order[t] : (int)t);
+      bwd_tile<DT, TS, PPT>(ct, rc, a, a.order ? (int)a.order[t] : (int)t);
     }
   } else {
     const int t = blockIdx.x;
-    bwd_tile<DT, PPT>(ct, rc, a, a.order ? (int)a.order[t] : t);
+    bwd_tile<DT, TS, PPT>(ct, rc, a, a.order ? (int)a.order[t] : t);
   }
 }
 
@@ -512,22 +520,22 @@ int record_event(void* ev, cudaStream_t st) {
   return GS_OK;
 }
 
-template <int DT, int PPT>
+template <int DT, int TS, int PPT>
 void launch_fwd_ppt(const CamTable& ct, const RenderConsts& rc, const FwdArgs& a, int ctas,
                     cudaStream_t st) {
   const int grid = ctas > 0 ? ctas : ct.total_tiles;
   const int pers = ctas > 0 ? 1 : 0;
   if (a.stats)
-    render_fwd_kernel<DT, PPT, true><<<grid, kTilePix / PPT, 0, st>>>(ct, rc, a, pers);
+    render_fwd_kernel<DT, TS, PPT, true><<<grid, TS * TS / PPT, 0, st>>>(ct, rc, a, pers);
   else
-    render_fwd_kernel<DT, PPT, false><<<grid, kTilePix / PPT, 0, st>>>(ct, rc, a, pers);
+    render_fwd_kernel<DT, TS, PPT, false><<<grid, TS * TS / PPT, 0, st>>>(ct, rc, a, pers);
 }
 
-template <int DT, int PPT>
+template <int DT, int TS, int PPT>
 void launch_bwd_ppt(const CamTable& ct, const RenderConsts& rc, const BwdArgs& a, int ctas,
                     cudaStream_t st) {
   const int grid = ctas > 0 ? ctas : ct.total_tiles;
-  render_bwd_kernel<DT, PPT><<<grid, kTilePix / PPT, 0, st>>>(ct, rc, a, ctas > 0 ? 1 : 0);
+  render_bwd_kernel<DT, TS, PPT><<<grid, TS * TS / PPT, 0, st>>>(ct, rc, a, ctas > 0 ? 1 : 0);
 }
 
 template <int DT>
@@ -537,9 +545,14 @@ int launch_fwd_t(const CamTable& ct, const RenderConsts& rc, const FwdArgs& a, i
   if (e != GS_OK) return e;
   const int ppt = (opt && opt->pixels_per_thread) ? opt->pixels_per_thread : 2;
   if (ct.total_tiles > 0) {
-    if (ppt == 1) launch_fwd_ppt<DT, 1>(ct, rc, a, ctas, st);
-    else if (ppt == 4) launch_fwd_ppt<DT, 4>(ct, rc, a, ctas, st);
-    else launch_fwd_ppt<DT, 2>(ct, rc, a, ctas, st);
+    if (ct.tile == 8) {  // 8x8 tiles: 1 or 2 px per thread (a CTA is at least one warp)
+      if (ppt == 1) launch_fwd_ppt<DT, 8, 1>(ct, rc, a, ctas, st);
+      else launch_fwd_ppt<DT, 8, 2>(ct, rc, a, ctas, st);
+    } else {
+      if (ppt == 1) launch_fwd_ppt<DT, 16, 1>(ct, rc, a, ctas, st);
+      else if (ppt == 4) launch_fwd_ppt<DT, 16, 4>(ct, rc, a, ctas, st);
+      else launch_fwd_ppt<DT, 16, 2>(ct, rc, a, ctas, st);
+    }
     count_launches(1);
   }
   e = record_event(opt ? opt->ev_end : nullptr, st);
@@ -554,9 +567,14 @@ int launch_bwd_t(const CamTable& ct, const RenderConsts& rc, const BwdArgs& a, i
   if (e != GS_OK) return e;
   const int ppt = (opt && opt->pixels_per_thread) ? opt->pixels_per_thread : 2;
   if (ct.total_tiles > 0) {
-    if (ppt == 1) launch_bwd_ppt<DT, 1>(ct, rc, a, ctas, st);
-    else if (ppt == 4) launch_bwd_ppt<DT, 4>(ct, rc, a, ctas, st);
-    else launch_bwd_ppt<DT, 2>(ct, rc, a, ctas, st);
+    if (ct.tile == 8) {
+      if (ppt == 1) launch_bwd_ppt<DT, 8, 1>(ct, rc, a, ctas, st);
+      else launch_bwd_ppt<DT, 8, 2>(ct, rc, a, ctas, st);
+    } else {
+      if (ppt == 1) launch_bwd_ppt<DT, 16, 1>(ct, rc, a, ctas, st);
+      else if (ppt == 4) launch_bwd_ppt<DT, 16, 4>(ct, rc, a, ctas, st);
+      else launch_bwd_ppt<DT, 16, 2>(ct, rc, a, ctas, st);
+    }
     count_launches(1);
   }
   e = record_event(opt ? opt->ev_end : nullptr, st);

@@ -39,7 +39,7 @@ class GsParams(ctypes.Structure):
                 ("t_min", ctypes.c_float), ("dilation", ctypes.c_float),
                 ("near_z", ctypes.c_float), ("fov_clamp", ctypes.c_float),
                 ("sh_degree", ctypes.c_int), ("sh_stride", ctypes.c_int),
-                ("attr_dtype", ctypes.c_int)]
+                ("attr_dtype", ctypes.c_int), ("tile_size", ctypes.c_int)]
 
 
 class GsProj(ctypes.Structure):
@@ -75,7 +75,7 @@ def _load():
     P = ctypes.POINTER
     sig = {
         "gs_record_bytes": (i, [i]),
-        "gs_total_tiles": (ll, [P(GsCamera), i]),
+        "gs_total_tiles": (ll, [P(GsCamera), i, i]),
         "gs_total_pixels": (ll, [P(GsCamera), i]),
         "gs_bin_sort_workspace_size": (sz, [ll, ll, ll]),
         "gs_loss_workspace_size": (sz, [ll]),
@@ -85,7 +85,8 @@ def _load():
         "gs_version": (ctypes.c_char_p, []),
         "gs_kernel_launches": (ctypes.c_ulonglong, []),
         "gs_preprocess": (i, [vp, vp, vp, vp, vp, i, P(GsCamera), i, P(GsParams), P(GsProj), vp]),
-        "gs_bin_sort": (i, [P(GsProj), i, P(GsCamera), i, vp, sz, ll, vp, vp, vp, vp, vp, vp, vp]),
+        "gs_bin_sort": (i, [P(GsProj), i, P(GsCamera), i, i, vp, sz, ll, vp, vp, vp, vp, vp, vp,
+                            vp]),
         "gs_render_fwd": (i, [P(GsProj), i, P(GsCamera), i, P(GsParams), vp, vp, vp, vp, vp, vp,
                               P(GsLaunch), vp]),
         "gs_loss_l1_entropy": (i, [vp, vp, vp, P(GsCamera), i, f, vp, vp, vp, vp, sz, vp]),
@@ -161,6 +162,7 @@ def make_params(prm, sh_stride=16, attr_dtype="f32"):
     p.sh_degree = int(prm.get("sh_degree", 0))
     p.sh_stride = int(sh_stride)
     p.attr_dtype = ATTR_DTYPES[attr_dtype] if isinstance(attr_dtype, str) else int(attr_dtype)
+    p.tile_size = int(prm.get("tile", 16))
     return p
 
 
@@ -186,8 +188,8 @@ def gs_record_bytes(attr_dtype):
     return _lib.gs_record_bytes(attr_dtype)
 
 
-def gs_total_tiles(cams_c):
-    return _lib.gs_total_tiles(cams_c, len(cams_c))
+def gs_total_tiles(cams_c, tile_size=16):
+    return _lib.gs_total_tiles(cams_c, len(cams_c), int(tile_size))
 
 
 def gs_total_pixels(cams_c):
@@ -230,11 +232,12 @@ def gs_preprocess(means, log_scales, quats, opacity_logits, sh, N, cams_c, prm_c
 
 
 def gs_bin_sort(proj_c, N, cams_c, workspace, pair_capacity, sorted_vals, sorted_keys, tile_ranges,
-                num_pairs_dev, status_dev, sync_count=True, stream=None):
+                num_pairs_dev, status_dev, sync_count=True, stream=None, tile_size=16):
     """Returns (status, P) with P the host pair count when sync_count, else None.
     GS_ERR_CAPACITY is returned, not raised."""
     nh = ctypes.c_longlong(0)
-    st = _lib.gs_bin_sort(ctypes.byref(proj_c), N, cams_c, len(cams_c), _ptr(workspace),
+    st = _lib.gs_bin_sort(ctypes.byref(proj_c), N, cams_c, len(cams_c), int(tile_size),
+                          _ptr(workspace),
                           workspace.numel() * workspace.element_size(), pair_capacity,
                           _ptr(sorted_vals), _ptr(sorted_keys), _ptr(tile_ranges),
                           _ptr(num_pairs_dev), ctypes.byref(nh) if sync_count else None,

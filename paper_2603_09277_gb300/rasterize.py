@@ -51,7 +51,8 @@ class Rasterizer:
         self.V = len(cams)
         self.sh_stride = sh_stride
         self.rows = self.N * self.V
-        self.total_tiles = gs.gs_total_tiles(self.cams_c)
+        self.tile = int(prm.get("tile", 16))
+        self.total_tiles = gs.gs_total_tiles(self.cams_c, self.tile)
         self.total_pixels = gs.gs_total_pixels(self.cams_c)
         if self.total_tiles < 0:
             raise ValueError("invalid cameras")
@@ -138,7 +139,7 @@ class Rasterizer:
             st, P = gs.gs_bin_sort(self.proj_c, self.N, self.cams_c, self.bin_ws, self.capacity,
                                    self.sorted_vals, self.sorted_keys if keys else None,
                                    self.tile_ranges, self.num_pairs_dev, self.status_dev,
-                                   sync_count=sync, stream=stream)
+                                   sync_count=sync, stream=stream, tile_size=self.tile)
             if st == gs.GS_OK:
                 break
             self._alloc_pairs(int(P * 1.25) + 1024)

@@ -51,7 +51,10 @@ def test_host_side_argument_checks(lib_path):
     from paper_2603_09277_gb300 import gs, scenes
     lib = gs._lib
     cams = gs.make_cameras([scenes.camera(64, 48, 64.0), scenes.camera(33, 17, 40.0)])
-    assert lib.gs_total_tiles(cams, 2) == 4 * 3 + 3 * 2
+    assert lib.gs_total_tiles(cams, 2, 16) == 4 * 3 + 3 * 2
+    assert lib.gs_total_tiles(cams, 2, 0) == 4 * 3 + 3 * 2
+    assert lib.gs_total_tiles(cams, 2, 8) == 8 * 6 + 5 * 3  # 8-pixel tiles
+    assert lib.gs_total_tiles(cams, 2, 12) == -1
     assert lib.gs_total_pixels(cams, 2) == 64 * 48 + 33 * 17
     assert lib.gs_record_bytes(gs.GS_ATTR_F32) == 48
     assert lib.gs_record_bytes(gs.GS_ATTR_F16) == 32
@@ -64,5 +67,13 @@ def test_host_side_argument_checks(lib_path):
     assert lib.gs_preprocess(None, None, None, None, None, 0, cams, 2, ctypes.byref(prm),
                              ctypes.byref(proj), None) == gs.GS_ERR_INVALID_ARG
     assert b"invalid argument" in lib.gs_last_error_string()
+    prm.sh_degree = 0
+    prm.tile_size = 12  # only 16 and 8 pixel tiles exist
+    assert lib.gs_preprocess(None, None, None, None, None, 0, cams, 2, ctypes.byref(prm),
+                             ctypes.byref(proj), None) == gs.GS_ERR_INVALID_ARG
+    ws = ctypes.c_void_p(256)  # never dereferenced: the tile side is rejected first
+    assert lib.gs_bin_sort(ctypes.byref(proj), 0, cams, 2, 12, ws, 0, 0, None, None, None, None,
+                           None, None, None) == gs.GS_ERR_INVALID_ARG
+    assert b"tile_size" in lib.gs_last_error_string()
     assert lib.gs_bin_sort_workspace_size(1000, 5000, 64) > 0
     assert b"sm_103a" in lib.gs_version()

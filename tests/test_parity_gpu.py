@@ -54,7 +54,7 @@ def check_projection(g, views, cams, N):
 
 
 def check_lists(g, views, cams, N):
-    vt = view_tiles(cams)
+    vt = view_tiles(cams, views[0]["proj"].get("tile", 16))
     for v, cam in enumerate(cams):
         ts, ids = views[v]["lists"]
         flagged = views[v]["proj"]["boundary"].astype(bool)
@@ -94,7 +94,8 @@ def check_pixels(g, views, cams, N):
         flagged = views[v]["proj"]["boundary"].any()
         if not flagged:
             assert (g["last"][a:b][ok] == f["last"].reshape(-1)[ok]).all()
-        assert (last_ids_gpu(g, cams, v, N)[ok] == last_ids_oracle(views[v], cam)[ok]).all()
+        side = views[v]["proj"].get("tile", 16)
+        assert (last_ids_gpu(g, cams, v, N, side)[ok] == last_ids_oracle(views[v], cam)[ok]).all()
         worst[v] = (img_err, t_err, h_err, int(bad.sum()))
         assert img_err <= IMG_TOL, worst
         assert t_err <= IMG_TOL, worst
