@@ -82,6 +82,11 @@ def parse():
                     help="run the synthetic training loop (cfg5 form) for this many iterations")
     ap.add_argument("--train-size", default="960x540", help="training view size WxH")
     ap.add_argument("--train-n", type=int, default=3_000_000, help="Gaussians in the training scene")
+    ap.add_argument("--train-epochs", type=int, default=0,
+                    help="run the epoch schedule (resolution scheduler, scale reset every "
+                         "--reset-every epochs, entropy on every other epoch) for N epochs")
+    ap.add_argument("--images-per-epoch", type=int, default=200)
+    ap.add_argument("--reset-every", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-band-rows", type=int, default=0,
                     help="tile rows of view 0 the CPU oracle sample renders (0 = the whole view)")
@@ -368,6 +373,113 @@ def run_train(args, dev):
                               "seconds": time.perf_counter() - t0}), flush=True)
 
 
+def run_train_schedule(args, dev):
+    """The training schedule of Sec. 5.2 on the cfg5 training scene: epochs of
+    --images-per-epoch images sampled with replacement from 32 orbit views,
+    the resolution scheduler (r_max: the largest factor <= 4 whose mean
+    per-tile list stays <= 150, measured on the lists themselves; levels
+    r_max .. 2 over the first half of the epochs, then full resolution), the
+    scale reset every --reset-every epochs and the entropy term on every other
+    epoch, with weaker zeta / gamma during the coarse stages.  One JSON line per
+    epoch: level, gamma, zeta applied, loss, PSNR at the level, mean list per
+    tile, milliseconds per iteration."""
+    import torch
+    from paper_2603_09277_gb300 import gs, scenes, schedule
+    from paper_2603_09277_gb300.rasterize import (Rasterizer, l1_entropy_loss, rasterize,
+                                                  scene_to_device)
+    W, H = (int(x) for x in args.train_size.split("x"))
+    n = args.train_n
+    gt_scene, _, _, prm = scenes.config5(seed=2, n=n, width=W, height=H)
+    prm["tile"] = args.tile
+    cams = scenes.orbit_cameras(32, W, H, seed=3)
+    gt = scene_to_device(gt_scene, dev)
+    targets = []
+    for c in cams:
+        rr = Rasterizer([c], prm, n, device=dev)
+        rr.preprocess(gt)
+        rr.bin_sort()
+        rr.render_fwd()
+        targets.append(rr.image.reshape(H, W, 3).clone())
+        del rr
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(4)
+    init = {k: np.array(v, copy=True) if isinstance(v, np.ndarray) else v
+            for k, v in gt_scene.items()}
+    init["means"] = (init["means"] + rng.normal(0, 0.01, init["means"].shape)).astype(np.float32)
+    init["log_scales"] = (init["log_scales"]
+                          + rng.normal(0, 0.1, init["log_scales"].shape)).astype(np.float32)
+    init["opacity_logits"] = (init["opacity_logits"] + rng.normal(0, 0.5, n)).astype(np.float32)
+    init["sh"][:, 0] = (init["sh"][:, 0] + rng.normal(0, 0.05, (n, 3))).astype(np.float32)
+    p = scene_to_device(init, dev, requires_grad=True)
+    opt = torch.optim.Adam([
+        {"params": [p["means"]], "lr": 1.6e-4},
+        {"params": [p["log_scales"]], "lr": 5e-3},
+        {"params": [p["quats"]], "lr": 1e-3},
+        {"params": [p["opacity_logits"]], "lr": 5e-2},
+        {"params": [p["sh"]], "lr": 2.5e-3},
+    ], eps=1e-15)
+
+    def mean_list(r):
+        # mean per-tile list length of the initial scene at factor r, over 4 views
+        tot = 0.0
+        for v in range(0, 32, 8):
+            rr = Rasterizer([schedule.scaled_camera(cams[v], r)], prm, n, device=dev)
+            rr.preprocess(p)
+            P = rr.bin_sort()
+            tot += P / rr.total_tiles
+            del rr
+        return tot / 4
+
+    probes = {}
+    r_max = schedule.choose_r_max(lambda r: probes.setdefault(r, mean_list(r)))
+    plan = schedule.EpochSchedule(epochs=args.train_epochs, images_per_epoch=args.images_per_epoch,
+                                  reset_every=args.reset_every, r_max=r_max)
+    print(json.dumps({"r_max": r_max, "mean_list_probes": probes,
+                      "threshold": schedule.LIST_THRESHOLD}), flush=True)
+    levels = plan.levels()
+    order = plan.image_order(len(cams), seed=5)
+    rasts, tcache = {}, {}
+    t0 = time.perf_counter()
+    for e in range(plan.epochs):
+        lv = int(levels[e])
+        if lv not in rasts:
+            rasts[lv] = Rasterizer([schedule.scaled_camera(cams[0], lv)], prm, n, device=dev)
+        r = rasts[lv]
+        gamma = plan.gamma_at(e)
+        te = time.perf_counter()
+        lsum, msum = 0.0, 0.0
+        for it in range(plan.images_per_epoch):
+            v = int(order[e, it])
+            cam = schedule.scaled_camera(cams[v], lv)
+            r.cams = [cam]
+            r.cams_c = gs.make_cameras([cam])
+            key = (v, lv)
+            if key not in tcache:
+                tcache[key] = schedule.downsample_image(targets[v], lv).reshape(-1, 3).contiguous()
+            tgt = tcache[key]
+            img, ent = rasterize(p, r)
+            loss = l1_entropy_loss(img, ent, tgt, r, gamma)
+            opt.zero_grad(set_to_none=True)
+            loss.backward()
+            opt.step()
+            with torch.no_grad():
+                p["quats"].div_(p["quats"].norm(dim=1, keepdim=True).clamp_min(1e-8))
+                if it == plan.images_per_epoch - 1:
+                    lsum = float(loss.item())
+                    msum = float(((img - tgt) ** 2).mean().item())
+        torch.cuda.synchronize()
+        ms_it = 1000.0 * (time.perf_counter() - te) / plan.images_per_epoch
+        zeta = None
+        if plan.reset_after(e):
+            zeta = plan.zeta_at(e)
+            gs.gs_scale_reset(p["log_scales"].data, zeta)
+        print(json.dumps({"epoch": e, "r": lv, "gamma": gamma, "scale_reset": zeta,
+                          "loss": lsum, "psnr": -10.0 * math.log10(max(msum, 1e-12)),
+                          "mean_list_per_tile": r.num_pairs / r.total_tiles,
+                          "ms_per_iter": ms_it, "seconds": time.perf_counter() - t0}),
+              flush=True)
+
+
 def time_variant(make, p, tgt, gamma, flush, steps, warmup=2):
     """Mean ms per fwd+bwd step (projection .. adjoint) of the rasterizers
     `make()` returns (run back to back: one per view for the per-view form)."""
@@ -426,6 +538,9 @@ def main():
         return
     if args.train:
         run_train(args, dev)
+        return
+    if args.train_epochs:
+        run_train_schedule(args, dev)
         return
 
     (scene, cams, targets, prm), wl = workload(args.config, rank, args.n)
