@@ -67,6 +67,7 @@ def _load():
         if _lib is None:
             _lib = ctypes.CDLL(build())
             _lib.ora_entropy.restype = ctypes.c_double
+            _lib.ora_ssim.restype = ctypes.c_double
             _lib.ora_loss.restype = ctypes.c_double
             _lib.ora_build_lists.restype = ctypes.c_longlong
             _lib.ora_num_threads.restype = ctypes.c_int
@@ -252,6 +253,30 @@ def loss(image, entropy, target, gamma, view_weight=1.0):
     L = lib.ora_loss(ctypes.c_int(M), _p(image), _p(_f32(target)), _p(entropy),
                      ctypes.c_double(gamma), ctypes.c_double(view_weight), _p(dC), _p(dH))
     return float(L), dC, dH
+
+
+def ssim(image, target, with_grad=False):
+    """Mean SSIM of an [H,W,3] image against its target (the D-SSIM term's
+    SSIM: 11x11 Gaussian window of sigma 1.5, zero padding, C1 = 0.01^2,
+    C2 = 0.03^2); with_grad also returns d SSIM / d image [H,W,3]."""
+    lib = _load()
+    image = _f64(image)
+    H, W = image.shape[:2]
+    g = np.zeros_like(image) if with_grad else None
+    s = lib.ora_ssim(ctypes.c_int(W), ctypes.c_int(H), _p(image), _p(_f32(target)), _p(g))
+    return (float(s), g) if with_grad else float(s)
+
+
+def loss_base(image, entropy, target, gamma, lam, view_weight=1.0):
+    """(1 - lam) L1 + lam (1 - SSIM) + gamma (1/M) sum H of one view (Sec. 3
+    Eq. base with D-SSIM = 1 - SSIM, plus the entropy term of Sec. 4.3), times
+    view_weight; returns (L, dL/dC, dL/dH)."""
+    L1, dC, dH = loss(image, entropy, target, 0.0, view_weight)
+    Lh, _, dH = loss(image, entropy, target, gamma, view_weight)
+    Lent = Lh - L1
+    s, gs = ssim(image, target, with_grad=True)
+    L = (1 - lam) * L1 + view_weight * lam * (1 - s) + Lent
+    return L, (1 - lam) * dC - view_weight * lam * gs, dH
 
 
 def entropy(alphas):

@@ -731,6 +731,107 @@ double ora_loss(int M, const double* image, const float* target, const double* e
     return view_weight * (l1 / (3.0 * M) + gamma * hs / M);
 }
 
+/* ------------------------------------------------------------------------ */
+/* SSIM of one view (the D-SSIM term of L_base, Sec. 3 Eq. base; the paper   */
+/* does not define it: the reading is 3DGS's, D-SSIM = 1 - SSIM with the     */
+/* 11x11 Gaussian window of sigma 1.5 (normalised), zero padding outside the */
+/* image, C1 = 0.01^2, C2 = 0.03^2, SSIM = mean over pixels and channels).   */
+/* Per pixel q and channel, over the 121 window samples (padding included as */
+/* zeros): mu_x = E[x], sigma_x^2 = E[(x - mu_x)^2], sigma_xy likewise;       */
+/* S = (2 mu_x mu_y + C1)(2 sigma_xy + C2) / ((mu_x^2 + mu_y^2 + C1)         */
+/*     (sigma_x^2 + sigma_y^2 + C2)).                                         */
+/* grad (nullable, H*W*3): d SSIM / d image, from                             */
+/*   dS(q)/dx(p) = G(q-p) [dS/dmu_x + 2 (x(p) - mu_x(q)) dS/dsigma_x^2        */
+/*                         + (y(p) - mu_y(q)) dS/dsigma_xy],                  */
+/* (d sigma_x^2(q) / dx(p) = 2 G(q-p)(x(p) - mu_x(q)) since the weights sum  */
+/* to 1), summed over the windows q that contain p, divided by 3 H W.        */
+/* ------------------------------------------------------------------------ */
+#define SSIM_R 5
+#define SSIM_C1 (0.01 * 0.01)
+#define SSIM_C2 (0.03 * 0.03)
+
+static void ssim_window(double g[2 * SSIM_R + 1]) {
+    double s = 0.0;
+    for (int k = -SSIM_R; k <= SSIM_R; ++k) {
+        g[k + SSIM_R] = exp(-(double)(k * k) / (2.0 * 1.5 * 1.5));
+        s += g[k + SSIM_R];
+    }
+    for (int k = 0; k < 2 * SSIM_R + 1; ++k) g[k] /= s;
+}
+
+double ora_ssim(int W, int H, const double* img, const float* tgt, double* grad) {
+    double g[2 * SSIM_R + 1];
+    ssim_window(g);
+    const size_t M = (size_t)W * H;
+    /* per pixel and channel: mu_x, mu_y, dS/dmu_x, dS/dsigma_x^2, dS/dsigma_xy */
+    double* maps = grad ? (double*)malloc(sizeof(double) * 5 * 3 * M) : NULL;
+    double total = 0.0;
+#pragma omp parallel for reduction(+ : total) schedule(static)
+    for (long long q = 0; q < (long long)M; ++q) {
+        int u = (int)(q % W), v = (int)(q / W);
+        for (int ch = 0; ch < 3; ++ch) {
+            double mx = 0, my = 0;
+            for (int dy = -SSIM_R; dy <= SSIM_R; ++dy)
+                for (int dx = -SSIM_R; dx <= SSIM_R; ++dx) {
+                    int uu = u + dx, vv = v + dy;
+                    if (uu < 0 || uu >= W || vv < 0 || vv >= H) continue;
+                    double w = g[dy + SSIM_R] * g[dx + SSIM_R];
+                    size_t k = 3 * ((size_t)vv * W + uu) + ch;
+                    mx += w * img[k];
+                    my += w * (double)tgt[k];
+                }
+            double sxx = 0, syy = 0, sxy = 0;
+            for (int dy = -SSIM_R; dy <= SSIM_R; ++dy)
+                for (int dx = -SSIM_R; dx <= SSIM_R; ++dx) {
+                    int uu = u + dx, vv = v + dy;
+                    double w = g[dy + SSIM_R] * g[dx + SSIM_R];
+                    double a = -mx, b = -my;  /* padding samples are zero */
+                    if (!(uu < 0 || uu >= W || vv < 0 || vv >= H)) {
+                        size_t k = 3 * ((size_t)vv * W + uu) + ch;
+                        a = img[k] - mx;
+                        b = (double)tgt[k] - my;
+                    }
+                    sxx += w * a * a;
+                    syy += w * b * b;
+                    sxy += w * a * b;
+                }
+            double A1 = 2 * mx * my + SSIM_C1, A2 = 2 * sxy + SSIM_C2;
+            double B1 = mx * mx + my * my + SSIM_C1, B2 = sxx + syy + SSIM_C2;
+            double D = B1 * B2, S = A1 * A2 / D;
+            total += S;
+            if (maps) {
+                double* m = maps + 15 * (size_t)q + 5 * ch;
+                m[0] = mx;
+                m[1] = my;
+                m[2] = (2 * my * A2 - S * 2 * mx * B2) / D;  /* dS/dmu_x, sigmas fixed */
+                m[3] = -S / B2;                              /* dS/dsigma_x^2 */
+                m[4] = 2 * A1 / D;                           /* dS/dsigma_xy */
+            }
+        }
+    }
+    if (grad) {
+#pragma omp parallel for schedule(static)
+        for (long long p = 0; p < (long long)M; ++p) {
+            int u = (int)(p % W), v = (int)(p / W);
+            for (int ch = 0; ch < 3; ++ch) {
+                double xp = img[3 * (size_t)p + ch], yp = (double)tgt[3 * (size_t)p + ch];
+                double acc = 0.0;
+                for (int dy = -SSIM_R; dy <= SSIM_R; ++dy)
+                    for (int dx = -SSIM_R; dx <= SSIM_R; ++dx) {
+                        int uu = u + dx, vv = v + dy;  /* window centre q containing p */
+                        if (uu < 0 || uu >= W || vv < 0 || vv >= H) continue;
+                        double w = g[dy + SSIM_R] * g[dx + SSIM_R];
+                        const double* m = maps + 15 * ((size_t)vv * W + uu) + 5 * ch;
+                        acc += w * (m[2] + 2 * (xp - m[0]) * m[3] + (yp - m[1]) * m[4]);
+                    }
+                grad[3 * (size_t)p + ch] = acc / (3.0 * M);
+            }
+        }
+        free(maps);
+    }
+    return total / (3.0 * M);
+}
+
 /* Scale reset (Sec. 4.2): s <- zeta s for every Gaussian, i.e. the stored
  * log-scale gains log(zeta). */
 void ora_scale_reset(int n, const float* log_scales, double zeta, double* out) {

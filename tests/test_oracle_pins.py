@@ -530,3 +530,93 @@ def test_fov_clamp_linearises_at_the_clamped_direction():
         P9 = proj["P9"][0]
         assert P9[0:2] == pytest.approx(_pinhole(cam, X), rel=1e-12)
         assert P9[[2, 3, 4]] == pytest.approx([K[0, 0], K[0, 1], K[1, 1]], rel=1e-6)
+
+
+# --------------------------------------------------------------------------
+# D-SSIM term of L_base (Sec. 3 Eq. base; SSIM as in 3DGS)
+# --------------------------------------------------------------------------
+
+def _ssim_scipy(x, y):
+    """Textbook SSIM with scipy's 2D correlation for every window sum:
+    mu = G * x, sigma^2 = G * x^2 - mu^2, sigma_xy = G * (x y) - mu_x mu_y,
+    zero fill outside the image."""
+    from scipy.signal import correlate2d
+    k = np.exp(-np.arange(-5, 6) ** 2 / (2 * 1.5 ** 2))
+    G = np.outer(k, k) / k.sum() ** 2
+    c1, c2 = 0.01 ** 2, 0.03 ** 2
+    vals = []
+    for ch in range(3):
+        a, b = x[..., ch], y[..., ch].astype(np.float64)
+        f = lambda z: correlate2d(z, G, mode="same", boundary="fill", fillvalue=0.0)
+        mx, my = f(a), f(b)
+        sxx, syy, sxy = f(a * a) - mx * mx, f(b * b) - my * my, f(a * b) - mx * my
+        vals.append(((2 * mx * my + c1) * (2 * sxy + c2)) /
+                    ((mx * mx + my * my + c1) * (sxx + syy + c2)))
+    return float(np.mean(vals))
+
+
+@pytest.mark.parametrize("shape", [(9, 11), (32, 17), (40, 40)])
+def test_ssim_matches_textbook_form(shape):
+    rng = np.random.default_rng(shape[0])
+    x = rng.random(shape + (3,))
+    y = rng.random(shape + (3,)).astype(np.float32)
+    # correlated pair too (high SSIM), where the variance forms differ most
+    z = np.clip(x + rng.normal(0, 0.02, x.shape), 0, 1)
+    for a, b in ((x, y), (z, x.astype(np.float32))):
+        assert oracle.ssim(a, b) == pytest.approx(_ssim_scipy(a, b), abs=1e-12)
+
+
+def test_ssim_identity_symmetry_and_constant_images():
+    rng = np.random.default_rng(1)
+    x = rng.random((20, 24, 3))
+    xs = x.astype(np.float32).astype(np.float64)
+    s, g = oracle.ssim(xs, xs.astype(np.float32), with_grad=True)
+    assert s == pytest.approx(1.0, abs=1e-14) and np.abs(g).max() < 1e-14
+    y = rng.random((20, 24, 3)).astype(np.float32)
+    assert oracle.ssim(xs, y) == pytest.approx(oracle.ssim(y.astype(np.float64),
+                                                             xs.astype(np.float32)), abs=1e-14)
+    # constant images a, b: away from the border every window sees no
+    # variance, S = (2ab + C1) / (a^2 + b^2 + C1); the textbook form agrees
+    a = np.full((30, 30, 3), 0.7)
+    b = np.full((30, 30, 3), 0.2, np.float32)
+    assert oracle.ssim(a, b) == pytest.approx(_ssim_scipy(a, b), abs=1e-12)
+
+
+def test_ssim_gradient_finite_differences():
+    rng = np.random.default_rng(2)
+    x = rng.random((10, 13, 3))
+    y = np.clip(x + rng.normal(0, 0.1, x.shape), 0, 1).astype(np.float32)
+    s, g = oracle.ssim(x, y, with_grad=True)
+    # central differences, h = 1e-5: truncation O(h^2) and rounding ~1e-16 / h,
+    # both far below the 1e-9 floor; typical entries are 1e-5 .. 1e-3
+    h = 1e-5
+    for idx in [(0, 0, 0), (4, 6, 1), (9, 12, 2), (5, 0, 0), (2, 9, 1)] + \
+               [tuple(int(rng.integers(0, n)) for n in x.shape) for _ in range(20)]:
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += h
+        xm[idx] -= h
+        fd = (oracle.ssim(xp, y) - oracle.ssim(xm, y)) / (2 * h)
+        assert fd == pytest.approx(g[idx], rel=1e-5, abs=1e-9)
+
+
+def test_loss_base_reduces_and_differentiates():
+    rng = np.random.default_rng(3)
+    img = rng.random((12, 14, 3))
+    ent = rng.random((12, 14))
+    tgt = rng.random((12, 14, 3)).astype(np.float32)
+    L0, d0, h0 = oracle.loss(img, ent, tgt, 0.015)
+    L, dC, dH = oracle.loss_base(img, ent, tgt, 0.015, 0.0)
+    assert L == pytest.approx(L0, abs=1e-15) and np.array_equal(dC, d0) and np.array_equal(dH, h0)
+    lam = 0.2
+    L, dC, dH = oracle.loss_base(img, ent, tgt, 0.015, lam)
+    L1 = np.abs(img - tgt).mean()
+    assert L == pytest.approx((1 - lam) * L1 + lam * (1 - oracle.ssim(img, tgt)) +
+                              0.015 * ent.mean(), abs=1e-14)
+    h = 1e-7
+    for idx in [(0, 0, 0), (6, 7, 1), (11, 13, 2)]:
+        ip, im = img.copy(), img.copy()
+        ip[idx] += h
+        im[idx] -= h
+        fd = (oracle.loss_base(ip, ent, tgt, 0.015, lam)[0] -
+              oracle.loss_base(im, ent, tgt, 0.015, lam)[0]) / (2 * h)
+        assert fd == pytest.approx(dC[idx], rel=1e-5, abs=1e-9)
