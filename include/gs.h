@@ -218,6 +218,24 @@ int gs_loss_l1_entropy(const float* image, const float* target, const float* ent
                        float* dL_dimage, float* dL_dentropy, void* workspace,
                        size_t workspace_bytes, gs_stream stream);
 
+/* Workspace bytes that gs_loss_base needs for the V views (host cams). */
+size_t gs_loss_base_workspace_size(const gs_camera* cams_host, int V);
+
+/* The full L_base of Sec. 3 Eq. base with its D-SSIM term, plus the entropy
+ * term of Sec. 4.3, per view averaged, then over the V views:
+ *   L = (1/V) sum_v [ (1 - lambda) L1_v + lambda (1 - SSIM_v) + gamma (1/M_v) sum_j H_j ].
+ * The paper does not define D-SSIM; it is 1 - SSIM with the SSIM of 3DGS:
+ * an 11x11 Gaussian window of sigma 1.5 (normalised), zero padding outside
+ * the image, C1 = 0.01^2, C2 = 0.03^2, mean over the view's pixels and
+ * channels.  lambda in [0, 1] (0 gives gs_loss_l1_entropy; 3DGS uses 0.2).
+ * Writes loss_dev, dL_dimage (the L1 and D-SSIM gradients) and dL_dentropy
+ * like gs_loss_l1_entropy.  workspace: device,
+ * gs_loss_base_workspace_size(cams, V) bytes (about 60 B per pixel). */
+int gs_loss_base(const float* image, const float* target, const float* entropy,
+                 const gs_camera* cams_host, int V, float lambda, float gamma, double* loss_dev,
+                 float* dL_dimage, float* dL_dentropy, void* workspace, size_t workspace_bytes,
+                 gs_stream stream);
+
 /* Reverse-order adjoint of gs_render_fwd and gs_preprocess (Sec. 4.4 and
  * Suppl. B-C).  Per pixel, from its last blended entry back to the first:
  * T_i = T_{i+1} / (1 - alpha_i), the colour part of dL/dalpha_i, and the

@@ -328,9 +328,10 @@ def forward(scene, cams, prm, mask=None):
     return views
 
 
-def step(scene, cams, targets, prm, gamma, with_grad=True):
+def step(scene, cams, targets, prm, gamma, with_grad=True, lam=0.0):
     """One forward + backward of L = (1/V) sum_v (L1_v + gamma L_E,v)
-    (reading: per-view pixel averages, then the mean over views).
+    (reading: per-view pixel averages, then the mean over views); with
+    lam > 0 the L1 term is L_base = (1 - lam) L1 + lam D-SSIM.
     Returns (L, views, grads, grad9 per view)."""
     views = forward(scene, cams, prm)
     V = len(cams)
@@ -339,7 +340,10 @@ def step(scene, cams, targets, prm, gamma, with_grad=True):
     g9s = []
     for v, cam in enumerate(cams):
         f = views[v]["fwd"]
-        Lv, dC, dH = loss(f["image"], f["entropy"], targets[v], gamma, 1.0 / V)
+        if lam > 0.0:
+            Lv, dC, dH = loss_base(f["image"], f["entropy"], targets[v], gamma, lam, 1.0 / V)
+        else:
+            Lv, dC, dH = loss(f["image"], f["entropy"], targets[v], gamma, 1.0 / V)
         L += Lv
         views[v]["dL_dC"], views[v]["dL_dH"] = dC, dH
         if with_grad:

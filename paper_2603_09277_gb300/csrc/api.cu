@@ -21,6 +21,10 @@ int launch_preprocess_bwd(const float* means, const float* log_scales, const flo
                           float* g_means, float* g_ls, float* g_quats, float* g_opac, float* g_sh,
                           cudaStream_t st);
 size_t bin_sort_workspace_size(long long n_rows, long long cap, long long total_tiles);
+size_t ssim_workspace_bytes(long long total_pixels);
+int ssim_blocks(const CamTable& ct);
+int launch_ssim(const float* image, const float* target, const CamTable& ct, float lambda,
+                float* maps, double* partials, float* dimg, cudaStream_t st);
 int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* workspace,
                     size_t ws_bytes, long long cap, unsigned* sorted_vals,
                     unsigned long long* sorted_keys, unsigned* ranges, long long* num_pairs_dev,
@@ -166,7 +170,8 @@ struct LossViews {
 __global__ void __launch_bounds__(kLossThreads) loss_kernel(
     const float* __restrict__ image, const float* __restrict__ target,
     const float* __restrict__ entropy, const LossViews lv, long long P, float gamma,
-    float* __restrict__ dimg, float* __restrict__ dent, double* __restrict__ partials) {
+    double l1_weight, float* __restrict__ dimg, float* __restrict__ dent,
+    double* __restrict__ partials) {
   double acc = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
        i += (long long)gridDim.x * blockDim.x) {
@@ -181,8 +186,8 @@ __global__ void __launch_bounds__(kLossThreads) loss_kernel(
     }
     const float h = entropy ? entropy[i] : 0.f;
     if (dent) dent[i] = lv.g_ent[v];
-    // per pixel: (1/(M_v V)) (|r|_1 / 3 + gamma H), summed in double
-    acc += lv.w[v] * ((double)l1 * (1.0 / 3.0) + (double)gamma * (double)h);
+    // per pixel: (1/(M_v V)) ((1 - lambda) |r|_1 / 3 + gamma H), summed in double
+    acc += lv.w[v] * (l1_weight * (double)l1 * (1.0 / 3.0) + (double)gamma * (double)h);
   }
   __shared__ double s[kLossThreads / 32];
 #pragma unroll
@@ -336,19 +341,22 @@ int gs_render_fwd(const gs_proj* proj, int N, const gs_camera* cams, int V, cons
                            entropy, opt, (cudaStream_t)stream);
 }
 
-int gs_loss_l1_entropy(const float* image, const float* target, const float* entropy,
-                       const gs_camera* cams, int V, float gamma, double* loss_dev,
-                       float* dL_dimage, float* dL_dentropy, void* workspace,
-                       size_t workspace_bytes, gs_stream stream) {
+namespace {
+int loss_impl(const float* image, const float* target, const float* entropy, const gs_camera* cams,
+              int V, float lambda, float gamma, double* loss_dev, float* dL_dimage,
+              float* dL_dentropy, void* workspace, size_t workspace_bytes, cudaStream_t st) {
   CamTable ct;
   if (!build_cam_table(cams, V, nullptr, 0, &ct)) return invalid("cameras");
   long long P = ct.c[V - 1].pix_off + (long long)ct.c[V - 1].W * ct.c[V - 1].H;
   if (!image || !target || !loss_dev || !dL_dimage) return invalid("pointers");
   if (gamma != 0.f && !entropy) return invalid("entropy is required when gamma != 0");
   if (!(gamma >= 0.f)) return invalid("gamma");
-  int nb = loss_blocks(P);
-  if (!workspace || workspace_bytes < sizeof(double) * (size_t)nb) return invalid("workspace");
-  cudaStream_t st = (cudaStream_t)stream;
+  if (!(lambda >= 0.f && lambda <= 1.f)) return invalid("lambda (0..1)");
+  const int nb = loss_blocks(P);
+  const int ns = lambda > 0.f ? ssim_blocks(ct) : 0;
+  const size_t need = sizeof(double) * (size_t)(nb + ns) +
+                      (lambda > 0.f ? ssim_workspace_bytes(P) + 256 : 0);
+  if (!workspace || workspace_bytes < need) return invalid("workspace");
   double* partials = reinterpret_cast<double*>(workspace);
   LossViews lv;
   lv.V = V;
@@ -356,14 +364,47 @@ int gs_loss_l1_entropy(const float* image, const float* target, const float* ent
     const double M = (double)ct.c[v].W * ct.c[v].H;
     lv.pix_off[v] = ct.c[v].pix_off;
     lv.w[v] = 1.0 / (M * V);
-    lv.g_img[v] = (float)(1.0 / (3.0 * M * V));
+    lv.g_img[v] = (float)((1.0 - (double)lambda) / (3.0 * M * V));
     lv.g_ent[v] = (float)((double)gamma / (M * V));
   }
   loss_kernel<<<nb, kLossThreads, 0, st>>>(image, target, gamma != 0.f ? entropy : nullptr, lv, P,
-                                           gamma, dL_dimage, dL_dentropy, partials);
-  loss_finalize_kernel<<<1, kLossThreads, 0, st>>>(partials, nb, loss_dev);
-  count_launches(2);
+                                           gamma, 1.0 - (double)lambda, dL_dimage, dL_dentropy,
+                                           partials);
+  count_launches(1);
+  if (lambda > 0.f) {
+    uintptr_t m = reinterpret_cast<uintptr_t>(partials + nb + ns);
+    float* maps = reinterpret_cast<float*>((m + 255) & ~uintptr_t(255));
+    const int e = launch_ssim(image, target, ct, lambda, maps, partials + nb, dL_dimage, st);
+    if (e != GS_OK) return e;
+  }
+  loss_finalize_kernel<<<1, kLossThreads, 0, st>>>(partials, nb + ns, loss_dev);
+  count_launches(1);
   return check_launch();
+}
+}  // namespace
+
+int gs_loss_l1_entropy(const float* image, const float* target, const float* entropy,
+                       const gs_camera* cams, int V, float gamma, double* loss_dev,
+                       float* dL_dimage, float* dL_dentropy, void* workspace,
+                       size_t workspace_bytes, gs_stream stream) {
+  return loss_impl(image, target, entropy, cams, V, 0.f, gamma, loss_dev, dL_dimage, dL_dentropy,
+                   workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+size_t gs_loss_base_workspace_size(const gs_camera* cams, int V) {
+  CamTable ct;
+  if (!build_cam_table(cams, V, nullptr, 0, &ct)) return 0;
+  const long long P = ct.c[V - 1].pix_off + (long long)ct.c[V - 1].W * ct.c[V - 1].H;
+  return sizeof(double) * (size_t)(loss_blocks(P) + ssim_blocks(ct)) + ssim_workspace_bytes(P) +
+         256;
+}
+
+int gs_loss_base(const float* image, const float* target, const float* entropy,
+                 const gs_camera* cams, int V, float lambda, float gamma, double* loss_dev,
+                 float* dL_dimage, float* dL_dentropy, void* workspace, size_t workspace_bytes,
+                 gs_stream stream) {
+  return loss_impl(image, target, entropy, cams, V, lambda, gamma, loss_dev, dL_dimage,
+                   dL_dentropy, workspace, workspace_bytes, (cudaStream_t)stream);
 }
 
 int gs_render_bwd(const gs_proj* proj, int N, const gs_camera* cams, int V, const gs_params* prm,

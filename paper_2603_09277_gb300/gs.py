@@ -90,6 +90,8 @@ def _load():
         "gs_render_fwd": (i, [P(GsProj), i, P(GsCamera), i, P(GsParams), vp, vp, vp, vp, vp, vp,
                               P(GsLaunch), vp]),
         "gs_loss_l1_entropy": (i, [vp, vp, vp, P(GsCamera), i, f, vp, vp, vp, vp, sz, vp]),
+        "gs_loss_base_workspace_size": (sz, [P(GsCamera), i]),
+        "gs_loss_base": (i, [vp, vp, vp, P(GsCamera), i, f, f, vp, vp, vp, vp, sz, vp]),
         "gs_render_bwd": (i, [P(GsProj), i, P(GsCamera), i, P(GsParams), vp, vp, vp, vp, vp, vp,
                               vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, P(GsLaunch), vp]),
         "gs_scale_reset": (i, [vp, ll, f, vp]),
@@ -107,7 +109,8 @@ _lib = _load()
 EXPORTED = ["gs_record_bytes", "gs_total_tiles", "gs_total_pixels", "gs_bin_sort_workspace_size",
             "gs_loss_workspace_size", "gs_tile_queue_workspace_size", "gs_status_string",
             "gs_last_error_string", "gs_version", "gs_kernel_launches", "gs_preprocess", "gs_bin_sort", "gs_render_fwd",
-            "gs_loss_l1_entropy", "gs_render_bwd", "gs_scale_reset", "gs_tile_queue",
+            "gs_loss_l1_entropy", "gs_loss_base_workspace_size", "gs_loss_base",
+            "gs_render_bwd", "gs_scale_reset", "gs_tile_queue",
             "gs_tile_queue_static"]
 
 
@@ -259,6 +262,18 @@ def gs_loss_l1_entropy(image, target, entropy, cams_c, gamma, loss_dev, dL_dimag
                        workspace, stream=None):
     return _check("gs_loss_l1_entropy", _lib.gs_loss_l1_entropy(
         _ptr(image), _ptr(target), _ptr(entropy), cams_c, len(cams_c), float(gamma),
+        _ptr(loss_dev), _ptr(dL_dimage), _ptr(dL_dentropy), _ptr(workspace),
+        workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def gs_loss_base_workspace_size(cams_c):
+    return _lib.gs_loss_base_workspace_size(cams_c, len(cams_c))
+
+
+def gs_loss_base(image, target, entropy, cams_c, lam, gamma, loss_dev, dL_dimage, dL_dentropy,
+                 workspace, stream=None):
+    return _check("gs_loss_base", _lib.gs_loss_base(
+        _ptr(image), _ptr(target), _ptr(entropy), cams_c, len(cams_c), float(lam), float(gamma),
         _ptr(loss_dev), _ptr(dL_dimage), _ptr(dL_dentropy), _ptr(workspace),
         workspace.numel() * workspace.element_size(), _stream(stream)))
 

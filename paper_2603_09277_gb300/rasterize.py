@@ -161,9 +161,23 @@ class Rasterizer:
                          self.tile_ranges, self.image, self.final_T, self.last_idx, self.entropy,
                          self._launch(stats, events), stream)
 
-    def loss(self, target, gamma, stream=None):
-        gs.gs_loss_l1_entropy(self.image, target, self.entropy, self.cams_c, gamma, self.loss_dev,
-                              self.dL_dimage, self.dL_dentropy, self.loss_ws, stream)
+    def _base_ws(self):
+        need = gs.gs_loss_base_workspace_size(self.cams_c)
+        if getattr(self, "loss_base_ws", None) is None or self.loss_base_ws.numel() < need:
+            self.loss_base_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        return self.loss_base_ws
+
+    def loss(self, target, gamma, stream=None, lam=0.0):
+        """L1 + gamma * entropy, or with lam > 0 the full L_base
+        (1 - lam) L1 + lam D-SSIM + gamma * entropy."""
+        if lam > 0.0:
+            gs.gs_loss_base(self.image, target, self.entropy, self.cams_c, lam, gamma,
+                            self.loss_dev, self.dL_dimage, self.dL_dentropy, self._base_ws(),
+                            stream)
+        else:
+            gs.gs_loss_l1_entropy(self.image, target, self.entropy, self.cams_c, gamma,
+                                  self.loss_dev, self.dL_dimage, self.dL_dentropy, self.loss_ws,
+                                  stream)
         return self.loss_dev
 
     def render_bwd(self, p, dL_dimage=None, dL_dentropy="auto", stream=None, events=None):
@@ -232,18 +246,25 @@ def rasterize(params, rast):
 
 class _L1Entropy(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, image, entropy, target, rast, gamma):
-        gs.gs_loss_l1_entropy(image.contiguous(), target, entropy.contiguous(), rast.cams_c, gamma,
-                              rast.loss_dev, rast.dL_dimage, rast.dL_dentropy, rast.loss_ws)
+    def forward(ctx, image, entropy, target, rast, gamma, lam):
+        if lam > 0.0:
+            gs.gs_loss_base(image.contiguous(), target, entropy.contiguous(), rast.cams_c, lam,
+                            gamma, rast.loss_dev, rast.dL_dimage, rast.dL_dentropy,
+                            rast._base_ws())
+        else:
+            gs.gs_loss_l1_entropy(image.contiguous(), target, entropy.contiguous(), rast.cams_c,
+                                  gamma, rast.loss_dev, rast.dL_dimage, rast.dL_dentropy,
+                                  rast.loss_ws)
         ctx.save_for_backward(rast.dL_dimage.clone(), rast.dL_dentropy.clone())
         return rast.loss_dev.clone().to(torch.float32).reshape(())
 
     @staticmethod
     def backward(ctx, g):
         di, de = ctx.saved_tensors
-        return di * g, de * g, None, None, None
+        return di * g, de * g, None, None, None, None
 
 
-def l1_entropy_loss(image, entropy, target, rast, gamma):
-    """L = (1/V) sum_v [mean L1_v + gamma mean H_v], computed by libgs."""
-    return _L1Entropy.apply(image, entropy, target, rast, gamma)
+def l1_entropy_loss(image, entropy, target, rast, gamma, lam=0.0):
+    """L = (1/V) sum_v [(1 - lam) mean L1_v + lam D-SSIM_v + gamma mean H_v],
+    computed by libgs (lam = 0: L1 + entropy)."""
+    return _L1Entropy.apply(image, entropy, target, rast, gamma, float(lam))
