@@ -5,18 +5,23 @@
 //
 // Forward, one CTA per 16x16 block of output pixels of one view: the block and
 // its 5-pixel halo of image and target (all three channels) are staged in
-// shared memory; each thread forms the window moments of its pixel from the
-// 121 samples centred on the pixel's own value c (d = s - c; padding samples
-// are s = 0): mu = c + E[d], sigma^2 = E[d^2] - E[d]^2, so smooth regions do
-// not cancel two large FP32 sums.  Per pixel and channel it writes
-// (mu_x, mu_y, dS/dmu_x, dS/dsigma_x^2, dS/dsigma_xy) for the backward and adds
-// lambda (1 - S) / (3 M_v V) to the loss partials.
+// shared memory.  The window moments are taken about a constant per block and
+// channel (the staged value at the block centre, c): with d = s - c (padding
+// samples s = 0), mu = c + E[d] and sigma^2 = E[d^2] - E[d]^2 hold exactly
+// for any constant, and around a value of the block two large FP32 sums do
+// not cancel in smooth regions.  Because c is constant over the block, the
+// 11x11 window sums are separable: a horizontal pass over the 26 staged rows
+// and a vertical pass per output pixel.  Per pixel and channel the forward
+// saves (mu_x, mu_y, dS/dmu_x, dS/dsigma_x^2, dS/dsigma_xy) (planar, one plane
+// per quantity) and adds lambda (1 - S) / (3 M_v V) to the loss partials.
 //
-// Backward, same blocking over the saved maps:
+// Backward, same blocking:
 //   dL/dx(p) -= lambda / (3 M_v V) sum_q G(q - p) [dS/dmu_x(q)
 //               + 2 (x(p) - mu_x(q)) dS/dsigma_x^2(q) + (y(p) - mu_y(q)) dS/dsigma_xy(q)]
 // over the window centres q inside the image (dsigma_x^2(q)/dx(p) =
-// 2 G(q-p)(x(p) - mu_x(q)) because the window weights sum to 1).
+// 2 G(q-p)(x(p) - mu_x(q)) because the window weights sum to 1); with the
+// block constant c the bracket splits into five separable correlations:
+// G*a + 2 (x(p) - c) G*b - 2 G*((mu_x - c) b) + (y(p) - c') G*e - G*((mu_y - c') e).
 #include <cmath>
 
 #include "gs_internal.cuh"
@@ -46,11 +51,16 @@ __device__ __forceinline__ int view_of_block(const SsimViews& sv, int b) {
   return v;
 }
 
+// Horizontal pass of the separable window: h[k][r][x] = sum_i w_i f_k(r, x + i)
+// for the 26 staged rows and 16 output columns.
+constexpr int kHN = kSsimS * kSsimB;  // 416 horizontal outputs per quantity
+
 __global__ void __launch_bounds__(kSsimThreads) ssim_fwd_kernel(
     const float* __restrict__ image, const float* __restrict__ target, const SsimViews sv,
-    float* __restrict__ maps /* [P][3][5] */, double* __restrict__ partials) {
+    float* __restrict__ maps /* 15 planes of P */, long long P, double* __restrict__ partials) {
   __shared__ float sx[3][kSsimS][kSsimS];
   __shared__ float sy[3][kSsimS][kSsimS];
+  __shared__ float sh[5][kHN];
   const int b = blockIdx.x;
   const int v = view_of_block(sv, b);
   const int lb = b - sv.block_off[v];
@@ -70,26 +80,44 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_fwd_kernel(
   __syncthreads();
   const int lx = threadIdx.x % kSsimB, ly = threadIdx.x / kSsimB;
   const int px = bx + lx, py = by + ly;
+  const bool mine = px < W && py < H;
+  const long long p = base + (long long)py * W + px;
   double acc = 0.0;
-  if (px < W && py < H) {
-    const long long p = base + (long long)py * W + px;
+  for (int ch = 0; ch < 3; ++ch) {
+    const float cx = sx[ch][kSsimR + kSsimB / 2][kSsimR + kSsimB / 2];
+    const float cy = sy[ch][kSsimR + kSsimB / 2][kSsimR + kSsimB / 2];
+    for (int t = threadIdx.x; t < kHN; t += kSsimThreads) {
+      const int r = t / kSsimB, x = t % kSsimB;
+      float m = 0.f, n = 0.f, dd = 0.f, ee = 0.f, de = 0.f;
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      const float cx = sx[ch][ly + kSsimR][lx + kSsimR], cy = sy[ch][ly + kSsimR][lx + kSsimR];
+      for (int i = 0; i < 2 * kSsimR + 1; ++i) {
+        const float w = sv.win[i];
+        const float d = sx[ch][r][x + i] - cx, e = sy[ch][r][x + i] - cy;
+        const float wd = w * d, we = w * e;
+        m += wd;
+        n += we;
+        dd = __fmaf_rn(wd, d, dd);
+        ee = __fmaf_rn(we, e, ee);
+        de = __fmaf_rn(wd, e, de);
+      }
+      sh[0][t] = m;
+      sh[1][t] = n;
+      sh[2][t] = dd;
+      sh[3][t] = ee;
+      sh[4][t] = de;
+    }
+    __syncthreads();
+    if (mine) {
       float m1 = 0.f, n1 = 0.f, dxx = 0.f, dyy = 0.f, dxy = 0.f;
-      for (int j = 0; j < 2 * kSsimR + 1; ++j) {
-        const float wj = sv.win[j];
 #pragma unroll
-        for (int i = 0; i < 2 * kSsimR + 1; ++i) {
-          const float w = wj * sv.win[i];
-          const float d = sx[ch][ly + j][lx + i] - cx, e = sy[ch][ly + j][lx + i] - cy;
-          const float wd = w * d, we = w * e;
-          m1 += wd;
-          n1 += we;
-          dxx = __fmaf_rn(wd, d, dxx);
-          dyy = __fmaf_rn(we, e, dyy);
-          dxy = __fmaf_rn(wd, e, dxy);
-        }
+      for (int j = 0; j < 2 * kSsimR + 1; ++j) {
+        const float w = sv.win[j];
+        const int t = (ly + j) * kSsimB + lx;
+        m1 = __fmaf_rn(w, sh[0][t], m1);
+        n1 = __fmaf_rn(w, sh[1][t], n1);
+        dxx = __fmaf_rn(w, sh[2][t], dxx);
+        dyy = __fmaf_rn(w, sh[3][t], dyy);
+        dxy = __fmaf_rn(w, sh[4][t], dxy);
       }
       const float mx = cx + m1, my = cy + n1;
       const float sxx = __fmaf_rn(-m1, m1, dxx), syy = __fmaf_rn(-n1, n1, dyy);
@@ -99,13 +127,14 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_fwd_kernel(
       const float D = B1 * B2;
       const float S = A1 * A2 / D;
       acc += (double)(1.f - S);
-      float* m = maps + 15 * p + 5 * ch;
+      float* m = maps + (long long)(5 * ch) * P + p;
       m[0] = mx;
-      m[1] = my;
-      m[2] = (2.f * my * A2 - S * 2.f * mx * B2) / D;  // dS/dmu_x, sigmas fixed
-      m[3] = -S / B2;                                  // dS/dsigma_x^2
-      m[4] = 2.f * A1 / D;                             // dS/dsigma_xy
+      m[P] = my;
+      m[2 * P] = (2.f * my * A2 - S * 2.f * mx * B2) / D;  // dS/dmu_x, sigmas fixed
+      m[3 * P] = -S / B2;                                  // dS/dsigma_x^2
+      m[4 * P] = 2.f * A1 / D;                             // dS/dsigma_xy
     }
+    __syncthreads();  // sh is rewritten for the next channel
   }
   acc *= (double)sv.scale[v];
   __shared__ double s_red[kSsimThreads / 32];
@@ -122,8 +151,10 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_fwd_kernel(
 
 __global__ void __launch_bounds__(kSsimThreads) ssim_bwd_kernel(
     const float* __restrict__ image, const float* __restrict__ target, const SsimViews sv,
-    const float* __restrict__ maps, float* __restrict__ dimg) {
+    const float* __restrict__ maps, long long P, float* __restrict__ dimg) {
   __shared__ float sm[5][kSsimS][kSsimS];  // one channel at a time
+  __shared__ float sh[5][kHN];
+  __shared__ float s_c[2];
   const int b = blockIdx.x;
   const int v = view_of_block(sv, b);
   const int lb = b - sv.block_off[v];
@@ -134,31 +165,61 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_bwd_kernel(
   const int px = bx + lx, py = by + ly;
   const bool mine = px < W && py < H;
   const long long p = base + (long long)py * W + px;
+  // block constants: the image and target at the block's first pixel
+  const long long p0 = base + (long long)by * W + bx;
   for (int ch = 0; ch < 3; ++ch) {
-    __syncthreads();  // the previous channel's readers are done
+    if (threadIdx.x == 0) {
+      s_c[0] = image[3 * p0 + ch];
+      s_c[1] = target[3 * p0 + ch];
+    }
+    __syncthreads();  // (also: the previous channel's readers are done)
+    const float cx = s_c[0], cy = s_c[1];
+    const float* mp = maps + (long long)(5 * ch) * P;
     for (int i = threadIdx.x; i < kSsimS * kSsimS; i += kSsimThreads) {
       const int yy = by - kSsimR + i / kSsimS, xx = bx - kSsimR + i % kSsimS;
       const bool in = xx >= 0 && xx < W && yy >= 0 && yy < H;  // window centres in the image
       const long long q = base + (long long)yy * W + xx;
+      float a = 0.f, bb = 0.f, e = 0.f, pm = 0.f, qm = 0.f;
+      if (in) {
+        const float mx = mp[q], my = mp[P + q];
+        a = mp[2 * P + q];
+        bb = mp[3 * P + q];
+        e = mp[4 * P + q];
+        pm = (mx - cx) * bb;
+        qm = (my - cy) * e;
+      }
+      sm[0][i / kSsimS][i % kSsimS] = a;
+      sm[1][i / kSsimS][i % kSsimS] = bb;
+      sm[2][i / kSsimS][i % kSsimS] = e;
+      sm[3][i / kSsimS][i % kSsimS] = pm;
+      sm[4][i / kSsimS][i % kSsimS] = qm;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kHN; t += kSsimThreads) {
+      const int r = t / kSsimB, x = t % kSsimB;
+      float h[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int k = 0; k < 5; ++k) sm[k][i / kSsimS][i % kSsimS] = in ? maps[15 * q + 5 * ch + k] : 0.f;
+      for (int i = 0; i < 2 * kSsimR + 1; ++i) {
+        const float w = sv.win[i];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) h[k] = __fmaf_rn(w, sm[k][r][x + i], h[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < 5; ++k) sh[k][t] = h[k];
     }
     __syncthreads();
     if (mine) {
-      const float xp = image[3 * p + ch], yp = target[3 * p + ch];
-      float acc = 0.f;
-      for (int j = 0; j < 2 * kSsimR + 1; ++j) {
-        const float wj = sv.win[j];
+      float g[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int i = 0; i < 2 * kSsimR + 1; ++i) {
-          const float w = wj * sv.win[i];
-          const int r = ly + j, c = lx + i;
-          const float t = __fmaf_rn(2.f * (xp - sm[0][r][c]), sm[3][r][c],
-                                    __fmaf_rn(yp - sm[1][r][c], sm[4][r][c], sm[2][r][c]));
-          acc = __fmaf_rn(w, t, acc);
-        }
+      for (int j = 0; j < 2 * kSsimR + 1; ++j) {
+        const float w = sv.win[j];
+        const int t = (ly + j) * kSsimB + lx;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) g[k] = __fmaf_rn(w, sh[k][t], g[k]);
       }
-      dimg[3 * p + ch] -= sv.scale[v] * acc;
+      const float xp = image[3 * p + ch], yp = target[3 * p + ch];
+      const float grad = g[0] + 2.f * ((xp - cx) * g[1] - g[3]) + (yp - cy) * g[2] - g[4];
+      dimg[3 * p + ch] -= sv.scale[v] * grad;
     }
   }
 }
@@ -202,8 +263,9 @@ int launch_ssim(const float* image, const float* target, const CamTable& ct, flo
   }
   const int nb = sv.block_off[ct.V];
   if (nb == 0) return GS_OK;
-  ssim_fwd_kernel<<<nb, kSsimThreads, 0, st>>>(image, target, sv, maps, partials);
-  ssim_bwd_kernel<<<nb, kSsimThreads, 0, st>>>(image, target, sv, maps, dimg);
+  const long long P = ct.c[ct.V - 1].pix_off + (long long)ct.c[ct.V - 1].W * ct.c[ct.V - 1].H;
+  ssim_fwd_kernel<<<nb, kSsimThreads, 0, st>>>(image, target, sv, maps, P, partials);
+  ssim_bwd_kernel<<<nb, kSsimThreads, 0, st>>>(image, target, sv, maps, P, dimg);
   count_launches(2);
   return check_launch();
 }
