@@ -106,9 +106,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(ScanSrc src, 
 
 // Phase 2: exclusive scan of the block sums in one block; writes the grand
 // total to *total.
-__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(unsigned long long* block_sums,
-                                                                   int nblocks,
-                                                                   long long* total) {
+__device__ __forceinline__ long long scan_blocks_dev(unsigned long long* block_sums, int nblocks) {
   __shared__ unsigned long long s_carry;
   if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
@@ -122,7 +120,36 @@ __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(unsigned long
     if (threadIdx.x == 0) s_carry += tot;
     __syncthreads();
   }
-  if (threadIdx.x == 0) *total = (long long)s_carry;
+  const long long t = (long long)s_carry;
+  __syncthreads();
+  return t;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(unsigned long long* block_sums,
+                                                                   int nblocks,
+                                                                   long long* total) {
+  const long long t = scan_blocks_dev(block_sums, nblocks);
+  if (threadIdx.x == 0) *total = t;
+}
+
+// Exclusive scans of the super-tile counts (sums_q) and the pair counts
+// (sums_p) over the blocks, then the capacity check: P, Q, the reported
+// count, the status and the counts later stages use (0 on overflow).
+__global__ void __launch_bounds__(kScanThreads) scan_counts_check_kernel(
+    unsigned long long* sums_q, unsigned long long* sums_p, int nblocks, long long capacity,
+    long long* Q, long long* P, long long* q_eff, long long* p_eff, long long* num_pairs_dev,
+    int* status) {
+  const long long q = scan_blocks_dev(sums_q, nblocks);
+  const long long pp = scan_blocks_dev(sums_p, nblocks);
+  if (threadIdx.x == 0) {
+    const bool over = pp > capacity;
+    *Q = q;
+    *P = pp;
+    *num_pairs_dev = pp;
+    *status = over ? GS_ERR_CAPACITY : GS_OK;
+    *p_eff = over ? 0 : pp;  // on overflow every later stage sees zero pairs
+    *q_eff = over ? 0 : q;   // (Q <= P: a super-pair holds at least one pair)
+  }
 }
 
 // Phase 3 (compaction form): rows with tiles_touched > 0 are written, in
@@ -210,10 +237,14 @@ __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
   }
 }
 
-// out[i] = exclusive prefix of the super-tile counts in depth order.
+// out[i] = exclusive prefix of the super-tile counts in depth order; and for
+// every block of kDupPairs items (b < n_marks) the row that owns its first
+// item (block_row[b]), for the load-balanced duplication.
+constexpr int kDupPairsScan = 1024;
 __global__ void __launch_bounds__(kScanThreads) row_offsets_kernel(
     const int4* __restrict__ rect_sorted, const long long* __restrict__ n_dev,
-    const unsigned long long* __restrict__ block_offsets, unsigned long long* __restrict__ out) {
+    const unsigned long long* __restrict__ block_offsets, unsigned long long* __restrict__ out,
+    unsigned* __restrict__ block_row, long long n_marks) {
   const long long n = *n_dev;
   const long long base = (long long)blockIdx.x * kScanTile;
   const long long first = base + (long long)threadIdx.x * kScanItems;
@@ -229,7 +260,12 @@ __global__ void __launch_bounds__(kScanThreads) row_offsets_kernel(
   unsigned long long off = block_excl_scan(sum, &tot) + block_offsets[blockIdx.x];
   for (int k = 0; k < kScanItems; ++k) {
     const long long i = first + k;
-    if (i < n) out[i] = off;
+    if (i < n) {
+      out[i] = off;
+      for (unsigned long long b = (off + kDupPairsScan - 1) / kDupPairsScan;
+           b * kDupPairsScan < off + loc[k] && (long long)b < n_marks; ++b)
+        block_row[b] = (unsigned)i;
+    }
     off += loc[k];
   }
 }
@@ -433,24 +469,12 @@ __global__ void __launch_bounds__(kRadixThreads, 3) radix_downsweep_kernel(
 }
 
 // ----------------------------------------------------------------------------
-// Capacity check, super-pair generation, per-tile expansion.
+// Super-pair generation, per-tile expansion.
 // ----------------------------------------------------------------------------
-__global__ void capacity_check_kernel(const long long* __restrict__ P,
-                                      const long long* __restrict__ Q, long long capacity,
-                                      int* __restrict__ status, long long* __restrict__ p_eff,
-                                      long long* __restrict__ q_eff) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    bool over = *P > capacity;
-    *status = over ? GS_ERR_CAPACITY : GS_OK;
-    *p_eff = over ? 0 : *P;  // on overflow every later stage sees zero pairs
-    *q_eff = over ? 0 : *Q;  // (Q <= P: a super-pair holds at least one pair)
-  }
-}
-
 // Super-pair duplication, load-balanced over super-pairs.  The depth-sorted
 // visible rows own contiguous ranges [offset_j, offset_j + count_j) of
 // (super-tile, row) items.  Items are cut into blocks of kDupPairs;
-// mark_block_starts records, for every block, the row that owns its first
+// row_offsets_kernel records, for every block, the row that owns its first
 // item, and duplicate_kernel has each CTA load the descriptors of the rows
 // overlapping its items into shared memory, mark where each row starts, and
 // find the owner of every item with a block-wide max-scan of those marks.
@@ -459,21 +483,7 @@ __global__ void capacity_check_kernel(const long long* __restrict__ P,
 constexpr int kDupThreads = 256;
 constexpr int kDupPairs = 1024;
 static_assert(kDupPairs == 4 * kDupThreads, "duplicate_kernel stores 4 items per thread");
-
-__global__ void __launch_bounds__(256) mark_block_starts_kernel(
-    const int4* __restrict__ rect_sorted, const long long* __restrict__ n_vis,
-    const unsigned long long* __restrict__ offsets, const long long* __restrict__ q_eff,
-    unsigned* __restrict__ block_row) {
-  const long long n = *n_vis;
-  if (*q_eff == 0) return;
-  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-       j += (long long)gridDim.x * blockDim.x) {
-    const unsigned long long o = offsets[j];
-    const unsigned long long c = st_count(rect_sorted[j]);
-    for (unsigned long long b = (o + kDupPairs - 1) / kDupPairs; b * kDupPairs < o + c; ++b)
-      block_row[b] = (unsigned)j;
-  }
-}
+static_assert(kDupPairs == kDupPairsScan, "row_offsets_kernel marks the duplication blocks");
 
 __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
     const unsigned* __restrict__ rows, const int4* __restrict__ rect_sorted,
@@ -644,13 +654,32 @@ __device__ __forceinline__ int view_of_st(const CamTable& ct, int s) {
 // Segments of every super-tile: seg_first[s] (exclusive scan of
 // ceil(len_s / kSeg)), seg_first[S] = total, seg_st[g] = super-tile of g.
 // One CTA of 1024 threads.
-__global__ void __launch_bounds__(1024) st_segments_kernel(const uint2* __restrict__ st_ranges,
-                                                           int S, unsigned* __restrict__ seg_first,
+__global__ void __launch_bounds__(1024) st_segments_kernel(uint2* __restrict__ st_ranges,
+                                                           int S, const unsigned* __restrict__ totals,
+                                                           const long long* __restrict__ q_eff,
+                                                           unsigned* __restrict__ seg_first,
                                                            unsigned* __restrict__ seg_st,
                                                            long long* __restrict__ n_seg) {
   __shared__ unsigned s_w[32];
   __shared__ unsigned s_carry;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (totals) {
+    // one radix pass sorted the items by super-tile (S <= 256): the per-digit
+    // totals are the per-super-tile counts, and their exclusive scan the starts
+    __shared__ unsigned s_tot[256];
+    if (tid < 256) s_tot[tid] = tid < S ? totals[tid] : 0u;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned run = 0u;
+      for (int t = 0; t < S; ++t) {
+        st_ranges[t] = make_uint2(s_tot[t] ? run : 0u, s_tot[t] ? run + s_tot[t] : 0u);
+        run += s_tot[t];
+      }
+    }
+  } else if (S == 1 && tid == 0) {  // no sort: one super-tile holds every item
+    const unsigned q = (unsigned)*q_eff;
+    st_ranges[0] = make_uint2(0u, q);
+  }
   if (tid == 0) s_carry = 0u;
   __syncthreads();
   for (int base = 0; base < S; base += 1024) {
@@ -967,9 +996,6 @@ __global__ void __launch_bounds__(256) st_emit_kernel(
   }
 }
 
-__global__ void set_count_kernel(long long* __restrict__ dst, const long long* __restrict__ src) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *dst = *src;
-}
 
 __global__ void set_value_kernel(long long* __restrict__ dst, long long v) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
@@ -1065,13 +1091,14 @@ int radix_resident_ctas() {
 }
 
 int radix_sort(unsigned* k[2], unsigned* v[2], const long long* n_dev, long long n_bound, int bits,
-               unsigned* hist, cudaStream_t st) {
+               unsigned* hist, cudaStream_t st, int* grid_out = nullptr) {
   int cur = 0;
   if (n_bound == 0) return cur;
   // one wave: at most the CTAs of the scatter kernel resident on the device
   int grid = (int)std::min<long long>(std::min(kRadixGrid, radix_resident_ctas()),
                                       (n_bound + kRadixTile - 1) / kRadixTile);
   if (grid < 1) grid = 1;
+  if (grid_out) *grid_out = grid;
   // the fewest 8-bit-or-narrower passes, with equal digit widths
   const int passes = (bits + 7) / 8;
   const int dbits = passes ? (bits + passes - 1) / passes : 0;
@@ -1132,15 +1159,20 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
     //    and the pair count P
     rows_gather_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(
         rows_sorted, n_vis, proj->rect, N, ct, w.rect_sorted, w.block_sums, w.block_sums2);
-    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(w.block_sums, (int)nb, Q);
-    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(w.block_sums2, (int)nb, P);
-    row_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(w.rect_sorted, n_vis, w.block_sums,
-                                                              w.offsets);
-    count_launches(7);
+    count_launches(4);
   }
-  capacity_check_kernel<<<1, 32, 0, st>>>(P, Q, cap, status_dev, p_eff, q_eff);
-  set_count_kernel<<<1, 32, 0, st>>>(num_pairs_dev, P);
-  count_launches(2);
+  // scans of Q and P over the blocks, the capacity check and the reported count
+  scan_counts_check_kernel<<<1, kScanThreads, 0, st>>>(w.block_sums, w.block_sums2,
+                                                       n_rows > 0 ? (int)nb : 0, cap, Q, P, q_eff,
+                                                       p_eff, num_pairs_dev, status_dev);
+  count_launches(1);
+  if (n_rows > 0) {
+    // super-tile offsets per row, and the first row of every duplication block
+    row_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(
+        w.rect_sorted, n_vis, w.block_sums, w.offsets, w.block_row,
+        (cap + kDupPairs - 1) / kDupPairs + 1);
+    count_launches(1);
+  }
   GS_TRY_CUDA(cudaGetLastError());
   long long p_bound = cap;
   if (num_pairs_host) {
@@ -1178,27 +1210,33 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
   for (int v = 0; v < ct.V; ++v)
     if (ct.c[v].TX > 8000 || ct.c[v].TY > 8000) packed = 0;
   {
-    const unsigned g1 = (unsigned)std::min<long long>((n_rows + 255) / 256, 152ll * 32);
-    mark_block_starts_kernel<<<g1, 256, 0, st>>>(w.rect_sorted, n_vis, w.offsets, q_eff,
-                                                w.block_row);
     const unsigned g2 = (unsigned)((q_bound + kDupPairs - 1) / kDupPairs);
     const int vec16 = (reinterpret_cast<uintptr_t>(sv[0]) % 16 == 0) ? 1 : 0;
     duplicate_kernel<<<g2, kDupThreads, 0, st>>>(rows_sorted, w.rect_sorted, n_vis, w.offsets, N,
                                                 ct, q_eff, w.block_row, sk[0], sv[0], vec16,
                                                 packed);
-    count_launches(2);
+    count_launches(1);
   }
   // 5. stable sort of the super-pairs by super-tile id
-  const int sres = radix_sort(sk, sv, q_eff, q_bound, sbits, w.hist, st);
+  int sgrid = 0;
+  const int sres = radix_sort(sk, sv, q_eff, q_bound, sbits, w.hist, st, &sgrid);
   const unsigned* sp_keys = sk[sres];
   const unsigned* sp_rows = sv[sres];  // == w.pv
   unsigned* desc = sk[1 - sres];
-  // 6. rows of every super-tile, segments, per-tile counts and list starts
-  GS_TRY_CUDA(cudaMemsetAsync(w.st_ranges, 0, 2 * sizeof(unsigned) * (size_t)S, st));
-  const unsigned gq = (unsigned)std::min<long long>((q_bound + 1023) / 1024, 152ll * 16);
-  ranges_kernel<<<gq, 256, 0, st>>>(sp_keys, q_eff, packed ? 0xffffu : 0xffffffffu, w.st_ranges);
-  st_segments_kernel<<<1, 1024, 0, st>>>(reinterpret_cast<const uint2*>(w.st_ranges), S,
-                                         w.seg_first, w.seg_st, n_seg);
+  // 6. rows of every super-tile (from the one-pass sort's digit totals, or
+  //    marked on the sorted keys), segments, per-tile counts and list starts
+  const unsigned* st_totals = nullptr;
+  if (spasses == 1) {
+    st_totals = w.hist + kRadixBins * sgrid;
+  } else if (spasses > 1) {
+    GS_TRY_CUDA(cudaMemsetAsync(w.st_ranges, 0, 2 * sizeof(unsigned) * (size_t)S, st));
+    const unsigned gq = (unsigned)std::min<long long>((q_bound + 1023) / 1024, 152ll * 16);
+    ranges_kernel<<<gq, 256, 0, st>>>(sp_keys, q_eff, packed ? 0xffffu : 0xffffffffu,
+                                      w.st_ranges);
+    count_launches(1);
+  }
+  st_segments_kernel<<<1, 1024, 0, st>>>(reinterpret_cast<uint2*>(w.st_ranges), S, st_totals,
+                                         q_eff, w.seg_first, w.seg_st, n_seg);
   const unsigned gs = (unsigned)std::min<long long>(max_segments(q_bound, S), 152ll * 8);
   st_count_kernel<<<gs, 256, 0, st>>>(sp_keys, sp_rows,
                                       reinterpret_cast<const uint2*>(w.st_ranges), w.seg_first,
@@ -1211,7 +1249,7 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
                                      reinterpret_cast<const uint2*>(w.st_ranges), w.seg_first,
                                      w.seg_st, n_seg, w.seg_hist, w.tile_start, ct, proj->depth,
                                      sorted_vals, sorted_keys);
-  count_launches(6);
+  count_launches(5);
   return check_launch();
 }
 
