@@ -7,7 +7,7 @@ downsampling factor r >= 1, from coarse to full resolution; the largest factor
 r_max is chosen so that the mean number of Gaussians per tile stays below a
 threshold (about 150 in the paper), and it is capped at 4.  The paper adopts
 the rest of the schedule from DashGaussian without stating it; the reading
-here (see DESIGN.md) is integer levels r_max, r_max - 1, ..., 2 over equal
+here is integer levels r_max, r_max - 1, ..., 2 over equal
 shares of the first `coarse_fraction` of the epochs, then r = 1.
 
 Epoch schedule (Sec. 5.2, "Scale Reset and Entropy Constraint"): an epoch is a
