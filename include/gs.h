@@ -244,8 +244,13 @@ int gs_loss_base(const float* image, const float* target, const float* entropy,
  * (Suppl. C), colour; then through the projection to the parameters.
  *   dL_dimage [P][3], dL_dentropy [P] (may be NULL: no entropy term),
  *   final_T, last_idx: from gs_render_fwd.  Parameters as in gs_preprocess.
- *   grad2d [V*N][12] device scratch/output (zeroed by the call): per row
- *   dL/d(mean2d x, y, conic a, b, c, sigma, r, g, b) and 3 pad floats.
+ *   grad2d [V*N][12] device scratch/output (zeroed by the call): per row,
+ *   summed over the pixels where the row is blended, the moments
+ *   dd dx, dd dy, dd dx^2, dd dx dy, dd dy^2, dd (dd = dL/dalpha alpha where
+ *   alpha is below its clamp, 0 where clamped; dx, dy = pixel centre minus
+ *   the 2D mean), then dL/d(r, g, b) and 3 pad floats.  From these,
+ *   dL/dsigma = dd-sum / sigma, dL/dconic = -(1/2) sum dd d d^T and
+ *   dL/dmean2d = conic (dd dx-sum, dd dy-sum).
  *   g_* : device, shapes of the parameters, overwritten. */
 int gs_render_bwd(const gs_proj* proj, int N, const gs_camera* cams_host, int V,
                   const gs_params* prm, const unsigned* sorted_vals, const unsigned* tile_ranges,

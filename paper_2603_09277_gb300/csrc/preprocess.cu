@@ -401,7 +401,14 @@ __global__ void __launch_bounds__(256) preprocess_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint of the projection.  grad2d rows: dL/d(mx, my, a, b, c, sigma, r, g, b).
+// Adjoint of the projection.  grad2d rows, summed over the pixels of every
+// blended pair of the row: dd (dx, dy, dx^2, dx dy, dy^2, 1) and w (r, g, b),
+// with dd = dL/dalpha alpha where alpha is not clamped and (dx, dy) the
+// pixel centre minus the 2D mean.  Since alpha = sigma exp(-d^T K d / 2)
+// (K the conic, d = pixel - mean):
+//   dL/dsigma = sum dd / sigma,  dL/dK = -(1/2) sum dd d d^T
+//   (so dL/da = -Sxx / 2, dL/db = -Sxy with b counted twice in d^T K d,
+//   dL/dc = -Syy / 2),  dL/dmean = K (Sx, Sy).
 // ---------------------------------------------------------------------------
 // Adjoint of one Gaussian (visible in at least one view); the outputs arrive
 // zeroed.
@@ -425,12 +432,14 @@ __device__ __forceinline__ void adjoint_one(
     if (tiles_touched[row] == 0u) continue;
     const float4* G4 = reinterpret_cast<const float4*>(grad2d + row * 12);
     float4 G0 = G4[0], G1 = G4[1], G2 = G4[2];
-    // G0 = (mx, my, a, b), G1 = (c, sigma, r, g), G2 = (b, pad, pad, pad)
+    // G0 = (Sx, Sy, Sxx, Sxy), G1 = (Syy, S1, r, g), G2 = (b, pad, pad, pad)
     const CamInfo& c = ct.c[v];
     float depth = depth_of(c, a.mean);
     Projected p = project(c, a, depth, dilation);
 
-    gsig += G1.y;
+    gsig += G1.y;  // sum dd; dL/dlogit = (sum dd / sigma) sigma (1 - sigma)
+    const float gmx = p.ca * G0.x + p.cb * G0.y;  // dL/dmean2d = K (Sx, Sy)
+    const float gmy = p.cb * G0.x + p.cc * G0.y;
 
     // --- colour -> SH coefficients and view direction
     float vx = a.mean[0] - c.cp[0], vy = a.mean[1] - c.cp[1], vz = a.mean[2] - c.cp[2];
@@ -498,7 +507,7 @@ __device__ __forceinline__ void adjoint_one(
       Z[j] = a.s[j] * (Th[0] * a.Rq[j] + Th[1] * a.Rq[3 + j] + Th[2] * a.Rq[6 + j]);
       Z[3 + j] = a.s[j] * (Th[3] * a.Rq[j] + Th[4] * a.Rq[3 + j] + Th[5] * a.Rq[6 + j]);
     }
-    const float ga = G0.z, gbh = 0.5f * G0.w, gc = G1.x;
+    const float ga = -0.5f * G0.z, gbh = -0.5f * G0.w, gc = -0.5f * G1.x;
     const float G00 = i11 * i11 * ga;
     const float G01 = i11 * (i21 * ga + i22 * gbh);
     const float G11 = i21 * i21 * ga + 2.f * i21 * i22 * gbh + i22 * i22 * gc;
@@ -546,9 +555,9 @@ __device__ __forceinline__ void adjoint_one(
       gty += -gJ12 * c.fy * itz * itz;
       gtz += -2.f * gJ12 * p.J12 * itz;
     }
-    gtx += G0.x * c.fx * itz;
-    gty += G0.y * c.fy * itz;
-    gtz += -(G0.x * c.fx * p.ux + G0.y * c.fy * p.uy) * itz;
+    gtx += gmx * c.fx * itz;
+    gty += gmy * c.fy * itz;
+    gtz += -(gmx * c.fx * p.ux + gmy * c.fy * p.uy) * itz;
     // --- t = W mean + t_w
     gm[0] += c.R[0] * gtx + c.R[3] * gty + c.R[6] * gtz;
     gm[1] += c.R[1] * gtx + c.R[4] * gty + c.R[7] * gtz;
@@ -557,7 +566,7 @@ __device__ __forceinline__ void adjoint_one(
   g_means[3ll * g] = gm[0];
   g_means[3ll * g + 1] = gm[1];
   g_means[3ll * g + 2] = gm[2];
-  g_opac[g] = gsig * a.sigma * (1.f - a.sigma);
+  g_opac[g] = gsig * (1.f - a.sigma);
 
   for (int j = 0; j < 3; ++j) g_ls[3ll * g + j] = gls[j];
   const float* GR = gRq;

@@ -25,12 +25,16 @@
 //   S += w_i c_i; R += (ln w_i + 1) w_i    (R starts at (ln T_N+1 + 1) T_N+1)
 //   (only g . S is needed, so it is carried instead of S: g . S += w_i g . c_i;
 //   R and gH are carried in base-2 units, R / ln 2 and gH ln 2)
-//   then dsigma = dalpha g, dd = dalpha alpha (unless clamped),
+//   then with dd = dalpha alpha (where alpha is not clamped) and (dx, dy)
+//   the pixel centre minus the 2D mean: dsigma = dd / sigma,
 //   dconic = dd (-dx^2/2, -dx dy, -dy^2/2), dmean = dd conic (dx, dy).
-// The thread sums the 9 per-Gaussian values over its pixels, the warp sums
-// them with a split-transpose shuffle reduction (12 shuffles leave one of
-// the 9 totals in each of 9 lane pairs) and 9 lanes add them to grad2d with
-// one atomic instruction.
+//   Every one of these is linear in the moments dd (1, dx, dy, dx^2, dx dy,
+//   dy^2), so the kernel sums the moments and the projection's adjoint
+//   applies 1 / sigma, the conic and the signs once per Gaussian.
+// The thread sums the 9 per-Gaussian values (6 moments, 3 colour weights)
+// over its pixels, the warp sums them with a split-transpose shuffle
+// reduction (12 shuffles leave one of the 9 totals in each of 9 lane pairs)
+// and 9 lanes add them to grad2d with one atomic instruction.
 //
 // Launch forms: one CTA per tile (optionally in a given tile order), or a
 // persistent grid whose CTAs claim tiles from a queue with one atomicAdd per
@@ -306,7 +310,7 @@ struct BwdArgs {
   const unsigned* last_idx;
   const float* dL_dimage;
   const float* dL_dentropy;
-  float* grad2d;  // [rows][12]
+  float* grad2d;  // [rows][12]: sums dd (dx, dy, dx^2, dx dy, dy^2, 1), w (r, g, b), pad
   const unsigned* order;
   unsigned* counter;
 };
@@ -357,7 +361,7 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
                                          const BwdArgs& a, int tile) {
   __shared__ float4 s0[kBatch];
   __shared__ float4 s1[kBatch];
-  __shared__ float2 s2[kBatch];  // (B, 1 / sigma)
+  __shared__ float s2[kBatch];  // B
   __shared__ unsigned s_row[kBatch];
   __shared__ unsigned short s_rows[kBatch];
   constexpr int NT = TileGeom<TS, PPT>::kThreads;
@@ -407,7 +411,7 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
       const float2 m = tile_relative_mean(s, tg.ox, tg.oy);
       s0[j] = make_float4(m.x, m.y, s.f11, s.f21);
       s1[j] = make_float4(s.f22, s.L2S, s.R, s.G);
-      s2[j] = make_float2(s.B, 1.f / s.sigma);
+      s2[j] = s.B;
       s_row[j] = row;
       s_rows[j] = (unsigned short)splat_rows<TS>(m.x, m.y, s.f11, s.f21, s.f22, s.L2S,
                                                  rc.log2_alpha_min, tg.xmax, tg.rows);
@@ -429,7 +433,7 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
       if (any_here) {
         const float4 g0 = s0[k];
         const float4 g1 = s1[k];
-        const float2 g2 = s2[k];
+        const float cB = s2[k];
         const float dx = tg.rx - g0.x;
         const SplatColumn col = splat_column(g0.z, g0.w, g1.y, dx);
 #pragma unroll
@@ -447,7 +451,7 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
           const float w = alpha * Ti;
           const float L = fast_log2(w) + kLog2e;
           // colour part: dL/dC . (T_i c_i - S / (1 - alpha_i)) = T_i gc - gS / (1 - alpha_i)
-          const float gc = __fmaf_rn(gb[q], g2.x, __fmaf_rn(gg[q], g1.w, gr[q] * g1.z));
+          const float gc = __fmaf_rn(gb[q], cB, __fmaf_rn(gg[q], g1.w, gr[q] * g1.z));
           float dA = __fmaf_rn(Ti, gc, -gS[q] * iom);
           dA = __fmaf_rn(gH[q], __fmaf_rn(-L, Ti, Rent[q] * iom), dA);
           gsum[6] += w * gr[q];
@@ -458,14 +462,13 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
           T[q] = Ti;
           if (araw <= rc.alpha_max) {
             const float dd = dA * araw;
-            gsum[5] += dd * g2.y;  // dA * g with g = araw / sigma
-            gsum[2] += -0.5f * dd * dx * dx;
-            gsum[3] += -dd * dx * dy;
-            gsum[4] += -0.5f * dd * dy * dy;
-            // d d / d mean = conic (dx, dy) = F^T (p, q) / (log2(e) / 2)
-            const float k2 = 2.f * kLn2 * dd;
-            gsum[0] += k2 * (g0.z * col.p + g0.w * qq);
-            gsum[1] += k2 * (g1.x * qq);
+            const float ddx = dd * dx, ddy = dd * dy;
+            gsum[0] += ddx;
+            gsum[1] += ddy;
+            gsum[2] = __fmaf_rn(ddx, dx, gsum[2]);
+            gsum[3] = __fmaf_rn(ddx, dy, gsum[3]);
+            gsum[4] = __fmaf_rn(ddy, dy, gsum[4]);
+            gsum[5] += dd;
           }
         }
       }
