@@ -49,7 +49,7 @@ L2_BYTES = 129 * 1024 * 1024
 #             gradient 3, S and R updates 9, alpha->sigma,d 2, conic 12,
 #             mean 8, per-pixel summation of the 9 gradients 9)
 FWD_EVAL, FWD_BLEND = 10, 14
-BWD_EVAL, BWD_BLEND = 10, 72
+BWD_EVAL, BWD_BLEND = 10, 56
 
 
 def log(*a):
