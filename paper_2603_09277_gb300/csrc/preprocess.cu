@@ -156,17 +156,6 @@ __device__ __forceinline__ Activated activate(const float* means, const float* l
   return a;
 }
 
-// Camera-space mean.  The depth is the FP32 rounding of the FP64 value
-// ((R20 mx + R21 my) + R22 mz) + t2 (products of FP32 values are exact in
-// FP64, so the result does not depend on FMA contraction).
-__device__ __forceinline__ float depth_of(const CamInfo& c, const float* m) {
-  double z = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)c.R[6], (double)m[0]),
-                                           __dmul_rn((double)c.R[7], (double)m[1])),
-                                 __dmul_rn((double)c.R[8], (double)m[2])),
-                       (double)c.t[2]);
-  return __double2float_rn(z);
-}
-
 // ---------------------------------------------------------------------------
 // Error-free FP32 transformations (FP32x2 "double-float" arithmetic): the
 // camera-space mean and the 2D mean are carried as unevaluated sums hi + lo,
@@ -203,6 +192,48 @@ __device__ __forceinline__ F2 dot3_plus(float r0, float r1, float r2, const floa
   float err = __fadd_rn(__fadd_rn(__fadd_rn(p0.lo, p1.lo), __fadd_rn(p2.lo, s1.lo)),
                         __fadd_rn(s2.lo, s3.lo));
   return fast_two_sum(s3.hi, err);
+}
+
+// Camera-space depth, defined as the FP32 rounding of the FP64 value
+// ((R20 mx + R21 my) + R22 mz) + t2 (products of FP32 values are exact in
+// FP64, so the value does not depend on FMA contraction).
+__device__ __forceinline__ float depth_fp64(const CamInfo& c, const float* m) {
+  double z = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)c.R[6], (double)m[0]),
+                                           __dmul_rn((double)c.R[7], (double)m[1])),
+                                 __dmul_rn((double)c.R[8], (double)m[2])),
+                       (double)c.t[2]);
+  return __double2float_rn(z);
+}
+
+// The same value without FP64 arithmetic in all but rare cases (FP64 runs at
+// a small fraction of the FP32 rate here).  With S the exact sum and A the
+// sum of the four terms' magnitudes: error-free FP32 transformations give
+// hi + lo with |hi + lo - S| <= 2^-44 A (six rounding-error terms, each at
+// most 2^-24 A, summed in FP32) and hi = RN(hi + lo); the FP64 expression
+// differs from S by at most 3 2^-53 A < 2^-51 A.  So when hi + lo lies more
+// than tol = 2^-40 A inside both rounding midpoints around hi, the FP64 value
+// lies strictly between them as well and rounds to hi.  Otherwise (hi + lo
+// within about 2^-16 (A / |hi|) ulp of a midpoint, a non-normal or very large
+// hi, or a non-finite term) the FP64 expression itself is evaluated.
+__device__ __forceinline__ float depth_of(const CamInfo& c, const float* m) {
+  const F2 p0 = two_prod(c.R[6], m[0]), p1 = two_prod(c.R[7], m[1]), p2 = two_prod(c.R[8], m[2]);
+  const F2 s1 = two_sum(p0.hi, p1.hi);
+  const F2 s2 = two_sum(s1.hi, p2.hi);
+  const F2 s3 = two_sum(s2.hi, c.t[2]);
+  const float err = __fadd_rn(__fadd_rn(__fadd_rn(p0.lo, p1.lo), __fadd_rn(p2.lo, s1.lo)),
+                              __fadd_rn(s2.lo, s3.lo));
+  const F2 z = two_sum(s3.hi, err);
+  const float A = __fadd_rn(__fadd_rn(fabsf(p0.hi), fabsf(p1.hi)),
+                            __fadd_rn(fabsf(p2.hi), fabsf(c.t[2])));
+  const float tol = __fmul_rn(A, 0x1p-40f);
+  const float a = fabsf(z.hi);
+  const int bits = __float_as_int(a);
+  const float up = __fsub_rn(__int_as_float(bits + 1), a);    // spacing above |hi|
+  const float down = __fsub_rn(a, __int_as_float(bits - 1));  // spacing below |hi|
+  const float l = z.hi < 0.f ? -z.lo : z.lo;                   // lo, away from zero
+  const bool sure = a >= 0x1p-100f && a < 0x1p+120f && __fsub_rn(0.5f * up, l) > tol &&
+                    __fadd_rn(0.5f * down, l) > tol;
+  return sure ? z.hi : depth_fp64(c, m);
 }
 
 // (x.hi + x.lo) / (y.hi + y.lo) as a double-float.
@@ -309,7 +340,7 @@ __device__ __forceinline__ Projected project(const CamInfo& c, const Activated& 
 }
 
 template <int DT>
-__global__ void __launch_bounds__(256) preprocess_kernel(
+__global__ void __launch_bounds__(256, 4) preprocess_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales,
     const float* __restrict__ quats, const float* __restrict__ opacity_logits,
     const float* __restrict__ sh, int N, const CamTable ct, float dilation, float near_z,
