@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "gs_internal.cuh"
 
@@ -56,6 +57,37 @@ int invalid(const char* what) {
   snprintf(buf, sizeof buf, "invalid argument: %s", what);
   set_error_text(buf);
   return GS_ERR_INVALID_ARG;
+}
+
+// A second stream per device for work a call can run beside its own kernels.
+// The call forks it from the caller's stream with an event and joins it back
+// before the dependent kernel, so the ordering on the caller's stream is
+// unchanged and a stream capture records the side work as a parallel branch.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool tried = false, ok = false;
+};
+constexpr int kMaxDevices = 64;
+SideStream g_side[kMaxDevices];
+std::mutex g_side_mu;  // guards g_side and every fork..join sequence
+
+// The current device's side stream, or nullptr (then the call stays on one
+// stream).  It is created on first use outside a stream capture.
+SideStream* side_stream_locked(cudaStream_t st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  SideStream& ss = g_side[dev];
+  if (!ss.tried) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+      return nullptr;
+    ss.tried = true;
+    ss.ok = cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming) == cudaSuccess;
+  }
+  return ss.ok ? &ss : nullptr;
 }
 }  // namespace
 
@@ -427,11 +459,31 @@ int gs_render_bwd(const gs_proj* proj, int N, const gs_camera* cams, int V, cons
   if (N > 0 && (!aligned(quats, 16) || !aligned(g_quats, 16))) return invalid("quat alignment");
   if (opt && opt->ctas > 0 && !opt->work_counter) return invalid("persistent launch needs work_counter");
   cudaStream_t st = (cudaStream_t)stream;
-  GS_TRY_CUDA(cudaMemsetAsync(grad2d, 0, sizeof(float) * 12 * (size_t)N * V, st));
-  int rc = launch_render_bwd(proj, ct, prm, sorted_vals, tile_ranges, final_T, last_idx,
-                             dL_dimage, dL_dentropy, grad2d, opt, st);
+  const size_t sh_bytes = sizeof(float) * 3 * (size_t)prm->sh_stride * N;
+  // The SH gradients are zeroed (the projection adjoint adds into them) on
+  // the side stream while the blending adjoint runs: that kernel is bound by
+  // instruction issue and leaves most of the memory bandwidth free.
+  std::lock_guard<std::mutex> lock(g_side_mu);
+  SideStream* ss = side_stream_locked(st);
+  if (ss) {
+    GS_TRY_CUDA(cudaEventRecord(ss->fork, st));
+    GS_TRY_CUDA(cudaStreamWaitEvent(ss->s, ss->fork, 0));
+    GS_TRY_CUDA(cudaMemsetAsync(g_sh, 0, sh_bytes, ss->s));
+    GS_TRY_CUDA(cudaEventRecord(ss->join, ss->s));
+  }
+  // (from here the side branch is joined back on every return path)
+  int rc = GS_OK;
+  cudaError_t e = cudaMemsetAsync(grad2d, 0, sizeof(float) * 12 * (size_t)N * V, st);
+  if (e == cudaSuccess)
+    rc = launch_render_bwd(proj, ct, prm, sorted_vals, tile_ranges, final_T, last_idx, dL_dimage,
+                           dL_dentropy, grad2d, opt, st);
+  if (ss) {
+    GS_TRY_CUDA(cudaStreamWaitEvent(st, ss->join, 0));
+  } else if (e == cudaSuccess && rc == GS_OK) {
+    e = cudaMemsetAsync(g_sh, 0, sh_bytes, st);
+  }
+  if (e != cudaSuccess) GS_TRY_CUDA(e);
   if (rc != GS_OK) return rc;
-  GS_TRY_CUDA(cudaMemsetAsync(g_sh, 0, sizeof(float) * 3 * (size_t)prm->sh_stride * N, st));
   return launch_preprocess_bwd(means, log_scales, quats, opacity_logits, sh, N, ct, prm,
                                proj->tiles_touched, grad2d, g_means, g_log_scales, g_quats,
                                g_opacity_logits, g_sh, st);

@@ -340,7 +340,7 @@ __device__ __forceinline__ Projected project(const CamInfo& c, const Activated& 
 }
 
 template <int DT>
-__global__ void __launch_bounds__(256, 4) preprocess_kernel(
+__global__ void __launch_bounds__(256, 5) preprocess_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales,
     const float* __restrict__ quats, const float* __restrict__ opacity_logits,
     const float* __restrict__ sh, int N, const CamTable ct, float dilation, float near_z,
