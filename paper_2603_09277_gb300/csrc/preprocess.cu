@@ -105,10 +105,36 @@ __device__ __forceinline__ float3 sh_basis_grad_dot(int deg, float x, float y, f
   return make_float3(gx, gy, gz);
 }
 
-// Loads SH coefficient k (3 channels) of Gaussian g.
-__device__ __forceinline__ float3 load_sh(const float* sh, long long g, int stride, int k) {
-  const float* p = sh + (g * stride + k) * 3;
-  return make_float3(__ldg(p), __ldg(p + 1), __ldg(p + 2));
+// Whether every Gaussian's SH block (3 * stride floats) starts on 16 bytes:
+// the array is 16-byte aligned and the stride a multiple of 4.
+__device__ __forceinline__ bool sh_vectors(const float* p, int stride) {
+  return (stride & 3) == 0 && (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+}
+
+// Calls f(e, value) for the floats e = 3k + channel, e < 3K, of Gaussian
+// g's SH block, in ascending e.  With vec, 16-byte loads: the last one may
+// read up to 3 floats past 3K, which stay inside the block (3 * stride is a
+// multiple of 4 and at least 3K) and are not passed on.
+template <typename F>
+__device__ __forceinline__ void for_sh_block(const float* sh, long long g, int stride, int K,
+                                             bool vec, F&& f) {
+  const float* p = sh + g * stride * 3;
+  if (vec) {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      if (4 * i < 3 * K) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(p) + i);
+        f(4 * i, t.x);
+        if (4 * i + 1 < 3 * K) f(4 * i + 1, t.y);
+        if (4 * i + 2 < 3 * K) f(4 * i + 2, t.z);
+        if (4 * i + 3 < 3 * K) f(4 * i + 3, t.w);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 48; ++e)
+      if (e < 3 * K) f(e, __ldg(p + e));
+  }
 }
 
 // Rotation matrix of a unit quaternion (w, x, y, z), row-major.
@@ -389,13 +415,10 @@ __global__ void __launch_bounds__(256, 5) preprocess_kernel(
     float il = rsqrtf(vx * vx + vy * vy + vz * vz);
     float Y[16];
     sh_basis(sh_deg, vx * il, vy * il, vz * il, Y);
-    float cr = 0.5f, cg = 0.5f, cbl = 0.5f;
-    for (int k = 0; k < K; ++k) {
-      float3 s = load_sh(sh, g, sh_stride, k);
-      cr += Y[k] * s.x;
-      cg += Y[k] * s.y;
-      cbl += Y[k] * s.z;
-    }
+    float col[3] = {0.5f, 0.5f, 0.5f};
+    for_sh_block(sh, g, sh_stride, K, sh_vectors(sh, sh_stride),
+                 [&](int e, float v) { col[e % 3] += Y[e / 3] * v; });
+    float cr = col[0], cg = col[1], cbl = col[2];
     cr = fmaxf(cr, 0.f);
     cg = fmaxf(cg, 0.f);
     cbl = fmaxf(cbl, 0.f);
@@ -451,6 +474,8 @@ __device__ __forceinline__ void adjoint_one(
     float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
     float* __restrict__ g_opac, float* __restrict__ g_sh) {
   const int K = sh_count(sh_deg);
+  const bool vec = sh_vectors(sh, sh_stride);
+  const bool vec_out = vec && (reinterpret_cast<uintptr_t>(g_sh) & 15) == 0;
   Activated a = activate(means, log_scales, quats, opacity_logits, g);
   float gm[3] = {0.f, 0.f, 0.f};
   float gls[3] = {0.f, 0.f, 0.f};  // dL/d log-scale, summed over views
@@ -476,34 +501,45 @@ __device__ __forceinline__ void adjoint_one(
     float vx = a.mean[0] - c.cp[0], vy = a.mean[1] - c.cp[1], vz = a.mean[2] - c.cp[2];
     float il = rsqrtf(vx * vx + vy * vy + vz * vz);
     float dx = vx * il, dy = vy * il, dz = vz * il;
-    float Y[16];
+    float Y[16] = {};
     sh_basis(sh_deg, dx, dy, dz, Y);
     float raw[3] = {0.5f, 0.5f, 0.5f};
-    for (int k = 0; k < K; ++k) {
-      float3 s = load_sh(sh, g, sh_stride, k);
-      raw[0] += Y[k] * s.x;
-      raw[1] += Y[k] * s.y;
-      raw[2] += Y[k] * s.z;
-    }
+    for_sh_block(sh, g, sh_stride, K, vec, [&](int e, float v) { raw[e % 3] += Y[e / 3] * v; });
     float grgb[3] = {raw[0] < 0.f ? 0.f : G1.z, raw[1] < 0.f ? 0.f : G1.w,
                      raw[2] < 0.f ? 0.f : G2.x};
-    float cdot[16];
-    // the first view that sees the Gaussian stores, later ones accumulate
-    for (int k = 0; k < K; ++k) {
-      {
-        float3 s = load_sh(sh, g, sh_stride, k);
-        float* gs = g_sh + ((long long)g * sh_stride + k) * 3;
-        const float a0 = Y[k] * grgb[0], a1 = Y[k] * grgb[1], a2 = Y[k] * grgb[2];
-        if (first_view) {
-          gs[0] = a0;
-          gs[1] = a1;
-          gs[2] = a2;
-        } else {
-          gs[0] += a0;
-          gs[1] += a1;
-          gs[2] += a2;
+    float cdot[16] = {};  // SH[k] . grgb
+    for_sh_block(sh, g, sh_stride, K, vec,
+                 [&](int e, float v) { cdot[e / 3] = __fmaf_rn(v, grgb[e % 3], cdot[e / 3]); });
+    // dL/dSH[k][ch] = Y_k grgb_ch; the first view that sees the Gaussian
+    // stores, later ones accumulate (entries past 3K are left untouched or
+    // get exact zeros)
+    float* gsh = g_sh + (long long)g * sh_stride * 3;
+    if (vec_out) {
+#pragma unroll
+      for (int i = 0; i < 12; ++i) {
+        if (4 * i < 3 * K) {
+          float o[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int e = 4 * i + j;
+            o[j] = e < 3 * K ? Y[e / 3] * grgb[e % 3] : 0.f;
+          }
+          float4* q = reinterpret_cast<float4*>(gsh) + i;
+          if (first_view) {
+            *q = make_float4(o[0], o[1], o[2], o[3]);
+          } else {
+            const float4 t = *q;
+            *q = make_float4(t.x + o[0], t.y + o[1], t.z + o[2], t.w + o[3]);
+          }
         }
-        cdot[k] = s.x * grgb[0] + s.y * grgb[1] + s.z * grgb[2];
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 48; ++e) {
+        if (e < 3 * K) {
+          const float a = Y[e / 3] * grgb[e % 3];
+          gsh[e] = first_view ? a : gsh[e] + a;
+        }
       }
     }
     first_view = false;
