@@ -196,15 +196,18 @@ struct LossViews {
   long long pix_off[GS_MAX_VIEWS];
   float g_img[GS_MAX_VIEWS];  // 1 / (3 M_v V): |dL/dC| per channel
   float g_ent[GS_MAX_VIEWS];  // gamma / (M_v V)
-  double w[GS_MAX_VIEWS];     // 1 / (M_v V)
+  float w[GS_MAX_VIEWS];      // 1 / (M_v V)
 };
 
 __global__ void __launch_bounds__(kLossThreads) loss_kernel(
     const float* __restrict__ image, const float* __restrict__ target,
     const float* __restrict__ entropy, const LossViews lv, long long P, float gamma,
-    double l1_weight, float* __restrict__ dimg, float* __restrict__ dent,
+    float l1_weight, float* __restrict__ dimg, float* __restrict__ dent,
     double* __restrict__ partials) {
-  double acc = 0.0;
+  // Every term is >= 0: a thread's few terms and the warp's 32 partials are
+  // summed in FP32 (relative error below 1e-6), the warps and blocks in FP64.
+  // (FP64 arithmetic runs at a small fraction of the FP32 rate here.)
+  float acc = 0.f;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
        i += (long long)gridDim.x * blockDim.x) {
     int v = 0;
@@ -218,13 +221,13 @@ __global__ void __launch_bounds__(kLossThreads) loss_kernel(
     }
     const float h = entropy ? entropy[i] : 0.f;
     if (dent) dent[i] = lv.g_ent[v];
-    // per pixel: (1/(M_v V)) ((1 - lambda) |r|_1 / 3 + gamma H), summed in double
-    acc += lv.w[v] * (l1_weight * (double)l1 * (1.0 / 3.0) + (double)gamma * (double)h);
+    // per pixel: (1/(M_v V)) ((1 - lambda) |r|_1 / 3 + gamma H)
+    acc = __fmaf_rn(lv.w[v], __fmaf_rn(l1_weight * (1.f / 3.f), l1, gamma * h), acc);
   }
   __shared__ double s[kLossThreads / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = (double)acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -395,12 +398,12 @@ int loss_impl(const float* image, const float* target, const float* entropy, con
   for (int v = 0; v < V; ++v) {
     const double M = (double)ct.c[v].W * ct.c[v].H;
     lv.pix_off[v] = ct.c[v].pix_off;
-    lv.w[v] = 1.0 / (M * V);
+    lv.w[v] = (float)(1.0 / (M * V));
     lv.g_img[v] = (float)((1.0 - (double)lambda) / (3.0 * M * V));
     lv.g_ent[v] = (float)((double)gamma / (M * V));
   }
   loss_kernel<<<nb, kLossThreads, 0, st>>>(image, target, gamma != 0.f ? entropy : nullptr, lv, P,
-                                           gamma, 1.0 - (double)lambda, dL_dimage, dL_dentropy,
+                                           gamma, (float)(1.0 - (double)lambda), dL_dimage, dL_dentropy,
                                            partials);
   count_launches(1);
   if (lambda > 0.f) {

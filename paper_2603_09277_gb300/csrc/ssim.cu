@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_fwd_kernel(
   const int px = bx + lx, py = by + ly;
   const bool mine = px < W && py < H;
   const long long p = base + (long long)py * W + px;
-  double acc = 0.0;
+  float acc = 0.f;  // 1 - S >= 0: FP32 within the thread and the warp, FP64 beyond
   for (int ch = 0; ch < 3; ++ch) {
     const float cx = sx[ch][kSsimR + kSsimB / 2][kSsimR + kSsimB / 2];
     const float cy = sy[ch][kSsimR + kSsimB / 2][kSsimR + kSsimB / 2];
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_fwd_kernel(
       const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
       const float D = B1 * B2;
       const float S = A1 * A2 / D;
-      acc += (double)(1.f - S);
+      acc += 1.f - S;
       float* m = maps + (long long)(5 * ch) * P + p;
       m[0] = mx;
       m[P] = my;
@@ -136,16 +136,15 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_fwd_kernel(
     }
     __syncthreads();  // sh is rewritten for the next channel
   }
-  acc *= (double)sv.scale[v];
   __shared__ double s_red[kSsimThreads / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = (double)acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int k = 0; k < kSsimThreads / 32; ++k) t += s_red[k];
-    partials[b] = t;
+    partials[b] = t * (double)sv.scale[v];
   }
 }
 
