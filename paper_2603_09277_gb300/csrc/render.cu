@@ -356,6 +356,69 @@ __device__ __forceinline__ float warp_sum9(const float v[9], int lane, int& slot
   return y;
 }
 
+// One list entry against a thread's two pixels (rows ry and ry + 1 of one
+// column), both through the same steps with packed FP32 (f32x2: one
+// instruction for the pair).  A pixel that does not take part (the entry
+// lies after its last blended one, or its alpha is below alpha_min) gets
+// alpha = 0: its transmittance is kept by a select and every contribution
+// is zero, and its L stays finite (w is floored at 1e-30 inside the log).
+// The exponent is the scalar path's value exactly: RN(q^2 - base) is
+// -RN(base - q^2).  Adds the pixel sums of the 6 moments and 3 colour
+// weights to gsum; returns whether either pixel took part.
+__device__ __forceinline__ bool bwd_pair(const RenderConsts& rc, const float4 g0, const float4 g1,
+                                         const float cB, float rx, float2 ry2, unsigned pos,
+                                         unsigned last0, unsigned last1, float2& T2,
+                                         const float2 gr2, const float2 gg2, const float2 gb2,
+                                         const float2 gH2, float2& gS2, float2& R2,
+                                         float gsum[9]) {
+  const float dx = rx - g0.x;
+  const SplatColumn col = splat_column(g0.z, g0.w, g1.y, dx);
+  const float2 dy = __fadd2_rn(ry2, make_float2(-g0.y, -g0.y));
+  const float2 qv = __ffma2_rn(make_float2(g1.x, g1.x), dy, make_float2(col.qx, col.qx));
+  const float2 en = __ffma2_rn(qv, qv, make_float2(-col.base, -col.base));  // -e
+  const bool a0 = pos < last0 && !(-en.x < rc.log2_alpha_min);
+  const bool a1 = pos < last1 && !(-en.y < rc.log2_alpha_min);
+  if (!(a0 || a1)) return false;
+  const float ar0 = a0 ? fast_exp2(-en.x) : 0.f;
+  const float ar1 = a1 ? fast_exp2(-en.y) : 0.f;
+  const float2 al = make_float2(fminf(rc.alpha_max, ar0), fminf(rc.alpha_max, ar1));
+  const float2 om = __fadd2_rn(make_float2(1.f, 1.f), make_float2(-al.x, -al.y));
+  const float2 iom = make_float2(fast_rcp(om.x), fast_rcp(om.y));
+  const float2 Ti = __fmul2_rn(T2, iom);
+  const float2 w = __fmul2_rn(al, Ti);
+  const float2 L = __fadd2_rn(
+      make_float2(fast_log2(fmaxf(w.x, 1e-30f)), fast_log2(fmaxf(w.y, 1e-30f))),
+      make_float2(kLog2e, kLog2e));
+  // colour part T_i gc - gS / (1 - alpha_i), entropy part gH (-L T_i + R / (1 - alpha_i))
+  const float2 gc = __ffma2_rn(gb2, make_float2(cB, cB),
+                               __ffma2_rn(gg2, make_float2(g1.w, g1.w),
+                                          __fmul2_rn(gr2, make_float2(g1.z, g1.z))));
+  const float2 sq = __fmul2_rn(gS2, iom);
+  float2 dA = __ffma2_rn(Ti, gc, make_float2(-sq.x, -sq.y));
+  const float2 ent = __ffma2_rn(make_float2(-L.x, -L.y), Ti, __fmul2_rn(R2, iom));
+  dA = __ffma2_rn(gH2, ent, dA);
+  const float2 c6 = __fmul2_rn(w, gr2), c7 = __fmul2_rn(w, gg2), c8 = __fmul2_rn(w, gb2);
+  gS2 = __ffma2_rn(w, gc, gS2);
+  R2 = __ffma2_rn(L, w, R2);
+  T2 = make_float2(a0 ? Ti.x : T2.x, a1 ? Ti.y : T2.y);
+  // dd = dalpha alpha where alpha is below its clamp, then the moments
+  const float2 dd = __fmul2_rn(dA, make_float2(ar0 <= rc.alpha_max ? ar0 : 0.f,
+                                               ar1 <= rc.alpha_max ? ar1 : 0.f));
+  const float2 dx2 = make_float2(dx, dx);
+  const float2 ddx = __fmul2_rn(dd, dx2), ddy = __fmul2_rn(dd, dy);
+  const float2 m2 = __fmul2_rn(ddx, dx2), m3 = __fmul2_rn(ddx, dy), m4 = __fmul2_rn(ddy, dy);
+  gsum[0] += ddx.x + ddx.y;
+  gsum[1] += ddy.x + ddy.y;
+  gsum[2] += m2.x + m2.y;
+  gsum[3] += m3.x + m3.y;
+  gsum[4] += m4.x + m4.y;
+  gsum[5] += dd.x + dd.y;
+  gsum[6] += c6.x + c6.y;
+  gsum[7] += c7.x + c7.y;
+  gsum[8] += c8.x + c8.y;
+  return true;
+}
+
 template <int DT, int TS, int PPT>
 __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts& rc,
                                          const BwdArgs& a, int tile) {
@@ -396,6 +459,18 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
     gH[q] *= kLn2;
     mylast = max(mylast, last[q]);
   }
+  // two pixels per thread: the state as FP32 pairs (packed f32x2 arithmetic)
+  float2 T2, gr2, gg2, gb2, gH2, gS2, R2;
+  if constexpr (PPT == 2) {
+    T2 = make_float2(T[0], T[1]);
+    gr2 = make_float2(gr[0], gr[1]);
+    gg2 = make_float2(gg[0], gg[1]);
+    gb2 = make_float2(gb[0], gb[1]);
+    gH2 = make_float2(gH[0], gH[1]);
+    gS2 = make_float2(0.f, 0.f);
+    R2 = make_float2(Rent[0], Rent[1]);
+  }
+  const float2 ry2 = make_float2(tg.ry0, tg.ry0 + 1.f);
   if (tid == 0) s_max = 0u;
   __syncthreads();
   if (mylast) atomicMax(&s_max, mylast);
@@ -430,7 +505,10 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
 #pragma unroll
       for (int i = 0; i < 9; ++i) gsum[i] = 0.f;
       bool contrib = false;
-      if (any_here) {
+      if constexpr (PPT == 2) {
+        if (any_here) contrib = bwd_pair(rc, s0[k], s1[k], s2[k], tg.rx, ry2, pos, last[0],
+                                         last[1], T2, gr2, gg2, gb2, gH2, gS2, R2, gsum);
+      } else if (any_here) {
         const float4 g0 = s0[k];
         const float4 g1 = s1[k];
         const float cB = s2[k];
