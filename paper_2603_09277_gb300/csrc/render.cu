@@ -159,6 +159,51 @@ struct FwdArgs {
   unsigned long long* stats;
 };
 
+// One list entry against a thread's two pixels (rows ry and ry + 1 of one
+// column) in the forward, both through the same steps with packed FP32
+// (f32x2); the exponent is the scalar path's value exactly (RN(q^2 - base)
+// is -RN(base - q^2)).  A pixel that is not reached gets w = 0 (every sum
+// unchanged, its T kept by a select); a pixel whose T (1 - alpha) would drop
+// below t_min finishes: its live bit clears and its row moves to kFar.
+// Returns the number of pixels blended.
+__device__ __forceinline__ int fwd_pair(const RenderConsts& rc, const float4 g0, const float4 g1,
+                                        const float cB, float rx, float2& ry2, float2& T2,
+                                        float2& cr2, float2& cg2, float2& cb2, float2& swl2,
+                                        unsigned& last0, unsigned& last1, unsigned& live,
+                                        unsigned pos1, unsigned& stop0, unsigned& stop1) {
+  const SplatColumn col = splat_column(g0.z, g0.w, g1.y, rx - g0.x);
+  const float2 dy = __fadd2_rn(ry2, make_float2(-g0.y, -g0.y));
+  const float2 qv = __ffma2_rn(make_float2(g1.x, g1.x), dy, make_float2(col.qx, col.qx));
+  const float2 en = __ffma2_rn(qv, qv, make_float2(-col.base, -col.base));  // -e
+  const bool p0 = !(-en.x < rc.log2_alpha_min), p1 = !(-en.y < rc.log2_alpha_min);
+  if (!(p0 || p1)) return 0;
+  const float2 al = make_float2(p0 ? fminf(rc.alpha_max, fast_exp2(-en.x)) : 0.f,
+                                p1 ? fminf(rc.alpha_max, fast_exp2(-en.y)) : 0.f);
+  const float2 tT = __fmul2_rn(T2, __fadd2_rn(make_float2(1.f, 1.f), make_float2(-al.x, -al.y)));
+  const bool f0 = p0 && tT.x < rc.t_min, f1 = p1 && tT.y < rc.t_min;
+  if (f0) {
+    live &= ~1u;
+    ry2.x = kFar;
+    stop0 = pos1;
+  }
+  if (f1) {
+    live &= ~2u;
+    ry2.y = kFar;
+    stop1 = pos1;
+  }
+  const bool b0 = p0 && !f0, b1 = p1 && !f1;
+  const float2 w = __fmul2_rn(make_float2(b0 ? al.x : 0.f, b1 ? al.y : 0.f), T2);
+  cr2 = __ffma2_rn(w, make_float2(g1.z, g1.z), cr2);
+  cg2 = __ffma2_rn(w, make_float2(g1.w, g1.w), cg2);
+  cb2 = __ffma2_rn(w, make_float2(cB, cB), cb2);
+  swl2 = __ffma2_rn(
+      w, make_float2(fast_log2(fmaxf(w.x, 1e-30f)), fast_log2(fmaxf(w.y, 1e-30f))), swl2);
+  T2 = make_float2(b0 ? tT.x : T2.x, b1 ? tT.y : T2.y);
+  if (b0) last0 = pos1;
+  if (b1) last1 = pos1;
+  return (int)b0 + (int)b1;
+}
+
 template <int DT, int TS, int PPT, bool STATS>
 __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts& rc,
                                          const FwdArgs& a, int tile, unsigned long long& n_bl,
@@ -187,6 +232,13 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
     stop[k] = r.y - r.x;
     ry[k] = (live & (1u << k)) ? tg.ry0 + (float)k : kFar;
   }
+  // two pixels per thread: the state as FP32 pairs (packed f32x2 arithmetic)
+  float2 T2, cr2, cg2, cb2, swl2, ry2;
+  if constexpr (PPT == 2) {
+    T2 = make_float2(T[0], T[1]);
+    cr2 = cg2 = cb2 = swl2 = make_float2(0.f, 0.f);
+    ry2 = make_float2(ry[0], ry[1]);
+  }
   unsigned nb = 0, ne = 0;
   for (unsigned base = r.x; base < r.y; base += kBatch) {
     if (__syncthreads_count(live == 0u) == NT) break;
@@ -210,6 +262,12 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
                       : 0;
     for (int i = 0; i < n && live; ++i) {
       const int k = s_list[warp][i];
+      if constexpr (PPT == 2) {
+        const int nbl = fwd_pair(rc, s0[k], s1[k], s2[k], tg.rx, ry2, T2, cr2, cg2, cb2, swl2,
+                                 last[0], last[1], live, base - r.x + k + 1, stop[0], stop[1]);
+        if (STATS) nb += nbl;
+        continue;
+      }
       const float4 g0 = s0[k];
       const float4 g1 = s1[k];
       const SplatColumn col = splat_column(g0.z, g0.w, g1.y, tg.rx - g0.x);
@@ -243,6 +301,18 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
         if (STATS) ++nb;
       }
     }
+  }
+  if constexpr (PPT == 2) {
+    T[0] = T2.x;
+    T[1] = T2.y;
+    cr[0] = cr2.x;
+    cr[1] = cr2.y;
+    cg[0] = cg2.x;
+    cg[1] = cg2.y;
+    cb[0] = cb2.x;
+    cb[1] = cb2.y;
+    swl[0] = swl2.x;
+    swl[1] = swl2.y;
   }
 #pragma unroll
   for (int q = 0; q < PPT; ++q) {
