@@ -45,6 +45,7 @@ namespace gs {
 namespace {
 
 constexpr int kBatch = 256;  // records per staging batch
+constexpr int kDirectLanes = 24;  // up to this many contributing lanes add directly
 constexpr unsigned kFull = 0xffffffffu;
 // A row coordinate this far from every mean makes the exponent -inf (f22 > 0),
 // so a finished or outside pixel never passes the alpha_min test again.
@@ -623,8 +624,9 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
       const unsigned who = __ballot_sync(kFull, contrib);
       if (who) {
         float* G = a.grad2d + 12ll * s_row[k];
-        if (__popc(who) == 1) {
-          // one contributing lane: its values are the warp totals
+        if (__popc(who) <= kDirectLanes) {
+          // few contributing lanes: each adds its own values (three vector
+          // atomics) instead of the 12-shuffle warp reduction
           if (contrib) {
             atomicAdd(reinterpret_cast<float4*>(G), make_float4(gsum[0], gsum[1], gsum[2], gsum[3]));
             atomicAdd(reinterpret_cast<float4*>(G) + 1,
