@@ -32,9 +32,14 @@
 //   dy^2), so the kernel sums the moments and the projection's adjoint
 //   applies 1 / sigma, the conic and the signs once per Gaussian.
 // The thread sums the 9 per-Gaussian values (6 moments, 3 colour weights)
-// over its pixels, the warp sums them with a split-transpose shuffle
-// reduction (12 shuffles leave one of the 9 totals in each of 9 lane pairs)
-// and 9 lanes add them to grad2d with one atomic instruction.
+// over its pixels.  When at most kDirectLanes lanes of the warp contribute,
+// each of them adds its values to grad2d with three vector atomics;
+// otherwise the warp sums them with a split-transpose shuffle reduction (12
+// shuffles leave one of the 9 totals in each of 9 lane pairs) and 9 lanes
+// add them with one atomic instruction.  (All 32 lanes adding to one address
+// in one instruction serialise in L2: the threshold stays below 32.)
+// With two pixels per thread both pixels go through packed FP32 (f32x2)
+// arithmetic, in the forward as well.
 //
 // Launch forms: one CTA per tile (optionally in a given tile order), or a
 // persistent grid whose CTAs claim tiles from a queue with one atomicAdd per
