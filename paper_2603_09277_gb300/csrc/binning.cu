@@ -153,27 +153,57 @@ __global__ void __launch_bounds__(kScanThreads) scan_counts_check_kernel(
 }
 
 // Phase 3 (compaction form): rows with tiles_touched > 0 are written, in
-// order, as (depth bits, row) to keys/vals.
+// order, as (depth bits, row) to keys/vals.  Item i = base + k * 256 + tid
+// (coalesced loads); the visible items of each (k, warp) are ranked by a
+// ballot, and the (k, warp) counts are scanned by one warp, so the output
+// order is the row order.
+constexpr int kScanWarps = kScanThreads / 32;
 __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
     const unsigned* __restrict__ tiles_touched, const float* __restrict__ depth, long long n,
     const unsigned long long* __restrict__ block_offsets, unsigned* __restrict__ keys,
     unsigned* __restrict__ vals) {
-  long long base = (long long)blockIdx.x * kScanTile;
-  // each thread owns kScanItems consecutive items for an ordered compaction
-  long long first = base + (long long)threadIdx.x * kScanItems;
-  unsigned cnt = 0;
+  __shared__ unsigned s_off[kScanItems * kScanWarps];
+  const long long base = (long long)blockIdx.x * kScanTile;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned ball[kScanItems];
+#pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    long long i = first + k;
-    if (i < n && tiles_touched[i] > 0u) ++cnt;
+    const long long i = base + (long long)k * kScanThreads + threadIdx.x;
+    ball[k] = __ballot_sync(0xffffffffu, i < n && tiles_touched[i] > 0u);
+    if (lane == 0) s_off[k * kScanWarps + w] = __popc(ball[k]);
   }
-  unsigned long long tot;
-  unsigned long long off = block_excl_scan(cnt, &tot) + block_offsets[blockIdx.x];
+  __syncthreads();
+  if (w == 0) {  // exclusive scan of the (k, warp) counts, 4 per lane
+    static_assert(kScanItems * kScanWarps == 4 * 32, "one warp scans the counts");
+    unsigned c[4], run = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      c[j] = s_off[4 * lane + j];
+      run += c[j];
+    }
+    unsigned inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    unsigned ex = inc - run;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      s_off[4 * lane + j] = ex;
+      ex += c[j];
+    }
+  }
+  __syncthreads();
+  const unsigned long long boff = block_offsets[blockIdx.x];
+  const unsigned below = (1u << lane) - 1u;
+#pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    long long i = first + k;
-    if (i < n && tiles_touched[i] > 0u) {
+    if ((ball[k] >> lane) & 1u) {
+      const long long i = base + (long long)k * kScanThreads + threadIdx.x;
+      const unsigned long long off = boff + s_off[k * kScanWarps + w] + __popc(ball[k] & below);
       keys[off] = __float_as_uint(depth[i]);
       vals[off] = (unsigned)i;
-      ++off;
     }
   }
 }
@@ -218,6 +248,13 @@ __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
     unsigned long long* __restrict__ sums_q, unsigned long long* __restrict__ sums_p) {
   const long long n = *n_dev;
   const long long base = (long long)blockIdx.x * kScanTile;
+  if (base >= n) {  // (the whole CTA) no rows: zero sums
+    if (threadIdx.x == 0) {
+      sums_q[blockIdx.x] = 0ull;
+      sums_p[blockIdx.x] = 0ull;
+    }
+    return;
+  }
   unsigned long long q = 0, pp = 0;
   for (int k = 0; k < kScanItems; ++k) {
     const long long i = base + (long long)k * kScanThreads + threadIdx.x;
@@ -286,15 +323,24 @@ __device__ __forceinline__ long long radix_chunk(long long n, int nblocks) {
   return (per + kRadixTile - 1) / kRadixTile * kRadixTile;
 }
 
+// CTAs of a pass that own items: the grid is sized for the bound on the
+// item count, so with few items (a small visible set) most CTAs own none;
+// they leave at once and the histogram scan covers only the active ones.
+__device__ __forceinline__ int radix_active(long long n, int nblocks) {
+  const long long chunk = radix_chunk(n, nblocks);
+  return chunk > 0 ? (int)min((long long)nblocks, (n + chunk - 1) / chunk) : 0;
+}
+
 __global__ void __launch_bounds__(kRadixThreads) radix_upsweep_kernel(
     const unsigned* __restrict__ keys, const long long* __restrict__ n_dev, int shift,
     unsigned dmask, unsigned* __restrict__ hist /* [256][nblocks] */) {
   __shared__ unsigned s_h[kRadixWarps][kRadixBins];
   const int w = threadIdx.x >> 5;
+  long long n = *n_dev;
+  if ((int)blockIdx.x >= radix_active(n, gridDim.x)) return;  // (the whole CTA)
   for (int i = threadIdx.x; i < kRadixWarps * kRadixBins; i += kRadixThreads)
     (&s_h[0][0])[i] = 0u;
   __syncthreads();
-  long long n = *n_dev;
   long long chunk = radix_chunk(n, gridDim.x);
   long long b0 = (long long)blockIdx.x * chunk;
   long long b1 = min(n, b0 + chunk);
@@ -318,26 +364,28 @@ __global__ void __launch_bounds__(kRadixThreads) radix_upsweep_kernel(
   }
 }
 
-// Per-digit exclusive scan over the blocks: block d scans hist[d][0..G) in
-// place and writes the digit total to totals[d].  G <= 1024.
-__global__ void __launch_bounds__(kScanThreads) radix_scan_kernel(unsigned* __restrict__ hist,
-                                                                  int G,
-                                                                  unsigned* __restrict__ totals) {
+// Per-digit exclusive scan over the blocks: block d scans hist[d][0..Ga) in
+// place (Ga = the pass's active CTAs) and writes the digit total to
+// totals[d].  G <= 1024.
+__global__ void __launch_bounds__(kScanThreads) radix_scan_kernel(
+    unsigned* __restrict__ hist, int G, const long long* __restrict__ n_dev,
+    unsigned* __restrict__ totals) {
   unsigned* h = hist + (long long)blockIdx.x * G;
+  const int Ga = radix_active(*n_dev, G);
   constexpr int kPer = 4;  // 256 threads x 4 >= 1024 blocks
   unsigned loc[kPer];
   unsigned long long s = 0;
   const int first = threadIdx.x * kPer;
 #pragma unroll
   for (int k = 0; k < kPer; ++k) {
-    loc[k] = first + k < G ? h[first + k] : 0u;
+    loc[k] = first + k < Ga ? h[first + k] : 0u;
     s += loc[k];
   }
   unsigned long long tot;
   unsigned long long off = block_excl_scan(s, &tot);
 #pragma unroll
   for (int k = 0; k < kPer; ++k) {
-    if (first + k < G) h[first + k] = (unsigned)off;
+    if (first + k < Ga) h[first + k] = (unsigned)off;
     off += loc[k];
   }
   if (threadIdx.x == 0) totals[blockIdx.x] = (unsigned)tot;
@@ -365,6 +413,7 @@ __global__ void __launch_bounds__(kRadixThreads, 3) radix_downsweep_kernel(
   const unsigned lt_mask = (1u << lane) - 1u;
   const unsigned dmask = (1u << dbits) - 1u;
   long long n = *n_dev;
+  if ((int)blockIdx.x >= radix_active(n, gridDim.x)) return;  // (the whole CTA)
   long long chunk = radix_chunk(n, gridDim.x);
   long long b0 = (long long)blockIdx.x * chunk;
   long long b1 = min(n, b0 + chunk);
@@ -1105,7 +1154,8 @@ int radix_sort(unsigned* k[2], unsigned* v[2], const long long* n_dev, long long
   for (int shift = 0; shift < bits; shift += dbits) {
     radix_upsweep_kernel<<<grid, kRadixThreads, 0, st>>>(k[cur], n_dev, shift,
                                                          (1u << dbits) - 1u, hist);
-    radix_scan_kernel<<<kRadixBins, kScanThreads, 0, st>>>(hist, grid, hist + kRadixBins * grid);
+    radix_scan_kernel<<<kRadixBins, kScanThreads, 0, st>>>(hist, grid, n_dev,
+                                                         hist + kRadixBins * grid);
     radix_downsweep_kernel<<<grid, kRadixThreads, 0, st>>>(k[cur], v[cur], k[1 - cur], v[1 - cur],
                                                            n_dev, shift, dbits, hist,
                                                            hist + kRadixBins * grid);
