@@ -248,7 +248,8 @@ int gs_loss_base(const float* image, const float* target, const float* entropy,
  *   summed over the pixels where the row is blended, the moments
  *   dd dx, dd dy, dd dx^2, dd dx dy, dd dy^2, dd (dd = dL/dalpha alpha where
  *   alpha is below its clamp, 0 where clamped; dx, dy = pixel centre minus
- *   the 2D mean), then dL/d(r, g, b) and 3 pad floats.  From these,
+ *   the 2D mean), then dL/d(r, g, b) and 3 floats of scratch (the list of
+ *   Gaussians some view sees, for the projection adjoint).  From these,
  *   dL/dsigma = dd-sum / sigma, dL/dconic = -(1/2) sum dd d d^T and
  *   dL/dmean2d = conic (dd dx-sum, dd dy-sum).
  *   g_* : device, shapes of the parameters, overwritten. */

@@ -21,6 +21,8 @@ int launch_preprocess_bwd(const float* means, const float* log_scales, const flo
                           const gs_params* prm, const unsigned* tiles_touched, const float* grad2d,
                           float* g_means, float* g_ls, float* g_quats, float* g_opac, float* g_sh,
                           cudaStream_t st);
+int launch_adjoint_list(const unsigned* tiles_touched, int N, int V, float* grad2d,
+                        cudaStream_t st);
 size_t bin_sort_workspace_size(long long n_rows, long long cap, long long total_tiles);
 size_t ssim_workspace_bytes(long long total_pixels);
 int ssim_blocks(const CamTable& ct);
@@ -462,30 +464,44 @@ int gs_render_bwd(const gs_proj* proj, int N, const gs_camera* cams, int V, cons
   if (N > 0 && (!aligned(quats, 16) || !aligned(g_quats, 16))) return invalid("quat alignment");
   if (opt && opt->ctas > 0 && !opt->work_counter) return invalid("persistent launch needs work_counter");
   cudaStream_t st = (cudaStream_t)stream;
+  if (N == 0) return GS_OK;  // no Gaussians: no gradients
   const size_t sh_bytes = sizeof(float) * 3 * (size_t)prm->sh_stride * N;
-  // The SH gradients are zeroed (the projection adjoint adds into them) on
-  // the side stream while the blending adjoint runs: that kernel is bound by
-  // instruction issue and leaves most of the memory bandwidth free.
+  GS_TRY_CUDA(cudaMemsetAsync(grad2d, 0, sizeof(float) * 12 * (size_t)N * V, st));
+  // Beside the blending adjoint (bound by instruction issue, most of the
+  // memory bandwidth free), on the side stream: the list of Gaussians some
+  // view sees (in grad2d's pad floats, after its zeroing) and the zeroing of
+  // every parameter gradient (the projection adjoint writes only the listed
+  // Gaussians').
+  auto side_work = [&](cudaStream_t s) -> int {
+    int r = launch_adjoint_list(proj->tiles_touched, N, V, grad2d, s);
+    if (r != GS_OK) return r;
+    GS_TRY_CUDA(cudaMemsetAsync(g_sh, 0, sh_bytes, s));
+    GS_TRY_CUDA(cudaMemsetAsync(g_means, 0, sizeof(float) * 3 * (size_t)N, s));
+    GS_TRY_CUDA(cudaMemsetAsync(g_log_scales, 0, sizeof(float) * 3 * (size_t)N, s));
+    GS_TRY_CUDA(cudaMemsetAsync(g_quats, 0, sizeof(float) * 4 * (size_t)N, s));
+    GS_TRY_CUDA(cudaMemsetAsync(g_opacity_logits, 0, sizeof(float) * (size_t)N, s));
+    return GS_OK;
+  };
   std::lock_guard<std::mutex> lock(g_side_mu);
   SideStream* ss = side_stream_locked(st);
+  int rc = GS_OK;
   if (ss) {
     GS_TRY_CUDA(cudaEventRecord(ss->fork, st));
     GS_TRY_CUDA(cudaStreamWaitEvent(ss->s, ss->fork, 0));
-    GS_TRY_CUDA(cudaMemsetAsync(g_sh, 0, sh_bytes, ss->s));
+    const int rs = side_work(ss->s);
+    // (the side branch is joined back on every path from here)
     GS_TRY_CUDA(cudaEventRecord(ss->join, ss->s));
-  }
-  // (from here the side branch is joined back on every return path)
-  int rc = GS_OK;
-  cudaError_t e = cudaMemsetAsync(grad2d, 0, sizeof(float) * 12 * (size_t)N * V, st);
-  if (e == cudaSuccess)
-    rc = launch_render_bwd(proj, ct, prm, sorted_vals, tile_ranges, final_T, last_idx, dL_dimage,
-                           dL_dentropy, grad2d, opt, st);
-  if (ss) {
+    if (rs == GS_OK)
+      rc = launch_render_bwd(proj, ct, prm, sorted_vals, tile_ranges, final_T, last_idx,
+                             dL_dimage, dL_dentropy, grad2d, opt, st);
     GS_TRY_CUDA(cudaStreamWaitEvent(st, ss->join, 0));
-  } else if (e == cudaSuccess && rc == GS_OK) {
-    e = cudaMemsetAsync(g_sh, 0, sh_bytes, st);
+    if (rs != GS_OK) return rs;
+  } else {
+    rc = side_work(st);
+    if (rc == GS_OK)
+      rc = launch_render_bwd(proj, ct, prm, sorted_vals, tile_ranges, final_T, last_idx,
+                             dL_dimage, dL_dentropy, grad2d, opt, st);
   }
-  if (e != cudaSuccess) GS_TRY_CUDA(e);
   if (rc != GS_OK) return rc;
   return launch_preprocess_bwd(means, log_scales, quats, opacity_logits, sh, N, ct, prm,
                                proj->tiles_touched, grad2d, g_means, g_log_scales, g_quats,

@@ -88,13 +88,38 @@ struct ScanSrc {
   }
 };
 
-// Phase 1: per-block sums.
+// A CTA's arrival at the end of a kernel whose last CTA goes on to a step
+// over every CTA's results (a scan of the block sums, say), in place of a
+// separate single-CTA launch.  Each CTA makes its results visible
+// (__threadfence) before it counts itself, so the CTA that counts last sees
+// all of them; it reads them through L2 (__ldcg).  No CTA waits for another.
+// The counter is zeroed with the pipeline's counters before the launch.
+// Returns true in every thread of the last CTA.
+__device__ __forceinline__ bool last_block_arrives(unsigned long long* counter,
+                                                   unsigned long long expected) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(counter, 1ull) == expected - 1ull ? 1 : 0;
+  __syncthreads();
+  const bool last = s_last != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+__device__ __forceinline__ long long scan_blocks_dev(unsigned long long* block_sums, int nblocks);
+
+// Phase 1: per-block sums; with `arrive`, the last CTA also scans them
+// (phase 2) and writes the grand total to *total.
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(ScanSrc src, const long long* n_dev,
                                                                    long long n_host,
-                                                                   unsigned long long* block_sums) {
+                                                                   unsigned long long* block_sums,
+                                                                   unsigned long long* arrive,
+                                                                   long long* total) {
   long long n = n_dev ? *n_dev : n_host;
   long long base = (long long)blockIdx.x * kScanTile;
   unsigned long long s = 0;
+#pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     long long i = base + (long long)k * kScanThreads + threadIdx.x;
     if (i < n) s += src.get(i);
@@ -102,6 +127,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(ScanSrc src, 
   unsigned long long tot;
   block_excl_scan(s, &tot);
   if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+  if (arrive && last_block_arrives(arrive, gridDim.x)) {
+    const long long t = scan_blocks_dev(block_sums, (int)gridDim.x);
+    if (threadIdx.x == 0) *total = t;
+  }
 }
 
 // Phase 2: exclusive scan of the block sums in one block; writes the grand
@@ -112,7 +141,7 @@ __device__ __forceinline__ long long scan_blocks_dev(unsigned long long* block_s
   __syncthreads();
   for (int base = 0; base < nblocks; base += kScanThreads) {
     int i = base + threadIdx.x;
-    unsigned long long x = i < nblocks ? block_sums[i] : 0ull;
+    unsigned long long x = i < nblocks ? __ldcg(block_sums + i) : 0ull;
     unsigned long long tot;
     unsigned long long ex = block_excl_scan(x, &tot);
     if (i < nblocks) block_sums[i] = s_carry + ex;
@@ -125,20 +154,32 @@ __device__ __forceinline__ long long scan_blocks_dev(unsigned long long* block_s
   return t;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(unsigned long long* block_sums,
-                                                                   int nblocks,
-                                                                   long long* total) {
-  const long long t = scan_blocks_dev(block_sums, nblocks);
-  if (threadIdx.x == 0) *total = t;
-}
 
 // Exclusive scans of the super-tile counts (sums_q) and the pair counts
 // (sums_p) over the blocks, then the capacity check: P, Q, the reported
 // count, the status and the counts later stages use (0 on overflow).
-__global__ void __launch_bounds__(kScanThreads) scan_counts_check_kernel(
-    unsigned long long* sums_q, unsigned long long* sums_p, int nblocks, long long capacity,
-    long long* Q, long long* P, long long* q_eff, long long* p_eff, long long* num_pairs_dev,
-    int* status) {
+struct CountsOut {
+  unsigned long long* sums_q;
+  unsigned long long* sums_p;
+  long long capacity;
+  long long *Q, *P, *q_eff, *p_eff, *num_pairs_dev;
+  int* status;
+};
+
+__device__ __forceinline__ void scan_counts_check_dev(const CountsOut& o, int nblocks);
+
+__global__ void __launch_bounds__(kScanThreads) scan_counts_check_kernel(const CountsOut o,
+                                                                         int nblocks) {
+  scan_counts_check_dev(o, nblocks);
+}
+
+__device__ __forceinline__ void scan_counts_check_dev(const CountsOut& o, int nblocks) {
+  unsigned long long* sums_q = o.sums_q;
+  unsigned long long* sums_p = o.sums_p;
+  const long long capacity = o.capacity;
+  long long *Q = o.Q, *P = o.P, *q_eff = o.q_eff, *p_eff = o.p_eff;
+  long long* num_pairs_dev = o.num_pairs_dev;
+  int* status = o.status;
   const long long q = scan_blocks_dev(sums_q, nblocks);
   const long long pp = scan_blocks_dev(sums_p, nblocks);
   if (threadIdx.x == 0) {
@@ -242,10 +283,14 @@ __device__ __forceinline__ unsigned st_count(const int4 r) {
 // Gathers the clamped rect of every depth-ordered row (so later stages read
 // them in order) and forms per-block sums of the super-tile counts and of
 // the pair counts.
+// The last CTA to finish scans both sums over the blocks and runs the
+// capacity check (scan_counts_check_dev).
 __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
     const unsigned* __restrict__ rows, const long long* __restrict__ n_dev,
     const int* __restrict__ rect, int N, const CamTable ct, int4* __restrict__ rect_sorted,
-    unsigned long long* __restrict__ sums_q, unsigned long long* __restrict__ sums_p) {
+    unsigned long long* __restrict__ arrive, const CountsOut co) {
+  unsigned long long* sums_q = co.sums_q;
+  unsigned long long* sums_p = co.sums_p;
   const long long n = *n_dev;
   const long long base = (long long)blockIdx.x * kScanTile;
   if (base >= n) {  // (the whole CTA) no rows: zero sums
@@ -253,13 +298,26 @@ __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
       sums_q[blockIdx.x] = 0ull;
       sums_p[blockIdx.x] = 0ull;
     }
+    if (last_block_arrives(arrive, gridDim.x)) scan_counts_check_dev(co, (int)gridDim.x);
     return;
   }
   unsigned long long q = 0, pp = 0;
+  // all row ids, then all rect gathers in flight before any use
+  unsigned row[kScanItems];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const long long i = base + (long long)k * kScanThreads + threadIdx.x;
+    row[k] = i < n ? rows[i] : 0xffffffffu;
+  }
+  int4 rr[kScanItems];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    rr[k] = row[k] != 0xffffffffu ? view_rect(rect, row[k], N, ct) : make_int4(0, 0, 0, 0);
+#pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     const long long i = base + (long long)k * kScanThreads + threadIdx.x;
     if (i < n) {
-      const int4 r = view_rect(rect, rows[i], N, ct);
+      const int4 r = rr[k];
       rect_sorted[i] = r;
       q += st_count(r);
       pp += (unsigned long long)((r.z - r.x) * (r.w - r.y));
@@ -272,6 +330,7 @@ __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
     sums_q[blockIdx.x] = tq;
     sums_p[blockIdx.x] = tp;
   }
+  if (last_block_arrives(arrive, gridDim.x)) scan_counts_check_dev(co, (int)gridDim.x);
 }
 
 // out[i] = exclusive prefix of the super-tile counts in depth order; and for
@@ -288,6 +347,7 @@ __global__ void __launch_bounds__(kScanThreads) row_offsets_kernel(
   if (base >= n) return;
   unsigned long long sum = 0;
   unsigned loc[kScanItems];
+#pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     const long long i = first + k;
     loc[k] = i < n ? st_count(rect_sorted[i]) : 0u;
@@ -534,11 +594,11 @@ constexpr int kDupPairs = 1024;
 static_assert(kDupPairs == 4 * kDupThreads, "duplicate_kernel stores 4 items per thread");
 static_assert(kDupPairs == kDupPairsScan, "row_offsets_kernel marks the duplication blocks");
 
-__global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
-    const unsigned* __restrict__ rows, const int4* __restrict__ rect_sorted,
-    const long long* __restrict__ n_vis, const unsigned long long* __restrict__ offsets, int N,
-    const CamTable ct, const long long* __restrict__ q_eff,
-    const unsigned* __restrict__ block_row, unsigned* __restrict__ skeys,
+// One block of kDupPairs items (b: the block's index).
+__device__ __forceinline__ void duplicate_block(
+    long long b, long long Q, long long n, const unsigned* __restrict__ rows,
+    const int4* __restrict__ rect_sorted, const unsigned long long* __restrict__ offsets, int N,
+    const CamTable& ct, const unsigned* __restrict__ block_row, unsigned* __restrict__ skeys,
     unsigned* __restrict__ svals, int vec16, int packed) {
   constexpr int kPer = kDupPairs / kDupThreads;  // 4 consecutive items per thread
   __shared__ int s_off[kDupPairs];     // row item offset relative to the block start
@@ -546,16 +606,13 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
   __shared__ unsigned s_rel[kDupPairs];  // rect relative to the span origin (packed)
   __shared__ int s_own[kDupPairs];     // slot of the row starting at item t (max-scanned)
   __shared__ int s_wmax[kDupThreads / 32];
-  const long long Q = *q_eff;
-  const long long start = (long long)blockIdx.x * kDupPairs;
-  if (start >= Q) return;
+  const long long start = b * kDupPairs;
   const long long end = min(Q, start + kDupPairs);
-  const long long n = *n_vis;
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-  const long long j0 = block_row[blockIdx.x];
+  const long long j0 = block_row[b];
   // rows j0 .. j1 overlap [start, end): j1 is the row holding the next block's
   // first item (it belongs here only if it starts before `end`), or the last row
-  const long long j1 = (end < Q) ? (long long)block_row[blockIdx.x + 1] : n - 1;
+  const long long j1 = (end < Q) ? (long long)block_row[b + 1] : n - 1;
   const int cand = (int)min((long long)kDupPairs, j1 - j0 + 1);
   for (int t = tid; t < kDupPairs; t += kDupThreads) s_own[t] = 0;
   __syncthreads();
@@ -648,6 +705,22 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
         svals[start + t0 + q] = vv[q];
       }
   }
+  __syncthreads();  // shared memory is reused by the CTA's next block
+}
+
+// Grid-stride over the blocks of the Q items (the grid is sized for the
+// bound on Q; a CTA beyond the last block leaves at once).
+__global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
+    const unsigned* __restrict__ rows, const int4* __restrict__ rect_sorted,
+    const long long* __restrict__ n_vis, const unsigned long long* __restrict__ offsets, int N,
+    const CamTable ct, const long long* __restrict__ q_eff,
+    const unsigned* __restrict__ block_row, unsigned* __restrict__ skeys,
+    unsigned* __restrict__ svals, int vec16, int packed) {
+  const long long Q = *q_eff;
+  const long long n = *n_vis;
+  for (long long b = blockIdx.x; b * kDupPairs < Q; b += gridDim.x)
+    duplicate_block(b, Q, n, rows, rect_sorted, offsets, N, ct, block_row, skeys, svals, vec16,
+                    packed);
 }
 
 // Per-key [start, end) from sorted u32 keys: each thread reads 4
@@ -884,10 +957,17 @@ __global__ void __launch_bounds__(256) st_count_kernel(
 // One CTA per super-tile, 16 groups x 64 tiles: exclusive scan of every
 // tile's counts over the super-tile's segments (in place), and the tile's
 // total list length.
+__device__ __forceinline__ void tile_scan_dev(const unsigned* __restrict__ tile_cnt, int T,
+                                              unsigned* __restrict__ tile_start,
+                                              unsigned* __restrict__ ranges);
+
 __global__ void __launch_bounds__(1024) st_scan_kernel(const unsigned* __restrict__ seg_first,
                                                        const CamTable ct,
                                                        unsigned* __restrict__ hist,
-                                                       unsigned* __restrict__ tile_cnt) {
+                                                       unsigned* __restrict__ tile_cnt,
+                                                       unsigned long long* __restrict__ arrive,
+                                                       unsigned* __restrict__ tile_start,
+                                                       unsigned* __restrict__ ranges) {
   __shared__ unsigned s_part[16][64];
   const int s = blockIdx.x;
   const int k = threadIdx.x >> 6, bt = threadIdx.x & 63;
@@ -919,13 +999,15 @@ __global__ void __launch_bounds__(1024) st_scan_kernel(const unsigned* __restric
     *h = run;
     run += x;
   }
+  if (last_block_arrives(arrive, gridDim.x)) tile_scan_dev(tile_cnt, ct.total_tiles, tile_start, ranges);
 }
 
 // Exclusive scan of the list lengths over all T tiles (one CTA of 1024
 // threads): list starts, and ranges [start, end) ((0, 0) for an empty list).
-__global__ void __launch_bounds__(1024) tile_scan_kernel(const unsigned* __restrict__ tile_cnt,
-                                                         int T, unsigned* __restrict__ tile_start,
-                                                         unsigned* __restrict__ ranges) {
+// Run by the last CTA of st_scan_kernel (tile_cnt read through L2).
+__device__ __forceinline__ void tile_scan_dev(const unsigned* __restrict__ tile_cnt, int T,
+                                              unsigned* __restrict__ tile_start,
+                                              unsigned* __restrict__ ranges) {
   __shared__ unsigned s_w[32];
   __shared__ unsigned s_carry;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -933,7 +1015,7 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const unsigned* __restr
   __syncthreads();
   for (int base = 0; base < T; base += 1024) {
     const int t = base + tid;
-    const unsigned cnt = t < T ? tile_cnt[t] : 0u;
+    const unsigned cnt = t < T ? __ldcg(tile_cnt + t) : 0u;
     unsigned incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -1084,6 +1166,8 @@ inline long long scan_blocks(long long n) { return (n + kScanTile - 1) / kScanTi
 // ceil(len / kSeg) <= Q / kSeg + super-tiles, and Q <= P <= cap.
 inline long long max_segments(long long cap, long long tiles) { return cap / kSeg + tiles + 2; }
 
+constexpr int kCounters = 12;  // 8 counts, then 3 arrival counters
+
 Workspace carve(void* base, long long n_rows, long long cap, long long tiles) {
   Workspace w;
   char* p = reinterpret_cast<char*>(base);
@@ -1097,7 +1181,7 @@ Workspace carve(void* base, long long n_rows, long long cap, long long tiles) {
   const long long ms = max_segments(cap, tiles);
   w.block_sums = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * nb));
   w.block_sums2 = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * nb));
-  w.counters = reinterpret_cast<long long*>(take(sizeof(long long) * 8));
+  w.counters = reinterpret_cast<long long*>(take(sizeof(long long) * kCounters));
   for (int i = 0; i < 2; ++i) w.rk[i] = reinterpret_cast<unsigned*>(take(4 * (n_rows + 1)));
   for (int i = 0; i < 2; ++i) w.rv[i] = reinterpret_cast<unsigned*>(take(4 * (n_rows + 1)));
   w.offsets = reinterpret_cast<unsigned long long*>(take(8 * (n_rows + 1)));
@@ -1192,14 +1276,18 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
   long long* Q = w.counters + 3;
   long long* q_eff = w.counters + 4;
   long long* n_seg = w.counters + 5;
-  GS_TRY_CUDA(cudaMemsetAsync(w.counters, 0, 8 * sizeof(long long), st));
+  // arrival counters of the kernels whose last CTA runs the following scan
+  unsigned long long* arrive = reinterpret_cast<unsigned long long*>(w.counters + 8);
+  GS_TRY_CUDA(cudaMemsetAsync(w.counters, 0, kCounters * sizeof(long long), st));
+  const CountsOut co{w.block_sums, w.block_sums2, cap, Q, P, q_eff, p_eff, num_pairs_dev,
+                     status_dev};
   unsigned* rows_sorted = w.rv[0];
   const long long nb = scan_blocks(n_rows);
   if (n_rows > 0) {
     // 1. compaction of the visible rows, keyed by FP32 depth bits
     ScanSrc vis{proj->tiles_touched, nullptr, 1};
-    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(vis, nullptr, n_rows, w.block_sums);
-    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(w.block_sums, (int)nb, n_vis);
+    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(vis, nullptr, n_rows, w.block_sums,
+                                                              arrive, n_vis);
     compact_visible_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(
         proj->tiles_touched, proj->depth, n_rows, w.block_sums, w.rk[0], w.rv[0]);
     // 2. stable depth sort of the visible rows (ties keep row order = id order)
@@ -1207,15 +1295,15 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
     rows_sorted = w.rv[res];
     // 3. per row in depth order: super-tile offsets, the super-pair count Q
     //    and the pair count P
+    //    (its last CTA: the scans of Q and P over the blocks, the capacity
+    //    check and the reported count)
     rows_gather_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(
-        rows_sorted, n_vis, proj->rect, N, ct, w.rect_sorted, w.block_sums, w.block_sums2);
-    count_launches(4);
+        rows_sorted, n_vis, proj->rect, N, ct, w.rect_sorted, arrive + 1, co);
+    count_launches(3);
+  } else {
+    scan_counts_check_kernel<<<1, kScanThreads, 0, st>>>(co, 0);
+    count_launches(1);
   }
-  // scans of Q and P over the blocks, the capacity check and the reported count
-  scan_counts_check_kernel<<<1, kScanThreads, 0, st>>>(w.block_sums, w.block_sums2,
-                                                       n_rows > 0 ? (int)nb : 0, cap, Q, P, q_eff,
-                                                       p_eff, num_pairs_dev, status_dev);
-  count_launches(1);
   if (n_rows > 0) {
     // super-tile offsets per row, and the first row of every duplication block
     row_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(
@@ -1260,7 +1348,8 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
   for (int v = 0; v < ct.V; ++v)
     if (ct.c[v].TX > 8000 || ct.c[v].TY > 8000) packed = 0;
   {
-    const unsigned g2 = (unsigned)((q_bound + kDupPairs - 1) / kDupPairs);
+    const unsigned g2 =
+        (unsigned)std::min<long long>((q_bound + kDupPairs - 1) / kDupPairs, 152ll * 6);
     const int vec16 = (reinterpret_cast<uintptr_t>(sv[0]) % 16 == 0) ? 1 : 0;
     duplicate_kernel<<<g2, kDupThreads, 0, st>>>(rows_sorted, w.rect_sorted, n_vis, w.offsets, N,
                                                 ct, q_eff, w.block_row, sk[0], sv[0], vec16,
@@ -1292,14 +1381,14 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
                                       reinterpret_cast<const uint2*>(w.st_ranges), w.seg_first,
                                       w.seg_st, n_seg, packed, proj->rect, N, ct, desc,
                                       w.seg_hist);
-  st_scan_kernel<<<(unsigned)S, 1024, 0, st>>>(w.seg_first, ct, w.seg_hist, w.tile_cnt);
-  tile_scan_kernel<<<1, 1024, 0, st>>>(w.tile_cnt, (int)T, w.tile_start, ranges);
+  st_scan_kernel<<<(unsigned)S, 1024, 0, st>>>(w.seg_first, ct, w.seg_hist, w.tile_cnt,
+                                                arrive + 2, w.tile_start, ranges);
   // 7. every row into the lists of the tiles it covers, in depth order
   st_emit_kernel<<<gs, 256, 0, st>>>(sp_keys, sp_rows, desc, packed,
                                      reinterpret_cast<const uint2*>(w.st_ranges), w.seg_first,
                                      w.seg_st, n_seg, w.seg_hist, w.tile_start, ct, proj->depth,
                                      sorted_vals, sorted_keys);
-  count_launches(5);
+  count_launches(4);
   return check_launch();
 }
 

@@ -15,6 +15,8 @@
 // Cholesky factor of the 2D covariance (whitened form) and accumulates the
 // log-scale and rotation-matrix gradients over views, pushed to the
 // quaternion once.
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -654,81 +656,49 @@ __device__ __forceinline__ void adjoint_one(
   reinterpret_cast<float4*>(g_quats)[g] = gq;
 }
 
-// Zeroes p[0, n) with the block's threads (16-byte stores where aligned).
-__device__ __forceinline__ void zero_span(float* p, long long n) {
-  if (n <= 0) return;
-  long long head = (long long)((16 - (reinterpret_cast<uintptr_t>(p) & 15)) & 15) / 4;
-  if ((reinterpret_cast<uintptr_t>(p) & 3) != 0) head = n;  // not even 4-byte aligned
-  head = min(head, n);
-  for (long long i = threadIdx.x; i < head; i += blockDim.x) p[i] = 0.f;
-  float4* q = reinterpret_cast<float4*>(p + head);
-  const long long n4 = (n - head) / 4;
-  for (long long i = threadIdx.x; i < n4; i += blockDim.x) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (long long i = head + 4 * n4 + threadIdx.x; i < n; i += blockDim.x) p[i] = 0.f;
+// The adjoint runs over a list of the Gaussians some view sees, kept in the
+// pad floats of grad2d (the blending adjoint writes floats 0..8 of a row):
+// entry k is float 9 of row k and the count is float 11 of row 0, all as
+// unsigned; grad2d is zeroed before.  A warp ranks its visible lanes by a
+// ballot and reserves their slots with one atomic, so the list is in no
+// particular order (each entry is independent).
+constexpr int kListThreads = 256;
+__global__ void __launch_bounds__(kListThreads) adjoint_list_kernel(
+    const unsigned* __restrict__ tiles_touched, int N, int V, float* __restrict__ grad2d) {
+  unsigned* g2 = reinterpret_cast<unsigned*>(grad2d);
+  const int lane = threadIdx.x & 31;
+  for (long long base = (long long)blockIdx.x * kListThreads; base < N;
+       base += (long long)gridDim.x * kListThreads) {
+    const long long g = base + threadIdx.x;
+    bool vis = false;
+    if (g < N)
+      for (int v = 0; v < V; ++v) vis |= tiles_touched[(long long)v * N + g] != 0u;
+    const unsigned b = __ballot_sync(0xffffffffu, vis);
+    unsigned slot = 0u;
+    if (lane == 0 && b) slot = atomicAdd(g2 + 11, (unsigned)__popc(b));
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (vis) g2[12ll * (slot + __popc(b & ((1u << lane) - 1u))) + 9] = (unsigned)g;
+  }
 }
 
-// The adjoint over Gaussians, compacted per block: each CTA owns 2048
-// consecutive Gaussians, zeroes their gradients, lists the ones some view
-// sees in shared memory (ascending), then its threads take the listed
-// Gaussians densely, so a scene where most Gaussians are culled does not run
-// the long adjoint on warps with one or two live lanes.  (The zeroing is
-// ordered before the adjoint's writes by the barriers of the list build.)
-constexpr int kAdjThreads = 256;
-constexpr int kAdjPer = 8;
-constexpr int kAdjSpan = kAdjThreads * kAdjPer;
-constexpr int kAdjWarps = kAdjThreads / 32;
-
-__global__ void __launch_bounds__(kAdjThreads) preprocess_bwd_kernel(
+// The adjoint over the listed Gaussians: a resident grid (4 CTAs of 128
+// threads per SM at up to 128 registers), one Gaussian per thread and
+// iteration.  Every gradient starts at zero (zeroed by the caller), so
+// Gaussians no view sees are never touched.
+constexpr int kAdjThreads = 128;
+__global__ void __launch_bounds__(kAdjThreads, 4) preprocess_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales,
     const float* __restrict__ quats, const float* __restrict__ opacity_logits,
     const float* __restrict__ sh, int N, const CamTable ct, float dilation, int sh_deg,
     int sh_stride, const unsigned* __restrict__ tiles_touched, const float* __restrict__ grad2d,
     float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
     float* __restrict__ g_opac, float* __restrict__ g_sh) {
-  __shared__ int s_list[kAdjSpan];
-  __shared__ int s_off[kAdjPer * kAdjWarps + 1];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int base = blockIdx.x * kAdjSpan;
-  const long long cnt = min((long long)kAdjSpan, (long long)N - base);
-  // every gradient of the CTA's Gaussians starts at zero (contiguous spans)
-  zero_span(g_means + 3ll * base, 3 * cnt);
-  zero_span(g_ls + 3ll * base, 3 * cnt);
-  zero_span(g_quats + 4ll * base, 4 * cnt);
-  zero_span(g_opac + base, cnt);  // (g_sh is zeroed by the caller)
-  unsigned ball[kAdjPer];
-  // pass k covers Gaussians base + k*256 + tid: the (k, warp, lane) order is
-  // ascending in g
-#pragma unroll
-  for (int k = 0; k < kAdjPer; ++k) {
-    const int g = base + k * kAdjThreads + tid;
-    bool any = false;
-    if (g < N) {
-      for (int v = 0; v < ct.V; ++v) any |= tiles_touched[(long long)v * N + g] != 0u;
-    }
-    ball[k] = __ballot_sync(0xffffffffu, any);
-    if (lane == 0) s_off[k * kAdjWarps + w] = __popc(ball[k]);
-  }
-  __syncthreads();
-  if (tid == 0) {
-    int run = 0;
-    for (int i = 0; i < kAdjPer * kAdjWarps; ++i) {
-      const int c = s_off[i];
-      s_off[i] = run;
-      run += c;
-    }
-    s_off[kAdjPer * kAdjWarps] = run;
-  }
-  __syncthreads();
-  const unsigned below = (1u << lane) - 1u;
-#pragma unroll
-  for (int k = 0; k < kAdjPer; ++k)
-    if (ball[k] & (1u << lane))
-      s_list[s_off[k * kAdjWarps + w] + __popc(ball[k] & below)] = base + k * kAdjThreads + tid;
-  __syncthreads();
-  const int total = s_off[kAdjPer * kAdjWarps];
-  for (int i = tid; i < total; i += kAdjThreads)
-    adjoint_one(s_list[i], means, log_scales, quats, opacity_logits, sh, N, ct, dilation, sh_deg,
-                sh_stride, tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh);
+  const unsigned* g2 = reinterpret_cast<const unsigned*>(grad2d);
+  const unsigned n = g2[11];
+  for (unsigned i = blockIdx.x * kAdjThreads + threadIdx.x; i < n; i += gridDim.x * kAdjThreads)
+    adjoint_one((int)g2[12ll * i + 9], means, log_scales, quats, opacity_logits, sh, N, ct,
+                dilation, sh_deg, sh_stride, tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac,
+                g_sh);
 }
 
 }  // namespace
@@ -764,9 +734,19 @@ int launch_preprocess_bwd(const float* means, const float* log_scales, const flo
                           float* g_means, float* g_ls, float* g_quats, float* g_opac, float* g_sh,
                           cudaStream_t st) {
   if (N == 0) return GS_OK;
-  preprocess_bwd_kernel<<<(N + kAdjSpan - 1) / kAdjSpan, kAdjThreads, 0, st>>>(
+  const int grid = (int)std::min<long long>(152ll * 4, ((long long)N + kAdjThreads - 1) / kAdjThreads);
+  preprocess_bwd_kernel<<<grid, kAdjThreads, 0, st>>>(
       means, log_scales, quats, opacity_logits, sh, N, ct, prm->dilation, prm->sh_degree,
       prm->sh_stride, tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh);
+  count_launches(1);
+  return check_launch();
+}
+
+int launch_adjoint_list(const unsigned* tiles_touched, int N, int V, float* grad2d,
+                        cudaStream_t st) {
+  if (N == 0) return GS_OK;
+  const int grid = (int)std::min<long long>(152ll * 8, ((long long)N + kListThreads - 1) / kListThreads);
+  adjoint_list_kernel<<<grid, kListThreads, 0, st>>>(tiles_touched, N, V, grad2d);
   count_launches(1);
   return check_launch();
 }
