@@ -465,17 +465,17 @@ int gs_render_bwd(const gs_proj* proj, int N, const gs_camera* cams, int V, cons
   if (opt && opt->ctas > 0 && !opt->work_counter) return invalid("persistent launch needs work_counter");
   cudaStream_t st = (cudaStream_t)stream;
   if (N == 0) return GS_OK;  // no Gaussians: no gradients
-  const size_t sh_bytes = sizeof(float) * 3 * (size_t)prm->sh_stride * N;
   GS_TRY_CUDA(cudaMemsetAsync(grad2d, 0, sizeof(float) * 12 * (size_t)N * V, st));
   // Beside the blending adjoint (bound by instruction issue, most of the
   // memory bandwidth free), on the side stream: the list of Gaussians some
   // view sees (in grad2d's pad floats, after its zeroing) and the zeroing of
-  // every parameter gradient (the projection adjoint writes only the listed
-  // Gaussians').
+  // every parameter gradient.  (Zeroing only the unseen Gaussians' gradients
+  // inside the list kernel was slower where most Gaussians are unseen and
+  // no faster where all are seen.)
   auto side_work = [&](cudaStream_t s) -> int {
-    int r = launch_adjoint_list(proj->tiles_touched, N, V, grad2d, s);
+    const int r = launch_adjoint_list(proj->tiles_touched, N, V, grad2d, s);
     if (r != GS_OK) return r;
-    GS_TRY_CUDA(cudaMemsetAsync(g_sh, 0, sh_bytes, s));
+    GS_TRY_CUDA(cudaMemsetAsync(g_sh, 0, sizeof(float) * 3 * (size_t)prm->sh_stride * N, s));
     GS_TRY_CUDA(cudaMemsetAsync(g_means, 0, sizeof(float) * 3 * (size_t)N, s));
     GS_TRY_CUDA(cudaMemsetAsync(g_log_scales, 0, sizeof(float) * 3 * (size_t)N, s));
     GS_TRY_CUDA(cudaMemsetAsync(g_quats, 0, sizeof(float) * 4 * (size_t)N, s));
