@@ -256,10 +256,25 @@ __global__ void __launch_bounds__(kLossThreads) loss_finalize_kernel(
   }
 }
 
+// log s += ln(zeta), 16-byte accesses for the aligned body.
 __global__ void scale_reset_kernel(float* __restrict__ ls, long long n, float delta) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    ls[i] += delta;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long head = (long long)((16 - (reinterpret_cast<uintptr_t>(ls) & 15)) & 15) / 4;
+  if ((reinterpret_cast<uintptr_t>(ls) & 3) != 0) head = n;
+  head = head < n ? head : n;
+  for (long long i = t0; i < head; i += stride) ls[i] += delta;
+  float4* q = reinterpret_cast<float4*>(ls + head);
+  const long long n4 = (n - head) / 4;
+  for (long long i = t0; i < n4; i += stride) {
+    float4 v = q[i];
+    v.x += delta;
+    v.y += delta;
+    v.z += delta;
+    v.w += delta;
+    q[i] = v;
+  }
+  for (long long i = head + 4 * n4 + t0; i < n; i += stride) ls[i] += delta;
 }
 
 int loss_blocks(long long P) {
@@ -513,7 +528,7 @@ int gs_scale_reset(float* log_scales, long long n, float zeta, gs_stream stream)
   if (n < 0 || (n > 0 && !log_scales)) return invalid("log_scales");
   if (n == 0) return GS_OK;
   const float delta = (float)log((double)zeta);
-  unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, 152ll * 8);
+  unsigned grid = (unsigned)std::min<long long>((n / 4 + 255) / 256 + 1, 152ll * 8);
   scale_reset_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(log_scales, n, delta);
   count_launches(1);
   return check_launch();

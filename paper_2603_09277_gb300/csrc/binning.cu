@@ -398,19 +398,27 @@ __global__ void __launch_bounds__(kRadixThreads) radix_upsweep_kernel(
   const int w = threadIdx.x >> 5;
   long long n = *n_dev;
   if ((int)blockIdx.x >= radix_active(n, gridDim.x)) return;  // (the whole CTA)
-  for (int i = threadIdx.x; i < kRadixWarps * kRadixBins; i += kRadixThreads)
-    (&s_h[0][0])[i] = 0u;
-  __syncthreads();
   long long chunk = radix_chunk(n, gridDim.x);
   long long b0 = (long long)blockIdx.x * chunk;
   long long b1 = min(n, b0 + chunk);
-  // kRadixIpt loads in flight per thread
-  for (long long t0 = b0; t0 < b1; t0 += kRadixTile) {
-    unsigned kk[kRadixIpt];
+  // kRadixIpt loads in flight per thread; the first tile's are requested
+  // before the histogram is cleared
+  unsigned kk[kRadixIpt];
 #pragma unroll
-    for (int i = 0; i < kRadixIpt; ++i) {
-      const long long j = t0 + i * kRadixThreads + threadIdx.x;
-      kk[i] = j < b1 ? keys[j] : 0xffffffffu;
+  for (int i = 0; i < kRadixIpt; ++i) {
+    const long long j = b0 + i * kRadixThreads + threadIdx.x;
+    kk[i] = j < b1 ? keys[j] : 0xffffffffu;
+  }
+  for (int i = threadIdx.x; i < kRadixWarps * kRadixBins; i += kRadixThreads)
+    (&s_h[0][0])[i] = 0u;
+  __syncthreads();
+  for (long long t0 = b0; t0 < b1; t0 += kRadixTile) {
+    if (t0 != b0) {
+#pragma unroll
+      for (int i = 0; i < kRadixIpt; ++i) {
+        const long long j = t0 + i * kRadixThreads + threadIdx.x;
+        kk[i] = j < b1 ? keys[j] : 0xffffffffu;
+      }
     }
 #pragma unroll
     for (int i = 0; i < kRadixIpt; ++i)
@@ -477,15 +485,8 @@ __global__ void __launch_bounds__(kRadixThreads, 3) radix_downsweep_kernel(
   long long chunk = radix_chunk(n, gridDim.x);
   long long b0 = (long long)blockIdx.x * chunk;
   long long b1 = min(n, b0 + chunk);
-  {
-    // digit base = exclusive scan of the digit totals (256 threads, one digit each)
-    unsigned long long tot;
-    unsigned long long db = block_excl_scan(totals[threadIdx.x], &tot);
-    s_base[threadIdx.x] = (unsigned)db + offsets[(long long)threadIdx.x * gridDim.x + blockIdx.x];
-  }
-  for (int i = threadIdx.x; i < kRadixWarps * (kRadixBins + 1); i += kRadixThreads)
-    (&s_wc[0][0])[i] = 0u;
-  __syncthreads();
+  // the first tile's keys and values are requested before the digit bases
+  // (independent loads, their latency overlaps the scan)
   unsigned nk[kRadixIpt], nv[kRadixIpt];
   const int lbase = w * (32 * kRadixIpt) + lane;
   if (b0 < b1) {
@@ -496,6 +497,16 @@ __global__ void __launch_bounds__(kRadixThreads, 3) radix_downsweep_kernel(
       nv[i] = j < b1 ? vals_in[j] : 0u;
     }
   }
+  {
+    // digit base = exclusive scan of the digit totals (256 threads, one digit each)
+    const unsigned off = offsets[(long long)threadIdx.x * gridDim.x + blockIdx.x];
+    unsigned long long tot;
+    unsigned long long db = block_excl_scan(totals[threadIdx.x], &tot);
+    s_base[threadIdx.x] = (unsigned)db + off;
+  }
+  for (int i = threadIdx.x; i < kRadixWarps * (kRadixBins + 1); i += kRadixThreads)
+    (&s_wc[0][0])[i] = 0u;
+  __syncthreads();
   for (long long t0 = b0; t0 < b1; t0 += kRadixTile) {
     const int cnt = (int)min((long long)kRadixTile, b1 - t0);
     unsigned k[kRadixIpt], v[kRadixIpt], dg[kRadixIpt], loc[kRadixIpt];

@@ -319,6 +319,19 @@ def test_scale_reset_parity():
     assert (np.abs(got - ref) <= 1.0 * ulp).all()
     with pytest.raises(Exception):
         gs.gs_scale_reset(t, 1.5)
+    # unaligned starts and ragged lengths (scalar head and tail around the
+    # 16-byte body), neighbours untouched
+    flat = rng.normal(-4, 1, 4099).astype(np.float32)
+    for off, n in ((1, 4097), (2, 5), (3, 4093), (0, 3), (1, 0)):
+        u = torch.as_tensor(flat).cuda()
+        gs.gs_scale_reset(u[off:off + n], 0.2)
+        torch.cuda.synchronize()
+        got = u.cpu().numpy().astype(np.float64)
+        want = flat.astype(np.float64).copy()
+        want[off:off + n] = oracle.scale_reset(flat[off:off + n], 0.2)
+        ulp = np.spacing(np.abs(want).astype(np.float32)).astype(np.float64)
+        assert (np.abs(got - want) <= ulp).all(), (off, n)
+        assert (got[:off] == flat[:off]).all() and (got[off + n:] == flat[off + n:]).all()
 
 
 # ---------------------------------------------------------------------------
