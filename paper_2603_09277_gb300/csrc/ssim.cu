@@ -51,16 +51,39 @@ __device__ __forceinline__ int view_of_block(const SsimViews& sv, int b) {
   return v;
 }
 
-// Horizontal pass of the separable window: h[k][r][x] = sum_i w_i f_k(r, x + i)
-// for the 26 staged rows and 16 output columns.
-constexpr int kHN = kSsimS * kSsimB;  // 416 horizontal outputs per quantity
+// Both passes of the separable window are register-blocked: a thread takes
+// kRun consecutive outputs along the pass direction, loads the kRun + 10
+// samples they share from shared memory once, and sums each output's 11 taps
+// in tap order (the same arithmetic per output as a tap-by-tap loop).  All
+// three channels are passed together.
+constexpr int kRun = 4;                          // outputs per thread and pass
+constexpr int kSpan = kRun + 2 * kSsimR;         // samples per run (14)
+constexpr int kHItems = 3 * kSsimS * (kSsimB / kRun);  // horizontal runs (312)
+constexpr int kVItems = 3 * kSsimB * (kSsimB / kRun);  // vertical runs (192)
+static_assert(kSsimB % kRun == 0, "runs tile the block");
+static_assert(kVItems <= kSsimThreads, "one vertical run per thread");
+
+// Exclusive per-block partial of sum (1 - S) (FP32 within the thread and the
+// warp: every term is >= 0; FP64 across the warps).
+__device__ __forceinline__ void block_partial(float acc, double scale, double* out) {
+  __shared__ double s_red[kSsimThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = (double)acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kSsimThreads / 32; ++k) t += s_red[k];
+    *out = t * scale;
+  }
+}
 
 __global__ void __launch_bounds__(kSsimThreads) ssim_fwd_kernel(
     const float* __restrict__ image, const float* __restrict__ target, const SsimViews sv,
     float* __restrict__ maps /* 15 planes of P */, long long P, double* __restrict__ partials) {
   __shared__ float sx[3][kSsimS][kSsimS];
   __shared__ float sy[3][kSsimS][kSsimS];
-  __shared__ float sh[5][kHN];
+  __shared__ __align__(16) float sh[3][5][kSsimS][kSsimB];  // horizontal sums
   const int b = blockIdx.x;
   const int v = view_of_block(sv, b);
   const int lb = b - sv.block_off[v];
@@ -78,147 +101,185 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_fwd_kernel(
     }
   }
   __syncthreads();
-  const int lx = threadIdx.x % kSsimB, ly = threadIdx.x / kSsimB;
-  const int px = bx + lx, py = by + ly;
-  const bool mine = px < W && py < H;
-  const long long p = base + (long long)py * W + px;
-  float acc = 0.f;  // 1 - S >= 0: FP32 within the thread and the warp, FP64 beyond
-  for (int ch = 0; ch < 3; ++ch) {
+  // horizontal: run (ch, staged row r, columns x0 .. x0 + kRun - 1)
+  for (int it = threadIdx.x; it < kHItems; it += kSsimThreads) {
+    const int g = it % (kSsimB / kRun), r = (it / (kSsimB / kRun)) % kSsimS;
+    const int ch = it / (kSsimS * (kSsimB / kRun));
+    const int x0 = g * kRun;
     const float cx = sx[ch][kSsimR + kSsimB / 2][kSsimR + kSsimB / 2];
     const float cy = sy[ch][kSsimR + kSsimB / 2][kSsimR + kSsimB / 2];
-    for (int t = threadIdx.x; t < kHN; t += kSsimThreads) {
-      const int r = t / kSsimB, x = t % kSsimB;
-      float m = 0.f, n = 0.f, dd = 0.f, ee = 0.f, de = 0.f;
+    float d[kSpan], e[kSpan];
 #pragma unroll
-      for (int i = 0; i < 2 * kSsimR + 1; ++i) {
-        const float w = sv.win[i];
-        const float d = sx[ch][r][x + i] - cx, e = sy[ch][r][x + i] - cy;
-        const float wd = w * d, we = w * e;
-        m += wd;
-        n += we;
-        dd = __fmaf_rn(wd, d, dd);
-        ee = __fmaf_rn(we, e, ee);
-        de = __fmaf_rn(wd, e, de);
-      }
-      sh[0][t] = m;
-      sh[1][t] = n;
-      sh[2][t] = dd;
-      sh[3][t] = ee;
-      sh[4][t] = de;
+    for (int j = 0; j < kSpan; ++j) {
+      d[j] = sx[ch][r][x0 + j] - cx;
+      e[j] = sy[ch][r][x0 + j] - cy;
     }
-    __syncthreads();
-    if (mine) {
-      float m1 = 0.f, n1 = 0.f, dxx = 0.f, dyy = 0.f, dxy = 0.f;
+    float m[kRun], n[kRun], dd[kRun], ee[kRun], de[kRun];
 #pragma unroll
-      for (int j = 0; j < 2 * kSsimR + 1; ++j) {
-        const float w = sv.win[j];
-        const int t = (ly + j) * kSsimB + lx;
-        m1 = __fmaf_rn(w, sh[0][t], m1);
-        n1 = __fmaf_rn(w, sh[1][t], n1);
-        dxx = __fmaf_rn(w, sh[2][t], dxx);
-        dyy = __fmaf_rn(w, sh[3][t], dyy);
-        dxy = __fmaf_rn(w, sh[4][t], dxy);
+    for (int o = 0; o < kRun; ++o) m[o] = n[o] = dd[o] = ee[o] = de[o] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 2 * kSsimR + 1; ++i) {
+      const float w = sv.win[i];
+#pragma unroll
+      for (int o = 0; o < kRun; ++o) {
+        const float wd = w * d[o + i], we = w * e[o + i];
+        m[o] += wd;
+        n[o] += we;
+        dd[o] = __fmaf_rn(wd, d[o + i], dd[o]);
+        ee[o] = __fmaf_rn(we, e[o + i], ee[o]);
+        de[o] = __fmaf_rn(wd, e[o + i], de[o]);
       }
-      const float mx = cx + m1, my = cy + n1;
-      const float sxx = __fmaf_rn(-m1, m1, dxx), syy = __fmaf_rn(-n1, n1, dyy);
-      const float sxy = __fmaf_rn(-m1, n1, dxy);
-      const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
-      const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
-      const float D = B1 * B2;
-      const float S = A1 * A2 / D;
-      acc += 1.f - S;
-      float* m = maps + (long long)(5 * ch) * P + p;
-      m[0] = mx;
-      m[P] = my;
-      m[2 * P] = (2.f * my * A2 - S * 2.f * mx * B2) / D;  // dS/dmu_x, sigmas fixed
-      m[3 * P] = -S / B2;                                  // dS/dsigma_x^2
-      m[4 * P] = 2.f * A1 / D;                             // dS/dsigma_xy
     }
-    __syncthreads();  // sh is rewritten for the next channel
+    *reinterpret_cast<float4*>(&sh[ch][0][r][x0]) = make_float4(m[0], m[1], m[2], m[3]);
+    *reinterpret_cast<float4*>(&sh[ch][1][r][x0]) = make_float4(n[0], n[1], n[2], n[3]);
+    *reinterpret_cast<float4*>(&sh[ch][2][r][x0]) = make_float4(dd[0], dd[1], dd[2], dd[3]);
+    *reinterpret_cast<float4*>(&sh[ch][3][r][x0]) = make_float4(ee[0], ee[1], ee[2], ee[3]);
+    *reinterpret_cast<float4*>(&sh[ch][4][r][x0]) = make_float4(de[0], de[1], de[2], de[3]);
   }
-  __shared__ double s_red[kSsimThreads / 32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = (double)acc;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int k = 0; k < kSsimThreads / 32; ++k) t += s_red[k];
-    partials[b] = t * (double)sv.scale[v];
+  // vertical: run (ch, column c, output rows y0 .. y0 + kRun - 1)
+  float acc = 0.f;
+  if (threadIdx.x < kVItems) {
+    const int c = threadIdx.x % kSsimB, q = (threadIdx.x / kSsimB) % (kSsimB / kRun);
+    const int ch = threadIdx.x / (kSsimB * (kSsimB / kRun));
+    const int y0 = q * kRun;
+    const float cx = sx[ch][kSsimR + kSsimB / 2][kSsimR + kSsimB / 2];
+    const float cy = sy[ch][kSsimR + kSsimB / 2][kSsimR + kSsimB / 2];
+    float mom[5][kRun];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      float col[kSpan];
+#pragma unroll
+      for (int j = 0; j < kSpan; ++j) col[j] = sh[ch][k][y0 + j][c];
+#pragma unroll
+      for (int o = 0; o < kRun; ++o) {
+        float t = 0.f;
+#pragma unroll
+        for (int j = 0; j < 2 * kSsimR + 1; ++j) t = __fmaf_rn(sv.win[j], col[o + j], t);
+        mom[k][o] = t;
+      }
+    }
+    const int px = bx + c;
+#pragma unroll
+    for (int o = 0; o < kRun; ++o) {
+      const int py = by + y0 + o;
+      if (px < W && py < H) {
+        const long long p = base + (long long)py * W + px;
+        const float m1 = mom[0][o], n1 = mom[1][o];
+        const float mx = cx + m1, my = cy + n1;
+        const float sxx = __fmaf_rn(-m1, m1, mom[2][o]), syy = __fmaf_rn(-n1, n1, mom[3][o]);
+        const float sxy = __fmaf_rn(-m1, n1, mom[4][o]);
+        const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
+        const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
+        const float D = B1 * B2;
+        const float S = A1 * A2 / D;
+        acc += 1.f - S;
+        float* mp = maps + (long long)(5 * ch) * P + p;
+        mp[0] = mx;
+        mp[P] = my;
+        mp[2 * P] = (2.f * my * A2 - S * 2.f * mx * B2) / D;  // dS/dmu_x, sigmas fixed
+        mp[3 * P] = -S / B2;                                   // dS/dsigma_x^2
+        mp[4 * P] = 2.f * A1 / D;                              // dS/dsigma_xy
+      }
+    }
   }
+  block_partial(acc, (double)sv.scale[v], partials + b);
 }
 
 __global__ void __launch_bounds__(kSsimThreads) ssim_bwd_kernel(
     const float* __restrict__ image, const float* __restrict__ target, const SsimViews sv,
     const float* __restrict__ maps, long long P, float* __restrict__ dimg) {
-  __shared__ float sm[5][kSsimS][kSsimS];  // one channel at a time
-  __shared__ float sh[5][kHN];
-  __shared__ float s_c[2];
+  __shared__ float sm[3][5][kSsimS][kSsimS + 1];             // staged map terms
+  __shared__ __align__(16) float sh[3][5][kSsimS][kSsimB];  // horizontal sums
+  __shared__ float s_c[3][2];
   const int b = blockIdx.x;
   const int v = view_of_block(sv, b);
   const int lb = b - sv.block_off[v];
   const int W = sv.W[v], H = sv.H[v];
   const int bx = (lb % sv.BX[v]) * kSsimB, by = (lb / sv.BX[v]) * kSsimB;
   const long long base = sv.pix_off[v];
-  const int lx = threadIdx.x % kSsimB, ly = threadIdx.x / kSsimB;
-  const int px = bx + lx, py = by + ly;
-  const bool mine = px < W && py < H;
-  const long long p = base + (long long)py * W + px;
   // block constants: the image and target at the block's first pixel
   const long long p0 = base + (long long)by * W + bx;
-  for (int ch = 0; ch < 3; ++ch) {
-    if (threadIdx.x == 0) {
-      s_c[0] = image[3 * p0 + ch];
-      s_c[1] = target[3 * p0 + ch];
-    }
-    __syncthreads();  // (also: the previous channel's readers are done)
-    const float cx = s_c[0], cy = s_c[1];
-    const float* mp = maps + (long long)(5 * ch) * P;
-    for (int i = threadIdx.x; i < kSsimS * kSsimS; i += kSsimThreads) {
-      const int yy = by - kSsimR + i / kSsimS, xx = bx - kSsimR + i % kSsimS;
-      const bool in = xx >= 0 && xx < W && yy >= 0 && yy < H;  // window centres in the image
-      const long long q = base + (long long)yy * W + xx;
+  if (threadIdx.x < 3) {
+    s_c[threadIdx.x][0] = image[3 * p0 + threadIdx.x];
+    s_c[threadIdx.x][1] = target[3 * p0 + threadIdx.x];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kSsimS * kSsimS; i += kSsimThreads) {
+    const int yy = by - kSsimR + i / kSsimS, xx = bx - kSsimR + i % kSsimS;
+    const bool in = xx >= 0 && xx < W && yy >= 0 && yy < H;  // window centres in the image
+    const long long q = base + (long long)yy * W + xx;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      const float* mp = maps + (long long)(5 * ch) * P;
       float a = 0.f, bb = 0.f, e = 0.f, pm = 0.f, qm = 0.f;
       if (in) {
         const float mx = mp[q], my = mp[P + q];
         a = mp[2 * P + q];
         bb = mp[3 * P + q];
         e = mp[4 * P + q];
-        pm = (mx - cx) * bb;
-        qm = (my - cy) * e;
+        pm = (mx - s_c[ch][0]) * bb;
+        qm = (my - s_c[ch][1]) * e;
       }
-      sm[0][i / kSsimS][i % kSsimS] = a;
-      sm[1][i / kSsimS][i % kSsimS] = bb;
-      sm[2][i / kSsimS][i % kSsimS] = e;
-      sm[3][i / kSsimS][i % kSsimS] = pm;
-      sm[4][i / kSsimS][i % kSsimS] = qm;
+      sm[ch][0][i / kSsimS][i % kSsimS] = a;
+      sm[ch][1][i / kSsimS][i % kSsimS] = bb;
+      sm[ch][2][i / kSsimS][i % kSsimS] = e;
+      sm[ch][3][i / kSsimS][i % kSsimS] = pm;
+      sm[ch][4][i / kSsimS][i % kSsimS] = qm;
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < kHN; t += kSsimThreads) {
-      const int r = t / kSsimB, x = t % kSsimB;
-      float h[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < kHItems; it += kSsimThreads) {
+    const int g = it % (kSsimB / kRun), r = (it / (kSsimB / kRun)) % kSsimS;
+    const int ch = it / (kSsimS * (kSsimB / kRun));
+    const int x0 = g * kRun;
 #pragma unroll
-      for (int i = 0; i < 2 * kSsimR + 1; ++i) {
-        const float w = sv.win[i];
+    for (int k = 0; k < 5; ++k) {
+      float row[kSpan];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) h[k] = __fmaf_rn(w, sm[k][r][x + i], h[k]);
+      for (int j = 0; j < kSpan; ++j) row[j] = sm[ch][k][r][x0 + j];
+      float h[kRun];
+#pragma unroll
+      for (int o = 0; o < kRun; ++o) {
+        float t = 0.f;
+#pragma unroll
+        for (int i = 0; i < 2 * kSsimR + 1; ++i) t = __fmaf_rn(sv.win[i], row[o + i], t);
+        h[o] = t;
       }
-#pragma unroll
-      for (int k = 0; k < 5; ++k) sh[k][t] = h[k];
+      *reinterpret_cast<float4*>(&sh[ch][k][r][x0]) = make_float4(h[0], h[1], h[2], h[3]);
     }
-    __syncthreads();
-    if (mine) {
-      float g[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  }
+  __syncthreads();
+  if (threadIdx.x < kVItems) {
+    const int c = threadIdx.x % kSsimB, q = (threadIdx.x / kSsimB) % (kSsimB / kRun);
+    const int ch = threadIdx.x / (kSsimB * (kSsimB / kRun));
+    const int y0 = q * kRun;
+    float gsum[5][kRun];
 #pragma unroll
-      for (int j = 0; j < 2 * kSsimR + 1; ++j) {
-        const float w = sv.win[j];
-        const int t = (ly + j) * kSsimB + lx;
+    for (int k = 0; k < 5; ++k) {
+      float col[kSpan];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) g[k] = __fmaf_rn(w, sh[k][t], g[k]);
+      for (int j = 0; j < kSpan; ++j) col[j] = sh[ch][k][y0 + j][c];
+#pragma unroll
+      for (int o = 0; o < kRun; ++o) {
+        float t = 0.f;
+#pragma unroll
+        for (int j = 0; j < 2 * kSsimR + 1; ++j) t = __fmaf_rn(sv.win[j], col[o + j], t);
+        gsum[k][o] = t;
       }
-      const float xp = image[3 * p + ch], yp = target[3 * p + ch];
-      const float grad = g[0] + 2.f * ((xp - cx) * g[1] - g[3]) + (yp - cy) * g[2] - g[4];
-      dimg[3 * p + ch] -= sv.scale[v] * grad;
+    }
+    const float cx = s_c[ch][0], cy = s_c[ch][1];
+    const int px = bx + c;
+#pragma unroll
+    for (int o = 0; o < kRun; ++o) {
+      const int py = by + y0 + o;
+      if (px < W && py < H) {
+        const long long p = base + (long long)py * W + px;
+        const float xp = image[3 * p + ch], yp = target[3 * p + ch];
+        const float grad = gsum[0][o] + 2.f * ((xp - cx) * gsum[1][o] - gsum[3][o]) +
+                           (yp - cy) * gsum[2][o] - gsum[4][o];
+        dimg[3 * p + ch] -= sv.scale[v] * grad;
+      }
     }
   }
 }
