@@ -24,9 +24,11 @@
 // with ties by Gaussian id.
 //
 // All kernels read their element counts from device memory and use grids
-// sized from host-known upper bounds, so the whole sequence can be captured
-// in a CUDA graph (no host synchronisation needed).  None of them waits on
-// another block.
+// sized from host-known upper bounds (blocks beyond the actual counts leave
+// at once), so the whole sequence can be captured in a CUDA graph (no host
+// synchronisation needed).  None of them waits on another block: where a
+// single-block scan follows a kernel, the kernel's last block to finish runs
+// it (each block counts its arrival after a __threadfence).
 #include <algorithm>
 #include <mutex>
 

@@ -4,17 +4,18 @@
 // quaternion and s = exp(log_scale); EWA splatting Sigma' = J W Sigma W^T J^T
 // + dilation I with the perspective Jacobian J at the camera-space mean; the
 // conic Sigma'^-1; opacity sigmoid(logit); real SH colour up to degree 3,
-// + 0.5, clamped at 0; the 3-sigma radius and the 16x16 tile rect.
+// + 0.5, clamped at 0; the 3-sigma radius and the rect of tiles (side 16 or
+// 8) it meets.
 //
 // One thread per Gaussian loops over the views, so the view-independent
 // part (activations, Sigma) is computed once.  Parameter loads are
 // coalesced across the warp; quaternions and SH rows use 16-byte loads.
 //
-// Backward: hand-derived adjoint of the same steps, one thread per
-// Gaussian, summing over views; the covariance part runs through the
-// Cholesky factor of the 2D covariance (whitened form) and accumulates the
-// log-scale and rotation-matrix gradients over views, pushed to the
-// quaternion once.
+// Backward: hand-derived adjoint of the same steps, one thread per Gaussian
+// that some view sees (a list built beside the blending adjoint), summing
+// over views; the covariance part runs through the Cholesky factor of the
+// 2D covariance (whitened form) and accumulates the log-scale and
+// rotation-matrix gradients over views, pushed to the quaternion once.
 #include <algorithm>
 
 #include "gs_internal.cuh"
