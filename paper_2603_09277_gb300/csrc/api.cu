@@ -201,30 +201,83 @@ struct LossViews {
   float w[GS_MAX_VIEWS];      // 1 / (M_v V)
 };
 
+// One pixel of the L1 + entropy loss: writes dL/dC (3 floats) and dL/dH,
+// returns the pixel's term (1/(M_v V)) ((1 - lambda) |r|_1 / 3 + gamma H).
+__device__ __forceinline__ float loss_pixel(const LossViews& lv, int v, float gamma,
+                                            float l1_weight, const float c[3], const float t[3],
+                                            float h, float g[3], float& gh) {
+  float l1 = 0.f;
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    const float r = c[ch] - t[ch];
+    l1 += fabsf(r);
+    g[ch] = r > 0.f ? lv.g_img[v] : (r < 0.f ? -lv.g_img[v] : 0.f);
+  }
+  gh = lv.g_ent[v];
+  return lv.w[v] * __fmaf_rn(l1_weight * (1.f / 3.f), l1, gamma * h);
+}
+
+__device__ __forceinline__ int view_of_pixel(const LossViews& lv, long long i) {
+  int v = 0;
+  while (v + 1 < lv.V && i >= lv.pix_off[v + 1]) ++v;
+  return v;
+}
+
+// Every term is >= 0: a thread's few terms and the warp's 32 partials are
+// summed in FP32 (relative error below 1e-6), the warps and blocks in FP64.
+// (FP64 arithmetic runs at a small fraction of the FP32 rate here.)  With
+// vec (every array 16-byte aligned) a thread takes 4 pixels at a time with
+// 16-byte loads and stores; the last P mod 4 pixels go through block 0.
 __global__ void __launch_bounds__(kLossThreads) loss_kernel(
     const float* __restrict__ image, const float* __restrict__ target,
     const float* __restrict__ entropy, const LossViews lv, long long P, float gamma,
     float l1_weight, float* __restrict__ dimg, float* __restrict__ dent,
-    double* __restrict__ partials) {
-  // Every term is >= 0: a thread's few terms and the warp's 32 partials are
-  // summed in FP32 (relative error below 1e-6), the warps and blocks in FP64.
-  // (FP64 arithmetic runs at a small fraction of the FP32 rate here.)
+    double* __restrict__ partials, int vec) {
   float acc = 0.f;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
-       i += (long long)gridDim.x * blockDim.x) {
-    int v = 0;
-    while (v + 1 < lv.V && i >= lv.pix_off[v + 1]) ++v;
-    float l1 = 0.f;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long done = 0;
+  if (vec) {
+    const long long Q4 = P / 4;
+    for (long long k = t0; k < Q4; k += stride) {
+      const float4* ci = reinterpret_cast<const float4*>(image) + 3 * k;
+      const float4* ti = reinterpret_cast<const float4*>(target) + 3 * k;
+      const float4 c0 = ci[0], c1 = ci[1], c2 = ci[2];
+      const float4 u0 = ti[0], u1 = ti[1], u2 = ti[2];
+      const float4 hh = entropy ? reinterpret_cast<const float4*>(entropy)[k]
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float cc[12] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z, c2.w};
+      const float tt[12] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w, u2.x, u2.y, u2.z, u2.w};
+      const float hv[4] = {hh.x, hh.y, hh.z, hh.w};
+      float gg[12], gh[4];
+      const int v0 = view_of_pixel(lv, 4 * k);
+      const bool one_view = v0 + 1 >= lv.V || 4 * k + 3 < lv.pix_off[v0 + 1];
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      const float r = image[3 * i + ch] - target[3 * i + ch];
-      l1 += fabsf(r);
-      dimg[3 * i + ch] = r > 0.f ? lv.g_img[v] : (r < 0.f ? -lv.g_img[v] : 0.f);
+      for (int j = 0; j < 4; ++j) {
+        const int v = one_view ? v0 : view_of_pixel(lv, 4 * k + j);
+        acc += loss_pixel(lv, v, gamma, l1_weight, cc + 3 * j, tt + 3 * j, hv[j], gg + 3 * j, gh[j]);
+      }
+      float4* gi = reinterpret_cast<float4*>(dimg) + 3 * k;
+      gi[0] = make_float4(gg[0], gg[1], gg[2], gg[3]);
+      gi[1] = make_float4(gg[4], gg[5], gg[6], gg[7]);
+      gi[2] = make_float4(gg[8], gg[9], gg[10], gg[11]);
+      if (dent) reinterpret_cast<float4*>(dent)[k] = make_float4(gh[0], gh[1], gh[2], gh[3]);
     }
-    const float h = entropy ? entropy[i] : 0.f;
-    if (dent) dent[i] = lv.g_ent[v];
-    // per pixel: (1/(M_v V)) ((1 - lambda) |r|_1 / 3 + gamma H)
-    acc = __fmaf_rn(lv.w[v], __fmaf_rn(l1_weight * (1.f / 3.f), l1, gamma * h), acc);
+    done = 4 * Q4;
+  }
+  // scalar pixels: all of them without vec, else the last P mod 4 (block 0)
+  const long long s0 = vec ? (blockIdx.x == 0 ? done + threadIdx.x : P) : t0;
+  const long long sstep = vec ? (long long)blockDim.x : stride;
+  for (long long i = s0; i < P; i += sstep) {
+    const int v = view_of_pixel(lv, i);
+    const float c[3] = {image[3 * i], image[3 * i + 1], image[3 * i + 2]};
+    const float t[3] = {target[3 * i], target[3 * i + 1], target[3 * i + 2]};
+    float g[3], gh;
+    acc += loss_pixel(lv, v, gamma, l1_weight, c, t, entropy ? entropy[i] : 0.f, g, gh);
+    dimg[3 * i] = g[0];
+    dimg[3 * i + 1] = g[1];
+    dimg[3 * i + 2] = g[2];
+    if (dent) dent[i] = gh;
   }
   __shared__ double s[kLossThreads / 32];
 #pragma unroll
@@ -419,9 +472,12 @@ int loss_impl(const float* image, const float* target, const float* entropy, con
     lv.g_img[v] = (float)((1.0 - (double)lambda) / (3.0 * M * V));
     lv.g_ent[v] = (float)((double)gamma / (M * V));
   }
+  const int vec = aligned(image, 16) && aligned(target, 16) && aligned(dL_dimage, 16) &&
+                  (gamma == 0.f || !entropy || aligned(entropy, 16)) &&
+                  (!dL_dentropy || aligned(dL_dentropy, 16));
   loss_kernel<<<nb, kLossThreads, 0, st>>>(image, target, gamma != 0.f ? entropy : nullptr, lv, P,
                                            gamma, (float)(1.0 - (double)lambda), dL_dimage, dL_dentropy,
-                                           partials);
+                                           partials, vec);
   count_launches(1);
   if (lambda > 0.f) {
     uintptr_t m = reinterpret_cast<uintptr_t>(partials + nb + ns);

@@ -192,6 +192,25 @@ def test_loss_kernel_parity():
     assert np.abs(rast.dL_dimage.cpu().numpy() - np.concatenate(dCs)).max() < 1e-12 + 1e-6 * np.abs(
         np.concatenate(dCs)).max()
     assert np.allclose(rast.dL_dentropy.cpu().numpy(), np.concatenate(dHs), rtol=1e-6)
+    # the same call on buffers that start 4 bytes past a 16-byte boundary
+    # (the kernel's scalar form): the same loss and gradients
+    from paper_2603_09277_gb300 import gs
+    Pn = rast.image.shape[0]
+    img_u = torch.empty(3 * Pn + 1, device="cuda")[1:]
+    img_u.copy_(rast.image.reshape(-1))
+    tgt_u = torch.empty(3 * Pn + 1, device="cuda")[1:]
+    tgt_u.copy_(targets_to_device(tg).reshape(-1))
+    ent_u = torch.empty(Pn + 1, device="cuda")[1:]
+    ent_u.copy_(rast.entropy)
+    dimg_u = torch.empty(3 * Pn + 1, device="cuda")[1:]
+    dent_u = torch.empty(Pn + 1, device="cuda")[1:]
+    loss_u = torch.zeros(1, dtype=torch.float64, device="cuda")
+    gs.gs_loss_l1_entropy(img_u, tgt_u, ent_u, rast.cams_c, 0.015, loss_u, dimg_u, dent_u,
+                          rast.loss_ws)
+    torch.cuda.synchronize()
+    assert loss_u.item() == pytest.approx(L, rel=1e-6)
+    assert torch.equal(dimg_u.reshape(-1, 3).cpu(), rast.dL_dimage.cpu())
+    assert torch.equal(dent_u.cpu(), rast.dL_dentropy.cpu())
 
 
 @pytest.mark.parametrize("seed", [0, 1])
