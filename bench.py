@@ -243,9 +243,9 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def traffic_from_profiles(kernel):
+def traffic_from_profiles(kernel, config):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was captured from the current render source."""
+    was captured on this workload from the current render source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -256,7 +256,7 @@ def traffic_from_profiles(kernel):
     src = os.path.join(ROOT, "paper_2603_09277_gb300", "csrc", "render.cu")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     ent = data.get(kernel)
-    if not ent or ent.get("render_cu_sha256_16") != h:
+    if not ent or ent.get("render_cu_sha256_16") != h or ent.get("config") != config:
         return None
     return ent.get("bytes_per_launch")
 
@@ -689,7 +689,8 @@ def main():
     achieved = flops / (kms / 1000.0) / 1e12
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic_from_profiles(kname),
+                "traffic": (traffic_from_profiles(kname, args.config)
+                            if not args.n and args.tile == 16 and args.attr == "f32" else None),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "flops_per_launch": flops}
 

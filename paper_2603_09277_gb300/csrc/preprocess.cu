@@ -671,15 +671,18 @@ __device__ __forceinline__ void adjoint_one(
 // The adjoint runs over a list of the Gaussians some view sees, kept in the
 // pad floats of grad2d (the blending adjoint writes floats 0..8 of a row):
 // entry k is float 9 of row k and the count is float 11 of row 0, all as
-// unsigned; grad2d is zeroed before.  A warp ranks its visible lanes by a
-// ballot and reserves their slots with one atomic, so the list is in no
-// particular order (each entry is independent).  A Gaussian's views are
-// tested in order up to the first that sees it.
+// unsigned; grad2d is zeroed before.  A CTA ranks its visible threads by
+// warp ballots and reserves their slots with one atomic (one per CTA keeps
+// the shared counter from serialising), so the list is in no particular
+// order (each entry is independent).  A Gaussian's views are tested in order
+// up to the first that sees it.
 constexpr int kListThreads = 256;
 __global__ void __launch_bounds__(kListThreads) adjoint_list_kernel(
     const unsigned* __restrict__ tiles_touched, int N, int V, float* __restrict__ grad2d) {
+  __shared__ unsigned s_cnt[kListThreads / 32];
+  __shared__ unsigned s_base;
   unsigned* g2 = reinterpret_cast<unsigned*>(grad2d);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (long long base = (long long)blockIdx.x * kListThreads; base < N;
        base += (long long)gridDim.x * kListThreads) {
     const long long g = base + threadIdx.x;
@@ -687,10 +690,20 @@ __global__ void __launch_bounds__(kListThreads) adjoint_list_kernel(
     if (g < N)
       for (int v = 0; v < V && !vis; ++v) vis = tiles_touched[(long long)v * N + g] != 0u;
     const unsigned b = __ballot_sync(0xffffffffu, vis);
-    unsigned slot = 0u;
-    if (lane == 0 && b) slot = atomicAdd(g2 + 11, (unsigned)__popc(b));
-    slot = __shfl_sync(0xffffffffu, slot, 0);
-    if (vis) g2[12ll * (slot + __popc(b & ((1u << lane) - 1u))) + 9] = (unsigned)g;
+    if (lane == 0) s_cnt[w] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned run = 0u;
+      for (int k = 0; k < kListThreads / 32; ++k) {
+        const unsigned c = s_cnt[k];
+        s_cnt[k] = run;
+        run += c;
+      }
+      s_base = run ? atomicAdd(g2 + 11, run) : 0u;
+    }
+    __syncthreads();
+    if (vis) g2[12ll * (s_base + s_cnt[w] + __popc(b & ((1u << lane) - 1u))) + 9] = (unsigned)g;
+    __syncthreads();  // s_cnt and s_base are rewritten by the next round
   }
 }
 
