@@ -707,15 +707,28 @@ def main():
         host_tgt = torch.cat([torch.as_tensor(t).reshape(-1, 3) for t in targets]).pin_memory()
         out_loss = torch.empty(1, dtype=torch.float64).pin_memory()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # the parameter upload runs on three copy streams (the SH block in two
+        # halves, the rest), joined before the step
+        copy_streams = [torch.cuda.Stream(device=dev) for _ in range(3)]
+        nh = host["sh"].shape[0] // 2
+        copy_plan = [[(p["sh"][:nh], host["sh"][:nh])], [(p["sh"][nh:], host["sh"][nh:])],
+                     [(p[kk], host[kk]) for kk in ("means", "log_scales", "quats",
+                                                    "opacity_logits")]]
 
         def run_e2e(upload_params):
             ms = []
+            cur = torch.cuda.current_stream()
             for k in range(K + 1):
                 flush.fill_(float(k))
                 a.record()
                 if upload_params:
-                    for kk, v in host.items():
-                        p[kk].copy_(v, non_blocking=True)
+                    for cs, plan in zip(copy_streams, copy_plan):
+                        cs.wait_stream(cur)
+                        with torch.cuda.stream(cs):
+                            for dst, src in plan:
+                                dst.copy_(src, non_blocking=True)
+                    for cs in copy_streams:
+                        cur.wait_stream(cs)
                 tgt.copy_(host_tgt, non_blocking=True)
                 r.preprocess(p)
                 r.bin_sort(sync=False)
