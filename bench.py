@@ -44,10 +44,11 @@ L2_BYTES = 129 * 1024 * 1024
 #   forward:  10 per evaluated pair (pixel offset 2, base-2 exponent 8)
 #             +14 per blended pair (exp, clamp, 1-alpha, T(1-alpha), w,
 #                 colour 3 FMA, log, entropy FMA)
-#   backward: 10 per evaluated pair, +72 per blended pair (transmittance
+#   backward: 10 per evaluated pair, +56 per blended pair (transmittance
 #             recovery 8, colour part of dL/dalpha 14, entropy part 7, colour
-#             gradient 3, S and R updates 9, alpha->sigma,d 2, conic 12,
-#             mean 8, per-pixel summation of the 9 gradients 9)
+#             gradient 3, S and R updates 9, dd and the six moments
+#             dd (1, dx, dy, dx^2, dx dy, dy^2) summed 12, colour sums 3; the
+#             conic, 1/sigma and the signs are applied once per Gaussian)
 FWD_EVAL, FWD_BLEND = 10, 14
 BWD_EVAL, BWD_BLEND = 10, 56
 
@@ -518,6 +519,44 @@ def time_variant(make, p, tgt, gamma, flush, steps, warmup=2):
     return out
 
 
+def measured_hbm_peak():
+    """(GB/s, source) of the measured STREAM-style copy on the GB300s,
+    else the stated fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def phase_graph_ms(fns, flush, reps=20):
+    """Median time of each phase replayed alone from its own CUDA graph (L2
+    flushed before every replay): without the eager launch gaps."""
+    import torch
+    out = {}
+    s = torch.cuda.Stream()
+    for name, fn in fns.items():
+        g = torch.cuda.CUDAGraph()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            fn()
+            with torch.cuda.graph(g, stream=s):
+                fn()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for k in range(reps):
+            flush.fill_(float(k))
+            a.record()
+            g.replay()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        out[name] = float(np.median(ts))
+    return out
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -694,6 +733,48 @@ def main():
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "flops_per_launch": flops}
 
+    # per-phase times replayed alone from graphs, and the rooflines of the
+    # phases other than the dominant kernel: HBM phases against the measured
+    # copy bandwidth with their minimal algorithmic bytes (what the step must
+    # move: the projection reads every Gaussian's geometry, the SH in use of
+    # the visible rows, writes depth, rect and count of every row and the
+    # record of every visible row; the lists read those per-row outputs and
+    # write the pair values and ranges; the loss reads colour, target and
+    # entropy and writes both gradients), the forward blending against the
+    # FP32 peak with its FLOP model
+    pg = phase_graph_ms({
+        "preprocess": lambda: r.preprocess(p),
+        "bin_sort": lambda: r.bin_sort(sync=False),
+        "render_fwd": lambda: r.render_fwd(),
+        "loss": lambda: r.loss(tgt, gamma, lam=args.dssim),
+        "render_bwd+preprocess_bwd": lambda: r.render_bwd(p),
+    }, flush)
+    hbm, hbm_src = measured_hbm_peak()
+    vis_rows = (r.tiles_touched[:r.rows] > 0)
+    n_rows_vis = int(vis_rows.sum().item())
+    n_gauss_vis = int(vis_rows.view(r.V, r.N).any(0).sum().item())
+    Kc = (int(prm.get("sh_degree", 0)) + 1) ** 2
+    n_g = int(scene["means"].shape[0])
+    n_pix = int(r.image.shape[0])
+    bytes_pre = (n_g * 44 + n_gauss_vis * 12 * Kc + r.rows * 24 +
+                 n_rows_vis * gs.gs_record_bytes(r.prm_c.attr_dtype))
+    bytes_bin = r.rows * 24 + P * 4 + r.total_tiles * 8
+    bytes_loss = n_pix * 44
+
+    def hbm_line(nbytes, ms_):
+        gbs = nbytes / (ms_ / 1000.0) / 1e9
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                "frac": gbs / hbm, "peak_source": hbm_src, "bytes": int(nbytes), "ms": ms_}
+
+    fwd_tf = (FWD_EVAL * ne_step + FWD_BLEND * nb_step) / (pg["render_fwd"] / 1000.0) / 1e12
+    phase_roofline = {
+        "preprocess": hbm_line(bytes_pre, pg["preprocess"]),
+        "bin_sort": hbm_line(bytes_bin, pg["bin_sort"]),
+        "render_fwd": {"bound": "alu", "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s",
+                       "frac": fwd_tf / peak, "ms": pg["render_fwd"]},
+        "loss": hbm_line(bytes_loss, pg["loss"]) if args.dssim == 0 else None,
+    }
+
     # end to end through the C ABI with host buffers.  Per step the step's
     # inputs, the target images of its views, come in from pinned host
     # memory and the loss goes out; the Gaussian parameters are model state
@@ -813,6 +894,8 @@ def main():
                        "kernels_per_step": kernels_per_step,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "phases_ms": phase,
+            "phases_graph_ms": pg,
+            "phase_roofline": phase_roofline,
             "variants": variants,
             "roofline": roofline,
             "cpu_baseline": cpu,
