@@ -78,6 +78,8 @@ def parse():
                          "stated loss; 3DGS uses 0.2)")
     ap.add_argument("--tile", type=int, default=16, choices=[16, 8],
                     help="tile side in pixels (16: 3DGS; 8: LiteGS and the paper's runs)")
+    ap.add_argument("--no-phase-graphs", action="store_true",
+                    help="skip the per-phase graph replays (launch-list captures)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use --ppt/--persistent as given instead of the autotuned launch form")
     ap.add_argument("--sweep", action="store_true",
@@ -742,7 +744,7 @@ def main():
     # write the pair values and ranges; the loss reads colour, target and
     # entropy and writes both gradients), the forward blending against the
     # FP32 peak with its FLOP model
-    pg = phase_graph_ms({
+    pg = {} if args.no_phase_graphs else phase_graph_ms({
         "preprocess": lambda: r.preprocess(p),
         "bin_sort": lambda: r.bin_sort(sync=False),
         "render_fwd": lambda: r.render_fwd(),
@@ -750,6 +752,10 @@ def main():
         "render_bwd+preprocess_bwd": lambda: r.render_bwd(p),
     }, flush)
     hbm, hbm_src = measured_hbm_peak()
+    if not pg:  # fall back on the eager phase events
+        pg = {"preprocess": phase["preprocess"], "bin_sort": phase["bin_sort"],
+              "render_fwd": phase["render_fwd_kernel"],
+              "loss": phase["render_fwd+loss"] - phase["render_fwd_kernel"]}
     vis_rows = (r.tiles_touched[:r.rows] > 0)
     n_rows_vis = int(vis_rows.sum().item())
     n_gauss_vis = int(vis_rows.view(r.V, r.N).any(0).sum().item())
