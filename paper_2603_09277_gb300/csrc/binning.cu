@@ -304,25 +304,31 @@ __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
     return;
   }
   unsigned long long q = 0, pp = 0;
-  // all row ids, then all rect gathers in flight before any use
-  unsigned row[kScanItems];
+  // groups of kGather rows: their ids, then their rect gathers in flight
+  // before any use (more per group would cost occupancy on large inputs)
+  constexpr int kGather = 4;
+  static_assert(kScanItems % kGather == 0, "whole groups");
+#pragma unroll 1
+  for (int k0 = 0; k0 < kScanItems; k0 += kGather) {
+    unsigned row[kGather];
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    const long long i = base + (long long)k * kScanThreads + threadIdx.x;
-    row[k] = i < n ? rows[i] : 0xffffffffu;
-  }
-  int4 rr[kScanItems];
+    for (int k = 0; k < kGather; ++k) {
+      const long long i = base + (long long)(k0 + k) * kScanThreads + threadIdx.x;
+      row[k] = i < n ? rows[i] : 0xffffffffu;
+    }
+    int4 rr[kGather];
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k)
-    rr[k] = row[k] != 0xffffffffu ? view_rect(rect, row[k], N, ct) : make_int4(0, 0, 0, 0);
+    for (int k = 0; k < kGather; ++k)
+      rr[k] = row[k] != 0xffffffffu ? view_rect(rect, row[k], N, ct) : make_int4(0, 0, 0, 0);
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    const long long i = base + (long long)k * kScanThreads + threadIdx.x;
-    if (i < n) {
-      const int4 r = rr[k];
-      rect_sorted[i] = r;
-      q += st_count(r);
-      pp += (unsigned long long)((r.z - r.x) * (r.w - r.y));
+    for (int k = 0; k < kGather; ++k) {
+      const long long i = base + (long long)(k0 + k) * kScanThreads + threadIdx.x;
+      if (i < n) {
+        const int4 r = rr[k];
+        rect_sorted[i] = r;
+        q += st_count(r);
+        pp += (unsigned long long)((r.z - r.x) * (r.w - r.y));
+      }
     }
   }
   unsigned long long tq, tp;
