@@ -1121,19 +1121,18 @@ __global__ void __launch_bounds__(256) st_emit_kernel(
         s_run[tid] = run;
       }
       __syncthreads();
-      const unsigned x0 = d & 15u, x1 = (d >> 4) & 15u;
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         if (B[r] == 0u) continue;  // warp-uniform
         const uint4 pa = *reinterpret_cast<const uint4*>(&s_pos[w][8 * r]);
         const uint4 pb = *reinterpret_cast<const uint4*>(&s_pos[w][8 * r + 4]);
         const unsigned sp[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
-        const bool in_row = (B[r] >> lane) & 1u;
 #pragma unroll
         for (unsigned c = 0; c < 8; ++c) {
+          // the lanes whose rows cover tile (r, c), this lane among them
           const unsigned bal = B[r] & X[c];
           if (bal == 0u) continue;  // warp-uniform
-          if (in_row && x0 <= c && c < x1) {
+          if ((bal >> lane) & 1u) {
             const unsigned pos = sp[c] + __popc(bal & lt);
             out_vals[pos] = row;
             if (out_keys)
