@@ -252,7 +252,15 @@ int gs_loss_base(const float* image, const float* target, const float* entropy,
  *   Gaussians some view sees, for the projection adjoint).  From these,
  *   dL/dsigma = dd-sum / sigma, dL/dconic = -(1/2) sum dd d d^T and
  *   dL/dmean2d = conic (dd dx-sum, dd dy-sum).
- *   g_* : device, shapes of the parameters, overwritten. */
+ *   g_* : device, shapes of the parameters, overwritten.
+ * Part of the work (the zeroing of g_*, the list of Gaussians some view sees)
+ * runs on a second stream of the library's own, forked from `stream` by an
+ * event and joined back before the projection adjoint, so every result is
+ * ordered on `stream` as usual and a stream capture records that work as a
+ * parallel branch; the second stream is created by the first call on a
+ * device made outside a stream capture (until then the call uses `stream`
+ * alone).  Calls from several host threads are serialised while they
+ * enqueue. */
 int gs_render_bwd(const gs_proj* proj, int N, const gs_camera* cams_host, int V,
                   const gs_params* prm, const unsigned* sorted_vals, const unsigned* tile_ranges,
                   const float* final_T, const unsigned* last_idx, const float* dL_dimage,
