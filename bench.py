@@ -521,6 +521,21 @@ def time_variant(make, p, tgt, gamma, flush, steps, warmup=2):
     return out
 
 
+def rank_totals(t_local, units_local, world, dev):
+    """Whole-job figures of a replicated run: the time is the slowest rank's
+    (max over ranks) and the work the sum over ranks; with one rank, the
+    local values.  Returns (seconds, units)."""
+    if world <= 1:
+        return float(t_local), float(units_local)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_local)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units_local)], device=dev, dtype=torch.float64)
+    dist.all_reduce(u)
+    return float(t.item()), float(u.item())
+
+
 def measured_hbm_peak():
     """(GB/s, source) of the measured STREAM-style copy on the GB300s,
     else the stated fallback."""
@@ -705,16 +720,7 @@ def main():
     if status != 0:
         raise RuntimeError("pair capacity overflow in the timed region (status %d)" % status)
     step_ms = [a.elapsed_time(b) for a, b in gev]
-    t_total = sum(step_ms) / 1000.0
-    if world > 1:
-        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
-        nbt = torch.tensor([nb_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(nbt)
-        nb_all = float(nbt.item())
-    else:
-        nb_all = float(nb_step)
+    t_total, nb_all = rank_totals(sum(step_ms) / 1000.0, nb_step, world, dev)
     value = nb_all * K / t_total
     ms = 1000.0 * t_total / K
 
@@ -828,11 +834,7 @@ def main():
                 b.synchronize()
                 if k > 0:
                     ms.append(a.elapsed_time(b))
-            t = sum(ms) / 1000.0
-            if world > 1:
-                tt = torch.tensor([t], device=dev, dtype=torch.float64)
-                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-                t = float(tt.item())
+            t, _ = rank_totals(sum(ms) / 1000.0, 0, world, dev)
             h2d = host_tgt.numel() * 4 + (sum(v.numel() * 4 for v in host.values())
                                           if upload_params else 0)
             return {"value": nb_all * K / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
