@@ -380,6 +380,31 @@ def test_nan_parameters_are_culled():
     assert np.isfinite(g["image"]).all()
 
 
+def test_degenerate_covariances():
+    """Point-like Gaussians (scales ~1e-9: the 2D covariance is the dilation
+    alone), needles and discs (axis ratios ~e^10) and zero quaternions (no
+    rotation: culled on both sides) in one scene: every output against the
+    oracle with the usual bars."""
+    cams = [scenes.camera(96, 72, 96.0)]
+    prm = scenes.params()
+    scene = scenes.box_scene(400, seed=11)
+    scene["log_scales"][:40] = -20.0
+    scene["log_scales"][40:60] = np.array([1.0, -9.0, -9.0], np.float32)
+    scene["log_scales"][60:80] = np.array([-9.0, -0.5, -0.5], np.float32)
+    scene["quats"][80:85] = 0.0
+    targets = scenes.noise_targets(cams, 12)
+    L, views, grads, g9 = _oracle_full(scene, cams, targets, prm)
+    g = run_gpu(scene, cams, prm, target=targets, dL_dimage=views[0]["dL_dC"],
+                dL_dentropy=views[0]["dL_dH"])
+    N = scene["means"].shape[0]
+    assert (g["tiles"][80:85] == 0).all()
+    assert (g["tiles"][:40] > 0).sum() > 20  # point-like Gaussians are drawn (dilation)
+    check_projection(g, views, cams, N)
+    check_lists(g, views, cams, N)
+    check_pixels(g, views, cams, N)
+    check_grads(g, grads, views, cams, N, 1)
+
+
 def test_capacity_overflow_regrows():
     scene, cams, targets, prm = scenes.config1(n=2000)
     from paper_2603_09277_gb300.rasterize import Rasterizer, scene_to_device
