@@ -380,6 +380,25 @@ def test_nan_parameters_are_culled():
     assert np.isfinite(g["image"]).all()
 
 
+@pytest.mark.parametrize("k,om,with_grads", [(-2, 4.0, False), (4, -2.0, True)])
+def test_cfg4_list_length_points(k, om, with_grads):
+    """Two ends of the list-length sweep: large opaque Gaussians (lists of
+    ~1,400 per tile, early stops) and small transparent ones (short lists
+    walked to the end).  (With the large opaque ones most Gaussians touch a
+    pixel near a threshold, so the element-wise gradient bar's exclusions
+    leave too few to judge; projection, lists and pixels are checked.)"""
+    scene, cams, targets, prm = scenes.config4(k=k, opacity_mean=om)
+    L, views, grads, g9 = _oracle_full(scene, cams, targets, prm)
+    g = run_gpu(scene, cams, prm, target=targets, dL_dimage=views[0]["dL_dC"],
+                dL_dentropy=views[0]["dL_dH"])
+    N = scene["means"].shape[0]
+    check_projection(g, views, cams, N)
+    check_lists(g, views, cams, N)
+    check_pixels(g, views, cams, N)
+    if with_grads:
+        check_grads(g, grads, views, cams, N, 1)
+
+
 def test_degenerate_covariances():
     """Point-like Gaussians (scales ~1e-9: the 2D covariance is the dilation
     alone), needles and discs (axis ratios ~e^10) and zero quaternions (no
