@@ -784,7 +784,11 @@ def main():
         "bin_sort": hbm_line(bytes_bin, pg["bin_sort"]),
         "render_fwd": {"bound": "alu", "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s",
                        "frac": fwd_tf / peak, "ms": pg["render_fwd"]},
-        "loss": hbm_line(bytes_loss, pg["loss"]) if args.dssim == 0 else None,
+        # with D-SSIM: the L1/entropy pass, then the SSIM forward (colour and
+        # target in, five maps per channel out) and backward (maps, colour
+        # and target in, dL/dC read and written)
+        "loss": hbm_line(bytes_loss if args.dssim == 0 else n_pix * (44 + 84 + 120),
+                         pg["loss"]),
     }
 
     # end to end through the C ABI with host buffers.  Per step the step's
