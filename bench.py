@@ -787,7 +787,7 @@ def main():
         # with D-SSIM: the L1/entropy pass, then the SSIM forward (colour and
         # target in, five maps per channel out) and backward (maps, colour
         # and target in, dL/dC read and written)
-        "loss": hbm_line(bytes_loss if args.dssim == 0 else n_pix * (44 + 84 + 120),
+        "loss": hbm_line(bytes_loss if args.dssim == 0 else n_pix * (44 + 84 + 108),
                          pg["loss"]),
     }
 
