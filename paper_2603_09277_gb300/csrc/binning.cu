@@ -40,8 +40,8 @@ namespace gs {
 namespace {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 16;                       // per thread
-constexpr int kScanTile = kScanThreads * kScanItems; // 4096 items per block
+constexpr int kScanItems = 4;                        // per thread
+constexpr int kScanTile = kScanThreads * kScanItems; // 1024 items per block
 
 // ----------------------------------------------------------------------------
 // Block-wide exclusive scan helpers (256 threads).
@@ -216,12 +216,15 @@ __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
     if (lane == 0) s_off[k * kScanWarps + w] = __popc(ball[k]);
   }
   __syncthreads();
-  if (w == 0) {  // exclusive scan of the (k, warp) counts, 4 per lane
-    static_assert(kScanItems * kScanWarps == 4 * 32, "one warp scans the counts");
-    unsigned c[4], run = 0;
+  if (w == 0) {  // exclusive scan of the (k, warp) counts, kPerLane per lane
+    constexpr int kCounts = kScanItems * kScanWarps;
+    constexpr int kPerLane = (kCounts + 31) / 32;
+    static_assert(kCounts % kPerLane == 0 && kCounts / kPerLane <= 32, "one warp scans the counts");
+    unsigned c[kPerLane], run = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      c[j] = s_off[4 * lane + j];
+    for (int j = 0; j < kPerLane; ++j) {
+      const int e = kPerLane * lane + j;
+      c[j] = e < kCounts ? s_off[e] : 0u;
       run += c[j];
     }
     unsigned inc = run;
@@ -232,8 +235,9 @@ __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
     }
     unsigned ex = inc - run;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      s_off[4 * lane + j] = ex;
+    for (int j = 0; j < kPerLane; ++j) {
+      const int e = kPerLane * lane + j;
+      if (e < kCounts) s_off[e] = ex;
       ex += c[j];
     }
   }
