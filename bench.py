@@ -1,9 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the differentiable tile rasterizer with the entropy term:
-one step = projection, per-tile list construction (key duplication and radix
-sort), front-to-back blending with the weight entropy, the L1 + entropy loss,
-the reverse-order adjoint back to every Gaussian parameter, and the scale
-reset, over one batch of synthetic inputs resident in HBM.
+one step = projection, per-tile list construction (depth sort of the visible
+rows, super-tile items, expansion into the tiles' lists), front-to-back
+blending with the weight entropy, the L1 + entropy loss, the reverse-order
+adjoint back to every Gaussian parameter, and the scale reset, over one batch
+of synthetic inputs resident in HBM.
+
+The JSON line carries, besides the contract's keys: the per-phase event times
+(eager) and graph replays, the roofline of the dominant kernel (FP32 FLOP
+model) and of the other phases (minimal algorithmic bytes against the
+measured HBM copy bandwidth), the FP64 oracle on the host cores as the CPU
+baseline, the end-to-end time through the C ABI (target images in, loss out;
+and the stricter form with every parameter uploaded), the library's own
+launch count and the SM clocks sampled during the timed region.  Other modes:
+--config cfg1..cfg5, --tile 8, --dssim LAMBDA, --attr f16|bf16, --sweep
+(list-length sweep), --train ITERS (training loop), --train-epochs E (epoch
+schedule with the resolution scheduler).
 
 Default workload (N=1): 1,000,000 Gaussians from 64 anisotropic clusters,
 SH degree 3, one 1237x822 view (the scene-scale configuration).
