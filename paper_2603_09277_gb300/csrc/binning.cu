@@ -40,8 +40,10 @@ namespace gs {
 namespace {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 4;                        // per thread
-constexpr int kScanTile = kScanThreads * kScanItems; // 1024 items per block
+// Scan blocks: ITEMS rows per thread (4 or 16, chosen from the row count at
+// launch); the workspace is sized for the smaller blocks (the most blocks).
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;  // 1024 rows per block
 
 // ----------------------------------------------------------------------------
 // Block-wide exclusive scan helpers (256 threads).
@@ -113,16 +115,17 @@ __device__ __forceinline__ long long scan_blocks_dev(unsigned long long* block_s
 
 // Phase 1: per-block sums; with `arrive`, the last CTA also scans them
 // (phase 2) and writes the grand total to *total.
+template <int ITEMS>
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(ScanSrc src, const long long* n_dev,
                                                                    long long n_host,
                                                                    unsigned long long* block_sums,
                                                                    unsigned long long* arrive,
                                                                    long long* total) {
   long long n = n_dev ? *n_dev : n_host;
-  long long base = (long long)blockIdx.x * kScanTile;
+  long long base = (long long)blockIdx.x * (kScanThreads * ITEMS);
   unsigned long long s = 0;
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
+  for (int k = 0; k < ITEMS; ++k) {
     long long i = base + (long long)k * kScanThreads + threadIdx.x;
     if (i < n) s += src.get(i);
   }
@@ -201,23 +204,24 @@ __device__ __forceinline__ void scan_counts_check_dev(const CountsOut& o, int nb
 // ballot, and the (k, warp) counts are scanned by one warp, so the output
 // order is the row order.
 constexpr int kScanWarps = kScanThreads / 32;
+template <int ITEMS>
 __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
     const unsigned* __restrict__ tiles_touched, const float* __restrict__ depth, long long n,
     const unsigned long long* __restrict__ block_offsets, unsigned* __restrict__ keys,
     unsigned* __restrict__ vals) {
-  __shared__ unsigned s_off[kScanItems * kScanWarps];
-  const long long base = (long long)blockIdx.x * kScanTile;
+  __shared__ unsigned s_off[ITEMS * kScanWarps];
+  const long long base = (long long)blockIdx.x * (kScanThreads * ITEMS);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned ball[kScanItems];
+  unsigned ball[ITEMS];
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
+  for (int k = 0; k < ITEMS; ++k) {
     const long long i = base + (long long)k * kScanThreads + threadIdx.x;
     ball[k] = __ballot_sync(0xffffffffu, i < n && tiles_touched[i] > 0u);
     if (lane == 0) s_off[k * kScanWarps + w] = __popc(ball[k]);
   }
   __syncthreads();
   if (w == 0) {  // exclusive scan of the (k, warp) counts, kPerLane per lane
-    constexpr int kCounts = kScanItems * kScanWarps;
+    constexpr int kCounts = ITEMS * kScanWarps;
     constexpr int kPerLane = (kCounts + 31) / 32;
     static_assert(kCounts % kPerLane == 0 && kCounts / kPerLane <= 32, "one warp scans the counts");
     unsigned c[kPerLane], run = 0;
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
   const unsigned long long boff = block_offsets[blockIdx.x];
   const unsigned below = (1u << lane) - 1u;
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
+  for (int k = 0; k < ITEMS; ++k) {
     if ((ball[k] >> lane) & 1u) {
       const long long i = base + (long long)k * kScanThreads + threadIdx.x;
       const unsigned long long off = boff + s_off[k * kScanWarps + w] + __popc(ball[k] & below);
@@ -291,6 +295,7 @@ __device__ __forceinline__ unsigned st_count(const int4 r) {
 // the pair counts.
 // The last CTA to finish scans both sums over the blocks and runs the
 // capacity check (scan_counts_check_dev).
+template <int ITEMS>
 __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
     const unsigned* __restrict__ rows, const long long* __restrict__ n_dev,
     const int* __restrict__ rect, int N, const CamTable ct, int4* __restrict__ rect_sorted,
@@ -298,7 +303,7 @@ __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
   unsigned long long* sums_q = co.sums_q;
   unsigned long long* sums_p = co.sums_p;
   const long long n = *n_dev;
-  const long long base = (long long)blockIdx.x * kScanTile;
+  const long long base = (long long)blockIdx.x * (kScanThreads * ITEMS);
   if (base >= n) {  // (the whole CTA) no rows: zero sums
     if (threadIdx.x == 0) {
       sums_q[blockIdx.x] = 0ull;
@@ -311,9 +316,9 @@ __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
   // groups of kGather rows: their ids, then their rect gathers in flight
   // before any use (more per group would cost occupancy on large inputs)
   constexpr int kGather = 4;
-  static_assert(kScanItems % kGather == 0, "whole groups");
+  static_assert(ITEMS % kGather == 0, "whole groups");
 #pragma unroll 1
-  for (int k0 = 0; k0 < kScanItems; k0 += kGather) {
+  for (int k0 = 0; k0 < ITEMS; k0 += kGather) {
     unsigned row[kGather];
 #pragma unroll
     for (int k = 0; k < kGather; ++k) {
@@ -349,25 +354,26 @@ __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
 // every block of kDupPairs items (b < n_marks) the row that owns its first
 // item (block_row[b]), for the load-balanced duplication.
 constexpr int kDupPairsScan = 1024;
+template <int ITEMS>
 __global__ void __launch_bounds__(kScanThreads) row_offsets_kernel(
     const int4* __restrict__ rect_sorted, const long long* __restrict__ n_dev,
     const unsigned long long* __restrict__ block_offsets, unsigned long long* __restrict__ out,
     unsigned* __restrict__ block_row, long long n_marks) {
   const long long n = *n_dev;
-  const long long base = (long long)blockIdx.x * kScanTile;
-  const long long first = base + (long long)threadIdx.x * kScanItems;
+  const long long base = (long long)blockIdx.x * (kScanThreads * ITEMS);
+  const long long first = base + (long long)threadIdx.x * ITEMS;
   if (base >= n) return;
   unsigned long long sum = 0;
-  unsigned loc[kScanItems];
+  unsigned loc[ITEMS];
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
+  for (int k = 0; k < ITEMS; ++k) {
     const long long i = first + k;
     loc[k] = i < n ? st_count(rect_sorted[i]) : 0u;
     sum += loc[k];
   }
   unsigned long long tot;
   unsigned long long off = block_excl_scan(sum, &tot) + block_offsets[blockIdx.x];
-  for (int k = 0; k < kScanItems; ++k) {
+  for (int k = 0; k < ITEMS; ++k) {
     const long long i = first + k;
     if (i < n) {
       out[i] = off;
@@ -1304,14 +1310,26 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
   const CountsOut co{w.block_sums, w.block_sums2, cap, Q, P, q_eff, p_eff, num_pairs_dev,
                      status_dev};
   unsigned* rows_sorted = w.rv[0];
-  const long long nb = scan_blocks(n_rows);
+  // scan blocks of 1,024 rows (4 per thread) keep many CTAs in flight when
+  // few rows are visible; on large row counts 4,096-row blocks (16 per
+  // thread) are faster
+  const bool small = n_rows <= (4ll << 20);
+  const int items = small ? 4 : 16;
+  const long long nb = (n_rows + kScanThreads * items - 1) / (kScanThreads * items);
   if (n_rows > 0) {
     // 1. compaction of the visible rows, keyed by FP32 depth bits
     ScanSrc vis{proj->tiles_touched, nullptr, 1};
-    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(vis, nullptr, n_rows, w.block_sums,
-                                                              arrive, n_vis);
-    compact_visible_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(
-        proj->tiles_touched, proj->depth, n_rows, w.block_sums, w.rk[0], w.rv[0]);
+    if (small) {
+      scan_reduce_kernel<4><<<(unsigned)nb, kScanThreads, 0, st>>>(vis, nullptr, n_rows,
+                                                                   w.block_sums, arrive, n_vis);
+      compact_visible_kernel<4><<<(unsigned)nb, kScanThreads, 0, st>>>(
+          proj->tiles_touched, proj->depth, n_rows, w.block_sums, w.rk[0], w.rv[0]);
+    } else {
+      scan_reduce_kernel<16><<<(unsigned)nb, kScanThreads, 0, st>>>(vis, nullptr, n_rows,
+                                                                    w.block_sums, arrive, n_vis);
+      compact_visible_kernel<16><<<(unsigned)nb, kScanThreads, 0, st>>>(
+          proj->tiles_touched, proj->depth, n_rows, w.block_sums, w.rk[0], w.rv[0]);
+    }
     // 2. stable depth sort of the visible rows (ties keep row order = id order)
     int res = radix_sort(w.rk, w.rv, n_vis, n_rows, 32, w.hist, st);
     rows_sorted = w.rv[res];
@@ -1319,8 +1337,12 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
     //    and the pair count P
     //    (its last CTA: the scans of Q and P over the blocks, the capacity
     //    check and the reported count)
-    rows_gather_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(
-        rows_sorted, n_vis, proj->rect, N, ct, w.rect_sorted, arrive + 1, co);
+    if (small)
+      rows_gather_kernel<4><<<(unsigned)nb, kScanThreads, 0, st>>>(
+          rows_sorted, n_vis, proj->rect, N, ct, w.rect_sorted, arrive + 1, co);
+    else
+      rows_gather_kernel<16><<<(unsigned)nb, kScanThreads, 0, st>>>(
+          rows_sorted, n_vis, proj->rect, N, ct, w.rect_sorted, arrive + 1, co);
     count_launches(3);
   } else {
     scan_counts_check_kernel<<<1, kScanThreads, 0, st>>>(co, 0);
@@ -1328,9 +1350,14 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
   }
   if (n_rows > 0) {
     // super-tile offsets per row, and the first row of every duplication block
-    row_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(
-        w.rect_sorted, n_vis, w.block_sums, w.offsets, w.block_row,
-        (cap + kDupPairs - 1) / kDupPairs + 1);
+    if (small)
+      row_offsets_kernel<4><<<(unsigned)nb, kScanThreads, 0, st>>>(
+          w.rect_sorted, n_vis, w.block_sums, w.offsets, w.block_row,
+          (cap + kDupPairs - 1) / kDupPairs + 1);
+    else
+      row_offsets_kernel<16><<<(unsigned)nb, kScanThreads, 0, st>>>(
+          w.rect_sorted, n_vis, w.block_sums, w.offsets, w.block_row,
+          (cap + kDupPairs - 1) / kDupPairs + 1);
     count_launches(1);
   }
   GS_TRY_CUDA(cudaGetLastError());
