@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the comparison of launch forms and staging precisions")
     ap.add_argument("--ppt", type=int, default=0, help="pixels per thread of the blending kernels")
+    ap.add_argument("--batch", type=int, default=0, choices=[0, 128, 256],
+                    help="list entries per shared-memory batch of the blending kernels (0 = 256)")
     ap.add_argument("--dssim", type=float, default=0.0,
                     help="lambda of the D-SSIM term of L_base (0: L1 + entropy, the workloads' "
                          "stated loss; 3DGS uses 0.2)")
@@ -93,7 +95,7 @@ def parse():
     ap.add_argument("--no-phase-graphs", action="store_true",
                     help="skip the per-phase graph replays (launch-list captures)")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="use --ppt/--persistent as given instead of the autotuned launch form")
+                    help="use --ppt/--batch/--persistent as given instead of the autotuned form")
     ap.add_argument("--sweep", action="store_true",
                     help="list-length sweep (cfg4): one JSON line per scale/opacity point")
     ap.add_argument("--train", type=int, default=0,
@@ -623,7 +625,7 @@ def main():
     N = scene["means"].shape[0]
     p = scene_to_device(scene, dev)
     tgt = targets_to_device(targets, dev)
-    form = {"pixels_per_thread": args.ppt, "persistent": args.persistent}
+    form = {"pixels_per_thread": args.ppt, "persistent": args.persistent, "batch": args.batch}
     tuned = None
     if not args.no_autotune:
         from paper_2603_09277_gb300 import autotune
@@ -869,8 +871,10 @@ def main():
         forms = [("plain_f32", dict()), ("persistent_f32", dict(persistent=152 * 8)),
                  ("plain_f16", dict(attr_dtype="f16")), ("plain_bf16", dict(attr_dtype="bf16")),
                  ("persistent_bf16", dict(persistent=152 * 8, attr_dtype="bf16")),
-                 ("plain_f32_1px", dict(pixels_per_thread=1)),
-                 ("plain_f32_4px", dict(pixels_per_thread=4))]
+                 ("plain_f32_1px", dict(pixels_per_thread=1))]
+        if args.tile == 16:
+            forms += [("plain_f32_4px", dict(pixels_per_thread=4)),
+                      ("plain_f32_batch128", dict(batch=128))]
         for name, kw in forms:
             variants[name] = time_variant(
                 lambda kw=kw: [Rasterizer(cams, prm, N, device=dev, pair_capacity=r.capacity,
@@ -910,7 +914,8 @@ def main():
                        "launch": ("persistent %d CTAs over the list-length queue"
                                   % form["persistent"] if form["persistent"]
                                   else "one CTA per %dx%d tile" % (args.tile, args.tile))
-                       + ", %d px/thread" % (form["pixels_per_thread"] or 2),
+                       + ", %d px/thread, %d-entry batches" % (form["pixels_per_thread"] or 2,
+                                                               form.get("batch") or 256),
                        "autotune_ms": tuned,
                        "l2": "flushed (256 MB write) before every timed step",
                        "timed_form": "whole step captured in one CUDA graph, replayed",

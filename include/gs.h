@@ -109,7 +109,10 @@ typedef struct {
     void* ev_begin;                /* optional cudaEvent_t recorded on the stream right before the
                                       blending kernel (for live per-kernel timing) */
     void* ev_end;                  /* optional cudaEvent_t recorded right after it */
-    int pixels_per_thread;         /* 1, 2 or 4 pixels of a column per thread (0 = 2) */
+    int pixels_per_thread;         /* 1, 2 or 4 pixels of a column per thread (0 = 2); 4 only
+                                      with 16-pixel tiles */
+    int batch;                     /* list entries staged in shared memory per batch: 256, or
+                                      128 with F32 records and 16-pixel tiles (0 = 256) */
 } gs_launch;
 
 /* ---------------------------------------------------------------------- */

@@ -1,7 +1,8 @@
 """Launch-form autotuner for the blending kernels.
 
-Times the candidate launch forms (pixels per thread 1/2/4, one CTA per tile
-or a persistent grid over the list-length-ordered tile queue) on the caller's
+Times the candidate launch forms (pixels per thread 1/2/4, list entries per
+shared-memory batch 128/256, one CTA per tile or a persistent grid of 4 or 8
+CTAs per SM over the list-length-ordered tile queue) on the caller's
 actual workload (a few whole fwd+bwd steps each, L2 flushed between steps),
 and caches the fastest form per workload signature (views and their sizes,
 Gaussian count, staging dtype, device name) in a JSON file under
@@ -18,24 +19,41 @@ import torch
 from .rasterize import Rasterizer
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+SMS = 152
 CANDIDATES = [
-    {"pixels_per_thread": 1, "persistent": 0},
-    {"pixels_per_thread": 2, "persistent": 0},
-    {"pixels_per_thread": 4, "persistent": 0},
-    {"pixels_per_thread": 2, "persistent": 152 * 8},
-    {"pixels_per_thread": 4, "persistent": 152 * 8},
+    {"pixels_per_thread": 1, "persistent": 0, "batch": 256},
+    {"pixels_per_thread": 2, "persistent": 0, "batch": 256},
+    {"pixels_per_thread": 4, "persistent": 0, "batch": 256},
+    {"pixels_per_thread": 2, "persistent": 0, "batch": 128},
+    {"pixels_per_thread": 4, "persistent": 0, "batch": 128},
+    {"pixels_per_thread": 2, "persistent": SMS * 8, "batch": 256},
+    {"pixels_per_thread": 4, "persistent": SMS * 8, "batch": 256},
+    {"pixels_per_thread": 2, "persistent": SMS * 4, "batch": 256},
 ]
 
 
 def signature(cams, N, attr_dtype, tile=16):
+    """Cache key: the views and their sizes, N, staging dtype, tile side, the
+    candidate set and the device."""
     views = ",".join("%dx%d" % (c["width"], c["height"]) for c in cams)
-    return "%s|N=%d|%s|tile=%d|%s" % (views, N, attr_dtype, tile, torch.cuda.get_device_name())
+    forms = ";".join(form_name(f) for f in candidates(tile, attr_dtype))
+    return "%s|N=%d|%s|tile=%d|%s|%s" % (views, N, attr_dtype, tile, forms,
+                                         torch.cuda.get_device_name())
 
 
-def candidates(tile=16):
+def candidates(tile=16, attr_dtype="f32"):
     """Launch forms to try; 8-pixel tiles take 1 or 2 pixels per thread (a
-    CTA of one tile must hold at least one full warp)."""
-    return [f for f in CANDIDATES if tile == 16 or f["pixels_per_thread"] <= 2]
+    CTA of one tile must hold at least one full warp); the 128-entry batch
+    exists for F32 records on 16-pixel tiles."""
+    return [f for f in CANDIDATES
+            if (tile == 16 or f["pixels_per_thread"] <= 2)
+            and (f["batch"] == 256 or (tile == 16 and attr_dtype == "f32"))]
+
+
+def form_name(form):
+    """e.g. "ppt2_b256_per_tile", "ppt4_b256_persistent1216"."""
+    where = "persistent%d" % form["persistent"] if form["persistent"] else "per_tile"
+    return "ppt%d_b%d_%s" % (form["pixels_per_thread"], form.get("batch", 256), where)
 
 
 def _load():
@@ -84,16 +102,12 @@ def tune(cams, prm, params, target, gamma, attr_dtype="f32", force=False, steps=
     if not force and key in db:
         return db[key]["best"], db[key]["ms"]
     times = {}
-    cands = candidates(tile)
+    cands = candidates(tile, attr_dtype)
     for form in cands:
-        name = "ppt%d_%s" % (form["pixels_per_thread"],
-                             "persistent" if form["persistent"] else "per_tile")
-        times[name] = time_form(cams, prm, params, target, gamma, form, attr_dtype, steps)
+        times[form_name(form)] = time_form(cams, prm, params, target, gamma, form, attr_dtype,
+                                           steps)
         torch.cuda.empty_cache()
-    best_name = min(times, key=times.get)
-    best = cands[[("ppt%d_%s" % (f["pixels_per_thread"],
-                                  "persistent" if f["persistent"] else "per_tile"))
-                  for f in cands].index(best_name)]
+    best = min(cands, key=lambda f: times[form_name(f)])
     db[key] = {"best": best, "ms": times, "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
     _store(db)
     return best, times

@@ -430,6 +430,22 @@ int gs_bin_sort(const gs_proj* proj, int N, const gs_camera* cams, int V, int ti
                          (cudaStream_t)stream);
 }
 
+namespace {
+// The launch controls of the render calls, checked on the host (NULL = defaults).
+const char* launch_opt_error(const gs_launch* opt, const gs_params* prm) {
+  if (!opt) return nullptr;
+  if (opt->ctas < 0) return "ctas < 0";
+  if (opt->ctas > 0 && !opt->work_counter) return "persistent launch needs work_counter";
+  const int ppt = opt->pixels_per_thread;
+  if (ppt != 0 && ppt != 1 && ppt != 2 && ppt != 4) return "pixels_per_thread (0, 1, 2 or 4)";
+  if (ppt == 4 && prm->tile_size == 8) return "pixels_per_thread 4 needs 16-pixel tiles";
+  if (opt->batch != 0 && opt->batch != 256 && opt->batch != 128) return "batch (0, 128 or 256)";
+  if (opt->batch == 128 && (prm->tile_size == 8 || prm->attr_dtype != GS_ATTR_F32))
+    return "batch 128 needs F32 records and 16-pixel tiles";
+  return nullptr;
+}
+}  // namespace
+
 int gs_render_fwd(const gs_proj* proj, int N, const gs_camera* cams, int V, const gs_params* prm,
                   const unsigned* sorted_vals, const unsigned* tile_ranges, float* image,
                   float* final_T, unsigned* last_idx, float* entropy, const gs_launch* opt,
@@ -441,7 +457,7 @@ int gs_render_fwd(const gs_proj* proj, int N, const gs_camera* cams, int V, cons
   if (!proj_ok(proj, true)) return invalid("projection buffers");
   if (!tile_ranges || !image || !final_T || !last_idx) return invalid("output pointers");
   if (!aligned(tile_ranges, 8)) return invalid("tile_ranges must be 8-byte aligned");
-  if (opt && opt->ctas > 0 && !opt->work_counter) return invalid("persistent launch needs work_counter");
+  if (const char* why = launch_opt_error(opt, prm)) return invalid(why);
   return launch_render_fwd(proj, ct, prm, sorted_vals, tile_ranges, image, final_T, last_idx,
                            entropy, opt, (cudaStream_t)stream);
 }
@@ -533,7 +549,7 @@ int gs_render_bwd(const gs_proj* proj, int N, const gs_camera* cams, int V, cons
   if (N > 0 && (!g_means || !g_log_scales || !g_quats || !g_opacity_logits || !g_sh))
     return invalid("gradient outputs");
   if (N > 0 && (!aligned(quats, 16) || !aligned(g_quats, 16))) return invalid("quat alignment");
-  if (opt && opt->ctas > 0 && !opt->work_counter) return invalid("persistent launch needs work_counter");
+  if (const char* why = launch_opt_error(opt, prm)) return invalid(why);
   cudaStream_t st = (cudaStream_t)stream;
   if (N == 0) return GS_OK;  // no Gaussians: no gradients
   GS_TRY_CUDA(cudaMemsetAsync(grad2d, 0, sizeof(float) * 12 * (size_t)N * V, st));

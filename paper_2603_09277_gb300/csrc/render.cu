@@ -43,13 +43,19 @@
 //
 // Launch forms: one CTA per tile (optionally in a given tile order), or a
 // persistent grid whose CTAs claim tiles from a queue with one atomicAdd per
-// tile (no CTA ever waits for another).
+// tile (no CTA ever waits for another); 1, 2 or 4 pixels per thread; 256 or
+// (F32 records, 16-pixel tiles) 128 list entries staged per batch.  The
+// batch size changes only how the list is staged, never which entries a
+// pixel meets or their order: the forward outputs do not depend on it.
 #include "gs_internal.cuh"
 
 namespace gs {
 namespace {
 
-constexpr int kBatch = 256;  // records per staging batch
+// Records per shared-memory staging batch: a template argument B of the
+// kernels, 256 or (F32 records, 16-pixel tiles) 128; at most 256 (a batch
+// position is one byte in the per-warp entry lists).
+constexpr int kMaxBatch = 256;
 constexpr int kDirectLanes = 24;  // up to this many contributing lanes add directly
 constexpr unsigned kFull = 0xffffffffu;
 // A row coordinate this far from every mean makes the exponent -inf (f22 > 0),
@@ -210,18 +216,19 @@ __device__ __forceinline__ int fwd_pair(const RenderConsts& rc, const float4 g0,
   return (int)b0 + (int)b1;
 }
 
-template <int DT, int TS, int PPT, bool STATS>
+template <int DT, int TS, int PPT, int B, bool STATS>
 __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts& rc,
                                          const FwdArgs& a, int tile, unsigned long long& n_bl,
                                          unsigned long long& n_ev) {
   constexpr int NT = TileGeom<TS, PPT>::kThreads;
   constexpr int NW = NT / 32;
   static_assert(NW >= 1, "a tile needs at least one full warp");
-  __shared__ float4 s0[kBatch];
-  __shared__ float4 s1[kBatch];
-  __shared__ float s2[kBatch];
-  __shared__ unsigned short s_rows[kBatch];
-  __shared__ unsigned char s_list[NW][kBatch];
+  static_assert(B % 32 == 0 && B <= kMaxBatch, "batch: a multiple of 32, at most 256");
+  __shared__ float4 s0[B];
+  __shared__ float4 s1[B];
+  __shared__ float s2[B];
+  __shared__ unsigned short s_rows[B];
+  __shared__ unsigned char s_list[NW][B];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const TileGeom<TS, PPT> tg = tile_geom<TS, PPT>(ct, tile);
   const uint2 r = a.ranges[tile];
@@ -246,9 +253,9 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
     ry2 = make_float2(ry[0], ry[1]);
   }
   unsigned nb = 0, ne = 0;
-  for (unsigned base = r.x; base < r.y; base += kBatch) {
+  for (unsigned base = r.x; base < r.y; base += B) {
     if (__syncthreads_count(live == 0u) == NT) break;
-    for (int j = tid; j < kBatch; j += NT) {
+    for (int j = tid; j < B; j += NT) {
       const unsigned idx = base + j;
       if (idx < r.y) {
         const Splat s = load_record<DT>(a.recs, a.vals[idx]);
@@ -261,7 +268,7 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
       }
     }
     __syncthreads();
-    const int cnt = (int)min((unsigned)kBatch, r.y - base);
+    const int cnt = (int)min((unsigned)B, r.y - base);
     // only the entries that may reach a pixel of this warp's rows
     const int n = __any_sync(kFull, live != 0u)
                       ? warp_entries<TS, PPT>(s_rows, s_list[warp], cnt, lane, warp)
@@ -352,7 +359,7 @@ __device__ __forceinline__ void flush_stats(unsigned long long* stats, unsigned 
   }
 }
 
-template <int DT, int TS, int PPT, bool STATS>
+template <int DT, int TS, int PPT, int B, bool STATS>
 __global__ void __launch_bounds__(TS * TS / PPT) render_fwd_kernel(const CamTable ct,
                                                                     const RenderConsts rc,
                                                                     const FwdArgs a,
@@ -366,11 +373,11 @@ __global__ void __launch_bounds__(TS * TS / PPT) render_fwd_kernel(const CamTabl
       const unsigned t = s_t;
       __syncthreads();
       if (t >= (unsigned)ct.total_tiles) break;
-      fwd_tile<DT, TS, PPT, STATS>(ct, rc, a, a.order ? (int)a.order[t] : (int)t, nb, ne);
+      fwd_tile<DT, TS, PPT, B, STATS>(ct, rc, a, a.order ? (int)a.order[t] : (int)t, nb, ne);
     }
   } else {
     const int t = blockIdx.x;
-    fwd_tile<DT, TS, PPT, STATS>(ct, rc, a, a.order ? (int)a.order[t] : t, nb, ne);
+    fwd_tile<DT, TS, PPT, B, STATS>(ct, rc, a, a.order ? (int)a.order[t] : t, nb, ne);
   }
   if (STATS) flush_stats(a.stats, nb, ne);
 }
@@ -495,18 +502,19 @@ __device__ __forceinline__ bool bwd_pair(const RenderConsts& rc, const float4 g0
   return true;
 }
 
-template <int DT, int TS, int PPT>
+template <int DT, int TS, int PPT, int B>
 __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts& rc,
                                          const BwdArgs& a, int tile) {
-  __shared__ float4 s0[kBatch];
-  __shared__ float4 s1[kBatch];
-  __shared__ float s2[kBatch];  // B
-  __shared__ unsigned s_row[kBatch];
-  __shared__ unsigned short s_rows[kBatch];
+  static_assert(B % 32 == 0 && B <= kMaxBatch, "batch: a multiple of 32, at most 256");
+  __shared__ float4 s0[B];
+  __shared__ float4 s1[B];
+  __shared__ float s2[B];  // blue
+  __shared__ unsigned s_row[B];
+  __shared__ unsigned short s_rows[B];
   constexpr int NT = TileGeom<TS, PPT>::kThreads;
   constexpr int NW = NT / 32;
   static_assert(NW >= 1, "a tile needs at least one full warp");
-  __shared__ unsigned char s_list[NW][kBatch];
+  __shared__ unsigned char s_list[NW][B];
   __shared__ unsigned s_max;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -553,7 +561,7 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
   __syncthreads();
   const unsigned maxlast = s_max;
   for (unsigned end = maxlast; end > 0;) {
-    const unsigned start = end > (unsigned)kBatch ? end - kBatch : 0u;
+    const unsigned start = end > (unsigned)B ? end - B : 0u;
     const int cnt = (int)(end - start);
     __syncthreads();
     for (int j = tid; j < cnt; j += NT) {
@@ -650,7 +658,7 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
   __syncthreads();
 }
 
-template <int DT, int TS, int PPT>
+template <int DT, int TS, int PPT, int B>
 __global__ void __launch_bounds__(TS * TS / PPT, (TS == 16 && PPT != 4) ? 4 * PPT : 1)
     render_bwd_kernel(const CamTable ct,
                                                                     const RenderConsts rc,
@@ -664,11 +672,11 @@ __global__ void __launch_bounds__(TS * TS / PPT, (TS == 16 && PPT != 4) ? 4 * PP
       const unsigned t = s_t;
       __syncthreads();
       if (t >= (unsigned)ct.total_tiles) break;
-      bwd_tile<DT, TS, PPT>(ct, rc, a, a.order ? (int)a.order[t] : (int)t);
+      bwd_tile<DT, TS, PPT, B>(ct, rc, a, a.order ? (int)a.order[t] : (int)t);
     }
   } else {
     const int t = blockIdx.x;
-    bwd_tile<DT, TS, PPT>(ct, rc, a, a.order ? (int)a.order[t] : t);
+    bwd_tile<DT, TS, PPT, B>(ct, rc, a, a.order ? (int)a.order[t] : t);
   }
 }
 
@@ -678,22 +686,42 @@ int record_event(void* ev, cudaStream_t st) {
   return GS_OK;
 }
 
-template <int DT, int TS, int PPT>
-void launch_fwd_ppt(const CamTable& ct, const RenderConsts& rc, const FwdArgs& a, int ctas,
-                    cudaStream_t st) {
+template <int DT, int TS, int PPT, int B>
+void launch_fwd_b(const CamTable& ct, const RenderConsts& rc, const FwdArgs& a, int ctas,
+                  cudaStream_t st) {
   const int grid = ctas > 0 ? ctas : ct.total_tiles;
   const int pers = ctas > 0 ? 1 : 0;
   if (a.stats)
-    render_fwd_kernel<DT, TS, PPT, true><<<grid, TS * TS / PPT, 0, st>>>(ct, rc, a, pers);
+    render_fwd_kernel<DT, TS, PPT, B, true><<<grid, TS * TS / PPT, 0, st>>>(ct, rc, a, pers);
   else
-    render_fwd_kernel<DT, TS, PPT, false><<<grid, TS * TS / PPT, 0, st>>>(ct, rc, a, pers);
+    render_fwd_kernel<DT, TS, PPT, B, false><<<grid, TS * TS / PPT, 0, st>>>(ct, rc, a, pers);
+}
+
+template <int DT, int TS, int PPT, int B>
+void launch_bwd_b(const CamTable& ct, const RenderConsts& rc, const BwdArgs& a, int ctas,
+                  cudaStream_t st) {
+  const int grid = ctas > 0 ? ctas : ct.total_tiles;
+  render_bwd_kernel<DT, TS, PPT, B><<<grid, TS * TS / PPT, 0, st>>>(ct, rc, a, ctas > 0 ? 1 : 0);
+}
+
+// The 128-record batch exists for F32 records on 16-pixel tiles only (the
+// host rejects it elsewhere); every other form stages 256 records.
+template <int DT, int TS, int PPT>
+void launch_fwd_ppt(const CamTable& ct, const RenderConsts& rc, const FwdArgs& a, int ctas,
+                    int batch, cudaStream_t st) {
+  if constexpr (DT == GS_ATTR_F32 && TS == 16) {
+    if (batch == 128) return launch_fwd_b<DT, TS, PPT, 128>(ct, rc, a, ctas, st);
+  }
+  launch_fwd_b<DT, TS, PPT, kMaxBatch>(ct, rc, a, ctas, st);
 }
 
 template <int DT, int TS, int PPT>
 void launch_bwd_ppt(const CamTable& ct, const RenderConsts& rc, const BwdArgs& a, int ctas,
-                    cudaStream_t st) {
-  const int grid = ctas > 0 ? ctas : ct.total_tiles;
-  render_bwd_kernel<DT, TS, PPT><<<grid, TS * TS / PPT, 0, st>>>(ct, rc, a, ctas > 0 ? 1 : 0);
+                    int batch, cudaStream_t st) {
+  if constexpr (DT == GS_ATTR_F32 && TS == 16) {
+    if (batch == 128) return launch_bwd_b<DT, TS, PPT, 128>(ct, rc, a, ctas, st);
+  }
+  launch_bwd_b<DT, TS, PPT, kMaxBatch>(ct, rc, a, ctas, st);
 }
 
 template <int DT>
@@ -702,14 +730,15 @@ int launch_fwd_t(const CamTable& ct, const RenderConsts& rc, const FwdArgs& a, i
   int e = record_event(opt ? opt->ev_begin : nullptr, st);
   if (e != GS_OK) return e;
   const int ppt = (opt && opt->pixels_per_thread) ? opt->pixels_per_thread : 2;
+  const int batch = (opt && opt->batch) ? opt->batch : kMaxBatch;
   if (ct.total_tiles > 0) {
     if (ct.tile == 8) {  // 8x8 tiles: 1 or 2 px per thread (a CTA is at least one warp)
-      if (ppt == 1) launch_fwd_ppt<DT, 8, 1>(ct, rc, a, ctas, st);
-      else launch_fwd_ppt<DT, 8, 2>(ct, rc, a, ctas, st);
+      if (ppt == 1) launch_fwd_ppt<DT, 8, 1>(ct, rc, a, ctas, batch, st);
+      else launch_fwd_ppt<DT, 8, 2>(ct, rc, a, ctas, batch, st);
     } else {
-      if (ppt == 1) launch_fwd_ppt<DT, 16, 1>(ct, rc, a, ctas, st);
-      else if (ppt == 4) launch_fwd_ppt<DT, 16, 4>(ct, rc, a, ctas, st);
-      else launch_fwd_ppt<DT, 16, 2>(ct, rc, a, ctas, st);
+      if (ppt == 1) launch_fwd_ppt<DT, 16, 1>(ct, rc, a, ctas, batch, st);
+      else if (ppt == 4) launch_fwd_ppt<DT, 16, 4>(ct, rc, a, ctas, batch, st);
+      else launch_fwd_ppt<DT, 16, 2>(ct, rc, a, ctas, batch, st);
     }
     count_launches(1);
   }
@@ -724,14 +753,15 @@ int launch_bwd_t(const CamTable& ct, const RenderConsts& rc, const BwdArgs& a, i
   int e = record_event(opt ? opt->ev_begin : nullptr, st);
   if (e != GS_OK) return e;
   const int ppt = (opt && opt->pixels_per_thread) ? opt->pixels_per_thread : 2;
+  const int batch = (opt && opt->batch) ? opt->batch : kMaxBatch;
   if (ct.total_tiles > 0) {
     if (ct.tile == 8) {
-      if (ppt == 1) launch_bwd_ppt<DT, 8, 1>(ct, rc, a, ctas, st);
-      else launch_bwd_ppt<DT, 8, 2>(ct, rc, a, ctas, st);
+      if (ppt == 1) launch_bwd_ppt<DT, 8, 1>(ct, rc, a, ctas, batch, st);
+      else launch_bwd_ppt<DT, 8, 2>(ct, rc, a, ctas, batch, st);
     } else {
-      if (ppt == 1) launch_bwd_ppt<DT, 16, 1>(ct, rc, a, ctas, st);
-      else if (ppt == 4) launch_bwd_ppt<DT, 16, 4>(ct, rc, a, ctas, st);
-      else launch_bwd_ppt<DT, 16, 2>(ct, rc, a, ctas, st);
+      if (ppt == 1) launch_bwd_ppt<DT, 16, 1>(ct, rc, a, ctas, batch, st);
+      else if (ppt == 4) launch_bwd_ppt<DT, 16, 4>(ct, rc, a, ctas, batch, st);
+      else launch_bwd_ppt<DT, 16, 2>(ct, rc, a, ctas, batch, st);
     }
     count_launches(1);
   }

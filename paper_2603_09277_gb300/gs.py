@@ -53,7 +53,7 @@ class GsLaunch(ctypes.Structure):
     _fields_ = [("tile_order", ctypes.c_void_p), ("work_counter", ctypes.c_void_p),
                 ("ctas", ctypes.c_int), ("stats", ctypes.c_void_p),
                 ("ev_begin", ctypes.c_void_p), ("ev_end", ctypes.c_void_p),
-                ("pixels_per_thread", ctypes.c_int)]
+                ("pixels_per_thread", ctypes.c_int), ("batch", ctypes.c_int)]
 
 
 class GsError(RuntimeError):
@@ -176,11 +176,12 @@ def make_proj(records, depth, rect, tiles_touched, radius=None, mean2d=None, con
 
 
 def make_launch(tile_order=None, work_counter=None, ctas=0, stats=None, ev_begin=None,
-                ev_end=None, pixels_per_thread=0):
+                ev_end=None, pixels_per_thread=0, batch=0):
     """ev_begin / ev_end: recorded torch.cuda.Event objects (or None)."""
     return GsLaunch(_ptr(tile_order), _ptr(work_counter), int(ctas), _ptr(stats),
                     ev_begin.cuda_event if ev_begin is not None else None,
-                    ev_end.cuda_event if ev_end is not None else None, int(pixels_per_thread))
+                    ev_end.cuda_event if ev_end is not None else None, int(pixels_per_thread),
+                    int(batch))
 
 
 # ---------------------------------------------------------------------------

@@ -37,11 +37,13 @@ class Rasterizer:
     N: Gaussian count; attr_dtype: "f32" | "f16" | "bf16" record staging;
     persistent: 0 (one CTA per tile) or the CTA count of a persistent launch
     claiming tiles from a list-length-ordered queue (the batched form);
-    pixels_per_thread: 1, 2 or 4 (0 = the library default, 2).
+    pixels_per_thread: 1, 2 or 4 (0 = the library default, 2);
+    batch: list entries staged per shared-memory batch, 128 or 256 (0 = 256).
     """
 
     def __init__(self, cams, prm, N, sh_stride=16, attr_dtype="f32", device="cuda",
-                 pair_capacity=None, persistent=0, keep_debug=False, pixels_per_thread=0):
+                 pair_capacity=None, persistent=0, keep_debug=False, pixels_per_thread=0,
+                 batch=0):
         self.device = torch.device(device)
         self.cams = cams
         self.cams_c = gs.make_cameras(cams)
@@ -100,6 +102,7 @@ class Rasterizer:
         self.stats = torch.zeros(2, dtype=torch.int64, device=dev)
         self.persistent = int(persistent)
         self.ppt = int(pixels_per_thread)
+        self.batch = int(batch)
         self.tile_order = None
         if self.persistent:
             self.tile_order = torch.empty(max(self.total_tiles, 1), **i32)
@@ -112,9 +115,10 @@ class Rasterizer:
         ev = events if events is not None else (None, None)
         if self.persistent:
             return gs.make_launch(self.tile_order, self.work_counter, self.persistent,
-                                  self.stats if stats else None, ev[0], ev[1], self.ppt)
+                                  self.stats if stats else None, ev[0], ev[1], self.ppt,
+                                  self.batch)
         return gs.make_launch(None, None, 0, self.stats if stats else None, ev[0], ev[1],
-                              self.ppt)
+                              self.ppt, self.batch)
 
     def _alloc_pairs(self, cap):
         cap = int(min(max(cap, 1), (1 << 32) - 1))

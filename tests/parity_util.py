@@ -24,13 +24,13 @@ GRAD_TOL = 1e-4     # relative, gradient tensors (norm), FP32 vs FP64
 
 
 def run_gpu(scene, cams, prm, target=None, gamma=0.015, attr="f32", persistent=0,
-            dL_dimage=None, dL_dentropy=None, keys=True, ppt=0):
+            dL_dimage=None, dL_dentropy=None, keys=True, ppt=0, batch=0):
     """Runs preprocess, bin_sort, render_fwd, loss (if target) and
     render_bwd through the C ABI.  dL_dimage / dL_dentropy (numpy, per
     pixel) override the loss gradients.  Returns numpy arrays."""
     N = scene["means"].shape[0]
     rast = Rasterizer(cams, prm, N, attr_dtype=attr, keep_debug=True, persistent=persistent,
-                      pixels_per_thread=ppt)
+                      pixels_per_thread=ppt, batch=batch)
     p = scene_to_device(scene)
     rast.preprocess(p)
     P = rast.bin_sort(keys=keys)

@@ -77,3 +77,54 @@ def test_host_side_argument_checks(lib_path):
     assert b"tile_size" in lib.gs_last_error_string()
     assert lib.gs_bin_sort_workspace_size(1000, 5000, 64) > 0
     assert b"sm_103a" in lib.gs_version()
+
+
+def test_render_launch_options_checked_on_the_host(lib_path):
+    """Launch controls that no kernel exists for are rejected by both render
+    calls before any launch (the pointers below are never dereferenced)."""
+    from paper_2603_09277_gb300 import gs, scenes
+    lib = gs._lib
+    cams = gs.make_cameras([scenes.camera(64, 48, 64.0)])
+    fake = 4096  # 16-byte aligned, never touched: every call fails validation
+    proj = gs.GsProj(fake, fake, fake, fake, None, None, None, None)
+
+    def calls(prm, opt):
+        fwd = lib.gs_render_fwd(ctypes.byref(proj), 10, cams, 1, ctypes.byref(prm), fake, fake,
+                                fake, fake, fake, fake, ctypes.byref(opt), None)
+        bwd = lib.gs_render_bwd(ctypes.byref(proj), 10, cams, 1, ctypes.byref(prm), fake, fake,
+                                fake, fake, fake, fake, fake, fake, fake, fake, fake, fake, fake,
+                                fake, fake, fake, fake, ctypes.byref(opt), None)
+        return fwd, bwd
+
+    bad = [(16, "f32", dict(pixels_per_thread=3), b"pixels_per_thread"),
+           (8, "f32", dict(pixels_per_thread=4), b"16-pixel tiles"),
+           (16, "f32", dict(batch=64), b"batch"),
+           (16, "bf16", dict(batch=128), b"F32 records"),
+           (8, "f32", dict(batch=128), b"F32 records"),
+           (16, "f32", dict(ctas=-1), b"ctas"),
+           (16, "f32", dict(ctas=152), b"work_counter")]
+    for tile, attr, kw, why in bad:
+        prm = gs.make_params(scenes.params(tile=tile), 16, attr)
+        for status in calls(prm, gs.make_launch(**kw)):
+            assert status == gs.GS_ERR_INVALID_ARG, (tile, attr, kw)
+            assert why in lib.gs_last_error_string(), (kw, lib.gs_last_error_string())
+
+
+def test_autotune_candidates_exist_for_the_workload():
+    """Every form the autotuner may pick is one the render calls accept: no
+    4-pixel form on 8-pixel tiles, the 128-entry batch only for F32 records
+    on 16-pixel tiles; forms have distinct names (the timing table's keys)."""
+    from paper_2603_09277_gb300 import autotune
+    for tile in (16, 8):
+        for attr in ("f32", "f16", "bf16"):
+            c = autotune.candidates(tile, attr)
+            names = [autotune.form_name(f) for f in c]
+            assert len(set(names)) == len(names) >= 3
+            for f in c:
+                assert f["pixels_per_thread"] in (1, 2, 4) and f["batch"] in (128, 256)
+                assert tile == 16 or f["pixels_per_thread"] <= 2
+                assert f["batch"] == 256 or (tile == 16 and attr == "f32")
+                assert f["persistent"] % autotune.SMS == 0
+    c = autotune.candidates(16, "f32")
+    assert {f["batch"] for f in c} == {128, 256}
+    assert len({f["persistent"] for f in c if f["persistent"]}) >= 2
