@@ -166,23 +166,33 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
-            except ValueError:
-                continue
+        with open(self.path) as f:
+            out = summarise_clock_rows(f.read().splitlines())
         os.unlink(self.path)
-        if not rows:
-            return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i] == "Active"})
-        return {"sm_mhz": float(np.median([r[0] for r in rows])),
-                "sm_max_mhz": float(max(r[1] for r in rows)), "reasons": reasons,
-                "samples": len(rows)}
+        return out
+
+
+def summarise_clock_rows(lines):
+    """The `clocks` object of the JSON line from nvidia-smi CSV rows (the
+    ClockSampler.FIELDS columns, no header, no units): the median SM clock,
+    the largest maximum clock, and every throttle reason seen Active.  Rows
+    that do not parse (a header, "[N/A]") are skipped; None without rows."""
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+        except ValueError:
+            continue
+    if not rows:
+        return None
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i] == "Active"})
+    return {"sm_mhz": float(np.median([r[0] for r in rows])),
+            "sm_max_mhz": float(max(r[1] for r in rows)), "reasons": reasons,
+            "samples": len(rows)}
 
 
 # ---------------------------------------------------------------------------
