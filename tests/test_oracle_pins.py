@@ -103,8 +103,8 @@ def test_list_lengths_match_tiles_touched(cfg1):
     dk = proj["depth"].view(np.uint32)
     for t in range(len(ts) - 1):
         seg = ids[ts[t]:ts[t + 1]]
-        key = dk[seg].astype(np.uint64) * (1 << 32) + seg.astype(np.uint64)
-        assert (np.diff(key.astype(np.float64)) > 0).all() or len(seg) < 2
+        key = (dk[seg].astype(np.uint64) << np.uint64(32)) | seg.astype(np.uint64)
+        assert (key[1:] > key[:-1]).all()  # exact 64-bit comparison, strictly increasing
 
 
 # --------------------------------------------------------------------------
@@ -335,6 +335,41 @@ def test_tiled_equals_brute_force(seed, tile):
     assert np.abs(fwd["final_T"] - Tf).max() < 1e-13
     assert np.abs(fwd["entropy"] - Hm).max() < 1e-13
     assert (fwd["last"] == last).all()
+
+
+def test_equal_depths_blend_in_id_order():
+    """Reading c6: Gaussians whose FP32 depths are equal are blended in
+    ascending id order.  Five Gaussians at the same camera depth (z = 4
+    exactly under the identity camera), of different colours, so that the
+    order changes the image; listed in reverse x order so that a sort on
+    position would disagree."""
+    n = 5
+    x = np.array([0.04, 0.03, 0.02, 0.01, 0.0])
+    scene = {"means": np.stack([x, np.zeros(n), np.full(n, 4.0)], 1).astype(np.float32),
+             "log_scales": np.full((n, 3), -2.5, np.float32),
+             "quats": np.tile(np.array([1.0, 0, 0, 0], np.float32), (n, 1)),
+             "opacity_logits": np.full(n, 0.5, np.float32),
+             "sh": np.zeros((n, 16, 3), np.float32), "sh_degree": 0}
+    for i in range(n):
+        scene["sh"][i, 0, i % 3] = 1.5
+    cam = scenes.camera(48, 40, 48.0)
+    prm = scenes.params()
+    proj = oracle.preprocess(scene, cam, prm)
+    assert (proj["depth"].astype(np.float32) == np.float32(4.0)).all()
+    lists = oracle.build_lists(proj, cam)
+    ts, ids = lists
+    for t in range(len(ts) - 1):
+        seg = ids[ts[t]:ts[t + 1]]
+        assert list(seg) == sorted(seg)
+    assert max(np.diff(ts)) == n  # every Gaussian shares at least one tile
+    fwd = oracle.render_fwd(proj, lists, cam, prm)
+    img, Tf, Hm, last = _brute_force(proj, cam, prm)
+    assert np.abs(fwd["image"] - img).max() < 1e-13
+    assert (fwd["last"] == last).all()
+    # blending in the reverse order gives a different image: the order is seen
+    rev = (ts, np.concatenate([ids[ts[t]:ts[t + 1]][::-1] for t in range(len(ts) - 1)]))
+    other = oracle.render_fwd(proj, rev, cam, prm)
+    assert np.abs(other["image"] - img).max() > 1e-3
 
 
 # --------------------------------------------------------------------------
