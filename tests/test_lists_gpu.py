@@ -3,7 +3,8 @@ the oracle's plain definition on layouts that exercise the list
 construction's corners: a view with more than 256 super-tiles of 8x8 tiles
 (the super-tile sort then takes two radix passes), views whose tile grids
 end inside a super-tile (1x1, 9x9, 2x19, 63x2 tiles), Gaussians whose rects
-span many super-tiles, and the largest view count (64 views)."""
+span many super-tiles, the largest view count (64 views), and more than
+4 M (view, Gaussian) rows (the row scans then take 4,096-row blocks)."""
 import numpy as np
 import pytest
 
@@ -84,3 +85,16 @@ def test_lists_sixty_four_views():
     scene = scenes.box_scene(2_000, seed=8)
     P, total, flagged = _compare_lists(scene, cams, scenes.params())
     assert P > 10_000 and (flagged or P == total)
+
+
+def test_lists_more_than_four_million_rows():
+    # 70,000 Gaussians x 64 views = 4.48 M rows: the row scans and the
+    # compaction run with 4,096-row blocks (1,024 up to 4 M rows)
+    rng = np.random.default_rng(9)
+    yaws = list(rng.uniform(-20.0, 20.0, 64))
+    sizes = [(int(w), int(h)) for w, h in zip(rng.integers(24, 200, 64), rng.integers(24, 160, 64))]
+    cams = scenes.yaw_cameras(sizes, yaws)
+    scene = scenes.box_scene(70_000, seed=10)
+    assert 70_000 * 64 > (4 << 20)
+    P, total, flagged = _compare_lists(scene, cams, scenes.params())
+    assert P > 10_000_000 and (flagged or P == total)
