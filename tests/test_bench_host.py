@@ -1,12 +1,14 @@
 """Host-side pieces of bench.py that need no GPU: the defaults of the
 command line, the summary of the nvidia-smi clock samples, the measured-peak
-lookup and the gate on the committed DRAM-traffic figures (a figure counts
-only for the render source and workload it was captured on)."""
+lookup, the gate on the committed DRAM-traffic figures (a figure counts only
+for the render source and workload it was captured on), and the launch-form
+autotuner's choice and cache with its timing replaced."""
 import hashlib
 import json
 import os
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -84,3 +86,36 @@ def test_committed_peaks_file_is_read_when_present():
         pytest.skip("no measured peaks in this checkout")
     want = float(json.load(open(path))["hbm_gbs"])
     assert bench.measured_hbm_peak() == (want, "measured")
+
+
+def test_autotune_picks_the_fastest_form_and_caches_it(tmp_path, monkeypatch):
+    """The autotuner's host logic with the timing replaced: the fastest
+    candidate wins, the choice is cached per workload signature (candidate
+    set included) and reused unless forced."""
+    from paper_2603_09277_gb300 import autotune, scenes
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "autotune.json"))
+    monkeypatch.setattr(autotune.torch.cuda, "get_device_name", lambda *a: "GB300 (fake)")
+    calls = []
+
+    def fake_time(cams, prm, params, target, gamma, form, attr_dtype="f32", steps=5, warmup=2):
+        calls.append(autotune.form_name(form))
+        # 2 px/thread, 128-entry batch, one CTA per tile is the fastest here
+        return 1.0 if autotune.form_name(form) == "ppt2_b128_per_tile" else 2.0 + len(calls)
+
+    monkeypatch.setattr(autotune, "time_form", fake_time)
+    cams = [scenes.camera(64, 48, 64.0)]
+    prm = scenes.params()
+    params = {"means": np.zeros((10, 3), np.float32)}
+    best, ms = autotune.tune(cams, prm, params, None, 0.015)
+    assert best == {"pixels_per_thread": 2, "persistent": 0, "batch": 128}
+    assert sorted(ms) == sorted(calls) == sorted(autotune.form_name(f)
+                                                 for f in autotune.candidates(16, "f32"))
+    n = len(calls)
+    assert autotune.tune(cams, prm, params, None, 0.015)[0] == best and len(calls) == n
+    autotune.tune(cams, prm, params, None, 0.015, force=True)
+    assert len(calls) == 2 * n
+    # another staging dtype is another workload, without the 128-entry forms
+    best16, ms16 = autotune.tune(cams, prm, params, None, 0.015, attr_dtype="bf16")
+    assert best16["batch"] == 256 and not any("_b128_" in k for k in ms16)
+    db = json.load(open(tmp_path / "autotune.json"))
+    assert len(db) == 2 and all("GB300 (fake)" in k for k in db)
