@@ -110,6 +110,7 @@ class Rasterizer:
             self.queue_ws = torch.empty(gs.gs_tile_queue_workspace_size(self.total_tiles),
                                         dtype=torch.uint8, device=dev)
         self.num_pairs = None
+        self.forward_count = 0  # forwards run through rasterize(); see _Rasterize
 
     def _launch(self, stats=False, events=None):
         ev = events if events is not None else (None, None)
@@ -219,6 +220,11 @@ class Rasterizer:
 
 
 class _Rasterize(torch.autograd.Function):
+    """The backward reads the lists, final transmittances and last indices
+    that the Rasterizer holds from its latest forward, so one Rasterizer
+    serves one live graph at a time: a backward after a newer forward through
+    the same Rasterizer raises instead of using the newer forward's state."""
+
     @staticmethod
     def forward(ctx, means, log_scales, quats, opacity_logits, sh, rast):
         p = {"means": means.contiguous(), "log_scales": log_scales.contiguous(),
@@ -227,13 +233,19 @@ class _Rasterize(torch.autograd.Function):
         rast.preprocess(p)
         rast.bin_sort()
         rast.render_fwd()
+        rast.forward_count += 1
         ctx.rast = rast
+        ctx.forward_id = rast.forward_count
         ctx.save_for_backward(*[p[k] for k in PARAM_KEYS])
         return rast.image.clone(), rast.entropy.clone()
 
     @staticmethod
     def backward(ctx, g_image, g_entropy):
         rast = ctx.rast
+        if rast.forward_count != ctx.forward_id:
+            raise RuntimeError("rasterize: this Rasterizer ran another forward after the one being "
+                               "differentiated; its saved lists belong to the newer call (use one "
+                               "Rasterizer per live graph)")
         p = dict(zip(PARAM_KEYS, ctx.saved_tensors))
         g_image = g_image.contiguous() if g_image is not None else torch.zeros_like(rast.image)
         g_entropy = g_entropy.contiguous() if g_entropy is not None else None
