@@ -1,8 +1,11 @@
-"""The boundary is a plain C ABI: a C11 program that includes include/gs.h
+"""The boundary is a plain C ABI. A C11 program that includes include/gs.h
 (no C++ and no CUDA headers), takes the address of every declared entry
 point, links against libgs.so and calls the host-only functions and the
-host-side argument checks.  Nothing here reaches a GPU: every compute call
-below fails validation before it enqueues anything."""
+host-side argument checks; another prints the C compiler's layout of the
+header's structs, which the binding's ctypes structs must match.  Nothing
+here reaches a GPU: every compute call below fails validation before it
+enqueues anything."""
+import ctypes
 import os
 import shutil
 import subprocess
@@ -97,3 +100,32 @@ def test_c11_program_links_and_calls_the_abi(lib_path, tmp_path):  # noqa: F811
     assert out[5].startswith("fwd -1 ") and "pixels_per_thread" in out[5]
     assert out[6].startswith("fwd -1 ") and "F32 records" in out[6]
     assert out[7].startswith("version ") and "sm_103a" in out[7]
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes structs of the binding have the C compiler's layout of the
+    header's structs: the same size and every field at the same offset."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2603_09277_gb300 import gs
+    structs = {"gs_camera": gs.GsCamera, "gs_params": gs.GsParams, "gs_proj": gs.GsProj,
+               "gs_launch": gs.GsLaunch}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "gs.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for field, _ in py._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));'
+                         % (cname, field, cname, field))
+    lines += ["  return 0;", "}"]
+    (tmp_path / "layout.c").write_text("\n".join(lines) + "\n")
+    exe = str(tmp_path / "layout")
+    r = subprocess.run([cc, "-std=c11", "-Wall", "-Werror", "-I", os.path.dirname(HEADER),
+                        str(tmp_path / "layout.c"), "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(line.rsplit(" ", 1) for line in
+               subprocess.run([exe], capture_output=True, text=True, check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got["%s size" % cname]) == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert int(got["%s %s" % (cname, field)]) == getattr(py, field).offset, (cname, field)
