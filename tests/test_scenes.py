@@ -88,3 +88,28 @@ def test_sweep_scales_by_powers_of_half(k):
     d = b["log_scales"].astype(np.float64) - a["log_scales"].astype(np.float64)
     assert np.allclose(d, k * math.log(0.5), atol=1e-5)
     assert np.array_equal(a["means"], b["means"])
+
+
+def test_cfg5_view_and_box_and_the_density_matched_cfg3():
+    s, cams, targets, prm = scenes.config5(n=50_000)
+    assert [(c["width"], c["height"], c["fx"]) for c in cams] == [(1920, 1080, 1920.0)]
+    assert targets[0].shape == (1080, 1920, 3) and prm["sh_degree"] == 0
+    m = s["means"].astype(np.float64)
+    ar = 1080 / 1920
+    assert (np.abs(m[:, 0]) <= 1).all() and (np.abs(m[:, 1]) <= ar + 1e-6).all()
+    assert m[:, 1].max() > 0.98 * ar and m[:, 1].min() < -0.98 * ar  # the 16:9 extent is filled
+    # the labelled density-matched cfg3 variant shifts the log-scale mean by ln((1e4/n)^(1/3))
+    a, _, _, _ = scenes.config3(n=20_000)
+    b, _, _, _ = scenes.config3(n=20_000, density_matched=True)
+    d = b["log_scales"].astype(np.float64) - a["log_scales"].astype(np.float64)
+    assert np.allclose(d, math.log((1e4 / 20_000) ** (1.0 / 3.0)), atol=1e-5)
+
+
+def test_orbit_cameras_look_at_the_centre():
+    cams = scenes.orbit_cameras(32, 64, 48, seed=3)
+    assert len(cams) == 32
+    for c in cams:
+        w = c["world_to_cam"].astype(np.float64)
+        pc = w[:, :3] @ np.array([0.0, 0.0, 4.0]) + w[:, 3]
+        assert abs(pc[0]) < 1e-4 and abs(pc[1]) < 1e-4
+        assert abs(pc[2] - math.hypot(4.0, 0.5)) < 1e-4  # radius 4, height offset 0.5
