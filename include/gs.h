@@ -202,7 +202,11 @@ int gs_bin_sort(const gs_proj* proj, int N, const gs_camera* cams_host, int V, i
  *   H = -sum w ln w - T ln T over the blended entries and the background.
  * Outputs (device, per pixel): image [P][3], final_T [P], last_idx [P]
  * (1-based list position of the last blended entry, 0 if none), entropy [P]
- * (may be NULL).  opt: see gs_launch (NULL = one CTA per tile). */
+ * (may be NULL).  opt: see gs_launch (NULL = one CTA per tile).  Launch
+ * options without a kernel (pixels_per_thread other than 0/1/2/4, or 4 with
+ * 8-pixel tiles; batch other than 0/128/256, or 128 with F16/BF16 records
+ * or 8-pixel tiles; ctas < 0; ctas > 0 without work_counter) return
+ * GS_ERR_INVALID_ARG, here and in gs_render_bwd. */
 int gs_render_fwd(const gs_proj* proj, int N, const gs_camera* cams_host, int V,
                   const gs_params* prm, const unsigned* sorted_vals, const unsigned* tile_ranges,
                   float* image, float* final_T, unsigned* last_idx, float* entropy,
