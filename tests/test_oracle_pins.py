@@ -539,6 +539,27 @@ def test_loss_definition():
     assert dH == pytest.approx(np.full((5, 7), 0.5 * 0.015 / M), rel=1e-15)
 
 
+def test_views_average_per_view_means():
+    """Reading c4: with several views the loss is the mean over views of each
+    view's own pixel means (not one mean over the pooled pixels), and so are
+    the gradients: two views of different sizes give the average of the two
+    single-view results."""
+    scene = scenes.box_scene(300, seed=4)
+    cams = scenes.yaw_cameras([(48, 32), (24, 40)], [0.0, 6.0])
+    targets = scenes.noise_targets(cams, 3)
+    prm = scenes.params()
+    L2, _, g2, _ = oracle.step(scene, cams, targets, prm, scenes.GAMMA)
+    La, _, ga, _ = oracle.step(scene, cams[:1], targets[:1], prm, scenes.GAMMA)
+    Lb, _, gb, _ = oracle.step(scene, cams[1:], targets[1:], prm, scenes.GAMMA)
+    assert L2 == pytest.approx(0.5 * (La + Lb), rel=1e-13)
+    # the pooled mean would weight the larger view by its pixel share instead
+    pooled = (48 * 32 * La + 24 * 40 * Lb) / (48 * 32 + 24 * 40)
+    assert abs(L2 - pooled) > 1e-6 * abs(L2)
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        want = 0.5 * (np.asarray(ga[k]) + np.asarray(gb[k]))
+        assert np.allclose(np.asarray(g2[k]), want, rtol=1e-11, atol=1e-15), k
+
+
 def test_fov_clamp_linearises_at_the_clamped_direction():
     """Outside the clamped field of view the EWA Jacobian is the pinhole
     Jacobian at the camera-space point whose x/z (y/z) is clamped to
