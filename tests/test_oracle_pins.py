@@ -560,6 +560,33 @@ def test_views_average_per_view_means():
         assert np.allclose(np.asarray(g2[k]), want, rtol=1e-11, atol=1e-15), k
 
 
+def test_negative_colour_clamps_to_zero_and_masks_its_gradient():
+    """Reading c9: rgb = Y00 sh0 + 0.5 is clamped below at 0.  A Gaussian
+    whose red DC term makes red negative adds no red to the image and gets an
+    exact zero gradient on that coefficient, while its green coefficient
+    (unclamped) gets the chain-rule value, matched by a central difference."""
+    y00 = 1 / (2 * math.sqrt(math.pi))
+    sh0 = (-1.0 / y00, 0.3 / y00, 0.2 / y00)  # rgb = (-0.5, 0.8, 0.7)
+    scene = _one((0.0, 0.0, 3.0), [math.log(0.1)] * 3, (1.0, 0.0, 0.0, 0.0), 1.0, sh0=sh0)
+    cam = scenes.camera(32, 32, 32.0)
+    prm = scenes.params()
+    target = [np.full((32, 32, 3), 0.25, np.float32)]
+    L, views, g, _ = oracle.step(scene, [cam], target, prm, scenes.GAMMA)
+    img = views[0]["fwd"]["image"]
+    assert (img[..., 0] == 0).all() and img[..., 1].max() > 0.1
+    assert g["sh"][0, 0, 0] == 0.0 and abs(g["sh"][0, 0, 1]) > 1e-4
+    h = 1e-4
+    for ch, want in ((1, g["sh"][0, 0, 1]), (0, 0.0)):
+        vals = []
+        for sg in (1, -1):
+            sc = {k: (np.array(v, np.float64) if isinstance(v, np.ndarray) else v)
+                  for k, v in scene.items()}
+            sc["sh"][0, 0, ch] += sg * h
+            vals.append(oracle.step(sc, [cam], target, prm, scenes.GAMMA, with_grad=False)[0])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - want) <= 1e-6 * max(abs(want), 1e-3), (ch, fd, want)
+
+
 def test_fov_clamp_linearises_at_the_clamped_direction():
     """Outside the clamped field of view the EWA Jacobian is the pinhole
     Jacobian at the camera-space point whose x/z (y/z) is clamped to
