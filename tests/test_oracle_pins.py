@@ -539,6 +539,18 @@ def test_loss_definition():
     assert dH == pytest.approx(np.full((5, 7), 0.5 * 0.015 / M), rel=1e-15)
 
 
+def test_l1_gradient_is_zero_where_image_equals_target():
+    """Reading c15: sign(0) = 0, so a pixel channel that equals its target
+    contributes no L1 gradient (the subgradient the definition picks)."""
+    rng = np.random.default_rng(1)
+    tgt = rng.random((4, 6, 3)).astype(np.float32)
+    img = tgt.astype(np.float64).copy()
+    img[:2] += 0.1  # rows 0-1 above the target, rows 2-3 equal to it
+    _, dC, _ = oracle.loss(img, np.zeros((4, 6)), tgt, 0.015, 1.0)
+    assert (dC[2:] == 0).all()
+    assert np.allclose(dC[:2], 1.0 / (3 * 24), rtol=1e-15)
+
+
 def test_views_average_per_view_means():
     """Reading c4: with several views the loss is the mean over views of each
     view's own pixel means (not one mean over the pooled pixels), and so are
