@@ -715,3 +715,35 @@ def test_loss_base_reduces_and_differentiates():
         fd = (oracle.loss_base(ip, ent, tgt, 0.015, lam)[0] -
               oracle.loss_base(im, ent, tgt, 0.015, lam)[0]) / (2 * h)
         assert fd == pytest.approx(dC[idx], rel=1e-5, abs=1e-9)
+
+
+# --------------------------------------------------------------------------
+# Regression: the oracle's outputs on two small scenes, as stored by
+# tests/golden/make_oracle_regression.py (which calls only the oracle).  The
+# pins above tie the oracle to the paper; this ties it to itself over time, so
+# that a change of its arithmetic is seen and has to be justified.
+# --------------------------------------------------------------------------
+
+def test_oracle_outputs_unchanged_on_stored_cases():
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    stored = json.load(open(os.path.join(here, "oracle_regression_tiny.json")))
+    for c in stored["cases"]:
+        scene, cams, targets, prm = scenes.tiny_scene(8, seed=c["seed"], width=40, height=36,
+                                                      sh_degree=c["sh_degree"])
+        prm["tile"] = c["tile"]
+        L, views, grads, _ = oracle.step(scene, cams, targets, prm, scenes.GAMMA)
+        f = views[0]["fwd"]
+        assert L == pytest.approx(c["loss"], rel=1e-12)
+        assert float(np.sum(f["image"])) == pytest.approx(c["image_sum"], rel=1e-12)
+        assert float(np.sum(f["final_T"])) == pytest.approx(c["final_T_sum"], rel=1e-12)
+        assert float(np.sum(f["entropy"])) == pytest.approx(c["entropy_sum"], rel=1e-12)
+        assert int(np.sum(f["last"])) == c["last_sum"]
+        y, x = c["brightest_pixel"]
+        assert list(f["image"][y, x]) == pytest.approx(c["brightest_rgb"], rel=1e-12)
+        K = (c["sh_degree"] + 1) ** 2
+        for k, want in c["grads"].items():
+            got = np.asarray(grads[k])
+            got = (got[:, :K] if k == "sh" else got).ravel()
+            np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-15, err_msg=k)
