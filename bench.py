@@ -17,10 +17,14 @@ launch count and the SM clocks sampled during the timed region.  Other modes:
 (list-length sweep), --train ITERS (training loop), --train-epochs E (epoch
 schedule with the resolution scheduler).
 
-Default workload (N=1): 1,000,000 Gaussians from 64 anisotropic clusters,
-SH degree 3, one 1237x822 view (the scene-scale configuration).
-Metric: blended Gaussian-pixels per second over the whole forward + backward
-step (higher is better); ms per step is reported alongside.
+Default workload (N=1): the batched configuration, 3,000,000 Gaussians
+seen from 8 views of uneven size (3 x 309x205, 3 x 618x411, 2 x 1237x822, a
+progressive-resolution mix) in one pipeline.  Metric: blended
+Gaussian-pixels per second over the whole forward + backward step (higher is
+better), ms per step alongside; the same line carries the plain form (one
+single-view FP32 pipeline per view), the FP16/BF16 staging forms and the other
+launch forms, each with its ms per step and its error against the FP64 oracle
+on view 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -72,10 +76,10 @@ def log(*a):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5"])
+    ap.add_argument("--config", default="cfg3", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5"])
     ap.add_argument("--attr", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--n", type=int, default=0,
                     help="override the configuration's Gaussian count (smaller cases for profiling)")
@@ -110,7 +114,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-band-rows", type=int, default=0,
                     help="tile rows of view 0 the CPU oracle sample renders (0 = the whole view)")
-    ap.add_argument("--ref-band-rows", type=int, default=8,
+    ap.add_argument("--ref-band-rows", type=int, default=2,
                     help="tile rows per step of the reference (oracle) arm")
     return ap.parse_args()
 
@@ -198,25 +202,31 @@ def summarise_clock_rows(lines):
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample of the workload
 # ---------------------------------------------------------------------------
-def oracle_sample(scene, cams, targets, prm, gamma, band_rows):
+def oracle_sample(scene, cams, targets, prm, gamma, band_rows, keep=False):
     """Runs the FP64 oracle's whole pipeline on a band of `band_rows` tile
     rows through the middle of view 0: projection of every Gaussian, the tile
-    lists, forward and backward on the band's pixels, and the projection
-    adjoint of every Gaussian that received a gradient.  Returns
-    (blended pairs, seconds, description)."""
+    lists of the band's tiles, forward and backward on the band's pixels, and
+    the projection adjoint of every Gaussian that received a gradient.
+    Returns (blended pairs, seconds, description[, reference]); with keep,
+    the reference holds the band mask, the oracle's image, final T and
+    entropy of view 0 and the pixels whose FP32 result may take the other
+    branch of a threshold test (excluded from the error statement)."""
     import oracle
     cam = cams[0]
     W, H = cam["width"], cam["height"]
-    TY = (H + 15) // 16
+    T = int(prm.get("tile", 16))
+    TX, TY = (W + T - 1) // T, (H + T - 1) // T
     if band_rows <= 0 or band_rows > TY:
         band_rows = TY
     t_start = max(0, TY // 2 - band_rows // 2)
-    rows = np.arange(H) // 16
+    rows = np.arange(H) // T
     band = (rows >= t_start) & (rows < t_start + band_rows)
     mask = np.repeat(band[:, None], W, axis=1)
+    tmask = np.zeros((TY, TX), bool)
+    tmask[t_start:t_start + band_rows] = True
     t0 = time.perf_counter()
     proj = oracle.preprocess(scene, cam, prm)
-    lists = oracle.build_lists(proj, cam)
+    lists = oracle.build_lists(proj, cam, tile_mask=None if band_rows == TY else tmask)
     fwd = oracle.render_fwd(proj, lists, cam, prm, mask=mask)
     M = W * H
     dC = np.where(fwd["image"] - targets[0] > 0, 1.0, -1.0) / (3 * M)
@@ -227,11 +237,40 @@ def oracle_sample(scene, cams, targets, prm, gamma, band_rows):
     oracle.preprocess_bwd(scene, cam, prm, g9, gmask=touched)
     dt = time.perf_counter() - t0
     nb = int(fwd["nblend"][mask].sum())
-    desc = ("FP64 oracle, %d tile rows (%d of %d pixels) of view 0: projection of all %d "
-            "Gaussians, lists, fwd+bwd on the band, projection adjoint of the %d Gaussians "
-            "with a gradient" % (band_rows, int(mask.sum()), M, scene["means"].shape[0],
-                                 int(touched.sum())))
-    return nb, dt, desc
+    desc = ("FP64 oracle, %d tile rows (%d of %d pixels) of view 0 (%dx%d): projection of all "
+            "%d Gaussians, the band's lists, fwd+bwd on the band, projection adjoint of the %d "
+            "Gaussians with a gradient" % (band_rows, int(mask.sum()), M, W, H,
+                                           scene["means"].shape[0], int(touched.sum())))
+    if not keep:
+        return nb, dt, desc
+    # threshold-boundary exclusions (from the oracle alone): pixels with a
+    # threshold test within 1e-4 (relative) of its limit, and pixels whose
+    # walk meets a Gaussian that an FP32 rounding may add to or drop from
+    # their tile's list
+    from oracle import exclusions
+    view = {"proj": proj, "lists": lists, "fwd": fwd}
+    excl = exclusions.pixel_exclusion(view, cam, prm=prm) & mask
+    summ = exclusions.summary(view, cam, mask, prm=prm)
+    summ["flagged_ids"] = summ["flagged_ids"][:32]
+    ref = {"mask": mask, "image": fwd["image"], "final_T": fwd["final_T"],
+           "entropy": fwd["entropy"], "excluded": excl,
+           "exclusions": dict(summ, view=0)}
+    return nb, dt, desc, ref
+
+
+def view0_error(ref, image, final_T, entropy):
+    """Largest absolute difference from the FP64 oracle over the compared
+    pixels of view 0 (device tensors of the whole pipeline; view 0 comes
+    first), per output."""
+    H, W = ref["mask"].shape
+    n = W * H
+    ok = ref["mask"] & ~ref["excluded"]
+    img = image[:n].detach().cpu().numpy().astype(np.float64).reshape(H, W, 3)
+    t = final_T[:n].detach().cpu().numpy().astype(np.float64).reshape(H, W)
+    h = entropy[:n].detach().cpu().numpy().astype(np.float64).reshape(H, W)
+    return {"image": float(np.abs(img - ref["image"])[ok].max()),
+            "final_T": float(np.abs(t - ref["final_T"])[ok].max()),
+            "entropy": float(np.abs(h - ref["entropy"])[ok].max())}
 
 
 def run_reference(args):
@@ -512,37 +551,70 @@ def run_train_schedule(args, dev):
 
 def time_variant(make, p, tgt, gamma, flush, steps, warmup=2):
     """Mean ms per fwd+bwd step (projection .. adjoint) of the rasterizers
-    `make()` returns (run back to back: one per view for the per-view form)."""
+    `make()` returns (run back to back: one per view for the per-view form),
+    each step captured once in a CUDA graph and replayed (the headline's
+    timed form), L2 flushed before every replay.  Returns (ms, the first
+    rasterizer, which holds view 0's forward outputs of the last step)."""
     import torch
     rs = make()
-    for _ in range(warmup):
+
+    def one(sync):
         for r in rs:
             r.preprocess(p)
-            r.bin_sort(sync=True)
+            r.bin_sort(sync=sync)
             r.render_fwd()
             r.loss(tgt[r], gamma) if isinstance(tgt, dict) else r.loss(tgt, gamma)
             r.render_bwd(p)
+
+    for _ in range(warmup):
+        one(True)  # sizes the pair buffers
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            one(False)
+    torch.cuda.current_stream().wait_stream(s)
+    g.replay()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ms = []
     for k in range(steps):
         flush.fill_(float(k))
         a.record()
-        for r in rs:
-            r.preprocess(p)
-            r.bin_sort(sync=False)
-            r.render_fwd()
-            r.loss(tgt[r], gamma) if isinstance(tgt, dict) else r.loss(tgt, gamma)
-            r.render_bwd(p)
+        g.replay()
         b.record()
         b.synchronize()
         ms.append(a.elapsed_time(b))
     if any(int(r.status_dev.item()) != 0 for r in rs):
         raise RuntimeError("pair capacity overflow in a variant")
     out = float(np.mean(ms))
-    del rs
-    torch.cuda.empty_cache()
-    return out
+    del g
+    return out, rs
+
+
+def sm_count(dev):
+    import torch
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+
+def fp32_peak_tflops(dev, clocks):
+    """FP32 peak of the device: SMs x 128 FP32 lanes x 2 flop x the largest
+    SM clock seen (the sampled maximum, else the measured peaks file's, else
+    2070 MHz).  Returns (TFLOP/s, description)."""
+    mhz = None
+    if clocks and clocks.get("sm_max_mhz"):
+        mhz, src = float(clocks["sm_max_mhz"]), "sampled max SM clock"
+    else:
+        try:
+            mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+            src = "measured peaks file's max SM clock"
+        except (OSError, ValueError, KeyError):
+            mhz, src = 2070.0, "2070 MHz (nominal max SM clock)"
+    sms = sm_count(dev)
+    return (sms * 128 * 2 * mhz * 1e6 / 1e12,
+            "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s)" % (sms, mhz, src))
 
 
 def rank_totals(t_local, units_local, world, dev):
@@ -743,6 +815,9 @@ def main():
     status = int(r.status_dev.item())
     if status != 0:
         raise RuntimeError("pair capacity overflow in the timed region (status %d)" % status)
+    # view-0 outputs of the timed form, for its error against the oracle
+    n0 = cams[0]["width"] * cams[0]["height"]
+    main_out = (r.image[:n0].clone(), r.final_T[:n0].clone(), r.entropy[:n0].clone())
     step_ms = [a.elapsed_time(b) for a, b in gev]
     t_total, nb_all = rank_totals(sum(step_ms) / 1000.0, nb_step, world, dev)
     value = nb_all * K / t_total
@@ -750,7 +825,7 @@ def main():
 
     # roofline of the dominant kernel (blending forward or backward)
     fwd_ms, bwd_ms = phase["render_fwd_kernel"], phase["render_bwd_kernel"]
-    peak = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 TFLOP/s at the maximum SM clock
+    peak, peak_src = fp32_peak_tflops(dev, clocks)
     if bwd_ms >= fwd_ms:
         kname, kms = "render_bwd_kernel", bwd_ms
         flops = BWD_EVAL * bwd_eval + BWD_BLEND * nb_step
@@ -762,7 +837,7 @@ def main():
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": (traffic_from_profiles(kname, args.config)
                             if not args.n and args.tile == 16 and args.attr == "f32" else None),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "peak_source": peak_src,
                 "flops_per_launch": flops}
 
     # per-phase times replayed alone from graphs, and the rooflines of the
@@ -871,44 +946,67 @@ def main():
         e2e = run_e2e(False)
         e2e_full = run_e2e(True)
 
+    # the FP64 oracle on view 0 (the CPU baseline); its view-0 outputs are
+    # also the reference for the error each form below states
+    cpu, ref = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        nb_c, dt_c, desc, ref = oracle_sample(scene, cams, targets, prm, gamma,
+                                              args.cpu_band_rows, keep=True)
+        cpu = {"value": nb_c / dt_c, "unit": UNIT, "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": desc, "seconds": dt_c}
+    main_err = view0_error(ref, *main_out) if ref is not None else None
+
     # launch forms and staging precisions on the same workload ("batched +
-    # mixed vs plain"): fwd+bwd ms per step, no scale reset, L2 flushed
+    # mixed vs plain"): fwd+bwd ms per step (graph replay, no scale reset, L2
+    # flushed), each with its error against the FP64 oracle on view 0
     variants = None
     if world == 1 and not args.no_variants:
         KV = max(5, min(20, K))
         variants = {}
         V = len(cams)
-        forms = [("plain_f32", dict()), ("persistent_f32", dict(persistent=152 * 8)),
-                 ("plain_f16", dict(attr_dtype="f16")), ("plain_bf16", dict(attr_dtype="bf16")),
-                 ("persistent_bf16", dict(persistent=152 * 8, attr_dtype="bf16")),
-                 ("plain_f32_1px", dict(pixels_per_thread=1))]
-        if args.tile == 16:
-            forms += [("plain_f32_4px", dict(pixels_per_thread=4)),
-                      ("plain_f32_batch128", dict(batch=128))]
-        for name, kw in forms:
-            variants[name] = time_variant(
-                lambda kw=kw: [Rasterizer(cams, prm, N, device=dev, pair_capacity=r.capacity,
-                                          **kw)], p, tgt, gamma, flush, KV)
+        pers = 8 * sm_count(dev)
+        forms = []
         if V > 1:
-            # the unbatched form: one single-view pipeline per view, back to back
+            # the plain, unbatched form: one single-view FP32 pipeline per
+            # view, back to back (each call of the per-view adjoint overwrites
+            # the gradients; a training step would add them up)
             offs = np.cumsum([0] + [c["width"] * c["height"] for c in cams])
 
             def per_view():
-                rs = [Rasterizer([c], prm, N, device=dev) for c in cams]
-                return rs
-            rs_probe = per_view()
-            tg = {rr: tgt[offs[v]:offs[v + 1]] for v, rr in enumerate(rs_probe)}
-            variants["per_view_f32"] = time_variant(lambda: rs_probe, p, tg, gamma, flush, KV)
-        variants = {k: {"ms_per_step": v, "value": nb_all / (v / 1000.0)}
-                    for k, v in variants.items()}
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        nb_c, dt_c, desc = oracle_sample(scene, cams, targets, prm, gamma, args.cpu_band_rows)
-        cpu = {"value": nb_c / dt_c, "unit": UNIT, "cores": oracle.num_threads(),
-               "kind": "oracle", "sample": desc, "seconds": dt_c}
+                return [Rasterizer([c], prm, N, device=dev) for c in cams]
+            forms.append(("per_view_f32", per_view, "views"))
+        # the one-pipeline forms (all views in each launch: batched when V > 1)
+        pre = "batched" if V > 1 else "plain"
+        forms += [(pre + "_f32", dict(form), None),
+                  (pre + "_f16", dict(form, attr_dtype="f16"), None),
+                  (pre + "_bf16", dict(form, attr_dtype="bf16"), None),
+                  ("persistent_f32", dict(form, persistent=pers), None),
+                  ("persistent_bf16", dict(form, persistent=pers, attr_dtype="bf16"), None),
+                  (pre + "_f32_1px", dict(form, pixels_per_thread=1), None)]
+        if args.tile == 16:
+            forms += [(pre + "_f32_4px", dict(form, pixels_per_thread=4), None)]
+            if form.get("batch", 256) != 128:
+                forms += [(pre + "_f32_batch128", dict(form, batch=128), None)]
+        for name, kw, kind in forms:
+            if kind == "views":
+                rs_probe = kw()
+                tg = {rr: tgt[offs[v]:offs[v + 1]] for v, rr in enumerate(rs_probe)}
+                ms_v, rs = time_variant(lambda: rs_probe, p, tg, gamma, flush, KV)
+            else:
+                if kw.get("attr_dtype", "f32") != "f32" and kw.get("batch") == 128:
+                    kw = dict(kw, batch=256)  # the 128-entry batch exists for F32 records
+                ms_v, rs = time_variant(
+                    lambda kw=kw: [Rasterizer(cams, prm, N, device=dev, pair_capacity=r.capacity,
+                                              **kw)], p, tgt, gamma, flush, KV)
+            ent = {"ms_per_step": ms_v, "value": nb_all / (ms_v / 1000.0)}
+            if ref is not None:
+                ent["err_vs_oracle_view0"] = view0_error(ref, rs[0].image, rs[0].final_T,
+                                                         rs[0].entropy)
+            variants[name] = ent
+            del rs
+            torch.cuda.empty_cache()
 
     if world > 1:
         dist.barrier()
@@ -935,6 +1033,8 @@ def main():
             "phases_ms": phase,
             "phases_graph_ms": pg,
             "phase_roofline": phase_roofline,
+            "error_vs_oracle_view0": main_err,
+            "exclusions_view0": ref["exclusions"] if ref is not None else None,
             "variants": variants,
             "roofline": roofline,
             "cpu_baseline": cpu,

@@ -312,8 +312,10 @@ int gs_tile_queue(const unsigned* tile_ranges, long long total_tiles, unsigned* 
  *   total_tiles > GS_TILE_QUEUE_STATIC_MAX_TILES: GS_ERR_INVALID_ARG, with the
  *   limit in gs_last_error_string(), before anything is enqueued.
  * The first call on a device looks up the scratch array's device address on
- * the current device (cudaGetSymbolAddress) and caches it; make that first
- * call before any stream capture on that device.
+ * the current device (cudaGetSymbolAddress) and caches it with the id of
+ * the current CUDA context; a call in another context of that device (after
+ * cudaDeviceReset, say) looks it up again.  Make the first call in a context
+ * before any stream capture in it.
  * All calls share the one array and it keeps the last call's contents (no
  * part needs to start at zero: a call writes every word before reading it).
  * Calls whose work overlaps on the GPU (different streams without ordering,

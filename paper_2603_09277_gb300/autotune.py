@@ -19,17 +19,26 @@ import torch
 from .rasterize import Rasterizer
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
-SMS = 152
-CANDIDATES = [
+# per-tile forms; the persistent forms are added with grids of 8 and 4 CTAs
+# per SM of the device in use
+BASE_CANDIDATES = [
     {"pixels_per_thread": 1, "persistent": 0, "batch": 256},
     {"pixels_per_thread": 2, "persistent": 0, "batch": 256},
     {"pixels_per_thread": 4, "persistent": 0, "batch": 256},
     {"pixels_per_thread": 2, "persistent": 0, "batch": 128},
     {"pixels_per_thread": 4, "persistent": 0, "batch": 128},
-    {"pixels_per_thread": 2, "persistent": SMS * 8, "batch": 256},
-    {"pixels_per_thread": 4, "persistent": SMS * 8, "batch": 256},
-    {"pixels_per_thread": 2, "persistent": SMS * 4, "batch": 256},
 ]
+PERSISTENT_PER_SM = [(2, 8), (4, 8), (2, 4)]  # (pixels per thread, CTAs per SM)
+
+
+def sm_count():
+    """Streaming multiprocessors of the current CUDA device (read at run time;
+    152 on a GB300), the unit of the persistent grid sizes.  Without a device
+    (host-side tests) the GB300 count."""
+    if torch.cuda.is_available():
+        return int(torch.cuda.get_device_properties(torch.cuda.current_device())
+                   .multi_processor_count)
+    return 152
 
 
 def signature(cams, N, attr_dtype, tile=16):
@@ -45,7 +54,10 @@ def candidates(tile=16, attr_dtype="f32"):
     """Launch forms to try; 8-pixel tiles take 1 or 2 pixels per thread (a
     CTA of one tile must hold at least one full warp); the 128-entry batch
     exists for F32 records on 16-pixel tiles."""
-    return [f for f in CANDIDATES
+    sms = sm_count()
+    pool = BASE_CANDIDATES + [{"pixels_per_thread": ppt, "persistent": sms * k, "batch": 256}
+                              for ppt, k in PERSISTENT_PER_SM]
+    return [f for f in pool
             if (tile == 16 or f["pixels_per_thread"] <= 2)
             and (f["batch"] == 256 or (tile == 16 and attr_dtype == "f32"))]
 

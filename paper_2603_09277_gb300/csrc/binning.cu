@@ -29,6 +29,8 @@
 // synchronisation needed).  None of them waits on another block: where a
 // single-block scan follows a kernel, the kernel's last block to finish runs
 // it (each block counts its arrival after a __threadfence).
+#include <cuda.h>
+
 #include <algorithm>
 #include <mutex>
 
@@ -1507,11 +1509,45 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_queue_scratch_mutex;
-void* g_queue_scratch_ptr[kMaxDevices] = {};
+struct ScratchAddr {
+  unsigned long long ctx_id;  // context the address belongs to (0: none yet)
+  void* ptr;
+};
+ScratchAddr g_queue_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_queue_scratch on the current device, looked up once per
-// device (in host code the array's name is only a stand-in, not a device
-// address).
+// Unique id of the calling thread's current CUDA context (ids are never
+// reused within a process), through the driver entry points the runtime
+// exposes; 0 when there is no current context or the query is unavailable.
+unsigned long long current_context_id() {
+  typedef CUresult (*GetCurrent)(CUcontext*);
+  typedef CUresult (*GetId)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    cudaGetLastError();
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx ||
+      get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of g_queue_scratch in the current device's context (in host
+// code the array's name is only a stand-in, not a device address).  Looked
+// up once per device and context: a device reset or a new primary context
+// (the module is then loaded again, at another address) brings a new lookup.
 int queue_scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1519,13 +1555,17 @@ int queue_scratch_address(void** out) {
   if (dev < 0 || dev >= kMaxDevices)
     return gs::set_error_text_and_status("unsupported device index", GS_ERR_UNSUPPORTED);
   std::lock_guard<std::mutex> lock(g_queue_scratch_mutex);
-  if (!g_queue_scratch_ptr[dev]) {
+  ScratchAddr& a = g_queue_scratch_addr[dev];
+  unsigned long long ctx = current_context_id();
+  if (!a.ptr || ctx == 0 || ctx != a.ctx_id) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_queue_scratch);
+    e = cudaGetSymbolAddress(&p, g_queue_scratch);  // makes the primary context current if needed
     if (e != cudaSuccess) return gs::set_cuda_error(e);
-    g_queue_scratch_ptr[dev] = p;
+    if (ctx == 0) ctx = current_context_id();
+    a.ptr = p;
+    a.ctx_id = ctx;
   }
-  *out = g_queue_scratch_ptr[dev];
+  *out = a.ptr;
   return GS_OK;
 }
 

@@ -1,26 +1,35 @@
 """Shared helpers of the GPU parity tests: run the libgs path through the
-C ABI, run the oracle, and derive the threshold-boundary exclusions.
+C ABI, run the oracle, and apply the threshold-boundary exclusions.
 
-Exclusion rules (from the oracle only, never from the GPU results):
+Exclusion rules (oracle.exclusions, from the oracle only, never from the GPU
+results):
 - a Gaussian whose rect could round differently in FP32 (oracle boundary
-  flag) is left out of the bit-exact rect/list checks, and the tiles that
-  lie in some but not every rect reachable under the rounding bands are
-  left out of the pixel checks (their lists may hold one entry more or less);
+  flag) is left out of the bit-exact rect/list checks; a pixel of a tile
+  that lies in some but not every rect reachable under the rounding bands
+  is left out of the pixel checks when its walk meets that Gaussian (does
+  not stop before the Gaussian's place in the depth order) and the
+  Gaussian's alpha reaches alpha_min there;
 - a pixel whose smallest relative distance of any threshold test
   (alpha_min, alpha_max, t_min) is below MARGIN may take the other branch in
   FP32 and is left out of the pixel checks;
 - gradients are compared per tensor on the relative norm, and element-wise
-  on the Gaussians that no excluded pixel evaluates.
+  (1e-4 relative with a floor of 1e-6 of the tensor's largest entry), on the
+  Gaussians that no excluded pixel's decision can change.
 """
 import numpy as np
 import torch
 
 import oracle
+import oracle.exclusions as _exc
 from paper_2603_09277_gb300.rasterize import Rasterizer, scene_to_device, targets_to_device
 
 MARGIN = 1e-4       # relative threshold margin below which a pixel is excluded
 IMG_TOL = 1e-5      # absolute, images / T / entropy (FP32 vs FP64)
 GRAD_TOL = 1e-4     # relative, gradient tensors (norm), FP32 vs FP64
+# element-wise gradient floor: 1e-6 of the tensor's largest entry (the
+# gradients of a pixel-mean loss scale with 1 / pixels, so the floor is
+# stated relative to the tensor; it is below 1e-6 absolute on every workload)
+ELEM_FLOOR = 1e-6
 
 
 def run_gpu(scene, cams, prm, target=None, gamma=0.015, attr="f32", persistent=0,
@@ -84,33 +93,9 @@ def view_tiles(cams, tile=16):
 
 
 def pixel_exclusion(ora_view, cam, margin=MARGIN):
-    """Boolean [H,W]: pixels left out of the pixel checks of one view."""
-    proj, fwd = ora_view["proj"], ora_view["fwd"]
-    W, H = cam["width"], cam["height"]
-    T = proj.get("tile", 16)
-    TX, TY = oracle.tile_grid(cam, {"tile": T})
-    bad_tiles = np.zeros((TY, TX), bool)
-    amin = float(np.float32(1.0 / 255))
-    for i in np.nonzero(proj["boundary"])[0]:
-        # tiles that are in some reachable rect but not in every one ...
-        hx0, hy0, hx1, hy1 = proj["rect_hi"][i]
-        lx0, ly0, lx1, ly1 = proj["rect_lo"][i]
-        m = np.zeros((TY, TX), bool)
-        m[hy0:hy1, hx0:hx1] = True
-        if lx1 > lx0 and ly1 > ly0:
-            m[ly0:ly1, lx0:lx1] = False
-        # ... and where the Gaussian's alpha reaches alpha_min at some pixel
-        # (elsewhere it is skipped whether or not it is listed)
-        g = proj["P9"][i]
-        for ty, tx in zip(*np.nonzero(m)):
-            u = np.arange(tx * T, min(W, tx * T + T)) + 0.5 - g[0]
-            v = np.arange(ty * T, min(H, ty * T + T)) + 0.5 - g[1]
-            du, dv = np.meshgrid(u, v)
-            a = g[5] * np.exp(-0.5 * (g[2] * du * du + 2 * g[3] * du * dv + g[4] * dv * dv))
-            if a.max() >= amin * (1 - margin):
-                bad_tiles[ty, tx] = True
-    px_tiles = bad_tiles[np.arange(H)[:, None] // T, np.arange(W)[None, :] // T]
-    return px_tiles | (fwd["margin"] < margin)
+    """Boolean [H,W]: pixels left out of the pixel checks of one view (the
+    rule of oracle.exclusions, from the oracle's outputs alone)."""
+    return _exc.pixel_exclusion(ora_view, cam, margin)
 
 
 def last_ids_gpu(g, cams, v, N, tile_px=16):
@@ -148,29 +133,22 @@ def last_ids_oracle(view, cam):
 
 def gaussian_exclusion(ora_view, cam, bad_pixels):
     """Boolean [N]: Gaussians whose gradient an FP32 threshold decision may
-    change by more than the tolerance: the boundary-flagged ones; at a pixel
-    with a near-threshold test, the entry at the first near-threshold list
-    position and the next two (a flipped skip or clamp changes that entry's
-    own contribution entirely; later entries only through T, by a factor
-    within alpha_min of 1, and a flipped stop adds entries of weight below
-    t_min); at a pixel of a tile whose list may gain or lose a flagged
-    Gaussian of visible alpha, the whole list."""
-    proj, fwd = ora_view["proj"], ora_view["fwd"]
-    ts, ids = ora_view["lists"]
-    T = proj.get("tile", 16)
-    TX, TY = oracle.tile_grid(cam, {"tile": T})
-    bad = proj["boundary"].astype(bool).copy()
-    margin_bad = fwd["margin"] < MARGIN
-    ys, xs = np.nonzero(bad_pixels)
-    for y, x in zip(ys, xs):
-        t = (y // T) * TX + x // T
-        fn = int(fwd["first_near"][y, x])
-        if margin_bad[y, x] and fn >= 0:
-            bad[ids[ts[t] + fn:min(ts[t + 1], ts[t] + fn + 3)]] = True
-        else:
-            bad[ids[ts[t]:ts[t + 1]]] = True
-    return bad
+    change by more than the tolerance (oracle.exclusions)."""
+    return _exc.gaussian_exclusion(ora_view, cam, bad_pixels, MARGIN)
 
 
 def rel_norm_err(a, b):
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def elementwise_violations(g, o):
+    """Entries of a gradient tensor outside the element-wise bar
+    |g - o| <= GRAD_TOL |o| + ELEM_FLOOR max|o|; returns (count, worst ratio
+    of the difference to its bound)."""
+    g = np.asarray(g, np.float64).ravel()
+    o = np.asarray(o, np.float64).ravel()
+    if o.size == 0:
+        return 0, 0.0
+    bound = GRAD_TOL * np.abs(o) + ELEM_FLOOR * np.abs(o).max()
+    ratio = np.abs(g - o) / np.maximum(bound, 1e-300)
+    return int((ratio > 1.0).sum()), float(ratio.max())

@@ -124,7 +124,7 @@ def test_autotune_candidates_exist_for_the_workload():
                 assert f["pixels_per_thread"] in (1, 2, 4) and f["batch"] in (128, 256)
                 assert tile == 16 or f["pixels_per_thread"] <= 2
                 assert f["batch"] == 256 or (tile == 16 and attr == "f32")
-                assert f["persistent"] % autotune.SMS == 0
+                assert f["persistent"] % autotune.sm_count() == 0
     c = autotune.candidates(16, "f32")
     assert {f["batch"] for f in c} == {128, 256}
     assert len({f["persistent"] for f in c if f["persistent"]}) >= 2

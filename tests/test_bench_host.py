@@ -21,7 +21,8 @@ def test_defaults_one_gpu_and_enough_warmup(monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py"])
     a = bench.parse()
     assert a.gpus == 1 and a.warmup >= 3 and a.steps >= 1
-    assert a.impl == "ours" and a.config == "cfg2" and a.attr == "f32" and a.tile == 16
+    # the metric's configuration: the batched workload of 8 views of uneven size
+    assert a.impl == "ours" and a.config == "cfg3" and a.attr == "f32" and a.tile == 16
     assert a.batch == 0 and a.ppt == 0 and a.persistent == 0
 
 
@@ -119,3 +120,27 @@ def test_autotune_picks_the_fastest_form_and_caches_it(tmp_path, monkeypatch):
     assert best16["batch"] == 256 and not any("_b128_" in k for k in ms16)
     db = json.load(open(tmp_path / "autotune.json"))
     assert len(db) == 2 and all("GB300 (fake)" in k for k in db)
+
+
+def test_view0_error_leaves_out_excluded_and_other_pixels():
+    """The error a form states is the largest difference over the compared
+    pixels of view 0 only: pixels outside the oracle's band, excluded pixels
+    and pixels of later views do not count."""
+    torch = pytest.importorskip("torch")
+    H, W = 4, 5
+    mask = np.zeros((H, W), bool)
+    mask[1:3] = True
+    excl = np.zeros((H, W), bool)
+    excl[1, 0] = True
+    ref = {"mask": mask, "excluded": excl, "image": np.zeros((H, W, 3)),
+           "final_T": np.ones((H, W)), "entropy": np.zeros((H, W))}
+    img = torch.zeros(H * W + 7, 3)
+    img[W * 1 + 0] = 5.0          # excluded pixel
+    img[0] = 3.0                  # outside the band
+    img[H * W + 2] = 9.0          # a later view
+    img[W * 2 + 3, 1] = 0.25      # compared
+    T = torch.ones(H * W + 7)
+    T[W * 1 + 1] = 0.5
+    h = torch.zeros(H * W + 7)
+    e = bench.view0_error(ref, img, T, h)
+    assert e == {"image": 0.25, "final_T": 0.5, "entropy": 0.0}

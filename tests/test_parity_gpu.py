@@ -12,8 +12,9 @@ torch = pytest.importorskip("torch")
 import oracle
 from paper_2603_09277_gb300 import scenes
 
-from parity_util import (GRAD_TOL, IMG_TOL, gaussian_exclusion, last_ids_gpu, last_ids_oracle,
-                         pixel_exclusion, rel_norm_err, run_gpu, view_pixels, view_tiles)
+from parity_util import (GRAD_TOL, IMG_TOL, elementwise_violations, gaussian_exclusion,
+                         last_ids_gpu, last_ids_oracle, pixel_exclusion, rel_norm_err, run_gpu,
+                         view_pixels, view_tiles)
 
 pytestmark = pytest.mark.gpu
 
@@ -121,11 +122,10 @@ def check_grads(g, ora_grads, views, cams, N, K):
         res[k] = e
         assert e <= GRAD_TOL, (k, e)
         assert rel_norm_err(gg, oo) <= 1e-2, k
-        scale = np.abs(oo[ok]).max()
-        d = np.abs(gg[ok] - oo[ok])
-        # element-wise: 1e-4 relative with an absolute floor of 1e-4 of the
-        # tensor's largest entry (atomic summation order in FP32)
-        assert (d <= GRAD_TOL * np.abs(oo[ok]) + GRAD_TOL * scale).all(), k
+        # element-wise: 1e-4 relative with a floor of 1e-6 of the tensor's
+        # largest entry (atomic summation order in FP32)
+        nv, worst = elementwise_violations(gg[ok], oo[ok])
+        assert nv == 0, (k, nv, worst)
     return res
 
 
@@ -493,51 +493,96 @@ def test_cfg2_projection_and_lists(cfg2_case):
     check_lists(g, views, cams, N)
 
 
-def test_cfg2_sampled_pixels_and_gradients(cfg2_case):
+def test_cfg2_sampled_pixels(cfg2_case):
+    """20,000 random pixels of the full-size view: images, final T and
+    entropy within 1e-5, the same last blended Gaussian.  Also the measured
+    FP32 error behind the exclusion bands: the largest relative error of the
+    final transmittance (the running T of the stop test T (1 - alpha) < t_min)
+    stays an order of magnitude inside MARGIN, and the 2D mean that places the
+    rect edges inside the oracle's edge band."""
+    from parity_util import MARGIN
     scene, cams, targets, prm, proj, lists = cfg2_case
     cam = cams[0]
     W, H = cam["width"], cam["height"]
     N = scene["means"].shape[0]
     rng = np.random.default_rng(0)
-    # Gaussians to check: visible, not flagged, small rect
-    cand = np.nonzero((proj["tiles"] > 0) & (proj["tiles"] <= 4) & (proj["boundary"] == 0))[0]
-    pick = rng.choice(cand, 24, replace=False)
-    TX, TY = oracle.tile_grid(cam)
-    tmask = np.zeros((TY, TX), bool)
-    for i in pick:
-        x0, y0, x1, y1 = proj["rect"][i]
-        tmask[y0:y1, x0:x1] = True
-    pmask = tmask[np.arange(H)[:, None] // 16, np.arange(W)[None, :] // 16]
-    # plus random pixels for the forward check
-    extra = np.zeros(H * W, bool)
-    extra[rng.choice(H * W, 3000, replace=False)] = True
-    fmask = pmask | extra.reshape(H, W)
+    fmask = np.zeros(H * W, bool)
+    fmask[rng.choice(H * W, 20000, replace=False)] = True
+    fmask = fmask.reshape(H, W)
     fwd = oracle.render_fwd(proj, lists, cam, prm, mask=fmask)
-    # oracle loss gradient on the masked pixels (fixed per-pixel weights of the full view)
-    M = W * H
-    dC = np.where(fwd["image"] - targets[0] > 0, 1.0, -1.0) / (3 * M)
-    dC[~fmask] = 0.0
-    dH = np.where(fmask, GAMMA / M, 0.0)
-    g9 = oracle.render_bwd(proj, lists, cam, prm, dC, dH, mask=pmask)
-    gm = np.zeros(N, np.uint8)
-    gm[pick] = 1
-    og = oracle.preprocess_bwd(scene, cam, prm, g9, gmask=gm)
-    g = run_gpu(scene, cams, prm, dL_dimage=dC.astype(np.float32), dL_dentropy=dH.astype(np.float32),
-                keys=False)
+    g = run_gpu(scene, cams, prm, keys=False)
     view = {"proj": proj, "lists": lists, "fwd": fwd}
     bad = pixel_exclusion(view, cam) | ~fmask
     ok = ~bad.reshape(-1)
-    assert ok.sum() > 2000
+    assert ok.sum() > 19000
     assert np.abs(g["image"][ok] - fwd["image"].reshape(-1, 3)[ok]).max() <= IMG_TOL
     assert np.abs(g["final_T"][ok] - fwd["final_T"].reshape(-1)[ok]).max() <= IMG_TOL
     assert np.abs(g["entropy"][ok] - fwd["entropy"].reshape(-1)[ok]).max() <= IMG_TOL
     assert (last_ids_gpu(g, cams, 0, N)[ok] == last_ids_oracle(view, cam)[ok]).all()
-    # gradients of the picked Gaussians: their whole footprint is inside pmask
+    To = fwd["final_T"].reshape(-1)[ok]
+    rel_T = float((np.abs(g["final_T"][ok] - To) / To).max())
+    vis = (proj["tiles"] > 0) & (proj["boundary"] == 0)
+    mean_err = float(np.abs(g["mean2d"][vis] - proj["P9"][vis, 0:2]).max())
+    print("cfg2 FP32 error: final T relative %.3g, 2D mean %.3g px" % (rel_T, mean_err))
+    assert rel_T <= 0.1 * MARGIN
+    assert mean_err <= 2e-4
+
+
+def test_cfg2_band_gradients_full_size(cfg2_case):
+    """Gradient parity at full size: the 12 tile rows of the cfg2 view that
+    hold the most pairs (its longest lists), every pixel of them rendered and
+    differentiated by the oracle, and every unflagged Gaussian whose rect lies
+    inside the band and that is reached there (its gradient is then complete)
+    compared with the GPU's, per tensor and element-wise.  Among them are
+    Gaussians with rects of 16 tiles and more and Gaussians reached at list
+    position 400 and deeper, where the backward's transmittance recovery by
+    division has run longest."""
+    scene, cams, targets, prm, proj, lists = cfg2_case
+    cam = cams[0]
+    W, H = cam["width"], cam["height"]
+    N = scene["means"].shape[0]
+    ts, ids = lists
+    TX, TY = oracle.tile_grid(cam)
+    L = np.diff(ts).reshape(TY, TX)
+    B = 12
+    rowsum = L.sum(1)
+    b0 = max(range(TY - B + 1), key=lambda b: rowsum[b:b + B].sum())
+    b1 = b0 + B
+    pmask = np.zeros((H, W), bool)
+    pmask[16 * b0:min(H, 16 * b1)] = True
+    fwd = oracle.render_fwd(proj, lists, cam, prm, mask=pmask)
+    M = W * H
+    dC = np.where(fwd["image"] - targets[0] > 0, 1.0, -1.0) / (3 * M)
+    dC[~pmask] = 0.0
+    dH = np.where(pmask, GAMMA / M, 0.0)
+    g9 = oracle.render_bwd(proj, lists, cam, prm, dC, dH, mask=pmask)
+    r = proj["rect"]
+    inside = (proj["tiles"] > 0) & (proj["boundary"] == 0) & (r[:, 1] >= b0) & (r[:, 3] <= b1)
+    view = {"proj": proj, "lists": lists, "fwd": fwd}
     badg = gaussian_exclusion(view, cam, pixel_exclusion(view, cam) & pmask)
-    use = pick[~badg[pick]]
-    assert len(use) >= 12
-    for k in ("means", "log_scales", "quats", "opacity_logits"):
-        e = rel_norm_err(g["grads"][k][use], og[k][use])
-        assert e <= GRAD_TOL, (k, e)
-    e = rel_norm_err(g["grads"]["sh"][use], og["sh"][use])
-    assert e <= GRAD_TOL
+    use = np.nonzero(inside & (np.abs(g9).sum(1) > 0) & ~badg)[0]
+    # deepest list position of each Gaussian in the band's lists
+    pos = np.zeros(N, np.int64)
+    for t in range(b0 * TX, b1 * TX):
+        seg = ids[ts[t]:ts[t + 1]]
+        pos[seg] = np.maximum(pos[seg], np.arange(len(seg)))
+    assert len(use) >= 500
+    assert (proj["tiles"][use] >= 16).sum() >= 100
+    assert (pos[use] >= 400).sum() >= 100 and fwd["last"][pmask].max() >= 500
+    gm = np.zeros(N, np.uint8)
+    gm[use] = 1
+    og = oracle.preprocess_bwd(scene, cam, prm, g9, gmask=gm)
+    g = run_gpu(scene, cams, prm, dL_dimage=dC.astype(np.float32),
+                dL_dentropy=dH.astype(np.float32), keys=False)
+    ok = ~(pixel_exclusion(view, cam) | ~pmask).reshape(-1)
+    assert np.abs(g["image"][ok] - fwd["image"].reshape(-1, 3)[ok]).max() <= IMG_TOL
+    rep = {}
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        gg, oo = g["grads"][k][use], og[k][use]
+        if k == "sh":
+            gg, oo = gg[:, :16], oo[:, :16]
+        e = rel_norm_err(gg, oo)
+        nv, worst = elementwise_violations(gg, oo)
+        rep[k] = (e, nv, worst)
+        assert e <= GRAD_TOL, rep
+        assert nv == 0, rep

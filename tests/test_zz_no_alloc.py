@@ -63,3 +63,35 @@ def test_static_queue_rejects_more_tiles_than_its_scratch_holds():
     assert "65536" in gs.gs_last_error_string()
     torch.cuda.synchronize()
     assert int(out.abs().sum().item()) == 0
+
+
+def test_static_queue_allocates_nothing_and_follows_its_stream():
+    """After a first call (which looks up the scratch address), a call leaves
+    the device's free memory unchanged; a call enqueued on a non-default
+    stream, ordered after the inputs by an event, gives the same order."""
+    from paper_2603_09277_gb300 import gs
+    T = 4056
+    lengths = np.random.default_rng(7).integers(0, 300, T)
+    ranges = _ranges(lengths, seed=7)
+    ref = _queue(gs, ranges, T)
+    got = torch.full((T,), -1, dtype=torch.int32, device="cuda")
+    assert gs.gs_tile_queue_static(ranges, T, got) == gs.GS_OK  # warm-up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    assert gs.gs_tile_queue_static(ranges, T, got) == gs.GS_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.equal(got, ref)
+    # on a side stream, after an event that follows the inputs' writes
+    s = torch.cuda.Stream()
+    side = torch.full((T,), -1, dtype=torch.int32, device="cuda")
+    ranges2 = ranges.clone()
+    ready = torch.cuda.Event()
+    ready.record()
+    s.wait_event(ready)
+    assert gs.gs_tile_queue_static(ranges2, T, side, stream=s) == gs.GS_OK
+    done = torch.cuda.Event()
+    done.record(s)
+    torch.cuda.current_stream().wait_event(done)
+    assert torch.equal(side, ref)
