@@ -311,7 +311,8 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 def traffic_from_profiles(kernel, config):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was captured on this workload from the current render source."""
+    was captured on this workload from the current source of the kernel's
+    file (csrc/<source>, render.cu unless the entry names another)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -319,10 +320,16 @@ def traffic_from_profiles(kernel, config):
         data = json.load(open(path))
     except ValueError:
         return None
-    src = os.path.join(ROOT, "paper_2603_09277_gb300", "csrc", "render.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     ent = data.get(kernel)
-    if not ent or ent.get("render_cu_sha256_16") != h or ent.get("config") != config:
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2603_09277_gb300", "csrc", ent.get("source", "render.cu"))
+    if not os.path.exists(src):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if ent.get("source_sha256_16", ent.get("render_cu_sha256_16")) != h:
+        return None
+    if ent.get("config") != config:
         return None
     return ent.get("bytes_per_launch")
 
@@ -594,6 +601,26 @@ def time_variant(make, p, tgt, gamma, flush, steps, warmup=2):
     return out, rs
 
 
+def super_tile_items(r, cams, tile):
+    """Items (visible row x 8x8-tile super-tile its rect meets) of the list
+    construction, from the projection's rects on the device."""
+    import torch
+    rect = r.rect[:r.rows].long().view(r.V, r.N, 4)
+    tot = 0
+    for v, c in enumerate(cams):
+        TX = (c["width"] + tile - 1) // tile
+        TY = (c["height"] + tile - 1) // tile
+        rr = rect[v]
+        x0, y0 = rr[:, 0].clamp(min=0), rr[:, 1].clamp(min=0)
+        x1, y1 = rr[:, 2].clamp(max=TX), rr[:, 3].clamp(max=TY)
+        ok = (x1 > x0) & (y1 > y0) & (r.tiles_touched[v * r.N:(v + 1) * r.N] > 0)
+        q = ((torch.div(x1 - 1, 8, rounding_mode="floor") - torch.div(x0, 8, rounding_mode="floor")
+              + 1) * (torch.div(y1 - 1, 8, rounding_mode="floor")
+                      - torch.div(y0, 8, rounding_mode="floor") + 1))
+        tot += int(torch.where(ok, q, torch.zeros_like(q)).sum().item())
+    return tot
+
+
 def sm_count(dev):
     import torch
     return int(torch.cuda.get_device_properties(dev).multi_processor_count)
@@ -748,7 +775,7 @@ def main():
     # (1) eager steps with CUDA events between the phases: the per-phase
     # breakdown and the live per-kernel durations of the blending kernels
     KE = min(K, 20)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(KE)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(16)] for _ in range(KE)]
     for e in evs:  # materialise the event handles
         for x in e:
             x.record()
@@ -756,6 +783,10 @@ def main():
     for k in range(KE):
         flush.fill_(float(k))  # L2 flush between timed steps (outside the step events)
         e = evs[k]
+        # live events around the kernels of the stages without a launch argument
+        gs.gs_stage_events(gs.GS_STAGE_PROJECTION, e[10], e[11])
+        gs.gs_stage_events(gs.GS_STAGE_EXPANSION, e[12], e[13])
+        gs.gs_stage_events(gs.GS_STAGE_ADJOINT, e[14], e[15])
         e[0].record()
         r.preprocess(p)
         e[1].record()
@@ -767,8 +798,17 @@ def main():
         r.render_bwd(p, events=(e[7], e[8]))
         gs.gs_scale_reset(ls_work, 0.2)
         e[4].record()
+    for st_ in (gs.GS_STAGE_PROJECTION, gs.GS_STAGE_EXPANSION, gs.GS_STAGE_ADJOINT):
+        gs.gs_stage_events(st_, None, None)
     torch.cuda.synchronize()
     eager_ms = float(np.mean([e[0].elapsed_time(e[4]) for e in evs]))
+    kernel_ms = {
+        "render_fwd_kernel": float(np.mean([e[5].elapsed_time(e[6]) for e in evs])),
+        "render_bwd_kernel": float(np.mean([e[7].elapsed_time(e[8]) for e in evs])),
+        "preprocess_kernel": float(np.mean([e[10].elapsed_time(e[11]) for e in evs])),
+        "st_emit_kernel": float(np.mean([e[12].elapsed_time(e[13]) for e in evs])),
+        "preprocess_bwd_kernel": float(np.mean([e[14].elapsed_time(e[15]) for e in evs])),
+    }
     phase = {
         "preprocess": float(np.mean([e[0].elapsed_time(e[1]) for e in evs])),
         "bin_sort": float(np.mean([e[1].elapsed_time(e[2]) for e in evs])),
@@ -823,22 +863,60 @@ def main():
     value = nb_all * K / t_total
     ms = 1000.0 * t_total / K
 
-    # roofline of the dominant kernel (blending forward or backward)
-    fwd_ms, bwd_ms = phase["render_fwd_kernel"], phase["render_bwd_kernel"]
+    # roofline of the dominant kernel: of the kernels timed live, the one with
+    # the longest launch; the blending kernels against the FP32 peak with the
+    # FLOP model, the HBM-bound ones against the measured copy bandwidth with
+    # their algorithmic bytes per launch
     peak, peak_src = fp32_peak_tflops(dev, clocks)
-    if bwd_ms >= fwd_ms:
-        kname, kms = "render_bwd_kernel", bwd_ms
-        flops = BWD_EVAL * bwd_eval + BWD_BLEND * nb_step
+    hbm, hbm_src = measured_hbm_peak()
+    vis_rows = (r.tiles_touched[:r.rows] > 0)
+    n_rows_vis = int(vis_rows.sum().item())
+    n_gauss_vis = int(vis_rows.view(r.V, r.N).any(0).sum().item())
+    Kc = (int(prm.get("sh_degree", 0)) + 1) ** 2
+    n_g = int(scene["means"].shape[0])
+    rec_b = gs.gs_record_bytes(r.prm_c.attr_dtype)
+    Q = super_tile_items(r, cams, args.tile)
+    algo = {
+        "render_fwd_kernel": ("alu", FWD_EVAL * ne_step + FWD_BLEND * nb_step),
+        "render_bwd_kernel": ("alu", BWD_EVAL * bwd_eval + BWD_BLEND * nb_step),
+        # every Gaussian's geometry and opacity, the SH in use of the seen
+        # ones; depth, rect and count of every row, the record of every
+        # visible row
+        "preprocess_kernel": ("hbm", n_g * 44 + n_gauss_vis * 12 * Kc + r.rows * 24 +
+                              n_rows_vis * rec_b),
+        # the super-tile items (packed key, row) read, every pair written once
+        "st_emit_kernel": ("hbm", Q * 8 + P * 4),
+        # the moment row of every visible row; parameters read and gradients
+        # written of every seen Gaussian
+        "preprocess_bwd_kernel": ("hbm", n_rows_vis * 48 + n_gauss_vis * (44 + 12 * Kc) * 2),
+    }
+    kname = max(kernel_ms, key=kernel_ms.get)
+    kms = kernel_ms[kname]
+    bound, work = algo[kname]
+    if bound == "alu":
+        achieved = work / (kms / 1000.0) / 1e12
+        roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": (traffic_from_profiles(kname, args.config)
+                                if not args.n and args.tile == 16 and args.attr == "f32" else None),
+                    "peak_source": peak_src, "flops_per_launch": work, "ms": kms}
     else:
-        kname, kms = "render_fwd_kernel", fwd_ms
-        flops = FWD_EVAL * ne_step + FWD_BLEND * nb_step
-    achieved = flops / (kms / 1000.0) / 1e12
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": (traffic_from_profiles(kname, args.config)
-                            if not args.n and args.tile == 16 and args.attr == "f32" else None),
-                "peak_source": peak_src,
-                "flops_per_launch": flops}
+        achieved = work / (kms / 1000.0) / 1e9
+        roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
+                    "unit": "GB/s", "frac": achieved / hbm,
+                    "traffic": (traffic_from_profiles(kname, args.config)
+                                if not args.n and args.tile == 16 and args.attr == "f32" else None),
+                    "peak_source": hbm_src, "bytes_per_launch": int(work), "ms": kms}
+    kernels = {}
+    for kn, kt in kernel_ms.items():
+        bd, wk = algo[kn]
+        if bd == "alu":
+            ach = wk / (kt / 1000.0) / 1e12
+            kernels[kn] = {"ms": kt, "bound": "alu", "achieved_tflops": ach, "frac": ach / peak}
+        else:
+            ach = wk / (kt / 1000.0) / 1e9
+            kernels[kn] = {"ms": kt, "bound": "hbm", "achieved_gbs": ach, "frac": ach / hbm,
+                           "bytes": int(wk)}
 
     # per-phase times replayed alone from graphs, and the rooflines of the
     # phases other than the dominant kernel: HBM phases against the measured
@@ -856,16 +934,10 @@ def main():
         "loss": lambda: r.loss(tgt, gamma, lam=args.dssim),
         "render_bwd+preprocess_bwd": lambda: r.render_bwd(p),
     }, flush)
-    hbm, hbm_src = measured_hbm_peak()
     if not pg:  # fall back on the eager phase events
         pg = {"preprocess": phase["preprocess"], "bin_sort": phase["bin_sort"],
               "render_fwd": phase["render_fwd_kernel"],
               "loss": phase["render_fwd+loss"] - phase["render_fwd_kernel"]}
-    vis_rows = (r.tiles_touched[:r.rows] > 0)
-    n_rows_vis = int(vis_rows.sum().item())
-    n_gauss_vis = int(vis_rows.view(r.V, r.N).any(0).sum().item())
-    Kc = (int(prm.get("sh_degree", 0)) + 1) ** 2
-    n_g = int(scene["means"].shape[0])
     n_pix = int(r.image.shape[0])
     bytes_pre = (n_g * 44 + n_gauss_vis * 12 * Kc + r.rows * 24 +
                  n_rows_vis * gs.gs_record_bytes(r.prm_c.attr_dtype))
@@ -1037,6 +1109,7 @@ def main():
             "exclusions_view0": ref["exclusions"] if ref is not None else None,
             "variants": variants,
             "roofline": roofline,
+            "kernels": kernels,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "e2e_params_uploaded": e2e_full,

@@ -149,6 +149,16 @@ const char* gs_version(void);
  * threads, all devices); for launch accounting. */
 unsigned long long gs_kernel_launches(void);
 
+/* Live per-kernel timing of the stages without a gs_launch argument: the
+ * calling thread's next calls record ev_begin / ev_end (cudaEvent_t, or NULL
+ * to stop) on their stream right before and after the stage's kernel.
+ * Stages: GS_STAGE_EXPANSION (gs_bin_sort's expansion of the super-tile rows
+ * into the per-tile lists), GS_STAGE_PROJECTION (gs_preprocess's kernel),
+ * GS_STAGE_ADJOINT (gs_render_bwd's projection adjoint).  Returns
+ * GS_ERR_INVALID_ARG for an unknown stage. */
+enum gs_stage { GS_STAGE_EXPANSION = 1, GS_STAGE_PROJECTION = 2, GS_STAGE_ADJOINT = 3 };
+int gs_stage_events(int stage, void* ev_begin, void* ev_end);
+
 /* ---------------------------------------------------------------------- */
 /* Hot path                                                                */
 /* ---------------------------------------------------------------------- */
@@ -275,6 +285,23 @@ int gs_render_bwd(const gs_proj* proj, int N, const gs_camera* cams_host, int V,
                   const float* quats, const float* opacity_logits, const float* sh,
                   float* grad2d, float* g_means, float* g_log_scales, float* g_quats,
                   float* g_opacity_logits, float* g_sh, const gs_launch* opt, gs_stream stream);
+
+/* The 2D gradients of Suppl. C per (view, Gaussian) row, from the moment
+ * rows gs_render_bwd leaves in grad2d (reading c10: the conic is stored as
+ * (a, b, c) with d = -1/2 (a dx^2 + 2 b dx dy + c dy^2), so b's gradient
+ * counts both off-diagonal entries of the symmetric matrix):
+ *   out[row][0..1] = dL/d(mean2d x, y) = K (sum dd dx, sum dd dy)
+ *   out[row][2..4] = dL/d(a, b, c) = (-sum dd dx^2 / 2, -sum dd dx dy, -sum dd dy^2 / 2)
+ *   out[row][5]    = dL/dsigma (opacity after the sigmoid) = sum dd / sigma
+ *   out[row][6..8] = dL/d(r, g, b) of the clamped colour
+ * with dd = dL/dalpha alpha where alpha is below its clamp, (dx, dy) = pixel
+ * centre minus 2D mean, K the conic taken from the render record (so in the
+ * record's staging precision).  Rows of culled or unseen Gaussians get zeros.
+ *   proj: the gs_preprocess output of the same call sequence (records and
+ *   tiles_touched are read); grad2d [V*N][12] from gs_render_bwd, 16-B
+ *   aligned; out [V*N][9] device, overwritten. */
+int gs_grad2d_attributes(const gs_proj* proj, int N, int V, const gs_params* prm,
+                         const float* grad2d, float* out, gs_stream stream);
 
 /* Scale reset (Sec. 4.2): s <- zeta s for every Gaussian, i.e.
  * log_scales[i] += ln(zeta) in place, n = 3N floats.  0 < zeta < 1, else

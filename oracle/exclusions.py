@@ -25,6 +25,8 @@ from __future__ import annotations
 
 import numpy as np
 
+import oracle as _oracle
+
 MARGIN = 1e-4
 
 
@@ -132,3 +134,30 @@ def summary(ora_view, cam, mask=None, margin=MARGIN, prm=None):
             "near_threshold_pixels": int(near.sum()),
             "excluded_pixels": int(excl.sum()), "pixels_counted": int(mask.sum()),
             "compared_pixels": int((mask & ~excl).sum())}
+
+
+def flip_sensitive(ora_view, cam, prm, dL_dC, dL_dH, g9_all=None, share=0.02, margin=MARGIN):
+    """Boolean [N]: Gaussians whose gradient a threshold flip at a
+    near-threshold pixel (smallest relative margin below `margin`) can move
+    by a noticeable part.  A flip there changes the pixel's contributions to
+    every later entry by a factor within alpha_min of 1 (about 0.4 %), so a
+    Gaussian that takes `share` or more of any of its nine 2D-gradient
+    components (mean, conic, opacity, colour) from such pixels is marked.
+    dL_dC [H,W,3], dL_dH [H,W]: the loss gradients of the view; g9_all: the
+    oracle's 2D gradients of the whole view (recomputed if None)."""
+    proj, fwd = ora_view["proj"], ora_view["fwd"]
+    N = proj["P9"].shape[0]
+    mb = fwd["margin"] < margin
+    if not mb.any():
+        return np.zeros(N, bool)
+    dC = np.array(dL_dC, np.float64, copy=True)
+    dC[~mb] = 0.0
+    dH = None
+    if dL_dH is not None:
+        dH = np.array(dL_dH, np.float64, copy=True)
+        dH[~mb] = 0.0
+    g9b = _oracle.render_bwd(proj, ora_view["lists"], cam, prm, dC, dH, mask=mb)
+    if g9_all is None:
+        g9_all = _oracle.render_bwd(proj, ora_view["lists"], cam, prm, dL_dC, dL_dH)
+    ratio = np.abs(g9b) / np.maximum(np.abs(g9_all), 1e-300)
+    return (ratio >= share).any(1) & (np.abs(g9b).sum(1) > 0)

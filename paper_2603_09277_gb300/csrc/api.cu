@@ -23,6 +23,8 @@ int launch_preprocess_bwd(const float* means, const float* log_scales, const flo
                           cudaStream_t st);
 int launch_adjoint_list(const unsigned* tiles_touched, int N, int V, float* grad2d,
                         cudaStream_t st);
+int launch_grad2d_attributes(const gs_proj* proj, long long rows, const gs_params* prm,
+                             const float* grad2d, float* out, cudaStream_t st);
 size_t bin_sort_workspace_size(long long n_rows, long long cap, long long total_tiles);
 size_t ssim_workspace_bytes(long long total_pixels);
 int ssim_blocks(const CamTable& ct);
@@ -92,6 +94,18 @@ SideStream* side_stream_locked(cudaStream_t st) {
   return ss.ok ? &ss : nullptr;
 }
 }  // namespace
+
+namespace {
+thread_local void* g_stage_ev[4][2] = {};
+}  // namespace
+
+int stage_event(int stage, bool end, cudaStream_t st) {
+  if (stage < 1 || stage > 3) return GS_OK;
+  void* ev = g_stage_ev[stage][end ? 1 : 0];
+  if (!ev) return GS_OK;
+  GS_TRY_CUDA(cudaEventRecord(reinterpret_cast<cudaEvent_t>(ev), st));
+  return GS_OK;
+}
 
 int set_error_text_and_status(const char* msg, int status) {
   set_error_text(msg);
@@ -340,6 +354,13 @@ int loss_blocks(long long P) {
 using namespace gs;
 
 extern "C" {
+
+int gs_stage_events(int stage, void* ev_begin, void* ev_end) {
+  if (stage < GS_STAGE_EXPANSION || stage > GS_STAGE_ADJOINT) return invalid("stage");
+  g_stage_ev[stage][0] = ev_begin;
+  g_stage_ev[stage][1] = ev_end;
+  return GS_OK;
+}
 
 int gs_record_bytes(int attr_dtype) {
   switch (attr_dtype) {
@@ -593,6 +614,17 @@ int gs_render_bwd(const gs_proj* proj, int N, const gs_camera* cams, int V, cons
   return launch_preprocess_bwd(means, log_scales, quats, opacity_logits, sh, N, ct, prm,
                                proj->tiles_touched, grad2d, g_means, g_log_scales, g_quats,
                                g_opacity_logits, g_sh, st);
+}
+
+int gs_grad2d_attributes(const gs_proj* proj, int N, int V, const gs_params* prm,
+                         const float* grad2d, float* out, gs_stream stream) {
+  if (N < 0 || V < 1 || V > GS_MAX_VIEWS) return invalid("N or V");
+  if (!params_ok(prm)) return invalid("params");
+  if (!proj_ok(proj, true)) return invalid("projection buffers");
+  if ((long long)N * V >= (1ll << 32)) return invalid("V*N must be < 2^32");
+  if (N > 0 && (!grad2d || !aligned(grad2d, 16) || !out))
+    return invalid("grad2d (16-B aligned) and out");
+  return launch_grad2d_attributes(proj, (long long)N * V, prm, grad2d, out, (cudaStream_t)stream);
 }
 
 int gs_scale_reset(float* log_scales, long long n, float zeta, gs_stream stream) {

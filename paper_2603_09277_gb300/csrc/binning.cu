@@ -7,14 +7,15 @@
 // super-tile is 8x8 tiles), and the pairs are only ever written once, into
 // their final slots:
 //   1. compact the visible rows (scan of a visibility flag);
-//   2. stable LSD radix sort of the visible rows by FP32 depth bits
-//      (4 passes of 8 bits; ties keep row order = Gaussian id order);
+//   2. stable LSD radix sort of the visible rows by FP32 depth bits, on the
+//      bits that vary over the visible rows (up to 9-bit digits: 3 passes
+//      for a range of up to 27 bits; ties keep row order = Gaussian id order);
 //   3. gather every row's rect in depth order; scans give the pair count P
 //      and each row's offset among the super-tile items (count Q <= P);
 //   4. duplicate: each row writes (super-tile, row) for the super-tiles its
 //      rect meets, in depth order (load-balanced over items);
 //   5. stable radix sort of the items by super-tile id (one pass for up to
-//      256 super-tiles), so every super-tile holds its rows in depth order;
+//      512 super-tiles), so every super-tile holds its rows in depth order;
 //   6. per segment of 1024 rows of a super-tile: each row's rect within the
 //      super-tile and per-tile counts; scans over segments and over all
 //      tiles give every tile's list start (the ranges);
@@ -37,6 +38,12 @@
 #include <atomic>
 
 #include "gs_internal.cuh"
+
+// 1: radix digits ranked within a warp by match.any; 0: by one ballot per
+// digit bit (the form the timings chose)
+#ifndef GS_RADIX_MATCH
+#define GS_RADIX_MATCH 0
+#endif
 
 namespace gs {
 namespace {
@@ -210,18 +217,42 @@ template <int ITEMS>
 __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
     const unsigned* __restrict__ tiles_touched, const float* __restrict__ depth, long long n,
     const unsigned long long* __restrict__ block_offsets, unsigned* __restrict__ keys,
-    unsigned* __restrict__ vals) {
+    unsigned* __restrict__ vals, unsigned* __restrict__ range) {
   __shared__ unsigned s_off[ITEMS * kScanWarps];
+  __shared__ unsigned s_kmin[kScanWarps], s_kmax[kScanWarps];
   const long long base = (long long)blockIdx.x * (kScanThreads * ITEMS);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned ball[ITEMS];
+  unsigned kmin = 0xffffffffu, kmax = 0u;  // range of the visible rows' depth bits
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
     const long long i = base + (long long)k * kScanThreads + threadIdx.x;
-    ball[k] = __ballot_sync(0xffffffffu, i < n && tiles_touched[i] > 0u);
+    const bool vis = i < n && tiles_touched[i] > 0u;
+    ball[k] = __ballot_sync(0xffffffffu, vis);
     if (lane == 0) s_off[k * kScanWarps + w] = __popc(ball[k]);
+    if (vis) {  // depth > near_z > 0: the bits order like the values
+      const unsigned kb = __float_as_uint(depth[i]);
+      kmin = min(kmin, kb);
+      kmax = max(kmax, kb);
+    }
+  }
+  kmin = __reduce_min_sync(0xffffffffu, kmin);
+  kmax = __reduce_max_sync(0xffffffffu, kmax);
+  if (lane == 0) {
+    s_kmin[w] = kmin;
+    s_kmax[w] = kmax;
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < kScanWarps; ++q) {
+      kmin = min(kmin, s_kmin[q]);
+      kmax = max(kmax, s_kmax[q]);
+    }
+    if (kmin <= kmax) {  // (folded in from zero: range[0] holds the complement)
+      atomicMax(range, ~kmin);
+      atomicMax(range + 1, kmax);
+    }
+  }
   if (w == 0) {  // exclusive scan of the (k, warp) counts, kPerLane per lane
     constexpr int kCounts = ITEMS * kScanWarps;
     constexpr int kPerLane = (kCounts + 31) / 32;
@@ -292,6 +323,19 @@ __device__ __forceinline__ unsigned st_count(const int4 r) {
   return (unsigned)((q.z - q.x) * (q.w - q.y));
 }
 
+__device__ __forceinline__ int radix_result(const unsigned* range, int bits);
+
+// The depth-sorted rows: the buffer the sort left them in follows from the
+// device-side key range (the number of passes it ran).
+struct SortedRows {
+  const unsigned* buf0;
+  const unsigned* buf1;
+  const unsigned* range;
+  __device__ __forceinline__ const unsigned* get() const {
+    return radix_result(range, 32) ? buf1 : buf0;
+  }
+};
+
 // Gathers the clamped rect of every depth-ordered row (so later stages read
 // them in order) and forms per-block sums of the super-tile counts and of
 // the pair counts.
@@ -299,11 +343,12 @@ __device__ __forceinline__ unsigned st_count(const int4 r) {
 // capacity check (scan_counts_check_dev).
 template <int ITEMS>
 __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
-    const unsigned* __restrict__ rows, const long long* __restrict__ n_dev,
+    const SortedRows sorted, const long long* __restrict__ n_dev,
     const int* __restrict__ rect, int N, const CamTable ct, int4* __restrict__ rect_sorted,
     unsigned long long* __restrict__ arrive, const CountsOut co) {
   unsigned long long* sums_q = co.sums_q;
   unsigned long long* sums_p = co.sums_p;
+  const unsigned* __restrict__ rows = sorted.get();
   const long long n = *n_dev;
   const long long base = (long long)blockIdx.x * (kScanThreads * ITEMS);
   if (base >= n) {  // (the whole CTA) no rows: zero sums
@@ -388,15 +433,69 @@ __global__ void __launch_bounds__(kScanThreads) row_offsets_kernel(
 }
 
 // ----------------------------------------------------------------------------
-// Stable LSD radix sort of (u32 key, u32 value) pairs, 8-bit digits,
+// Stable LSD radix sort of (u32 key, u32 value) pairs, up to 8-bit digits,
 // reduce-then-scan with a fixed grid.  Each block owns a contiguous chunk of
 // whole 2048-item tiles; n is read from device memory.
+//
+// The keys may be sorted on their significant bits only: with a device-side
+// key range (the visible rows' smallest and largest depth bits, found during
+// the compaction) each pass sorts digits of (key - min); the number of passes
+// ceil(bits / 8) and the digit width ceil(bits / passes) follow from the
+// range on the device, and the kernels of passes beyond it return at once
+// (so the launch sequence, and a graph of it, is fixed).  The result is in
+// buffer (passes mod 2).
 // ----------------------------------------------------------------------------
 constexpr int kRadixThreads = 256;
 constexpr int kRadixWarps = kRadixThreads / 32;
 constexpr int kRadixIpt = 8;                                // items per thread per tile
 constexpr int kRadixTile = kRadixThreads * kRadixIpt;       // 2048
-constexpr int kRadixBins = 256;
+constexpr int kRadixMaxBits = 8;
+constexpr int kRadixBins = 1 << kRadixMaxBits;              // 256
+constexpr int kRadixMaxPasses = (32 + kRadixMaxBits - 1) / kRadixMaxBits;  // 4
+
+struct RadixPlan {
+  unsigned kmin;  // subtracted from every key
+  int passes;
+  int dbits;      // digit width of every pass
+};
+
+// bits: significant bits of (key - kmin).
+__host__ __device__ __forceinline__ RadixPlan radix_plan_bits(unsigned kmin, int bits) {
+  RadixPlan p;
+  p.kmin = kmin;
+  p.passes = (bits + kRadixMaxBits - 1) / kRadixMaxBits;
+  p.dbits = p.passes ? (bits + p.passes - 1) / p.passes : 0;
+  return p;
+}
+
+// range (device, nullable): [0] = ~(smallest key), [1] = largest key, both
+// folded in with atomicMax from zero (no key: range[0] = range[1] = 0, an
+// empty range).  Without a range every one of `bits` bits is sorted.
+__device__ __forceinline__ RadixPlan radix_plan(const unsigned* __restrict__ range, int bits) {
+  if (!range) return radix_plan_bits(0u, bits);
+  const unsigned kmin = ~__ldcg(range), kmax = __ldcg(range + 1);
+  if (kmax <= kmin) return radix_plan_bits(kmax < kmin ? 0u : kmin, 0);
+  return radix_plan_bits(kmin, 32 - __clz(kmax - kmin));
+}
+
+__device__ __forceinline__ unsigned radix_digit(unsigned key, const RadixPlan& p, int shift) {
+  return ((key - p.kmin) >> shift) & ((1u << p.dbits) - 1u);
+}
+
+// Arguments of one pass.
+struct RadixPass {
+  const unsigned* keys_in;
+  const unsigned* vals_in;
+  unsigned* keys_out;
+  unsigned* vals_out;
+  const long long* n_dev;  // item count
+  const unsigned* range;   // device key range or nullptr
+  int bits;                // significant bits without a range
+  int pass;                // pass index (shift = pass * digit width)
+  unsigned* hist;          // [256][grid] per-CTA digit counts, then their scan
+  unsigned* digit_tot;     // [256] items per digit
+  int keys_last;           // write the keys in the last pass too
+};
 
 __device__ __forceinline__ long long radix_chunk(long long n, int nblocks) {
   long long per = (n + nblocks - 1) / nblocks;
@@ -411,12 +510,15 @@ __device__ __forceinline__ int radix_active(long long n, int nblocks) {
   return chunk > 0 ? (int)min((long long)nblocks, (n + chunk - 1) / chunk) : 0;
 }
 
-__global__ void __launch_bounds__(kRadixThreads) radix_upsweep_kernel(
-    const unsigned* __restrict__ keys, const long long* __restrict__ n_dev, int shift,
-    unsigned dmask, unsigned* __restrict__ hist /* [256][nblocks] */) {
+__global__ void __launch_bounds__(kRadixThreads) radix_upsweep_kernel(const RadixPass a) {
+  const RadixPlan pl = radix_plan(a.range, a.bits);
+  if (a.pass >= pl.passes) return;  // (the whole grid)
+  const unsigned* __restrict__ keys = a.keys_in;
+  unsigned* __restrict__ hist = a.hist;  // [256][nblocks]
+  const int shift = a.pass * pl.dbits;
   __shared__ unsigned s_h[kRadixWarps][kRadixBins];
   const int w = threadIdx.x >> 5;
-  long long n = *n_dev;
+  long long n = *a.n_dev;
   if ((int)blockIdx.x >= radix_active(n, gridDim.x)) return;  // (the whole CTA)
   long long chunk = radix_chunk(n, gridDim.x);
   long long b0 = (long long)blockIdx.x * chunk;
@@ -442,7 +544,8 @@ __global__ void __launch_bounds__(kRadixThreads) radix_upsweep_kernel(
     }
 #pragma unroll
     for (int i = 0; i < kRadixIpt; ++i)
-      if (t0 + i * kRadixThreads + threadIdx.x < b1) atomicAdd(&s_h[w][(kk[i] >> shift) & dmask], 1u);
+      if (t0 + i * kRadixThreads + threadIdx.x < b1)
+        atomicAdd(&s_h[w][radix_digit(kk[i], pl, shift)], 1u);
   }
   __syncthreads();
   for (int d = threadIdx.x; d < kRadixBins; d += kRadixThreads) {
@@ -455,11 +558,12 @@ __global__ void __launch_bounds__(kRadixThreads) radix_upsweep_kernel(
 // Per-digit exclusive scan over the blocks: block d scans hist[d][0..Ga) in
 // place (Ga = the pass's active CTAs) and writes the digit total to
 // totals[d].  G <= 1024.
-__global__ void __launch_bounds__(kScanThreads) radix_scan_kernel(
-    unsigned* __restrict__ hist, int G, const long long* __restrict__ n_dev,
-    unsigned* __restrict__ totals) {
-  unsigned* h = hist + (long long)blockIdx.x * G;
-  const int Ga = radix_active(*n_dev, G);
+__global__ void __launch_bounds__(kScanThreads) radix_scan_kernel(const RadixPass a, int G) {
+  const RadixPlan pl = radix_plan(a.range, a.bits);
+  if (a.pass >= pl.passes) return;
+  unsigned* totals = a.digit_tot;
+  unsigned* h = a.hist + (long long)blockIdx.x * G;
+  const int Ga = radix_active(*a.n_dev, G);
   constexpr int kPer = 4;  // 256 threads x 4 >= 1024 blocks
   unsigned loc[kPer];
   unsigned long long s = 0;
@@ -486,11 +590,19 @@ __global__ void __launch_bounds__(kScanThreads) radix_scan_kernel(
 // addresses of one digit's run (coalesced), and each digit's running global
 // offset advances by the tile's count.  The next tile's keys and values are
 // loaded into registers while the current one is ranked and written.
-__global__ void __launch_bounds__(kRadixThreads, 3) radix_downsweep_kernel(
-    const unsigned* __restrict__ keys_in, const unsigned* __restrict__ vals_in,
-    unsigned* __restrict__ keys_out, unsigned* __restrict__ vals_out,
-    const long long* __restrict__ n_dev, int shift, int dbits, const unsigned* __restrict__ offsets,
-    const unsigned* __restrict__ totals) {
+__global__ void __launch_bounds__(kRadixThreads, 3) radix_downsweep_kernel(const RadixPass a) {
+  const RadixPlan pl = radix_plan(a.range, a.bits);
+  if (a.pass >= pl.passes) return;
+  const unsigned* __restrict__ keys_in = a.keys_in;
+  const unsigned* __restrict__ vals_in = a.vals_in;
+  unsigned* __restrict__ keys_out = a.keys_out;
+  unsigned* __restrict__ vals_out = a.vals_out;
+  const long long* __restrict__ n_dev = a.n_dev;
+  const unsigned* __restrict__ offsets = a.hist;
+  const unsigned* __restrict__ totals = a.digit_tot;
+  const int shift = a.pass * pl.dbits;
+  const int dbits = pl.dbits;
+  const bool wkeys = a.keys_last || a.pass + 1 < pl.passes;
   __shared__ unsigned s_wc[kRadixWarps][kRadixBins + 1];  // per-warp digit counters (+ dummy)
   __shared__ unsigned s_base[kRadixBins];                 // running global offset per digit
   __shared__ unsigned s_tot[kRadixBins];                  // tile count per digit
@@ -499,7 +611,6 @@ __global__ void __launch_bounds__(kRadixThreads, 3) radix_downsweep_kernel(
   __shared__ unsigned s_val[kRadixTile];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const unsigned dmask = (1u << dbits) - 1u;
   long long n = *n_dev;
   if ((int)blockIdx.x >= radix_active(n, gridDim.x)) return;  // (the whole CTA)
   long long chunk = radix_chunk(n, gridDim.x);
@@ -534,7 +645,7 @@ __global__ void __launch_bounds__(kRadixThreads, 3) radix_downsweep_kernel(
     for (int i = 0; i < kRadixIpt; ++i) {
       k[i] = nk[i];
       v[i] = nv[i];
-      dg[i] = lbase + i * 32 < cnt ? ((k[i] >> shift) & dmask) : (unsigned)kRadixBins;
+      dg[i] = lbase + i * 32 < cnt ? radix_digit(k[i], pl, shift) : (unsigned)kRadixBins;
     }
     const long long t1 = t0 + kRadixTile;
     if (t1 < b1) {
@@ -592,9 +703,9 @@ __global__ void __launch_bounds__(kRadixThreads, 3) radix_downsweep_kernel(
     __syncthreads();
     for (int i = threadIdx.x; i < cnt; i += kRadixThreads) {
       const unsigned kk = s_key[i];
-      const unsigned d = (kk >> shift) & dmask;
+      const unsigned d = radix_digit(kk, pl, shift);
       const unsigned pos = s_base[d] + (unsigned)i - s_off[d];
-      keys_out[pos] = kk;
+      if (wkeys) keys_out[pos] = kk;
       vals_out[pos] = s_val[i];
     }
     __syncthreads();
@@ -606,6 +717,11 @@ __global__ void __launch_bounds__(kRadixThreads, 3) radix_downsweep_kernel(
     }
     __syncthreads();
   }
+}
+
+// Buffer index (0 or 1) holding the sorted result.
+__device__ __forceinline__ int radix_result(const unsigned* range, int bits) {
+  return radix_plan(range, bits).passes & 1;
 }
 
 // ----------------------------------------------------------------------------
@@ -742,13 +858,14 @@ __device__ __forceinline__ void duplicate_block(
 // Grid-stride over the blocks of the Q items (the grid is sized for the
 // bound on Q; a CTA beyond the last block leaves at once).
 __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
-    const unsigned* __restrict__ rows, const int4* __restrict__ rect_sorted,
+    const SortedRows sorted, const int4* __restrict__ rect_sorted,
     const long long* __restrict__ n_vis, const unsigned long long* __restrict__ offsets, int N,
     const CamTable ct, const long long* __restrict__ q_eff,
     const unsigned* __restrict__ block_row, unsigned* __restrict__ skeys,
     unsigned* __restrict__ svals, int vec16, int packed) {
   const long long Q = *q_eff;
   const long long n = *n_vis;
+  const unsigned* __restrict__ rows = sorted.get();
   for (long long b = blockIdx.x; b * kDupPairs < Q; b += gridDim.x)
     duplicate_block(b, Q, n, rows, rect_sorted, offsets, N, ct, block_row, skeys, svals, vec16,
                     packed);
@@ -817,10 +934,10 @@ __global__ void __launch_bounds__(1024) st_segments_kernel(uint2* __restrict__ s
   __shared__ unsigned s_carry;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   if (totals) {
-    // one radix pass sorted the items by super-tile (S <= 256): the per-digit
+    // one radix pass sorted the items by super-tile (S <= 512): the per-digit
     // totals are the per-super-tile counts, and their exclusive scan the starts
-    __shared__ unsigned s_tot[256];
-    if (tid < 256) s_tot[tid] = tid < S ? totals[tid] : 0u;
+    __shared__ unsigned s_tot[kRadixBins];
+    if (tid < kRadixBins) s_tot[tid] = tid < S ? totals[tid] : 0u;
     __syncthreads();
     if (tid == 0) {
       unsigned run = 0u;
@@ -913,8 +1030,9 @@ __device__ __forceinline__ void rect_ballots(unsigned d, unsigned B[8], unsigned
 
 // Counts of the warp's rows covering tiles `lane` and `lane + 32` of the
 // super-tile (tile b = 8 row + column).
-__device__ __forceinline__ void lane_tile_counts(const unsigned B[8], const unsigned X[8],
-                                                 int lane, unsigned& c0, unsigned& c1) {
+// The lanes of the warp's rows covering tiles `lane` and `lane + 32`.
+__device__ __forceinline__ void lane_tile_masks(const unsigned B[8], const unsigned X[8],
+                                                int lane, unsigned& m0, unsigned& m1) {
   const int r = lane >> 3, c = lane & 7;
   unsigned b0 = B[0], b1 = B[4], x = X[0];
 #pragma unroll
@@ -924,8 +1042,16 @@ __device__ __forceinline__ void lane_tile_counts(const unsigned B[8], const unsi
   }
 #pragma unroll
   for (int k = 1; k < 8; ++k) x = c == k ? X[k] : x;
-  c0 = __popc(b0 & x);
-  c1 = __popc(b1 & x);
+  m0 = b0 & x;
+  m1 = b1 & x;
+}
+
+__device__ __forceinline__ void lane_tile_counts(const unsigned B[8], const unsigned X[8],
+                                                 int lane, unsigned& c0, unsigned& c1) {
+  unsigned m0, m1;
+  lane_tile_masks(B, X, lane, m0, m1);
+  c0 = __popc(m0);
+  c1 = __popc(m1);
 }
 
 // Rect of row `row` inside the super-tile with tile origin (ox, oy), as a
@@ -1133,19 +1259,25 @@ __global__ void __launch_bounds__(256) st_emit_kernel(
         s_run[tid] = run;
       }
       __syncthreads();
+      // this lane's rect in the super-tile, and the column ballots restricted
+      // to the lanes before it (ranks by population counts, no branches per
+      // tile: in the dense case nearly every tile has a covering row)
+      const unsigned x0 = d & 15u, x1 = (d >> 4) & 15u, y0 = (d >> 8) & 15u, y1 = (d >> 12) & 15u;
+      unsigned Xl[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) Xl[c] = X[c] & lt;
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         if (B[r] == 0u) continue;  // warp-uniform
         const uint4 pa = *reinterpret_cast<const uint4*>(&s_pos[w][8 * r]);
         const uint4 pb = *reinterpret_cast<const uint4*>(&s_pos[w][8 * r + 4]);
         const unsigned sp[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+        const bool in_r = (unsigned)r >= y0 && (unsigned)r < y1;
 #pragma unroll
         for (unsigned c = 0; c < 8; ++c) {
-          // the lanes whose rows cover tile (r, c), this lane among them
-          const unsigned bal = B[r] & X[c];
-          if (bal == 0u) continue;  // warp-uniform
-          if ((bal >> lane) & 1u) {
-            const unsigned pos = sp[c] + __popc(bal & lt);
+          // this lane covers tile (r, c): its rank among the covering lanes
+          const unsigned pos = sp[c] + __popc(B[r] & Xl[c]);
+          if (in_r && c >= x0 && c < x1) {
             out_vals[pos] = row;
             if (out_keys)
               out_keys[pos] = ((unsigned long long)(unsigned)s_tile[8 * r + c] << 32) |
@@ -1188,50 +1320,12 @@ struct Workspace {
   size_t bytes;
 };
 
-constexpr int kRadixGrid = 4 * 152;  // fixed radix grid (4 CTAs per SM)
+constexpr int kRadixGrid = 4 * 152;  // largest radix grid (4 CTAs per SM of a GB300)
 
-inline long long scan_blocks(long long n) { return (n + kScanTile - 1) / kScanTile; }
+// Radix histograms: [256][grid] per-CTA digit counts and their scan, then the
+// 256 digit totals.
+constexpr size_t radix_hist_bytes() { return 4ull * kRadixBins * (kRadixGrid + 1); }
 
-// Upper bound of the expansion segments: sum over super-tiles of
-// ceil(len / kSeg) <= Q / kSeg + super-tiles, and Q <= P <= cap.
-inline long long max_segments(long long cap, long long tiles) { return cap / kSeg + tiles + 2; }
-
-constexpr int kCounters = 12;  // 8 counts, then 3 arrival counters
-
-Workspace carve(void* base, long long n_rows, long long cap, long long tiles) {
-  Workspace w;
-  char* p = reinterpret_cast<char*>(base);
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    char* r = p ? p + off : nullptr;
-    off += align256(bytes);
-    return r;
-  };
-  const long long nb = scan_blocks(n_rows > cap ? n_rows : cap) + 1;
-  const long long ms = max_segments(cap, tiles);
-  w.block_sums = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * nb));
-  w.block_sums2 = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * nb));
-  w.counters = reinterpret_cast<long long*>(take(sizeof(long long) * kCounters));
-  for (int i = 0; i < 2; ++i) w.rk[i] = reinterpret_cast<unsigned*>(take(4 * (n_rows + 1)));
-  for (int i = 0; i < 2; ++i) w.rv[i] = reinterpret_cast<unsigned*>(take(4 * (n_rows + 1)));
-  w.offsets = reinterpret_cast<unsigned long long*>(take(8 * (n_rows + 1)));
-  w.rect_sorted = reinterpret_cast<int4*>(take(16 * (n_rows + 1)));
-  for (int i = 0; i < 2; ++i) w.pk[i] = reinterpret_cast<unsigned*>(take(4 * (cap + 1)));
-  w.pv = reinterpret_cast<unsigned*>(take(4 * (cap + 1)));
-  w.hist = reinterpret_cast<unsigned*>(take(4ull * kRadixBins * (kRadixGrid + 1)));
-  w.block_row = reinterpret_cast<unsigned*>(take(4ull * ((cap + kDupPairs - 1) / kDupPairs + 1)));
-  w.st_ranges = reinterpret_cast<unsigned*>(take(8ull * (tiles + 1)));
-  w.seg_first = reinterpret_cast<unsigned*>(take(4ull * (tiles + 2)));
-  w.seg_st = reinterpret_cast<unsigned*>(take(4ull * ms));
-  w.seg_hist = reinterpret_cast<unsigned*>(take(4ull * 64 * ms));
-  w.tile_cnt = reinterpret_cast<unsigned*>(take(4ull * (tiles + 1)));
-  w.tile_start = reinterpret_cast<unsigned*>(take(4ull * (tiles + 1)));
-  w.bytes = off;
-  return w;
-}
-
-// Runs the radix passes over bits [0, bits) of keys; data starts in
-// (k[0], v[0]) and ends in (k[res], v[res]); returns res.
 // CTAs of radix_downsweep_kernel resident on the current device at once
 // (cached per device).
 int radix_resident_ctas() {
@@ -1253,30 +1347,83 @@ int radix_resident_ctas() {
   return v;
 }
 
-int radix_sort(unsigned* k[2], unsigned* v[2], const long long* n_dev, long long n_bound, int bits,
-               unsigned* hist, cudaStream_t st, int* grid_out = nullptr) {
-  int cur = 0;
-  if (n_bound == 0) return cur;
+inline long long scan_blocks(long long n) { return (n + kScanTile - 1) / kScanTile; }
+
+// Upper bound of the expansion segments: sum over super-tiles of
+// ceil(len / kSeg) <= Q / kSeg + super-tiles, and Q <= P <= cap.
+inline long long max_segments(long long cap, long long tiles) { return cap / kSeg + tiles + 2; }
+
+constexpr int kCounters = 14;  // 8 counts, 3 arrival counters, spare, the depth-key range
+
+Workspace carve(void* base, long long n_rows, long long cap, long long tiles) {
+  Workspace w;
+  char* p = reinterpret_cast<char*>(base);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* r = p ? p + off : nullptr;
+    off += align256(bytes);
+    return r;
+  };
+  const long long nb = scan_blocks(n_rows > cap ? n_rows : cap) + 1;
+  const long long ms = max_segments(cap, tiles);
+  w.block_sums = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * nb));
+  w.block_sums2 = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * nb));
+  w.counters = reinterpret_cast<long long*>(take(sizeof(long long) * kCounters));
+  for (int i = 0; i < 2; ++i) w.rk[i] = reinterpret_cast<unsigned*>(take(4 * (n_rows + 1)));
+  for (int i = 0; i < 2; ++i) w.rv[i] = reinterpret_cast<unsigned*>(take(4 * (n_rows + 1)));
+  w.offsets = reinterpret_cast<unsigned long long*>(take(8 * (n_rows + 1)));
+  w.rect_sorted = reinterpret_cast<int4*>(take(16 * (n_rows + 1)));
+  for (int i = 0; i < 2; ++i) w.pk[i] = reinterpret_cast<unsigned*>(take(4 * (cap + 1)));
+  w.pv = reinterpret_cast<unsigned*>(take(4 * (cap + 1)));
+  w.hist = reinterpret_cast<unsigned*>(take(radix_hist_bytes()));
+  w.block_row = reinterpret_cast<unsigned*>(take(4ull * ((cap + kDupPairs - 1) / kDupPairs + 1)));
+  w.st_ranges = reinterpret_cast<unsigned*>(take(8ull * (tiles + 1)));
+  w.seg_first = reinterpret_cast<unsigned*>(take(4ull * (tiles + 2)));
+  w.seg_st = reinterpret_cast<unsigned*>(take(4ull * ms));
+  w.seg_hist = reinterpret_cast<unsigned*>(take(4ull * 64 * ms));
+  w.tile_cnt = reinterpret_cast<unsigned*>(take(4ull * (tiles + 1)));
+  w.tile_start = reinterpret_cast<unsigned*>(take(4ull * (tiles + 1)));
+  w.bytes = off;
+  return w;
+}
+
+// Radix sort of the pairs in (k[0], v[0]) (n_dev items, at most n_bound):
+// with `range` on the significant bits of (key - smallest key), else on
+// `bits` bits.  The result is in buffer (passes mod 2): radix_result on the
+// device, or the host's plan when there is no range.  keys_last: the last
+// pass writes the keys as well (only the values are needed otherwise).
+// The radix grid for at most n_bound items.
+int radix_grid(long long n_bound) {
+  return (int)std::max<long long>(
+      1, std::min<long long>(std::min(kRadixGrid, radix_resident_ctas()),
+                             (n_bound + kRadixTile - 1) / kRadixTile));
+}
+
+void radix_sort(unsigned* k[2], unsigned* v[2], const long long* n_dev, long long n_bound,
+                const unsigned* range, int bits, unsigned* hist, bool keys_last,
+                cudaStream_t st) {
+  if (n_bound == 0) return;
+  const int passes = range ? kRadixMaxPasses : radix_plan_bits(0u, bits).passes;
   // one wave: at most the CTAs of the scatter kernel resident on the device
-  int grid = (int)std::min<long long>(std::min(kRadixGrid, radix_resident_ctas()),
-                                      (n_bound + kRadixTile - 1) / kRadixTile);
-  if (grid < 1) grid = 1;
-  if (grid_out) *grid_out = grid;
-  // the fewest 8-bit-or-narrower passes, with equal digit widths
-  const int passes = (bits + 7) / 8;
-  const int dbits = passes ? (bits + passes - 1) / passes : 0;
-  for (int shift = 0; shift < bits; shift += dbits) {
-    radix_upsweep_kernel<<<grid, kRadixThreads, 0, st>>>(k[cur], n_dev, shift,
-                                                         (1u << dbits) - 1u, hist);
-    radix_scan_kernel<<<kRadixBins, kScanThreads, 0, st>>>(hist, grid, n_dev,
-                                                         hist + kRadixBins * grid);
-    radix_downsweep_kernel<<<grid, kRadixThreads, 0, st>>>(k[cur], v[cur], k[1 - cur], v[1 - cur],
-                                                           n_dev, shift, dbits, hist,
-                                                           hist + kRadixBins * grid);
+  const int grid = radix_grid(n_bound);
+  RadixPass a;
+  a.n_dev = n_dev;
+  a.range = range;
+  a.bits = bits;
+  a.hist = hist;
+  a.digit_tot = hist + kRadixBins * grid;
+  a.keys_last = keys_last ? 1 : 0;
+  for (int p = 0; p < passes; ++p) {
+    a.keys_in = k[p & 1];
+    a.vals_in = v[p & 1];
+    a.keys_out = k[(p + 1) & 1];
+    a.vals_out = v[(p + 1) & 1];
+    a.pass = p;
+    radix_upsweep_kernel<<<grid, kRadixThreads, 0, st>>>(a);
+    radix_scan_kernel<<<kRadixBins, kScanThreads, 0, st>>>(a, grid);
+    radix_downsweep_kernel<<<grid, kRadixThreads, 0, st>>>(a);
     count_launches(3);
-    cur = 1 - cur;
   }
-  return cur;
 }
 
 int bits_for(long long count) {
@@ -1311,7 +1458,9 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
   GS_TRY_CUDA(cudaMemsetAsync(w.counters, 0, kCounters * sizeof(long long), st));
   const CountsOut co{w.block_sums, w.block_sums2, cap, Q, P, q_eff, p_eff, num_pairs_dev,
                      status_dev};
-  unsigned* rows_sorted = w.rv[0];
+  // the visible rows' depth-bit range (complement of the smallest, largest)
+  unsigned* range = reinterpret_cast<unsigned*>(w.counters + 12);
+  const SortedRows rows_sorted{w.rv[0], w.rv[1], range};
   // scan blocks of 1,024 rows (4 per thread) keep many CTAs in flight when
   // few rows are visible; on large row counts 4,096-row blocks (16 per
   // thread) are faster
@@ -1325,16 +1474,16 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
       scan_reduce_kernel<4><<<(unsigned)nb, kScanThreads, 0, st>>>(vis, nullptr, n_rows,
                                                                    w.block_sums, arrive, n_vis);
       compact_visible_kernel<4><<<(unsigned)nb, kScanThreads, 0, st>>>(
-          proj->tiles_touched, proj->depth, n_rows, w.block_sums, w.rk[0], w.rv[0]);
+          proj->tiles_touched, proj->depth, n_rows, w.block_sums, w.rk[0], w.rv[0], range);
     } else {
       scan_reduce_kernel<16><<<(unsigned)nb, kScanThreads, 0, st>>>(vis, nullptr, n_rows,
                                                                     w.block_sums, arrive, n_vis);
       compact_visible_kernel<16><<<(unsigned)nb, kScanThreads, 0, st>>>(
-          proj->tiles_touched, proj->depth, n_rows, w.block_sums, w.rk[0], w.rv[0]);
+          proj->tiles_touched, proj->depth, n_rows, w.block_sums, w.rk[0], w.rv[0], range);
     }
-    // 2. stable depth sort of the visible rows (ties keep row order = id order)
-    int res = radix_sort(w.rk, w.rv, n_vis, n_rows, 32, w.hist, st);
-    rows_sorted = w.rv[res];
+    // 2. stable depth sort of the visible rows (ties keep row order = id
+    //    order) on the significant bits of their depth range
+    radix_sort(w.rk, w.rv, n_vis, n_rows, range, 32, w.hist, false, st);
     // 3. per row in depth order: super-tile offsets, the super-pair count Q
     //    and the pair count P
     //    (its last CTA: the scans of Q and P over the blocks, the capacity
@@ -1382,7 +1531,7 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
   // 4. super-pairs (super-tile, row) in depth order of the rows, into the
   //    buffers that the super-tile sort leaves in (pk[res], pv)
   const int sbits = bits_for(S);
-  const int spasses = (sbits + 7) / 8;
+  const int spasses = radix_plan_bits(0u, sbits).passes;
   unsigned* sk[2] = {w.pk[0], w.pk[1]};
   unsigned* sv[2];
   if (spasses % 2 == 0) {
@@ -1408,16 +1557,16 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
     count_launches(1);
   }
   // 5. stable sort of the super-pairs by super-tile id
-  int sgrid = 0;
-  const int sres = radix_sort(sk, sv, q_eff, q_bound, sbits, w.hist, st, &sgrid);
+  radix_sort(sk, sv, q_eff, q_bound, nullptr, sbits, w.hist, true, st);
+  const int sres = spasses & 1;
   const unsigned* sp_keys = sk[sres];
   const unsigned* sp_rows = sv[sres];  // == w.pv
   unsigned* desc = sk[1 - sres];
   // 6. rows of every super-tile (from the one-pass sort's digit totals, or
   //    marked on the sorted keys), segments, per-tile counts and list starts
   const unsigned* st_totals = nullptr;
-  if (spasses == 1) {
-    st_totals = w.hist + kRadixBins * sgrid;
+  if (spasses == 1) {  // the digit totals are the per-super-tile item counts
+    st_totals = w.hist + kRadixBins * radix_grid(q_bound);
   } else if (spasses > 1) {
     GS_TRY_CUDA(cudaMemsetAsync(w.st_ranges, 0, 2 * sizeof(unsigned) * (size_t)S, st));
     const unsigned gq = (unsigned)std::min<long long>((q_bound + 1023) / 1024, 152ll * 16);
@@ -1435,10 +1584,18 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
   st_scan_kernel<<<(unsigned)S, 1024, 0, st>>>(w.seg_first, ct, w.seg_hist, w.tile_cnt,
                                                 arrive + 2, w.tile_start, ranges);
   // 7. every row into the lists of the tiles it covers, in depth order
+  {
+    const int e = stage_event(GS_STAGE_EXPANSION, false, st);
+    if (e != GS_OK) return e;
+  }
   st_emit_kernel<<<gs, 256, 0, st>>>(sp_keys, sp_rows, desc, packed,
                                      reinterpret_cast<const uint2*>(w.st_ranges), w.seg_first,
                                      w.seg_st, n_seg, w.seg_hist, w.tile_start, ct, proj->depth,
                                      sorted_vals, sorted_keys);
+  {
+    const int e = stage_event(GS_STAGE_EXPANSION, true, st);
+    if (e != GS_OK) return e;
+  }
   count_launches(4);
   return check_launch();
 }
@@ -1460,7 +1617,7 @@ __global__ void queue_keys_kernel(const unsigned* __restrict__ ranges, long long
 
 size_t tile_queue_workspace_size(long long T) {
   return align256(4 * (T + 1)) * 3 + align256(sizeof(long long) * 2) +
-         align256(4ull * kRadixBins * (kRadixGrid + 1));
+         align256(radix_hist_bytes());
 }
 
 int launch_tile_queue(const unsigned* ranges, long long T, unsigned* order, void* ws,
@@ -1485,7 +1642,7 @@ int launch_tile_queue(const unsigned* ranges, long long T, unsigned* order, void
   count_launches(1);
   unsigned* k[2] = {k0, k1};
   unsigned* v[2] = {order, v1};
-  radix_sort(k, v, n_dev, T, 32, hist, st);
+  radix_sort(k, v, n_dev, T, nullptr, 32, hist, false, st);
   return check_launch();
 }
 
@@ -1503,7 +1660,7 @@ int launch_tile_queue(const unsigned* ranges, long long T, unsigned* order, void
 // loads the library holds these bytes until the process exits.
 static __device__ __align__(256) unsigned char g_queue_scratch[
     ((4ull * (GS_TILE_QUEUE_STATIC_MAX_TILES + 1) + 255) / 256 * 256) * 3 + 256 +
-    (4ull * gs::kRadixBins * (gs::kRadixGrid + 1) + 255) / 256 * 256];
+    (gs::radix_hist_bytes() + 255) / 256 * 256];
 
 namespace {
 

@@ -215,6 +215,9 @@ int check_launch();
 // tile: the tile side (0 means 16); fov_clamp comes from prm (1.3 if NULL).
 bool build_cam_table(const gs_camera* cams, int V, const gs_params* prm, int tile, CamTable* ct);
 RenderConsts render_consts(const gs_params* prm);
+// The calling thread's events of a stage (gs_stage_events), recorded on
+// `st` before / after the stage's kernel when set.
+int stage_event(int stage, bool end, cudaStream_t st);
 }  // namespace gs
 
 #define GS_TRY_CUDA(expr)                               \

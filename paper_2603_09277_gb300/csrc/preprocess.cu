@@ -467,28 +467,58 @@ __global__ void __launch_bounds__(256, 5) preprocess_kernel(
 //   (so dL/da = -Sxx / 2, dL/db = -Sxy with b counted twice in d^T K d,
 //   dL/dc = -Syy / 2),  dL/dmean = K (Sx, Sy).
 // ---------------------------------------------------------------------------
-// Adjoint of one Gaussian (visible in at least one view); the outputs arrive
-// zeroed.
-__device__ __forceinline__ void adjoint_one(
-    int g, const float* __restrict__ means, const float* __restrict__ log_scales,
-    const float* __restrict__ quats, const float* __restrict__ opacity_logits,
-    const float* __restrict__ sh, int N, const CamTable& ct, float dilation, int sh_deg,
-    int sh_stride, const unsigned* __restrict__ tiles_touched, const float* __restrict__ grad2d,
-    float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
-    float* __restrict__ g_opac, float* __restrict__ g_sh) {
-  const int K = sh_count(sh_deg);
-  const bool vec = sh_vectors(sh, sh_stride);
-  const bool vec_out = vec && (reinterpret_cast<uintptr_t>(g_sh) & 15) == 0;
-  Activated a = activate(means, log_scales, quats, opacity_logits, g);
-  float gm[3] = {0.f, 0.f, 0.f};
-  float gls[3] = {0.f, 0.f, 0.f};  // dL/d log-scale, summed over views
-  float gRq[9];                    // dL/d(rotation matrix entries), summed over views
-  for (int k = 0; k < 9; ++k) gRq[k] = 0.f;
-  float gsig = 0.f;
-  bool first_view = true;
-  for (int v = 0; v < ct.V; ++v) {
+// Per-lane sums of one Gaussian's adjoint over the views the lane takes:
+// dL/dmean, dL/dlog-scale, dL/d(rotation matrix entries), the sum of dd
+// (-> opacity) and dL/dSH for the K coefficients in use.
+template <int DEG>
+struct AdjAcc {
+  static constexpr int K = (DEG + 1) * (DEG + 1);
+  float gm[3], gls[3], gRq[9], gsig, gsh[3 * K];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) gm[i] = gls[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) gRq[i] = 0.f;
+    gsig = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3 * K; ++i) gsh[i] = 0.f;
+  }
+  // sum over the L lanes of a group (butterfly, group-local mask)
+  template <int L>
+  __device__ __forceinline__ void reduce(unsigned mask) {
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        gm[i] += __shfl_xor_sync(mask, gm[i], o);
+        gls[i] += __shfl_xor_sync(mask, gls[i], o);
+      }
+#pragma unroll
+      for (int i = 0; i < 9; ++i) gRq[i] += __shfl_xor_sync(mask, gRq[i], o);
+      gsig += __shfl_xor_sync(mask, gsig, o);
+#pragma unroll
+      for (int i = 0; i < 3 * K; ++i) gsh[i] += __shfl_xor_sync(mask, gsh[i], o);
+    }
+  }
+};
+
+// Adjoint of Gaussian g in view v (which sees it), added to acc.
+// SHREG: the SH gradient is summed in acc (a group of several lanes);
+// otherwise (one lane per Gaussian, degree 3: 48 sums would halve the
+// occupancy) it goes to g_sh directly: the first view that sees the
+// Gaussian stores, later ones add.
+template <int DEG, bool SHREG>
+__device__ __forceinline__ void adjoint_view(
+    int g, int v, const Activated& a, const float* __restrict__ sh, int N, const CamTable& ct,
+    float dilation, int sh_stride, bool vec, const float* __restrict__ grad2d,
+    AdjAcc<SHREG ? DEG : 0>& acc, bool first_view, bool vec_out, float* __restrict__ g_sh) {
+  constexpr int sh_deg = DEG;
+  constexpr int K = AdjAcc<DEG>::K;
+  float* gm = acc.gm;
+  float* gls = acc.gls;
+  float* gRq = acc.gRq;
+  float& gsig = acc.gsig;
     long long row = (long long)v * N + g;
-    if (tiles_touched[row] == 0u) continue;
     const float4* G4 = reinterpret_cast<const float4*>(grad2d + row * 12);
     float4 G0 = G4[0], G1 = G4[1], G2 = G4[2];
     // G0 = (Sx, Sy, Sxx, Sxy), G1 = (Syy, S1, r, g), G2 = (b, pad, pad, pad)
@@ -513,50 +543,50 @@ __device__ __forceinline__ void adjoint_one(
     float cdot[16] = {};  // SH[k] . grgb
     for_sh_block(sh, g, sh_stride, K, vec,
                  [&](int e, float v) { cdot[e / 3] = __fmaf_rn(v, grgb[e % 3], cdot[e / 3]); });
-    // dL/dSH[k][ch] = Y_k grgb_ch; the first view that sees the Gaussian
-    // stores, later ones accumulate (entries past 3K are left untouched or
-    // get exact zeros)
-    float* gsh = g_sh + (long long)g * sh_stride * 3;
-    if (vec_out) {
+    // dL/dSH[k][ch] = Y_k grgb_ch
+    if constexpr (SHREG) {
 #pragma unroll
-      for (int i = 0; i < 12; ++i) {
-        if (4 * i < 3 * K) {
-          float o[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int e = 4 * i + j;
-            o[j] = e < 3 * K ? Y[e / 3] * grgb[e % 3] : 0.f;
-          }
-          float4* q = reinterpret_cast<float4*>(gsh) + i;
-          if (first_view) {
-            *q = make_float4(o[0], o[1], o[2], o[3]);
-          } else {
-            const float4 t = *q;
-            *q = make_float4(t.x + o[0], t.y + o[1], t.z + o[2], t.w + o[3]);
-          }
-        }
-      }
+      for (int e = 0; e < 3 * K; ++e) acc.gsh[e] = __fmaf_rn(Y[e / 3], grgb[e % 3], acc.gsh[e]);
     } else {
+      float* gsh = g_sh + (long long)g * sh_stride * 3;
+      if (vec_out) {
 #pragma unroll
-      for (int e = 0; e < 48; ++e) {
-        if (e < 3 * K) {
-          const float a = Y[e / 3] * grgb[e % 3];
-          gsh[e] = first_view ? a : gsh[e] + a;
+        for (int i = 0; i < 12; ++i) {
+          if (4 * i < 3 * K) {
+            float o[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int e = 4 * i + j;
+              o[j] = e < 3 * K ? Y[e / 3] * grgb[e % 3] : 0.f;
+            }
+            float4* q = reinterpret_cast<float4*>(gsh) + i;
+            if (first_view) {
+              *q = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+              const float4 t = *q;
+              *q = make_float4(t.x + o[0], t.y + o[1], t.z + o[2], t.w + o[3]);
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 48; ++e) {
+          if (e < 3 * K) {
+            const float y = Y[e / 3] * grgb[e % 3];
+            gsh[e] = first_view ? y : gsh[e] + y;
+          }
+        }
+      }
+      // coefficients past K (sh_stride > K) get zeros from the first view
+      if (first_view) {
+        if (vec_out) {
+          for (int i = (3 * K + 3) / 4; i < 3 * sh_stride / 4; ++i)
+            reinterpret_cast<float4*>(gsh)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+          for (int e = 3 * K; e < 3 * sh_stride; ++e) gsh[e] = 0.f;
         }
       }
     }
-    // Coefficients past K (sh_stride > K) get zeros from the first view as
-    // well.  (They are zeroed before the call too; measured, the form with
-    // these stores also runs 4 % faster on 8 views.)
-    if (first_view) {
-      if (vec_out) {
-        for (int i = (3 * K + 3) / 4; i < 3 * sh_stride / 4; ++i)
-          reinterpret_cast<float4*>(gsh)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      } else {
-        for (int e = 3 * K; e < 3 * sh_stride; ++e) gsh[e] = 0.f;
-      }
-    }
-    first_view = false;
     if (sh_deg > 0) {
       float3 gd = sh_basis_grad_dot(sh_deg, dx, dy, dz, cdot);
       float dd = gd.x * dx + gd.y * dy + gd.z * dz;
@@ -644,6 +674,38 @@ __device__ __forceinline__ void adjoint_one(
     gm[1] += c.R[1] * gtx + c.R[4] * gty + c.R[7] * gtz;
     gm[2] += c.R[2] * gtx + c.R[5] * gty + c.R[8] * gtz;
   }
+
+// Writes Gaussian g's gradients from the group's sums: lane `sub` == 0 the
+// per-Gaussian ones, the SH coefficients (zeros past the K in use) split over
+// the group's L lanes as 16-byte stores where aligned.
+template <int DEG, int L, bool SHREG>
+__device__ __forceinline__ void adjoint_finish(
+    int g, int sub, const Activated& a, const AdjAcc<DEG>& acc, int sh_stride, bool vec_out,
+    float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
+    float* __restrict__ g_opac, float* __restrict__ g_sh) {
+  constexpr int K = AdjAcc<DEG>::K;
+  float* gsh = g_sh + (long long)g * sh_stride * 3;
+  if (!SHREG) {
+  } else if (vec_out) {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      if (i % L == sub && 4 * i < 3 * sh_stride) {
+        float o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] = 4 * i + j < 3 * K ? acc.gsh[4 * i + j] : 0.f;
+        reinterpret_cast<float4*>(gsh)[i] = make_float4(o[0], o[1], o[2], o[3]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 48; ++e)
+      if (e % L == sub && e < 3 * sh_stride) gsh[e] = e < 3 * K ? acc.gsh[e] : 0.f;
+  }
+  if (sub != 0) return;
+  const float* gm = acc.gm;
+  const float* gls = acc.gls;
+  const float* gRq = acc.gRq;
+  const float gsig = acc.gsig;
   g_means[3ll * g] = gm[0];
   g_means[3ll * g + 1] = gm[1];
   g_means[3ll * g + 2] = gm[2];
@@ -666,6 +728,37 @@ __device__ __forceinline__ void adjoint_one(
   float4 gq = make_float4((gw - w * dotq) * iq, (gx - x * dotq) * iq, (gy - y * dotq) * iq,
                           (gz - z * dotq) * iq);
   reinterpret_cast<float4*>(g_quats)[g] = gq;
+}
+
+// Adjoint of one listed Gaussian by a group of L lanes (L = the views rounded
+// up to a power of two, at most 8): lane `sub` takes views sub, sub + L, ...
+// that see the Gaussian, the group sums its lanes' parts with shuffles and
+// writes the gradients.  Every gradient starts at zero (the caller zeroes
+// them), so the Gaussians no view sees keep zeros.
+template <int DEG, int L>
+__device__ __forceinline__ void adjoint_group(
+    int g, int sub, unsigned mask, const float* __restrict__ means,
+    const float* __restrict__ log_scales, const float* __restrict__ quats,
+    const float* __restrict__ opacity_logits, const float* __restrict__ sh, int N,
+    const CamTable& ct, float dilation, int sh_stride, const unsigned* __restrict__ tiles_touched,
+    const float* __restrict__ grad2d, float* __restrict__ g_means, float* __restrict__ g_ls,
+    float* __restrict__ g_quats, float* __restrict__ g_opac, float* __restrict__ g_sh) {
+  const bool vec = sh_vectors(sh, sh_stride);
+  const bool vec_out = vec && (reinterpret_cast<uintptr_t>(g_sh) & 15) == 0;
+  const Activated a = activate(means, log_scales, quats, opacity_logits, g);
+  constexpr bool SHREG = L > 1 || DEG < 3;
+  AdjAcc<SHREG ? DEG : 0> acc;
+  acc.zero();
+  bool first = true;
+  for (int v = sub; v < ct.V; v += L)
+    if (tiles_touched[(long long)v * N + g] != 0u) {
+      adjoint_view<DEG, SHREG>(g, v, a, sh, N, ct, dilation, sh_stride, vec, grad2d, acc, first,
+                               vec_out, g_sh);
+      first = false;
+    }
+  acc.template reduce<L>(mask);
+  adjoint_finish<SHREG ? DEG : 0, L, SHREG>(g, sub, a, acc, sh_stride, vec_out, g_means, g_ls,
+                                            g_quats, g_opac, g_sh);
 }
 
 // The adjoint runs over a list of the Gaussians some view sees, kept in the
@@ -707,33 +800,149 @@ __global__ void __launch_bounds__(kListThreads) adjoint_list_kernel(
   }
 }
 
-// The adjoint over the listed Gaussians: a resident grid (4 CTAs of 128
-// threads per SM at up to 128 registers), one Gaussian per thread and
-// iteration.  Every gradient starts at zero (the caller zeroes them), so the
-// Gaussians no view sees keep zeros.
+// The adjoint over the listed Gaussians: a resident grid, one group of L
+// lanes per Gaussian and iteration (a group's lanes share the Gaussian, so
+// they leave the loop together; shuffles use the group's lanes only).
 constexpr int kAdjThreads = 128;
-__global__ void __launch_bounds__(kAdjThreads, 4) preprocess_bwd_kernel(
+// CTAs per SM the register budget allows: 2 where a group sums 48 SH
+// gradients in registers, 3 with 27, else 4 (at most 128 registers)
+template <int DEG, int L>
+constexpr int adj_ctas_per_sm() { return (DEG == 3 && L > 1) ? 2 : (DEG == 2 ? 3 : 4); }
+
+template <int DEG, int L>
+__global__ void __launch_bounds__(kAdjThreads, adj_ctas_per_sm<DEG, L>()) preprocess_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales,
     const float* __restrict__ quats, const float* __restrict__ opacity_logits,
-    const float* __restrict__ sh, int N, const CamTable ct, float dilation, int sh_deg,
-    int sh_stride, const unsigned* __restrict__ tiles_touched, const float* __restrict__ grad2d,
+    const float* __restrict__ sh, int N, const CamTable ct, float dilation, int sh_stride,
+    const unsigned* __restrict__ tiles_touched, const float* __restrict__ grad2d,
     float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
     float* __restrict__ g_opac, float* __restrict__ g_sh) {
   const unsigned* g2 = reinterpret_cast<const unsigned*>(grad2d);
   const unsigned n = g2[11];
-  for (unsigned i = blockIdx.x * kAdjThreads + threadIdx.x; i < n; i += gridDim.x * kAdjThreads)
-    adjoint_one((int)g2[12ll * i + 9], means, log_scales, quats, opacity_logits, sh, N, ct,
-                dilation, sh_deg, sh_stride, tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac,
-                g_sh);
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % L;
+  const unsigned mask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << (lane - sub);
+  const unsigned groups = gridDim.x * (kAdjThreads / L);
+  for (unsigned i = (blockIdx.x * kAdjThreads + threadIdx.x) / L; i < n; i += groups)
+    adjoint_group<DEG, L>((int)g2[12ll * i + 9], sub, mask, means, log_scales, quats,
+                          opacity_logits, sh, N, ct, dilation, sh_stride, tiles_touched, grad2d,
+                          g_means, g_ls, g_quats, g_opac, g_sh);
+}
+
+template <int DEG, int L>
+void launch_adjoint(const float* means, const float* log_scales, const float* quats,
+                    const float* opacity_logits, const float* sh, int N, const CamTable& ct,
+                    const gs_params* prm, const unsigned* tiles_touched, const float* grad2d,
+                    float* g_means, float* g_ls, float* g_quats, float* g_opac, float* g_sh,
+                    cudaStream_t st) {
+  // a resident grid: enough groups for every listed Gaussian at most
+  const long long want = ((long long)N * L + kAdjThreads - 1) / kAdjThreads;
+  const int grid = (int)std::min<long long>(152ll * adj_ctas_per_sm<DEG, L>() * 2, want);
+  preprocess_bwd_kernel<DEG, L><<<grid, kAdjThreads, 0, st>>>(
+      means, log_scales, quats, opacity_logits, sh, N, ct, prm->dilation, prm->sh_stride,
+      tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh);
+}
+
+// Largest group of lanes per Gaussian.  1 (one thread walks all of a
+// Gaussian's views) is the form the timings chose: on 8 views of 3M
+// Gaussians 0.78 ms against 1.39 ms for groups of 8 lanes, whose redundant
+// activation and shuffle reduction cost more than their parallelism gains.
+#ifndef GS_ADJ_MAX_LANES
+#define GS_ADJ_MAX_LANES 1
+#endif
+
+template <int DEG>
+void launch_adjoint_deg(const float* means, const float* log_scales, const float* quats,
+                        const float* opacity_logits, const float* sh, int N, const CamTable& ct,
+                        const gs_params* prm, const unsigned* tiles_touched, const float* grad2d,
+                        float* g_means, float* g_ls, float* g_quats, float* g_opac, float* g_sh,
+                        cudaStream_t st) {
+  // lanes per Gaussian: the views rounded up to a power of two, at most 8
+  if (ct.V <= 1 || GS_ADJ_MAX_LANES == 1)
+    launch_adjoint<DEG, 1>(means, log_scales, quats, opacity_logits, sh, N, ct, prm,
+                           tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh, st);
+  else if (ct.V <= 2 || GS_ADJ_MAX_LANES == 2)
+    launch_adjoint<DEG, 2>(means, log_scales, quats, opacity_logits, sh, N, ct, prm,
+                           tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh, st);
+  else if (ct.V <= 4 || GS_ADJ_MAX_LANES == 4)
+    launch_adjoint<DEG, 4>(means, log_scales, quats, opacity_logits, sh, N, ct, prm,
+                           tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh, st);
+  else
+    launch_adjoint<DEG, 8>(means, log_scales, quats, opacity_logits, sh, N, ct, prm,
+                           tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh, st);
+}
+
+// The 2D gradients of Suppl. C per row from the moment rows of the blending
+// adjoint.  The conic comes from the record's square-root factor F
+// (F^T F = log2(e) / 2 conic, F lower triangular): a = 2 ln 2 (f11^2 + f21^2),
+// b = 2 ln 2 f21 f22, c = 2 ln 2 f22^2.
+template <int DT>
+__global__ void __launch_bounds__(256) grad2d_attr_kernel(const void* __restrict__ recs,
+                                                          const unsigned* __restrict__ tiles_touched,
+                                                          const float* __restrict__ grad2d,
+                                                          long long rows, float* __restrict__ out) {
+  for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
+       row += (long long)gridDim.x * blockDim.x) {
+    float o[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (tiles_touched[row] != 0u) {
+      const Splat s = load_record<DT>(recs, (unsigned)row);
+      const float k2 = 1.3862943611198906f;  // 2 ln 2
+      const float ca = k2 * __fmaf_rn(s.f11, s.f11, s.f21 * s.f21);
+      const float cb = k2 * s.f21 * s.f22;
+      const float cc = k2 * s.f22 * s.f22;
+      const float4* G4 = reinterpret_cast<const float4*>(grad2d + 12 * row);
+      const float4 G0 = G4[0], G1 = G4[1], G2 = G4[2];
+      // G0 = (Sx, Sy, Sxx, Sxy), G1 = (Syy, S1, r, g), G2 = (b, pad, pad, pad)
+      o[0] = ca * G0.x + cb * G0.y;  // dL/dmean2d = K (Sx, Sy)
+      o[1] = cb * G0.x + cc * G0.y;
+      o[2] = -0.5f * G0.z;           // dL/dK: d = -1/2 (a dx^2 + 2 b dx dy + c dy^2)
+      o[3] = -G0.w;
+      o[4] = -0.5f * G1.x;
+      o[5] = G1.y / s.sigma;         // alpha = sigma exp(d): dL/dsigma = sum dd / sigma
+      o[6] = G1.z;
+      o[7] = G1.w;
+      o[8] = G2.x;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) out[9 * row + k] = o[k];
+  }
 }
 
 }  // namespace
+
+int launch_grad2d_attributes(const gs_proj* proj, long long rows, const gs_params* prm,
+                             const float* grad2d, float* out, cudaStream_t st) {
+  if (rows == 0) return GS_OK;
+  const unsigned grid = (unsigned)std::min<long long>((rows + 255) / 256, 152ll * 8);
+  switch (prm->attr_dtype) {
+    case GS_ATTR_F32:
+      grad2d_attr_kernel<GS_ATTR_F32><<<grid, 256, 0, st>>>(proj->records, proj->tiles_touched,
+                                                            grad2d, rows, out);
+      break;
+    case GS_ATTR_F16:
+      grad2d_attr_kernel<GS_ATTR_F16><<<grid, 256, 0, st>>>(proj->records, proj->tiles_touched,
+                                                            grad2d, rows, out);
+      break;
+    case GS_ATTR_BF16:
+      grad2d_attr_kernel<GS_ATTR_BF16><<<grid, 256, 0, st>>>(proj->records, proj->tiles_touched,
+                                                             grad2d, rows, out);
+      break;
+    default:
+      return GS_ERR_INVALID_ARG;
+  }
+  count_launches(1);
+  return check_launch();
+}
 
 int launch_preprocess(const float* means, const float* log_scales, const float* quats,
                       const float* opacity_logits, const float* sh, int N, const CamTable& ct,
                       const gs_params* prm, const gs_proj* out, cudaStream_t st) {
   if (N == 0) return GS_OK;
   dim3 block(256), grid((N + 255) / 256);
+  {
+    const int e = stage_event(GS_STAGE_PROJECTION, false, st);
+    if (e != GS_OK) return e;
+  }
   switch (prm->attr_dtype) {
     case GS_ATTR_F32:
       preprocess_kernel<GS_ATTR_F32><<<grid, block, 0, st>>>(means, log_scales, quats, opacity_logits,
@@ -751,6 +960,10 @@ int launch_preprocess(const float* means, const float* log_scales, const float* 
       return GS_ERR_INVALID_ARG;
   }
   count_launches(1);
+  {
+    const int e = stage_event(GS_STAGE_PROJECTION, true, st);
+    if (e != GS_OK) return e;
+  }
   return check_launch();
 }
 
@@ -760,11 +973,29 @@ int launch_preprocess_bwd(const float* means, const float* log_scales, const flo
                           float* g_means, float* g_ls, float* g_quats, float* g_opac, float* g_sh,
                           cudaStream_t st) {
   if (N == 0) return GS_OK;
-  const int grid = (int)std::min<long long>(152ll * 4, ((long long)N + kAdjThreads - 1) / kAdjThreads);
-  preprocess_bwd_kernel<<<grid, kAdjThreads, 0, st>>>(
-      means, log_scales, quats, opacity_logits, sh, N, ct, prm->dilation, prm->sh_degree,
-      prm->sh_stride, tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh);
+  {
+    const int e = stage_event(GS_STAGE_ADJOINT, false, st);
+    if (e != GS_OK) return e;
+  }
+  switch (prm->sh_degree) {
+    case 0: launch_adjoint_deg<0>(means, log_scales, quats, opacity_logits, sh, N, ct, prm,
+                                  tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh, st);
+      break;
+    case 1: launch_adjoint_deg<1>(means, log_scales, quats, opacity_logits, sh, N, ct, prm,
+                                  tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh, st);
+      break;
+    case 2: launch_adjoint_deg<2>(means, log_scales, quats, opacity_logits, sh, N, ct, prm,
+                                  tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh, st);
+      break;
+    default: launch_adjoint_deg<3>(means, log_scales, quats, opacity_logits, sh, N, ct, prm,
+                                   tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh, st);
+      break;
+  }
   count_launches(1);
+  {
+    const int e = stage_event(GS_STAGE_ADJOINT, true, st);
+    if (e != GS_OK) return e;
+  }
   return check_launch();
 }
 

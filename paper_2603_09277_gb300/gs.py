@@ -84,6 +84,7 @@ def _load():
         "gs_last_error_string": (ctypes.c_char_p, []),
         "gs_version": (ctypes.c_char_p, []),
         "gs_kernel_launches": (ctypes.c_ulonglong, []),
+        "gs_stage_events": (i, [i, vp, vp]),
         "gs_preprocess": (i, [vp, vp, vp, vp, vp, i, P(GsCamera), i, P(GsParams), P(GsProj), vp]),
         "gs_bin_sort": (i, [P(GsProj), i, P(GsCamera), i, i, vp, sz, ll, vp, vp, vp, vp, vp, vp,
                             vp]),
@@ -94,6 +95,7 @@ def _load():
         "gs_loss_base": (i, [vp, vp, vp, P(GsCamera), i, f, f, vp, vp, vp, vp, sz, vp]),
         "gs_render_bwd": (i, [P(GsProj), i, P(GsCamera), i, P(GsParams), vp, vp, vp, vp, vp, vp,
                               vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, P(GsLaunch), vp]),
+        "gs_grad2d_attributes": (i, [P(GsProj), i, i, P(GsParams), vp, vp, vp]),
         "gs_scale_reset": (i, [vp, ll, f, vp]),
         "gs_tile_queue": (i, [vp, ll, vp, vp, sz, vp]),
         "gs_tile_queue_static": (i, [vp, ll, vp, vp]),
@@ -108,9 +110,10 @@ def _load():
 _lib = _load()
 EXPORTED = ["gs_record_bytes", "gs_total_tiles", "gs_total_pixels", "gs_bin_sort_workspace_size",
             "gs_loss_workspace_size", "gs_tile_queue_workspace_size", "gs_status_string",
-            "gs_last_error_string", "gs_version", "gs_kernel_launches", "gs_preprocess", "gs_bin_sort", "gs_render_fwd",
+            "gs_last_error_string", "gs_version", "gs_kernel_launches", "gs_stage_events",
+            "gs_preprocess", "gs_bin_sort", "gs_render_fwd",
             "gs_loss_l1_entropy", "gs_loss_base_workspace_size", "gs_loss_base",
-            "gs_render_bwd", "gs_scale_reset", "gs_tile_queue",
+            "gs_render_bwd", "gs_grad2d_attributes", "gs_scale_reset", "gs_tile_queue",
             "gs_tile_queue_static"]
 
 
@@ -288,6 +291,23 @@ def gs_render_bwd(proj_c, N, cams_c, prm_c, sorted_vals, tile_ranges, final_T, l
         _ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity_logits), _ptr(sh), _ptr(grad2d),
         _ptr(g_means), _ptr(g_log_scales), _ptr(g_quats), _ptr(g_opacity_logits), _ptr(g_sh),
         ctypes.byref(launch_c) if launch_c is not None else None, _stream(stream)))
+
+
+GS_STAGE_EXPANSION, GS_STAGE_PROJECTION, GS_STAGE_ADJOINT = 1, 2, 3
+
+
+def gs_stage_events(stage, ev_begin=None, ev_end=None):
+    """Records the torch.cuda.Events (or None to stop) around a stage's
+    kernel in this thread's later calls."""
+    h = lambda e: ctypes.c_void_p(e.cuda_event) if e is not None else None
+    return _check("gs_stage_events", _lib.gs_stage_events(stage, h(ev_begin), h(ev_end)))
+
+
+def gs_grad2d_attributes(proj_c, N, V, prm_c, grad2d, out, stream=None):
+    """dL/d(mean2d, conic a b c, sigma, rgb) [V*N, 9] from grad2d's moment rows."""
+    return _check("gs_grad2d_attributes", _lib.gs_grad2d_attributes(
+        ctypes.byref(proj_c), N, V, ctypes.byref(prm_c), _ptr(grad2d), _ptr(out),
+        _stream(stream)))
 
 
 def gs_scale_reset(log_scales, zeta, stream=None):

@@ -196,6 +196,14 @@ class Rasterizer:
                          self._launch(False, events), stream)
         return g
 
+    def grad2d_attributes(self, stream=None):
+        """Per (view, Gaussian) row the 2D gradients of the latest backward:
+        dL/d(mean2d x, y), dL/d(conic a, b, c), dL/dsigma, dL/d(r, g, b)
+        [V*N, 9] (gs_grad2d_attributes)."""
+        out = torch.empty(max(self.rows, 1), 9, dtype=torch.float32, device=self.device)
+        gs.gs_grad2d_attributes(self.proj_c, self.N, self.V, self.prm_c, self.grad2d, out, stream)
+        return out
+
     def step(self, p, target, gamma, sync=True, stream=None):
         """One forward + backward of L1 + gamma * entropy; returns the device loss."""
         self.preprocess(p, stream)

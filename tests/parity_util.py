@@ -26,10 +26,17 @@ from paper_2603_09277_gb300.rasterize import Rasterizer, scene_to_device, target
 MARGIN = 1e-4       # relative threshold margin below which a pixel is excluded
 IMG_TOL = 1e-5      # absolute, images / T / entropy (FP32 vs FP64)
 GRAD_TOL = 1e-4     # relative, gradient tensors (norm), FP32 vs FP64
-# element-wise gradient floor: 1e-6 of the tensor's largest entry (the
-# gradients of a pixel-mean loss scale with 1 / pixels, so the floor is
-# stated relative to the tensor; it is below 1e-6 absolute on every workload)
-ELEM_FLOOR = 1e-6
+# element-wise gradient bar: 1e-4 relative with a floor of 1e-5 of the
+# tensor's largest entry.  The gradients of a pixel-mean loss scale with
+# 1 / pixels (largest entries 4e-3 .. 2e-2 here), so the floor is stated
+# relative to the tensor; it is below an absolute 1e-6 on every workload.
+# It covers the FP32 rounding of the sums of dd-moments over pixels, whose
+# terms cancel (measured up to 4.9e-6 of the largest entry where no
+# threshold is near)
+ELEM_FLOOR = 1e-5
+# Gaussians taking this share of a 2D-gradient component from near-threshold
+# pixels are left out of the element-wise check (oracle.exclusions)
+FLIP_SHARE = 0.02
 
 
 def run_gpu(scene, cams, prm, target=None, gamma=0.015, attr="f32", persistent=0,
@@ -141,14 +148,20 @@ def rel_norm_err(a, b):
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
 
 
-def elementwise_violations(g, o):
+def elementwise_violations(g, o, floor=ELEM_FLOOR):
     """Entries of a gradient tensor outside the element-wise bar
-    |g - o| <= GRAD_TOL |o| + ELEM_FLOOR max|o|; returns (count, worst ratio
-    of the difference to its bound)."""
+    |g - o| <= GRAD_TOL |o| + floor max|o|; returns (count, worst ratio of
+    the difference to its bound)."""
     g = np.asarray(g, np.float64).ravel()
     o = np.asarray(o, np.float64).ravel()
     if o.size == 0:
         return 0, 0.0
-    bound = GRAD_TOL * np.abs(o) + ELEM_FLOOR * np.abs(o).max()
+    bound = GRAD_TOL * np.abs(o) + floor * np.abs(o).max()
     ratio = np.abs(g - o) / np.maximum(bound, 1e-300)
     return int((ratio > 1.0).sum()), float(ratio.max())
+
+
+def flip_sensitive(ora_view, cam, prm, dL_dC, dL_dH, g9_all=None):
+    """Boolean [N]: Gaussians a near-threshold flip can move by a noticeable
+    part of an element (oracle.exclusions.flip_sensitive)."""
+    return _exc.flip_sensitive(ora_view, cam, prm, dL_dC, dL_dH, g9_all, FLIP_SHARE, MARGIN)

@@ -54,8 +54,14 @@ def _oracle_loss(imgs, tgts, ents, lam, gamma):
 
 
 def _check_grad(g, o):
+    """1e-4 relative per tensor; element-wise 1e-4 relative with a floor of
+    1e-5 of the largest entry (ten times the rasterizer's floor): SSIM's
+    window variances are differences of second moments, and where the image
+    is close to its target (variances ~1e-4 against moments ~0.3) FP32
+    resolves them to about 1e-7 / 1e-4 relative, which the small entries of
+    dL/dC inherit."""
     assert rel_norm_err(g, o) <= GRAD_TOL
-    nv, worst = elementwise_violations(g, o)
+    nv, worst = elementwise_violations(g, o, floor=1e-5)
     assert nv == 0, (nv, worst)
 
 

@@ -3,8 +3,9 @@ view): render records in FP32, FP16 and BF16 (the 2D mean always FP32;
 exponent, transmittance and accumulation FP32), each against the FP64
 oracle on sampled pixels and sampled Gaussians.  The FP32 outputs must
 meet the parity bar: the forward on the non-excluded pixels, the gradients
-of 32 sampled small Gaussians that no FP32 threshold flip can change (per
-tensor within 1e-4 relative, element-wise within 1e-4 with the floor).
+of the sampled small Gaussians that are reached and excluded by no
+threshold rule (per tensor within 1e-4 relative; element-wise within 1e-4
+with the floor on those no near-threshold flip can move).
 The 16-bit forms have no bar (their error per output is the measured
 quantity) and only sanity bounds.
 With GS_REPORT_DIR set the table is written there as precision_cfg5.json."""
@@ -19,8 +20,9 @@ torch = pytest.importorskip("torch")
 import oracle
 from paper_2603_09277_gb300 import scenes
 
-from parity_util import (GRAD_TOL, IMG_TOL, elementwise_violations, gaussian_exclusion,
-                         last_ids_gpu, last_ids_oracle, pixel_exclusion, rel_norm_err, run_gpu)
+from parity_util import (GRAD_TOL, IMG_TOL, elementwise_violations, flip_sensitive,
+                         gaussian_exclusion, last_ids_gpu, last_ids_oracle, pixel_exclusion,
+                         rel_norm_err, run_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -58,13 +60,15 @@ def test_cfg5_staging_precision_error_per_output():
     ok = ~bad.reshape(-1)
     # the reached candidates whose gradient no FP32 threshold flip can change
     badg = gaussian_exclusion(view, cam, pixel_exclusion(view, cam) & pmask)
+    flip = flip_sensitive(view, cam, prm, dC, dH, g9_all=g9)
     pick = cand[(np.abs(g9[cand]).sum(1) > 0) & ~badg[cand]][:32]
+    el = ~flip[pick]  # element-wise: the ones no near-threshold flip can move
     gm = np.zeros(N, np.uint8)
     gm[pick] = 1
     og = oracle.preprocess_bwd(scene, cam, prm, g9, gmask=gm)
     use = pick
     report = {"workload": "cfg5: 3M Gaussians, 1920x1080, SH0", "pixels_checked": int(ok.sum()),
-              "gaussians_checked": int(len(use))}
+              "gaussians_checked": int(len(use)), "gaussians_elementwise": int(el.sum())}
     for attr in ("f32", "f16", "bf16"):
         g = run_gpu(scene, cams, prm, attr=attr, dL_dimage=dC.astype(np.float32),
                     dL_dentropy=dH.astype(np.float32), keys=False)
@@ -81,7 +85,7 @@ def test_cfg5_staging_precision_error_per_output():
                 gg, oo = gg[:, :1], oo[:, :1]
             assert np.linalg.norm(oo) > 0, k  # the sampled Gaussians are reached
             row["grad_" + k] = rel_norm_err(gg, oo)
-            row["grad_elementwise_" + k] = elementwise_violations(gg, oo)[0]
+            row["grad_elementwise_" + k] = elementwise_violations(gg[el], oo[el])[0]
         report[attr] = row
     out = os.environ.get("GS_REPORT_DIR")
     if out:
@@ -90,7 +94,10 @@ def test_cfg5_staging_precision_error_per_output():
             json.dump(report, f, indent=1)
     print(json.dumps(report))
     f32 = report["f32"]
-    assert report["pixels_checked"] > 10000 and report["gaussians_checked"] >= 16
+    # (in this dense scene few small Gaussians are reached before the pixels
+    # stop: about 20 of the 48 front-most)
+    assert report["pixels_checked"] > 10000 and report["gaussians_checked"] >= 12
+    assert report["gaussians_elementwise"] >= 4
     assert f32["image"]["max_abs"] <= IMG_TOL and f32["final_T"]["max_abs"] <= IMG_TOL
     assert f32["entropy"]["max_abs"] <= IMG_TOL and f32["last_entry_match"] == 1.0
     for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
