@@ -23,6 +23,8 @@
  *    tile_offset_v + ty * TX_v + tx with TX_v = ceil(W_v / 16),
  *    TY_v = ceil(H_v / 16), tile_offset_v = sum_{u<v} TX_u TY_u.
  *  - Pixel (x, y) is sampled at (x + 0.5, y + 0.5); the background is black.
+ *  - A view is at most 65535 tiles wide and high (1,048,560 pixels at 16-pixel
+ *    tiles); larger cameras are invalid arguments.
  *
  * Error behaviour on the device: no kernel traps or asserts.  Capacity
  * overflow of the pair buffers is reported through a device status word

@@ -150,6 +150,7 @@ bool build_cam_table(const gs_camera* cams, int V, const gs_params* prm, int til
     d.W = c.width; d.H = c.height;
     d.TX = (c.width + tile - 1) / tile;
     d.TY = (c.height + tile - 1) / tile;
+    if (d.TX > 65535 || d.TY > 65535) return false;  // tile rects travel in 16-bit fields
     d.STX = (d.TX + kSuperTile - 1) / kSuperTile;
     d.STY = (d.TY + kSuperTile - 1) / kSuperTile;
     d.st_off = (int)sts;

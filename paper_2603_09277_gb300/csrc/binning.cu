@@ -10,10 +10,12 @@
 //   2. stable LSD radix sort of the visible rows by FP32 depth bits, on the
 //      bits that vary over the visible rows (up to 9-bit digits: 3 passes
 //      for a range of up to 27 bits; ties keep row order = Gaussian id order);
-//   3. gather every row's rect in depth order; scans give the pair count P
-//      and each row's offset among the super-tile items (count Q <= P);
-//   4. duplicate: each row writes (super-tile, row) for the super-tiles its
-//      rect meets, in depth order (load-balanced over items);
+//   3. gather every row's rect in depth order (16-bit packed); block scans
+//      give the pair count P and each block's first super-tile item (count
+//      Q <= P);
+//   4. duplicate: each block of rows scans its rows' item offsets and writes
+//      (super-tile, row) for the super-tiles each rect meets, in depth order
+//      (4 consecutive items per thread, owners by binary search);
 //   5. stable radix sort of the items by super-tile id (one pass for up to
 //      512 super-tiles), so every super-tile holds its rows in depth order;
 //   6. per segment of 1024 rows of a super-tile: each row's rect within the
@@ -323,6 +325,15 @@ __device__ __forceinline__ unsigned st_count(const int4 r) {
   return (unsigned)((q.z - q.x) * (q.w - q.y));
 }
 
+// A clamped tile rect packed in 16-bit fields (x0 | y0 << 16, x1 | y1 << 16);
+// views are at most 65535 tiles wide and high.
+__device__ __forceinline__ uint2 pack_rect(const int4 r) {
+  return make_uint2((unsigned)r.x | ((unsigned)r.y << 16), (unsigned)r.z | ((unsigned)r.w << 16));
+}
+__device__ __forceinline__ int4 unpack_rect(const uint2 p) {
+  return make_int4((int)(p.x & 0xffffu), (int)(p.x >> 16), (int)(p.y & 0xffffu), (int)(p.y >> 16));
+}
+
 __device__ __forceinline__ int radix_result(const unsigned* range, int bits);
 
 // The depth-sorted rows: the buffer the sort left them in follows from the
@@ -344,7 +355,7 @@ struct SortedRows {
 template <int ITEMS>
 __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
     const SortedRows sorted, const long long* __restrict__ n_dev,
-    const int* __restrict__ rect, int N, const CamTable ct, int4* __restrict__ rect_sorted,
+    const int* __restrict__ rect, int N, const CamTable ct, uint2* __restrict__ rect_sorted,
     unsigned long long* __restrict__ arrive, const CountsOut co) {
   unsigned long long* sums_q = co.sums_q;
   unsigned long long* sums_p = co.sums_p;
@@ -381,7 +392,7 @@ __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
       const long long i = base + (long long)(k0 + k) * kScanThreads + threadIdx.x;
       if (i < n) {
         const int4 r = rr[k];
-        rect_sorted[i] = r;
+        rect_sorted[i] = pack_rect(r);
         q += st_count(r);
         pp += (unsigned long long)((r.z - r.x) * (r.w - r.y));
       }
@@ -395,41 +406,6 @@ __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
     sums_p[blockIdx.x] = tp;
   }
   if (last_block_arrives(arrive, gridDim.x)) scan_counts_check_dev(co, (int)gridDim.x);
-}
-
-// out[i] = exclusive prefix of the super-tile counts in depth order; and for
-// every block of kDupPairs items (b < n_marks) the row that owns its first
-// item (block_row[b]), for the load-balanced duplication.
-constexpr int kDupPairsScan = 1024;
-template <int ITEMS>
-__global__ void __launch_bounds__(kScanThreads) row_offsets_kernel(
-    const int4* __restrict__ rect_sorted, const long long* __restrict__ n_dev,
-    const unsigned long long* __restrict__ block_offsets, unsigned long long* __restrict__ out,
-    unsigned* __restrict__ block_row, long long n_marks) {
-  const long long n = *n_dev;
-  const long long base = (long long)blockIdx.x * (kScanThreads * ITEMS);
-  const long long first = base + (long long)threadIdx.x * ITEMS;
-  if (base >= n) return;
-  unsigned long long sum = 0;
-  unsigned loc[ITEMS];
-#pragma unroll
-  for (int k = 0; k < ITEMS; ++k) {
-    const long long i = first + k;
-    loc[k] = i < n ? st_count(rect_sorted[i]) : 0u;
-    sum += loc[k];
-  }
-  unsigned long long tot;
-  unsigned long long off = block_excl_scan(sum, &tot) + block_offsets[blockIdx.x];
-  for (int k = 0; k < ITEMS; ++k) {
-    const long long i = first + k;
-    if (i < n) {
-      out[i] = off;
-      for (unsigned long long b = (off + kDupPairsScan - 1) / kDupPairsScan;
-           b * kDupPairsScan < off + loc[k] && (long long)b < n_marks; ++b)
-        block_row[b] = (unsigned)i;
-    }
-    off += loc[k];
-  }
 }
 
 // ----------------------------------------------------------------------------
@@ -727,148 +703,111 @@ __device__ __forceinline__ int radix_result(const unsigned* range, int bits) {
 // ----------------------------------------------------------------------------
 // Super-pair generation, per-tile expansion.
 // ----------------------------------------------------------------------------
-// Super-pair duplication, load-balanced over super-pairs.  The depth-sorted
-// visible rows own contiguous ranges [offset_j, offset_j + count_j) of
-// (super-tile, row) items.  Items are cut into blocks of kDupPairs;
-// row_offsets_kernel records, for every block, the row that owns its first
-// item, and duplicate_kernel has each CTA load the descriptors of the rows
-// overlapping its items into shared memory, mark where each row starts, and
-// find the owner of every item with a block-wide max-scan of those marks.
-// Each thread then walks 4 consecutive items through the owner's super-tile
-// rect and stores them with one 16-byte store per array.
-constexpr int kDupThreads = 256;
-constexpr int kDupPairs = 1024;
-static_assert(kDupPairs == 4 * kDupThreads, "duplicate_kernel stores 4 items per thread");
-static_assert(kDupPairs == kDupPairsScan, "row_offsets_kernel marks the duplication blocks");
-
-// One block of kDupPairs items (b: the block's index).
-__device__ __forceinline__ void duplicate_block(
-    long long b, long long Q, long long n, const unsigned* __restrict__ rows,
-    const int4* __restrict__ rect_sorted, const unsigned long long* __restrict__ offsets, int N,
-    const CamTable& ct, const unsigned* __restrict__ block_row, unsigned* __restrict__ skeys,
+// Super-pair duplication.  Each CTA takes one scan block of the depth-sorted
+// visible rows (the blocks of rows_gather_kernel, whose item counts are
+// already scanned into the blocks' item bases), scans its rows' super-tile
+// counts in shared memory, and expands its items: every thread takes 4
+// consecutive items, finds the row owning the first by a binary search over
+// the rows' item offsets, walks through the owner's super-tile span (and on
+// to the next rows) and stores the 4 (super-tile, row) items with one
+// 16-byte store per array where aligned.  Items keep the rows' depth order.
+template <int ITEMS>
+__global__ void __launch_bounds__(kScanThreads) rows_expand_kernel(
+    const SortedRows sorted, const uint2* __restrict__ rect_sorted,
+    const long long* __restrict__ n_dev, const unsigned long long* __restrict__ block_items,
+    const long long* __restrict__ q_eff, int N, const CamTable ct, unsigned* __restrict__ skeys,
     unsigned* __restrict__ svals, int vec16, int packed) {
-  constexpr int kPer = kDupPairs / kDupThreads;  // 4 consecutive items per thread
-  __shared__ int s_off[kDupPairs];     // row item offset relative to the block start
-  __shared__ int4 s_info[kDupPairs];   // (super-tile id of the span origin, span width, STX, row)
-  __shared__ unsigned s_rel[kDupPairs];  // rect relative to the span origin (packed)
-  __shared__ int s_own[kDupPairs];     // slot of the row starting at item t (max-scanned)
-  __shared__ int s_wmax[kDupThreads / 32];
-  const long long start = b * kDupPairs;
-  const long long end = min(Q, start + kDupPairs);
-  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-  const long long j0 = block_row[b];
-  // rows j0 .. j1 overlap [start, end): j1 is the row holding the next block's
-  // first item (it belongs here only if it starts before `end`), or the last row
-  const long long j1 = (end < Q) ? (long long)block_row[b + 1] : n - 1;
-  const int cand = (int)min((long long)kDupPairs, j1 - j0 + 1);
-  for (int t = tid; t < kDupPairs; t += kDupThreads) s_own[t] = 0;
+  constexpr int RB = kScanThreads * ITEMS;
+  __shared__ unsigned s_off[RB + 1];  // item offset of each row in the block (+ the total)
+  const long long n = *n_dev, Q = *q_eff;
+  const long long base = (long long)blockIdx.x * RB;
+  if (base >= n || Q == 0) return;  // (the whole CTA)
+  const int nr = (int)min((long long)RB, n - base);
+  const int first = threadIdx.x * ITEMS;
+  unsigned loc[ITEMS];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    const int i = first + k;
+    loc[k] = i < nr ? st_count(unpack_rect(rect_sorted[base + i])) : 0u;
+    sum += loc[k];
+  }
+  unsigned long long tot;
+  unsigned off = (unsigned)block_excl_scan(sum, &tot);
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    s_off[first + k] = off;
+    off += loc[k];
+  }
+  if (threadIdx.x == 0) s_off[RB] = (unsigned)tot;
   __syncthreads();
-  for (int i = tid; i < cand; i += kDupThreads) {
-    const long long j = j0 + i;
-    const long long o = (long long)offsets[j];
-    if (o < end) {
-      const unsigned row = rows[j];
-      const int4 r = rect_sorted[j];
-      const int4 q = st_span(r);
-      const CamInfo& c = ct.c[row / (unsigned)N];
-      s_off[i] = (int)(o - start);  // negative for a row that began before the block
-      s_info[i] = make_int4(c.st_off + q.y * c.STX + q.x, q.z - q.x, c.STX, (int)row);
-      // first-column / first-row offsets inside the super-tile and the rect's
-      // end relative to the span origin (tiles; < 8192 when packed)
-      s_rel[i] = (unsigned)(r.x & 7) | ((unsigned)(r.y & 7) << 3) |
-                 ((unsigned)(r.z - 8 * q.x) << 6) | ((unsigned)(r.w - 8 * q.y) << 19);
-      // a row with no items shares its start with the next row: the later wins
-      if (o >= start) atomicMax(&s_own[o - start], i);
+  const unsigned total = (unsigned)tot;
+  const long long gbase = (long long)block_items[blockIdx.x];
+  const unsigned* __restrict__ rows = sorted.get();
+  for (unsigned c0 = 0; c0 < total; c0 += 4 * kScanThreads) {
+    const unsigned e0 = c0 + 4u * threadIdx.x;
+    if (e0 >= total) continue;
+    // the owner of e0: the last row whose items start at or before it (rows
+    // without items share their start with the next row)
+    int lo = 0, hi = nr - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_off[mid] <= e0) lo = mid;
+      else hi = mid - 1;
     }
-  }
-  __syncthreads();
-  // owner of item t = the last row starting at or before t: an inclusive
-  // max-scan of the start marks (slot numbers grow with the offset)
-  int own[kPer];
-  int m = 0;
+    int j = lo;
+    unsigned kk[4], vv[4];
+    unsigned row = 0u;
+    int4 r = make_int4(0, 0, 0, 0), q = r;
+    int id0 = 0, wdt = 1, stx = 1, x = 0, y = 0;
+    int cur = -1;
+    int cnt = 0;
 #pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    m = max(m, s_own[tid * kPer + q]);
-    own[q] = m;
-  }
-  int incl = m;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl = max(incl, y);
-  }
-  if (lane == 31) s_wmax[wp] = incl;
-  int before = __shfl_up_sync(0xffffffffu, incl, 1);
-  if (lane == 0) before = 0;
-  __syncthreads();
-  for (int k = 0; k < wp; ++k) before = max(before, s_wmax[k]);
-  const int np = (int)(end - start);
-  unsigned kk[kPer], vv[kPer];
-  int cur = -1, id = 0, x = 0, y = 0, wdt = 1, stride = 1;
-  unsigned rel = 0u;
-#pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    const int t = tid * kPer + q;
-    const int slot = max(before, own[q]);
-    if (slot != cur) {
-      // first item of this row in the thread: position within the span
-      const int4 in = s_info[slot];
-      const int k = t - s_off[slot];
-      wdt = max(in.y, 1);
-      stride = in.z;
-      y = k / wdt;
-      x = k - y * wdt;
-      id = in.x + y * stride;
-      vv[q] = (unsigned)in.w;
-      rel = s_rel[slot];
-      cur = slot;
-    } else {
-      vv[q] = vv[q > 0 ? q - 1 : 0];
-      if (++x == wdt) {  // next span row
+    for (int t = 0; t < 4; ++t) {
+      const unsigned e = e0 + (unsigned)t;
+      if (e >= total) break;
+      while (s_off[j + 1] <= e) ++j;  // (s_off[nr .. RB] = total > e)
+      if (j != cur) {
+        row = rows[base + j];
+        r = unpack_rect(rect_sorted[base + j]);
+        q = st_span(r);
+        const CamInfo& c = ct.c[row / (unsigned)N];
+        id0 = c.st_off + q.y * c.STX + q.x;
+        wdt = max(q.z - q.x, 1);
+        stx = c.STX;
+        const int k = (int)(e - s_off[j]);
+        y = k / wdt;
+        x = k - y * wdt;
+        cur = j;
+      } else if (++x == wdt) {  // next span row
         x = 0;
         ++y;
-        id += stride;
       }
+      unsigned key = (unsigned)(id0 + y * stx + x);
+      if (packed) {
+        // the row's rect inside this super-tile: x0 | x1 << 4 | y0 << 8 | y1 << 12
+        const int ox = 8 * (q.x + x), oy = 8 * (q.y + y);
+        const unsigned dx0 = (unsigned)max(r.x - ox, 0), dx1 = (unsigned)min(r.z - ox, 8);
+        const unsigned dy0 = (unsigned)max(r.y - oy, 0), dy1 = (unsigned)min(r.w - oy, 8);
+        key |= (dx0 | (dx1 << 4) | (dy0 << 8) | (dy1 << 12)) << 16;
+      }
+      kk[t] = key;
+      vv[t] = row;
+      cnt = t + 1;
     }
-    unsigned key = (unsigned)(id + x);
-    if (packed) {
-      // the row's rect inside this super-tile: x0 | x1 << 4 | y0 << 8 | y1 << 12
-      const int ex = (int)((rel >> 6) & 8191u), ey = (int)(rel >> 19);
-      const unsigned x0 = x == 0 ? (rel & 7u) : 0u, y0 = y == 0 ? ((rel >> 3) & 7u) : 0u;
-      const unsigned x1 = (unsigned)min(ex - 8 * x, 8), y1 = (unsigned)min(ey - 8 * y, 8);
-      key |= (x0 | (x1 << 4) | (y0 << 8) | (y1 << 12)) << 16;
-    }
-    kk[q] = key;
-  }
-  const int t0 = tid * kPer;
-  if (vec16 && t0 + kPer <= np) {  // skeys and svals 16-byte aligned
-    reinterpret_cast<uint4*>(skeys + start)[tid] = make_uint4(kk[0], kk[1], kk[2], kk[3]);
-    reinterpret_cast<uint4*>(svals + start)[tid] = make_uint4(vv[0], vv[1], vv[2], vv[3]);
-  } else {
+    const long long g0 = gbase + e0;
+    if (vec16 && cnt == 4 && (g0 & 3) == 0 && g0 + 3 < Q) {  // skeys, svals 16-byte aligned
+      reinterpret_cast<uint4*>(skeys + g0)[0] = make_uint4(kk[0], kk[1], kk[2], kk[3]);
+      reinterpret_cast<uint4*>(svals + g0)[0] = make_uint4(vv[0], vv[1], vv[2], vv[3]);
+    } else {
 #pragma unroll
-    for (int q = 0; q < kPer; ++q)
-      if (t0 + q < np) {
-        skeys[start + t0 + q] = kk[q];
-        svals[start + t0 + q] = vv[q];
-      }
+      for (int t = 0; t < 4; ++t)
+        if (t < cnt && g0 + t < Q) {
+          skeys[g0 + t] = kk[t];
+          svals[g0 + t] = vv[t];
+        }
+    }
   }
-  __syncthreads();  // shared memory is reused by the CTA's next block
-}
-
-// Grid-stride over the blocks of the Q items (the grid is sized for the
-// bound on Q; a CTA beyond the last block leaves at once).
-__global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
-    const SortedRows sorted, const int4* __restrict__ rect_sorted,
-    const long long* __restrict__ n_vis, const unsigned long long* __restrict__ offsets, int N,
-    const CamTable ct, const long long* __restrict__ q_eff,
-    const unsigned* __restrict__ block_row, unsigned* __restrict__ skeys,
-    unsigned* __restrict__ svals, int vec16, int packed) {
-  const long long Q = *q_eff;
-  const long long n = *n_vis;
-  const unsigned* __restrict__ rows = sorted.get();
-  for (long long b = blockIdx.x; b * kDupPairs < Q; b += gridDim.x)
-    duplicate_block(b, Q, n, rows, rect_sorted, offsets, N, ct, block_row, skeys, svals, vec16,
-                    packed);
 }
 
 // Per-key [start, end) from sorted u32 keys: each thread reads 4
@@ -1305,12 +1244,10 @@ struct Workspace {
   long long* counters;             // [0] n_vis, [1] P, [2] P eff., [3] Q, [4] Q eff., [5] segments
   unsigned* rk[2];                 // row keys (depth bits), double buffer
   unsigned* rv[2];                 // row values, double buffer
-  unsigned long long* offsets;     // super-pair offsets per visible row
-  int4* rect_sorted;               // clamped rect per visible row, depth order
+  uint2* rect_sorted;              // clamped rect per visible row, depth order (16-bit packed)
   unsigned* pk[2];                 // super-pair keys (super-tile), double buffer; later descriptors
   unsigned* pv;                    // super-pair values (rows)
   unsigned* hist;                  // radix histograms
-  unsigned* block_row;             // first row of every duplication block
   unsigned* st_ranges;             // [2 * super-tiles] rows of each super-tile
   unsigned* seg_first;             // [super-tiles + 1] first segment of each super-tile
   unsigned* seg_st;                // super-tile of every segment
@@ -1371,12 +1308,10 @@ Workspace carve(void* base, long long n_rows, long long cap, long long tiles) {
   w.counters = reinterpret_cast<long long*>(take(sizeof(long long) * kCounters));
   for (int i = 0; i < 2; ++i) w.rk[i] = reinterpret_cast<unsigned*>(take(4 * (n_rows + 1)));
   for (int i = 0; i < 2; ++i) w.rv[i] = reinterpret_cast<unsigned*>(take(4 * (n_rows + 1)));
-  w.offsets = reinterpret_cast<unsigned long long*>(take(8 * (n_rows + 1)));
-  w.rect_sorted = reinterpret_cast<int4*>(take(16 * (n_rows + 1)));
+  w.rect_sorted = reinterpret_cast<uint2*>(take(8 * (n_rows + 1)));
   for (int i = 0; i < 2; ++i) w.pk[i] = reinterpret_cast<unsigned*>(take(4 * (cap + 1)));
   w.pv = reinterpret_cast<unsigned*>(take(4 * (cap + 1)));
   w.hist = reinterpret_cast<unsigned*>(take(radix_hist_bytes()));
-  w.block_row = reinterpret_cast<unsigned*>(take(4ull * ((cap + kDupPairs - 1) / kDupPairs + 1)));
   w.st_ranges = reinterpret_cast<unsigned*>(take(8ull * (tiles + 1)));
   w.seg_first = reinterpret_cast<unsigned*>(take(4ull * (tiles + 2)));
   w.seg_st = reinterpret_cast<unsigned*>(take(4ull * ms));
@@ -1499,18 +1434,6 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
     scan_counts_check_kernel<<<1, kScanThreads, 0, st>>>(co, 0);
     count_launches(1);
   }
-  if (n_rows > 0) {
-    // super-tile offsets per row, and the first row of every duplication block
-    if (small)
-      row_offsets_kernel<4><<<(unsigned)nb, kScanThreads, 0, st>>>(
-          w.rect_sorted, n_vis, w.block_sums, w.offsets, w.block_row,
-          (cap + kDupPairs - 1) / kDupPairs + 1);
-    else
-      row_offsets_kernel<16><<<(unsigned)nb, kScanThreads, 0, st>>>(
-          w.rect_sorted, n_vis, w.block_sums, w.offsets, w.block_row,
-          (cap + kDupPairs - 1) / kDupPairs + 1);
-    count_launches(1);
-  }
   GS_TRY_CUDA(cudaGetLastError());
   long long p_bound = cap;
   if (num_pairs_host) {
@@ -1548,12 +1471,17 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
   for (int v = 0; v < ct.V; ++v)
     if (ct.c[v].TX > 8000 || ct.c[v].TY > 8000) packed = 0;
   {
-    const unsigned g2 =
-        (unsigned)std::min<long long>((q_bound + kDupPairs - 1) / kDupPairs, 152ll * 6);
-    const int vec16 = (reinterpret_cast<uintptr_t>(sv[0]) % 16 == 0) ? 1 : 0;
-    duplicate_kernel<<<g2, kDupThreads, 0, st>>>(rows_sorted, w.rect_sorted, n_vis, w.offsets, N,
-                                                ct, q_eff, w.block_row, sk[0], sv[0], vec16,
-                                                packed);
+    // (the scan blocks of rows_gather_kernel: their item bases are scanned)
+    const int vec16 = (reinterpret_cast<uintptr_t>(sv[0]) % 16 == 0 &&
+                       reinterpret_cast<uintptr_t>(sk[0]) % 16 == 0) ? 1 : 0;
+    if (small)
+      rows_expand_kernel<4><<<(unsigned)nb, kScanThreads, 0, st>>>(
+          rows_sorted, w.rect_sorted, n_vis, w.block_sums, q_eff, N, ct, sk[0], sv[0], vec16,
+          packed);
+    else
+      rows_expand_kernel<16><<<(unsigned)nb, kScanThreads, 0, st>>>(
+          rows_sorted, w.rect_sorted, n_vis, w.block_sums, q_eff, N, ct, sk[0], sv[0], vec16,
+          packed);
     count_launches(1);
   }
   // 5. stable sort of the super-pairs by super-tile id
