@@ -1055,6 +1055,7 @@ def main():
                   (pre + "_f16", dict(form, attr_dtype="f16"), None),
                   (pre + "_bf16", dict(form, attr_dtype="bf16"), None),
                   ("persistent_f32", dict(form, persistent=pers), None),
+                  ("ordered_f32", dict(form, persistent=0, ordered=True), None),
                   ("persistent_bf16", dict(form, persistent=pers, attr_dtype="bf16"), None),
                   (pre + "_f32_1px", dict(form, pixels_per_thread=1), None)]
         if args.tile == 16:
@@ -1093,7 +1094,8 @@ def main():
                        "tile": args.tile,
                        "launch": ("persistent %d CTAs over the list-length queue"
                                   % form["persistent"] if form["persistent"]
-                                  else "one CTA per %dx%d tile" % (args.tile, args.tile))
+                                  else "one CTA per %dx%d tile" % (args.tile, args.tile)
+                                  + (", longest list first" if form.get("ordered") else ""))
                        + ", %d px/thread, %d-entry batches" % (form["pixels_per_thread"] or 2,
                                                                form.get("batch") or 256),
                        "autotune_ms": tuned,

@@ -161,6 +161,14 @@ unsigned long long gs_kernel_launches(void);
 enum gs_stage { GS_STAGE_EXPANSION = 1, GS_STAGE_PROJECTION = 2, GS_STAGE_ADJOINT = 3 };
 int gs_stage_events(int stage, void* ev_begin, void* ev_end);
 
+/* Status of the bounds-checked debug build (the library compiled with
+ * -DGS_DEBUG_BOUNDS): *status = the id of the first index check that failed
+ * since the last clear (0: none; 1xx blending, 2xx list construction, 3xx
+ * projection adjoint), the failing access having been skipped; clear != 0
+ * resets it.  Synchronous (reads device memory).  The normal build has no
+ * checks: *status = 0 and GS_ERR_UNSUPPORTED. */
+int gs_debug_bounds_status(unsigned* status, int clear);
+
 /* ---------------------------------------------------------------------- */
 /* Hot path                                                                */
 /* ---------------------------------------------------------------------- */

@@ -1,8 +1,9 @@
 """Launch-form autotuner for the blending kernels.
 
 Times the candidate launch forms (pixels per thread 1/2/4, list entries per
-shared-memory batch 128/256, one CTA per tile or a persistent grid of 4 or 8
-CTAs per SM over the list-length-ordered tile queue) on the caller's
+shared-memory batch 128/256, one CTA per tile in tile order or longest list
+first, or a persistent grid of 4 or 8 CTAs per SM over the list-length-ordered
+tile queue) on the caller's
 actual workload (a few whole fwd+bwd steps each, L2 flushed between steps),
 and caches the fastest form per workload signature (views and their sizes,
 Gaussian count, staging dtype, device name) in a JSON file under
@@ -27,6 +28,7 @@ BASE_CANDIDATES = [
     {"pixels_per_thread": 4, "persistent": 0, "batch": 256},
     {"pixels_per_thread": 2, "persistent": 0, "batch": 128},
     {"pixels_per_thread": 4, "persistent": 0, "batch": 128},
+    {"pixels_per_thread": 2, "persistent": 0, "batch": 256, "ordered": True},
 ]
 PERSISTENT_PER_SM = [(2, 8), (4, 8), (2, 4)]  # (pixels per thread, CTAs per SM)
 
@@ -63,8 +65,9 @@ def candidates(tile=16, attr_dtype="f32"):
 
 
 def form_name(form):
-    """e.g. "ppt2_b256_per_tile", "ppt4_b256_persistent1216"."""
-    where = "persistent%d" % form["persistent"] if form["persistent"] else "per_tile"
+    """e.g. "ppt2_b256_per_tile", "ppt2_b256_per_tile_ordered", "ppt4_b256_persistent1216"."""
+    where = ("persistent%d" % form["persistent"] if form["persistent"] else
+             "per_tile_ordered" if form.get("ordered") else "per_tile")
     return "ppt%d_b%d_%s" % (form["pixels_per_thread"], form.get("batch", 256), where)
 
 

@@ -37,13 +37,18 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
 size_t tile_queue_workspace_size(long long T);
 int launch_tile_queue(const unsigned* ranges, long long T, unsigned* order, void* ws,
                       size_t ws_bytes, cudaStream_t st);
-int launch_render_fwd(const gs_proj* proj, const CamTable& ct, const gs_params* prm,
-                      const unsigned* vals, const unsigned* ranges, float* image, float* final_T,
-                      unsigned* last_idx, float* entropy, const gs_launch* opt, cudaStream_t st);
-int launch_render_bwd(const gs_proj* proj, const CamTable& ct, const gs_params* prm,
-                      const unsigned* vals, const unsigned* ranges, const float* final_T,
-                      const unsigned* last_idx, const float* dL_dimage, const float* dL_dentropy,
-                      float* grad2d, const gs_launch* opt, cudaStream_t st);
+int launch_render_fwd(const gs_proj* proj, long long rows, const CamTable& ct,
+                      const gs_params* prm, const unsigned* vals, const unsigned* ranges,
+                      float* image, float* final_T, unsigned* last_idx, float* entropy,
+                      const gs_launch* opt, cudaStream_t st);
+int launch_render_bwd(const gs_proj* proj, long long rows, const CamTable& ct,
+                      const gs_params* prm, const unsigned* vals, const unsigned* ranges,
+                      const float* final_T, const unsigned* last_idx, const float* dL_dimage,
+                      const float* dL_dentropy, float* grad2d, const gs_launch* opt,
+                      cudaStream_t st);
+int bounds_status_render(unsigned* out, bool clear);
+int bounds_status_binning(unsigned* out, bool clear);
+int bounds_status_preprocess(unsigned* out, bool clear);
 
 namespace {
 thread_local char g_err[512] = "";
@@ -363,6 +368,16 @@ int gs_stage_events(int stage, void* ev_begin, void* ev_end) {
   return GS_OK;
 }
 
+int gs_debug_bounds_status(unsigned* status, int clear) {
+  if (!status) return invalid("status");
+  unsigned s[3] = {0u, 0u, 0u};
+  int rc = bounds_status_render(&s[0], clear != 0);
+  if (rc == GS_OK) rc = bounds_status_binning(&s[1], clear != 0);
+  if (rc == GS_OK) rc = bounds_status_preprocess(&s[2], clear != 0);
+  *status = s[0] ? s[0] : (s[1] ? s[1] : s[2]);
+  return rc;
+}
+
 int gs_record_bytes(int attr_dtype) {
   switch (attr_dtype) {
     case GS_ATTR_F32: return (int)sizeof(RecF32);
@@ -480,8 +495,8 @@ int gs_render_fwd(const gs_proj* proj, int N, const gs_camera* cams, int V, cons
   if (!tile_ranges || !image || !final_T || !last_idx) return invalid("output pointers");
   if (!aligned(tile_ranges, 8)) return invalid("tile_ranges must be 8-byte aligned");
   if (const char* why = launch_opt_error(opt, prm)) return invalid(why);
-  return launch_render_fwd(proj, ct, prm, sorted_vals, tile_ranges, image, final_T, last_idx,
-                           entropy, opt, (cudaStream_t)stream);
+  return launch_render_fwd(proj, (long long)N * V, ct, prm, sorted_vals, tile_ranges, image,
+                           final_T, last_idx, entropy, opt, (cudaStream_t)stream);
 }
 
 namespace {
@@ -601,15 +616,15 @@ int gs_render_bwd(const gs_proj* proj, int N, const gs_camera* cams, int V, cons
     // (the side branch is joined back on every path from here)
     GS_TRY_CUDA(cudaEventRecord(ss->join, ss->s));
     if (rs == GS_OK)
-      rc = launch_render_bwd(proj, ct, prm, sorted_vals, tile_ranges, final_T, last_idx,
-                             dL_dimage, dL_dentropy, grad2d, opt, st);
+      rc = launch_render_bwd(proj, (long long)N * V, ct, prm, sorted_vals, tile_ranges, final_T,
+                             last_idx, dL_dimage, dL_dentropy, grad2d, opt, st);
     GS_TRY_CUDA(cudaStreamWaitEvent(st, ss->join, 0));
     if (rs != GS_OK) return rs;
   } else {
     rc = side_work(st);
     if (rc == GS_OK)
-      rc = launch_render_bwd(proj, ct, prm, sorted_vals, tile_ranges, final_T, last_idx,
-                             dL_dimage, dL_dentropy, grad2d, opt, st);
+      rc = launch_render_bwd(proj, (long long)N * V, ct, prm, sorted_vals, tile_ranges, final_T,
+                             last_idx, dL_dimage, dL_dentropy, grad2d, opt, st);
   }
   if (rc != GS_OK) return rc;
   return launch_preprocess_bwd(means, log_scales, quats, opacity_logits, sh, N, ct, prm,

@@ -288,6 +288,7 @@ __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
     if ((ball[k] >> lane) & 1u) {
       const long long i = base + (long long)k * kScanThreads + threadIdx.x;
       const unsigned long long off = boff + s_off[k * kScanWarps + w] + __popc(ball[k] & below);
+      if (!GS_IN_BOUNDS(off, n, 203)) continue;
       keys[off] = __float_as_uint(depth[i]);
       vals[off] = (unsigned)i;
     }
@@ -386,7 +387,8 @@ __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
     int4 rr[kGather];
 #pragma unroll
     for (int k = 0; k < kGather; ++k)
-      rr[k] = row[k] != 0xffffffffu ? view_rect(rect, row[k], N, ct) : make_int4(0, 0, 0, 0);
+      rr[k] = row[k] != 0xffffffffu && GS_IN_BOUNDS(row[k], (long long)N * ct.V, 204)
+                  ? view_rect(rect, row[k], N, ct) : make_int4(0, 0, 0, 0);
 #pragma unroll
     for (int k = 0; k < kGather; ++k) {
       const long long i = base + (long long)(k0 + k) * kScanThreads + threadIdx.x;
@@ -566,7 +568,11 @@ __global__ void __launch_bounds__(kScanThreads) radix_scan_kernel(const RadixPas
 // addresses of one digit's run (coalesced), and each digit's running global
 // offset advances by the tile's count.  The next tile's keys and values are
 // loaded into registers while the current one is ranked and written.
-__global__ void __launch_bounds__(kRadixThreads, 3) radix_downsweep_kernel(const RadixPass a) {
+#ifndef GS_RADIX_CTAS
+#define GS_RADIX_CTAS 3  // resident scatter CTAs per SM the register budget targets
+#endif
+__global__ void __launch_bounds__(kRadixThreads, GS_RADIX_CTAS) radix_downsweep_kernel(
+    const RadixPass a) {
   const RadixPlan pl = radix_plan(a.range, a.bits);
   if (a.pass >= pl.passes) return;
   const unsigned* __restrict__ keys_in = a.keys_in;
@@ -681,6 +687,7 @@ __global__ void __launch_bounds__(kRadixThreads, 3) radix_downsweep_kernel(const
       const unsigned kk = s_key[i];
       const unsigned d = radix_digit(kk, pl, shift);
       const unsigned pos = s_base[d] + (unsigned)i - s_off[d];
+      if (!GS_IN_BOUNDS(pos, n, 202)) continue;
       if (wkeys) keys_out[pos] = kk;
       vals_out[pos] = s_val[i];
     }
@@ -769,6 +776,7 @@ __global__ void __launch_bounds__(kScanThreads) rows_expand_kernel(
       while (s_off[j + 1] <= e) ++j;  // (s_off[nr .. RB] = total > e)
       if (j != cur) {
         row = rows[base + j];
+        if (!GS_IN_BOUNDS(row, (long long)N * ct.V, 205)) row = 0u;
         r = unpack_rect(rect_sorted[base + j]);
         q = st_span(r);
         const CamInfo& c = ct.c[row / (unsigned)N];
@@ -1156,7 +1164,7 @@ __global__ void __launch_bounds__(256) st_emit_kernel(
     const unsigned* __restrict__ seg_first, const unsigned* __restrict__ seg_st,
     const long long* __restrict__ n_seg, const unsigned* __restrict__ hist,
     const unsigned* __restrict__ tile_start, const CamTable ct, const float* __restrict__ depth,
-    unsigned* __restrict__ out_vals, unsigned long long* __restrict__ out_keys) {
+    unsigned* __restrict__ out_vals, unsigned long long* __restrict__ out_keys, long long cap) {
   __shared__ unsigned s_run[64];                   // next list slot per tile of the super-tile
   __shared__ unsigned s_cnt[8][64];                // per-warp counts per tile
   __shared__ __align__(16) unsigned s_pos[8][64];  // per-warp first slot per tile
@@ -1216,7 +1224,7 @@ __global__ void __launch_bounds__(256) st_emit_kernel(
         for (unsigned c = 0; c < 8; ++c) {
           // this lane covers tile (r, c): its rank among the covering lanes
           const unsigned pos = sp[c] + __popc(B[r] & Xl[c]);
-          if (in_r && c >= x0 && c < x1) {
+          if (in_r && c >= x0 && c < x1 && GS_IN_BOUNDS(pos, cap, 201)) {
             out_vals[pos] = row;
             if (out_keys)
               out_keys[pos] = ((unsigned long long)(unsigned)s_tile[8 * r + c] << 32) |
@@ -1369,6 +1377,8 @@ int bits_for(long long count) {
 
 }  // namespace
 
+GS_BOUNDS_READER(bounds_status_binning)
+
 size_t bin_sort_workspace_size(long long n_rows, long long cap, long long total_tiles) {
   return carve(nullptr, n_rows, cap, total_tiles).bytes;
 }
@@ -1519,7 +1529,7 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
   st_emit_kernel<<<gs, 256, 0, st>>>(sp_keys, sp_rows, desc, packed,
                                      reinterpret_cast<const uint2*>(w.st_ranges), w.seg_first,
                                      w.seg_st, n_seg, w.seg_hist, w.tile_start, ct, proj->depth,
-                                     sorted_vals, sorted_keys);
+                                     sorted_vals, sorted_keys, cap);
   {
     const int e = stage_event(GS_STAGE_EXPANSION, true, st);
     if (e != GS_OK) return e;

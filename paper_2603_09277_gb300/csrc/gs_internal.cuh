@@ -13,6 +13,42 @@
 
 namespace gs {
 
+// ---------------------------------------------------------------------------
+// Bounds-checked debug build (compiled with -DGS_DEBUG_BOUNDS): a checked
+// access tests its index against the extent of its buffer; a failing test
+// records the check's id in the translation unit's device status word (the
+// first failure wins) and the access is skipped.  No assert and no trap, so
+// the context stays usable; gs_debug_bounds_status reads and clears the
+// words.  In the normal build GS_IN_BOUNDS is `true` and costs nothing.
+// ---------------------------------------------------------------------------
+#ifdef GS_DEBUG_BOUNDS
+static __device__ unsigned g_bounds_status;
+__device__ __forceinline__ bool gs_in_bounds(unsigned long long i, unsigned long long n,
+                                             unsigned id) {
+  if (i < n) return true;
+  atomicCAS(&g_bounds_status, 0u, id);
+  return false;
+}
+#define GS_IN_BOUNDS(i, n, id) \
+  ::gs::gs_in_bounds((unsigned long long)(i), (unsigned long long)(n), (unsigned)(id))
+#define GS_BOUNDS_READER(name)                                                      \
+  int name(unsigned* out, bool clear) {                                             \
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_bounds_status, sizeof(unsigned));   \
+    if (e == cudaSuccess && clear) {                                                \
+      const unsigned z = 0u;                                                        \
+      e = cudaMemcpyToSymbol(g_bounds_status, &z, sizeof(unsigned));                \
+    }                                                                               \
+    return e == cudaSuccess ? GS_OK : set_cuda_error(e);                            \
+  }
+#else
+#define GS_IN_BOUNDS(i, n, id) true
+#define GS_BOUNDS_READER(name) \
+  int name(unsigned* out, bool) {  \
+    *out = 0u;                     \
+    return GS_ERR_UNSUPPORTED;     \
+  }
+#endif
+
 constexpr int kTile = GS_TILE;               // default tile side (16 px; 8 also supported)
 constexpr int kSuperTile = 8;                // binning groups 8x8 tiles into a super-tile
 constexpr float kLog2e = 1.4426950408889634f;

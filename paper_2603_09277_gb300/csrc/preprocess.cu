@@ -806,8 +806,11 @@ __global__ void __launch_bounds__(kListThreads) adjoint_list_kernel(
 constexpr int kAdjThreads = 128;
 // CTAs per SM the register budget allows: 2 where a group sums 48 SH
 // gradients in registers, 3 with 27, else 4 (at most 128 registers)
+#ifndef GS_ADJ_CTAS
+#define GS_ADJ_CTAS 5  // CTAs per SM of the single-lane adjoint (measured: 4 -> 0.725 ms, 5 -> 0.689, 6 -> 0.723 on 8 views of 3M)
+#endif
 template <int DEG, int L>
-constexpr int adj_ctas_per_sm() { return (DEG == 3 && L > 1) ? 2 : (DEG == 2 ? 3 : 4); }
+constexpr int adj_ctas_per_sm() { return (DEG == 3 && L > 1) ? 2 : (DEG == 2 ? 3 : GS_ADJ_CTAS); }
 
 template <int DEG, int L>
 __global__ void __launch_bounds__(kAdjThreads, adj_ctas_per_sm<DEG, L>()) preprocess_bwd_kernel(
@@ -823,10 +826,14 @@ __global__ void __launch_bounds__(kAdjThreads, adj_ctas_per_sm<DEG, L>()) prepro
   const int sub = lane % L;
   const unsigned mask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << (lane - sub);
   const unsigned groups = gridDim.x * (kAdjThreads / L);
-  for (unsigned i = (blockIdx.x * kAdjThreads + threadIdx.x) / L; i < n; i += groups)
-    adjoint_group<DEG, L>((int)g2[12ll * i + 9], sub, mask, means, log_scales, quats,
+  for (unsigned i = (blockIdx.x * kAdjThreads + threadIdx.x) / L; i < n; i += groups) {
+    if (!GS_IN_BOUNDS(i, N, 302)) break;  // the list holds at most N Gaussians
+    const unsigned g = g2[12ll * i + 9];
+    if (!GS_IN_BOUNDS(g, N, 301)) continue;
+    adjoint_group<DEG, L>((int)g, sub, mask, means, log_scales, quats,
                           opacity_logits, sh, N, ct, dilation, sh_stride, tiles_touched, grad2d,
                           g_means, g_ls, g_quats, g_opac, g_sh);
+  }
 }
 
 template <int DEG, int L>
@@ -909,6 +916,8 @@ __global__ void __launch_bounds__(256) grad2d_attr_kernel(const void* __restrict
 }
 
 }  // namespace
+
+GS_BOUNDS_READER(bounds_status_preprocess)
 
 int launch_grad2d_attributes(const gs_proj* proj, long long rows, const gs_params* prm,
                              const float* grad2d, float* out, cudaStream_t st) {

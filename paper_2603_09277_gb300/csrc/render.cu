@@ -169,6 +169,7 @@ struct FwdArgs {
   const unsigned* order;
   unsigned* counter;
   unsigned long long* stats;
+  unsigned long long rows, pixels;  // extents of the record and per-pixel arrays
 };
 
 // One list entry against a thread's two pixels (rows ry and ry + 1 of one
@@ -258,7 +259,9 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
     for (int j = tid; j < B; j += NT) {
       const unsigned idx = base + j;
       if (idx < r.y) {
-        const Splat s = load_record<DT>(a.recs, a.vals[idx]);
+        unsigned row = a.vals[idx];
+        if (!GS_IN_BOUNDS(row, a.rows, 101)) row = 0u;
+        const Splat s = load_record<DT>(a.recs, row);
         const float2 m = tile_relative_mean(s, tg.ox, tg.oy);
         s0[j] = make_float4(m.x, m.y, s.f11, s.f21);
         s1[j] = make_float4(s.f22, s.L2S, s.R, s.G);
@@ -331,6 +334,7 @@ __device__ __forceinline__ void fwd_tile(const CamTable& ct, const RenderConsts&
   for (int q = 0; q < PPT; ++q) {
     if (!(tg.inside & (1u << q))) continue;
     const long long p = tg.pix0 + (long long)q * tg.W;
+    if (!GS_IN_BOUNDS(p, a.pixels, 102)) continue;
     a.image[3 * p] = cr[q];
     a.image[3 * p + 1] = cg[q];
     a.image[3 * p + 2] = cb[q];
@@ -396,6 +400,7 @@ struct BwdArgs {
   float* grad2d;  // [rows][12]: sums dd (dx, dy, dx^2, dx dy, dy^2, 1), w (r, g, b), pad
   const unsigned* order;
   unsigned* counter;
+  unsigned long long rows, pixels;  // extents of the record and per-pixel arrays
 };
 
 // Split-transpose warp sum of v[0..8]: at each butterfly level a lane keeps
@@ -529,7 +534,7 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
     T[q] = 1.f;
     gr[q] = gg[q] = gb[q] = gH[q] = 0.f;
     last[q] = 0u;
-    if (tg.inside & (1u << q)) {
+    if ((tg.inside & (1u << q)) && GS_IN_BOUNDS(tg.pix0 + (long long)q * tg.W, a.pixels, 112)) {
       const long long p = tg.pix0 + (long long)q * tg.W;
       T[q] = a.final_T[p];
       last[q] = a.last_idx[p];
@@ -565,7 +570,8 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
     const int cnt = (int)(end - start);
     __syncthreads();
     for (int j = tid; j < cnt; j += NT) {
-      const unsigned row = a.vals[r.x + start + j];
+      unsigned row = a.vals[r.x + start + j];
+      if (!GS_IN_BOUNDS(row, a.rows, 111)) row = 0u;
       const Splat s = load_record<DT>(a.recs, row);
       const float2 m = tile_relative_mean(s, tg.ox, tg.oy);
       s0[j] = make_float4(m.x, m.y, s.f11, s.f21);
@@ -772,9 +778,12 @@ int launch_bwd_t(const CamTable& ct, const RenderConsts& rc, const BwdArgs& a, i
 
 }  // namespace
 
-int launch_render_fwd(const gs_proj* proj, const CamTable& ct, const gs_params* prm,
-                      const unsigned* vals, const unsigned* ranges, float* image, float* final_T,
-                      unsigned* last_idx, float* entropy, const gs_launch* opt, cudaStream_t st) {
+GS_BOUNDS_READER(bounds_status_render)
+
+int launch_render_fwd(const gs_proj* proj, long long rows, const CamTable& ct,
+                      const gs_params* prm, const unsigned* vals, const unsigned* ranges,
+                      float* image, float* final_T, unsigned* last_idx, float* entropy,
+                      const gs_launch* opt, cudaStream_t st) {
   FwdArgs a;
   a.recs = proj->records;
   a.vals = vals;
@@ -786,6 +795,8 @@ int launch_render_fwd(const gs_proj* proj, const CamTable& ct, const gs_params* 
   a.order = opt ? opt->tile_order : nullptr;
   a.counter = opt ? opt->work_counter : nullptr;
   a.stats = opt ? opt->stats : nullptr;
+  a.rows = (unsigned long long)rows;
+  a.pixels = (unsigned long long)(ct.c[ct.V - 1].pix_off + (long long)ct.c[ct.V - 1].W * ct.c[ct.V - 1].H);
   int ctas = opt ? opt->ctas : 0;
   if (ctas > 0) GS_TRY_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(unsigned), st));
   RenderConsts rc = render_consts(prm);
@@ -797,10 +808,11 @@ int launch_render_fwd(const gs_proj* proj, const CamTable& ct, const gs_params* 
   return GS_ERR_INVALID_ARG;
 }
 
-int launch_render_bwd(const gs_proj* proj, const CamTable& ct, const gs_params* prm,
-                      const unsigned* vals, const unsigned* ranges, const float* final_T,
-                      const unsigned* last_idx, const float* dL_dimage, const float* dL_dentropy,
-                      float* grad2d, const gs_launch* opt, cudaStream_t st) {
+int launch_render_bwd(const gs_proj* proj, long long rows, const CamTable& ct,
+                      const gs_params* prm, const unsigned* vals, const unsigned* ranges,
+                      const float* final_T, const unsigned* last_idx, const float* dL_dimage,
+                      const float* dL_dentropy, float* grad2d, const gs_launch* opt,
+                      cudaStream_t st) {
   BwdArgs a;
   a.recs = proj->records;
   a.vals = vals;
@@ -812,6 +824,8 @@ int launch_render_bwd(const gs_proj* proj, const CamTable& ct, const gs_params* 
   a.grad2d = grad2d;
   a.order = opt ? opt->tile_order : nullptr;
   a.counter = opt ? opt->work_counter : nullptr;
+  a.rows = (unsigned long long)rows;
+  a.pixels = (unsigned long long)(ct.c[ct.V - 1].pix_off + (long long)ct.c[ct.V - 1].W * ct.c[ct.V - 1].H);
   int ctas = opt ? opt->ctas : 0;
   if (ctas > 0) GS_TRY_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(unsigned), st));
   RenderConsts rc = render_consts(prm);

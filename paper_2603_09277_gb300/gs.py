@@ -65,7 +65,8 @@ class GsError(RuntimeError):
 
 
 def _load():
-    path = _build.LIB
+    # GS_LIBRARY selects another build of the library (the bounds-checked one)
+    path = os.environ.get("GS_LIBRARY") or _build.LIB
     if not os.path.exists(path):
         raise ImportError("libgs.so is not built (%s); run paper_2603_09277_gb300.build.build() "
                           "or __graft_entry__.build()" % path)
@@ -85,6 +86,7 @@ def _load():
         "gs_version": (ctypes.c_char_p, []),
         "gs_kernel_launches": (ctypes.c_ulonglong, []),
         "gs_stage_events": (i, [i, vp, vp]),
+        "gs_debug_bounds_status": (i, [P(ctypes.c_uint), i]),
         "gs_preprocess": (i, [vp, vp, vp, vp, vp, i, P(GsCamera), i, P(GsParams), P(GsProj), vp]),
         "gs_bin_sort": (i, [P(GsProj), i, P(GsCamera), i, i, vp, sz, ll, vp, vp, vp, vp, vp, vp,
                             vp]),
@@ -111,6 +113,7 @@ _lib = _load()
 EXPORTED = ["gs_record_bytes", "gs_total_tiles", "gs_total_pixels", "gs_bin_sort_workspace_size",
             "gs_loss_workspace_size", "gs_tile_queue_workspace_size", "gs_status_string",
             "gs_last_error_string", "gs_version", "gs_kernel_launches", "gs_stage_events",
+            "gs_debug_bounds_status",
             "gs_preprocess", "gs_bin_sort", "gs_render_fwd",
             "gs_loss_l1_entropy", "gs_loss_base_workspace_size", "gs_loss_base",
             "gs_render_bwd", "gs_grad2d_attributes", "gs_scale_reset", "gs_tile_queue",
@@ -301,6 +304,14 @@ def gs_stage_events(stage, ev_begin=None, ev_end=None):
     kernel in this thread's later calls."""
     h = lambda e: ctypes.c_void_p(e.cuda_event) if e is not None else None
     return _check("gs_stage_events", _lib.gs_stage_events(stage, h(ev_begin), h(ev_end)))
+
+
+def gs_debug_bounds_status(clear=True):
+    """(status, first failed check id) of the bounds-checked debug build;
+    status is GS_ERR_UNSUPPORTED in the normal build."""
+    v = ctypes.c_uint(0)
+    st = _lib.gs_debug_bounds_status(ctypes.byref(v), 1 if clear else 0)
+    return st, int(v.value)
 
 
 def gs_grad2d_attributes(proj_c, N, V, prm_c, grad2d, out, stream=None):

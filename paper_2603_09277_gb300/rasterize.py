@@ -37,13 +37,15 @@ class Rasterizer:
     N: Gaussian count; attr_dtype: "f32" | "f16" | "bf16" record staging;
     persistent: 0 (one CTA per tile) or the CTA count of a persistent launch
     claiming tiles from a list-length-ordered queue (the batched form);
+    ordered: with one CTA per tile, launch the tiles longest list first (the
+    same queue as the block order);
     pixels_per_thread: 1, 2 or 4 (0 = the library default, 2);
     batch: list entries staged per shared-memory batch, 128 or 256 (0 = 256).
     """
 
     def __init__(self, cams, prm, N, sh_stride=16, attr_dtype="f32", device="cuda",
                  pair_capacity=None, persistent=0, keep_debug=False, pixels_per_thread=0,
-                 batch=0):
+                 batch=0, ordered=False):
         self.device = torch.device(device)
         self.cams = cams
         self.cams_c = gs.make_cameras(cams)
@@ -104,7 +106,8 @@ class Rasterizer:
         self.ppt = int(pixels_per_thread)
         self.batch = int(batch)
         self.tile_order = None
-        if self.persistent:
+        self.ordered = bool(ordered) and not self.persistent
+        if self.persistent or self.ordered:
             self.tile_order = torch.empty(max(self.total_tiles, 1), **i32)
             self.work_counter = torch.zeros(1, **i32)
             self.queue_ws = torch.empty(gs.gs_tile_queue_workspace_size(self.total_tiles),
@@ -118,8 +121,8 @@ class Rasterizer:
             return gs.make_launch(self.tile_order, self.work_counter, self.persistent,
                                   self.stats if stats else None, ev[0], ev[1], self.ppt,
                                   self.batch)
-        return gs.make_launch(None, None, 0, self.stats if stats else None, ev[0], ev[1],
-                              self.ppt, self.batch)
+        return gs.make_launch(self.tile_order if self.ordered else None, None, 0,
+                              self.stats if stats else None, ev[0], ev[1], self.ppt, self.batch)
 
     def _alloc_pairs(self, cap):
         cap = int(min(max(cap, 1), (1 << 32) - 1))
@@ -152,7 +155,7 @@ class Rasterizer:
                 self.sorted_keys = torch.empty(self.capacity, dtype=torch.int64, device=self.device)
         if P is not None:
             self.num_pairs = P
-        if self.persistent:
+        if self.persistent or self.ordered:
             gs.gs_tile_queue(self.tile_ranges, self.total_tiles, self.tile_order, self.queue_ws,
                              stream)
         return P

@@ -128,3 +128,13 @@ def test_autotune_candidates_exist_for_the_workload():
     c = autotune.candidates(16, "f32")
     assert {f["batch"] for f in c} == {128, 256}
     assert len({f["persistent"] for f in c if f["persistent"]}) >= 2
+
+
+def test_debug_bounds_status_needs_the_debug_build():
+    """The normal build carries no index checks: the status call says so
+    (GS_ERR_UNSUPPORTED) and reports no failed check."""
+    from paper_2603_09277_gb300 import gs
+    if os.environ.get("GS_LIBRARY"):
+        pytest.skip("another build of the library is loaded")
+    st, first = gs.gs_debug_bounds_status(clear=True)
+    assert st == gs.GS_ERR_UNSUPPORTED and first == 0
