@@ -310,9 +310,10 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 def traffic_from_profiles(kernel, config):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was captured on this workload from the current source of the kernel's
-    file (csrc/<source>, render.cu unless the entry names another)."""
+    """DRAM bytes per launch of `kernel` on workload `config` from the
+    committed ncu summary (profiles/traffic.json: a list of entries, one per
+    kernel and workload), if that entry was captured from the current source
+    of the kernel's file (csrc/<source>)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -320,18 +321,16 @@ def traffic_from_profiles(kernel, config):
         data = json.load(open(path))
     except ValueError:
         return None
-    ent = data.get(kernel)
-    if not ent:
-        return None
-    src = os.path.join(ROOT, "paper_2603_09277_gb300", "csrc", ent.get("source", "render.cu"))
-    if not os.path.exists(src):
-        return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if ent.get("source_sha256_16", ent.get("render_cu_sha256_16")) != h:
-        return None
-    if ent.get("config") != config:
-        return None
-    return ent.get("bytes_per_launch")
+    entries = data.get("entries", []) if isinstance(data, dict) else []
+    for ent in entries:
+        if ent.get("kernel") != kernel or ent.get("config") != config:
+            continue
+        src = os.path.join(ROOT, "paper_2603_09277_gb300", "csrc", ent.get("source", ""))
+        if not ent.get("source") or not os.path.exists(src):
+            return None
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return ent.get("bytes_per_launch") if ent.get("source_sha256_16") == h else None
+    return None
 
 
 def run_sweep(args, dev):
@@ -917,6 +916,9 @@ def main():
             ach = wk / (kt / 1000.0) / 1e9
             kernels[kn] = {"ms": kt, "bound": "hbm", "achieved_gbs": ach, "frac": ach / hbm,
                            "bytes": int(wk)}
+        kernels[kn]["traffic"] = (traffic_from_profiles(kn, args.config)
+                                  if not args.n and args.tile == 16 and args.attr == "f32"
+                                  else None)
 
     # per-phase times replayed alone from graphs, and the rooflines of the
     # phases other than the dominant kernel: HBM phases against the measured

@@ -96,6 +96,14 @@ typedef struct {
     float* mean2d;           /* optional [V*N][2] */
     float* conic_opacity;    /* optional [V*N][4]: a, b, c, sigma; d = -1/2(a dx^2 + 2b dx dy + c dy^2) */
     float* rgb;              /* optional [V*N][3]: clamped SH colour */
+    unsigned* rect8;         /* optional [V*N]: the rect of every visible row packed in 8-bit
+                                fields, x0 | y0 << 8 | x1 << 16 | y1 << 24, written by
+                                gs_preprocess when every view is at most 255 tiles per side
+                                (rows it culls, and wider views, leave it untouched) and read by
+                                gs_bin_sort under the same condition, where it replaces the
+                                random 16-byte gather of `rect` in depth order by a 4-byte one;
+                                when set for gs_bin_sort it must hold gs_preprocess's output for
+                                the same cameras and tile side */
 } gs_proj;
 
 /* Optional launch controls of the render calls (NULL = defaults). */

@@ -41,12 +41,6 @@
 
 #include "gs_internal.cuh"
 
-// 1: radix digits ranked within a warp by match.any; 0: by one ballot per
-// digit bit (the form the timings chose)
-#ifndef GS_RADIX_MATCH
-#define GS_RADIX_MATCH 0
-#endif
-
 namespace gs {
 namespace {
 
@@ -335,6 +329,16 @@ __device__ __forceinline__ int4 unpack_rect(const uint2 p) {
   return make_int4((int)(p.x & 0xffffu), (int)(p.x >> 16), (int)(p.y & 0xffffu), (int)(p.y >> 16));
 }
 
+// The projection's 8-bit packed rect (gs_proj.rect8: x0 | y0 << 8 | x1 << 16 |
+// y1 << 24, views of at most 255 tiles per side): the depth-ordered gather
+// reads 4 bytes from an array a quarter the size of the int4 rects, most of
+// which stays in L2 (a random 16-byte gather from the int4 rects fetches
+// several times its size from DRAM).
+__device__ __forceinline__ int4 unpack_rect8(unsigned p) {
+  return make_int4((int)(p & 0xffu), (int)((p >> 8) & 0xffu), (int)((p >> 16) & 0xffu),
+                   (int)(p >> 24));
+}
+
 __device__ __forceinline__ int radix_result(const unsigned* range, int bits);
 
 // The depth-sorted rows: the buffer the sort left them in follows from the
@@ -356,8 +360,9 @@ struct SortedRows {
 template <int ITEMS>
 __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
     const SortedRows sorted, const long long* __restrict__ n_dev,
-    const int* __restrict__ rect, int N, const CamTable ct, uint2* __restrict__ rect_sorted,
-    unsigned long long* __restrict__ arrive, const CountsOut co) {
+    const int* __restrict__ rect, const unsigned* __restrict__ rect8, int N, const CamTable ct,
+    uint2* __restrict__ rect_sorted, unsigned long long* __restrict__ arrive,
+    const CountsOut co) {
   unsigned long long* sums_q = co.sums_q;
   unsigned long long* sums_p = co.sums_p;
   const unsigned* __restrict__ rows = sorted.get();
@@ -385,10 +390,20 @@ __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
       row[k] = i < n ? rows[i] : 0xffffffffu;
     }
     int4 rr[kGather];
+    if (rect8) {  // (uniform)
+      unsigned p8[kGather];
 #pragma unroll
-    for (int k = 0; k < kGather; ++k)
-      rr[k] = row[k] != 0xffffffffu && GS_IN_BOUNDS(row[k], (long long)N * ct.V, 204)
-                  ? view_rect(rect, row[k], N, ct) : make_int4(0, 0, 0, 0);
+      for (int k = 0; k < kGather; ++k)
+        p8[k] = row[k] != 0xffffffffu && GS_IN_BOUNDS(row[k], (long long)N * ct.V, 205)
+                    ? rect8[row[k]] : 0u;
+#pragma unroll
+      for (int k = 0; k < kGather; ++k) rr[k] = unpack_rect8(p8[k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kGather; ++k)
+        rr[k] = row[k] != 0xffffffffu && GS_IN_BOUNDS(row[k], (long long)N * ct.V, 204)
+                    ? view_rect(rect, row[k], N, ct) : make_int4(0, 0, 0, 0);
+    }
 #pragma unroll
     for (int k = 0; k < kGather; ++k) {
       const long long i = base + (long long)(k0 + k) * kScanThreads + threadIdx.x;
@@ -861,6 +876,7 @@ __global__ void __launch_bounds__(256) ranges_kernel(const unsigned* __restrict_
 // so each list keeps the depth order of the rows.
 // ----------------------------------------------------------------------------
 constexpr int kSeg = 1024;
+static_assert(kSeg % 256 == 0, "st_count_kernel loads a segment in groups of 256");
 
 __device__ __forceinline__ int view_of_st(const CamTable& ct, int s) {
   int v = 0;
@@ -1028,19 +1044,28 @@ __global__ void __launch_bounds__(256) st_count_kernel(
   for (long long g = blockIdx.x; g < G; g += gridDim.x) {
     const SegInfo si = seg_info(g, st_ranges, seg_first, seg_st, ct);
     unsigned a0 = 0u, a1 = 0u;
-    for (unsigned c0 = si.b + 32u * w; c0 < si.e; c0 += 256u) {  // warp-uniform
-      const unsigned i = c0 + lane;
-      unsigned d = 0u;
+    // a segment holds at most kSeg = 4 x 256 items: each warp's (up to) four
+    // groups of 32 are loaded before any is counted
+    constexpr int kGroups = kSeg / 256;
+    unsigned dd[kGroups];
+#pragma unroll
+    for (int k = 0; k < kGroups; ++k) {
+      const unsigned i = si.b + 32u * w + 256u * k + lane;
+      dd[k] = 0u;
       if (i < si.e) {
         if (packed) {
-          d = sp_keys[i] >> 16;
+          dd[k] = sp_keys[i] >> 16;
         } else {
-          d = st_desc(rect, sp_rows[i], N, ct, si.ox, si.oy);
-          desc[i] = d;
+          dd[k] = st_desc(rect, sp_rows[i], N, ct, si.ox, si.oy);
+          desc[i] = dd[k];
         }
       }
+    }
+#pragma unroll
+    for (int k = 0; k < kGroups; ++k) {
+      if (si.b + 32u * w + 256u * k >= si.e) break;  // warp-uniform
       unsigned B[8], X[8], n0, n1;
-      rect_ballots(d, B, X);
+      rect_ballots(dd[k], B, X);
       lane_tile_counts(B, X, lane, n0, n1);
       a0 += n0;
       a1 += n1;
@@ -1158,6 +1183,7 @@ __device__ __forceinline__ void tile_scan_dev(const unsigned* __restrict__ tile_
 // lanes covering tile (r, c) (B[r] & X[c]) write their rows at consecutive
 // slots, so every list receives its rows in the segment's (depth) order with
 // coalesced stores.
+template <bool KEYS>
 __global__ void __launch_bounds__(256) st_emit_kernel(
     const unsigned* __restrict__ sp_keys, const unsigned* __restrict__ sp_rows,
     const unsigned* __restrict__ desc, int packed, const uint2* __restrict__ st_ranges,
@@ -1210,6 +1236,7 @@ __global__ void __launch_bounds__(256) st_emit_kernel(
       // to the lanes before it (ranks by population counts, no branches per
       // tile: in the dense case nearly every tile has a covering row)
       const unsigned x0 = d & 15u, x1 = (d >> 4) & 15u, y0 = (d >> 8) & 15u, y1 = (d >> 12) & 15u;
+      const unsigned cols = ((1u << x1) - 1u) & ~((1u << x0) - 1u);  // bit c: x0 <= c < x1
       unsigned Xl[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) Xl[c] = X[c] & lt;
@@ -1219,14 +1246,14 @@ __global__ void __launch_bounds__(256) st_emit_kernel(
         const uint4 pa = *reinterpret_cast<const uint4*>(&s_pos[w][8 * r]);
         const uint4 pb = *reinterpret_cast<const uint4*>(&s_pos[w][8 * r + 4]);
         const unsigned sp[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
-        const bool in_r = (unsigned)r >= y0 && (unsigned)r < y1;
+        const unsigned cov = ((unsigned)r >= y0 && (unsigned)r < y1) ? cols : 0u;
 #pragma unroll
         for (unsigned c = 0; c < 8; ++c) {
           // this lane covers tile (r, c): its rank among the covering lanes
           const unsigned pos = sp[c] + __popc(B[r] & Xl[c]);
-          if (in_r && c >= x0 && c < x1 && GS_IN_BOUNDS(pos, cap, 201)) {
+          if ((cov & (1u << c)) && GS_IN_BOUNDS(pos, cap, 201)) {
             out_vals[pos] = row;
-            if (out_keys)
+            if (KEYS)
               out_keys[pos] = ((unsigned long long)(unsigned)s_tile[8 * r + c] << 32) |
                               __float_as_uint(depth[row]);
           }
@@ -1409,6 +1436,8 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
   // scan blocks of 1,024 rows (4 per thread) keep many CTAs in flight when
   // few rows are visible; on large row counts 4,096-row blocks (16 per
   // thread) are faster
+  // the projection's 8-bit packed rects (views of at most 255 tiles per side)
+  const unsigned* rect8 = rect8_fits(ct) ? proj->rect8 : nullptr;
   const bool small = n_rows <= (4ll << 20);
   const int items = small ? 4 : 16;
   const long long nb = (n_rows + kScanThreads * items - 1) / (kScanThreads * items);
@@ -1435,10 +1464,10 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
     //    check and the reported count)
     if (small)
       rows_gather_kernel<4><<<(unsigned)nb, kScanThreads, 0, st>>>(
-          rows_sorted, n_vis, proj->rect, N, ct, w.rect_sorted, arrive + 1, co);
+          rows_sorted, n_vis, proj->rect, rect8, N, ct, w.rect_sorted, arrive + 1, co);
     else
       rows_gather_kernel<16><<<(unsigned)nb, kScanThreads, 0, st>>>(
-          rows_sorted, n_vis, proj->rect, N, ct, w.rect_sorted, arrive + 1, co);
+          rows_sorted, n_vis, proj->rect, rect8, N, ct, w.rect_sorted, arrive + 1, co);
     count_launches(3);
   } else {
     scan_counts_check_kernel<<<1, kScanThreads, 0, st>>>(co, 0);
@@ -1526,10 +1555,15 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
     const int e = stage_event(GS_STAGE_EXPANSION, false, st);
     if (e != GS_OK) return e;
   }
-  st_emit_kernel<<<gs, 256, 0, st>>>(sp_keys, sp_rows, desc, packed,
-                                     reinterpret_cast<const uint2*>(w.st_ranges), w.seg_first,
-                                     w.seg_st, n_seg, w.seg_hist, w.tile_start, ct, proj->depth,
-                                     sorted_vals, sorted_keys, cap);
+  if (sorted_keys)
+    st_emit_kernel<true><<<gs, 256, 0, st>>>(
+        sp_keys, sp_rows, desc, packed, reinterpret_cast<const uint2*>(w.st_ranges), w.seg_first,
+        w.seg_st, n_seg, w.seg_hist, w.tile_start, ct, proj->depth, sorted_vals, sorted_keys,
+        cap);
+  else
+    st_emit_kernel<false><<<gs, 256, 0, st>>>(
+        sp_keys, sp_rows, desc, packed, reinterpret_cast<const uint2*>(w.st_ranges), w.seg_first,
+        w.seg_st, n_seg, w.seg_hist, w.tile_start, ct, proj->depth, sorted_vals, nullptr, cap);
   {
     const int e = stage_event(GS_STAGE_EXPANSION, true, st);
     if (e != GS_OK) return e;

@@ -76,6 +76,15 @@ struct CamTable {
   CamInfo c[GS_MAX_VIEWS];
 };
 
+// gs_proj.rect8 carries the rects when every view is at most 255 tiles per
+// side (the projection writes it and the list construction reads it under
+// this same rule).
+inline bool rect8_fits(const CamTable& ct) {
+  for (int v = 0; v < ct.V; ++v)
+    if (ct.c[v].TX > 255 || ct.c[v].TY > 255) return false;
+  return true;
+}
+
 // Threshold constants in the forms the kernels test them.
 struct RenderConsts {
   float alpha_max;

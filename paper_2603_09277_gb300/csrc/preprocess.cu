@@ -442,6 +442,9 @@ __global__ void __launch_bounds__(256, 5) preprocess_kernel(
     s.sigma = a.sigma;
     store_record<DT>(out.records, row, s);
     reinterpret_cast<int4*>(out.rect)[row] = make_int4(x0, y0, x1, y1);
+    if (out.rect8)  // (views of at most 255 tiles per side)
+      out.rect8[row] =
+          (unsigned)x0 | ((unsigned)y0 << 8) | ((unsigned)x1 << 16) | ((unsigned)y1 << 24);
     out.tiles_touched[row] = (unsigned)((x1 - x0) * (y1 - y0));
     if (out.radius) out.radius[row] = (int)r;
     if (out.mean2d)
@@ -948,6 +951,8 @@ int launch_preprocess(const float* means, const float* log_scales, const float* 
                       const gs_params* prm, const gs_proj* out, cudaStream_t st) {
   if (N == 0) return GS_OK;
   dim3 block(256), grid((N + 255) / 256);
+  gs_proj o = *out;
+  if (!rect8_fits(ct)) o.rect8 = nullptr;
   {
     const int e = stage_event(GS_STAGE_PROJECTION, false, st);
     if (e != GS_OK) return e;
@@ -955,15 +960,15 @@ int launch_preprocess(const float* means, const float* log_scales, const float* 
   switch (prm->attr_dtype) {
     case GS_ATTR_F32:
       preprocess_kernel<GS_ATTR_F32><<<grid, block, 0, st>>>(means, log_scales, quats, opacity_logits,
-          sh, N, ct, prm->dilation, prm->near_z, prm->sh_degree, prm->sh_stride, *out);
+          sh, N, ct, prm->dilation, prm->near_z, prm->sh_degree, prm->sh_stride, o);
       break;
     case GS_ATTR_F16:
       preprocess_kernel<GS_ATTR_F16><<<grid, block, 0, st>>>(means, log_scales, quats, opacity_logits,
-          sh, N, ct, prm->dilation, prm->near_z, prm->sh_degree, prm->sh_stride, *out);
+          sh, N, ct, prm->dilation, prm->near_z, prm->sh_degree, prm->sh_stride, o);
       break;
     case GS_ATTR_BF16:
       preprocess_kernel<GS_ATTR_BF16><<<grid, block, 0, st>>>(means, log_scales, quats, opacity_logits,
-          sh, N, ct, prm->dilation, prm->near_z, prm->sh_degree, prm->sh_stride, *out);
+          sh, N, ct, prm->dilation, prm->near_z, prm->sh_degree, prm->sh_stride, o);
       break;
     default:
       return GS_ERR_INVALID_ARG;

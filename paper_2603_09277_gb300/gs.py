@@ -46,7 +46,8 @@ class GsProj(ctypes.Structure):
     _fields_ = [("records", ctypes.c_void_p), ("depth", ctypes.c_void_p),
                 ("rect", ctypes.c_void_p), ("tiles_touched", ctypes.c_void_p),
                 ("radius", ctypes.c_void_p), ("mean2d", ctypes.c_void_p),
-                ("conic_opacity", ctypes.c_void_p), ("rgb", ctypes.c_void_p)]
+                ("conic_opacity", ctypes.c_void_p), ("rgb", ctypes.c_void_p),
+                ("rect8", ctypes.c_void_p)]
 
 
 class GsLaunch(ctypes.Structure):
@@ -176,9 +177,9 @@ def make_params(prm, sh_stride=16, attr_dtype="f32"):
 
 
 def make_proj(records, depth, rect, tiles_touched, radius=None, mean2d=None, conic_opacity=None,
-              rgb=None):
+              rgb=None, rect8=None):
     return GsProj(_ptr(records), _ptr(depth), _ptr(rect), _ptr(tiles_touched), _ptr(radius),
-                  _ptr(mean2d), _ptr(conic_opacity), _ptr(rgb))
+                  _ptr(mean2d), _ptr(conic_opacity), _ptr(rgb), _ptr(rect8))
 
 
 def make_launch(tile_order=None, work_counter=None, ctas=0, stats=None, ev_begin=None,

@@ -69,6 +69,7 @@ class Rasterizer:
         self.depth = torch.empty(R, **f32)
         self.rect = torch.empty(R, 4, **i32)
         self.tiles_touched = torch.empty(R, **i32)
+        self.rect8 = torch.empty(R, **i32)  # rects packed in 8-bit fields (small views)
         self.keep_debug = keep_debug
         if keep_debug:
             self.radius = torch.empty(R, **i32)
@@ -76,9 +77,11 @@ class Rasterizer:
             self.conic_opacity = torch.empty(R, 4, **f32)
             self.rgb = torch.empty(R, 3, **f32)
             self.proj_c = gs.make_proj(self.records, self.depth, self.rect, self.tiles_touched,
-                                       self.radius, self.mean2d, self.conic_opacity, self.rgb)
+                                       self.radius, self.mean2d, self.conic_opacity, self.rgb,
+                                       self.rect8)
         else:
-            self.proj_c = gs.make_proj(self.records, self.depth, self.rect, self.tiles_touched)
+            self.proj_c = gs.make_proj(self.records, self.depth, self.rect, self.tiles_touched,
+                                       rect8=self.rect8)
         self.tile_ranges = torch.zeros(max(self.total_tiles, 1), 2, **i32)
         self.num_pairs_dev = torch.zeros(1, dtype=torch.int64, device=dev)
         self.status_dev = torch.zeros(1, **i32)

@@ -50,9 +50,11 @@ def _fake_root(tmp_path, src=b"// kernels\n", entry=None):
     (csrc / "render.cu").write_bytes(src)
     (tmp_path / "profiles").mkdir()
     h = hashlib.sha256(src).hexdigest()[:16]
-    ent = {"bytes_per_launch": 4.5e7, "render_cu_sha256_16": h, "config": "cfg2"}
+    ent = {"kernel": "render_bwd_kernel", "bytes_per_launch": 4.5e7, "source": "render.cu",
+           "source_sha256_16": h, "config": "cfg2"}
     ent.update(entry or {})
-    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"render_bwd_kernel": ent}))
+    other = dict(ent, config="cfg3", bytes_per_launch=1.4e8)
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"entries": [ent, other]}))
     return h
 
 
@@ -60,7 +62,8 @@ def test_traffic_counts_only_for_its_source_and_workload(tmp_path, monkeypatch):
     _fake_root(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.traffic_from_profiles("render_bwd_kernel", "cfg2") == 4.5e7
-    assert bench.traffic_from_profiles("render_bwd_kernel", "cfg3") is None
+    assert bench.traffic_from_profiles("render_bwd_kernel", "cfg3") == 1.4e8
+    assert bench.traffic_from_profiles("render_bwd_kernel", "cfg5") is None
     assert bench.traffic_from_profiles("render_fwd_kernel", "cfg2") is None
     # the source changed after the capture: no figure
     (tmp_path / "paper_2603_09277_gb300" / "csrc" / "render.cu").write_bytes(b"// changed\n")

@@ -3,8 +3,10 @@ the oracle's plain definition on layouts that exercise the list
 construction's corners: a view with more than 256 super-tiles of 8x8 tiles
 (the super-tile sort then takes two radix passes), views whose tile grids
 end inside a super-tile (1x1, 9x9, 2x19, 63x2 tiles), Gaussians whose rects
-span many super-tiles, the largest view count (64 views), and more than
-4 M (view, Gaussian) rows (the row scans then take 4,096-row blocks)."""
+span many super-tiles, the largest view count (64 views), more than
+4 M (view, Gaussian) rows (the row scans then take 4,096-row blocks), and
+views of 255 and 263 tiles per side (the rects travel 8-bit packed up to
+255 tiles, in 16-bit fields beyond)."""
 import numpy as np
 import pytest
 
@@ -98,3 +100,13 @@ def test_lists_more_than_four_million_rows():
     assert 70_000 * 64 > (4 << 20)
     P, total, flagged = _compare_lists(scene, cams, scenes.params())
     assert P > 10_000_000 and (flagged or P == total)
+
+
+@pytest.mark.parametrize("width", [4080, 4200])
+def test_lists_rect_packing_limits(width):
+    # 4080 px: 255 tiles, the widest grid of the 8-bit rect packing;
+    # 4200 px: 263 tiles, the 16-bit fields; Gaussians reach both edges
+    scene = scenes.box_scene(6_000, seed=11, ls_mean=-3.0, ls_std=0.8)
+    cams = [scenes.camera(width, 48, float(width) / 2.0)]
+    P, total, flagged = _compare_lists(scene, cams, scenes.params())
+    assert P > 5_000 and (flagged or P == total)
