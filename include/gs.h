@@ -123,6 +123,18 @@ typedef struct {
                                       with 16-pixel tiles */
     int batch;                     /* list entries staged in shared memory per batch: 256, or
                                       128 with F32 records and 16-pixel tiles (0 = 256) */
+    void* zero_beside;             /* gs_render_fwd (optional): device memory that the blending
+                                      kernel zeroes with streaming stores at the start of its
+                                      CTAs (ragged ends off 16-byte boundaries by a memset on
+                                      `stream`); meant for the grad2d buffer of the following
+                                      gs_render_bwd, whose own zeroing would otherwise sit
+                                      between the two blending kernels (the forward is bound by
+                                      instruction issue and leaves the memory bandwidth mostly
+                                      idle) */
+    unsigned long long zero_bytes; /* bytes of zero_beside to zero (0: none) */
+    int grad2d_zeroed;             /* gs_render_bwd: nonzero when grad2d is already zero (e.g.
+                                      through the forward's zero_beside); the call then skips
+                                      its own zeroing of grad2d */
 } gs_launch;
 
 /* ---------------------------------------------------------------------- */

@@ -589,7 +589,8 @@ int gs_render_bwd(const gs_proj* proj, int N, const gs_camera* cams, int V, cons
   if (const char* why = launch_opt_error(opt, prm)) return invalid(why);
   cudaStream_t st = (cudaStream_t)stream;
   if (N == 0) return GS_OK;  // no Gaussians: no gradients
-  GS_TRY_CUDA(cudaMemsetAsync(grad2d, 0, sizeof(float) * 12 * (size_t)N * V, st));
+  if (!opt || !opt->grad2d_zeroed)
+    GS_TRY_CUDA(cudaMemsetAsync(grad2d, 0, sizeof(float) * 12 * (size_t)N * V, st));
   // Beside the blending adjoint (bound by instruction issue, most of the
   // memory bandwidth free), on the side stream: the list of Gaussians some
   // view sees (in grad2d's pad floats, after its zeroing) and the zeroing of

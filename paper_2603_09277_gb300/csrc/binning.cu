@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
 #pragma unroll
     for (int k = 0; k < kGather; ++k) {
       const long long i = base + (long long)(k0 + k) * kScanThreads + threadIdx.x;
-      row[k] = i < n ? rows[i] : 0xffffffffu;
+      row[k] = i < n ? __ldcs(rows + i) : 0xffffffffu;  // streamed: evict first
     }
     int4 rr[kGather];
     if (rect8) {  // (uniform)
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
       const long long i = base + (long long)(k0 + k) * kScanThreads + threadIdx.x;
       if (i < n) {
         const int4 r = rr[k];
-        rect_sorted[i] = pack_rect(r);
+        __stcs(rect_sorted + i, pack_rect(r));  // streamed: keeps rect8 in L2
         q += st_count(r);
         pp += (unsigned long long)((r.z - r.x) * (r.w - r.y));
       }

@@ -580,15 +580,7 @@ __device__ __forceinline__ void adjoint_view(
           }
         }
       }
-      // coefficients past K (sh_stride > K) get zeros from the first view
-      if (first_view) {
-        if (vec_out) {
-          for (int i = (3 * K + 3) / 4; i < 3 * sh_stride / 4; ++i)
-            reinterpret_cast<float4*>(gsh)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        } else {
-          for (int e = 3 * K; e < 3 * sh_stride; ++e) gsh[e] = 0.f;
-        }
-      }
+      // (coefficients past K keep the zeros of the caller's zeroing)
     }
     if (sh_deg > 0) {
       float3 gd = sh_basis_grad_dot(sh_deg, dx, dy, dz, cdot);
@@ -679,20 +671,25 @@ __device__ __forceinline__ void adjoint_view(
   }
 
 // Writes Gaussian g's gradients from the group's sums: lane `sub` == 0 the
-// per-Gaussian ones, the SH coefficients (zeros past the K in use) split over
-// the group's L lanes as 16-byte stores where aligned.
+// per-Gaussian ones, the K SH coefficients in use split over the group's L
+// lanes as 16-byte stores where aligned, up to the end of the 32-byte sector
+// holding the last of them (a partly written sector is filled from DRAM
+// first); the coefficients past that keep the zeros of the caller's zeroing
+// (with 16 coefficients stored per Gaussian and degree 0 in use, rewriting
+// them was 15/16 of this kernel's SH writes).
 template <int DEG, int L, bool SHREG>
 __device__ __forceinline__ void adjoint_finish(
     int g, int sub, const Activated& a, const AdjAcc<DEG>& acc, int sh_stride, bool vec_out,
     float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
     float* __restrict__ g_opac, float* __restrict__ g_sh) {
   constexpr int K = AdjAcc<DEG>::K;
+  constexpr int kSectorFloats = (3 * K + 7) / 8 * 8;  // 3K rounded up to 32 bytes
   float* gsh = g_sh + (long long)g * sh_stride * 3;
   if (!SHREG) {
   } else if (vec_out) {
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
-      if (i % L == sub && 4 * i < 3 * sh_stride) {
+      if (i % L == sub && 4 * i < kSectorFloats && 4 * i < 3 * sh_stride) {
         float o[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) o[j] = 4 * i + j < 3 * K ? acc.gsh[4 * i + j] : 0.f;
@@ -702,7 +699,7 @@ __device__ __forceinline__ void adjoint_finish(
   } else {
 #pragma unroll
     for (int e = 0; e < 48; ++e)
-      if (e % L == sub && e < 3 * sh_stride) gsh[e] = e < 3 * K ? acc.gsh[e] : 0.f;
+      if (e % L == sub && e < 3 * K) gsh[e] = acc.gsh[e];
   }
   if (sub != 0) return;
   const float* gm = acc.gm;

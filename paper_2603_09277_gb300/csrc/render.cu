@@ -170,7 +170,22 @@ struct FwdArgs {
   unsigned* counter;
   unsigned long long* stats;
   unsigned long long rows, pixels;  // extents of the record and per-pixel arrays
+  uint4* zero;                      // zeroed by the kernel's CTAs (optional)
+  unsigned long long zero_n16;      // its size in 16-byte units
 };
+
+// A CTA's stripe of FwdArgs::zero, stored at the start of the forward with
+// evict-first stores: the blending is bound by instruction issue and leaves
+// the memory bandwidth mostly idle, so this costs a few issue slots where a
+// separate zeroing kernel (even on a second stream: the forward's CTAs fill
+// the register file, nothing runs beside them) added its whole duration.
+__device__ __forceinline__ void zero_stripe(uint4* __restrict__ z, unsigned long long n16) {
+  const unsigned long long per = (n16 + gridDim.x - 1) / gridDim.x;
+  const unsigned long long b = (unsigned long long)blockIdx.x * per;
+  const unsigned long long e = min(n16, b + per);
+  for (unsigned long long i = b + threadIdx.x; i < e; i += blockDim.x)
+    __stcs(z + i, make_uint4(0u, 0u, 0u, 0u));
+}
 
 // One list entry against a thread's two pixels (rows ry and ry + 1 of one
 // column) in the forward, both through the same steps with packed FP32
@@ -369,6 +384,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) render_fwd_kernel(const CamTabl
                                                                     const FwdArgs a,
                                                                     int persistent) {
   unsigned long long nb = 0, ne = 0;
+  if (a.zero) zero_stripe(a.zero, a.zero_n16);
   if (persistent) {
     __shared__ unsigned s_t;
     for (;;) {
@@ -797,6 +813,23 @@ int launch_render_fwd(const gs_proj* proj, long long rows, const CamTable& ct,
   a.stats = opt ? opt->stats : nullptr;
   a.rows = (unsigned long long)rows;
   a.pixels = (unsigned long long)(ct.c[ct.V - 1].pix_off + (long long)ct.c[ct.V - 1].W * ct.c[ct.V - 1].H);
+  // memory to zero beside the blending: the kernel's CTAs take the 16-byte
+  // aligned whole units, a memset the ragged ends
+  a.zero = nullptr;
+  a.zero_n16 = 0;
+  if (opt && opt->zero_beside && opt->zero_bytes > 0) {
+    const uintptr_t z0 = reinterpret_cast<uintptr_t>(opt->zero_beside);
+    const uintptr_t z1 = z0 + (uintptr_t)opt->zero_bytes;
+    const uintptr_t a0 = (z0 + 15) & ~uintptr_t(15), a1 = z1 & ~uintptr_t(15);
+    if (a1 > a0) {
+      a.zero = reinterpret_cast<uint4*>(a0);
+      a.zero_n16 = (unsigned long long)((a1 - a0) / 16);
+      if (a0 > z0) GS_TRY_CUDA(cudaMemsetAsync(opt->zero_beside, 0, a0 - z0, st));
+      if (z1 > a1) GS_TRY_CUDA(cudaMemsetAsync(reinterpret_cast<void*>(a1), 0, z1 - a1, st));
+    } else {
+      GS_TRY_CUDA(cudaMemsetAsync(opt->zero_beside, 0, (size_t)opt->zero_bytes, st));
+    }
+  }
   int ctas = opt ? opt->ctas : 0;
   if (ctas > 0) GS_TRY_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(unsigned), st));
   RenderConsts rc = render_consts(prm);

@@ -54,7 +54,9 @@ class GsLaunch(ctypes.Structure):
     _fields_ = [("tile_order", ctypes.c_void_p), ("work_counter", ctypes.c_void_p),
                 ("ctas", ctypes.c_int), ("stats", ctypes.c_void_p),
                 ("ev_begin", ctypes.c_void_p), ("ev_end", ctypes.c_void_p),
-                ("pixels_per_thread", ctypes.c_int), ("batch", ctypes.c_int)]
+                ("pixels_per_thread", ctypes.c_int), ("batch", ctypes.c_int),
+                ("zero_beside", ctypes.c_void_p), ("zero_bytes", ctypes.c_ulonglong),
+                ("grad2d_zeroed", ctypes.c_int)]
 
 
 class GsError(RuntimeError):
@@ -183,12 +185,14 @@ def make_proj(records, depth, rect, tiles_touched, radius=None, mean2d=None, con
 
 
 def make_launch(tile_order=None, work_counter=None, ctas=0, stats=None, ev_begin=None,
-                ev_end=None, pixels_per_thread=0, batch=0):
-    """ev_begin / ev_end: recorded torch.cuda.Event objects (or None)."""
+                ev_end=None, pixels_per_thread=0, batch=0, zero_beside=None, grad2d_zeroed=False):
+    """ev_begin / ev_end: recorded torch.cuda.Event objects (or None);
+    zero_beside: a device tensor the forward zeroes beside its kernel."""
+    zb = 0 if zero_beside is None else zero_beside.numel() * zero_beside.element_size()
     return GsLaunch(_ptr(tile_order), _ptr(work_counter), int(ctas), _ptr(stats),
                     ev_begin.cuda_event if ev_begin is not None else None,
                     ev_end.cuda_event if ev_end is not None else None, int(pixels_per_thread),
-                    int(batch))
+                    int(batch), _ptr(zero_beside), zb, 1 if grad2d_zeroed else 0)
 
 
 # ---------------------------------------------------------------------------

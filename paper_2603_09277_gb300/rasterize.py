@@ -97,6 +97,7 @@ class Rasterizer:
         self.dL_dentropy = torch.empty(P, **f32)
         self.loss_ws = torch.empty(gs.gs_loss_workspace_size(P), dtype=torch.uint8, device=dev)
         self.grad2d = torch.empty(R, 12, **f32)
+        self._grad2d_zero = False  # grad2d zeroed by the latest forward, not yet used
         self.grads = {
             "means": torch.empty(max(self.N, 1), 3, **f32),
             "log_scales": torch.empty(max(self.N, 1), 3, **f32),
@@ -118,14 +119,15 @@ class Rasterizer:
         self.num_pairs = None
         self.forward_count = 0  # forwards run through rasterize(); see _Rasterize
 
-    def _launch(self, stats=False, events=None):
+    def _launch(self, stats=False, events=None, zero_beside=None, grad2d_zeroed=False):
         ev = events if events is not None else (None, None)
         if self.persistent:
             return gs.make_launch(self.tile_order, self.work_counter, self.persistent,
                                   self.stats if stats else None, ev[0], ev[1], self.ppt,
-                                  self.batch)
+                                  self.batch, zero_beside, grad2d_zeroed)
         return gs.make_launch(self.tile_order if self.ordered else None, None, 0,
-                              self.stats if stats else None, ev[0], ev[1], self.ppt, self.batch)
+                              self.stats if stats else None, ev[0], ev[1], self.ppt, self.batch,
+                              zero_beside, grad2d_zeroed)
 
     def _alloc_pairs(self, cap):
         cap = int(min(max(cap, 1), (1 << 32) - 1))
@@ -168,9 +170,11 @@ class Rasterizer:
         around the blending kernel."""
         if stats:
             self.stats.zero_()
+        # the backward's grad2d is zeroed beside the forward kernel
         gs.gs_render_fwd(self.proj_c, self.N, self.cams_c, self.prm_c, self.sorted_vals,
                          self.tile_ranges, self.image, self.final_T, self.last_idx, self.entropy,
-                         self._launch(stats, events), stream)
+                         self._launch(stats, events, zero_beside=self.grad2d), stream)
+        self._grad2d_zero = True
 
     def _base_ws(self):
         need = gs.gs_loss_base_workspace_size(self.cams_c)
@@ -199,7 +203,8 @@ class Rasterizer:
                          self.tile_ranges, self.final_T, self.last_idx, dimg, dent, p["means"],
                          p["log_scales"], p["quats"], p["opacity_logits"], p["sh"], self.grad2d,
                          g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"],
-                         self._launch(False, events), stream)
+                         self._launch(False, events, grad2d_zeroed=self._grad2d_zero), stream)
+        self._grad2d_zero = False  # a second backward of one forward zeroes it itself
         return g
 
     def grad2d_attributes(self, stream=None):

@@ -5,7 +5,9 @@ gradient is zeroed.  Every gradient buffer is filled with NaN before the
 call, so an entry that the call leaves unwritten shows up; the written values
 are checked against the oracle elsewhere (test_parity_gpu.py), here only that
 unseen Gaussians get exact zeros, that SH coefficients past the degree in use
-get exact zeros, and that repeated calls give the same gradients.
+get exact zeros, that repeated calls give the same gradients, and that the
+moment rows are zero when the backward starts whether the forward zeroed
+them beside its kernel or the backward zeroes them itself.
 """
 import numpy as np
 import pytest
@@ -62,3 +64,32 @@ def test_every_gradient_written_unseen_zero_sh_tail_zero(views):
     # the same inputs give the same gradients (no stale state between calls)
     for k in g:
         np.testing.assert_allclose(outs[1][k], g[k], rtol=1e-5, atol=1e-7)
+
+
+def test_grad2d_zeroed_beside_the_forward_or_by_the_backward():
+    # grad2d starts as NaN: the forward zeroes it beside its kernel for the
+    # first backward; a second backward of the same forward finds the first
+    # one's sums there and zeroes them itself
+    import torch
+    from paper_2603_09277_gb300.rasterize import Rasterizer, scene_to_device, targets_to_device
+    n = 4000
+    scene = scenes.box_scene(n, seed=12)
+    prm = scenes.params()
+    cams = scenes.yaw_cameras([(96, 64), (80, 80)], [0.0, 6.0])
+    r = Rasterizer(cams, prm, n)
+    p = scene_to_device(scene)
+    tg = targets_to_device(scenes.noise_targets(cams, 6))
+    r.preprocess(p)
+    r.bin_sort()
+    r.grad2d.fill_(float("nan"))
+    r.render_fwd()
+    r.loss(tg, scenes.GAMMA)
+    outs = []
+    for _ in range(2):
+        g = r.render_bwd(p)
+        torch.cuda.synchronize()
+        outs.append({k: v.cpu().numpy().copy() for k, v in g.items()})
+    for k in outs[0]:
+        assert np.isfinite(outs[0][k]).all(), k
+        assert np.abs(outs[0][k]).sum() > 0, k
+        np.testing.assert_allclose(outs[1][k], outs[0][k], rtol=1e-5, atol=1e-7)
