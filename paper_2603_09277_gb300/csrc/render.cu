@@ -467,8 +467,11 @@ __device__ __forceinline__ float warp_sum9(const float v[9], int lane, int& slot
 // alpha = 0: its transmittance is kept by a select and every contribution
 // is zero, and its L stays finite (w is floored at 1e-30 inside the log).
 // The exponent is the scalar path's value exactly: RN(q^2 - base) is
-// -RN(base - q^2).  Adds the pixel sums of the 6 moments and 3 colour
-// weights to gsum; returns whether either pixel took part.
+// -RN(base - q^2).  Sets gsum to the pixel sums of the 6 moments and 3
+// colour weights, which are exact zeros where neither pixel takes part
+// (alpha = 0 makes w and dd zero; every other factor is finite), so a lane
+// past its last blended entry needs no branch of its own; returns whether
+// either pixel took part.
 __device__ __forceinline__ bool bwd_pair(const RenderConsts& rc, const float4 g0, const float4 g1,
                                          const float cB, float rx, float2 ry2, unsigned pos,
                                          unsigned last0, unsigned last1, float2& T2,
@@ -482,7 +485,11 @@ __device__ __forceinline__ bool bwd_pair(const RenderConsts& rc, const float4 g0
   const float2 en = __ffma2_rn(qv, qv, make_float2(-col.base, -col.base));  // -e
   const bool a0 = pos < last0 && !(-en.x < rc.log2_alpha_min);
   const bool a1 = pos < last1 && !(-en.y < rc.log2_alpha_min);
-  if (!(a0 || a1)) return false;
+  if (!__any_sync(kFull, a0 || a1)) {  // (warp-uniform) no pixel of the warp takes part
+#pragma unroll
+    for (int i = 0; i < 9; ++i) gsum[i] = 0.f;
+    return false;
+  }
   const float ar0 = a0 ? fast_exp2(-en.x) : 0.f;
   const float ar1 = a1 ? fast_exp2(-en.y) : 0.f;
   const float2 al = make_float2(fminf(rc.alpha_max, ar0), fminf(rc.alpha_max, ar1));
@@ -511,16 +518,16 @@ __device__ __forceinline__ bool bwd_pair(const RenderConsts& rc, const float4 g0
   const float2 dx2 = make_float2(dx, dx);
   const float2 ddx = __fmul2_rn(dd, dx2), ddy = __fmul2_rn(dd, dy);
   const float2 m2 = __fmul2_rn(ddx, dx2), m3 = __fmul2_rn(ddx, dy), m4 = __fmul2_rn(ddy, dy);
-  gsum[0] += ddx.x + ddx.y;
-  gsum[1] += ddy.x + ddy.y;
-  gsum[2] += m2.x + m2.y;
-  gsum[3] += m3.x + m3.y;
-  gsum[4] += m4.x + m4.y;
-  gsum[5] += dd.x + dd.y;
-  gsum[6] += c6.x + c6.y;
-  gsum[7] += c7.x + c7.y;
-  gsum[8] += c8.x + c8.y;
-  return true;
+  gsum[0] = ddx.x + ddx.y;
+  gsum[1] = ddy.x + ddy.y;
+  gsum[2] = m2.x + m2.y;
+  gsum[3] = m3.x + m3.y;
+  gsum[4] = m4.x + m4.y;
+  gsum[5] = dd.x + dd.y;
+  gsum[6] = c6.x + c6.y;
+  gsum[7] = c7.x + c7.y;
+  gsum[8] = c8.x + c8.y;
+  return a0 || a1;
 }
 
 template <int DT, int TS, int PPT, int B>
@@ -608,13 +615,16 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
       const bool any_here = pos < mylast;
       if (!__any_sync(kFull, any_here)) continue;
       float gsum[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) gsum[i] = 0.f;
       bool contrib = false;
       if constexpr (PPT == 2) {
-        if (any_here) contrib = bwd_pair(rc, s0[k], s1[k], s2[k], tg.rx, ry2, pos, last[0],
-                                         last[1], T2, gr2, gg2, gb2, gH2, gS2, R2, gsum);
-      } else if (any_here) {
+        // every lane (one past its last blended entry takes no part and adds zeros)
+        contrib = bwd_pair(rc, s0[k], s1[k], s2[k], tg.rx, ry2, pos, last[0], last[1], T2, gr2,
+                           gg2, gb2, gH2, gS2, R2, gsum);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) gsum[i] = 0.f;
+      }
+      if (PPT != 2 && any_here) {
         const float4 g0 = s0[k];
         const float4 g1 = s1[k];
         const float cB = s2[k];
