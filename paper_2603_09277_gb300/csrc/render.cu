@@ -470,9 +470,10 @@ __device__ __forceinline__ float warp_sum9(const float v[9], int lane, int& slot
 // -RN(base - q^2).  Sets gsum to the pixel sums of the 6 moments and 3
 // colour weights, which are exact zeros where neither pixel takes part
 // (alpha = 0 makes w and dd zero; every other factor is finite), so a lane
-// past its last blended entry needs no branch of its own; returns whether
-// either pixel took part.
-__device__ __forceinline__ bool bwd_pair(const RenderConsts& rc, const float4 g0, const float4 g1,
+// past its last blended entry needs no branch of its own.  Returns the
+// warp's lanes where either pixel took part (gsum is left unset when there
+// are none).
+__device__ __forceinline__ unsigned bwd_pair(const RenderConsts& rc, const float4 g0, const float4 g1,
                                          const float cB, float rx, float2 ry2, unsigned pos,
                                          unsigned last0, unsigned last1, float2& T2,
                                          const float2 gr2, const float2 gg2, const float2 gb2,
@@ -485,11 +486,8 @@ __device__ __forceinline__ bool bwd_pair(const RenderConsts& rc, const float4 g0
   const float2 en = __ffma2_rn(qv, qv, make_float2(-col.base, -col.base));  // -e
   const bool a0 = pos < last0 && !(-en.x < rc.log2_alpha_min);
   const bool a1 = pos < last1 && !(-en.y < rc.log2_alpha_min);
-  if (!__any_sync(kFull, a0 || a1)) {  // (warp-uniform) no pixel of the warp takes part
-#pragma unroll
-    for (int i = 0; i < 9; ++i) gsum[i] = 0.f;
-    return false;
-  }
+  const unsigned who = __ballot_sync(kFull, a0 || a1);
+  if (!who) return 0u;  // (warp-uniform) no pixel of the warp takes part
   const float ar0 = a0 ? fast_exp2(-en.x) : 0.f;
   const float ar1 = a1 ? fast_exp2(-en.y) : 0.f;
   const float2 al = make_float2(fminf(rc.alpha_max, ar0), fminf(rc.alpha_max, ar1));
@@ -515,19 +513,19 @@ __device__ __forceinline__ bool bwd_pair(const RenderConsts& rc, const float4 g0
   // dd = dalpha alpha where alpha is below its clamp, then the moments
   const float2 dd = __fmul2_rn(dA, make_float2(ar0 <= rc.alpha_max ? ar0 : 0.f,
                                                ar1 <= rc.alpha_max ? ar1 : 0.f));
-  const float2 dx2 = make_float2(dx, dx);
-  const float2 ddx = __fmul2_rn(dd, dx2), ddy = __fmul2_rn(dd, dy);
-  const float2 m2 = __fmul2_rn(ddx, dx2), m3 = __fmul2_rn(ddx, dy), m4 = __fmul2_rn(ddy, dy);
-  gsum[0] = ddx.x + ddx.y;
-  gsum[1] = ddy.x + ddy.y;
-  gsum[2] = m2.x + m2.y;
-  gsum[3] = m3.x + m3.y;
-  gsum[4] = m4.x + m4.y;
+  // the two pixels share the column offset dx: the dx-moments are dx times
+  // the pixel sums of dd and dd dy
+  const float2 ddy = __fmul2_rn(dd, dy);
   gsum[5] = dd.x + dd.y;
+  gsum[1] = ddy.x + ddy.y;
+  gsum[0] = dx * gsum[5];
+  gsum[2] = dx * gsum[0];
+  gsum[3] = dx * gsum[1];
+  gsum[4] = __fmaf_rn(ddy.x, dy.x, ddy.y * dy.y);
   gsum[6] = c6.x + c6.y;
   gsum[7] = c7.x + c7.y;
   gsum[8] = c8.x + c8.y;
-  return a0 || a1;
+  return who;
 }
 
 template <int DT, int TS, int PPT, int B>
@@ -616,10 +614,12 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
       if (!__any_sync(kFull, any_here)) continue;
       float gsum[9];
       bool contrib = false;
+      unsigned who = 0u;
       if constexpr (PPT == 2) {
         // every lane (one past its last blended entry takes no part and adds zeros)
-        contrib = bwd_pair(rc, s0[k], s1[k], s2[k], tg.rx, ry2, pos, last[0], last[1], T2, gr2,
-                           gg2, gb2, gH2, gS2, R2, gsum);
+        who = bwd_pair(rc, s0[k], s1[k], s2[k], tg.rx, ry2, pos, last[0], last[1], T2, gr2, gg2,
+                       gb2, gH2, gS2, R2, gsum);
+        contrib = (who >> lane) & 1u;
       } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) gsum[i] = 0.f;
@@ -666,7 +666,7 @@ __device__ __forceinline__ void bwd_tile(const CamTable& ct, const RenderConsts&
           }
         }
       }
-      const unsigned who = __ballot_sync(kFull, contrib);
+      if constexpr (PPT != 2) who = __ballot_sync(kFull, contrib);
       if (who) {
         float* G = a.grad2d + 12ll * s_row[k];
         if (__popc(who) <= kDirectLanes) {
