@@ -517,6 +517,31 @@ struct AdjAcc {
 };
 
 // Adjoint of Gaussian g in view v (which sees it), added to acc.
+// A Gaussian's SH coefficients for the adjoint's views: held in registers at
+// degree 0 (3 floats, read once per Gaussian instead of twice per view; the
+// 12 floats of degree 1 would spill), read from the block on each use above.
+template <int DEG>
+struct ShCoef {
+  static constexpr int K = (DEG + 1) * (DEG + 1);
+  static constexpr bool kCached = DEG == 0;
+  float c[kCached ? 3 * K : 1];
+  __device__ __forceinline__ void load(const float* __restrict__ sh, long long g, int stride,
+                                       bool vec) {
+    if constexpr (kCached) for_sh_block(sh, g, stride, K, vec, [&](int e, float v) { c[e] = v; });
+  }
+  // f(e, value) for e < 3K, like for_sh_block
+  template <typename F>
+  __device__ __forceinline__ void each(const float* __restrict__ sh, long long g, int stride,
+                                       bool vec, F&& f) const {
+    if constexpr (kCached) {
+#pragma unroll
+      for (int e = 0; e < 3 * K; ++e) f(e, c[e]);
+    } else {
+      for_sh_block(sh, g, stride, K, vec, f);
+    }
+  }
+};
+
 // SHREG: the SH gradient is summed in acc (a group of several lanes);
 // otherwise (one lane per Gaussian, degree 3: 48 sums would halve the
 // occupancy) it goes to g_sh directly: the first view that sees the
@@ -525,7 +550,8 @@ template <int DEG, bool SHREG>
 __device__ __forceinline__ void adjoint_view(
     int g, int v, const Activated& a, const float* __restrict__ sh, int N, const CamTable& ct,
     float dilation, int sh_stride, bool vec, const float* __restrict__ grad2d,
-    AdjAcc<SHREG ? DEG : 0>& acc, bool first_view, bool vec_out, float* __restrict__ g_sh) {
+    AdjAcc<SHREG ? DEG : 0>& acc, bool first_view, bool vec_out, float* __restrict__ g_sh,
+    const ShCoef<DEG>& shc) {
   constexpr int sh_deg = DEG;
   constexpr int K = AdjAcc<DEG>::K;
   float* gm = acc.gm;
@@ -551,12 +577,12 @@ __device__ __forceinline__ void adjoint_view(
     float Y[16] = {};
     sh_basis(sh_deg, dx, dy, dz, Y);
     float raw[3] = {0.5f, 0.5f, 0.5f};
-    for_sh_block(sh, g, sh_stride, K, vec, [&](int e, float v) { raw[e % 3] += Y[e / 3] * v; });
+    shc.each(sh, g, sh_stride, vec, [&](int e, float v) { raw[e % 3] += Y[e / 3] * v; });
     float grgb[3] = {raw[0] < 0.f ? 0.f : G1.z, raw[1] < 0.f ? 0.f : G1.w,
                      raw[2] < 0.f ? 0.f : G2.x};
     float cdot[16] = {};  // SH[k] . grgb
-    for_sh_block(sh, g, sh_stride, K, vec,
-                 [&](int e, float v) { cdot[e / 3] = __fmaf_rn(v, grgb[e % 3], cdot[e / 3]); });
+    shc.each(sh, g, sh_stride, vec,
+             [&](int e, float v) { cdot[e / 3] = __fmaf_rn(v, grgb[e % 3], cdot[e / 3]); });
     // dL/dSH[k][ch] = Y_k grgb_ch
     if constexpr (SHREG) {
 #pragma unroll
@@ -760,13 +786,23 @@ __device__ __forceinline__ void adjoint_group(
   constexpr bool SHREG = L > 1 || DEG < 3;
   AdjAcc<SHREG ? DEG : 0> acc;
   acc.zero();
-  bool first = true;
+  // the views (of this lane's share) that see the Gaussian, as a mask: the
+  // loads are issued together instead of one memory latency per view ahead
+  // of its moment row's
+  unsigned long long seen = 0ull;
+#pragma unroll 8
   for (int v = sub; v < ct.V; v += L)
-    if (tiles_touched[(long long)v * N + g] != 0u) {
-      adjoint_view<DEG, SHREG>(g, v, a, sh, N, ct, dilation, sh_stride, vec, grad2d, acc, first,
-                               vec_out, g_sh);
-      first = false;
-    }
+    seen |= (unsigned long long)(tiles_touched[(long long)v * N + g] != 0u) << v;
+  ShCoef<DEG> shc;
+  shc.load(sh, g, sh_stride, vec);
+  bool first = true;
+  while (seen) {
+    const int v = __ffsll((long long)seen) - 1;
+    seen &= seen - 1ull;
+    adjoint_view<DEG, SHREG>(g, v, a, sh, N, ct, dilation, sh_stride, vec, grad2d, acc, first,
+                             vec_out, g_sh, shc);
+    first = false;
+  }
   acc.template reduce<L>(mask);
   adjoint_finish<SHREG ? DEG : 0, L, SHREG>(g, sub, a, acc, sh_stride, vec_out, g_means, g_ls,
                                             g_quats, g_opac, g_sh);
