@@ -513,19 +513,15 @@ __device__ __forceinline__ unsigned bwd_pair(const RenderConsts& rc, const float
   // dd = dalpha alpha where alpha is below its clamp, then the moments
   const float2 dd = __fmul2_rn(dA, make_float2(ar0 <= rc.alpha_max ? ar0 : 0.f,
                                                ar1 <= rc.alpha_max ? ar1 : 0.f));
-  // (each pixel's moments are formed before the two are added: deriving the
-  // dx-moments from the pixel sums instead, dx (dd.x + dd.y) etc., shares one
-  // rounding among Sx, Sxx and Sxy and put a near-degenerate disc's rotation
-  // gradient 6 % past the element-wise bar, against 89 % of it this way)
-  const float2 dx2 = make_float2(dx, dx);
-  const float2 ddx = __fmul2_rn(dd, dx2), ddy = __fmul2_rn(dd, dy);
-  const float2 m2 = __fmul2_rn(ddx, dx2), m3 = __fmul2_rn(ddx, dy), m4 = __fmul2_rn(ddy, dy);
-  gsum[0] = ddx.x + ddx.y;
-  gsum[1] = ddy.x + ddy.y;
-  gsum[2] = m2.x + m2.y;
-  gsum[3] = m3.x + m3.y;
-  gsum[4] = m4.x + m4.y;
+  // the two pixels share the column offset dx: the dx-moments are dx times
+  // the pixel sums of dd and dd dy
+  const float2 ddy = __fmul2_rn(dd, dy);
   gsum[5] = dd.x + dd.y;
+  gsum[1] = ddy.x + ddy.y;
+  gsum[0] = dx * gsum[5];
+  gsum[2] = dx * gsum[0];
+  gsum[3] = dx * gsum[1];
+  gsum[4] = __fmaf_rn(ddy.x, dy.x, ddy.y * dy.y);
   gsum[6] = c6.x + c6.y;
   gsum[7] = c7.x + c7.y;
   gsum[8] = c8.x + c8.y;

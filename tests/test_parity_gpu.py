@@ -455,10 +455,13 @@ def test_degenerate_covariances():
     check_projection(g, views, cams, N)
     check_lists(g, views, cams, N)
     check_pixels(g, views, cams, N)
-    # needles and discs with axis ratios near e^10: the whitened adjoint keeps
-    # their FP32 gradients to about 1e-5 of the largest entry (measured
-    # 1.2e-5), so this scene takes an element-wise floor of 1e-4 of it
-    check_grads(g, grads, views, cams, N, 1, floor=1e-4)
+    # needles and discs with axis ratios near e^10: most of their FP32
+    # gradients stay within 1.2e-5 of the largest entry, but one disc's
+    # rotation gradient (0.1 % of that entry, the sum of large cancelling
+    # terms) lands 0.89e-4 or 1.06e-4 of it from the oracle depending on the
+    # order in which the blending adjoint's atomics add its moment row, so
+    # this scene takes an element-wise floor of 2e-4 of the largest entry
+    check_grads(g, grads, views, cams, N, 1, floor=2e-4)
 
 
 def test_capacity_overflow_regrows():
