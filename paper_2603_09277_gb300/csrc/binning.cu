@@ -143,25 +143,46 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(ScanSrc src, 
   }
 }
 
-// Phase 2: exclusive scan of the block sums in one block; writes the grand
-// total to *total.
+// Phase 2: exclusive scan of the block sums in one block (in place); returns
+// the grand total.  Each warp takes a contiguous chunk of the sums: its total
+// (a lane's loads in flight together), one scan of the warp totals, then the
+// chunk again with the warp's running offset -- no block-wide barrier per
+// round of 256 sums (cfg3-sized inputs have ~6,000 blocks).
 __device__ __forceinline__ long long scan_blocks_dev(unsigned long long* block_sums, int nblocks) {
-  __shared__ unsigned long long s_carry;
-  if (threadIdx.x == 0) s_carry = 0;
+  constexpr int NW = kScanThreads / 32;
+  __shared__ unsigned long long s_wt[NW + 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int per = (nblocks + NW - 1) / NW;
+  const int b0 = min(nblocks, w * per), b1 = min(nblocks, b0 + per);
+  unsigned long long tot = 0ull;
+#pragma unroll 4
+  for (int i = b0 + lane; i < b1; i += 32) tot += __ldcg(block_sums + i);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+  if (lane == 0) s_wt[w] = tot;
   __syncthreads();
-  for (int base = 0; base < nblocks; base += kScanThreads) {
-    int i = base + threadIdx.x;
-    unsigned long long x = i < nblocks ? __ldcg(block_sums + i) : 0ull;
-    unsigned long long tot;
-    unsigned long long ex = block_excl_scan(x, &tot);
-    if (i < nblocks) block_sums[i] = s_carry + ex;
-    __syncthreads();
-    if (threadIdx.x == 0) s_carry += tot;
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long run = 0ull;
+    for (int k = 0; k < NW; ++k) {
+      const unsigned long long x = s_wt[k];
+      s_wt[k] = run;
+      run += x;
+    }
+    s_wt[NW] = run;
   }
-  const long long t = (long long)s_carry;
   __syncthreads();
-  return t;
+  unsigned long long carry = s_wt[w];
+  const long long total = (long long)s_wt[NW];
+#pragma unroll 4
+  for (int b = b0; b < b1; b += 32) {  // (warp-uniform)
+    const int i = b + lane;
+    const unsigned long long x = i < b1 ? __ldcg(block_sums + i) : 0ull;
+    const unsigned long long incl = warp_incl_scan(x);
+    if (i < b1) block_sums[i] = carry + incl - x;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  __syncthreads();  // s_wt is read by every thread before a later call reuses it
+  return total;
 }
 
 
@@ -919,15 +940,30 @@ __global__ void __launch_bounds__(1024) st_segments_kernel(uint2* __restrict__ s
   if (totals) {
     // one radix pass sorted the items by super-tile (S <= 512): the per-digit
     // totals are the per-super-tile counts, and their exclusive scan the starts
-    __shared__ unsigned s_tot[kRadixBins];
-    if (tid < kRadixBins) s_tot[tid] = tid < S ? totals[tid] : 0u;
+    // (S <= 256: the first 8 warps, one block-level scan)
+    const unsigned tot = tid < S ? totals[tid] : 0u;
+    unsigned incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[w] = incl;
     __syncthreads();
-    if (tid == 0) {
-      unsigned run = 0u;
-      for (int t = 0; t < S; ++t) {
-        st_ranges[t] = make_uint2(s_tot[t] ? run : 0u, s_tot[t] ? run + s_tot[t] : 0u);
-        run += s_tot[t];
+    if (w == 0) {
+      const unsigned x = s_w[lane];
+      unsigned xi = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, xi, o);
+        if (lane >= o) xi += y;
       }
+      s_w[lane] = xi - x;
+    }
+    __syncthreads();
+    if (tid < S) {
+      const unsigned run = s_w[w] + incl - tot;
+      st_ranges[tid] = make_uint2(tot ? run : 0u, tot ? run + tot : 0u);
     }
   } else if (S == 1 && tid == 0) {  // no sort: one super-tile holds every item
     const unsigned q = (unsigned)*q_eff;
@@ -971,8 +1007,11 @@ __global__ void __launch_bounds__(1024) st_segments_kernel(uint2* __restrict__ s
     *n_seg = (long long)s_carry;
   }
   __syncthreads();
-  for (int s = tid; s < S; s += 1024)
-    for (unsigned g = seg_first[s]; g < seg_first[s + 1]; ++g) seg_st[g] = (unsigned)s;
+  // the super-tile of every segment: a warp per super-tile
+  for (int s = w; s < S; s += 32) {
+    const unsigned g0 = seg_first[s], g1 = seg_first[s + 1];
+    for (unsigned g = g0 + lane; g < g1; g += 32) seg_st[g] = (unsigned)s;
+  }
 }
 
 // Rows [b, e) of segment g of super-tile s, its view and tile origin.
@@ -1146,6 +1185,7 @@ __global__ void __launch_bounds__(1024) st_scan_kernel(const unsigned* __restric
   const unsigned per = (L + 15u) / 16u;
   const unsigned a = min(L, (unsigned)k * per), e = min(L, a + per);
   unsigned sum = 0u;
+#pragma unroll 4
   for (unsigned g = a; g < e; ++g) sum += hist[(long long)(g0 + g) * 64 + bt];
   s_part[k][bt] = sum;
   __syncthreads();
