@@ -7,7 +7,9 @@ are checked against the oracle elsewhere (test_parity_gpu.py), here only that
 unseen Gaussians get exact zeros, that SH coefficients past the degree in use
 get exact zeros, that repeated calls give the same gradients, and that the
 moment rows are zero when the backward starts whether the forward zeroed
-them beside its kernel or the backward zeroes them itself.
+them beside its kernel or the backward zeroes them itself.  The forward's
+zeroing of a caller's region (gs_launch.zero_beside) is exact at unaligned
+ends and leaves the forward's outputs unchanged.
 """
 import numpy as np
 import pytest
@@ -93,3 +95,32 @@ def test_grad2d_zeroed_beside_the_forward_or_by_the_backward():
         assert np.isfinite(outs[0][k]).all(), k
         assert np.abs(outs[0][k]).sum() > 0, k
         np.testing.assert_allclose(outs[1][k], outs[0][k], rtol=1e-5, atol=1e-7)
+
+
+@pytest.mark.parametrize("off,size", [(3, 1001), (16, 4096), (5, 7), (0, 100_003)])
+def test_forward_zeroes_an_unaligned_region_exactly(off, size):
+    # gs_launch.zero_beside: the forward kernel's CTAs zero the region's
+    # 16-byte-aligned body and memsets its ragged ends; the bytes around it
+    # stay as they were and the forward's outputs do not change
+    import torch
+    from paper_2603_09277_gb300 import gs
+    from paper_2603_09277_gb300.rasterize import Rasterizer, scene_to_device
+    n = 3000
+    scene = scenes.box_scene(n, seed=13)
+    cams = scenes.yaw_cameras([(96, 64), (64, 80)], [0.0, 5.0])
+    r = Rasterizer(cams, scenes.params(), n)
+    r.preprocess(scene_to_device(scene))
+    r.bin_sort()
+    gs.gs_render_fwd(r.proj_c, r.N, r.cams_c, r.prm_c, r.sorted_vals, r.tile_ranges, r.image,
+                     r.final_T, r.last_idx, r.entropy, gs.make_launch())
+    ref = (r.image.clone(), r.final_T.clone(), r.last_idx.clone(), r.entropy.clone())
+    buf = torch.full((off + size + 64,), 0xAB, dtype=torch.uint8, device="cuda")
+    region = buf[off:off + size]
+    gs.gs_render_fwd(r.proj_c, r.N, r.cams_c, r.prm_c, r.sorted_vals, r.tile_ranges, r.image,
+                     r.final_T, r.last_idx, r.entropy, gs.make_launch(zero_beside=region))
+    torch.cuda.synchronize()
+    b = buf.cpu().numpy()
+    assert (b[off:off + size] == 0).all()
+    assert (b[:off] == 0xAB).all() and (b[off + size:] == 0xAB).all()
+    for got, want in zip((r.image, r.final_T, r.last_idx, r.entropy), ref):
+        assert torch.equal(got, want)
