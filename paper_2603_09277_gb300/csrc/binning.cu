@@ -1185,7 +1185,6 @@ __global__ void __launch_bounds__(1024) st_scan_kernel(const unsigned* __restric
   const unsigned per = (L + 15u) / 16u;
   const unsigned a = min(L, (unsigned)k * per), e = min(L, a + per);
   unsigned sum = 0u;
-#pragma unroll 4
   for (unsigned g = a; g < e; ++g) sum += hist[(long long)(g0 + g) * 64 + bt];
   s_part[k][bt] = sum;
   __syncthreads();
