@@ -85,6 +85,21 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
   return r;
 }
 
+// The block's total of x (256 threads), in every thread.
+__device__ __forceinline__ unsigned long long block_sum(unsigned long long x) {
+  __shared__ unsigned long long s_ws[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if (lane == 0) s_ws[w] = x;
+  __syncthreads();
+  unsigned long long t = 0ull;
+#pragma unroll
+  for (int k = 0; k < kScanThreads / 32; ++k) t += s_ws[k];
+  __syncthreads();  // s_ws is read by every thread before a later call reuses it
+  return t;
+}
+
 // Value source for the scans: either tiles_touched[i] (or its gather through
 // an index array) or a visibility flag.
 struct ScanSrc {
@@ -134,8 +149,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(ScanSrc src, 
     long long i = base + (long long)k * kScanThreads + threadIdx.x;
     if (i < n) s += src.get(i);
   }
-  unsigned long long tot;
-  block_excl_scan(s, &tot);
+  const unsigned long long tot = block_sum(s);
   if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
   if (arrive && last_block_arrives(arrive, gridDim.x)) {
     const long long t = scan_blocks_dev(block_sums, (int)gridDim.x);
@@ -436,9 +450,7 @@ __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
       }
     }
   }
-  unsigned long long tq, tp;
-  block_excl_scan(q, &tq);
-  block_excl_scan(pp, &tp);
+  const unsigned long long tq = block_sum(q), tp = block_sum(pp);
   if (threadIdx.x == 0) {
     sums_q[blockIdx.x] = tq;
     sums_p[blockIdx.x] = tp;

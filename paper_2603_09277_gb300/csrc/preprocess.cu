@@ -305,19 +305,11 @@ struct Projected {
 // Cholesky factor of Sigma' + dilation I and its determinant are formed from
 // N directly (rows n0, n1): det = |n0 x n1|^2 + d (|n0|^2 + |n1|^2) + d^2,
 // which avoids squaring the condition number of Sigma'.
-__device__ __forceinline__ Projected project(const CamInfo& c, const Activated& a, float depth,
-                                             float dilation) {
-  Projected p;
-  const float* m = a.mean;
-  F2 tx = dot3_plus(c.R[0], c.R[1], c.R[2], m, c.t[0]);
-  F2 ty = dot3_plus(c.R[3], c.R[4], c.R[5], m, c.t[1]);
-  F2 tz = {depth, 0.f};
-  p.tx = tx.hi;
-  p.ty = ty.hi;
-  p.tz = depth;
-  F2 ux = div2(tx, tz), uy = div2(ty, tz);
-  p.ux = ux.hi;
-  p.uy = uy.hi;
+// From the camera-space position (p.tz, p.ux = tx / tz, p.uy = ty / tz): the
+// clamped EWA Jacobian, Sigma' + dilation I, its Cholesky factor and the
+// conic.  Shared by the projection and its adjoint.
+__device__ __forceinline__ void project_tail(const CamInfo& c, const Activated& a, float dilation,
+                                             Projected& p) {
   float itz = 1.f / p.tz;
   p.clx = p.ux < -c.limx || p.ux > c.limx;
   p.cly = p.uy < -c.limy || p.uy > c.limy;
@@ -362,8 +354,57 @@ __device__ __forceinline__ Projected project(const CamInfo& c, const Activated& 
   p.ca = i11 * i11 + i21 * i21;
   p.cb = i21 * i22;
   p.cc = i22 * i22;
+}
+
+__device__ __forceinline__ Projected project(const CamInfo& c, const Activated& a, float depth,
+                                             float dilation) {
+  Projected p;
+  const float* m = a.mean;
+  F2 tx = dot3_plus(c.R[0], c.R[1], c.R[2], m, c.t[0]);
+  F2 ty = dot3_plus(c.R[3], c.R[4], c.R[5], m, c.t[1]);
+  F2 tz = {depth, 0.f};
+  p.tx = tx.hi;
+  p.ty = ty.hi;
+  p.tz = depth;
+  F2 ux = div2(tx, tz), uy = div2(ty, tz);
+  p.ux = ux.hi;
+  p.uy = uy.hi;
+  project_tail(c, a, dilation, p);
   p.mx = affine2(c.fx, ux, c.cx);
   p.my = affine2(c.fy, uy, c.cy);
+  return p;
+}
+
+// The exact projection as a call of its own, for the adjoint's rare fallback
+// (inlined a second time it would raise the adjoint's register pressure).
+__device__ __noinline__ Projected project_exact(const CamInfo& c, const Activated& a,
+                                                float dilation) {
+  return project(c, a, depth_of(c, a.mean), dilation);
+}
+
+// The projection as its adjoint needs it: camera-space position and its
+// ratios in plain FP32 (the adjoint's gradients are compared at 1e-4, the
+// exact depth key and double-float mean serve the forward's list order and
+// tile-relative means).  The one decision that must match the forward's, the
+// Jacobian clamp of x/z and y/z, is taken from the exact projection whenever
+// a ratio lies within 1e-5 (relative) of its limit.
+__device__ __forceinline__ Projected project_adjoint(const CamInfo& c, const Activated& a,
+                                                     float dilation) {
+  const float* m = a.mean;
+  const float tx = __fmaf_rn(c.R[2], m[2], __fmaf_rn(c.R[1], m[1], __fmaf_rn(c.R[0], m[0], c.t[0])));
+  const float ty = __fmaf_rn(c.R[5], m[2], __fmaf_rn(c.R[4], m[1], __fmaf_rn(c.R[3], m[0], c.t[1])));
+  const float tz = __fmaf_rn(c.R[8], m[2], __fmaf_rn(c.R[7], m[1], __fmaf_rn(c.R[6], m[0], c.t[2])));
+  const float itz = __frcp_rn(tz);
+  const float ux = tx * itz, uy = ty * itz;
+  if (fabsf(fabsf(ux) - c.limx) <= 1e-5f * c.limx || fabsf(fabsf(uy) - c.limy) <= 1e-5f * c.limy)
+    return project_exact(c, a, dilation);
+  Projected p;
+  p.tx = tx;
+  p.ty = ty;
+  p.tz = tz;
+  p.ux = ux;
+  p.uy = uy;
+  project_tail(c, a, dilation, p);
   return p;
 }
 
@@ -563,8 +604,9 @@ __device__ __forceinline__ void adjoint_view(
     float4 G0 = G4[0], G1 = G4[1], G2 = G4[2];
     // G0 = (Sx, Sy, Sxx, Sxy), G1 = (Syy, S1, r, g), G2 = (b, pad, pad, pad)
     const CamInfo& c = ct.c[v];
-    float depth = depth_of(c, a.mean);
-    Projected p = project(c, a, depth, dilation);
+    // (degree 3 keeps the exact projection: the FP32 head with its fallback
+    // spills there, 31 -> 33 us on a 1M-Gaussian view)
+    Projected p = DEG < 3 ? project_adjoint(c, a, dilation) : project(c, a, depth_of(c, a.mean), dilation);
 
     gsig += G1.y;  // sum dd; dL/dlogit = (sum dd / sigma) sigma (1 - sigma)
     const float gmx = p.ca * G0.x + p.cb * G0.y;  // dL/dmean2d = K (Sx, Sy)
