@@ -298,6 +298,7 @@ struct Projected {
   float det;           // det(Sigma' + dilation I)
   float ca, cb, cc;    // conic
   float f11, f21, f22; // sqrt(log2(e)/2) L^-1 with L L^T = Sigma' + dilation I
+  float l21, i11, i22; // L = [[l11, 0], [l21, l22]] and 1 / l11, 1 / l22
   F2 mx, my;           // 2D mean (double-float)
 };
 
@@ -351,6 +352,9 @@ __device__ __forceinline__ void project_tail(const CamInfo& c, const Activated& 
   p.f21 = -kc * l21 / (l11 * l22);
   // conic = L^-T L^-1
   const float i11 = 1.f / l11, i22 = 1.f / l22, i21 = -l21 / (l11 * l22);
+  p.l21 = l21;
+  p.i11 = i11;
+  p.i22 = i22;
   p.ca = i11 * i11 + i21 * i21;
   p.cb = i21 * i22;
   p.cc = i22 * i22;
@@ -677,10 +681,8 @@ __device__ __forceinline__ void adjoint_view(
     // Every factor is scaled by L^-1, so the condition number of Sigma' is
     // not squared as it would be through dL/dSigma' = -K Gk K.
     const float* T = p.T;
-    const float l11 = sqrtf(p.A);
-    const float l21 = p.B / l11;
-    const float l22 = sqrtf(p.det) / l11;
-    const float i11 = 1.f / l11, i22 = 1.f / l22;
+    // the projection's Cholesky factor of Sigma' + dilation I
+    const float l21 = p.l21, i11 = p.i11, i22 = p.i22;
     const float i21 = -l21 * i11 * i22;
     float Th[6];
     for (int j = 0; j < 3; ++j) {
