@@ -299,6 +299,7 @@ struct Projected {
   float ca, cb, cc;    // conic
   float f11, f21, f22; // sqrt(log2(e)/2) L^-1 with L L^T = Sigma' + dilation I
   float l21, i11, i22; // L = [[l11, 0], [l21, l22]] and 1 / l11, 1 / l22
+  float itz;           // 1 / tz
   F2 mx, my;           // 2D mean (double-float)
 };
 
@@ -308,10 +309,15 @@ struct Projected {
 // which avoids squaring the condition number of Sigma'.
 // From the camera-space position (p.tz, p.ux = tx / tz, p.uy = ty / tz): the
 // clamped EWA Jacobian, Sigma' + dilation I, its Cholesky factor and the
-// conic.  Shared by the projection and its adjoint.
+// conic.  Shared by the projection and its adjoint; ADJ: the adjoint's form,
+// which takes one correctly rounded reciprocal per Cholesky diagonal and
+// multiplies where the projection divides (its records keep the division
+// forms bit for bit).
+template <bool ADJ = false>
 __device__ __forceinline__ void project_tail(const CamInfo& c, const Activated& a, float dilation,
                                              Projected& p) {
-  float itz = 1.f / p.tz;
+  float itz = ADJ ? __frcp_rn(p.tz) : 1.f / p.tz;
+  p.itz = itz;
   p.clx = p.ux < -c.limx || p.ux > c.limx;
   p.cly = p.uy < -c.limy || p.uy > c.limy;
   float uxc = fminf(fmaxf(p.ux, -c.limx), c.limx);
@@ -344,6 +350,19 @@ __device__ __forceinline__ void project_tail(const CamInfo& c, const Activated& 
   p.ok = p.det > 0.f && p.A > 0.f;
   // L = [[l11, 0], [l21, l22]], L L^T = [[A, B], [B, C]]
   const float l11 = sqrtf(p.A);
+  if constexpr (ADJ) {
+    const float i11 = __frcp_rn(l11);
+    const float l21 = p.B * i11;
+    const float i22 = __frcp_rn(sqrtf(p.det) * i11);
+    const float i21 = -l21 * i11 * i22;
+    p.l21 = l21;
+    p.i11 = i11;
+    p.i22 = i22;
+    p.ca = i11 * i11 + i21 * i21;
+    p.cb = i21 * i22;
+    p.cc = i22 * i22;
+    return;
+  }
   const float l21 = p.B / l11;
   const float l22 = sqrtf(p.det) / l11;
   const float kc = 0.8493218002880191f;  // sqrt(log2(e) / 2)
@@ -408,7 +427,7 @@ __device__ __forceinline__ Projected project_adjoint(const CamInfo& c, const Act
   p.tz = tz;
   p.ux = ux;
   p.uy = uy;
-  project_tail(c, a, dilation, p);
+  project_tail<true>(c, a, dilation, p);
   return p;
 }
 
@@ -727,7 +746,7 @@ __device__ __forceinline__ void adjoint_view(
     float gJ11 = gT[3] * c.R[3] + gT[4] * c.R[4] + gT[5] * c.R[5];
     float gJ12 = gT[3] * c.R[6] + gT[4] * c.R[7] + gT[5] * c.R[8];
     // --- J(t) and the 2D mean(t)
-    float itz = 1.f / p.tz;
+    const float itz = p.itz;
     float gtx = 0.f, gty = 0.f, gtz = 0.f;
     gtz += -gJ00 * c.fx * itz * itz - gJ11 * c.fy * itz * itz;
     if (p.clx) {
