@@ -349,11 +349,11 @@ __device__ __forceinline__ void project_tail(const CamInfo& c, const Activated& 
   p.det = (cx0 * cx0 + cx1 * cx1 + cx2 * cx2) + dilation * (s00 + s11) + dilation * dilation;
   p.ok = p.det > 0.f && p.A > 0.f;
   // L = [[l11, 0], [l21, l22]], L L^T = [[A, B], [B, C]]
-  const float l11 = sqrtf(p.A);
   if constexpr (ADJ) {
-    const float i11 = __frcp_rn(l11);
+    // 1 / l11 = A^-1/2 and 1 / l22 = l11 / sqrt(det) = A det^-1/2 A^-1/2
+    const float i11 = rsqrtf(p.A);
     const float l21 = p.B * i11;
-    const float i22 = __frcp_rn(sqrtf(p.det) * i11);
+    const float i22 = rsqrtf(p.det) * (p.A * i11);
     const float i21 = -l21 * i11 * i22;
     p.l21 = l21;
     p.i11 = i11;
@@ -363,6 +363,7 @@ __device__ __forceinline__ void project_tail(const CamInfo& c, const Activated& 
     p.cc = i22 * i22;
     return;
   }
+  const float l11 = sqrtf(p.A);
   const float l21 = p.B / l11;
   const float l22 = sqrtf(p.det) / l11;
   const float kc = 0.8493218002880191f;  // sqrt(log2(e) / 2)
