@@ -310,13 +310,11 @@ struct Projected {
 // From the camera-space position (p.tz, p.ux = tx / tz, p.uy = ty / tz): the
 // clamped EWA Jacobian, Sigma' + dilation I, its Cholesky factor and the
 // conic.  Shared by the projection and its adjoint; ADJ: the adjoint's form,
-// which takes one correctly rounded reciprocal per Cholesky diagonal and
-// multiplies where the projection divides (its records keep the division
-// forms bit for bit).
+// with the inverse Cholesky diagonal from reciprocal square roots.
 template <bool ADJ = false>
 __device__ __forceinline__ void project_tail(const CamInfo& c, const Activated& a, float dilation,
                                              Projected& p) {
-  float itz = ADJ ? __frcp_rn(p.tz) : 1.f / p.tz;
+  const float itz = __frcp_rn(p.tz);  // (correctly rounded: the value of 1.f / tz)
   p.itz = itz;
   p.clx = p.ux < -c.limx || p.ux > c.limx;
   p.cly = p.uy < -c.limy || p.uy > c.limy;
@@ -363,15 +361,18 @@ __device__ __forceinline__ void project_tail(const CamInfo& c, const Activated& 
     p.cc = i22 * i22;
     return;
   }
+  // one correctly rounded reciprocal per diagonal entry, then products
   const float l11 = sqrtf(p.A);
-  const float l21 = p.B / l11;
-  const float l22 = sqrtf(p.det) / l11;
+  const float i11 = __frcp_rn(l11);
+  const float l21 = p.B * i11;
+  const float l22 = sqrtf(p.det) * i11;
+  const float i22 = __frcp_rn(l22);
+  const float i21 = -l21 * i11 * i22;
   const float kc = 0.8493218002880191f;  // sqrt(log2(e) / 2)
-  p.f11 = kc / l11;
-  p.f22 = kc / l22;
-  p.f21 = -kc * l21 / (l11 * l22);
+  p.f11 = kc * i11;
+  p.f22 = kc * i22;
+  p.f21 = kc * i21;
   // conic = L^-T L^-1
-  const float i11 = 1.f / l11, i22 = 1.f / l22, i21 = -l21 / (l11 * l22);
   p.l21 = l21;
   p.i11 = i11;
   p.i22 = i22;
