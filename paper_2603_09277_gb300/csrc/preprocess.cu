@@ -264,13 +264,16 @@ __device__ __forceinline__ float depth_of(const CamInfo& c, const float* m) {
   return sure ? z.hi : depth_fp64(c, m);
 }
 
-// (x.hi + x.lo) / (y.hi + y.lo) as a double-float.
-__device__ __forceinline__ F2 div2(F2 x, F2 y) {
-  float q = __fdiv_rn(x.hi, y.hi);
-  // x - q y, exactly for the hi parts
+// (x.hi + x.lo) / (y.hi + y.lo) as a double-float, with the correctly rounded
+// reciprocal iy = 1 / y.hi given: the quotient's high part is x.hi iy (within
+// about an ulp of x.hi / y.hi), the FMA remainder and the low part correct
+// it, so the double-float result keeps its accuracy; the two divisions by tz
+// share the reciprocal.
+__device__ __forceinline__ F2 div2_rcp(F2 x, F2 y, float iy) {
+  const float q = __fmul_rn(x.hi, iy);
   float r = __fmaf_rn(-q, y.hi, x.hi);
   r = __fadd_rn(r, __fsub_rn(x.lo, __fmul_rn(q, y.lo)));
-  return fast_two_sum(q, __fdiv_rn(r, y.hi));
+  return fast_two_sum(q, __fmul_rn(r, iy));
 }
 
 // f (u.hi + u.lo) + c as a double-float.
@@ -391,7 +394,8 @@ __device__ __forceinline__ Projected project(const CamInfo& c, const Activated& 
   p.tx = tx.hi;
   p.ty = ty.hi;
   p.tz = depth;
-  F2 ux = div2(tx, tz), uy = div2(ty, tz);
+  const float itz = __frcp_rn(depth);
+  F2 ux = div2_rcp(tx, tz, itz), uy = div2_rcp(ty, tz, itz);
   p.ux = ux.hi;
   p.uy = uy.hi;
   project_tail(c, a, dilation, p);
@@ -455,6 +459,15 @@ __global__ void __launch_bounds__(256, pre_ctas_per_sm<DEG>()) preprocess_kernel
   Activated a = activate(means, log_scales, quats, opacity_logits, g);
   constexpr int sh_deg = DEG;
   constexpr int K = (DEG + 1) * (DEG + 1);
+  // per Gaussian, not per view: log2 of the opacity and, at degree 0, the colour
+  const float L2S = log2f(a.sigma);
+  float col0[3] = {0.5f, 0.5f, 0.5f};
+  if constexpr (DEG == 0) {
+    float Y[16];
+    sh_basis(0, 0.f, 0.f, 1.f, Y);
+    for_sh_block(sh, g, sh_stride, K, sh_vectors(sh, sh_stride),
+                 [&](int e, float v) { col0[e % 3] += Y[e / 3] * v; });
+  }
   for (int v = 0; v < ct.V; ++v) {
     const CamInfo& c = ct.c[v];
     long long row = (long long)v * N + g;
@@ -490,14 +503,17 @@ __global__ void __launch_bounds__(256, pre_ctas_per_sm<DEG>()) preprocess_kernel
       if (out.radius) out.radius[row] = 0;
       continue;
     }
-    // SH colour at the direction from the camera centre to the mean
-    float vx = a.mean[0] - c.cp[0], vy = a.mean[1] - c.cp[1], vz = a.mean[2] - c.cp[2];
-    float il = rsqrtf(vx * vx + vy * vy + vz * vz);
-    float Y[16];
-    sh_basis(sh_deg, vx * il, vy * il, vz * il, Y);
-    float col[3] = {0.5f, 0.5f, 0.5f};
-    for_sh_block(sh, g, sh_stride, K, sh_vectors(sh, sh_stride),
-                 [&](int e, float v) { col[e % 3] += Y[e / 3] * v; });
+    // SH colour at the direction from the camera centre to the mean (at
+    // degree 0 it does not depend on the view: taken once per Gaussian)
+    float col[3] = {col0[0], col0[1], col0[2]};
+    if constexpr (DEG > 0) {
+      float vx = a.mean[0] - c.cp[0], vy = a.mean[1] - c.cp[1], vz = a.mean[2] - c.cp[2];
+      float il = rsqrtf(vx * vx + vy * vy + vz * vz);
+      float Y[16];
+      sh_basis(sh_deg, vx * il, vy * il, vz * il, Y);
+      for_sh_block(sh, g, sh_stride, K, sh_vectors(sh, sh_stride),
+                   [&](int e, float v) { col[e % 3] += Y[e / 3] * v; });
+    }
     float cr = col[0], cg = col[1], cbl = col[2];
     cr = fmaxf(cr, 0.f);
     cg = fmaxf(cg, 0.f);
@@ -512,7 +528,7 @@ __global__ void __launch_bounds__(256, pre_ctas_per_sm<DEG>()) preprocess_kernel
     s.f11 = p.f11;
     s.f21 = p.f21;
     s.f22 = p.f22;
-    s.L2S = log2f(a.sigma);
+    s.L2S = L2S;
     s.R = cr;
     s.G = cg;
     s.B = cbl;
