@@ -478,6 +478,7 @@ constexpr int kRadixTile = kRadixThreads * kRadixIpt;       // 2048
 constexpr int kRadixMaxBits = 8;
 constexpr int kRadixBins = 1 << kRadixMaxBits;              // 256
 constexpr int kRadixMaxPasses = (32 + kRadixMaxBits - 1) / kRadixMaxBits;  // 4
+static_assert(kRadixThreads == kRadixBins, "the scatter's threads own one digit each");
 
 struct RadixPlan {
   unsigned kmin;  // subtracted from every key
@@ -631,12 +632,12 @@ __global__ void __launch_bounds__(kRadixThreads, GS_RADIX_CTAS) radix_downsweep_
   const unsigned* __restrict__ offsets = a.hist;
   const unsigned* __restrict__ totals = a.digit_tot;
   const int shift = a.pass * pl.dbits;
-  const int dbits = pl.dbits;
   const bool wkeys = a.keys_last || a.pass + 1 < pl.passes;
   __shared__ unsigned s_wc[kRadixWarps][kRadixBins + 1];  // per-warp digit counters (+ dummy)
-  __shared__ unsigned s_base[kRadixBins];                 // running global offset per digit
-  __shared__ unsigned s_tot[kRadixBins];                  // tile count per digit
+  __shared__ unsigned s_pre[kRadixWarps][kRadixBins];     // per-warp start within the digit's run
   __shared__ unsigned s_off[kRadixBins];                  // tile-local start per digit
+  __shared__ unsigned s_gl[kRadixBins];                   // global minus tile-local start per digit
+  __shared__ unsigned s_ws[kRadixWarps];                  // warp totals of the digit scan
   __shared__ unsigned s_key[kRadixTile];
   __shared__ unsigned s_val[kRadixTile];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -658,16 +659,22 @@ __global__ void __launch_bounds__(kRadixThreads, GS_RADIX_CTAS) radix_downsweep_
       nv[i] = j < b1 ? vals_in[j] : 0u;
     }
   }
+  // thread d owns digit d (kRadixThreads == kRadixBins): its running global
+  // offset = exclusive scan of the digit totals + this CTA's offset
+  const int dd = threadIdx.x;
+  unsigned gbase;
   {
-    // digit base = exclusive scan of the digit totals (256 threads, one digit each)
-    const unsigned off = offsets[(long long)threadIdx.x * gridDim.x + blockIdx.x];
+    const unsigned off = offsets[(long long)dd * gridDim.x + blockIdx.x];
     unsigned long long tot;
-    unsigned long long db = block_excl_scan(totals[threadIdx.x], &tot);
-    s_base[threadIdx.x] = (unsigned)db + off;
+    gbase = (unsigned)block_excl_scan(totals[dd], &tot) + off;
   }
   for (int i = threadIdx.x; i < kRadixWarps * (kRadixBins + 1); i += kRadixThreads)
     (&s_wc[0][0])[i] = 0u;
   __syncthreads();
+  // Four barriers per tile.  The counters s_wc are read and cleared between
+  // the first two, so the next tile's ranking may start while this tile is
+  // still being written out; the next tile's first barrier orders that
+  // write-out before the shared tile and the offsets are overwritten.
   for (long long t0 = b0; t0 < b1; t0 += kRadixTile) {
     const int cnt = (int)min((long long)kRadixTile, b1 - t0);
     unsigned k[kRadixIpt], v[kRadixIpt], dg[kRadixIpt], loc[kRadixIpt];
@@ -692,40 +699,56 @@ __global__ void __launch_bounds__(kRadixThreads, GS_RADIX_CTAS) radix_downsweep_
       const bool valid = dg[i] < (unsigned)kRadixBins;
       const unsigned vm = __ballot_sync(0xffffffffu, valid);
       unsigned peers = valid ? vm : ~vm;
+      // (digit bits at or above the pass's width are zero in every lane:
+      // their ballots leave peers unchanged)
 #pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        if (b < dbits) {
-          const bool bit = (dg[i] >> b) & 1u;
-          const unsigned m = __ballot_sync(0xffffffffu, bit);
-          peers &= bit ? m : ~m;
-        }
+      for (int b = 0; b < kRadixMaxBits; ++b) {
+        const bool bit = (dg[i] >> b) & 1u;
+        const unsigned m = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? m : ~m;
       }
-      unsigned rank = __popc(peers & lt_mask);
-      unsigned base = s_wc[w][dg[i]];
+      const unsigned rank = __popc(peers & lt_mask);
+      const unsigned base = s_wc[w][dg[i]];
       __syncwarp();
       if (rank == 0) s_wc[w][dg[i]] = base + __popc(peers);
       __syncwarp();
       loc[i] = base + rank;
     }
     __syncthreads();
+    unsigned run = 0, inc;
     {
-      // per digit (one per thread): prefix over warps, tile count, tile-local start
-      const int d = threadIdx.x;
-      unsigned run = 0;
+      // digit dd: prefix over the warps (counters cleared for the next
+      // tile), then a 32-bit scan of the tile counts over the digits
+#pragma unroll
       for (int ww = 0; ww < kRadixWarps; ++ww) {
-        unsigned c = s_wc[ww][d];
-        s_wc[ww][d] = run;
+        const unsigned c = s_wc[ww][dd];
+        s_pre[ww][dd] = run;
+        s_wc[ww][dd] = 0u;
         run += c;
       }
-      s_tot[d] = run;
-      unsigned long long tt;
-      s_off[d] = (unsigned)block_excl_scan(run, &tt);
+      inc = run;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      if (lane == 31) s_ws[w] = inc;
+    }
+    __syncthreads();
+    {
+      unsigned wo = 0;
+#pragma unroll
+      for (int ww = 0; ww < kRadixWarps - 1; ++ww) wo += ww < w ? s_ws[ww] : 0u;
+      const unsigned off = wo + inc - run;
+      s_off[dd] = off;
+      s_gl[dd] = gbase - off;
+      gbase += run;
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kRadixIpt; ++i) {
       if (dg[i] < (unsigned)kRadixBins) {
-        const unsigned lp = s_off[dg[i]] + s_wc[w][dg[i]] + loc[i];
+        const unsigned lp = s_off[dg[i]] + s_pre[w][dg[i]] + loc[i];
         s_key[lp] = k[i];
         s_val[lp] = v[i];
       }
@@ -733,20 +756,11 @@ __global__ void __launch_bounds__(kRadixThreads, GS_RADIX_CTAS) radix_downsweep_
     __syncthreads();
     for (int i = threadIdx.x; i < cnt; i += kRadixThreads) {
       const unsigned kk = s_key[i];
-      const unsigned d = radix_digit(kk, pl, shift);
-      const unsigned pos = s_base[d] + (unsigned)i - s_off[d];
+      const unsigned pos = s_gl[radix_digit(kk, pl, shift)] + (unsigned)i;
       if (!GS_IN_BOUNDS(pos, n, 202)) continue;
       if (wkeys) keys_out[pos] = kk;
       vals_out[pos] = s_val[i];
     }
-    __syncthreads();
-    {
-      const int d = threadIdx.x;
-      s_base[d] += s_tot[d];
-      for (int ww = 0; ww < kRadixWarps; ++ww) s_wc[ww][d] = 0u;
-      if (d < kRadixWarps) s_wc[d][kRadixBins] = 0u;
-    }
-    __syncthreads();
   }
 }
 
