@@ -604,7 +604,11 @@ def super_tile_items(r, cams, tile):
     """Items (visible row x 8x8-tile super-tile its rect meets) of the list
     construction, from the projection's rects on the device."""
     import torch
-    rect = r.rect[:r.rows].long().view(r.V, r.N, 4)
+    if r.rect is None:  # the 8-bit packed rects x0 | y0 << 8 | x1 << 16 | y1 << 24
+        p8 = r.rect8[:r.rows].long() & 0xFFFFFFFF
+        rect = torch.stack([(p8 >> s) & 255 for s in (0, 8, 16, 24)], 1).view(r.V, r.N, 4)
+    else:
+        rect = r.rect[:r.rows].long().view(r.V, r.N, 4)
     tot = 0
     for v, c in enumerate(cams):
         TX = (c["width"] + tile - 1) // tile

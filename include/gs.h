@@ -90,7 +90,10 @@ typedef struct {
 typedef struct {
     void* records;           /* required: gs_record_bytes(attr_dtype) per row, 16-B aligned */
     float* depth;            /* required [V*N]: FP32 camera-space depth of every row */
-    int* rect;               /* required [V*N][4]: tile rect x0, y0, x1, y1 (half-open) */
+    int* rect;               /* [V*N][4]: tile rect x0, y0, x1, y1 (half-open); required
+                                unless rect8 is set and every view is at most 255 tiles wide and
+                                high, where NULL leaves it out (gs_bin_sort then reads rect8
+                                alone; the projection saves 16 bytes of writes per row) */
     unsigned* tiles_touched; /* required [V*N]: (x1-x0)(y1-y0), 0 when culled */
     int* radius;             /* optional [V*N]: ceil(3 sqrt(lambda_max)) px */
     float* mean2d;           /* optional [V*N][2] */
@@ -203,7 +206,9 @@ int gs_debug_bounds_status(unsigned* status, int clear);
  *   cams_host [V], prm host.  out: device buffers with V*N rows.
  * A Gaussian is culled (tiles_touched 0) when its FP32 depth (the FP32
  * rounding of the FP64 camera-space z) is <= near_z, its 2D covariance is
- * singular, a projected value is not finite, or its rect is empty. */
+ * singular, a projected value is not finite, or its rect is empty.
+ * GS_ERR_INVALID when out->rect is NULL and out->rect8 is NULL or a view is
+ * more than 255 tiles wide or high. */
 int gs_preprocess(const float* means, const float* log_scales, const float* quats,
                   const float* opacity_logits, const float* sh, int N,
                   const gs_camera* cams_host, int V, const gs_params* prm, const gs_proj* out,
@@ -215,7 +220,9 @@ int gs_preprocess(const float* means, const float* log_scales, const float* quat
  * (global tile, FP32 depth bits, g), i.e. the order of the 64-bit key
  * (tile << 32) | depth_bits with ties by Gaussian id; tile_ranges[2t],
  * tile_ranges[2t+1] = [start, end) of tile t in sorted_vals (0, 0 if empty).
- *   proj: output of gs_preprocess (depth, rect, tiles_touched are read).
+ *   proj: output of gs_preprocess (depth, tiles_touched and the rects are
+ *   read: rect8 when set and every view is at most 255 tiles wide and high,
+ *   else rect, which must then be set).
  *   tile_size: the tile side gs_preprocess used (prm->tile_size).
  *   workspace: device, >= gs_bin_sort_workspace_size(V*N, pair_capacity,
  *   total_tiles) bytes, 256-B aligned.

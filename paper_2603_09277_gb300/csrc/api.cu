@@ -197,9 +197,10 @@ bool params_ok(const gs_params* p) {
 }
 
 bool proj_ok(const gs_proj* p, bool need_records) {
-  if (!p || !p->depth || !p->rect || !p->tiles_touched) return false;
+  if (!p || !p->depth || !p->tiles_touched) return false;
+  if (!p->rect && !p->rect8) return false;
   if (need_records && (!p->records || !aligned(p->records, 16))) return false;
-  if (!aligned(p->rect, 16)) return false;
+  if (p->rect && !aligned(p->rect, 16)) return false;
   if (p->mean2d && !aligned(p->mean2d, 8)) return false;
   if (p->conic_opacity && !aligned(p->conic_opacity, 16)) return false;
   return true;
@@ -439,6 +440,8 @@ int gs_preprocess(const float* means, const float* log_scales, const float* quat
   if (!build_cam_table(cams, V, prm, prm->tile_size, &ct)) return invalid("cameras");
   if ((long long)N * V >= (1ll << 32)) return invalid("V*N must be < 2^32");
   if (!proj_ok(out, true)) return invalid("projection buffers (NULL or misaligned)");
+  if (!out->rect && !rect8_fits(ct))
+    return invalid("rect is required when a view is more than 255 tiles wide or high");
   if (N > 0 && (!means || !log_scales || !quats || !opacity_logits || !sh))
     return invalid("parameter pointers");
   if (N > 0 && !aligned(quats, 16)) return invalid("quats must be 16-byte aligned");
@@ -456,6 +459,9 @@ int gs_bin_sort(const gs_proj* proj, int N, const gs_camera* cams, int V, int ti
   if (tile_size != 0 && tile_size != 8 && tile_size != 16) return invalid("tile_size (8 or 16)");
   if (!build_cam_table(cams, V, nullptr, tile_size, &ct)) return invalid("cameras");
   if (!proj_ok(proj, false)) return invalid("projection buffers");
+  if (!proj->rect && !(proj->rect8 && rect8_fits(ct)))
+    return invalid("rect is required unless rect8 is set and every view is at most 255 tiles "
+                   "wide and high");
   if (pair_capacity < 0 || pair_capacity >= (1ll << 32)) return invalid("pair_capacity");
   if (!tile_ranges || !num_pairs_dev || !status_dev) return invalid("output pointers");
   if (pair_capacity > 0 && !sorted_vals) return invalid("sorted_vals");

@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(256, pre_ctas_per_sm<DEG>()) preprocess_kernel
       vis = (x1 > x0) && (y1 > y0) && isfinite(r);
     }
     if (!vis) {
-      reinterpret_cast<int4*>(out.rect)[row] = make_int4(0, 0, 0, 0);
+      if (out.rect) reinterpret_cast<int4*>(out.rect)[row] = make_int4(0, 0, 0, 0);
       out.tiles_touched[row] = 0u;
       if (out.radius) out.radius[row] = 0;
       continue;
@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(256, pre_ctas_per_sm<DEG>()) preprocess_kernel
     s.B = cbl;
     s.sigma = a.sigma;
     store_record<DT>(out.records, row, s);
-    reinterpret_cast<int4*>(out.rect)[row] = make_int4(x0, y0, x1, y1);
+    if (out.rect) reinterpret_cast<int4*>(out.rect)[row] = make_int4(x0, y0, x1, y1);
     if (out.rect8)  // (views of at most 255 tiles per side)
       out.rect8[row] =
           (unsigned)x0 | ((unsigned)y0 << 8) | ((unsigned)x1 << 16) | ((unsigned)y1 << 24);

@@ -67,9 +67,15 @@ class Rasterizer:
         R = max(self.rows, 1)
         self.records = torch.empty(R * rb, dtype=torch.uint8, device=dev)
         self.depth = torch.empty(R, **f32)
-        self.rect = torch.empty(R, 4, **i32)
         self.tiles_touched = torch.empty(R, **i32)
         self.rect8 = torch.empty(R, **i32)  # rects packed in 8-bit fields (small views)
+        # with every view at most 255 tiles per side the packed rects carry
+        # the list construction and the int4 rects are left out (16 bytes of
+        # projection writes per row), unless the debug outputs are kept
+        self.rect8_only = not keep_debug and all(
+            -(-c["width"] // self.tile) <= 255 and -(-c["height"] // self.tile) <= 255
+            for c in cams)
+        self.rect = None if self.rect8_only else torch.empty(R, 4, **i32)
         self.keep_debug = keep_debug
         if keep_debug:
             self.radius = torch.empty(R, **i32)

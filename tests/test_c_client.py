@@ -70,6 +70,24 @@ int main(void) {
                      (float*)fake, (float*)fake, (unsigned*)fake, (float*)fake, &opt, NULL);
   printf("fwd %%d %%s\n", st, gs_last_error_string());
   printf("version %%s\n", gs_version());
+
+  /* the int4 rects may be left out only where the packed rects carry them */
+  const float* ff = (const float*)fake;
+  prm.attr_dtype = GS_ATTR_F32;
+  proj.rect = NULL;
+  proj.rect8 = NULL;
+  st = gs_preprocess(ff, ff, ff, ff, ff, 10, c, 2, &prm, &proj, NULL);
+  printf("norect %%d %%s\n", st, gs_last_error_string());
+  gs_camera wide;
+  camera(&wide, 16 * 300, 48, 1000.f);  /* 300 tiles wide */
+  proj.rect8 = (unsigned*)fake;
+  st = gs_preprocess(ff, ff, ff, ff, ff, 10, &wide, 1, &prm, &proj, NULL);
+  printf("norect %%d %%s\n", st, gs_last_error_string());
+  long long np = 0;
+  int status = 0;
+  st = gs_bin_sort(&proj, 10, &wide, 1, 16, fake, 1u << 30, 100, (unsigned*)fake, NULL,
+                   (unsigned*)fake, &np, NULL, &status, NULL);
+  printf("norect %%d %%s\n", st, gs_last_error_string());
   return 0;
 }
 """
@@ -100,6 +118,9 @@ def test_c11_program_links_and_calls_the_abi(lib_path, tmp_path):  # noqa: F811
     assert out[5].startswith("fwd -1 ") and "pixels_per_thread" in out[5]
     assert out[6].startswith("fwd -1 ") and "F32 records" in out[6]
     assert out[7].startswith("version ") and "sm_103a" in out[7]
+    assert out[8].startswith("norect -1 ") and "projection buffers" in out[8]
+    assert out[9].startswith("norect -1 ") and "255 tiles" in out[9]
+    assert out[10].startswith("norect -1 ") and "255 tiles" in out[10]
 
 
 def test_binding_structs_match_the_header_layout(tmp_path):

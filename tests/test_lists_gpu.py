@@ -110,3 +110,32 @@ def test_lists_rect_packing_limits(width):
     cams = [scenes.camera(width, 48, float(width) / 2.0)]
     P, total, flagged = _compare_lists(scene, cams, scenes.params())
     assert P > 5_000 and (flagged or P == total)
+
+
+@pytest.mark.parametrize("sizes", [[(4080, 48)], [(309, 205), (618, 411), (1237, 822)],
+                                   [(4200, 48)]])
+def test_lists_and_images_from_the_packed_rects_alone(sizes):
+    # with every view at most 255 tiles per side the projection leaves the
+    # int4 rects out (rect NULL) and the lists come from the packed rects
+    # alone: lists, ranges and the forward's outputs equal those of the
+    # call that writes both, bit for bit; a wider view keeps the int4 rects
+    from paper_2603_09277_gb300.rasterize import Rasterizer, scene_to_device
+    scene = scenes.box_scene(8_000, seed=12, ls_mean=-3.0, ls_std=0.8)
+    cams = [scenes.camera(w, h, float(w)) for w, h in sizes]
+    fits = all(-(-w // 16) <= 255 and -(-h // 16) <= 255 for w, h in sizes)
+    p = scene_to_device(scene)
+    out = []
+    for debug in (False, True):
+        r = Rasterizer(cams, scenes.params(), scene["means"].shape[0], keep_debug=debug)
+        assert r.rect8_only == (fits and not debug) and (r.rect is None) == r.rect8_only
+        r.preprocess(p)
+        P = r.bin_sort(keys=True)
+        r.render_fwd()
+        torch.cuda.synchronize()
+        out.append({"P": P, "vals": r.sorted_vals[:P].cpu(), "keys": r.sorted_keys[:P].cpu(),
+                    "ranges": r.tile_ranges.cpu(), "image": r.image.cpu(),
+                    "T": r.final_T.cpu(), "last": r.last_idx.cpu(), "H": r.entropy.cpu()})
+    a, b = out
+    assert a["P"] == b["P"] > 1_000
+    for k in ("vals", "keys", "ranges", "image", "T", "last", "H"):
+        assert torch.equal(a[k], b[k]), k
