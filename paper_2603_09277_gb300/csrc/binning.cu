@@ -100,18 +100,6 @@ __device__ __forceinline__ unsigned long long block_sum(unsigned long long x) {
   return t;
 }
 
-// Value source for the scans: either tiles_touched[i] (or its gather through
-// an index array) or a visibility flag.
-struct ScanSrc {
-  const unsigned* vals;   // values
-  const unsigned* index;  // optional gather index (vals[index[i]])
-  int flag;               // 1: use (value > 0) instead of the value
-  __device__ __forceinline__ unsigned get(long long i) const {
-    unsigned v = index ? vals[index[i]] : vals[i];
-    return flag ? (v > 0u ? 1u : 0u) : v;
-  }
-};
-
 // A CTA's arrival at the end of a kernel whose last CTA goes on to a step
 // over every CTA's results (a scan of the block sums, say), in place of a
 // separate single-CTA launch.  Each CTA makes its results visible
@@ -133,31 +121,7 @@ __device__ __forceinline__ bool last_block_arrives(unsigned long long* counter,
 
 __device__ __forceinline__ long long scan_blocks_dev(unsigned long long* block_sums, int nblocks);
 
-// Phase 1: per-block sums; with `arrive`, the last CTA also scans them
-// (phase 2) and writes the grand total to *total.
-template <int ITEMS>
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(ScanSrc src, const long long* n_dev,
-                                                                   long long n_host,
-                                                                   unsigned long long* block_sums,
-                                                                   unsigned long long* arrive,
-                                                                   long long* total) {
-  long long n = n_dev ? *n_dev : n_host;
-  long long base = (long long)blockIdx.x * (kScanThreads * ITEMS);
-  unsigned long long s = 0;
-#pragma unroll
-  for (int k = 0; k < ITEMS; ++k) {
-    long long i = base + (long long)k * kScanThreads + threadIdx.x;
-    if (i < n) s += src.get(i);
-  }
-  const unsigned long long tot = block_sum(s);
-  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
-  if (arrive && last_block_arrives(arrive, gridDim.x)) {
-    const long long t = scan_blocks_dev(block_sums, (int)gridDim.x);
-    if (threadIdx.x == 0) *total = t;
-  }
-}
-
-// Phase 2: exclusive scan of the block sums in one block (in place); returns
+// Exclusive scan of the block sums in one block (in place); returns
 // the grand total.  Each warp takes a contiguous chunk of the sums: its total
 // (a lane's loads in flight together), one scan of the warp totals, then the
 // chunk again with the warp's running offset -- no block-wide barrier per
@@ -238,91 +202,6 @@ __device__ __forceinline__ void scan_counts_check_dev(const CountsOut& o, int nb
   }
 }
 
-// Phase 3 (compaction form): rows with tiles_touched > 0 are written, in
-// order, as (depth bits, row) to keys/vals.  Item i = base + k * 256 + tid
-// (coalesced loads); the visible items of each (k, warp) are ranked by a
-// ballot, and the (k, warp) counts are scanned by one warp, so the output
-// order is the row order.
-constexpr int kScanWarps = kScanThreads / 32;
-template <int ITEMS>
-__global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
-    const unsigned* __restrict__ tiles_touched, const float* __restrict__ depth, long long n,
-    const unsigned long long* __restrict__ block_offsets, unsigned* __restrict__ keys,
-    unsigned* __restrict__ vals, unsigned* __restrict__ range) {
-  __shared__ unsigned s_off[ITEMS * kScanWarps];
-  __shared__ unsigned s_kmin[kScanWarps], s_kmax[kScanWarps];
-  const long long base = (long long)blockIdx.x * (kScanThreads * ITEMS);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned ball[ITEMS];
-  unsigned kmin = 0xffffffffu, kmax = 0u;  // range of the visible rows' depth bits
-#pragma unroll
-  for (int k = 0; k < ITEMS; ++k) {
-    const long long i = base + (long long)k * kScanThreads + threadIdx.x;
-    const bool vis = i < n && tiles_touched[i] > 0u;
-    ball[k] = __ballot_sync(0xffffffffu, vis);
-    if (lane == 0) s_off[k * kScanWarps + w] = __popc(ball[k]);
-    if (vis) {  // depth > near_z > 0: the bits order like the values
-      const unsigned kb = __float_as_uint(depth[i]);
-      kmin = min(kmin, kb);
-      kmax = max(kmax, kb);
-    }
-  }
-  kmin = __reduce_min_sync(0xffffffffu, kmin);
-  kmax = __reduce_max_sync(0xffffffffu, kmax);
-  if (lane == 0) {
-    s_kmin[w] = kmin;
-    s_kmax[w] = kmax;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int q = 1; q < kScanWarps; ++q) {
-      kmin = min(kmin, s_kmin[q]);
-      kmax = max(kmax, s_kmax[q]);
-    }
-    if (kmin <= kmax) {  // (folded in from zero: range[0] holds the complement)
-      atomicMax(range, ~kmin);
-      atomicMax(range + 1, kmax);
-    }
-  }
-  if (w == 0) {  // exclusive scan of the (k, warp) counts, kPerLane per lane
-    constexpr int kCounts = ITEMS * kScanWarps;
-    constexpr int kPerLane = (kCounts + 31) / 32;
-    static_assert(kCounts % kPerLane == 0 && kCounts / kPerLane <= 32, "one warp scans the counts");
-    unsigned c[kPerLane], run = 0;
-#pragma unroll
-    for (int j = 0; j < kPerLane; ++j) {
-      const int e = kPerLane * lane + j;
-      c[j] = e < kCounts ? s_off[e] : 0u;
-      run += c[j];
-    }
-    unsigned inc = run;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    unsigned ex = inc - run;
-#pragma unroll
-    for (int j = 0; j < kPerLane; ++j) {
-      const int e = kPerLane * lane + j;
-      if (e < kCounts) s_off[e] = ex;
-      ex += c[j];
-    }
-  }
-  __syncthreads();
-  const unsigned long long boff = block_offsets[blockIdx.x];
-  const unsigned below = (1u << lane) - 1u;
-#pragma unroll
-  for (int k = 0; k < ITEMS; ++k) {
-    if ((ball[k] >> lane) & 1u) {
-      const long long i = base + (long long)k * kScanThreads + threadIdx.x;
-      const unsigned long long off = boff + s_off[k * kScanWarps + w] + __popc(ball[k] & below);
-      if (!GS_IN_BOUNDS(off, n, 203)) continue;
-      keys[off] = __float_as_uint(depth[i]);
-      vals[off] = (unsigned)i;
-    }
-  }
-}
 
 // ----------------------------------------------------------------------------
 // Per visible row (depth order): its tile rect clamped to the view, the
@@ -463,13 +342,14 @@ __global__ void __launch_bounds__(kScanThreads) rows_gather_kernel(
 // reduce-then-scan with a fixed grid.  Each block owns a contiguous chunk of
 // whole 2048-item tiles; n is read from device memory.
 //
-// The keys may be sorted on their significant bits only: with a device-side
-// key range (the visible rows' smallest and largest depth bits, found during
-// the compaction) each pass sorts digits of (key - min); the number of passes
-// ceil(bits / 8) and the digit width ceil(bits / passes) follow from the
-// range on the device, and the kernels of passes beyond it return at once
-// (so the launch sequence, and a graph of it, is fixed).  The result is in
-// buffer (passes mod 2).
+// The depth sort reads the rows themselves in its first pass (RadixRows):
+// the visible rows' depth bits with their row ids, the culled rows dropped,
+// so no separate compaction runs.  That pass's upsweep folds in the visible
+// rows' key range (smallest and largest depth bits); the later passes sort
+// digits of (key - min) on the range's significant bits, their number and
+// width following from the range on the device (radix_plan).  The kernels of
+// passes beyond the plan return at once, so the launch sequence, and a graph
+// of it, is fixed.  The result is in buffer (passes mod 2).
 // ----------------------------------------------------------------------------
 constexpr int kRadixThreads = 256;
 constexpr int kRadixWarps = kRadixThreads / 32;
@@ -483,31 +363,72 @@ static_assert(kRadixThreads == kRadixBins, "the scatter's threads own one digit 
 struct RadixPlan {
   unsigned kmin;  // subtracted from every key
   int passes;
-  int dbits;      // digit width of every pass
+  int d0;         // digit width of the first pass
+  int dbits;      // digit width of the later passes
 };
 
-// bits: significant bits of (key - kmin).
+// bits: significant bits of (key - kmin), in digits of equal width.
 __host__ __device__ __forceinline__ RadixPlan radix_plan_bits(unsigned kmin, int bits) {
   RadixPlan p;
   p.kmin = kmin;
   p.passes = (bits + kRadixMaxBits - 1) / kRadixMaxBits;
   p.dbits = p.passes ? (bits + p.passes - 1) / p.passes : 0;
+  p.d0 = p.dbits;
   return p;
 }
 
 // range (device, nullable): [0] = ~(smallest key), [1] = largest key, both
 // folded in with atomicMax from zero (no key: range[0] = range[1] = 0, an
 // empty range).  Without a range every one of `bits` bits is sorted.
+//
+// With a range the first pass reads the rows themselves and runs before the
+// range is known (its upsweep folds the range in): its digit is the low byte
+// of the key.  The smallest key is therefore rounded down to a multiple of
+// 256, which leaves the low byte of (key - kmin) equal to that of the key;
+// the later passes take the remaining significant bits of (key - kmin) in
+// digits of equal width.  There is always at least the first pass.
 __device__ __forceinline__ RadixPlan radix_plan(const unsigned* __restrict__ range, int bits) {
   if (!range) return radix_plan_bits(0u, bits);
+  RadixPlan p;
+  p.kmin = 0u;
+  p.passes = 1;
+  p.d0 = kRadixMaxBits;
+  p.dbits = kRadixMaxBits;
   const unsigned kmin = ~__ldcg(range), kmax = __ldcg(range + 1);
-  if (kmax <= kmin) return radix_plan_bits(kmax < kmin ? 0u : kmin, 0);
-  return radix_plan_bits(kmin, 32 - __clz(kmax - kmin));
+  if (kmax > kmin) {
+    p.kmin = kmin & ~(unsigned)(kRadixBins - 1);
+    const int b = 32 - __clz(kmax - p.kmin);
+    if (b > p.d0) {
+      const int rest = (b - p.d0 + kRadixMaxBits - 1) / kRadixMaxBits;
+      p.passes = 1 + rest;
+      p.dbits = (b - p.d0 + rest - 1) / rest;
+    }
+  }
+  return p;
 }
 
-__device__ __forceinline__ unsigned radix_digit(unsigned key, const RadixPlan& p, int shift) {
-  return ((key - p.kmin) >> shift) & ((1u << p.dbits) - 1u);
+// Bit offset of a pass's digit in (key - kmin), and its mask.
+__device__ __forceinline__ int radix_shift(const RadixPlan& p, int pass) {
+  return pass == 0 ? 0 : p.d0 + (pass - 1) * p.dbits;
 }
+__device__ __forceinline__ unsigned radix_mask(const RadixPlan& p, int pass) {
+  return (1u << (pass == 0 ? p.d0 : p.dbits)) - 1u;
+}
+__device__ __forceinline__ unsigned radix_digit(unsigned key, const RadixPlan& p, int shift,
+                                                unsigned mask) {
+  return ((key - p.kmin) >> shift) & mask;
+}
+
+// Rows as the first pass's input (the depth sort): the key of row j is the
+// bits of depth[j], its value j, and only the rows with tiles_touched[j] > 0
+// take part (the visible rows: depth > near_z > 0, so the bits order like
+// the values).  The pass writes the visible rows' count to *n_vis.
+struct RadixRows {
+  const float* depth;
+  const unsigned* tiles_touched;
+  long long n;     // rows
+  long long* n_vis;
+};
 
 // Arguments of one pass.
 struct RadixPass {
@@ -515,13 +436,16 @@ struct RadixPass {
   const unsigned* vals_in;
   unsigned* keys_out;
   unsigned* vals_out;
-  const long long* n_dev;  // item count
+  const long long* n_dev;  // item count (the later passes with rows)
   const unsigned* range;   // device key range or nullptr
   int bits;                // significant bits without a range
-  int pass;                // pass index (shift = pass * digit width)
+  int pass;                // pass index
   unsigned* hist;          // [256][grid] per-CTA digit counts, then their scan
   unsigned* digit_tot;     // [256] items per digit
   int keys_last;           // write the keys in the last pass too
+  RadixRows rows;          // rows.depth set: the first pass reads the rows
+  __device__ __forceinline__ bool from_rows() const { return pass == 0 && rows.depth; }
+  __device__ __forceinline__ long long count() const { return from_rows() ? rows.n : *n_dev; }
 };
 
 __device__ __forceinline__ long long radix_chunk(long long n, int nblocks) {
@@ -537,48 +461,96 @@ __device__ __forceinline__ int radix_active(long long n, int nblocks) {
   return chunk > 0 ? (int)min((long long)nblocks, (n + chunk - 1) / chunk) : 0;
 }
 
+// Item j of a pass: key, value and whether it takes part.
+__device__ __forceinline__ void radix_load(const RadixPass& a, long long j, long long end,
+                                           unsigned& k, unsigned& v, bool& in) {
+  if (a.from_rows()) {
+    const unsigned t = j < end ? a.rows.tiles_touched[j] : 0u;
+    k = j < end ? __float_as_uint(a.rows.depth[j]) : 0u;
+    in = t > 0u;
+    v = (unsigned)j;
+  } else {
+    in = j < end;
+    k = in ? a.keys_in[j] : 0u;
+    v = in ? a.vals_in[j] : 0u;
+  }
+}
+
 __global__ void __launch_bounds__(kRadixThreads) radix_upsweep_kernel(const RadixPass a) {
-  const RadixPlan pl = radix_plan(a.range, a.bits);
-  if (a.pass >= pl.passes) return;  // (the whole grid)
-  const unsigned* __restrict__ keys = a.keys_in;
+  // the first pass over rows folds the key range in, so it cannot read the
+  // plan: its digit is the low byte of the key
+  const bool rows = a.from_rows();
+  RadixPlan pl;
+  if (rows) {
+    pl.kmin = 0u;
+    pl.passes = 1;
+    pl.d0 = pl.dbits = kRadixMaxBits;
+  } else {
+    pl = radix_plan(a.range, a.bits);
+    if (a.pass >= pl.passes) return;  // (the whole grid)
+  }
+  const int shift = radix_shift(pl, a.pass);
+  const unsigned mask = radix_mask(pl, a.pass);
   unsigned* __restrict__ hist = a.hist;  // [256][nblocks]
-  const int shift = a.pass * pl.dbits;
   __shared__ unsigned s_h[kRadixWarps][kRadixBins];
-  const int w = threadIdx.x >> 5;
-  long long n = *a.n_dev;
+  __shared__ unsigned s_kmin[kRadixWarps], s_kmax[kRadixWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long n = a.count();
   if ((int)blockIdx.x >= radix_active(n, gridDim.x)) return;  // (the whole CTA)
-  long long chunk = radix_chunk(n, gridDim.x);
-  long long b0 = (long long)blockIdx.x * chunk;
-  long long b1 = min(n, b0 + chunk);
+  const long long chunk = radix_chunk(n, gridDim.x);
+  const long long b0 = (long long)blockIdx.x * chunk;
+  const long long b1 = min(n, b0 + chunk);
   // kRadixIpt loads in flight per thread; the first tile's are requested
   // before the histogram is cleared
-  unsigned kk[kRadixIpt];
+  unsigned kk[kRadixIpt], unused;
+  bool in[kRadixIpt];
 #pragma unroll
-  for (int i = 0; i < kRadixIpt; ++i) {
-    const long long j = b0 + i * kRadixThreads + threadIdx.x;
-    kk[i] = j < b1 ? keys[j] : 0xffffffffu;
-  }
+  for (int i = 0; i < kRadixIpt; ++i)
+    radix_load(a, b0 + i * kRadixThreads + threadIdx.x, b1, kk[i], unused, in[i]);
   for (int i = threadIdx.x; i < kRadixWarps * kRadixBins; i += kRadixThreads)
     (&s_h[0][0])[i] = 0u;
   __syncthreads();
+  unsigned kmin = 0xffffffffu, kmax = 0u;  // (rows) range of the keys taking part
   for (long long t0 = b0; t0 < b1; t0 += kRadixTile) {
     if (t0 != b0) {
 #pragma unroll
-      for (int i = 0; i < kRadixIpt; ++i) {
-        const long long j = t0 + i * kRadixThreads + threadIdx.x;
-        kk[i] = j < b1 ? keys[j] : 0xffffffffu;
-      }
+      for (int i = 0; i < kRadixIpt; ++i)
+        radix_load(a, t0 + i * kRadixThreads + threadIdx.x, b1, kk[i], unused, in[i]);
     }
 #pragma unroll
-    for (int i = 0; i < kRadixIpt; ++i)
-      if (t0 + i * kRadixThreads + threadIdx.x < b1)
-        atomicAdd(&s_h[w][radix_digit(kk[i], pl, shift)], 1u);
+    for (int i = 0; i < kRadixIpt; ++i) {
+      if (in[i]) {
+        atomicAdd(&s_h[w][radix_digit(kk[i], pl, shift, mask)], 1u);
+        if (rows) {
+          kmin = min(kmin, kk[i]);
+          kmax = max(kmax, kk[i]);
+        }
+      }
+    }
+  }
+  if (rows) {
+    kmin = __reduce_min_sync(0xffffffffu, kmin);
+    kmax = __reduce_max_sync(0xffffffffu, kmax);
+    if (lane == 0) {
+      s_kmin[w] = kmin;
+      s_kmax[w] = kmax;
+    }
   }
   __syncthreads();
   for (int d = threadIdx.x; d < kRadixBins; d += kRadixThreads) {
     unsigned s = 0;
     for (int k = 0; k < kRadixWarps; ++k) s += s_h[k][d];
     hist[(long long)d * gridDim.x + blockIdx.x] = s;
+  }
+  if (rows && threadIdx.x == 0) {
+    for (int q = 1; q < kRadixWarps; ++q) {
+      kmin = min(kmin, s_kmin[q]);
+      kmax = max(kmax, s_kmax[q]);
+    }
+    if (kmin <= kmax) {  // (folded in from zero: range[0] holds the complement)
+      atomicMax(const_cast<unsigned*>(a.range), ~kmin);
+      atomicMax(const_cast<unsigned*>(a.range) + 1, kmax);
+    }
   }
 }
 
@@ -590,7 +562,7 @@ __global__ void __launch_bounds__(kScanThreads) radix_scan_kernel(const RadixPas
   if (a.pass >= pl.passes) return;
   unsigned* totals = a.digit_tot;
   unsigned* h = a.hist + (long long)blockIdx.x * G;
-  const int Ga = radix_active(*a.n_dev, G);
+  const int Ga = radix_active(a.count(), G);
   constexpr int kPer = 4;  // 256 threads x 4 >= 1024 blocks
   unsigned loc[kPer];
   unsigned long long s = 0;
@@ -624,40 +596,38 @@ __global__ void __launch_bounds__(kRadixThreads, GS_RADIX_CTAS) radix_downsweep_
     const RadixPass a) {
   const RadixPlan pl = radix_plan(a.range, a.bits);
   if (a.pass >= pl.passes) return;
-  const unsigned* __restrict__ keys_in = a.keys_in;
-  const unsigned* __restrict__ vals_in = a.vals_in;
   unsigned* __restrict__ keys_out = a.keys_out;
   unsigned* __restrict__ vals_out = a.vals_out;
-  const long long* __restrict__ n_dev = a.n_dev;
   const unsigned* __restrict__ offsets = a.hist;
   const unsigned* __restrict__ totals = a.digit_tot;
-  const int shift = a.pass * pl.dbits;
+  const int shift = radix_shift(pl, a.pass);
+  const unsigned mask = radix_mask(pl, a.pass);
   const bool wkeys = a.keys_last || a.pass + 1 < pl.passes;
   __shared__ unsigned s_wc[kRadixWarps][kRadixBins + 1];  // per-warp digit counters (+ dummy)
   __shared__ unsigned s_pre[kRadixWarps][kRadixBins];     // per-warp start within the digit's run
   __shared__ unsigned s_off[kRadixBins];                  // tile-local start per digit
   __shared__ unsigned s_gl[kRadixBins];                   // global minus tile-local start per digit
   __shared__ unsigned s_ws[kRadixWarps];                  // warp totals of the digit scan
+  __shared__ unsigned s_nt;                               // items of the tile taking part
   __shared__ unsigned s_key[kRadixTile];
   __shared__ unsigned s_val[kRadixTile];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
-  long long n = *n_dev;
+  const long long n = a.count();
   if ((int)blockIdx.x >= radix_active(n, gridDim.x)) return;  // (the whole CTA)
-  long long chunk = radix_chunk(n, gridDim.x);
-  long long b0 = (long long)blockIdx.x * chunk;
-  long long b1 = min(n, b0 + chunk);
+  const long long chunk = radix_chunk(n, gridDim.x);
+  const long long b0 = (long long)blockIdx.x * chunk;
+  const long long b1 = min(n, b0 + chunk);
   // the first tile's keys and values are requested before the digit bases
   // (independent loads, their latency overlaps the scan)
   unsigned nk[kRadixIpt], nv[kRadixIpt];
+  unsigned nin = 0u;  // bit i: item i takes part
   const int lbase = w * (32 * kRadixIpt) + lane;
-  if (b0 < b1) {
 #pragma unroll
-    for (int i = 0; i < kRadixIpt; ++i) {
-      const long long j = b0 + lbase + i * 32;
-      nk[i] = j < b1 ? keys_in[j] : 0u;
-      nv[i] = j < b1 ? vals_in[j] : 0u;
-    }
+  for (int i = 0; i < kRadixIpt; ++i) {
+    bool in;
+    radix_load(a, b0 + lbase + i * 32, b1, nk[i], nv[i], in);
+    nin |= (in ? 1u : 0u) << i;
   }
   // thread d owns digit d (kRadixThreads == kRadixBins): its running global
   // offset = exclusive scan of the digit totals + this CTA's offset
@@ -667,6 +637,8 @@ __global__ void __launch_bounds__(kRadixThreads, GS_RADIX_CTAS) radix_downsweep_
     const unsigned off = offsets[(long long)dd * gridDim.x + blockIdx.x];
     unsigned long long tot;
     gbase = (unsigned)block_excl_scan(totals[dd], &tot) + off;
+    // the first pass over rows reports the count of the rows taking part
+    if (a.from_rows() && blockIdx.x == 0 && threadIdx.x == 0) *a.rows.n_vis = (long long)tot;
   }
   for (int i = threadIdx.x; i < kRadixWarps * (kRadixBins + 1); i += kRadixThreads)
     (&s_wc[0][0])[i] = 0u;
@@ -676,21 +648,21 @@ __global__ void __launch_bounds__(kRadixThreads, GS_RADIX_CTAS) radix_downsweep_
   // still being written out; the next tile's first barrier orders that
   // write-out before the shared tile and the offsets are overwritten.
   for (long long t0 = b0; t0 < b1; t0 += kRadixTile) {
-    const int cnt = (int)min((long long)kRadixTile, b1 - t0);
     unsigned k[kRadixIpt], v[kRadixIpt], dg[kRadixIpt], loc[kRadixIpt];
 #pragma unroll
     for (int i = 0; i < kRadixIpt; ++i) {
       k[i] = nk[i];
       v[i] = nv[i];
-      dg[i] = lbase + i * 32 < cnt ? radix_digit(k[i], pl, shift) : (unsigned)kRadixBins;
+      dg[i] = (nin >> i) & 1u ? radix_digit(k[i], pl, shift, mask) : (unsigned)kRadixBins;
     }
     const long long t1 = t0 + kRadixTile;
     if (t1 < b1) {
+      nin = 0u;
 #pragma unroll
       for (int i = 0; i < kRadixIpt; ++i) {
-        const long long j = t1 + lbase + i * 32;
-        nk[i] = j < b1 ? keys_in[j] : 0u;
-        nv[i] = j < b1 ? vals_in[j] : 0u;
+        bool in;
+        radix_load(a, t1 + lbase + i * 32, b1, nk[i], nv[i], in);
+        nin |= (in ? 1u : 0u) << i;
       }
     }
 #pragma unroll
@@ -743,6 +715,7 @@ __global__ void __launch_bounds__(kRadixThreads, GS_RADIX_CTAS) radix_downsweep_
       s_off[dd] = off;
       s_gl[dd] = gbase - off;
       gbase += run;
+      if (dd == kRadixBins - 1) s_nt = off + run;
     }
     __syncthreads();
 #pragma unroll
@@ -754,9 +727,10 @@ __global__ void __launch_bounds__(kRadixThreads, GS_RADIX_CTAS) radix_downsweep_
       }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += kRadixThreads) {
+    const int nt = (int)s_nt;
+    for (int i = threadIdx.x; i < nt; i += kRadixThreads) {
       const unsigned kk = s_key[i];
-      const unsigned pos = s_gl[radix_digit(kk, pl, shift)] + (unsigned)i;
+      const unsigned pos = s_gl[radix_digit(kk, pl, shift, mask)] + (unsigned)i;
       if (!GS_IN_BOUNDS(pos, n, 202)) continue;
       if (wkeys) keys_out[pos] = kk;
       vals_out[pos] = s_val[i];
@@ -1477,7 +1451,7 @@ int radix_grid(long long n_bound) {
 
 void radix_sort(unsigned* k[2], unsigned* v[2], const long long* n_dev, long long n_bound,
                 const unsigned* range, int bits, unsigned* hist, bool keys_last,
-                cudaStream_t st) {
+                cudaStream_t st, const RadixRows* rows = nullptr) {
   if (n_bound == 0) return;
   const int passes = range ? kRadixMaxPasses : radix_plan_bits(0u, bits).passes;
   // one wave: at most the CTAs of the scatter kernel resident on the device
@@ -1489,6 +1463,7 @@ void radix_sort(unsigned* k[2], unsigned* v[2], const long long* n_dev, long lon
   a.hist = hist;
   a.digit_tot = hist + kRadixBins * grid;
   a.keys_last = keys_last ? 1 : 0;
+  a.rows = rows ? *rows : RadixRows{nullptr, nullptr, 0, nullptr};
   for (int p = 0; p < passes; ++p) {
     a.keys_in = k[p & 1];
     a.vals_in = v[p & 1];
@@ -1548,22 +1523,12 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
   const int items = small ? 4 : 16;
   const long long nb = (n_rows + kScanThreads * items - 1) / (kScanThreads * items);
   if (n_rows > 0) {
-    // 1. compaction of the visible rows, keyed by FP32 depth bits
-    ScanSrc vis{proj->tiles_touched, nullptr, 1};
-    if (small) {
-      scan_reduce_kernel<4><<<(unsigned)nb, kScanThreads, 0, st>>>(vis, nullptr, n_rows,
-                                                                   w.block_sums, arrive, n_vis);
-      compact_visible_kernel<4><<<(unsigned)nb, kScanThreads, 0, st>>>(
-          proj->tiles_touched, proj->depth, n_rows, w.block_sums, w.rk[0], w.rv[0], range);
-    } else {
-      scan_reduce_kernel<16><<<(unsigned)nb, kScanThreads, 0, st>>>(vis, nullptr, n_rows,
-                                                                    w.block_sums, arrive, n_vis);
-      compact_visible_kernel<16><<<(unsigned)nb, kScanThreads, 0, st>>>(
-          proj->tiles_touched, proj->depth, n_rows, w.block_sums, w.rk[0], w.rv[0], range);
-    }
-    // 2. stable depth sort of the visible rows (ties keep row order = id
-    //    order) on the significant bits of their depth range
-    radix_sort(w.rk, w.rv, n_vis, n_rows, range, 32, w.hist, false, st);
+    // 1-2. stable depth sort of the visible rows (ties keep row order = id
+    //    order) on the significant bits of their depth range; the first pass
+    //    reads the rows (depth bits, visible when tiles_touched > 0), drops
+    //    the culled ones, folds the range in and counts the visible rows
+    const RadixRows rr{proj->depth, proj->tiles_touched, n_rows, n_vis};
+    radix_sort(w.rk, w.rv, n_vis, n_rows, range, 32, w.hist, false, st, &rr);
     // 3. per row in depth order: super-tile offsets, the super-pair count Q
     //    and the pair count P
     //    (its last CTA: the scans of Q and P over the blocks, the capacity
@@ -1574,7 +1539,7 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
     else
       rows_gather_kernel<16><<<(unsigned)nb, kScanThreads, 0, st>>>(
           rows_sorted, n_vis, proj->rect, rect8, N, ct, w.rect_sorted, arrive + 1, co);
-    count_launches(3);
+    count_launches(1);
   } else {
     scan_counts_check_kernel<<<1, kScanThreads, 0, st>>>(co, 0);
     count_launches(1);
