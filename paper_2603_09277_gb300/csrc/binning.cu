@@ -779,12 +779,19 @@ __global__ void __launch_bounds__(kScanThreads) rows_expand_kernel(
     const SortedRows sorted, const uint2* __restrict__ rect_sorted,
     const long long* __restrict__ n_dev, const unsigned long long* __restrict__ block_items,
     const long long* __restrict__ q_eff, int N, unsigned n_magic, const CamTable ct,
-    unsigned* __restrict__ skeys, unsigned* __restrict__ svals, int vec16, int packed) {
+    unsigned* __restrict__ skeys, unsigned* __restrict__ svals, int vec16, int packed,
+    unsigned* __restrict__ hist, int hgrid, unsigned hmask) {
   constexpr int RB = kScanThreads * ITEMS;
   __shared__ unsigned s_off[RB + 1];  // item offset of each row in the block (+ the total)
+  // the super-tile sort's first-pass histogram (hist: [256][hgrid], zeroed):
+  // the block's items are one contiguous range of positions, which meets
+  // one or two of the sort's chunks; their digit counts are summed here
+  __shared__ unsigned s_h[2][kRadixBins];
   const long long n = *n_dev, Q = *q_eff;
   const long long base = (long long)blockIdx.x * RB;
   if (base >= n || Q == 0) return;  // (the whole CTA)
+  if (hist)
+    for (int i = threadIdx.x; i < 2 * kRadixBins; i += kScanThreads) (&s_h[0][0])[i] = 0u;
   const int nr = (int)min((long long)RB, n - base);
   const int first = threadIdx.x * ITEMS;
   unsigned loc[ITEMS];
@@ -807,6 +814,10 @@ __global__ void __launch_bounds__(kScanThreads) rows_expand_kernel(
   const unsigned total = (unsigned)tot;
   const long long gbase = (long long)block_items[blockIdx.x];
   const unsigned* __restrict__ rows = sorted.get();
+  // the sort's chunk of a position: div_magic by the chunk (Q < 2^32)
+  const unsigned hchunk = hist ? (unsigned)radix_chunk(Q, hgrid) : 1u;
+  const unsigned hmagic = hist ? (unsigned)(0x100000000ull / hchunk) : 0u;
+  const unsigned hc0 = hist ? div_magic((unsigned)gbase, hchunk, hmagic) : 0u;
   for (unsigned c0 = 0; c0 < total; c0 += 4 * kScanThreads) {
     const unsigned e0 = c0 + 4u * threadIdx.x;
     if (e0 >= total) continue;
@@ -860,6 +871,21 @@ __global__ void __launch_bounds__(kScanThreads) rows_expand_kernel(
       cnt = t + 1;
     }
     const long long g0 = gbase + e0;
+    if (hist) {
+      // the 4 positions cross at most one chunk boundary (chunks hold whole
+      // 2048-item tiles)
+      const unsigned c = div_magic((unsigned)g0, hchunk, hmagic);
+      const unsigned long long next = (unsigned long long)(c + 1u) * hchunk;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (t < cnt && g0 + t < Q) {
+          const unsigned ct_ = (unsigned long long)(g0 + t) >= next ? c + 1u : c;
+          const unsigned d = kk[t] & hmask;
+          if (ct_ - hc0 < 2u) atomicAdd(&s_h[ct_ - hc0][d], 1u);
+          else atomicAdd(hist + (long long)d * hgrid + ct_, 1u);
+        }
+      }
+    }
     if (vec16 && cnt == 4 && (g0 & 3) == 0 && g0 + 3 < Q) {  // skeys, svals 16-byte aligned
       reinterpret_cast<uint4*>(skeys + g0)[0] = make_uint4(kk[0], kk[1], kk[2], kk[3]);
       reinterpret_cast<uint4*>(svals + g0)[0] = make_uint4(vv[0], vv[1], vv[2], vv[3]);
@@ -870,6 +896,13 @@ __global__ void __launch_bounds__(kScanThreads) rows_expand_kernel(
           skeys[g0 + t] = kk[t];
           svals[g0 + t] = vv[t];
         }
+    }
+  }
+  if (hist) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * kRadixBins; i += kScanThreads) {
+      const unsigned v = (&s_h[0][0])[i];
+      if (v) atomicAdd(hist + (long long)(i % kRadixBins) * hgrid + hc0 + i / kRadixBins, v);
     }
   }
 }
@@ -1451,7 +1484,7 @@ int radix_grid(long long n_bound) {
 
 void radix_sort(unsigned* k[2], unsigned* v[2], const long long* n_dev, long long n_bound,
                 const unsigned* range, int bits, unsigned* hist, bool keys_last,
-                cudaStream_t st, const RadixRows* rows = nullptr) {
+                cudaStream_t st, const RadixRows* rows = nullptr, bool hist0_ready = false) {
   if (n_bound == 0) return;
   const int passes = range ? kRadixMaxPasses : radix_plan_bits(0u, bits).passes;
   // one wave: at most the CTAs of the scatter kernel resident on the device
@@ -1470,10 +1503,12 @@ void radix_sort(unsigned* k[2], unsigned* v[2], const long long* n_dev, long lon
     a.keys_out = k[(p + 1) & 1];
     a.vals_out = v[(p + 1) & 1];
     a.pass = p;
-    radix_upsweep_kernel<<<grid, kRadixThreads, 0, st>>>(a);
+    // (hist0_ready: the first pass's per-CTA digit counts are already in
+    // hist, summed by the kernel that wrote the items)
+    if (p > 0 || !hist0_ready) radix_upsweep_kernel<<<grid, kRadixThreads, 0, st>>>(a);
     radix_scan_kernel<<<kRadixBins, kScanThreads, 0, st>>>(a, grid);
     radix_downsweep_kernel<<<grid, kRadixThreads, 0, st>>>(a);
-    count_launches(3);
+    count_launches(p > 0 || !hist0_ready ? 3 : 2);
   }
 }
 
@@ -1580,24 +1615,30 @@ int launch_bin_sort(const gs_proj* proj, int N, const CamTable& ct, void* worksp
   int packed = S <= 65536 ? 1 : 0;
   for (int v = 0; v < ct.V; ++v)
     if (ct.c[v].TX > 8000 || ct.c[v].TY > 8000) packed = 0;
+  // the expansion sums the super-tile sort's first-pass histogram as it
+  // writes the items (positions below 2^31)
+  const bool hist0 = q_bound < (1ll << 31);
+  const int sgrid = radix_grid(q_bound);
+  if (hist0)
+    GS_TRY_CUDA(cudaMemsetAsync(w.hist, 0, sizeof(unsigned) * kRadixBins * (size_t)sgrid, st));
   {
     // (the scan blocks of rows_gather_kernel: their item bases are scanned)
     const int vec16 = (reinterpret_cast<uintptr_t>(sv[0]) % 16 == 0 &&
                        reinterpret_cast<uintptr_t>(sk[0]) % 16 == 0) ? 1 : 0;
+    unsigned* h = hist0 ? w.hist : nullptr;
+    const unsigned hmask = (1u << radix_plan_bits(0u, sbits).d0) - 1u;
     if (small)
       rows_expand_kernel<4><<<(unsigned)nb, kScanThreads, 0, st>>>(
           rows_sorted, w.rect_sorted, n_vis, w.block_sums, q_eff, N, div_magic_host((unsigned)N),
-          ct, sk[0], sv[0], vec16,
-          packed);
+          ct, sk[0], sv[0], vec16, packed, h, sgrid, hmask);
     else
       rows_expand_kernel<16><<<(unsigned)nb, kScanThreads, 0, st>>>(
           rows_sorted, w.rect_sorted, n_vis, w.block_sums, q_eff, N, div_magic_host((unsigned)N),
-          ct, sk[0], sv[0], vec16,
-          packed);
+          ct, sk[0], sv[0], vec16, packed, h, sgrid, hmask);
     count_launches(1);
   }
   // 5. stable sort of the super-pairs by super-tile id
-  radix_sort(sk, sv, q_eff, q_bound, nullptr, sbits, w.hist, true, st);
+  radix_sort(sk, sv, q_eff, q_bound, nullptr, sbits, w.hist, true, st, nullptr, hist0);
   const int sres = spasses & 1;
   const unsigned* sp_keys = sk[sres];
   const unsigned* sp_rows = sv[sres];  // == w.pv
