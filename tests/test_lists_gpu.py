@@ -139,3 +139,31 @@ def test_lists_and_images_from_the_packed_rects_alone(sizes):
     assert a["P"] == b["P"] > 1_000
     for k in ("vals", "keys", "ranges", "image", "T", "last", "H"):
         assert torch.equal(a[k], b[k]), k
+
+
+def test_lists_all_depths_equal():
+    # every Gaussian at the same depth: the depth range has no significant
+    # bits, the sort is its first pass alone, and every list is in Gaussian
+    # id order (the ties of the (tile, depth, id) order)
+    scene = scenes.box_scene(5_000, seed=13, ls_mean=-3.0, ls_std=0.6)
+    scene["means"][:, 2] = np.float32(4.0)
+    cams = [scenes.camera(256, 256, 256.0), scenes.camera(200, 120, 180.0)]
+    P, total, flagged = _compare_lists(scene, cams, scenes.params())
+    assert P > 5_000 and (flagged or P == total)
+
+
+@pytest.mark.parametrize("span", [0xFF10, 0xFFFF10])
+def test_lists_depth_range_across_digit_boundaries(span):
+    # depth bits from m to m + span with m's low byte 0xF0: rounding the
+    # range's minimum down to a multiple of 256 for the later passes adds a
+    # significant bit (17 instead of 16, 25 instead of 24), so one more pass
+    # runs; the lists still follow (tile, depth, id)
+    rng = np.random.default_rng(14)
+    scene = scenes.box_scene(6_000, seed=14, ls_mean=-3.0, ls_std=0.6)
+    m = np.uint32(0x40800000 + 0xF0)  # just above 4.0
+    bits = (m + rng.integers(0, span + 1, 6_000, dtype=np.uint64).astype(np.uint32))
+    bits[0], bits[1] = m, m + np.uint32(span)
+    scene["means"][:, 2] = bits.view(np.float32)
+    cams = [scenes.camera(256, 256, 256.0)]
+    P, total, flagged = _compare_lists(scene, cams, scenes.params())
+    assert P > 5_000 and (flagged or P == total)
