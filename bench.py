@@ -1003,7 +1003,9 @@ def main():
                                 dst.copy_(src, non_blocking=True)
                     for cs in copy_streams:
                         cur.wait_stream(cs)
-                tgt.copy_(host_tgt, non_blocking=True)
+                # the targets are first read by the loss: their copy runs on a
+                # copy stream beside the projection and the list construction
+                r.upload_target_async(host_tgt, tgt)
                 r.preprocess(p)
                 r.bin_sort(sync=False)
                 r.render_fwd()

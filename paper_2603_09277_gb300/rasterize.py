@@ -188,9 +188,29 @@ class Rasterizer:
             self.loss_base_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
         return self.loss_base_ws
 
+    def upload_target_async(self, host_target, target, stream=None):
+        """Starts the copy of a step's target images from pinned host memory
+        into the device tensor `target` on a copy stream, ordered after the
+        work already on `stream` (default: the current stream); the next
+        loss() on that target waits for it.  The copy then runs beside the
+        projection and the list construction, which do not read it."""
+        cur = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if getattr(self, "_copy_stream", None) is None:
+            self._copy_stream = torch.cuda.Stream(device=self.device)
+            self._copy_done = torch.cuda.Event()
+        self._copy_stream.wait_stream(cur)
+        with torch.cuda.stream(self._copy_stream):
+            target.copy_(host_target, non_blocking=True)
+            self._copy_done.record(self._copy_stream)
+        self._copy_pending = target
+
     def loss(self, target, gamma, stream=None, lam=0.0):
         """L1 + gamma * entropy, or with lam > 0 the full L_base
         (1 - lam) L1 + lam D-SSIM + gamma * entropy."""
+        if getattr(self, "_copy_pending", None) is target:
+            cur = stream if stream is not None else torch.cuda.current_stream(self.device)
+            cur.wait_event(self._copy_done)
+            self._copy_pending = None
         if lam > 0.0:
             gs.gs_loss_base(self.image, target, self.entropy, self.cams_c, lam, gamma,
                             self.loss_dev, self.dL_dimage, self.dL_dentropy, self._base_ws(),

@@ -342,6 +342,34 @@ def test_cuda_graph_replay_matches_eager():
     assert not torch.equal(r.image, ref["image"])
 
 
+def test_async_target_upload_matches_a_synchronous_copy():
+    """The step's target images copied from pinned host memory on the copy
+    stream (beside the projection and the list construction) give the loss
+    and its pixel gradients of a step whose targets were copied before it,
+    bit for bit; a new target is seen by the next step."""
+    from paper_2603_09277_gb300.rasterize import Rasterizer, scene_to_device, targets_to_device
+    scene = scenes.box_scene(6000, seed=10)
+    cams = scenes.yaw_cameras([(100, 70), (160, 96)], [0.0, 5.0])
+    r = Rasterizer(cams, scenes.params(), 6000)
+    p = scene_to_device(scene)
+    host = targets_to_device(scenes.noise_targets(cams, 3)).cpu().pin_memory()
+    tgt = torch.empty_like(host, device="cuda")
+    tgt.copy_(host)
+    r.step(p, tgt, GAMMA, sync=True)
+    torch.cuda.synchronize()
+    ref_loss, ref_d = r.loss_dev.clone(), r.dL_dimage.clone()
+    tgt.zero_()
+    r.upload_target_async(host, tgt)
+    r.step(p, tgt, GAMMA, sync=False)
+    torch.cuda.synchronize()
+    assert torch.equal(r.loss_dev, ref_loss) and torch.equal(r.dL_dimage, ref_d)
+    host.mul_(0.5)
+    r.upload_target_async(host, tgt)
+    r.step(p, tgt, GAMMA, sync=False)
+    torch.cuda.synchronize()
+    assert not torch.equal(r.loss_dev, ref_loss)
+
+
 @pytest.mark.parametrize("attr", ["f16", "bf16"])
 def test_mixed_precision_error_is_reported(attr):
     """Attributes staged in 16 bits, FP32 exponent/transmittance/accumulation:
