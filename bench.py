@@ -716,7 +716,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_2603_09277_gb300 import gs, scenes
-    from paper_2603_09277_gb300.rasterize import Rasterizer, scene_to_device, targets_to_device
+    from paper_2603_09277_gb300.rasterize import (Rasterizer, scene_to_device, sh_layout_for,
+                                                   sh_to_layout, targets_to_device)
 
     if args.sweep:
         run_sweep(args, dev)
@@ -735,7 +736,10 @@ def main():
     if args.dssim > 0:
         wl += ", L_base with D-SSIM (lambda %.2f)" % args.dssim
     N = scene["means"].shape[0]
-    p = scene_to_device(scene, dev)
+    # the SH layout for the degree in use: each coefficient of all Gaussians
+    # together where the degree reads fewer coefficients than are stored
+    sh_layout = sh_layout_for(scene["sh_degree"], scene["sh"].shape[1])
+    p = scene_to_device(scene, dev, sh_layout=sh_layout)
     tgt = targets_to_device(targets, dev)
     form = {"pixels_per_thread": args.ppt, "persistent": args.persistent, "batch": args.batch}
     tuned = None
@@ -976,7 +980,9 @@ def main():
     e2e = None
     e2e_full = None
     if not args.no_e2e:
-        host = {k: torch.as_tensor(scene[k], dtype=torch.float32).contiguous().pin_memory()
+        host = {k: torch.as_tensor(np.ascontiguousarray(
+                    sh_to_layout(scene[k], p["sh_layout"]) if k == "sh" else scene[k]),
+                    dtype=torch.float32).contiguous().pin_memory()
                 for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
         host_tgt = torch.cat([torch.as_tensor(t).reshape(-1, 3) for t in targets]).pin_memory()
         out_loss = torch.empty(1, dtype=torch.float64).pin_memory()
@@ -1099,6 +1105,8 @@ def main():
             "config": {"workload": wl, "N": N, "views": len(cams), "pairs": P,
                        "blended_pairs": nb_step, "evaluated_pairs": ne_step,
                        "bwd_evaluated_pairs": bwd_eval, "attr_dtype": args.attr,
+                       "sh_layout": ("[stride][N][3] (each coefficient of all Gaussians together)"
+                                     if sh_layout else "[N][stride][3]"),
                        "tile": args.tile,
                        "launch": ("persistent %d CTAs over the list-length queue"
                                   % form["persistent"] if form["persistent"]

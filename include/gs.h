@@ -84,6 +84,10 @@ typedef struct {
     int tile_size;  /* tile side in pixels: 16 (3DGS; 0 also means 16) or 8 (LiteGS and the
                        paper's own runs, Sec. 5 "Effect of tile sizes"); every call of one
                        pipeline must use the same side */
+    int sh_layout;  /* layout of the SH coefficients and of their gradient: 0 = [N][sh_stride][3]
+                       (a Gaussian's coefficients together), 1 = [sh_stride][N][3] (each
+                       coefficient of all Gaussians together: the loads of one coefficient are
+                       contiguous, and a degree below sh_stride reads only its coefficients) */
 } gs_params;
 
 /* Projected per-(view, Gaussian) attributes, V*N rows, device memory. */
@@ -202,7 +206,8 @@ int gs_debug_bounds_status(unsigned* status, int clear);
  * inverse covariance, opacity sigmoid(logit), SH colour up to degree 3 plus
  * 0.5 clamped at 0), the 3-sigma radius and the tile rect.
  *   means [N][3], log_scales [N][3], quats [N][4] (need not be unit length),
- *   opacity_logits [N], sh [N][prm->sh_stride][3]: device, FP32.
+ *   opacity_logits [N], sh [N][prm->sh_stride][3] (prm->sh_layout 0) or
+ *   [prm->sh_stride][N][3] (layout 1): device, FP32.
  *   cams_host [V], prm host.  out: device buffers with V*N rows.
  * A Gaussian is culled (tiles_touched 0) when its FP32 depth (the FP32
  * rounding of the FP64 camera-space z) is <= near_z, its 2D covariance is
@@ -306,7 +311,7 @@ int gs_loss_base(const float* image, const float* target, const float* entropy,
  *   Gaussians some view sees, for the projection adjoint).  From these,
  *   dL/dsigma = dd-sum / sigma, dL/dconic = -(1/2) sum dd d d^T and
  *   dL/dmean2d = conic (dd dx-sum, dd dy-sum).
- *   g_* : device, shapes of the parameters, overwritten.
+ *   g_* : device, shapes of the parameters (g_sh in prm->sh_layout), overwritten.
  * Part of the work (the zeroing of g_*, the list of Gaussians some view sees)
  * runs on a second stream of the library's own, forked from `stream` by an
  * event and joined back before the projection adjoint, so every result is

@@ -187,6 +187,7 @@ bool params_ok(const gs_params* p) {
   if (p->sh_degree < 0 || p->sh_degree > 3) return false;
   int K = (p->sh_degree + 1) * (p->sh_degree + 1);
   if (p->sh_stride < K || p->sh_stride > GS_SH_COEFFS_MAX) return false;
+  if (p->sh_layout != 0 && p->sh_layout != 1) return false;
   if (p->attr_dtype < GS_ATTR_F32 || p->attr_dtype > GS_ATTR_BF16) return false;
   if (!(p->alpha_max > 0.f && p->alpha_max < 1.f)) return false;
   if (!(p->alpha_min > 0.f && p->alpha_min < p->alpha_max)) return false;

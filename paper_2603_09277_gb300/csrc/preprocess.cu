@@ -107,21 +107,43 @@ __device__ __forceinline__ float3 sh_basis_grad_dot(int deg, float x, float y, f
   return make_float3(gx, gy, gz);
 }
 
-// Whether every Gaussian's SH block (3 * stride floats) starts on 16 bytes:
-// the array is 16-byte aligned and the stride a multiple of 4.
-__device__ __forceinline__ bool sh_vectors(const float* p, int stride) {
-  return (stride & 3) == 0 && (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+// Where value e = 3k + channel of Gaussian g's SH lies: sh[g * gs + k * ks +
+// channel].  Layout 0 keeps a Gaussian's coefficients together (gs = 3 *
+// stride, ks = 3); layout 1 keeps each coefficient of all Gaussians together
+// (gs = 3, ks = 3N), so that a warp's loads of one coefficient are
+// contiguous and a degree below the stored one reads only its coefficients.
+struct ShPtr {
+  long long gs, ks;
+  int vec;  // layout 0, 16-byte aligned array, stride a multiple of 4: 16-byte loads
+};
+
+inline ShPtr sh_ptr(const float* sh, const gs_params* prm, int N) {
+  ShPtr L;
+  if (prm->sh_layout == 1) {
+    L.gs = 3;
+    L.ks = 3ll * N;
+    L.vec = 0;
+  } else {
+    L.gs = 3ll * prm->sh_stride;
+    L.ks = 3;
+    L.vec = (prm->sh_stride & 3) == 0 && (reinterpret_cast<uintptr_t>(sh) & 15) == 0;
+  }
+  return L;
+}
+
+__device__ __forceinline__ long long sh_index(const ShPtr& L, long long g, int e) {
+  return g * L.gs + (long long)(e / 3) * L.ks + e % 3;
 }
 
 // Calls f(e, value) for the floats e = 3k + channel, e < 3K, of Gaussian
-// g's SH block, in ascending e.  With vec, 16-byte loads: the last one may
-// read up to 3 floats past 3K, which stay inside the block (3 * stride is a
-// multiple of 4 and at least 3K) and are not passed on.
+// g's SH, in ascending e.  With vec, 16-byte loads of the Gaussian's block:
+// the last one may read up to 3 floats past 3K, which stay inside the block
+// (3 * stride is a multiple of 4 and at least 3K) and are not passed on.
 template <typename F>
-__device__ __forceinline__ void for_sh_block(const float* sh, long long g, int stride, int K,
-                                             bool vec, F&& f) {
-  const float* p = sh + g * stride * 3;
-  if (vec) {
+__device__ __forceinline__ void for_sh_block(const float* sh, long long g, const ShPtr& L,
+                                             int K, F&& f) {
+  if (L.vec) {
+    const float* p = sh + g * L.gs;
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
       if (4 * i < 3 * K) {
@@ -134,8 +156,14 @@ __device__ __forceinline__ void for_sh_block(const float* sh, long long g, int s
     }
   } else {
 #pragma unroll
-    for (int e = 0; e < 48; ++e)
-      if (e < 3 * K) f(e, __ldg(p + e));
+    for (int k = 0; k < 16; ++k) {
+      if (k < K) {
+        const float* q = sh + g * L.gs + k * L.ks;
+        f(3 * k, __ldg(q));
+        f(3 * k + 1, __ldg(q + 1));
+        f(3 * k + 2, __ldg(q + 2));
+      }
+    }
   }
 }
 
@@ -453,7 +481,7 @@ __global__ void __launch_bounds__(256, pre_ctas_per_sm<DEG>()) preprocess_kernel
     const float* __restrict__ means, const float* __restrict__ log_scales,
     const float* __restrict__ quats, const float* __restrict__ opacity_logits,
     const float* __restrict__ sh, int N, const CamTable ct, float dilation, float near_z,
-    int sh_stride, gs_proj out) {
+    const ShPtr shp, gs_proj out) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
   Activated a = activate(means, log_scales, quats, opacity_logits, g);
@@ -465,8 +493,7 @@ __global__ void __launch_bounds__(256, pre_ctas_per_sm<DEG>()) preprocess_kernel
   if constexpr (DEG == 0) {
     float Y[16];
     sh_basis(0, 0.f, 0.f, 1.f, Y);
-    for_sh_block(sh, g, sh_stride, K, sh_vectors(sh, sh_stride),
-                 [&](int e, float v) { col0[e % 3] += Y[e / 3] * v; });
+    for_sh_block(sh, g, shp, K, [&](int e, float v) { col0[e % 3] += Y[e / 3] * v; });
   }
   for (int v = 0; v < ct.V; ++v) {
     const CamInfo& c = ct.c[v];
@@ -511,8 +538,7 @@ __global__ void __launch_bounds__(256, pre_ctas_per_sm<DEG>()) preprocess_kernel
       float il = rsqrtf(vx * vx + vy * vy + vz * vz);
       float Y[16];
       sh_basis(sh_deg, vx * il, vy * il, vz * il, Y);
-      for_sh_block(sh, g, sh_stride, K, sh_vectors(sh, sh_stride),
-                   [&](int e, float v) { col[e % 3] += Y[e / 3] * v; });
+      for_sh_block(sh, g, shp, K, [&](int e, float v) { col[e % 3] += Y[e / 3] * v; });
     }
     float cr = col[0], cg = col[1], cbl = col[2];
     cr = fmaxf(cr, 0.f);
@@ -607,19 +633,18 @@ struct ShCoef {
   static constexpr int K = (DEG + 1) * (DEG + 1);
   static constexpr bool kCached = DEG == 0;
   float c[kCached ? 3 * K : 1];
-  __device__ __forceinline__ void load(const float* __restrict__ sh, long long g, int stride,
-                                       bool vec) {
-    if constexpr (kCached) for_sh_block(sh, g, stride, K, vec, [&](int e, float v) { c[e] = v; });
+  __device__ __forceinline__ void load(const float* __restrict__ sh, long long g, const ShPtr& L) {
+    if constexpr (kCached) for_sh_block(sh, g, L, K, [&](int e, float v) { c[e] = v; });
   }
   // f(e, value) for e < 3K, like for_sh_block
   template <typename F>
-  __device__ __forceinline__ void each(const float* __restrict__ sh, long long g, int stride,
-                                       bool vec, F&& f) const {
+  __device__ __forceinline__ void each(const float* __restrict__ sh, long long g, const ShPtr& L,
+                                       F&& f) const {
     if constexpr (kCached) {
 #pragma unroll
       for (int e = 0; e < 3 * K; ++e) f(e, c[e]);
     } else {
-      for_sh_block(sh, g, stride, K, vec, f);
+      for_sh_block(sh, g, L, K, f);
     }
   }
 };
@@ -631,7 +656,7 @@ struct ShCoef {
 template <int DEG, bool SHREG>
 __device__ __forceinline__ void adjoint_view(
     int g, int v, const Activated& a, const float* __restrict__ sh, int N, const CamTable& ct,
-    float dilation, int sh_stride, bool vec, const float* __restrict__ grad2d,
+    float dilation, const ShPtr& shp, const float* __restrict__ grad2d,
     AdjAcc<SHREG ? DEG : 0>& acc, bool first_view, bool vec_out, float* __restrict__ g_sh,
     const ShCoef<DEG>& shc) {
   constexpr int sh_deg = DEG;
@@ -660,18 +685,18 @@ __device__ __forceinline__ void adjoint_view(
     float Y[16] = {};
     sh_basis(sh_deg, dx, dy, dz, Y);
     float raw[3] = {0.5f, 0.5f, 0.5f};
-    shc.each(sh, g, sh_stride, vec, [&](int e, float v) { raw[e % 3] += Y[e / 3] * v; });
+    shc.each(sh, g, shp, [&](int e, float v) { raw[e % 3] += Y[e / 3] * v; });
     float grgb[3] = {raw[0] < 0.f ? 0.f : G1.z, raw[1] < 0.f ? 0.f : G1.w,
                      raw[2] < 0.f ? 0.f : G2.x};
     float cdot[16] = {};  // SH[k] . grgb
-    shc.each(sh, g, sh_stride, vec,
+    shc.each(sh, g, shp,
              [&](int e, float v) { cdot[e / 3] = __fmaf_rn(v, grgb[e % 3], cdot[e / 3]); });
     // dL/dSH[k][ch] = Y_k grgb_ch
     if constexpr (SHREG) {
 #pragma unroll
       for (int e = 0; e < 3 * K; ++e) acc.gsh[e] = __fmaf_rn(Y[e / 3], grgb[e % 3], acc.gsh[e]);
     } else {
-      float* gsh = g_sh + (long long)g * sh_stride * 3;
+      float* gsh = g_sh + (long long)g * shp.gs;  // (vec_out: layout 0)
       if (vec_out) {
 #pragma unroll
         for (int i = 0; i < 12; ++i) {
@@ -696,7 +721,8 @@ __device__ __forceinline__ void adjoint_view(
         for (int e = 0; e < 48; ++e) {
           if (e < 3 * K) {
             const float y = Y[e / 3] * grgb[e % 3];
-            gsh[e] = first_view ? y : gsh[e] + y;
+            float& o = g_sh[sh_index(shp, g, e)];
+            o = first_view ? y : o + y;
           }
         }
       }
@@ -797,17 +823,17 @@ __device__ __forceinline__ void adjoint_view(
 // them was 15/16 of this kernel's SH writes).
 template <int DEG, int L, bool SHREG>
 __device__ __forceinline__ void adjoint_finish(
-    int g, int sub, const Activated& a, const AdjAcc<DEG>& acc, int sh_stride, bool vec_out,
+    int g, int sub, const Activated& a, const AdjAcc<DEG>& acc, const ShPtr& shp, bool vec_out,
     float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
     float* __restrict__ g_opac, float* __restrict__ g_sh) {
   constexpr int K = AdjAcc<DEG>::K;
   constexpr int kSectorFloats = (3 * K + 7) / 8 * 8;  // 3K rounded up to 32 bytes
-  float* gsh = g_sh + (long long)g * sh_stride * 3;
+  float* gsh = g_sh + (long long)g * shp.gs;  // (vec_out: layout 0, the block's start)
   if (!SHREG) {
   } else if (vec_out) {
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
-      if (i % L == sub && 4 * i < kSectorFloats && 4 * i < 3 * sh_stride) {
+      if (i % L == sub && 4 * i < kSectorFloats && 4 * i < shp.gs) {
         float o[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) o[j] = 4 * i + j < 3 * K ? acc.gsh[4 * i + j] : 0.f;
@@ -817,7 +843,7 @@ __device__ __forceinline__ void adjoint_finish(
   } else {
 #pragma unroll
     for (int e = 0; e < 48; ++e)
-      if (e % L == sub && e < 3 * K) gsh[e] = acc.gsh[e];
+      if (e % L == sub && e < 3 * K) g_sh[sh_index(shp, g, e)] = acc.gsh[e];
   }
   if (sub != 0) return;
   const float* gm = acc.gm;
@@ -858,11 +884,11 @@ __device__ __forceinline__ void adjoint_group(
     int g, int sub, unsigned mask, const float* __restrict__ means,
     const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ opacity_logits, const float* __restrict__ sh, int N,
-    const CamTable& ct, float dilation, int sh_stride, const unsigned* __restrict__ tiles_touched,
-    const float* __restrict__ grad2d, float* __restrict__ g_means, float* __restrict__ g_ls,
-    float* __restrict__ g_quats, float* __restrict__ g_opac, float* __restrict__ g_sh) {
-  const bool vec = sh_vectors(sh, sh_stride);
-  const bool vec_out = vec && (reinterpret_cast<uintptr_t>(g_sh) & 15) == 0;
+    const CamTable& ct, float dilation, const ShPtr& shp,
+    const unsigned* __restrict__ tiles_touched, const float* __restrict__ grad2d,
+    float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
+    float* __restrict__ g_opac, float* __restrict__ g_sh) {
+  const bool vec_out = shp.vec && (reinterpret_cast<uintptr_t>(g_sh) & 15) == 0;
   const Activated a = activate(means, log_scales, quats, opacity_logits, g);
   constexpr bool SHREG = L > 1 || DEG < 3;
   AdjAcc<SHREG ? DEG : 0> acc;
@@ -875,17 +901,17 @@ __device__ __forceinline__ void adjoint_group(
   for (int v = sub; v < ct.V; v += L)
     seen |= (unsigned long long)(tiles_touched[(long long)v * N + g] != 0u) << v;
   ShCoef<DEG> shc;
-  shc.load(sh, g, sh_stride, vec);
+  shc.load(sh, g, shp);
   bool first = true;
   while (seen) {
     const int v = __ffsll((long long)seen) - 1;
     seen &= seen - 1ull;
-    adjoint_view<DEG, SHREG>(g, v, a, sh, N, ct, dilation, sh_stride, vec, grad2d, acc, first,
-                             vec_out, g_sh, shc);
+    adjoint_view<DEG, SHREG>(g, v, a, sh, N, ct, dilation, shp, grad2d, acc, first, vec_out,
+                             g_sh, shc);
     first = false;
   }
   acc.template reduce<L>(mask);
-  adjoint_finish<SHREG ? DEG : 0, L, SHREG>(g, sub, a, acc, sh_stride, vec_out, g_means, g_ls,
+  adjoint_finish<SHREG ? DEG : 0, L, SHREG>(g, sub, a, acc, shp, vec_out, g_means, g_ls,
                                             g_quats, g_opac, g_sh);
 }
 
@@ -944,7 +970,7 @@ template <int DEG, int L>
 __global__ void __launch_bounds__(kAdjThreads, adj_ctas_per_sm<DEG, L>()) preprocess_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales,
     const float* __restrict__ quats, const float* __restrict__ opacity_logits,
-    const float* __restrict__ sh, int N, const CamTable ct, float dilation, int sh_stride,
+    const float* __restrict__ sh, int N, const CamTable ct, float dilation, const ShPtr shp,
     const unsigned* __restrict__ tiles_touched, const float* __restrict__ grad2d,
     float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
     float* __restrict__ g_opac, float* __restrict__ g_sh) {
@@ -959,7 +985,7 @@ __global__ void __launch_bounds__(kAdjThreads, adj_ctas_per_sm<DEG, L>()) prepro
     const unsigned g = g2[12ll * i + 9];
     if (!GS_IN_BOUNDS(g, N, 301)) continue;
     adjoint_group<DEG, L>((int)g, sub, mask, means, log_scales, quats,
-                          opacity_logits, sh, N, ct, dilation, sh_stride, tiles_touched, grad2d,
+                          opacity_logits, sh, N, ct, dilation, shp, tiles_touched, grad2d,
                           g_means, g_ls, g_quats, g_opac, g_sh);
   }
 }
@@ -974,7 +1000,7 @@ void launch_adjoint(const float* means, const float* log_scales, const float* qu
   const long long want = ((long long)N * L + kAdjThreads - 1) / kAdjThreads;
   const int grid = (int)std::min<long long>(152ll * adj_ctas_per_sm<DEG, L>() * 2, want);
   preprocess_bwd_kernel<DEG, L><<<grid, kAdjThreads, 0, st>>>(
-      means, log_scales, quats, opacity_logits, sh, N, ct, prm->dilation, prm->sh_stride,
+      means, log_scales, quats, opacity_logits, sh, N, ct, prm->dilation, sh_ptr(sh, prm, N),
       tiles_touched, grad2d, g_means, g_ls, g_quats, g_opac, g_sh);
 }
 
@@ -1079,7 +1105,7 @@ void launch_preprocess_dt(int deg, dim3 grid, dim3 block, const float* means,
 #define GS_PRE_LAUNCH(D)                                                                   \
   preprocess_kernel<DT, D><<<grid, block, 0, st>>>(means, log_scales, quats, opacity_logits, \
                                                    sh, N, ct, prm->dilation, prm->near_z,    \
-                                                   prm->sh_stride, o)
+                                                   sh_ptr(sh, prm, N), o)
   switch (deg) {
     case 0: GS_PRE_LAUNCH(0); break;
     case 1: GS_PRE_LAUNCH(1); break;

@@ -39,7 +39,8 @@ class GsParams(ctypes.Structure):
                 ("t_min", ctypes.c_float), ("dilation", ctypes.c_float),
                 ("near_z", ctypes.c_float), ("fov_clamp", ctypes.c_float),
                 ("sh_degree", ctypes.c_int), ("sh_stride", ctypes.c_int),
-                ("attr_dtype", ctypes.c_int), ("tile_size", ctypes.c_int)]
+                ("attr_dtype", ctypes.c_int), ("tile_size", ctypes.c_int),
+                ("sh_layout", ctypes.c_int)]
 
 
 class GsProj(ctypes.Structure):
@@ -167,7 +168,7 @@ def make_cameras(cams):
     return arr
 
 
-def make_params(prm, sh_stride=16, attr_dtype="f32"):
+def make_params(prm, sh_stride=16, attr_dtype="f32", sh_layout=0):
     p = GsParams()
     p.alpha_max, p.alpha_min, p.t_min = prm["alpha_max"], prm["alpha_min"], prm["t_min"]
     p.dilation, p.near_z, p.fov_clamp = prm["dilation"], prm["near_z"], prm["fov_clamp"]
@@ -175,6 +176,7 @@ def make_params(prm, sh_stride=16, attr_dtype="f32"):
     p.sh_stride = int(sh_stride)
     p.attr_dtype = ATTR_DTYPES[attr_dtype] if isinstance(attr_dtype, str) else int(attr_dtype)
     p.tile_size = int(prm.get("tile", 16))
+    p.sh_layout = int(sh_layout)
     return p
 
 

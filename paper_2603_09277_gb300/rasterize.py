@@ -7,6 +7,7 @@ torch.autograd.Function wrappers for training loops.
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import gs
@@ -14,13 +15,32 @@ from . import gs
 PARAM_KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 
 
-def scene_to_device(scene, device="cuda", requires_grad=False):
-    """numpy scene dict -> dict of contiguous float32 CUDA tensors."""
+def sh_to_layout(sh, sh_layout):
+    """[N][K][3] SH coefficients in the library's layout sh_layout: 0 keeps
+    them, 1 gives [K][N][3] (each coefficient of all Gaussians together)."""
+    return sh if sh_layout == 0 else sh.transpose(1, 0, 2) if isinstance(sh, np.ndarray) \
+        else sh.transpose(0, 1)
+
+
+def sh_layout_for(sh_degree, sh_stride):
+    """The faster SH layout for a degree in use: 1 (each coefficient of all
+    Gaussians together) when it reads fewer coefficients than are stored, so
+    that its loads stay contiguous instead of picking a few floats out of
+    every Gaussian's block; 0 when it reads them all (16-byte loads of each
+    Gaussian's block)."""
+    return 1 if (int(sh_degree) + 1) ** 2 < int(sh_stride) else 0
+
+
+def scene_to_device(scene, device="cuda", requires_grad=False, sh_layout=0):
+    """numpy scene dict -> dict of contiguous float32 CUDA tensors; the SH
+    coefficients in layout sh_layout (recorded as "sh_layout")."""
     out = {}
     for k in PARAM_KEYS:
-        t = torch.as_tensor(scene[k], dtype=torch.float32).contiguous().to(device)
+        a = sh_to_layout(scene[k], sh_layout) if k == "sh" else scene[k]
+        t = torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).contiguous().to(device)
         out[k] = t.requires_grad_(requires_grad) if requires_grad else t
     out["sh_degree"] = int(scene["sh_degree"])
+    out["sh_layout"] = int(sh_layout)
     return out
 
 
@@ -111,6 +131,7 @@ class Rasterizer:
             "opacity_logits": torch.empty(max(self.N, 1), **f32),
             "sh": torch.empty(max(self.N, 1), sh_stride, 3, **f32),
         }
+        self._gsh = self.grads["sh"]  # its storage, viewed in the parameters' SH layout
         self.stats = torch.zeros(2, dtype=torch.int64, device=dev)
         self.persistent = int(persistent)
         self.ppt = int(pixels_per_thread)
@@ -145,7 +166,17 @@ class Rasterizer:
         self.sorted_keys = None
 
     # -- steps -------------------------------------------------------------
+    def _sh_layout(self, p):
+        """Takes the SH layout of the parameters p (their "sh_layout", 0 when
+        absent) for the calls and the SH gradient."""
+        lay = int(p.get("sh_layout", 0)) if isinstance(p, dict) else 0
+        if lay != self.prm_c.sh_layout:
+            self.prm_c.sh_layout = lay
+            self.grads["sh"] = (self._gsh if lay == 0 else
+                                self._gsh.view(self.sh_stride, max(self.N, 1), 3))
+
     def preprocess(self, p, stream=None):
+        self._sh_layout(p)
         gs.gs_preprocess(p["means"], p["log_scales"], p["quats"], p["opacity_logits"], p["sh"],
                          self.N, self.cams_c, self.prm_c, self.proj_c, stream)
 
@@ -224,6 +255,7 @@ class Rasterizer:
     def render_bwd(self, p, dL_dimage=None, dL_dentropy="auto", stream=None, events=None):
         dimg = self.dL_dimage if dL_dimage is None else dL_dimage
         dent = self.dL_dentropy if isinstance(dL_dentropy, str) else dL_dentropy
+        self._sh_layout(p)
         g = self.grads
         gs.gs_render_bwd(self.proj_c, self.N, self.cams_c, self.prm_c, self.sorted_vals,
                          self.tile_ranges, self.final_T, self.last_idx, dimg, dent, p["means"],

@@ -40,14 +40,16 @@ FLIP_SHARE = 0.02
 
 
 def run_gpu(scene, cams, prm, target=None, gamma=0.015, attr="f32", persistent=0,
-            dL_dimage=None, dL_dentropy=None, keys=True, ppt=0, batch=0):
+            dL_dimage=None, dL_dentropy=None, keys=True, ppt=0, batch=0, sh_layout=0):
     """Runs preprocess, bin_sort, render_fwd, loss (if target) and
     render_bwd through the C ABI.  dL_dimage / dL_dentropy (numpy, per
-    pixel) override the loss gradients.  Returns numpy arrays."""
+    pixel) override the loss gradients; sh_layout is the layout of the SH
+    coefficients on the device (the SH gradient comes back as [N][K][3]).
+    Returns numpy arrays."""
     N = scene["means"].shape[0]
-    rast = Rasterizer(cams, prm, N, attr_dtype=attr, keep_debug=True, persistent=persistent,
-                      pixels_per_thread=ppt, batch=batch)
-    p = scene_to_device(scene)
+    rast = Rasterizer(cams, prm, N, sh_stride=scene["sh"].shape[1], attr_dtype=attr,
+                      keep_debug=True, persistent=persistent, pixels_per_thread=ppt, batch=batch)
+    p = scene_to_device(scene, sh_layout=sh_layout)
     rast.preprocess(p)
     P = rast.bin_sort(keys=keys)
     rast.render_fwd(stats=True)
@@ -76,7 +78,8 @@ def run_gpu(scene, cams, prm, target=None, gamma=0.015, attr="f32", persistent=0
         "last": n(rast.last_idx).astype(np.int64), "entropy": n(rast.entropy),
         "stats": n(rast.stats),
         "grad2d": n(rast.grad2d),
-        "grads": {k: n(v) for k, v in rast.grads.items()},
+        "grads": {k: (n(v.transpose(0, 1)) if k == "sh" and sh_layout == 1 else n(v))
+                  for k, v in rast.grads.items()},
     })
     return out
 

@@ -247,9 +247,10 @@ def test_loss_kernel_parity():
     assert torch.equal(dent_u.cpu(), rast.dL_dentropy.cpu())
 
 
-@pytest.mark.parametrize("seed", [0, 1])
-def test_sh3_small_scene(seed):
-    """SH degree 3, rotated orbit camera, ragged image size, 20k Gaussians."""
+@pytest.mark.parametrize("seed,sh_layout", [(0, 0), (1, 1)])
+def test_sh3_small_scene(seed, sh_layout):
+    """SH degree 3, rotated orbit camera, ragged image size, 20k Gaussians;
+    the SH coefficients on the device in either layout."""
     scene = scenes.cluster_scene(20_000, seed=seed, radius=3.0)
     pos = np.array([2.5, 0.4, -2.0])
     cams = [scenes.camera(200, 137, 170.0, scenes.look_at(pos, (0.0, 0.0, 0.0)), pos)]
@@ -257,7 +258,7 @@ def test_sh3_small_scene(seed):
     targets = scenes.noise_targets(cams, seed + 7)
     L, views, grads, g9 = _oracle_full(scene, cams, targets, prm)
     g = run_gpu(scene, cams, prm, target=targets, dL_dimage=views[0]["dL_dC"],
-                dL_dentropy=views[0]["dL_dH"])
+                dL_dentropy=views[0]["dL_dH"], sh_layout=sh_layout)
     N = scene["means"].shape[0]
     check_projection(g, views, cams, N)
     check_lists(g, views, cams, N)
@@ -265,9 +266,11 @@ def test_sh3_small_scene(seed):
     check_grads(g, grads, views, cams, N, 16)
 
 
-def test_multiview_uneven_sizes():
+@pytest.mark.parametrize("sh_layout", [0, 1])
+def test_multiview_uneven_sizes(sh_layout):
     """Three views of uneven size in one launch: every per-view output equals
-    the oracle's; gradients sum over views."""
+    the oracle's; gradients sum over views; degree 0 of 16 stored SH
+    coefficients in either layout."""
     scene = scenes.box_scene(6000, seed=2)
     cams = scenes.yaw_cameras([(77, 51), (154, 102), (160, 96)], [0.0, 6.0, -9.0])
     prm = scenes.params()
@@ -275,7 +278,8 @@ def test_multiview_uneven_sizes():
     L, views, grads, g9 = _oracle_full(scene, cams, targets, prm)
     dC = np.concatenate([v["dL_dC"].reshape(-1, 3) for v in views])
     dH = np.concatenate([v["dL_dH"].reshape(-1) for v in views])
-    g = run_gpu(scene, cams, prm, target=targets, dL_dimage=dC, dL_dentropy=dH)
+    g = run_gpu(scene, cams, prm, target=targets, dL_dimage=dC, dL_dentropy=dH,
+                sh_layout=sh_layout)
     N = scene["means"].shape[0]
     check_projection(g, views, cams, N)
     check_lists(g, views, cams, N)
