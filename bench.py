@@ -883,13 +883,19 @@ def main():
     n_g = int(scene["means"].shape[0])
     rec_b = gs.gs_record_bytes(r.prm_c.attr_dtype)
     Q = super_tile_items(r, cams, args.tile)
+    # the rect bytes of a row: the int4 rect of every row when it is written,
+    # the 8-bit packed rect of every visible row when the views fit it
+    r8 = all(-(-c["width"] // args.tile) <= 255 and -(-c["height"] // args.tile) <= 255
+             for c in cams)
+    rect_w = (r.rows * 16 if r.rect is not None else 0) + (n_rows_vis * 4 if r8 else 0)
+    rect_r = n_rows_vis * 4 if r8 else r.rows * 16
     algo = {
         "render_fwd_kernel": ("alu", FWD_EVAL * ne_step + FWD_BLEND * nb_step),
         "render_bwd_kernel": ("alu", BWD_EVAL * bwd_eval + BWD_BLEND * nb_step),
         # every Gaussian's geometry and opacity, the SH in use of the seen
-        # ones; depth, rect and count of every row, the record of every
+        # ones; depth and count of every row, its rects, the record of every
         # visible row
-        "preprocess_kernel": ("hbm", n_g * 44 + n_gauss_vis * 12 * Kc + r.rows * 24 +
+        "preprocess_kernel": ("hbm", n_g * 44 + n_gauss_vis * 12 * Kc + r.rows * 8 + rect_w +
                               n_rows_vis * rec_b),
         # the super-tile items (packed key, row) read, every pair written once
         "st_emit_kernel": ("hbm", Q * 8 + P * 4),
@@ -949,9 +955,9 @@ def main():
               "render_fwd": phase["render_fwd_kernel"],
               "loss": phase["render_fwd+loss"] - phase["render_fwd_kernel"]}
     n_pix = int(r.image.shape[0])
-    bytes_pre = (n_g * 44 + n_gauss_vis * 12 * Kc + r.rows * 24 +
+    bytes_pre = (n_g * 44 + n_gauss_vis * 12 * Kc + r.rows * 8 + rect_w +
                  n_rows_vis * gs.gs_record_bytes(r.prm_c.attr_dtype))
-    bytes_bin = r.rows * 24 + P * 4 + r.total_tiles * 8
+    bytes_bin = r.rows * 8 + rect_r + P * 4 + r.total_tiles * 8
     bytes_loss = n_pix * 44
 
     def hbm_line(nbytes, ms_):
