@@ -90,8 +90,8 @@ def test_lists_sixty_four_views():
 
 
 def test_lists_more_than_four_million_rows():
-    # 70,000 Gaussians x 64 views = 4.48 M rows: the row scans and the
-    # compaction run with 4,096-row blocks (1,024 up to 4 M rows)
+    # 70,000 Gaussians x 64 views = 4.48 M rows: the depth-ordered gather and
+    # the expansion run on 4,096-row blocks (1,024 up to 4 M rows)
     rng = np.random.default_rng(9)
     yaws = list(rng.uniform(-20.0, 20.0, 64))
     sizes = [(int(w), int(h)) for w, h in zip(rng.integers(24, 200, 64), rng.integers(24, 160, 64))]
