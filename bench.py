@@ -985,6 +985,7 @@ def main():
     # measurement also uploads every parameter each step.
     e2e = None
     e2e_full = None
+    e2e_eager = None
     if not args.no_e2e:
         host = {k: torch.as_tensor(np.ascontiguousarray(
                     sh_to_layout(scene[k], p["sh_layout"]) if k == "sh" else scene[k]),
@@ -1001,42 +1002,65 @@ def main():
                      [(p[kk], host[kk]) for kk in ("means", "log_scales", "quats",
                                                     "opacity_logits")]]
 
-        def run_e2e(upload_params):
-            ms = []
+        def e2e_body(upload_params):
             cur = torch.cuda.current_stream()
+            if upload_params:
+                for cs, plan in zip(copy_streams, copy_plan):
+                    cs.wait_stream(cur)
+                    with torch.cuda.stream(cs):
+                        for dst, src in plan:
+                            dst.copy_(src, non_blocking=True)
+                for cs in copy_streams:
+                    cur.wait_stream(cs)
+            # the targets are first read by the loss: their copy runs on a
+            # copy stream beside the projection and the list construction
+            r.upload_target_async(host_tgt, tgt)
+            r.preprocess(p)
+            r.bin_sort(sync=False)
+            r.render_fwd()
+            r.loss(tgt, gamma, lam=args.dssim)
+            r.render_bwd(p)
+            gs.gs_scale_reset(ls_work, 0.2)
+            out_loss.copy_(r.loss_dev, non_blocking=True)
+
+        def run_e2e(upload_params, graph=True):
+            """Every step: the copies in from pinned host memory, the step and
+            the loss read back; with graph, all of it captured once in a CUDA
+            graph (copies included) and replayed per step, as a training loop
+            on this library runs it; otherwise the calls issued eagerly."""
+            step = lambda: e2e_body(upload_params)
+            gr = None
+            if graph:
+                gr = torch.cuda.CUDAGraph()
+                cap = torch.cuda.Stream(device=dev)
+                cap.wait_stream(torch.cuda.current_stream())
+                with torch.cuda.stream(cap):
+                    with torch.cuda.graph(gr, stream=cap):
+                        e2e_body(upload_params)
+                torch.cuda.current_stream().wait_stream(cap)
+                step = gr.replay
+            ms = []
             for k in range(K + 1):
                 flush.fill_(float(k))
                 a.record()
-                if upload_params:
-                    for cs, plan in zip(copy_streams, copy_plan):
-                        cs.wait_stream(cur)
-                        with torch.cuda.stream(cs):
-                            for dst, src in plan:
-                                dst.copy_(src, non_blocking=True)
-                    for cs in copy_streams:
-                        cur.wait_stream(cs)
-                # the targets are first read by the loss: their copy runs on a
-                # copy stream beside the projection and the list construction
-                r.upload_target_async(host_tgt, tgt)
-                r.preprocess(p)
-                r.bin_sort(sync=False)
-                r.render_fwd()
-                r.loss(tgt, gamma, lam=args.dssim)
-                r.render_bwd(p)
-                gs.gs_scale_reset(ls_work, 0.2)
-                out_loss.copy_(r.loss_dev, non_blocking=True)
+                step()
                 b.record()
                 b.synchronize()
                 if k > 0:
                     ms.append(a.elapsed_time(b))
+            if int(r.status_dev.item()) != 0:
+                raise RuntimeError("pair capacity overflow in the end-to-end step")
+            del gr
             t, _ = rank_totals(sum(ms) / 1000.0, 0, world, dev)
             h2d = host_tgt.numel() * 4 + (sum(v.numel() * 4 for v in host.values())
                                           if upload_params else 0)
             return {"value": nb_all * K / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(out_loss.numel() * 8), "ms_per_step": 1000.0 * t / K}
+                    "d2h_bytes_per_step": int(out_loss.numel() * 8), "ms_per_step": 1000.0 * t / K,
+                    "form": "CUDA graph replay" if graph else "eager calls"}
 
         e2e = run_e2e(False)
         e2e_full = run_e2e(True)
+        e2e_eager = run_e2e(False, graph=False)
 
     # the FP64 oracle on view 0 (the CPU baseline); its view-0 outputs are
     # also the reference for the error each form below states
@@ -1137,6 +1161,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "e2e_params_uploaded": e2e_full,
+            "e2e_eager": e2e_eager,
             "gpu_launches": launches,
             "clocks": clocks,
         }
