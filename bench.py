@@ -716,8 +716,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_2603_09277_gb300 import gs, scenes
-    from paper_2603_09277_gb300.rasterize import (Rasterizer, scene_to_device, sh_layout_for,
-                                                   sh_to_layout, targets_to_device)
+    from paper_2603_09277_gb300.rasterize import (Rasterizer, capture_step, scene_to_device,
+                                                   sh_layout_for, sh_to_layout, targets_to_device)
 
     if args.sweep:
         run_sweep(args, dev)
@@ -1031,13 +1031,7 @@ def main():
             step = lambda: e2e_body(upload_params)
             gr = None
             if graph:
-                gr = torch.cuda.CUDAGraph()
-                cap = torch.cuda.Stream(device=dev)
-                cap.wait_stream(torch.cuda.current_stream())
-                with torch.cuda.stream(cap):
-                    with torch.cuda.graph(gr, stream=cap):
-                        e2e_body(upload_params)
-                torch.cuda.current_stream().wait_stream(cap)
+                gr = capture_step(step, dev)
                 step = gr.replay
             ms = []
             for k in range(K + 1):

@@ -50,6 +50,25 @@ def targets_to_device(targets, device="cuda"):
         device).contiguous()
 
 
+def capture_step(fn, device="cuda"):
+    """Captures fn() -- a whole step of Rasterizer calls, copies from pinned
+    host memory and the loss read-back included -- in a CUDA graph on a side
+    stream and returns the graph; graph.replay() reruns the step with the
+    buffers' current contents.  Run the step once eagerly first (the pair
+    buffers are sized there, and the library's second stream is created
+    outside a capture); list construction inside the graph keeps the pair
+    count on the device (bin_sort(sync=False)): after a replay, a nonzero
+    status_dev means the pair buffers overflowed."""
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream(device=device)
+    s.wait_stream(torch.cuda.current_stream(device))
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            fn()
+    torch.cuda.current_stream(device).wait_stream(s)
+    return g
+
+
 class Rasterizer:
     """Buffers and calls for one fixed set of views and Gaussian count.
 

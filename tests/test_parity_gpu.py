@@ -372,6 +372,21 @@ def test_async_target_upload_matches_a_synchronous_copy():
     r.step(p, tgt, GAMMA, sync=False)
     torch.cuda.synchronize()
     assert not torch.equal(r.loss_dev, ref_loss)
+    # the same step with its copies captured in one graph (capture_step) and
+    # replayed: the host buffers' current contents are read at each replay
+    from paper_2603_09277_gb300.rasterize import capture_step
+    loss_host = torch.zeros(1, dtype=torch.float64).pin_memory()
+
+    def body():
+        r.upload_target_async(host, tgt)
+        r.step(p, tgt, GAMMA, sync=False)
+        loss_host.copy_(r.loss_dev, non_blocking=True)
+    g = capture_step(body)
+    host.mul_(2.0)  # back to the first targets
+    g.replay()
+    torch.cuda.synchronize()
+    assert int(r.status_dev.item()) == 0
+    assert loss_host.item() == ref_loss.item() and torch.equal(r.dL_dimage, ref_d)
 
 
 @pytest.mark.parametrize("attr", ["f16", "bf16"])
