@@ -997,14 +997,28 @@ def main():
         # the parameter upload runs on three copy streams (the SH block in two
         # halves, the rest), joined before the step
         copy_streams = [torch.cuda.Stream(device=dev) for _ in range(3)]
-        nh = host["sh"].shape[0] // 2
-        copy_plan = [[(p["sh"][:nh], host["sh"][:nh])], [(p["sh"][nh:], host["sh"][nh:])],
-                     [(p[kk], host[kk]) for kk in ("means", "log_scales", "quats",
-                                                    "opacity_logits")]]
+        geo = [(p[kk], host[kk]) for kk in ("means", "log_scales", "quats", "opacity_logits")]
+        k_used = (int(scene["sh_degree"]) + 1) ** 2
+        late_plan = []
+        if p["sh_layout"] == 1 and k_used < host["sh"].shape[0]:
+            # coefficient-major SH: the step reads only the coefficients of
+            # the degree in use; the others are copied beside the step (on
+            # their own stream, joined before the step ends)
+            copy_plan = [[(p["sh"][:k_used], host["sh"][:k_used])], geo, []]
+            late_plan = [(p["sh"][k_used:], host["sh"][k_used:])]
+        else:
+            nh = host["sh"].shape[0] // 2
+            copy_plan = [[(p["sh"][:nh], host["sh"][:nh])], [(p["sh"][nh:], host["sh"][nh:])], geo]
+        late_stream = torch.cuda.Stream(device=dev)
 
         def e2e_body(upload_params):
             cur = torch.cuda.current_stream()
             if upload_params:
+                if late_plan:
+                    late_stream.wait_stream(cur)
+                    with torch.cuda.stream(late_stream):
+                        for dst, src in late_plan:
+                            dst.copy_(src, non_blocking=True)
                 for cs, plan in zip(copy_streams, copy_plan):
                     cs.wait_stream(cur)
                     with torch.cuda.stream(cs):
@@ -1022,6 +1036,8 @@ def main():
             r.render_bwd(p)
             gs.gs_scale_reset(ls_work, 0.2)
             out_loss.copy_(r.loss_dev, non_blocking=True)
+            if upload_params and late_plan:
+                cur.wait_stream(late_stream)
 
         def run_e2e(upload_params, graph=True):
             """Every step: the copies in from pinned host memory, the step and
