@@ -34,11 +34,13 @@ def long_lists():
     return scene, cams, targets, prm, L, views, grads, dC, dH
 
 
-@pytest.mark.parametrize("ppt,persistent", [(1, 0), (2, 0), (4, 0), (2, 152 * 4)])
-def test_batch128_matches_batch256_and_the_oracle(long_lists, ppt, persistent):
+@pytest.mark.parametrize("ppt,persistent,sh_layout", [(1, 0, 0), (2, 0, 1), (4, 0, 0),
+                                                       (2, 152 * 4, 1)])
+def test_batch128_matches_batch256_and_the_oracle(long_lists, ppt, persistent, sh_layout):
     scene, cams, targets, prm, L, views, grads, dC, dH = long_lists
     N = scene["means"].shape[0]
-    kw = dict(target=targets, dL_dimage=dC, dL_dentropy=dH, ppt=ppt, persistent=persistent)
+    kw = dict(target=targets, dL_dimage=dC, dL_dentropy=dH, ppt=ppt, persistent=persistent,
+              sh_layout=sh_layout)
     g = run_gpu(scene, cams, prm, batch=128, **kw)
     ref = run_gpu(scene, cams, prm, batch=256, **kw)
     lengths = np.diff(g["ranges"], axis=1)

@@ -48,16 +48,18 @@ def test_tile8_pixels_loss_and_gradients(cfg1_tile8):
     check_grads(g, grads, views, cams, N, 1)
 
 
-@pytest.mark.parametrize("ppt,persistent", [(1, 0), (2, 152 * 8)])
-def test_tile8_launch_forms_and_uneven_views(ppt, persistent):
+@pytest.mark.parametrize("ppt,persistent,sh_layout", [(1, 0, 0), (2, 152 * 8, 1)])
+def test_tile8_launch_forms_and_uneven_views(ppt, persistent, sh_layout):
     # views whose sizes are not multiples of 8, one pixel per thread or a
-    # persistent grid over the list-length queue
+    # persistent grid over the list-length queue (with the SH coefficients
+    # in layout 1)
     sizes = [(61, 45), (130, 97), (256, 200)]
     cams = scenes.yaw_cameras(sizes, [0.0, 7.0, -9.0])
     scene = scenes.box_scene(4_000, seed=11)
     targets = scenes.noise_targets(cams, 12)
     prm = scenes.params(tile=8)
-    L, views, grads, g = _case(scene, cams, targets, prm, ppt=ppt, persistent=persistent)
+    L, views, grads, g = _case(scene, cams, targets, prm, ppt=ppt, persistent=persistent,
+                               sh_layout=sh_layout)
     N = scene["means"].shape[0]
     check_lists(g, views, cams, N)
     check_pixels(g, views, cams, N)
