@@ -322,16 +322,17 @@ class _Rasterize(torch.autograd.Function):
     the same Rasterizer raises instead of using the newer forward's state."""
 
     @staticmethod
-    def forward(ctx, means, log_scales, quats, opacity_logits, sh, rast):
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, rast, sh_layout):
         p = {"means": means.contiguous(), "log_scales": log_scales.contiguous(),
              "quats": quats.contiguous(), "opacity_logits": opacity_logits.contiguous(),
-             "sh": sh.contiguous()}
+             "sh": sh.contiguous(), "sh_layout": sh_layout}
         rast.preprocess(p)
         rast.bin_sort()
         rast.render_fwd()
         rast.forward_count += 1
         ctx.rast = rast
         ctx.forward_id = rast.forward_count
+        ctx.sh_layout = sh_layout
         ctx.save_for_backward(*[p[k] for k in PARAM_KEYS])
         return rast.image.clone(), rast.entropy.clone()
 
@@ -343,17 +344,21 @@ class _Rasterize(torch.autograd.Function):
                                "differentiated; its saved lists belong to the newer call (use one "
                                "Rasterizer per live graph)")
         p = dict(zip(PARAM_KEYS, ctx.saved_tensors))
+        p["sh_layout"] = ctx.sh_layout
         g_image = g_image.contiguous() if g_image is not None else torch.zeros_like(rast.image)
         g_entropy = g_entropy.contiguous() if g_entropy is not None else None
         g = rast.render_bwd(p, g_image, g_entropy)
         return (g["means"].clone(), g["log_scales"].clone(), g["quats"].clone(),
-                g["opacity_logits"].clone(), g["sh"].clone(), None)
+                g["opacity_logits"].clone(), g["sh"].clone(), None, None)
 
 
 def rasterize(params, rast):
-    """Differentiable render: returns (image [sum HW, 3], entropy [sum HW])."""
+    """Differentiable render: returns (image [sum HW, 3], entropy [sum HW]).
+    The SH coefficients are in params["sh_layout"] (0 when absent), their
+    gradient in the same layout."""
     return _Rasterize.apply(params["means"], params["log_scales"], params["quats"],
-                            params["opacity_logits"], params["sh"], rast)
+                            params["opacity_logits"], params["sh"], rast,
+                            int(params.get("sh_layout", 0)))
 
 
 class _L1Entropy(torch.autograd.Function):

@@ -25,26 +25,30 @@ def _scene():
     return scene, cams, targets, prm
 
 
-def _loss_and_grads(scene, cams, targets, prm, backward=True):
+def _loss_and_grads(scene, cams, targets, prm, backward=True, sh_layout=0):
     import torch
     from paper_2603_09277_gb300.rasterize import (PARAM_KEYS, Rasterizer, l1_entropy_loss,
                                                   rasterize, scene_to_device, targets_to_device)
     n = scene["means"].shape[0]
     r = Rasterizer(cams, prm, n, sh_stride=scene["sh"].shape[1])
-    p = scene_to_device(scene, requires_grad=True)
+    p = scene_to_device(scene, requires_grad=True, sh_layout=sh_layout)
     img, ent = rasterize(p, r)
     loss = l1_entropy_loss(img, ent, targets_to_device(targets), r, GAMMA)
     if backward:
         loss.backward()
     torch.cuda.synchronize()
-    return float(loss.item()), {k: (p[k].grad.detach().cpu().numpy() if backward else None)
-                                for k in PARAM_KEYS}, r
+
+    def grad(k):  # the SH gradient back in [N][K][3]
+        t = p[k].grad.detach()
+        return (t.transpose(0, 1) if k == "sh" and sh_layout == 1 else t).cpu().numpy()
+    return float(loss.item()), {k: (grad(k) if backward else None) for k in PARAM_KEYS}, r
 
 
-def test_autograd_gradients_match_the_oracle():
+@pytest.mark.parametrize("sh_layout", [0, 1])
+def test_autograd_gradients_match_the_oracle(sh_layout):
     scene, cams, targets, prm = _scene()
     L, _, ora, _ = oracle.step(scene, cams, targets, prm, GAMMA)
-    loss, grads, _ = _loss_and_grads(scene, cams, targets, prm)
+    loss, grads, _ = _loss_and_grads(scene, cams, targets, prm, sh_layout=sh_layout)
     assert loss == pytest.approx(L, rel=1e-5)
     n = scene["means"].shape[0]
     K = (prm["sh_degree"] + 1) ** 2
